@@ -1,0 +1,381 @@
+"""Seeded synthetic problem generators (inputs only: nothing of the method).
+
+Every workload of the augmented HOC method is a clamped problem
+    -Laplace(alpha * Laplace u) = f   in a box                    (Sec. 2, Eq. 1, beta = 0)
+    u = g_D on the whole boundary, u_n = g_N on every face        (Eq. 2, fully clamped)
+whose data are manufactured analytically from an exact u and a coefficient
+alpha.  This module turns such a definition into sampled arrays in the layout
+the C ABI uses; both the CUDA path and the CPU oracle consume them.  It holds
+no discrete operator, no solver step and nothing else of the method.
+
+Layouts (shared convention of the library's boundary):
+  * full-grid arrays have (N_a + 1) points per axis a, x fastest; numpy shape
+    is therefore reversed: (N_z+1, N_y+1, N_x+1) in 3D, (N_y+1, N_x+1) in 2D;
+  * face arrays (g_N, lapt_gD, Q) list the relative-interior points of the
+    faces in the order x-, x+, y-, y+, z-, z+; within a face the remaining
+    axes keep the same order (lowest axis fastest).
+
+The random coefficient fields follow a fixed recipe: phi(x) is a sum of M
+cosines cos(2 pi k_m . x + theta_m) with integer wave vectors 0 <= k_m,a <= K
+(k_m != 0), amplitudes c_m ~ U(-1, 1) and phases theta_m ~ U(0, 2 pi) drawn
+from numpy's default_rng(seed); phi is normalised by its maximum modulus on a
+fixed lattice (1025 points per axis in 2D, 129 in 3D) so that the coefficient
+does not depend on the solve resolution, and alpha = 1 + A * phi / max|phi|.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import sympy as sp
+
+X = sp.symbols("x y z", real=True)
+
+__all__ = [
+    "Problem", "fourier_alpha", "config_problem", "sample", "face_sizes",
+    "n_gamma", "CONFIGS",
+]
+
+
+# ----------------------------------------------------------------------------
+# coefficient fields
+# ----------------------------------------------------------------------------
+
+def fourier_modes(dim: int, M: int, K: int, seed: int):
+    """Draw the M Fourier modes of a seeded smooth random field."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    for _ in range(M):
+        while True:
+            k = rng.integers(0, K + 1, size=dim)
+            if np.any(k != 0):
+                break
+        c = rng.uniform(-1.0, 1.0)
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        modes.append((tuple(int(v) for v in k), float(c), float(th)))
+    return modes
+
+
+def fourier_alpha(dim: int, M: int, K: int, A: float, seed: int) -> sp.Expr:
+    """alpha = 1 + A * phi / max|phi| with phi a seeded sum of M cosines."""
+    modes = fourier_modes(dim, M, K, seed)
+    xs = X[:dim]
+    phi = sum(sp.Float(c) * sp.cos(2 * sp.pi * sum(int(k[a]) * xs[a] for a in range(dim)) + sp.Float(th))
+              for k, c, th in modes)
+    L = 1024 if dim == 2 else 128
+    t = np.linspace(0.0, 1.0, L + 1)
+    grids = np.meshgrid(*([t] * dim), indexing="ij")
+    val = np.zeros_like(grids[0])
+    for k, c, th in modes:
+        val += c * np.cos(2 * np.pi * sum(k[a] * grids[a] for a in range(dim)) + th)
+    mx = float(np.max(np.abs(val)))
+    return 1 + sp.Float(A) * phi / sp.Float(mx)
+
+
+# ----------------------------------------------------------------------------
+# problem definitions
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    """A clamped problem: exact u (optional), alpha, and data overrides.
+
+    f defaults to -Laplace(alpha * Laplace u) applied analytically; g_D, g_N,
+    the tangential Laplacian of g_D on faces and alpha*Laplace(u) on edges and
+    corners default to the exact u's traces.  Problems without an exact
+    solution (the cavity, the plate) give their data explicitly.
+    """
+
+    name: str
+    dim: int
+    alpha: sp.Expr
+    u: Optional[sp.Expr] = None
+    f_grid: Optional[Callable] = None          # f_grid(N, lo, hi) -> full-grid array
+    gN_face: Optional[Callable] = None         # gN_face(axis, side, coords) -> values
+    lo: Tuple[float, ...] = (0.0, 0.0, 0.0)
+    hi: Tuple[float, ...] = (1.0, 1.0, 1.0)
+    note: str = ""
+
+    def exprs(self) -> Dict[str, sp.Expr]:
+        xs = X[: self.dim]
+        out = {"alpha": self.alpha}
+        if self.u is not None:
+            u = self.u
+            lap = sum(sp.diff(u, v, 2) for v in xs)
+            w = self.alpha * lap
+            out["u"] = u
+            out["lap"] = lap
+            out["v"] = w
+            out["f"] = -sum(sp.diff(w, v, 2) for v in xs)
+            for a, v in enumerate(xs):
+                out[f"du{a}"] = sp.diff(u, v)
+                out[f"d2u{a}"] = sp.diff(u, v, 2)
+        return out
+
+
+def _sinsq(v):
+    return sp.sin(sp.pi * v) ** 2
+
+
+def config_problem(name: str) -> Problem:
+    """The named synthetic workloads."""
+    x, y, z = X
+    if name == "cfg1_2d":
+        # 2D, unit square, alpha = 1 + 0.5 sin(2 pi x) sin(2 pi y), u = sin^2 sin^2
+        return Problem(name, 2, 1 + sp.Rational(1, 2) * sp.sin(2 * sp.pi * x) * sp.sin(2 * sp.pi * y),
+                       _sinsq(x) * _sinsq(y))
+    if name == "cfg2_2d":
+        # 2D, alpha = 1 + 0.4 * (8 seeded modes, |k| <= 6), u = sin^2 sin^2 cos(pi x)
+        return Problem(name, 2, fourier_alpha(2, 8, 6, 0.4, 1), _sinsq(x) * _sinsq(y) * sp.cos(sp.pi * x))
+    if name == "cfg3_3d":
+        return Problem(name, 3, fourier_alpha(3, 6, 4, 0.4, 2), _sinsq(x) * _sinsq(y) * _sinsq(z))
+    if name == "cfg4_3d":
+        k = 32
+        u = _sinsq(x) * _sinsq(y) * _sinsq(z) * sp.sin(k * sp.pi * x) * sp.sin(k * sp.pi * y) * sp.sin(k * sp.pi * z)
+        return Problem(name, 3, fourier_alpha(3, 6, 4, 0.5, 3), u)
+    if name == "sincos2d":
+        # nonzero g_D, g_N, tangential Laplacian and corner v: exercises every data term
+        return Problem(name, 2, 1 + x ** 2 + y ** 2, sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)))
+    if name == "sincos3d":
+        return Problem(name, 3, 1 + x ** 2 + y ** 2 + z ** 2,
+                       sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)) * sp.sin(2 * z + sp.Rational(1, 2)))
+    if name == "poly2d":
+        # degree-4 polynomial with nonzero data everywhere and constant alpha
+        return Problem(name, 2, sp.Integer(1), x ** 4 + x * y ** 3 - 2 * x ** 2 * y + y + 1)
+    if name == "cavity":
+        # lid-driven cavity streamfunction: f = 0, u = 0, u_y = 1 on y = 1 (Sec. 4, Table 6)
+        def gN(axis, side, coords):
+            return np.ones_like(coords[0]) if (axis == 1 and side == 1) else np.zeros_like(coords[0])
+        return Problem(name, 2, sp.Integer(1), None, f_grid=_zero_f, gN_face=gN)
+    if name == "plate":
+        # clamped plate under a unit central load; the library solves -Lap^2 u = f, so f = -load.
+        return Problem(name, 2, sp.Integer(1), None, f_grid=_plate_f, gN_face=_zero_gN,
+                       note="trapezoid-weighted 3x3 load of total mass 1")
+    raise KeyError(name)
+
+
+def _zero_f(N, lo, hi):
+    return np.zeros(tuple(n + 1 for n in reversed(N)))
+
+
+def _zero_gN(axis, side, coords):
+    return np.zeros_like(coords[0])
+
+
+def _plate_f(N, lo, hi):
+    """-(unit load) spread over the 3x3 grid points around the centre.
+
+    The load density is 1/(4h^2) on |x-1/2| <= h, |y-1/2| <= h; the nine grid
+    points of that closed square get trapezoid weights (1, 1/2, 1/4) so that
+    the discrete load h^2 * sum f is exactly 1.
+    """
+    Nx, Ny = N
+    assert Nx % 2 == 0 and Ny % 2 == 0
+    hx = (hi[0] - lo[0]) / Nx
+    hy = (hi[1] - lo[1]) / Ny
+    f = np.zeros((Ny + 1, Nx + 1))
+    cx, cy = Nx // 2, Ny // 2
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            w = (0.5 if di else 1.0) * (0.5 if dj else 1.0)
+            f[cy + dj, cx + di] = -w / (4.0 * hx * hy)
+    return f
+
+
+CONFIGS = {
+    "cfg1_2d": dict(dim=2, Ns=[64]),
+    "cfg2_2d": dict(dim=2, Ns=[256, 512, 1024, 2048, 4096]),
+    "cfg3_3d": dict(dim=3, Ns=[256, 512]),
+    "cfg4_3d": dict(dim=3, Ns=[1024]),
+}
+
+
+# ----------------------------------------------------------------------------
+# sampling
+# ----------------------------------------------------------------------------
+
+def face_sizes(N: Sequence[int]) -> List[int]:
+    """Number of relative-interior points of each face, in face order."""
+    d = len(N)
+    out = []
+    for a in range(d):
+        s = 1
+        for b in range(d):
+            if b != a:
+                s *= N[b] - 1
+        out += [s, s]
+    return out
+
+
+def n_gamma(N: Sequence[int]) -> int:
+    return sum(face_sizes(N))
+
+
+_TORCH_MAP = None
+
+
+def _lamb(expr, dim, backend):
+    xs = X[:dim]
+    if backend == "numpy":
+        return sp.lambdify(xs, expr, modules="numpy", cse=True)
+    import torch
+    global _TORCH_MAP
+    if _TORCH_MAP is None:
+        _TORCH_MAP = {"sin": torch.sin, "cos": torch.cos, "exp": torch.exp, "sqrt": torch.sqrt,
+                      "pi": math.pi, "E": math.e}
+    return sp.lambdify(xs, expr, modules=[_TORCH_MAP], cse=True)
+
+
+def _coords(N, lo, hi, dim):
+    return [lo[a] + (hi[a] - lo[a]) * np.arange(N[a] + 1) / N[a] for a in range(dim)]
+
+
+def _eval_full(fn, N, lo, hi, dim, backend, device, chunk_pts=1 << 24):
+    """Evaluate fn on the full (N+1)^d grid, chunked over the slowest axis."""
+    c = _coords(N, lo, hi, dim)
+    shape = tuple(N[a] + 1 for a in reversed(range(dim)))
+    if backend == "numpy":
+        out = np.empty(shape)
+        plane = int(np.prod(shape[1:]))
+        step = max(1, chunk_pts // plane)
+        for s in range(0, shape[0], step):
+            e = min(shape[0], s + step)
+            sl = [c[a] for a in range(dim)]
+            sl[dim - 1] = c[dim - 1][s:e]
+            g = np.meshgrid(*reversed(sl), indexing="ij")  # slowest first
+            args = list(reversed(g))
+            out[s:e] = np.broadcast_to(fn(*args), g[0].shape)
+        return out
+    import torch
+    out = torch.empty(shape, dtype=torch.float64, device=device)
+    tc = [torch.tensor(v, dtype=torch.float64, device=device) for v in c]
+    plane = int(np.prod(shape[1:]))
+    step = max(1, chunk_pts // plane)
+    for s in range(0, shape[0], step):
+        e = min(shape[0], s + step)
+        sl = list(tc)
+        sl[dim - 1] = tc[dim - 1][s:e]
+        g = torch.meshgrid(*reversed(sl), indexing="ij")
+        args = list(reversed(g))
+        val = fn(*args)
+        if not torch.is_tensor(val):
+            val = torch.full(g[0].shape, float(val), dtype=torch.float64, device=device)
+        out[s:e] = val
+    return out
+
+
+def face_coords(N, lo, hi, axis, side):
+    """Coordinates (one array per axis) of a face's relative-interior points."""
+    dim = len(N)
+    c = _coords(N, lo, hi, dim)
+    rest = [b for b in range(dim) if b != axis]
+    g = np.meshgrid(*[c[b][1:-1] for b in reversed(rest)], indexing="ij")
+    g = list(reversed(g))  # g[i] varies along rest[i]; rest[0] fastest
+    out = [None] * dim
+    for i, b in enumerate(rest):
+        out[b] = g[i].reshape(-1)
+    n = out[rest[0]].size
+    out[axis] = np.full(n, c[axis][0] if side == 0 else c[axis][-1])
+    return out
+
+
+def _edge_mask(N, dim):
+    shape = tuple(N[a] + 1 for a in reversed(range(dim)))
+    cnt = np.zeros(shape, dtype=np.int8)
+    for a in range(dim):
+        idx = [slice(None)] * dim
+        ax = dim - 1 - a
+        idx[ax] = 0
+        cnt[tuple(idx)] += 1
+        idx[ax] = N[a]
+        cnt[tuple(idx)] += 1
+    return cnt
+
+
+def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "numpy",
+           device=None, with_exact: bool = True) -> Dict[str, object]:
+    """Sample a problem on a grid with N[a] intervals per axis.
+
+    Returns full-grid arrays alpha, f, g_D (boundary values of u; interior
+    entries 0), v_edge (alpha * Laplace u at edge and corner points; 0
+    elsewhere), face arrays g_N (outward normal derivative) and lapt_gD (sum of
+    the tangential second derivatives of g_D), and, when the problem has one,
+    the exact u and v = alpha * Laplace u on the full grid.  ``backend`` is
+    "numpy" (host float64) or "torch" (float64 tensors on ``device``); face
+    arrays are always computed on the host and converted.
+    """
+    dim = prob.dim
+    N = [int(n) for n in N]
+    lo = tuple(lo) if lo is not None else prob.lo[:dim]
+    hi = tuple(hi) if hi is not None else prob.hi[:dim]
+    ex = prob.exprs()
+    out: Dict[str, object] = {"dim": dim, "N": N, "lo": lo, "hi": hi, "name": prob.name}
+
+    def full(key):
+        return _eval_full(_lamb(ex[key], dim, backend), N, lo, hi, dim, backend, device)
+
+    out["alpha"] = full("alpha")
+    if prob.f_grid is not None:
+        f = prob.f_grid(N, lo, hi)
+        out["f"] = f if backend == "numpy" else _to_t(f, device)
+    else:
+        out["f"] = full("f")
+
+    # boundary data from exact u (host side; boundary-only sizes)
+    fs = []
+    gN = []
+    lapt = []
+    for a in range(dim):
+        for side in (0, 1):
+            pc = face_coords(N, lo, hi, a, side)
+            fs.append(pc[0].size)
+            if prob.u is not None:
+                du = _lamb(ex[f"du{a}"], dim, "numpy")(*pc)
+                val = np.broadcast_to(np.asarray(du, dtype=float), pc[0].shape).copy()
+                gN.append(-val if side == 0 else val)
+                lt = np.zeros(pc[0].size)
+                for b in range(dim):
+                    if b != a:
+                        lt += np.broadcast_to(np.asarray(_lamb(ex[f"d2u{b}"], dim, "numpy")(*pc), float), lt.shape)
+                lapt.append(lt)
+            else:
+                gN.append(np.asarray(prob.gN_face(a, side, pc), dtype=float))
+                lapt.append(np.zeros(pc[0].size))
+    gN = np.concatenate(gN)
+    lapt = np.concatenate(lapt)
+
+    cnt = _edge_mask(N, dim)
+    if prob.u is not None:
+        u_full = full("u")
+        v_full = full("v")
+        if backend == "numpy":
+            bmask = cnt > 0
+            gD = np.where(bmask, u_full, 0.0)
+            vE = np.where(cnt >= 2, v_full, 0.0)
+        else:
+            import torch
+            cm = torch.from_numpy(cnt).to(device)
+            gD = torch.where(cm > 0, u_full, torch.zeros_like(u_full))
+            vE = torch.where(cm >= 2, v_full, torch.zeros_like(v_full))
+        if with_exact:
+            out["u_exact"] = u_full
+            out["v_exact"] = v_full
+        else:
+            del u_full, v_full
+    else:
+        z = np.zeros(tuple(n + 1 for n in reversed(N)))
+        gD = z if backend == "numpy" else _to_t(z, device)
+        vE = z.copy() if backend == "numpy" else _to_t(z, device)
+    out["g_D"] = gD
+    out["v_edge"] = vE
+    out["g_N"] = gN if backend == "numpy" else _to_t(gN, device)
+    out["lapt_gD"] = lapt if backend == "numpy" else _to_t(lapt, device)
+    return out
+
+
+def _to_t(a, device):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
