@@ -1,0 +1,329 @@
+"""Benchmark: biharmonic DOF/s to a fixed error on one or more B300s.
+
+A step is one whole solve (Algorithm 1: Schur right-hand side, GMRES on the
+Schur system to relative residual 1e-12, recovery of V and U) of the 2D
+variable-coefficient clamped problem on a 4096 x 4096 grid (coefficient
+1 + 0.4 * 8 seeded Fourier modes, u = sin^2(pi x) sin^2(pi y) cos(pi x)),
+FP64 throughout.  DOF = interior unknowns (N-1)^2 per solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun) solve independent replicas, one per rank (the
+solve does not shard on this pool: every box has one GPU); value is the sum
+over ranks.  The reference arm times the CPU oracle (assembled coupled
+system + SuperLU) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "biharmonic DOF/s to fixed error"
+UNIT = "DOF/s"
+FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of a B300 (no FP64 tensor path is used)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def dst_flops_per_line(N: int) -> float:
+    """FP64 flops one DST-I line of the x-kernel executes (FMA = 2 flops).
+
+    pre-processing 8 per pair (N/2 pairs); radix-2 stage 4 per butterfly;
+    radix-4 stage 34 per butterfly (16 without twiddles in the first stage);
+    post-processing 14 per pair (M/2 pairs); prefix sum ~2 per odd output;
+    output scaling 1 per element.
+    """
+    M = N // 2
+    logM = int(round(math.log2(M)))
+    f = 8 * (N // 2)
+    stages = []
+    ns = 1
+    if logM % 2:
+        f += 4 * (M // 2)
+        ns = 2
+    while ns < M:
+        f += (34 if ns > 1 else 16) * (M // 4)
+        ns *= 4
+    f += 14 * (M // 2) + 2 * M + N
+    return float(f)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            sm.sort()
+            out["sm_mhz"] = sm[len(sm) // 2]
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+_SAMPLES = {}
+
+
+def cpu_oracle_sample(N_cpu: int):
+    """Time the CPU oracle (assembly + SuperLU) on cfg2 at N_cpu; returns (DOF/s, seconds, err).
+
+    The synthetic inputs are generated once, outside the timed region."""
+    import numpy as np
+
+    from oracle import coupled
+    from paper_2609_16478_b300 import inputs
+
+    if N_cpu not in _SAMPLES:
+        _SAMPLES[N_cpu] = inputs.sample(inputs.config_problem("cfg2_2d"), [N_cpu, N_cpu])
+    d = _SAMPLES[N_cpu]
+    t0 = time.perf_counter()
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    dt = time.perf_counter() - t0
+    err = float(np.max(np.abs(sol.U - d["u_exact"])))
+    return (N_cpu - 1) ** 2 / dt, dt, err
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    N_cpu = args.cpu_n
+    for _ in range(args.warmup):
+        cpu_oracle_sample(N_cpu)
+    t0 = time.perf_counter()
+    errs = []
+    for _ in range(args.steps):
+        _, _, e = cpu_oracle_sample(N_cpu)
+        errs.append(e)
+    dt = time.perf_counter() - t0
+    value = args.steps * (N_cpu - 1) ** 2 / dt
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D variable-coefficient clamped biharmonic (cfg2), oracle sample N=%d" % N_cpu,
+                   "dim": 2, "N": N_cpu, "err_inf_vs_exact": max(errs)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "direct solve of the assembled coupled system at N=%d per step "
+                                   "(SuperLU, single-threaded; %d host cores visible)" % (N_cpu, cores)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2609_16478_b300 import ahoc, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N = args.n
+    dim = 2
+    prob = inputs.config_problem("cfg2_2d")
+    data = inputs.sample(prob, [N, N], backend="torch", device=dev)
+    plan = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters)
+    f = data["f"].reshape(-1).contiguous()
+    u = torch.empty_like(f)
+    st = plan.stream
+    dof = (N - 1) ** dim
+
+    for _ in range(args.warmup):
+        _, info = plan.solve(f, u, tol=args.tol)
+    torch.cuda.synchronize()
+    err = float((u.reshape(N + 1, N + 1) - data["u_exact"]).abs().max())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # device-resident timed region
+    infos = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            _, info = plan.solve(f, u, tol=args.tol)
+            infos.append(info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty(f.numel(), dtype=torch.float64).pin_memory()
+    f_dev = torch.empty_like(f)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            f_dev.copy_(f_host, non_blocking=True)
+        plan.solve(f_dev, u, tol=args.tol)
+        with torch.cuda.stream(st):
+            u_host.copy_(u, non_blocking=True)
+        st.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+
+    value = world * args.steps * dof / (ms / 1e3)
+    e2e_value = world * args.steps * dof / (e2e_ms / 1e3)
+    launches = sum(i["launches"] for i in infos)
+    kms = {k: sum(i["kernel_ms"][k] for i in infos) for k in ahoc.KERNEL_NAMES}
+    kn = {k: sum(i["kernel_launches"][k] for i in infos) for k in ahoc.KERNEL_NAMES}
+    top = max(kms, key=lambda k: kms[k])
+    avg_ms = kms["dst_x"] / max(1, kn["dst_x"])
+    flops = dst_flops_per_line(N) * (N - 1)          # one launch transforms N-1 lines of N
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    roof = {"kernel": "k_dst_x<double> (DST-I along x, FP64)", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "nominal B300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+            "traffic": None, "avg_launch_ms": avg_ms, "launches": kn["dst_x"],
+            "algorithmic_bytes_per_launch": 16 * N * (N - 1), "flops_per_launch": flops,
+            "hbm_achieved_GBs": 16 * N * (N - 1) / (avg_ms / 1e3) / 1e9,
+            "hbm_peak_GBs": _peaks().get("hbm_gbs"),
+            "share_of_step": kms["dst_x"] / sum(kms.values()), "top_kernel_by_time": top}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, _ = cpu_oracle_sample(args.cpu_n)
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "direct solve (assembly + SuperLU) of the same workload at N=%d, %.1f s; "
+                         "single-threaded, %d host cores visible" % (args.cpu_n, dt, cores)}
+    nbytes = f.numel() * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D variable-coefficient clamped biharmonic (cfg2) N=%d, FP64, GMRES tol %g"
+                               % (N, args.tol),
+                   "dim": dim, "N": N, "dof_per_solve": dof, "tol": args.tol,
+                   "gmres_iters": infos[-1]["iters"], "err_inf_vs_exact": err,
+                   "rel_resid": infos[-1]["rel_resid"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set (two 134 MB fields + coefficient/data arrays) larger than L2; no flush"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--restart", type=int, default=300)
+    ap.add_argument("--max-iters", type=int, default=2000)
+    ap.add_argument("--cpu-n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * ahoc.h -- C ABI of the matrix-free augmented high-order compact (HOC)
+ * solver for clamped, variable-coefficient biharmonic problems
+ *
+ *     -Laplace(alpha * Laplace u) = f        in a box (d = 2, 3)       (Sec. 2, Eq. 1, beta = 0)
+ *     u = g_D on the boundary,  u_n = g_N on every face                 (Eq. 2, fully clamped)
+ *
+ * discretised by the compact fourth-order scheme of Sec. 2.2 (mixed form
+ * v = alpha Laplace u, 9-point / 19-point L_h, weighting M, one-sided second
+ * normal derivative with the augmented unknowns Q = v on the face interiors),
+ * and solved by the Schur-complement method of Sec. 2.3: GMRES on S_h Q = b
+ * with the matrix-free action S_h Q = R(Q) - R(0), b = -R(0) of Lemma 1, each
+ * action running two Dirichlet HOC Poisson solves (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      N[a] intervals along axis a (x = 0, y = 1, z = 2), N[a] a power of
+ *           two with 8 <= N[a] <= 4096, spacing h_a = (hi[a] - lo[a]) / N[a].
+ * Full grid arrays hold (N[0]+1) x ... x (N[d-1]+1) doubles, x fastest.
+ * Interior arrays hold (N[0]-1) x ... x (N[d-1]-1) doubles, x fastest.
+ * Face arrays (g_N, lapt_gD, Q, y) hold the relative-interior points of the
+ *           faces in the order x-, x+, y-, y+, z-, z+; within a face the
+ *           remaining axes keep their order, lowest axis fastest.  Their
+ *           length is n_gamma = sum over faces of prod_{b != a} (N[b] - 1).
+ * Memory    every array pointer is DEVICE memory owned by the caller unless
+ *           stated otherwise; the library never frees caller memory.
+ * Streams   all work is enqueued on the plan's CUDA stream; calls return
+ *           once the work is enqueued, except where stated.
+ * Errors    every call returns an ahoc_status; no call aborts, throws or
+ *           prints.  ahoc_last_error() gives a one-line description of the
+ *           most recent failure on the calling thread.
+ */
+#ifndef AHOC_H
+#define AHOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AHOC_OK = 0,
+  AHOC_EINVAL = 1,        /* bad argument (checked before any allocation or launch) */
+  AHOC_ENOMEM = 2,        /* device allocation failed, or caller workspace too small */
+  AHOC_ECUDA = 3,         /* a CUDA runtime call failed */
+  AHOC_ENOCONV = 4,       /* GMRES reached max_iters; outputs hold the best iterate */
+  AHOC_ENUMERIC = 5,      /* NaN or Inf met in a residual norm */
+  AHOC_ETIMEOUT = 6,      /* reserved: a bounded device wait ran out */
+  AHOC_EUNSUPPORTED = 7,  /* valid request outside what this build supports */
+  AHOC_EINTERNAL = 8
+} ahoc_status;
+
+typedef enum { AHOC_FP64 = 0, AHOC_MIXED = 1 } ahoc_precision;
+
+/* Kernel classes reported by ahoc_info when opts.timing is set. */
+enum {
+  AHOC_K_DST_X = 0,   /* DST-I along x (Sec. 2.3 fast solver)            */
+  AHOC_K_DST_Y = 1,   /* DST-I along y (3D)                              */
+  AHOC_K_TRI = 2,     /* tridiagonal solve along the last axis           */
+  AHOC_K_VRHS = 3,    /* v-equation right-hand side                      */
+  AHOC_K_URHS = 4,    /* u-equation right-hand side M(V/alpha)           */
+  AHOC_K_TRACE = 5,   /* boundary residual R (Lemma 1)                   */
+  AHOC_K_KRYLOV = 6,  /* GMRES dot products, updates                     */
+  AHOC_K_OTHER = 7,   /* layout conversion, output                       */
+  AHOC_NK = 8
+};
+
+typedef struct ahoc_plan ahoc_plan;  /* opaque; created and owned by the library */
+
+/* Boundary data (Sec. 2, Eq. 2; Lemma 1).  Device pointers, NULL = zero.
+ * They are copied into the plan at creation; the caller may free them after. */
+typedef struct {
+  const double* g_D;     /* full grid; only boundary entries are read: u on the boundary        */
+  const double* g_N;     /* face array: outward normal derivative of u on the face interiors     */
+  const double* lapt_gD; /* face array: sum of the tangential second derivatives of g_D          */
+  const double* v_edge;  /* full grid; only edge and corner entries are read: alpha * Laplace u,
+                            known there from g_D by tangential differentiation (Remark, Sec. 2.2) */
+} ahoc_bdata;
+
+/* Options; a NULL pointer selects the defaults given in brackets. */
+typedef struct {
+  ahoc_precision prec;    /* [AHOC_FP64] arithmetic of the Poisson solves                      */
+  int max_iters;          /* [500] total GMRES iterations allowed                               */
+  int restart;            /* [100] Krylov basis size before a restart (the paper's GMRES is not
+                             restarted; the cap only bounds memory)                            */
+  int precond;            /* [0] reserved for a boundary preconditioner; must be 0              */
+  double refine_tol;      /* [0] reserved                                                      */
+  int timing;             /* [0] nonzero: time every kernel launch of ahoc_solve with CUDA
+                             events on the plan's stream (ahoc_info.kernel_ms)               */
+  void* workspace;        /* [NULL] caller-owned device workspace of at least
+                             ahoc_workspace_bytes() bytes, 256-byte aligned; NULL lets the
+                             plan allocate its own with cudaMalloc                             */
+  size_t workspace_bytes; /* size of the caller workspace                                      */
+} ahoc_opts;
+
+typedef struct {
+  int iters;              /* GMRES iterations (matrix-vector products) of the last solve        */
+  int restarts;
+  double rel_resid;       /* ||b - S_h Q|| / ||b|| estimated by GMRES at exit                   */
+  double ms_total;        /* wall time of the last ahoc_solve, host clock                       */
+  double ms_matvec;       /* device time of the matvecs of the last solve (CUDA events)         */
+  int64_t launches;       /* kernels this library launched during the last solve                */
+  double kernel_ms[AHOC_NK];      /* with opts.timing: summed device time per kernel class      */
+  int64_t kernel_launches[AHOC_NK];
+} ahoc_info;
+
+/* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:
+ * two interior fields, coefficient and boundary copies, the Krylov basis).
+ * Returns AHOC_EINVAL on a bad shape.  Allocates nothing. */
+ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opts, size_t* bytes);
+
+/* Create a plan (Sec. 2.2 discretisation on the box [lo, hi]).
+ *   dim      2 or 3;  N, lo, hi: host arrays of length dim, lo[a] < hi[a]
+ *   alpha    device, full grid, alpha > 0 (not checked on the device)
+ *   bd       host struct of device pointers (NULL = homogeneous data)
+ *   opts     host struct (NULL = defaults)
+ *   stream   a cudaStream_t (NULL = the legacy default stream)
+ * Precomputes the DST twiddle tables, the per-mode tridiagonal factors of
+ * L_h along the last axis, 1/alpha and the boundary data copies.  Arguments
+ * are checked before any allocation.  On success *out owns the plan. */
+ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo,
+                             const double* hi, const double* alpha, const ahoc_bdata* bd,
+                             const ahoc_opts* opts, void* stream);
+
+/* Solve the discrete problem (Algorithm 1, Main procedure):
+ *   b = -R(0) (ConstructSchurRHS), GMRES on S_h Q = b to relative residual
+ *   tol, then V and U by two Poisson solves with the converged Q.
+ *   f     device, full grid (boundary entries are used by M near the boundary)
+ *   u     device, full grid output; boundary entries = g_D
+ *   tol   relative residual of the Schur system, > 0
+ *   info  host, may be NULL
+ * Synchronises the plan's stream (it reads residual norms) and returns when
+ * u is written.  AHOC_ENOCONV: u holds the solution for the best iterate. */
+ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info);
+
+/* y = S_h q = R(q) - R(0) (Lemma 1; Algorithm 1, SchurMatVec), the
+ * homogeneous part of the boundary residual: V(q) by the v-equation with
+ * zero f and edge data, U(V) by the u-equation with zero g_D, then
+ * y_p = alpha_p * delta_nn U_p - q_p with the one-sided formula of Sec. 2.2.
+ * q, y: device face arrays (n_gamma); may not alias. */
+ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y);
+
+/* b = -R(0) (Lemma 1; Algorithm 1, ConstructSchurRHS) for right-hand side f
+ * (device, full grid); b: device face array. */
+ahoc_status ahoc_schur_rhs(ahoc_plan* p, const double* f, double* b);
+
+/* Copy the augmented unknowns Q of the last successful ahoc_solve into q
+ * (device face array), and, if v is not NULL, V on the full grid (faces =
+ * Q, edges and corners = v_edge) into v.  AHOC_EINVAL before any solve. */
+ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v);
+
+/* Component entry points (the building blocks of SchurMatVec) ------------- */
+
+/* DST-I along axis (0 <= axis < dim - 1) of an interior array:
+ * out_k = scale * sum_{j=1}^{N-1} in_j sin(pi j k / N), all other indices
+ * fixed (the sine expansion of Lemma 4).  in, out: device interior arrays;
+ * they may alias. */
+ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, double scale);
+
+/* Dirichlet HOC Poisson solve (the FFT-based solver of Algorithm 1):
+ * L_h w = rhs at interior points, w = 0 on the boundary.  rhs, w: device
+ * interior arrays; they may alias. */
+ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w);
+
+ahoc_status ahoc_plan_destroy(ahoc_plan* p);
+
+/* Static strings; never NULL. */
+const char* ahoc_status_string(ahoc_status s);
+const char* ahoc_last_error(void);
+
+/* Length of the face arrays of a plan. */
+int64_t ahoc_n_gamma(const ahoc_plan* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AHOC_H */

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the C ABI in ``include/ahoc.h`` (argument marshalling only).
+
+Every array argument is a CUDA float64 tensor whose ``data_ptr()`` is passed
+straight to the library; work runs on the plan's stream (by default torch's
+current stream at plan creation).  Nothing here computes: there is no CPU or
+PyTorch fallback, and :func:`lib` raises if the shared library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libahoc.so")
+
+AHOC_OK, AHOC_EINVAL, AHOC_ENOMEM, AHOC_ECUDA, AHOC_ENOCONV, AHOC_ENUMERIC, AHOC_ETIMEOUT, \
+    AHOC_EUNSUPPORTED, AHOC_EINTERNAL = range(9)
+AHOC_FP64, AHOC_MIXED = 0, 1
+
+# every entry point declared in include/ahoc.h
+SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
+           "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
+           "ahoc_last_error", "ahoc_n_gamma")
+
+
+class ahoc_bdata(C.Structure):
+    _fields_ = [("g_D", C.c_void_p), ("g_N", C.c_void_p), ("lapt_gD", C.c_void_p), ("v_edge", C.c_void_p)]
+
+
+AHOC_NK = 8
+KERNEL_NAMES = ("dst_x", "dst_y", "tri", "vrhs", "urhs", "trace", "krylov", "other")
+
+
+class ahoc_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
+                ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class ahoc_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("rel_resid", C.c_double),
+                ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("launches", C.c_int64),
+                ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK)]
+
+
+class AhocError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(what)
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree ``libahoc.so`` (build it with ``python -m paper_2609_16478_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libahoc.so not built: run `python -m paper_2609_16478_b300.build` (no fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    i64p = C.POINTER(C.c_int64)
+    dp = C.POINTER(C.c_double)
+    L.ahoc_workspace_bytes.argtypes = [C.c_int, i64p, C.POINTER(ahoc_opts), C.POINTER(C.c_size_t)]
+    L.ahoc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, i64p, dp, dp, C.c_void_p,
+                                   C.POINTER(ahoc_bdata), C.POINTER(ahoc_opts), C.c_void_p]
+    L.ahoc_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
+    L.ahoc_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ahoc_schur_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ahoc_last_qv.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ahoc_dst1.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double]
+    L.ahoc_poisson.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ahoc_plan_destroy.argtypes = [C.c_void_p]
+    L.ahoc_status_string.argtypes = [C.c_int]
+    L.ahoc_status_string.restype = C.c_char_p
+    L.ahoc_last_error.argtypes = []
+    L.ahoc_last_error.restype = C.c_char_p
+    L.ahoc_n_gamma.argtypes = [C.c_void_p]
+    L.ahoc_n_gamma.restype = C.c_int64
+    for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
+                 "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, call: str):
+    if status != AHOC_OK:
+        L = lib()
+        raise AhocError(status, "%s: %s (%s)" % (call, L.ahoc_status_string(status).decode(),
+                                                 L.ahoc_last_error().decode()))
+
+
+def _ptr(t: Optional[torch.Tensor], numel: int, name: str):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA float64 tensor" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return C.c_void_p(t.data_ptr())
+
+
+def _opts(prec, max_iters, restart, precond, workspace=None, timing=0):
+    o = ahoc_opts()
+    o.timing = int(timing)
+    o.prec = prec
+    o.max_iters = max_iters
+    o.restart = restart
+    o.precond = precond
+    o.refine_tol = 0.0
+    if workspace is not None:
+        o.workspace = C.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel()
+    return o
+
+
+def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64) -> int:
+    L = lib()
+    n = (C.c_int64 * dim)(*N)
+    o = _opts(prec, 500, restart, 0)
+    out = C.c_size_t(0)
+    _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
+    return int(out.value)
+
+
+class Plan:
+    """A solver plan for one grid, coefficient and boundary data (``ahoc_plan_create``).
+
+    The device workspace is a torch uint8 tensor handed to the library, so
+    device memory comes from PyTorch's allocator.
+    """
+
+    def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
+                 g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
+                 max_iters: int = 500, restart: int = 100, precond: int = 0, stream=None, timing: bool = False):
+        L = lib()
+        self.dim = dim
+        self.N = [int(n) for n in N]
+        self.lo = list(lo) if lo is not None else [0.0] * dim
+        self.hi = list(hi) if hi is not None else [1.0] * dim
+        self.nfull = 1
+        self.nint = 1
+        for n in self.N:
+            self.nfull *= n + 1
+            self.nint *= n - 1
+        self.ngamma = 0
+        for a in range(dim):
+            s = 1
+            for b in range(dim):
+                if b != a:
+                    s *= self.N[b] - 1
+            self.ngamma += 2 * s
+        self.device = alpha.device
+        nb = workspace_bytes(dim, self.N, restart, prec)
+        self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
+                        _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing)
+        h = C.c_void_p(0)
+        n = (C.c_int64 * dim)(*self.N)
+        lo_ = (C.c_double * dim)(*self.lo)
+        hi_ = (C.c_double * dim)(*self.hi)
+        _check(L.ahoc_plan_create(C.byref(h), dim, n, lo_, hi_, _ptr(alpha, self.nfull, "alpha"), C.byref(bd),
+                                  C.byref(o), C.c_void_p(self.stream.cuda_stream)), "ahoc_plan_create")
+        self._h = h
+        assert L.ahoc_n_gamma(h) == self.ngamma
+
+    # -- Algorithm 1 ---------------------------------------------------------
+    def solve(self, f: torch.Tensor, u: Optional[torch.Tensor] = None, tol: float = 1e-12,
+              check: bool = True) -> (torch.Tensor, Dict):
+        if u is None:
+            u = torch.empty(self.nfull, dtype=torch.float64, device=self.device)
+        info = ahoc_info()
+        st = lib().ahoc_solve(self._h, _ptr(f, self.nfull, "f"), _ptr(u, self.nfull, "u"), float(tol),
+                              C.byref(info))
+        if check:
+            _check(st, "ahoc_solve")
+        return u, dict(iters=info.iters, restarts=info.restarts, rel_resid=info.rel_resid,
+                       ms_total=info.ms_total, ms_matvec=info.ms_matvec, status=st, launches=info.launches,
+                       kernel_ms={k: info.kernel_ms[i] for i, k in enumerate(KERNEL_NAMES)},
+                       kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)})
+
+    def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if y is None:
+            y = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
+        _check(lib().ahoc_matvec(self._h, _ptr(q, self.ngamma, "q"), _ptr(y, self.ngamma, "y")), "ahoc_matvec")
+        return y
+
+    def schur_rhs(self, f: torch.Tensor, b: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if b is None:
+            b = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
+        _check(lib().ahoc_schur_rhs(self._h, _ptr(f, self.nfull, "f"), _ptr(b, self.ngamma, "b")), "ahoc_schur_rhs")
+        return b
+
+    def last_qv(self, with_v: bool = True):
+        q = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
+        v = torch.empty(self.nfull, dtype=torch.float64, device=self.device) if with_v else None
+        _check(lib().ahoc_last_qv(self._h, _ptr(q, self.ngamma, "q"), _ptr(v, self.nfull, "v")), "ahoc_last_qv")
+        return q, v
+
+    # -- components -------------------------------------------------------------
+    def dst1(self, x: torch.Tensor, axis: int, out: Optional[torch.Tensor] = None, scale: float = 1.0):
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().ahoc_dst1(self._h, int(axis), _ptr(x, self.nint, "x"), _ptr(out, self.nint, "out"),
+                               float(scale)), "ahoc_dst1")
+        return out
+
+    def poisson(self, rhs: torch.Tensor, out: Optional[torch.Tensor] = None):
+        if out is None:
+            out = torch.empty_like(rhs)
+        _check(lib().ahoc_poisson(self._h, _ptr(rhs, self.nint, "rhs"), _ptr(out, self.nint, "out")), "ahoc_poisson")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().ahoc_plan_destroy(self._h), "ahoc_plan_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_for(data: Dict, device="cuda", **kw) -> "Plan":
+    """Create a plan from a sampled problem (see ``paper_2609_16478_b300.inputs.sample``)."""
+    def dev(key):
+        v = data.get(key)
+        if v is None:
+            return None
+        t = torch.as_tensor(v, dtype=torch.float64)
+        return t.reshape(-1).contiguous().to(device)
+    return Plan(data["dim"], data["N"], dev("alpha"), lo=data["lo"], hi=data["hi"], g_D=dev("g_D"),
+                g_N=dev("g_N"), lapt_gD=dev("lapt_gD"), v_edge=dev("v_edge"), **kw)

@@ -1,0 +1,58 @@
+// Shared definitions of the augmented HOC library (device + host).
+//
+// Internal field layout ("padded interior"): an array of N0 x N1 (x N2)
+// elements, x fastest, holding grid point (i, j, k) with 1 <= i <= N_a - 1 at
+// offset i + N0 * (j + N1 * k).  The slots with an index 0 are padding and
+// stay zero; along a line they are the zero x_0 of the DST-I input, so every
+// line is N elements long and 16-byte aligned.  In 2D there is one layer
+// k = 0 (no z padding).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ahoc {
+
+constexpr int kMaxN = 4096;
+
+struct Geom {
+  int dim;
+  int N[3];           // intervals per axis (N[2] = 1 in 2D)
+  double h[3];
+  int64_t n0, n1, n2; // padded extents (N0, N1, N2 or 1)
+  int64_t npad;       // n0 * n1 * n2
+  int64_t f0, f1, f2; // full-grid extents N + 1 (f2 = 1 in 2D)
+  int64_t nfull;
+  int64_t face_off[7];
+  int64_t ngamma;
+  int kmin, kmax;     // layers holding interior points: 3D [1, N2), 2D [0, 1)
+  int64_t nint;       // interior points
+
+  __host__ __device__ inline int64_t pad(int i, int j, int k) const { return i + n0 * (j + n1 * (int64_t)k); }
+  __host__ __device__ inline int64_t full(int i, int j, int k) const { return i + f0 * (j + f1 * (int64_t)k); }
+  // index of a face point within the face arrays (axis a on the boundary)
+  __host__ __device__ inline int64_t face(int a, int side, int i, int j, int k) const {
+    int64_t o = face_off[2 * a + side];
+    if (a == 0) return o + (j - 1) + (int64_t)(N[1] - 1) * (dim == 3 ? (k - 1) : 0);
+    if (a == 1) return o + (i - 1) + (int64_t)(N[0] - 1) * (dim == 3 ? (k - 1) : 0);
+    return o + (i - 1) + (int64_t)(N[0] - 1) * (j - 1);
+  }
+};
+
+// Stencil coefficients for one plan (anisotropic h).  L is indexed
+// (dz+1)*9 + (dy+1)*3 + (dx+1); in 2D only the dz = 0 plane is used.
+struct Coefs {
+  double L[27];
+  double Mc, Mn;          // weighting M: centre and each axis neighbour
+  double w[3][4];         // one-sided u_nn weights on U0..U3 per normal axis (1/h^2 scaled)
+  double wg[3];           // weight on g_N per normal axis (11/(3h))
+};
+
+// Per-mode factors of the tridiagonal solve along the last axis (see tri.cu).
+template <typename T>
+struct alignas(16) Mode {
+  T r, rinv, s, kap, rj0;
+  int j0;
+};
+
+}  // namespace ahoc

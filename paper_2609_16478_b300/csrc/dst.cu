@@ -1,0 +1,325 @@
+// DST-I along the x axis (contiguous lines) and the y axis (strided lines).
+//
+// The transform is X_k = sum_{j=1}^{N-1} x_j sin(pi j k / N), k = 1..N-1,
+// the sine expansion that diagonalises the compact operators (Lemma 4 and its
+// appendix proof).  It is computed through one complex FFT of length M = N/2:
+//   z_j = sin(pi j/N)(x_j + x_{N-j}) + (x_j - x_{N-j})/2        (z_0 = 0)
+//   C   = FFT_M(z_0 + i z_1, z_2 + i z_3, ...)
+//   F_k = E_k + e^{-2 pi i k/N} O_k,  E_k = (C_k + conj C_{M-k})/2,
+//         O_k = -i (C_k - conj C_{M-k})/2                       (real FFT of z)
+//   X_{2k} = -Im F_k,   X_{2k+1} = Re F_0 / 2 + sum_{m=1}^{k} Re F_m,
+// i.e. the odd outputs are a prefix sum.  The 1/2 factors are folded into the
+// pre-processing table (sn[j] = sin(pi j/N)/2, and 1/4 on the difference).
+//
+// The FFT is a self-sorting (Stockham) radix-4 transform in shared memory,
+// with one radix-2 stage first when log2 M is odd.  A line of N elements is
+// handled by TPL = N/8 threads (one radix-4 butterfly each per stage); a CTA
+// holds LPC lines.  All twiddles come from per-plan tables computed on the
+// host in long double: tw[t] = exp(-2 pi i t/N), t < N.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ahoc {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using t = double2; };
+template <> struct Cplx<float> { using t = float2; };
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return ::fmaf(a, b, c); }
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = fmaT(a.x, b.x, -a.y * b.y);
+  r.y = fmaT(a.x, b.y, a.y * b.x);
+  return r;
+}
+
+// In-place DST-I of the LPC lines of this CTA.  Line l occupies s[l*LS .. l*LS+N)
+// with s[l*LS] == 0.  Every thread of the CTA must call this.  wsum: >= 32
+// elements of scratch for the cross-warp scan.
+template <typename T>
+__device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename Cplx<T>::t* __restrict__ tw,
+                          const T* __restrict__ sn, T* wsum) {
+  using C = typename Cplx<T>::t;
+  const int tid = threadIdx.x;
+  const int l = tid / TPL;
+  const int lt = tid - l * TPL;
+  T* y = s + (int64_t)l * LS;
+  C* c = reinterpret_cast<C*>(y);
+  const int M = N >> 1;
+  const int logM = logN - 1;
+
+  // 1. pre-processing, pairs (j, N-j)
+  for (int j = lt + 1; j <= (N >> 1); j += TPL) {
+    T a = y[j], b = y[N - j];
+    T sum = a + b, dif = a - b;
+    T sj = sn[j];
+    T za = fmaT(sj, sum, (T)0.25 * dif);
+    T zb = fmaT(sj, sum, (T)-0.25 * dif);
+    y[j] = za;
+    if (j != (N >> 1)) y[N - j] = zb;
+  }
+  __syncthreads();
+
+  // 2. complex FFT of length M (Stockham, natural order in and out)
+  int Ns = 1;
+  if (logM & 1) {
+    C x[4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int j = lt + q * TPL;
+      x[2 * q] = c[j];
+      x[2 * q + 1] = c[j + (M >> 1)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int j = lt + q * TPL;
+      C a = x[2 * q], b = x[2 * q + 1];
+      C u, v;
+      u.x = a.x + b.x; u.y = a.y + b.y;
+      v.x = a.x - b.x; v.y = a.y - b.y;
+      c[2 * j] = u;
+      c[2 * j + 1] = v;
+    }
+    __syncthreads();
+    Ns = 2;
+  }
+  const int M4 = M >> 2;
+  for (; Ns < M; Ns <<= 2) {
+    const int j = lt;
+    const int kk = j & (Ns - 1);
+    C x0 = c[j], x1 = c[j + M4], x2 = c[j + 2 * M4], x3 = c[j + 3 * M4];
+    if (Ns > 1) {
+      // W_M^{r*kk*M/(4Ns)} = W_N^{2*r*t}
+      const int t = kk * (M / (4 * Ns));
+      x1 = cmul(x1, tw[2 * t]);
+      x2 = cmul(x2, tw[4 * t]);
+      x3 = cmul(x3, tw[6 * t]);
+    }
+    __syncthreads();
+    C a0, a1, b0, b1;
+    a0.x = x0.x + x2.x; a0.y = x0.y + x2.y;
+    a1.x = x0.x - x2.x; a1.y = x0.y - x2.y;
+    b0.x = x1.x + x3.x; b0.y = x1.y + x3.y;
+    b1.x = x1.x - x3.x; b1.y = x1.y - x3.y;
+    C y0, y1, y2, y3;
+    y0.x = a0.x + b0.x; y0.y = a0.y + b0.y;
+    y2.x = a0.x - b0.x; y2.y = a0.y - b0.y;
+    // -i * b1 = (b1.y, -b1.x)
+    y1.x = a1.x + b1.y; y1.y = a1.y - b1.x;
+    y3.x = a1.x - b1.y; y3.y = a1.y + b1.x;
+    const int o = ((j - kk) << 2) + kk;
+    c[o] = y0;
+    c[o + Ns] = y1;
+    c[o + 2 * Ns] = y2;
+    c[o + 3 * Ns] = y3;
+    __syncthreads();
+  }
+
+  // 3. post-processing: F_k and F_{M-k} from C_k, C_{M-k}; even outputs in
+  //    place, prefix-sum inputs Re F_k into the odd slots
+  for (int k = lt; k <= (M >> 1); k += TPL) {
+    if (k == 0) {
+      C a = c[0];
+      y[0] = (T)0;
+      y[1] = a.x + a.y;
+    } else if (k == (M >> 1)) {
+      C a = c[k];
+      y[2 * k] = (T)2 * a.y;
+      y[2 * k + 1] = (T)2 * a.x;
+    } else {
+      C A = c[k], B = c[M - k];
+      C E, D, O;
+      E.x = A.x + B.x; E.y = A.y - B.y;
+      D.x = A.x - B.x; D.y = A.y + B.y;
+      O.x = D.y; O.y = -D.x;
+      C Tt = cmul(tw[k], O);
+      y[2 * k] = -(E.y + Tt.y);
+      y[2 * k + 1] = E.x + Tt.x;
+      y[2 * (M - k)] = E.y - Tt.y;
+      y[2 * (M - k) + 1] = E.x - Tt.x;
+    }
+  }
+  __syncthreads();
+
+  // 4. inclusive prefix sum over the odd slots: each thread owns 4 consecutive values
+  T v0 = y[8 * lt + 1], v1 = y[8 * lt + 3], v2 = y[8 * lt + 5], v3 = y[8 * lt + 7];
+  v1 += v0;
+  v2 += v1;
+  v3 += v2;
+  const int lane = tid & 31;
+  const int W = TPL < 32 ? TPL : 32;
+  T x = v3;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    if (off < W) {
+      T n = __shfl_up_sync(0xffffffffu, x, off, W);
+      if ((lane & (W - 1)) >= off) x += n;
+    }
+  }
+  T ex = __shfl_up_sync(0xffffffffu, x, 1, W);
+  if ((lane & (W - 1)) == 0) ex = (T)0;
+  if (TPL > 32) {
+    // cross-warp: warp totals of this line, scanned by the line's first warp
+    const int warp = tid >> 5;
+    const int wpl = TPL >> 5;  // warps per line (<= 32)
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    const int wl = warp - l * wpl;  // warp index within the line
+    if (wl == 0) {
+      T t = (lane < wpl) ? wsum[warp + lane] : (T)0;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, t, off);
+        if (lane >= off) t += n;
+      }
+      T te = __shfl_up_sync(0xffffffffu, t, 1);
+      if (lane == 0) te = (T)0;
+      if (lane < wpl) wsum[warp + lane] = te;
+    }
+    __syncthreads();
+    ex += wsum[warp];
+  }
+  y[8 * lt + 1] = v0 + ex;
+  y[8 * lt + 3] = v1 + ex;
+  y[8 * lt + 5] = v2 + ex;
+  y[8 * lt + 7] = v3 + ex;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// x axis: lines are rows (j, k) of the padded layout, contiguous in memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
+                                               const T* __restrict__ sn, T scale, int logN, int TPL, int LPC) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* wsum = s + (int64_t)LPC * g.n0;
+  const int N = (int)g.n0;
+  const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
+  const int64_t r0 = (int64_t)blockIdx.x * LPC;
+  using C = typename Cplx<T>::t;
+  // load (vectorised pairs); slot 0 of each line is the zero pad
+  const int tot2 = (LPC * N) >> 1;
+  for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
+    const int l = (2 * e) >> logN;
+    const int pos = (2 * e) & (N - 1);
+    const int64_t r = r0 + l;
+    C v;
+    v.x = 0; v.y = 0;
+    if (r < nrows) {
+      const int j = 1 + (int)(r % (g.N[1] - 1));
+      const int k = g.kmin + (int)(r / (g.N[1] - 1));
+      v = *reinterpret_cast<const C*>(a + g.pad(pos, j, k));
+      if (pos == 0) v.x = 0;
+    }
+    *reinterpret_cast<C*>(s + l * N + pos) = v;
+  }
+  __syncthreads();
+  dst_lines<T>(s, N, N, logN, TPL, tw, sn, wsum);
+  for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
+    const int l = (2 * e) >> logN;
+    const int pos = (2 * e) & (N - 1);
+    const int64_t r = r0 + l;
+    if (r < nrows) {
+      const int j = 1 + (int)(r % (g.N[1] - 1));
+      const int k = g.kmin + (int)(r / (g.N[1] - 1));
+      C v = *reinterpret_cast<const C*>(s + l * N + pos);
+      v.x *= scale;
+      v.y *= scale;
+      if (pos == 0) v.x = 0;
+      *reinterpret_cast<C*>(a + g.pad(pos, j, k)) = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y axis (3D only): a CTA takes LPC adjacent x-columns of one z-plane; the
+// columns are staged through shared memory so global accesses stay row-wise.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_dst_y(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
+                                               const T* __restrict__ sn, T scale, int logN, int TPL, int LPC, int LS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* wsum = s + (int64_t)LPC * LS;
+  const int N = g.N[1];
+  const int i0 = blockIdx.x * LPC;
+  const int k = g.kmin + blockIdx.y;
+  const int tot = LPC * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int c = e % LPC;
+    const int j = e / LPC;
+    const int i = i0 + c;
+    T v = 0;
+    if (i < g.n0 && j > 0) v = a[g.pad(i, j, k)];
+    s[c * LS + j] = v;
+  }
+  __syncthreads();
+  dst_lines<T>(s, LS, N, logN, TPL, tw, sn, wsum);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int c = e % LPC;
+    const int j = e / LPC;
+    const int i = i0 + c;
+    if (i < g.n0) a[g.pad(i, j, k)] = (j > 0) ? s[c * LS + j] * scale : (T)0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename T>
+cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
+  const int N = (int)g.n0;
+  const int logN = ilog2(N);
+  const int TPL = N / 8;
+  const int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  const int threads = TPL * LPC;
+  const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
+  const int64_t blocks = (nrows + LPC - 1) / LPC;
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_dst_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_dst_x<T><<<(unsigned)blocks, threads, smem, st>>>(g, a, reinterpret_cast<const typename Cplx<T>::t*>(tw), sn,
+                                                       scale, logN, TPL, LPC);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
+  const int N = g.N[1];
+  const int logN = ilog2(N);
+  const int TPL = N / 8;
+  int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  if (LPC > g.n0) LPC = (int)g.n0;
+  const int threads = TPL * LPC;
+  const int LS = N + (int)(16 / sizeof(T));
+  dim3 grid((unsigned)((g.n0 + LPC - 1) / LPC), (unsigned)(g.kmax - g.kmin));
+  const size_t smem = ((size_t)LPC * LS + 32) * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_dst_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_dst_y<T><<<grid, threads, smem, st>>>(g, a, reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, scale, logN,
+                                          TPL, LPC, LS);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dst_x<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
+template cudaError_t launch_dst_y<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
+template cudaError_t launch_dst_x<float>(const Geom&, float*, const void*, const float*, float, cudaStream_t);
+template cudaError_t launch_dst_y<float>(const Geom&, float*, const void*, const float*, float, cudaStream_t);
+
+}  // namespace ahoc

@@ -1,0 +1,51 @@
+// Launchers of the device kernels (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace ahoc {
+
+template <typename T>
+cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st);
+
+// V-equation right-hand side for L_h V_int = rhs:
+//   rhs = -M f - L_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
+template <typename T>
+cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
+                        const double* vedge, cudaStream_t st);
+// u-equation right-hand side for L_h U_int = rhs:
+//   rhs = M(V / alpha) - L_bdry(g_D),  V = Q on face points (M reaches no edges).
+template <typename T>
+cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
+                        const double* gD, cudaStream_t st);
+// Boundary residual R_p = alpha_p [u_nn(U)_p + lapt_p] - Q_p at every face point.
+template <typename T>
+cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
+                         const double* afac, const double* gD, const double* gN, const double* lapt,
+                         cudaStream_t st);
+
+cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st);
+cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st);
+cudaError_t launch_unpack(const Geom& g, double* padded, const double* dense, cudaStream_t st);
+cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, cudaStream_t st);
+cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st);
+cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,
+                          cudaStream_t st);
+
+// GMRES level-1/2 kernels on face vectors (FP64).
+// partial[b * ncols + c] = sum over block b's rows of V[c*ld + i] * w[i]
+cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
+                        int nblocks, cudaStream_t st);
+cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st);
+// w -= V h (h on device, ncols entries)
+cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
+                            cudaStream_t st);
+// y = a * x (+ y if accumulate)
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
+
+}  // namespace ahoc

@@ -1,0 +1,720 @@
+// Plan, solver engine and C ABI of the augmented HOC method (Sec. 2.3,
+// Algorithm 1): ConstructSchurRHS, SchurMatVec, GMRES on S_h Q = b, recovery.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ahoc.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace ahoc;
+
+namespace {
+
+thread_local std::string g_err;
+
+ahoc_status fail(ahoc_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(AHOC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+#define CKS(expr)                  \
+  do {                             \
+    ahoc_status s_ = (expr);       \
+    if (s_ != AHOC_OK) return s_;  \
+  } while (0)
+
+bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct Opts {
+  ahoc_precision prec = AHOC_FP64;
+  int max_iters = 500;
+  int restart = 100;
+  int precond = 0;
+  int timing = 0;
+  void* workspace = nullptr;
+  size_t workspace_bytes = 0;
+};
+
+ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
+  Opts d;
+  if (o) {
+    d.prec = o->prec;
+    if (o->max_iters > 0) d.max_iters = o->max_iters;
+    if (o->restart > 0) d.restart = o->restart;
+    d.precond = o->precond;
+    d.timing = o->timing;
+    d.workspace = o->workspace;
+    d.workspace_bytes = o->workspace_bytes;
+  }
+  if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "only AHOC_FP64 is implemented");
+  if (d.precond != 0) return fail(AHOC_EUNSUPPORTED, "precond must be 0");
+  if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
+  if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
+    return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
+  *out = d;
+  return AHOC_OK;
+}
+
+ahoc_status make_geom(int dim, const int64_t* N, const double* lo, const double* hi, Geom* g) {
+  if (dim != 2 && dim != 3) return fail(AHOC_EINVAL, "dim must be 2 or 3");
+  if (!N) return fail(AHOC_EINVAL, "N is NULL");
+  for (int a = 0; a < dim; ++a) {
+    if (N[a] < 8 || N[a] > kMaxN || !pow2(N[a]))
+      return fail(AHOC_EUNSUPPORTED, "N[a] must be a power of two in [8, 4096]");
+  }
+  std::memset(g, 0, sizeof(*g));
+  g->dim = dim;
+  for (int a = 0; a < 3; ++a) g->N[a] = (a < dim) ? (int)N[a] : 1;
+  for (int a = 0; a < dim; ++a) {
+    const double l = lo ? lo[a] : 0.0, r = hi ? hi[a] : 1.0;
+    if (!(r > l) || !std::isfinite(l) || !std::isfinite(r)) return fail(AHOC_EINVAL, "need lo[a] < hi[a], finite");
+    g->h[a] = (r - l) / (double)N[a];
+  }
+  g->n0 = g->N[0];
+  g->n1 = g->N[1];
+  g->n2 = (dim == 3) ? g->N[2] : 1;
+  g->npad = g->n0 * g->n1 * g->n2;
+  g->f0 = g->N[0] + 1;
+  g->f1 = g->N[1] + 1;
+  g->f2 = (dim == 3) ? g->N[2] + 1 : 1;
+  g->nfull = g->f0 * g->f1 * g->f2;
+  g->kmin = (dim == 3) ? 1 : 0;
+  g->kmax = (dim == 3) ? g->N[2] : 1;
+  g->nint = 1;
+  for (int a = 0; a < dim; ++a) g->nint *= (N[a] - 1);
+  g->face_off[0] = 0;
+  for (int a = 0; a < 3; ++a) {
+    int64_t s = 0;
+    if (a < dim) {
+      s = 1;
+      for (int b = 0; b < dim; ++b)
+        if (b != a) s *= (N[b] - 1);
+    }
+    g->face_off[2 * a + 1] = g->face_off[2 * a] + s;
+    g->face_off[2 * a + 2] = g->face_off[2 * a + 1] + s;
+  }
+  g->ngamma = g->face_off[6];
+  return AHOC_OK;
+}
+
+// Stencil coefficients (Sec. 2.2; prefactor 1/12; 2D nine-point operator).
+Coefs make_coefs(const Geom& g) {
+  Coefs c;
+  std::memset(&c, 0, sizeof(c));
+  double inv[3] = {0, 0, 0};
+  for (int a = 0; a < g.dim; ++a) inv[a] = 1.0 / (g.h[a] * g.h[a]);
+  if (g.dim == 2) {
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        double v;
+        if (dx && dy) v = inv[0] + inv[1];
+        else if (dx) v = 10 * inv[0] - 2 * inv[1];
+        else if (dy) v = 10 * inv[1] - 2 * inv[0];
+        else v = -20 * (inv[0] + inv[1]);
+        c.L[9 + (dy + 1) * 3 + (dx + 1)] = v / 12.0;
+      }
+    c.Mc = 8.0 / 12.0;
+  } else {
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int o[3] = {dx, dy, dz};
+          int nz[3], cnt = 0;
+          for (int a = 0; a < 3; ++a)
+            if (o[a]) nz[cnt++] = a;
+          double v = 0;
+          if (cnt == 3) continue;
+          if (cnt == 2) v = inv[nz[0]] + inv[nz[1]];
+          else if (cnt == 1) {
+            const int a = nz[0];
+            v = 8 * inv[a];
+            for (int b = 0; b < 3; ++b)
+              if (b != a) v -= 2 * inv[b];
+          } else v = -16 * (inv[0] + inv[1] + inv[2]);
+          c.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = v / 12.0;
+        }
+    c.Mc = 6.0 / 12.0;
+  }
+  c.Mn = 1.0 / 12.0;
+  const double os[4] = {-85.0 / 18.0, 6.0, -1.5, 2.0 / 9.0};
+  for (int a = 0; a < g.dim; ++a) {
+    for (int m = 0; m < 4; ++m) c.w[a][m] = os[m] * inv[a];
+    c.wg[a] = (11.0 / 3.0) / g.h[a];
+  }
+  return c;
+}
+
+// DST tables for one axis: tw[t] = exp(-2 pi i t / N) (t < N), sn[j] = sin(pi j/N)/2 (j <= N/2)
+void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
+  tw.resize(2 * (size_t)N);
+  sn.resize((size_t)N / 2 + 1);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int t = 0; t < N; ++t) {
+    const long double ang = -2.0L * pi * (long double)t / (long double)N;
+    tw[2 * t] = (double)cosl(ang);
+    tw[2 * t + 1] = (double)sinl(ang);
+  }
+  for (int j = 0; j <= N / 2; ++j) sn[j] = (double)(0.5L * sinl(pi * (long double)j / (long double)N));
+}
+
+// Per-mode factors of the tridiagonal solve along the last axis (tri.cu).
+ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<double>>& out) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const int nx = g.N[0] - 1;
+  const int ny = (g.dim == 3) ? g.N[1] - 1 : 1;
+  const int Nt = (g.dim == 3) ? g.N[2] : g.N[1];
+  const int nt = Nt - 1;
+  long double scale = 2.0L / g.N[0];
+  if (g.dim == 3) scale *= 2.0L / g.N[1];
+  auto L = [&](int dx, int dy, int dz) { return (long double)cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)]; };
+  out.resize((size_t)nx * ny);
+  for (int ky = 1; ky <= ny; ++ky) {
+    const long double cy = (g.dim == 3) ? cosl(pi * ky / g.N[1]) : 0.0L;
+    for (int kx = 1; kx <= nx; ++kx) {
+      const long double cx = cosl(pi * kx / g.N[0]);
+      long double a, b;
+      if (g.dim == 2) {
+        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0);
+        b = L(0, 1, 0) + 2 * cx * L(1, 1, 0);
+      } else {
+        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0) + 2 * cy * L(0, 1, 0) + 4 * cx * cy * L(1, 1, 0);
+        b = L(0, 0, 1) + 2 * cx * L(1, 0, 1) + 2 * cy * L(0, 1, 1);
+      }
+      const long double gam = -b / a;
+      if (!(fabsl(gam) < 0.5L)) return fail(AHOC_EUNSUPPORTED, "tridiagonal factor not diagonally dominant (mesh aspect ratio)");
+      const long double r = 2 * gam / (1 + sqrtl(1 - 4 * gam * gam));
+      const long double sigma = a / (1 + r * r);
+      Mode<double> m;
+      m.r = (double)r;
+      m.s = (double)(scale / sigma);
+      const long double r2N = powl(r, 2.0L * Nt);
+      m.kap = (double)(-r * (1 - r * r) / (1 - r2N));
+      if (r == 0.0L) {
+        m.rinv = 0;
+        m.rj0 = 0;
+        m.j0 = 0;
+      } else {
+        long double lim = -290.0L * logl(10.0L) / logl(fabsl(r));
+        int j0 = (lim >= nt) ? nt : (int)lim;
+        if (j0 < 0) j0 = 0;
+        m.rinv = (double)(1.0L / r);
+        m.rj0 = (double)powl(r, (long double)j0);
+        m.j0 = j0;
+      }
+      out[(size_t)(ky - 1) * nx + (kx - 1)] = m;
+    }
+  }
+  return AHOC_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, modes, b, Q, r, Kry, partial, hdev, tmp,
+      total;
+};
+
+constexpr int kDotBlocks = 296;  // 2 x 148 SMs
+
+Layout make_layout(const Geom& g, const Opts& o) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t p = off;
+    off += align256(bytes);
+    return p;
+  };
+  const size_t fld = (size_t)g.npad * sizeof(double);
+  const size_t full = (size_t)g.nfull * sizeof(double);
+  const size_t face = (size_t)g.ngamma * sizeof(double);
+  L.W1 = take(fld);
+  L.W2 = take(fld);
+  L.ainv = take(full);
+  L.afac = take(face);
+  L.gD = take(full);
+  L.vedge = take(full);
+  L.gN = take(face);
+  L.lapt = take(face);
+  L.twx = take(2 * (size_t)g.N[0] * sizeof(double));
+  L.snx = take(((size_t)g.N[0] / 2 + 1) * sizeof(double));
+  L.twy = take(2 * (size_t)g.N[1] * sizeof(double));
+  L.sny = take(((size_t)g.N[1] / 2 + 1) * sizeof(double));
+  const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
+  L.modes = take(nmodes * sizeof(Mode<double>));
+  L.b = take(face);
+  L.Q = take(face);
+  L.r = take(face);
+  L.tmp = take(face);
+  L.Kry = take(face * (size_t)(o.restart + 1));
+  L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
+  L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct ahoc_plan {
+  Geom g;
+  Coefs cf;
+  Opts o;
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  bool own_ws = false;
+  Layout L;
+  double *W1, *W2, *ainv, *afac, *gD = nullptr, *vedge = nullptr, *gN = nullptr, *lapt = nullptr;
+  double *twx, *snx, *twy, *sny, *b, *Q, *r, *tmp, *Kry, *partial, *hdev;
+  Mode<double>* modes;
+  double* hhost = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool have_last = false;
+  // launch accounting (and, with opts.timing, per-launch CUDA events)
+  struct EvPair {
+    cudaEvent_t a, b;
+    int kid;
+  };
+  std::vector<EvPair> pool, pending;
+  int64_t launches = 0;
+  double kms[AHOC_NK] = {0};
+  int64_t kn[AHOC_NK] = {0};
+};
+
+namespace {
+
+template <typename P>
+P* at(ahoc_plan* p, size_t off) {
+  return reinterpret_cast<P*>(p->ws + off);
+}
+
+// Launch one kernel through `f`, counting it and, when timing is on,
+// bracketing it with CUDA events on the plan's stream.
+template <class F>
+ahoc_status run(ahoc_plan* p, int kid, const char* what, F&& f) {
+  ahoc_plan::EvPair ev{nullptr, nullptr, kid};
+  if (p->o.timing) {
+    if (!p->pool.empty()) {
+      ev = p->pool.back();
+      p->pool.pop_back();
+      ev.kid = kid;
+    } else {
+      CK(cudaEventCreate(&ev.a));
+      CK(cudaEventCreate(&ev.b));
+    }
+    CK(cudaEventRecord(ev.a, p->st));
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return fail(AHOC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  if (p->o.timing) {
+    CK(cudaEventRecord(ev.b, p->st));
+    p->pending.push_back(ev);
+  }
+  ++p->launches;
+  ++p->kn[kid];
+  return AHOC_OK;
+}
+
+// Collect the event timings of completed launches (call after a stream sync).
+ahoc_status harvest(ahoc_plan* p) {
+  for (auto& ev : p->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    p->kms[ev.kid] += ms;
+    p->pool.push_back(ev);
+  }
+  p->pending.clear();
+  return AHOC_OK;
+}
+
+#define RUN(kid, call) CKS(run(p, kid, #call, [&]() { return (call); }))
+
+ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
+  const Geom& g = p->g;
+  RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
+  if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
+  RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
+  if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
+  return AHOC_OK;
+}
+
+// V-solve then U-solve (Algorithm 1, two FFT-based solves); leaves V in W1, U in W2.
+ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) {
+  const Geom& g = p->g;
+  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data ? p->vedge : nullptr, p->st));
+  CKS(poisson_inplace(p, p->W1));
+  RUN(AHOC_K_URHS, launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data ? p->gD : nullptr, p->st));
+  CKS(poisson_inplace(p, p->W2));
+  return AHOC_OK;
+}
+
+ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
+  CKS(solve_VU(p, q, nullptr, false));
+  RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
+  return AHOC_OK;
+}
+
+ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
+  CKS(solve_VU(p, nullptr, f, true));
+  RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, b, p->W2, nullptr, p->afac, p->gD, p->gN, p->lapt, p->st));
+  RUN(AHOC_K_KRYLOV, launch_axpby(b, b, -1.0, 0.0, p->g.ngamma, p->st));
+  return AHOC_OK;
+}
+
+// dots: out[c] = <V_c, w>, c < ncols (device); returns via hdev+off
+ahoc_status mdot(ahoc_plan* p, const double* V, int ncols, const double* w, double* out) {
+  RUN(AHOC_K_KRYLOV, launch_mdot(V, p->g.ngamma, ncols, w, p->g.ngamma, p->partial, kDotBlocks, p->st));
+  RUN(AHOC_K_KRYLOV, launch_reduce_cols(p->partial, kDotBlocks, ncols, out, p->st));
+  return AHOC_OK;
+}
+
+ahoc_status fetch(ahoc_plan* p, int n) {
+  CK(cudaMemcpyAsync(p->hhost, p->hdev, n * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return harvest(p);
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+extern "C" {
+
+const char* ahoc_status_string(ahoc_status s) {
+  switch (s) {
+    case AHOC_OK: return "AHOC_OK";
+    case AHOC_EINVAL: return "AHOC_EINVAL: invalid argument";
+    case AHOC_ENOMEM: return "AHOC_ENOMEM: out of device memory or workspace too small";
+    case AHOC_ECUDA: return "AHOC_ECUDA: CUDA runtime error";
+    case AHOC_ENOCONV: return "AHOC_ENOCONV: GMRES did not reach the tolerance";
+    case AHOC_ENUMERIC: return "AHOC_ENUMERIC: NaN or Inf in a residual";
+    case AHOC_ETIMEOUT: return "AHOC_ETIMEOUT: device wait timed out";
+    case AHOC_EUNSUPPORTED: return "AHOC_EUNSUPPORTED: not supported by this build";
+    case AHOC_EINTERNAL: return "AHOC_EINTERNAL: internal error";
+  }
+  return "unknown ahoc_status";
+}
+
+const char* ahoc_last_error(void) { return g_err.c_str(); }
+
+ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opts, size_t* bytes) {
+  if (!bytes) return fail(AHOC_EINVAL, "bytes is NULL");
+  Geom g;
+  CKS(make_geom(dim, N, nullptr, nullptr, &g));
+  Opts o;
+  CKS(read_opts(opts, &o));
+  *bytes = make_layout(g, o).total;
+  return AHOC_OK;
+}
+
+int64_t ahoc_n_gamma(const ahoc_plan* p) { return p ? p->g.ngamma : -1; }
+
+ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi,
+                             const double* alpha, const ahoc_bdata* bd, const ahoc_opts* opts, void* stream) {
+  if (!out) return fail(AHOC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!alpha) return fail(AHOC_EINVAL, "alpha is NULL");
+  Geom g;
+  CKS(make_geom(dim, N, lo, hi, &g));
+  Opts o;
+  CKS(read_opts(opts, &o));
+  Coefs cf = make_coefs(g);
+  std::vector<Mode<double>> modes;
+  CKS(mode_table(g, cf, modes));
+  Layout L = make_layout(g, o);
+  if (o.workspace && o.workspace_bytes < L.total) return fail(AHOC_ENOMEM, "caller workspace too small");
+
+  ahoc_plan* p = new (std::nothrow) ahoc_plan();
+  if (!p) return fail(AHOC_ENOMEM, "host allocation failed");
+  p->g = g;
+  p->cf = cf;
+  p->o = o;
+  p->L = L;
+  p->st = reinterpret_cast<cudaStream_t>(stream);
+  if (o.workspace) {
+    p->ws = reinterpret_cast<char*>(o.workspace);
+  } else {
+    cudaError_t e = cudaMalloc(&p->ws, L.total);
+    if (e != cudaSuccess) {
+      delete p;
+      cudaGetLastError();
+      return fail(AHOC_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    }
+    p->own_ws = true;
+  }
+  auto cleanup = [&](ahoc_status s) {
+    ahoc_plan_destroy(p);
+    return s;
+  };
+  p->W1 = at<double>(p, L.W1);
+  p->W2 = at<double>(p, L.W2);
+  p->ainv = at<double>(p, L.ainv);
+  p->afac = at<double>(p, L.afac);
+  p->twx = at<double>(p, L.twx);
+  p->snx = at<double>(p, L.snx);
+  p->twy = at<double>(p, L.twy);
+  p->sny = at<double>(p, L.sny);
+  p->modes = at<Mode<double>>(p, L.modes);
+  p->b = at<double>(p, L.b);
+  p->Q = at<double>(p, L.Q);
+  p->r = at<double>(p, L.r);
+  p->tmp = at<double>(p, L.tmp);
+  p->Kry = at<double>(p, L.Kry);
+  p->partial = at<double>(p, L.partial);
+  p->hdev = at<double>(p, L.hdev);
+  const size_t fld = (size_t)g.npad * sizeof(double);
+  const size_t full = (size_t)g.nfull * sizeof(double);
+  const size_t face = (size_t)g.ngamma * sizeof(double);
+  cudaError_t e;
+#define CKC(call)                                                                                        \
+  do {                                                                                                   \
+    e = (call);                                                                                          \
+    if (e != cudaSuccess)                                                                                \
+      return cleanup(fail(AHOC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e)));               \
+  } while (0)
+  CKC(cudaMallocHost(&p->hhost, (size_t)(2 * (o.restart + 1) + 4) * sizeof(double)));
+  CKC(cudaEventCreate(&p->ev0));
+  CKC(cudaEventCreate(&p->ev1));
+  CKC(cudaMemsetAsync(p->W1, 0, fld, p->st));
+  CKC(cudaMemsetAsync(p->W2, 0, fld, p->st));
+  std::vector<double> tw, sn;
+  dst_tables(g.N[0], tw, sn);
+  CKC(cudaMemcpyAsync(p->twx, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  CKC(cudaMemcpyAsync(p->snx, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  CKC(cudaStreamSynchronize(p->st));
+  dst_tables(g.N[1], tw, sn);
+  CKC(cudaMemcpyAsync(p->twy, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  CKC(cudaMemcpyAsync(p->sny, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+  CKC(cudaMemcpyAsync(p->modes, modes.data(), modes.size() * sizeof(Mode<double>), cudaMemcpyHostToDevice, p->st));
+  CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
+  CKC(launch_face_gather(g, p->afac, alpha, p->st));
+  if (bd && bd->g_D) {
+    p->gD = at<double>(p, L.gD);
+    CKC(cudaMemcpyAsync(p->gD, bd->g_D, full, cudaMemcpyDeviceToDevice, p->st));
+  }
+  if (bd && bd->v_edge) {
+    p->vedge = at<double>(p, L.vedge);
+    CKC(cudaMemcpyAsync(p->vedge, bd->v_edge, full, cudaMemcpyDeviceToDevice, p->st));
+  }
+  if (bd && bd->g_N) {
+    p->gN = at<double>(p, L.gN);
+    CKC(cudaMemcpyAsync(p->gN, bd->g_N, face, cudaMemcpyDeviceToDevice, p->st));
+  }
+  if (bd && bd->lapt_gD) {
+    p->lapt = at<double>(p, L.lapt);
+    CKC(cudaMemcpyAsync(p->lapt, bd->lapt_gD, face, cudaMemcpyDeviceToDevice, p->st));
+  }
+  CKC(cudaStreamSynchronize(p->st));
+#undef CKC
+  *out = p;
+  return AHOC_OK;
+}
+
+ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
+  if (!p) return AHOC_OK;
+  ahoc_status s = AHOC_OK;
+  if (p->st) {
+    if (cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "stream sync at destroy failed");
+  }
+  if (p->own_ws && p->ws) cudaFree(p->ws);
+  if (p->hhost) cudaFreeHost(p->hhost);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  for (auto& ev : p->pool) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  for (auto& ev : p->pending) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  delete p;
+  return s;
+}
+
+ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y) {
+  if (!p || !q || !y) return fail(AHOC_EINVAL, "NULL argument");
+  if (q == y) return fail(AHOC_EINVAL, "q and y may not alias");
+  return matvec_dev(p, q, y);
+}
+
+ahoc_status ahoc_schur_rhs(ahoc_plan* p, const double* f, double* b) {
+  if (!p || !f || !b) return fail(AHOC_EINVAL, "NULL argument");
+  return schur_rhs_dev(p, f, b);
+}
+
+ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, double scale) {
+  if (!p || !in || !out) return fail(AHOC_EINVAL, "NULL argument");
+  if (axis < 0 || axis >= p->g.dim - 1) return fail(AHOC_EINVAL, "axis must be < dim - 1");
+  RUN(AHOC_K_OTHER, launch_unpack(p->g, p->W1, in, p->st));
+  if (axis == 0) RUN(AHOC_K_DST_X, launch_dst_x<double>(p->g, p->W1, p->twx, p->snx, scale, p->st));
+  else RUN(AHOC_K_DST_Y, launch_dst_y<double>(p->g, p->W1, p->twy, p->sny, scale, p->st));
+  RUN(AHOC_K_OTHER, launch_pack(p->g, out, p->W1, p->st));
+  return AHOC_OK;
+}
+
+ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
+  if (!p || !rhs || !w) return fail(AHOC_EINVAL, "NULL argument");
+  RUN(AHOC_K_OTHER, launch_unpack(p->g, p->W1, rhs, p->st));
+  CKS(poisson_inplace(p, p->W1));
+  RUN(AHOC_K_OTHER, launch_pack(p->g, w, p->W1, p->st));
+  return AHOC_OK;
+}
+
+ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
+  if (!p || !q) return fail(AHOC_EINVAL, "NULL argument");
+  if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
+  CK(cudaMemcpyAsync(q, p->Q, p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  if (v) RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->W1, p->Q, p->vedge, p->st));
+  return AHOC_OK;
+}
+
+// Algorithm 1, Main procedure, with GMRES (CGS2 Arnoldi, Givens rotations).
+ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info) {
+  if (!p || !f || !u) return fail(AHOC_EINVAL, "NULL argument");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(AHOC_EINVAL, "tol must be positive");
+  const auto t0 = std::chrono::steady_clock::now();
+  p->have_last = false;
+  CK(cudaStreamSynchronize(p->st));
+  CKS(harvest(p));
+  p->launches = 0;
+  for (int k = 0; k < AHOC_NK; ++k) {
+    p->kms[k] = 0;
+    p->kn[k] = 0;
+  }
+  const Geom& g = p->g;
+  const int64_t n = g.ngamma;
+  const int m = p->o.restart;
+  double ms_mv = 0.0;
+  // b = -R(0)
+  CKS(schur_rhs_dev(p, f, p->b));
+  CKS(mdot(p, p->b, 1, p->b, p->hdev));
+  CKS(fetch(p, 1));
+  const double beta0 = std::sqrt(p->hhost[0]);
+  if (!is_fin(beta0)) return fail(AHOC_ENUMERIC, "non-finite ||b||");
+  CK(cudaMemsetAsync(p->Q, 0, n * sizeof(double), p->st));
+  int iters = 0, restarts = 0;
+  double rel = 0.0;
+  ahoc_status status = AHOC_OK;
+  if (beta0 > 0) {
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    double beta = beta0;
+    bool done = false;
+    while (!done) {
+      rel = beta / beta0;
+      if (rel <= tol) break;
+      if (iters >= p->o.max_iters) {
+        status = AHOC_ENOCONV;
+        break;
+      }
+      double* V = p->Kry;
+      RUN(AHOC_K_KRYLOV, launch_axpby(V, p->r, 1.0 / beta, 0.0, n, p->st));
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = beta;
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        double* w = V + (int64_t)(j + 1) * n;
+        CK(cudaEventRecord(p->ev0, p->st));
+        CKS(matvec_dev(p, V + (int64_t)j * n, w));
+        CK(cudaEventRecord(p->ev1, p->st));
+        // CGS2
+        double* h1 = p->hdev;
+        double* h2 = p->hdev + (j + 1);
+        double* nr = p->hdev + 2 * (j + 1);
+        CKS(mdot(p, V, j + 1, w, h1));
+        RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h1, w, n, p->st));
+        CKS(mdot(p, V, j + 1, w, h2));
+        RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h2, w, n, p->st));
+        CKS(mdot(p, w, 1, w, nr));
+        CKS(fetch(p, 2 * (j + 1) + 1));
+        float evms = 0.f;
+        if (cudaEventElapsedTime(&evms, p->ev0, p->ev1) == cudaSuccess) ms_mv += evms;
+        ++iters;
+        double* Hc = &H[(size_t)j * (m + 1)];
+        for (int i = 0; i <= j; ++i) Hc[i] = p->hhost[i] + p->hhost[j + 1 + i];
+        const double hn = std::sqrt(p->hhost[2 * (j + 1)]);
+        if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
+        Hc[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hc[i], bb = Hc[i + 1];
+          Hc[i] = cs[i] * a + sn[i] * bb;
+          Hc[i + 1] = -sn[i] * a + cs[i] * bb;
+        }
+        const double den = std::hypot(Hc[j], Hc[j + 1]);
+        cs[j] = (den > 0) ? Hc[j] / den : 1.0;
+        sn[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
+        Hc[j] = den;
+        Hc[j + 1] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        jend = j + 1;
+        rel = std::fabs(gv[j + 1]) / beta0;
+        if (rel <= tol || hn == 0.0 || iters >= p->o.max_iters) {
+          done = (rel <= tol || hn == 0.0);
+          break;
+        }
+        RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 1.0 / hn, 0.0, n, p->st));
+      }
+      // y = H^-1 g (upper triangular), Q += V y
+      for (int i = jend - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int k = i + 1; k < jend; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
+        y[i] = s / H[(size_t)i * (m + 1) + i];
+      }
+      for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
+      CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->Q, n, p->st));
+      CK(cudaStreamSynchronize(p->st));
+      CKS(harvest(p));
+      if (done) break;
+      if (iters >= p->o.max_iters) {
+        status = AHOC_ENOCONV;
+        break;
+      }
+      // restart: explicit residual r = b - S Q
+      ++restarts;
+      CKS(matvec_dev(p, p->Q, p->tmp));
+      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+      RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
+      CKS(mdot(p, p->r, 1, p->r, p->hdev));
+      CKS(fetch(p, 1));
+      beta = std::sqrt(p->hhost[0]);
+      if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite restart residual");
+    }
+  }
+  // recovery: V and U with the converged Q (and the data)
+  CKS(solve_VU(p, p->Q, f, true));
+  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->gD, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  CKS(harvest(p));
+  p->have_last = true;
+  if (info) {
+    info->iters = iters;
+    info->restarts = restarts;
+    info->rel_resid = rel;
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->ms_matvec = ms_mv;
+    info->launches = p->launches;
+    for (int k = 0; k < AHOC_NK; ++k) {
+      info->kernel_ms[k] = p->kms[k];
+      info->kernel_launches[k] = p->kn[k];
+    }
+  }
+  if (status != AHOC_OK) return fail(status, "GMRES reached max_iters");
+  return AHOC_OK;
+}
+
+}  // extern "C"

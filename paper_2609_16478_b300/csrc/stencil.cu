@@ -1,0 +1,297 @@
+// Compact-stencil kernels of the augmented HOC scheme (Sec. 2.2):
+// right-hand sides of the v- and u-equations, the boundary residual R of
+// Lemma 1, and layout conversions.
+//
+// Stencils (coefficients per plan, anisotropic h): the 9-point (2D) /
+// 19-point (3D) fourth-order Laplacian L_h with prefactor 1/12, the
+// weighting M (centre 8/12 in 2D, 6/12 in 3D, 1/12 per axis neighbour) and
+// the one-sided second normal derivative
+//   u_nn ~ h^-2 (-85/18 U0 + 6 U1 - 3/2 U2 + 2/9 U3) + 11/(3h) g_N.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ahoc {
+
+__device__ __forceinline__ void decompose(const Geom& g, int64_t t, int& i, int& j, int& k) {
+  i = (int)(t % g.n0);
+  int64_t r = t / g.n0;
+  j = (int)(r % g.n1);
+  k = (int)(r / g.n1);
+}
+
+__device__ __forceinline__ bool is_pad(const Geom& g, int i, int j, int k) {
+  return i == 0 || j == 0 || (g.dim == 3 && k == 0);
+}
+
+// number of coordinates of (i, j, k) on the boundary, and the first such axis/side
+__device__ __forceinline__ int bclass(const Geom& g, int i, int j, int k, int& axis, int& side) {
+  int nb = 0;
+  axis = -1;
+  side = 0;
+  if (i == 0 || i == g.N[0]) { ++nb; axis = 0; side = (i != 0); }
+  if (j == 0 || j == g.N[1]) { if (!nb) { axis = 1; side = (j != 0); } ++nb; }
+  if (g.dim == 3 && (k == 0 || k == g.N[2])) { if (!nb) { axis = 2; side = (k != 0); } ++nb; }
+  return nb;
+}
+
+__device__ __forceinline__ bool near_bdry(const Geom& g, int i, int j, int k) {
+  return i == 1 || i == g.N[0] - 1 || j == 1 || j == g.N[1] - 1 ||
+         (g.dim == 3 && (k == 1 || k == g.N[2] - 1));
+}
+
+template <typename T>
+__global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __restrict__ Q,
+                       const double* __restrict__ f, const double* __restrict__ vedge) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.npad) return;
+  int i, j, k;
+  decompose(g, t, i, j, k);
+  if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
+  double acc = 0.0;
+  if ((Q || vedge) && near_bdry(g, i, j, k)) {
+    const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
+    for (int dz = dzlo; dz <= dzhi; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const double c = cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+          if (c == 0.0) continue;
+          const int ii = i + dx, jj = j + dy, kk = k + dz;
+          int ax, sd;
+          const int nb = bclass(g, ii, jj, kk, ax, sd);
+          if (nb == 0) continue;
+          double vb = 0.0;
+          if (nb == 1) {
+            if (Q) vb = Q[g.face(ax, sd, ii, jj, kk)];
+          } else if (vedge) {
+            vb = vedge[g.full(ii, jj, kk)];
+          }
+          acc -= c * vb;
+        }
+  }
+  if (f) {
+    double m = cf.Mc * f[g.full(i, j, k)];
+    m += cf.Mn * (f[g.full(i - 1, j, k)] + f[g.full(i + 1, j, k)] + f[g.full(i, j - 1, k)] + f[g.full(i, j + 1, k)]);
+    if (g.dim == 3) m += cf.Mn * (f[g.full(i, j, k - 1)] + f[g.full(i, j, k + 1)]);
+    acc -= m;
+  }
+  out[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restrict__ V,
+                       const double* __restrict__ ainv, const double* __restrict__ Q,
+                       const double* __restrict__ gD) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.npad) return;
+  int i, j, k;
+  decompose(g, t, i, j, k);
+  if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
+  // M(V / alpha): centre and the axis neighbours; a neighbour on a face holds Q
+  double acc = cf.Mc * (double)V[t] * ainv[g.full(i, j, k)];
+  const int nd = g.dim;
+  for (int a = 0; a < nd; ++a) {
+    for (int s = -1; s <= 1; s += 2) {
+      const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
+      const int ia = (a == 0) ? ii : (a == 1) ? jj : kk;
+      double v;
+      if (ia == 0 || ia == g.N[a]) {
+        v = Q ? Q[g.face(a, ia != 0, ii, jj, kk)] : 0.0;
+      } else {
+        v = (double)V[g.pad(ii, jj, kk)];
+      }
+      acc += cf.Mn * v * ainv[g.full(ii, jj, kk)];
+    }
+  }
+  if (gD && near_bdry(g, i, j, k)) {
+    const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
+    for (int dz = dzlo; dz <= dzhi; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const double c = cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+          if (c == 0.0) continue;
+          const int ii = i + dx, jj = j + dy, kk = k + dz;
+          int ax, sd;
+          if (bclass(g, ii, jj, kk, ax, sd) == 0) continue;
+          acc -= c * gD[g.full(ii, jj, kk)];
+        }
+  }
+  out[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __restrict__ U,
+                        const double* __restrict__ Q, const double* __restrict__ afac,
+                        const double* __restrict__ gD, const double* __restrict__ gN,
+                        const double* __restrict__ lapt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.ngamma) return;
+  int f = 0;
+  while (q >= g.face_off[f + 1]) ++f;
+  const int a = f >> 1, side = f & 1;
+  const int64_t loc = q - g.face_off[f];
+  int c[3] = {0, 0, 0};
+  // remaining axes, lowest fastest
+  int64_t r = loc;
+  for (int b = 0; b < g.dim; ++b) {
+    if (b == a) continue;
+    const int nb = g.N[b] - 1;
+    c[b] = 1 + (int)(r % nb);
+    r /= nb;
+  }
+  c[a] = side ? g.N[a] : 0;
+  const int step = side ? -1 : 1;
+  double U1, U2, U3;
+  {
+    int p[3] = {c[0], c[1], c[2]};
+    p[a] = c[a] + step;
+    U1 = (double)U[g.pad(p[0], p[1], p[2])];
+    p[a] = c[a] + 2 * step;
+    U2 = (double)U[g.pad(p[0], p[1], p[2])];
+    p[a] = c[a] + 3 * step;
+    U3 = (double)U[g.pad(p[0], p[1], p[2])];
+  }
+  double unn = cf.w[a][1] * U1 + cf.w[a][2] * U2 + cf.w[a][3] * U3;
+  if (gD) unn += cf.w[a][0] * gD[g.full(c[0], c[1], c[2])];
+  if (gN) unn += cf.wg[a] * gN[q];
+  if (lapt) unn += lapt[q];
+  double res = afac[q] * unn;
+  if (Q) res -= Q[q];
+  y[q] = res;
+}
+
+// full-grid output: interior from the padded field, boundary from bnd (or 0)
+__global__ void k_write_full(Geom g, double* __restrict__ out, const double* __restrict__ Uin,
+                             const double* __restrict__ bnd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nfull) return;
+  const int i = (int)(t % g.f0);
+  const int64_t r = t / g.f0;
+  const int j = (int)(r % g.f1);
+  const int k = (int)(r / g.f1);
+  int ax, sd;
+  if (bclass(g, i, j, k, ax, sd) == 0) out[t] = Uin[g.pad(i, j, k)];
+  else out[t] = bnd ? bnd[t] : 0.0;
+}
+
+// full-grid V: interior from the padded field, faces = Q, edges/corners = vedge
+__global__ void k_v_full(Geom g, double* __restrict__ out, const double* __restrict__ Vin,
+                         const double* __restrict__ Q, const double* __restrict__ vedge) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nfull) return;
+  const int i = (int)(t % g.f0);
+  const int64_t r = t / g.f0;
+  const int j = (int)(r % g.f1);
+  const int k = (int)(r / g.f1);
+  int ax, sd;
+  const int nb = bclass(g, i, j, k, ax, sd);
+  if (nb == 0) out[t] = Vin[g.pad(i, j, k)];
+  else if (nb == 1) out[t] = Q ? Q[g.face(ax, sd, i, j, k)] : 0.0;
+  else out[t] = vedge ? vedge[t] : 0.0;
+}
+
+__global__ void k_pack(Geom g, double* __restrict__ dense, const double* __restrict__ padded) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nint) return;
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1;
+  const int i = 1 + (int)(t % nx);
+  const int64_t r = t / nx;
+  const int j = 1 + (int)(r % ny);
+  const int k = g.kmin + (int)(r / ny);
+  dense[t] = padded[g.pad(i, j, k)];
+}
+
+__global__ void k_unpack(Geom g, double* __restrict__ padded, const double* __restrict__ dense) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nint) return;
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1;
+  const int i = 1 + (int)(t % nx);
+  const int64_t r = t / nx;
+  const int j = 1 + (int)(r % ny);
+  const int k = g.kmin + (int)(r / ny);
+  padded[g.pad(i, j, k)] = dense[t];
+}
+
+__global__ void k_face_gather(Geom g, double* __restrict__ face, const double* __restrict__ full) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.ngamma) return;
+  int f = 0;
+  while (q >= g.face_off[f + 1]) ++f;
+  const int a = f >> 1, side = f & 1;
+  int64_t r = q - g.face_off[f];
+  int c[3] = {0, 0, 0};
+  for (int b = 0; b < g.dim; ++b) {
+    if (b == a) continue;
+    const int nb = g.N[b] - 1;
+    c[b] = 1 + (int)(r % nb);
+    r /= nb;
+  }
+  c[a] = side ? g.N[a] : 0;
+  face[q] = full[g.full(c[0], c[1], c[2])];
+}
+
+__global__ void k_recip(double* __restrict__ out, const double* __restrict__ in, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = 1.0 / in[t];
+}
+
+static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+template <typename T>
+cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
+                        const double* vedge, cudaStream_t st) {
+  k_vrhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, Q, f, vedge);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
+                        const double* gD, cudaStream_t st) {
+  k_urhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, V, ainv, Q, gD);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
+                         const double* afac, const double* gD, const double* gN, const double* lapt,
+                         cudaStream_t st) {
+  k_trace<T><<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt);
+  return cudaGetLastError();
+}
+cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st) {
+  k_write_full<<<nblk(g.nfull, 256), 256, 0, st>>>(g, out, Uin, bnd);
+  return cudaGetLastError();
+}
+cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,
+                          cudaStream_t st) {
+  k_v_full<<<nblk(g.nfull, 256), 256, 0, st>>>(g, vfull, Vpad, Q, vedge);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st) {
+  k_pack<<<nblk(g.nint, 256), 256, 0, st>>>(g, dense, padded);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack(const Geom& g, double* padded, const double* dense, cudaStream_t st) {
+  k_unpack<<<nblk(g.nint, 256), 256, 0, st>>>(g, padded, dense);
+  return cudaGetLastError();
+}
+cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, cudaStream_t st) {
+  k_face_gather<<<nblk(g.ngamma, 256), 256, 0, st>>>(g, face, full);
+  return cudaGetLastError();
+}
+cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st) {
+  k_recip<<<nblk(n, 256), 256, 0, st>>>(out, in, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_vrhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
+                                         const double*, cudaStream_t);
+template cudaError_t launch_urhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
+                                         const double*, const double*, cudaStream_t);
+template cudaError_t launch_trace<double>(const Geom&, const Coefs&, double*, const double*, const double*,
+                                          const double*, const double*, const double*, const double*, cudaStream_t);
+template cudaError_t launch_vrhs<float>(const Geom&, const Coefs&, float*, const double*, const double*,
+                                        const double*, cudaStream_t);
+template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const double*,
+                                        const double*, const double*, cudaStream_t);
+template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, const float*, const double*,
+                                         const double*, const double*, const double*, const double*, cudaStream_t);
+
+}  // namespace ahoc

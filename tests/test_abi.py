@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared
+entry point, and rejects bad arguments before touching a device."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2609_16478_b300 import ahoc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ahoc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ahoc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = ahoc.lib()
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(ahoc.SYMBOLS)
+
+
+def test_status_strings():
+    L = ahoc.lib()
+    for s in range(9):
+        assert L.ahoc_status_string(s).startswith(b"AHOC_")
+    assert L.ahoc_status_string(99) == b"unknown ahoc_status"
+
+
+def test_workspace_bytes_and_validation():
+    L = ahoc.lib()
+    nb2 = ahoc.workspace_bytes(2, [64, 64])
+    nb3 = ahoc.workspace_bytes(3, [16, 16, 16])
+    assert nb2 > 2 * 64 * 64 * 8 and nb3 > 2 * 16 ** 3 * 8
+    # grows with the Krylov cap
+    assert ahoc.workspace_bytes(2, [64, 64], restart=200) > nb2
+    out = C.c_size_t(0)
+    bad = [(4, [64, 64, 64, 64]), (2, [48, 64]), (2, [4, 64]), (3, [8192, 8, 8])]
+    for dim, N in bad:
+        n = (C.c_int64 * len(N))(*N)
+        st = L.ahoc_workspace_bytes(dim, n, None, C.byref(out))
+        assert st in (ahoc.AHOC_EINVAL, ahoc.AHOC_EUNSUPPORTED)
+        assert L.ahoc_last_error()
+
+
+def test_plan_create_rejects_before_allocating():
+    L = ahoc.lib()
+    h = C.c_void_p(0)
+    n = (C.c_int64 * 2)(64, 64)
+    lo = (C.c_double * 2)(0.0, 0.0)
+    hi = (C.c_double * 2)(1.0, 1.0)
+    # NULL alpha
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, None, None, None, None) == ahoc.AHOC_EINVAL
+    # empty box
+    assert L.ahoc_plan_create(C.byref(h), 2, n, hi, hi, C.c_void_p(256), None, None, None) == ahoc.AHOC_EINVAL
+    # unsupported precision / preconditioner
+    o = ahoc.ahoc_opts()
+    o.prec = 7
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), None, C.byref(o), None) == ahoc.AHOC_EUNSUPPORTED
+    # misaligned caller workspace
+    o = ahoc.ahoc_opts()
+    o.workspace = C.c_void_p(8)
+    o.workspace_bytes = 1 << 40
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), None, C.byref(o), None) == ahoc.AHOC_EINVAL
+    # too-small caller workspace
+    o.workspace = C.c_void_p(4096)
+    o.workspace_bytes = 16
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), None, C.byref(o), None) == ahoc.AHOC_ENOMEM
+    assert h.value is None
+    # NULL plan to the compute calls
+    assert L.ahoc_matvec(None, None, None) == ahoc.AHOC_EINVAL
+    assert L.ahoc_solve(None, None, None, C.c_double(1e-12), None) == ahoc.AHOC_EINVAL
+    assert L.ahoc_plan_destroy(None) == ahoc.AHOC_OK
+    assert L.ahoc_n_gamma(None) == -1

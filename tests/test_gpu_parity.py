@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the FP64 path must match the oracle's direct solve to relative
+L2 <= 1e-10 on U (the method reaches the same discrete solution up to the
+GMRES tolerance 1e-12 times the Schur condition number); component kernels
+(DST, Poisson, Schur action) are held to 1e-12 relative.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import golden
+from oracle import coupled, dst, residual
+from paper_2609_16478_b300 import ahoc, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_SOLVE = 1e-10
+TOL_COMP = 1e-12
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).reshape(-1).cuda()
+
+
+def _host(t, shape):
+    return t.detach().cpu().numpy().reshape(shape)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _plan(data, **kw):
+    return ahoc.plan_for(data, **kw)
+
+
+def _blank(N, dim, lo=None, hi=None):
+    shape = tuple(n + 1 for n in reversed(N))
+    return dict(dim=dim, N=list(N), lo=lo or [0.0] * dim, hi=hi or [1.0] * dim, alpha=np.ones(shape))
+
+
+# --- component kernels --------------------------------------------------------
+
+@pytest.mark.parametrize("N,axis", [((8, 8), 0), ((64, 64), 0), ((4096, 16), 0), ((32, 16), 0),
+                                    ((16, 32, 8), 0), ((16, 32, 8), 1), ((8, 1024, 8), 1), ((128, 64, 16), 1)])
+def test_dst1_matches_definition(N, axis):
+    dim = len(N)
+    p = _plan(_blank(N, dim))
+    rng = np.random.default_rng(7)
+    shape = tuple(n - 1 for n in reversed(N))
+    x = rng.normal(size=shape)
+    y = _host(p.dst1(_dev(x), axis), shape)
+    ref = dst.dst1(x, axis=dim - 1 - axis)
+    assert _rel(y, ref) < TOL_COMP * math.log2(N[axis])
+
+
+@pytest.mark.parametrize("N,lo,hi", [((64, 64), None, None), ((32, 16), [0, -0.5], [1, 0.3]), ((8, 8), None, None),
+                                     ((16, 16, 8), None, None), ((8, 16, 32), [0, 0, 0], [1, 2, 0.5])])
+def test_poisson_matches_sparse_solve(N, lo, hi):
+    dim = len(N)
+    p = _plan(_blank(N, dim, lo, hi))
+    rng = np.random.default_rng(3)
+    shape = tuple(n - 1 for n in reversed(N))
+    r = rng.normal(size=shape)
+    w = _host(p.poisson(_dev(r)), shape)
+    ref = coupled.poisson_solve(N, r, lo, hi)
+    assert _rel(w, ref) < TOL_COMP * 10
+
+
+# --- Lemma 1: the Schur action and right-hand side ---------------------------
+
+@pytest.mark.parametrize("name,N", [("sincos2d", [8, 8]), ("cfg1_2d", [16, 16]), ("sincos2d", [16, 8]),
+                                    ("sincos3d", [8, 8, 8]), ("cfg3_3d", [8, 16, 8])])
+def test_schur_matrix_columns(name, N):
+    prob = inputs.config_problem(name)
+    d = inputs.sample(prob, N)
+    p = _plan(d)
+    B = coupled.Blocks(coupled.assemble(d))
+    S = B.schur_dense()
+    ng = p.ngamma
+    Sg = np.empty((ng, ng))
+    e = torch.zeros(ng, dtype=torch.float64, device="cuda")
+    for j in range(ng):
+        e.zero_()
+        e[j] = 1.0
+        Sg[:, j] = p.matvec(e).cpu().numpy()
+    assert _rel(Sg, S) < TOL_COMP * 10
+    b = p.schur_rhs(_dev(d["f"])).cpu().numpy()
+    assert _rel(b, B.schur_rhs()) < TOL_COMP * 10
+
+
+# --- full solves against the direct solve -------------------------------------
+
+@pytest.mark.parametrize("name,N,lo,hi", [
+    ("cfg1_2d", [64, 64], None, None),          # the small configuration, GMRES tol 1e-12
+    ("sincos2d", [32, 32], None, None),         # nonzero g_D, g_N, tangential Laplacian, corner v
+    ("sincos2d", [64, 16], (0.0, -0.2), (1.0, 0.4)),   # anisotropic box and grid
+    ("cfg2_2d", [128, 128], None, None),
+    ("cavity", [64, 64], None, None),
+    ("plate", [64, 64], None, None),
+    ("sincos3d", [16, 16, 16], None, None),
+    ("cfg3_3d", [16, 8, 16], None, None),
+    ("poly2d", [8, 8], None, None),             # smallest grid
+])
+def test_solve_matches_oracle(name, N, lo, hi):
+    prob = inputs.config_problem(name)
+    d = inputs.sample(prob, N, lo=lo, hi=hi)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    p = _plan(d)
+    u, info = p.solve(_dev(d["f"]), tol=1e-12)
+    shape = tuple(n + 1 for n in reversed(N))
+    U = _host(u, shape)
+    inner = tuple(slice(1, -1) for _ in N)
+    assert _rel(U[inner], sol.U[inner]) < TOL_SOLVE, info
+    # boundary entries are g_D exactly
+    Ub = U.copy()
+    Ub[inner] = 0
+    Gb = np.asarray(d["g_D"]).reshape(shape).copy()
+    Gb[inner] = 0
+    assert np.array_equal(Ub, Gb)
+    q, v = p.last_qv()
+    assert _rel(q.cpu().numpy(), sol.Q) < 1e-9
+    assert _rel(_host(v, shape), sol.V) < 1e-9
+    assert info["iters"] >= 1 and info["rel_resid"] <= 1e-12
+
+
+def test_ragged_box_and_minimum_grid():
+    """Unequal N per axis (a ragged tail of tiles) and the smallest grid N = 8."""
+    for N in ([8, 8, 8], [64, 8], [8, 256]):
+        prob = inputs.config_problem("sincos3d" if len(N) == 3 else "sincos2d")
+        d = inputs.sample(prob, N)
+        sol = coupled.solve_direct(coupled.assemble(d), d)
+        u, _ = _plan(d).solve(_dev(d["f"]), tol=1e-12)
+        shape = tuple(n + 1 for n in reversed(N))
+        assert _rel(_host(u, shape), sol.U) < TOL_SOLVE
+
+
+def test_zero_data_gives_zero():
+    d = inputs.sample(inputs.config_problem("cavity"), [32, 32])
+    d["g_N"] = np.zeros_like(d["g_N"])
+    u, info = _plan(d).solve(_dev(d["f"]), tol=1e-12)
+    assert float(u.abs().max()) == 0.0 and info["iters"] == 0
+
+
+# --- the paper's printed benchmark values through the CUDA path ----------------
+
+def test_cavity_table6_n1024():
+    """Max |U| of the lid-driven cavity at N=1024 equals the paper's Table 6 value."""
+    rows = golden("cavity_table6.txt")
+    N = int(rows[0][0])
+    d = inputs.sample(inputs.config_problem("cavity"), [N, N])
+    u, info = _plan(d).solve(_dev(d["f"]), tol=1e-13)
+    U = _host(u, (N + 1, N + 1))
+    k = np.unravel_index(np.argmax(np.abs(U)), U.shape)
+    assert abs(abs(U[k]) - float(rows[0][1])) < 2e-10
+    assert abs(k[1] / N - 0.5) < 1e-12 and abs(k[0] / N - float(rows[0][3])) < 1e-4
+
+
+def test_plate_point_load():
+    ref = {r[0]: float(r[1]) for r in golden("plate_sec4.txt")}
+    N = 1024
+    d = inputs.sample(inputs.config_problem("plate"), [N, N])
+    p = _plan(d)
+    u, _ = p.solve(_dev(d["f"]), tol=1e-13)
+    U = _host(u, (N + 1, N + 1))
+    _, v = p.last_qv()
+    V = _host(v, (N + 1, N + 1))
+    assert abs(U[N // 2, N // 2] - ref["U_center"]) / ref["U_center"] < 2e-4
+    assert abs(-V[N, N // 2] - ref["minus_V_top_mid"]) / abs(ref["minus_V_top_mid"]) < 2e-4
+
+
+# --- full-size configurations: properties that hold at any size ---------------
+
+@pytest.mark.parametrize("name,N", [("cfg2_2d", [4096, 4096]), ("cfg3_3d", [128, 128, 128])])
+def test_large_grid_certificate(name, N):
+    """Beyond the direct solver's reach: the oracle's residual certificate of the
+    coupled equations evaluated on the GPU solution, and fourth-order accuracy."""
+    prob = inputs.config_problem(name)
+    dd = inputs.sample(prob, N, backend="torch", device="cuda")
+    p = _plan(dd)
+    u, info = p.solve(dd["f"].reshape(-1).contiguous(), tol=1e-12)
+    shape = tuple(n + 1 for n in reversed(N))
+    d = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in dd.items()}
+    U = _host(u, shape)
+    _, v = p.last_qv()
+    V = _host(v, shape)
+    ru, rv, rq = residual.coupled_residual(U, V, d)
+    vmax = np.max(np.abs(V))
+    assert np.max(np.abs(ru)) < 1e-9 * vmax
+    assert np.max(np.abs(rv)) < 1e-9 * np.max(np.abs(d["f"]))
+    assert np.max(np.abs(rq)) < 1e-9 * vmax
+    err = np.max(np.abs(U - d["u_exact"]))
+    assert err < (1e-8 if len(N) == 2 else 1e-6), err
