@@ -85,7 +85,9 @@ typedef struct {
   int max_iters;          /* [500] total GMRES iterations allowed                               */
   int restart;            /* [100] Krylov basis size before a restart (the paper's GMRES is not
                              restarted; the cap only bounds memory)                            */
-  int precond;            /* [0] reserved for a boundary preconditioner; must be 0              */
+  int precond;            /* [1] 1: right-precondition GMRES with the boundary-symbol operator
+                             (inverse single-face Schur symbol per face, coefficient frozen
+                             pointwise on the face); 0: no preconditioner                    */
   double refine_tol;      /* [0] reserved                                                      */
   int timing;             /* [0] nonzero: time every kernel launch of ahoc_solve with CUDA
                              events on the plan's stream (ahoc_info.kernel_ms)               */

@@ -123,7 +123,7 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0):
 def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 0)
+    o = _opts(prec, 500, restart, 1)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -138,7 +138,7 @@ class Plan:
 
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
-                 max_iters: int = 500, restart: int = 100, precond: int = 0, stream=None, timing: bool = False):
+                 max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False):
         L = lib()
         self.dim = dim
         self.N = [int(n) for n in N]

@@ -52,6 +52,7 @@ struct Coefs {
 template <typename T>
 struct alignas(16) Mode {
   T r, rinv, s, kap, rj0;
+  T kapC;  // -r / (1 - r^(2N)): coefficient of the boundary correction r^j - r^(2N-j)
   int j0;
 };
 

@@ -270,6 +270,42 @@ __global__ void __launch_bounds__(512) k_dst_y(Geom g, T* __restrict__ a, const 
 }
 
 // ---------------------------------------------------------------------------
+// Generic lines (face arrays): line l has N-1 elements at
+//   base + (l / lpg) * gstride + (l % lpg) * lstride + (j - 1) * estride,  j = 1..N-1
+// (the zero x_0 is implicit).  Used for the transverse DSTs of the boundary
+// preconditioner on the face arrays.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_dst_gen(T* __restrict__ base, int nlines, int lpg, int64_t gstride,
+                                                 int64_t lstride, int64_t estride, int N,
+                                                 const typename Cplx<T>::t* __restrict__ tw, const T* __restrict__ sn,
+                                                 int logN, int TPL, int LPC) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* wsum = s + (int64_t)LPC * N;
+  const int l0 = blockIdx.x * LPC;
+  const int tot = LPC * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e >> logN;
+    const int j = e & (N - 1);
+    const int line = l0 + l;
+    T v = 0;
+    if (j > 0 && line < nlines)
+      v = base[(int64_t)(line / lpg) * gstride + (int64_t)(line % lpg) * lstride + (int64_t)(j - 1) * estride];
+    s[e] = v;
+  }
+  __syncthreads();
+  dst_lines<T>(s, N, N, logN, TPL, tw, sn, wsum);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e >> logN;
+    const int j = e & (N - 1);
+    const int line = l0 + l;
+    if (j > 0 && line < nlines)
+      base[(int64_t)(line / lpg) * gstride + (int64_t)(line % lpg) * lstride + (int64_t)(j - 1) * estride] = s[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline int ilog2(int n) {
@@ -316,6 +352,26 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
                                           TPL, LPC, LS);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_t lstride, int64_t estride, int N,
+                           const void* tw, const T* sn, cudaStream_t st) {
+  const int logN = ilog2(N);
+  const int TPL = N / 8;
+  const int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  const int threads = TPL * LPC;
+  const int blocks = (nlines + LPC - 1) / LPC;
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_dst_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_dst_gen<T><<<blocks, threads, smem, st>>>(base, nlines, lpg, gstride, lstride, estride, N,
+                                               reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, logN, TPL, LPC);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dst_gen<double>(double*, int, int, int64_t, int64_t, int64_t, int, const void*,
+                                            const double*, cudaStream_t);
 
 template cudaError_t launch_dst_x<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
 template cudaError_t launch_dst_y<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);

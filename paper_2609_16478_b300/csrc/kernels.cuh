@@ -10,6 +10,27 @@ cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T sca
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
 
+// DST-I of generic strided lines (see dst.cu, k_dst_gen)
+template <typename T>
+cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_t lstride, int64_t estride, int N,
+                           const void* tw, const T* sn, cudaStream_t st);
+
+// Boundary preconditioner (precond.cu)
+struct SymAxis {
+  const double* stab;  // sin(j pi / N_a), j < 2 N_a
+  const double* ctab;  // cos(k pi / N_b) per transverse axis b (indexed by axis)
+};
+cudaError_t launch_face_symbols(const Geom& g, const Coefs& cf, double* pre, const double* const* stab,
+                                const double* const* ctab, cudaStream_t st);
+// out[q] = in[q] * (mul ? mul[q] : 1) / (div ? div[q] : 1)
+cudaError_t launch_face_muldiv(double* out, const double* in, const double* mul, const double* div, int64_t n,
+                               cudaStream_t st);
+
+// chunked tridiagonal solve (2D: few columns, many chunks per column)
+template <typename T>
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, cudaStream_t st);
+size_t tri_chunked_scratch(const Geom& g, int L);
+
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st);
 

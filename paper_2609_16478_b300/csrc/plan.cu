@@ -42,7 +42,7 @@ struct Opts {
   ahoc_precision prec = AHOC_FP64;
   int max_iters = 500;
   int restart = 100;
-  int precond = 0;
+  int precond = 1;
   int timing = 0;
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
@@ -54,13 +54,13 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.prec = o->prec;
     if (o->max_iters > 0) d.max_iters = o->max_iters;
     if (o->restart > 0) d.restart = o->restart;
-    d.precond = o->precond;
+    d.precond = o->precond < 0 ? 1 : o->precond;
     d.timing = o->timing;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
   if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "only AHOC_FP64 is implemented");
-  if (d.precond != 0) return fail(AHOC_EUNSUPPORTED, "precond must be 0");
+  if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
     return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
@@ -202,6 +202,7 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<double>>
       m.s = (double)(scale / sigma);
       const long double r2N = powl(r, 2.0L * Nt);
       m.kap = (double)(-r * (1 - r * r) / (1 - r2N));
+      m.kapC = (double)(-r / (1 - r2N));
       if (r == 0.0L) {
         m.rinv = 0;
         m.rj0 = 0;
@@ -223,9 +224,15 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<double>>
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, modes, b, Q, r, Kry, partial, hdev, tmp,
-      total;
+  size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
+      tmp, z, pre, stab[3], ctab[3], tri, total;
 };
+
+// The chunked tridiagonal form is used when the transverse modes alone give
+// too few threads (2D, small 3D grids).
+constexpr int64_t kChunkedBelow = 65536;
+int tri_chunk_len(const Geom& g) { return ((g.dim == 3 ? g.N[2] : g.N[1]) >= 1024) ? 32 : 16; }
+int64_t tri_ncols(const Geom& g) { return (int64_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1); }
 
 constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 
@@ -252,6 +259,15 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.snx = take(((size_t)g.N[0] / 2 + 1) * sizeof(double));
   L.twy = take(2 * (size_t)g.N[1] * sizeof(double));
   L.sny = take(((size_t)g.N[1] / 2 + 1) * sizeof(double));
+  L.twz = take(2 * (size_t)g.N[2] * sizeof(double));
+  L.snz = take(((size_t)g.N[2] / 2 + 1) * sizeof(double));
+  for (int a = 0; a < 3; ++a) {
+    L.stab[a] = take(2 * (size_t)g.N[a] * sizeof(double));
+    L.ctab[a] = take(((size_t)g.N[a] + 1) * sizeof(double));
+  }
+  L.pre = take(face);
+  L.z = take(face);
+  L.tri = take(tri_ncols(g) < kChunkedBelow ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
   const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
   L.modes = take(nmodes * sizeof(Mode<double>));
   L.b = take(face);
@@ -276,7 +292,8 @@ struct ahoc_plan {
   bool own_ws = false;
   Layout L;
   double *W1, *W2, *ainv, *afac, *gD = nullptr, *vedge = nullptr, *gN = nullptr, *lapt = nullptr;
-  double *twx, *snx, *twy, *sny, *b, *Q, *r, *tmp, *Kry, *partial, *hdev;
+  double *twx, *snx, *twy, *sny, *twz, *snz, *b, *Q, *r, *tmp, *Kry, *partial, *hdev, *z, *pre, *tri;
+  double *stab[3], *ctab[3];
   Mode<double>* modes;
   double* hhost = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -344,7 +361,10 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
   const Geom& g = p->g;
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
-  RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
+  if (tri_ncols(g) < kChunkedBelow)
+    RUN(AHOC_K_TRI, launch_tri_chunked<double>(g, W, p->modes, p->tri, tri_chunk_len(g), p->st));
+  else
+    RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   return AHOC_OK;
@@ -363,6 +383,43 @@ ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) 
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
+  return AHOC_OK;
+}
+
+// Transverse DST-I of every face with normal `a`, along each in-face axis.
+ahoc_status face_dsts(ahoc_plan* p, double* v, int a) {
+  const Geom& g = p->g;
+  double* base = v + g.face_off[2 * a];
+  const int64_t fs = g.face_off[2 * a + 1] - g.face_off[2 * a];
+  int rem[2], nr = 0;
+  for (int b = 0; b < g.dim; ++b)
+    if (b != a) rem[nr++] = b;
+  const double* tw[3] = {p->twx, p->twy, p->twz};
+  const double* sn[3] = {p->snx, p->sny, p->snz};
+  if (nr == 1) {
+    const int b = rem[0];
+    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2, 1, fs, 0, 1, g.N[b], tw[b], sn[b], p->st));
+  } else {
+    const int b0 = rem[0], b1 = rem[1];
+    const int n0 = g.N[b0] - 1, n1 = g.N[b1] - 1;
+    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n1, n1, fs, n0, 1, g.N[b0], tw[b0], sn[b0], p->st));
+    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n0, n0, fs, 1, n0, g.N[b1], tw[b1], sn[b1], p->st));
+  }
+  return AHOC_OK;
+}
+
+// out = P^-1 in: the boundary-symbol preconditioner (precond.cu); in, out may alias.
+ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
+  const int64_t n = p->g.ngamma;
+  if (!p->o.precond) {
+    if (in != out) CK(cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    return AHOC_OK;
+  }
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, in, nullptr, p->afac, n, p->st));
+  for (int a = 0; a < p->g.dim; ++a) CKS(face_dsts(p, out, a));
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->pre, nullptr, n, p->st));
+  for (int a = 0; a < p->g.dim; ++a) CKS(face_dsts(p, out, a));
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->afac, nullptr, n, p->st));
   return AHOC_OK;
 }
 
@@ -466,6 +523,15 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->snx = at<double>(p, L.snx);
   p->twy = at<double>(p, L.twy);
   p->sny = at<double>(p, L.sny);
+  p->twz = at<double>(p, L.twz);
+  p->snz = at<double>(p, L.snz);
+  for (int a = 0; a < 3; ++a) {
+    p->stab[a] = at<double>(p, L.stab[a]);
+    p->ctab[a] = at<double>(p, L.ctab[a]);
+  }
+  p->pre = at<double>(p, L.pre);
+  p->z = at<double>(p, L.z);
+  p->tri = at<double>(p, L.tri);
   p->modes = at<Mode<double>>(p, L.modes);
   p->b = at<double>(p, L.b);
   p->Q = at<double>(p, L.Q);
@@ -498,8 +564,35 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   CKC(cudaMemcpyAsync(p->twy, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
   CKC(cudaMemcpyAsync(p->sny, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
   CKC(cudaMemcpyAsync(p->modes, modes.data(), modes.size() * sizeof(Mode<double>), cudaMemcpyHostToDevice, p->st));
+  CKC(cudaStreamSynchronize(p->st));
+  if (g.dim == 3) {
+    dst_tables(g.N[2], tw, sn);
+    CKC(cudaMemcpyAsync(p->twz, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaMemcpyAsync(p->snz, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaStreamSynchronize(p->st));
+  }
+  {
+    // sin(j pi / N_a), j < 2 N_a and cos(k pi / N_a), k <= N_a, for the preconditioner symbols
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double> st, ct;
+    for (int a = 0; a < g.dim; ++a) {
+      const int Na = g.N[a];
+      st.resize(2 * (size_t)Na);
+      ct.resize((size_t)Na + 1);
+      for (int j = 0; j < 2 * Na; ++j) st[j] = (double)sinl(pi * j / Na);
+      for (int k = 0; k <= Na; ++k) ct[k] = (double)cosl(pi * k / Na);
+      CKC(cudaMemcpyAsync(p->stab[a], st.data(), st.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      CKC(cudaMemcpyAsync(p->ctab[a], ct.data(), ct.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      CKC(cudaStreamSynchronize(p->st));
+    }
+  }
   CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
   CKC(launch_face_gather(g, p->afac, alpha, p->st));
+  if (o.precond) {
+    const double* stp[3] = {p->stab[0], p->stab[1], g.dim == 3 ? p->stab[2] : nullptr};
+    const double* ctp[3] = {p->ctab[0], p->ctab[1], g.dim == 3 ? p->ctab[2] : nullptr};
+    CKC(launch_face_symbols(g, cf, p->pre, stp, ctp, p->st));
+  }
   if (bd && bd->g_D) {
     p->gD = at<double>(p, L.gD);
     CKC(cudaMemcpyAsync(p->gD, bd->g_D, full, cudaMemcpyDeviceToDevice, p->st));
@@ -628,7 +721,8 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
       for (int j = 0; j < m; ++j) {
         double* w = V + (int64_t)(j + 1) * n;
         CK(cudaEventRecord(p->ev0, p->st));
-        CKS(matvec_dev(p, V + (int64_t)j * n, w));
+        CKS(precond_apply(p, V + (int64_t)j * n, p->z));
+        CKS(matvec_dev(p, p->z, w));
         CK(cudaEventRecord(p->ev1, p->st));
         // CGS2
         double* h1 = p->hdev;
@@ -676,7 +770,11 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
       }
       for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
       CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
-      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->Q, n, p->st));
+      // Q += P^-1 (V y)
+      CK(cudaMemsetAsync(p->tmp, 0, n * sizeof(double), p->st));
+      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->tmp, n, p->st));
+      CKS(precond_apply(p, p->tmp, p->z));
+      RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->z, 1.0, 1.0, n, p->st));
       CK(cudaStreamSynchronize(p->st));
       CKS(harvest(p));
       if (done) break;

@@ -89,6 +89,225 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   }
 }
 
+// ---------------------------------------------------------------------------
+// Chunked form for few columns (2D): each column is cut into chunks of L rows
+// so that (columns x chunks) threads share the work.  With u = p + C phi,
+// phi_j = r^j - r^(2N-j) and C = kapC * p_1:
+//   T1  forward recurrence per chunk from a zero carry: chunk end value E_c
+//   T1b per column: carries  w_{s_c - 1} = E_{c-1} + r^len carry_{c-1}
+//   T2  forward recurrence with the true carry, then the backward recurrence
+//       from a zero carry at the chunk end: local p stored, chunk start B_c
+//   T2b per column: backward carries p_{e_c + 1} and p_1, hence C
+//   T3  u_j = p_local_j + r^(e_c + 1 - j) p_{e_c + 1} + C (r^j - r^(2N - j))
+// Powers are run in the direction in which they shrink (no underflow is ever
+// scaled back up); r^n at a chunk boundary comes from binary powering.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ipow(T r, int n) {
+  T out = 1, b = r;
+  while (n > 0) {
+    if (n & 1) out *= b;
+    b *= b;
+    n >>= 1;
+  }
+  return out;
+}
+
+struct TriShape {
+  int64_t ncols;
+  int nt, Nt, C, L;
+  int64_t stride;
+};
+
+__device__ __forceinline__ TriShape tri_shape(const Geom& g, int L) {
+  TriShape s;
+  const int nx = g.N[0] - 1;
+  s.ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  s.Nt = (g.dim == 3) ? g.N[2] : g.N[1];
+  s.nt = s.Nt - 1;
+  s.L = L;
+  s.C = (s.nt + L - 1) / L;
+  s.stride = (g.dim == 3) ? g.n0 * g.n1 : g.n0;
+  return s;
+}
+
+__device__ __forceinline__ int64_t col_base(const Geom& g, int64_t m) {
+  const int nx = g.N[0] - 1;
+  const int ix = 1 + (int)(m % nx);
+  const int iy = (g.dim == 3) ? 1 + (int)(m / nx) : 0;
+  return ix + g.n0 * (int64_t)iy;
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
+                                                T* __restrict__ E) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int len = min(L, sh.nt - s0 + 1);
+  const T* col = a + col_base(g, m);
+  const T r = modes[m].r, s = modes[m].s;
+  T d[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
+  T w = 0;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) w = r * w + s * d[q];
+  E[(int64_t)c * sh.ncols + m] = w;
+}
+
+template <typename T>
+__global__ void k_tri_t1b(Geom g, const Mode<T>* __restrict__ modes, const T* __restrict__ E, T* __restrict__ carry,
+                          int L) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= sh.ncols) return;
+  const T r = modes[m].r;
+  const T rL = ipow(r, L);
+  T cy = 0;
+  for (int c = 0; c < sh.C; ++c) {
+    carry[(int64_t)c * sh.ncols + m] = cy;
+    cy = E[(int64_t)c * sh.ncols + m] + rL * cy;  // only the last chunk may be shorter; its carry-out is unused
+  }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
+                                                const T* __restrict__ carry, T* __restrict__ B) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int len = min(L, sh.nt - s0 + 1);
+  T* col = a + col_base(g, m);
+  const T r = modes[m].r, s = modes[m].s;
+  T d[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
+  T w = carry[(int64_t)c * sh.ncols + m];
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) {
+      w = r * w + s * d[q];
+      d[q] = w;
+    }
+  T p = 0;
+#pragma unroll
+  for (int q = L - 1; q >= 0; --q)
+    if (q < len) {
+      p = r * p + d[q];
+      d[q] = p;
+    }
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+  B[(int64_t)c * sh.ncols + m] = p;
+}
+
+template <typename T>
+__global__ void k_tri_t2b(Geom g, const Mode<T>* __restrict__ modes, const T* __restrict__ B, T* __restrict__ bcarry,
+                          T* __restrict__ Cc, int L) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= sh.ncols) return;
+  const T r = modes[m].r;
+  const T rL = ipow(r, L);
+  const int lastlen = sh.nt - (sh.C - 1) * L;
+  T bc = 0;
+  for (int c = sh.C - 1; c >= 0; --c) {
+    bcarry[(int64_t)c * sh.ncols + m] = bc;
+    const T rlen = (c == sh.C - 1) ? ipow(r, lastlen) : rL;
+    bc = B[(int64_t)c * sh.ncols + m] + rlen * bc;  // p at the chunk start
+  }
+  Cc[m] = modes[m].kapC * bc;  // bc = p_1
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
+                                                const T* __restrict__ bcarry, const T* __restrict__ Cc) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int len = min(L, sh.nt - s0 + 1);
+  const int e0 = s0 + len - 1;
+  T* col = a + col_base(g, m);
+  const T r = modes[m].r;
+  const T bc = bcarry[(int64_t)c * sh.ncols + m];
+  const T Cm = Cc[m];
+  T d[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
+  // descending: r^(e0 + 1 - j) * bc and - C r^(2N - j), both shrinking as j decreases
+  T rb = r * bc;
+  T Bj = Cm * ipow(r, 2 * sh.Nt - e0);
+#pragma unroll
+  for (int q = L - 1; q >= 0; --q)
+    if (q < len) {
+      d[q] += rb - Bj;
+      rb *= r;
+      Bj *= r;
+    }
+  // ascending: + C r^j, shrinking as j increases
+  T Aj = Cm * ipow(r, s0);
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) {
+      d[q] += Aj;
+      Aj *= r;
+    }
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+}
+
+size_t tri_chunked_scratch(const Geom& g, int L) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  return (size_t)(4 * C + 1) * ncols;  // elements
+}
+
+template <typename T, int L>
+static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* scratch, cudaStream_t st) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  T* E = scratch;
+  T* carry = E + (int64_t)C * ncols;
+  T* B = carry + (int64_t)C * ncols;
+  T* bcarry = B + (int64_t)C * ncols;
+  T* Cc = bcarry + (int64_t)C * ncols;
+  const int64_t work = ncols * C;
+  const unsigned gb = (unsigned)((work + 127) / 128);
+  const unsigned cb = (unsigned)((ncols + 127) / 128);
+  k_tri_t1<T, L><<<gb, 128, 0, st>>>(g, a, modes, E);
+  k_tri_t1b<T><<<cb, 128, 0, st>>>(g, modes, E, carry, L);
+  k_tri_t2<T, L><<<gb, 128, 0, st>>>(g, a, modes, carry, B);
+  k_tri_t2b<T><<<cb, 128, 0, st>>>(g, modes, B, bcarry, Cc, L);
+  k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, bcarry, Cc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, cudaStream_t st) {
+  if (L == 32) return tri_chunked_L<T, 32>(g, a, modes, scratch, st);
+  if (L == 16) return tri_chunked_L<T, 16>(g, a, modes, scratch, st);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, double*, int, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st) {
   const int nx = g.N[0] - 1;
