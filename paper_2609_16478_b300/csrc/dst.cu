@@ -192,9 +192,42 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
 
 // ---------------------------------------------------------------------------
 // x axis: lines are rows (j, k) of the padded layout, contiguous in memory.
+// LOAD 0: plain load of src.  LOAD 1 (2D): the u-equation right-hand side
+// M(W) with W = V/alpha in src (W = 0 in the pad slots) plus the face
+// values Q/alpha where M reaches the boundary; src must not alias dst.
+// STORE 0: out = scale * X.  STORE 1: out = X * (1/alpha) at the point.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
+struct DstIO {
+  const T* src;
+  const double* Q;      // LOAD 1: face values
+  const double* afac;   // LOAD 1: alpha at face points
+  const double* ainv;   // STORE 1: 1/alpha on the full grid
+  double Mc, Mn;        // LOAD 1: weighting M
+};
+
+template <typename T>
+__device__ __forceinline__ T mstencil2d(const Geom& g, const DstIO<T>& io, int i, int j) {
+  const T* W = io.src;
+  const int64_t o = g.pad(i, j, 0);
+  double acc = io.Mc * (double)W[o];
+  double nb = 0.0;
+  // x neighbours (i-1 = 0 and i+1 = N0 are faces x-/x+)
+  if (i > 1) nb += (double)W[o - 1];
+  else { const int64_t q = g.face(0, 0, 0, j, 0); nb += io.Q[q] / io.afac[q]; }
+  if (i < g.N[0] - 1) nb += (double)W[o + 1];
+  else { const int64_t q = g.face(0, 1, g.N[0], j, 0); nb += io.Q[q] / io.afac[q]; }
+  // y neighbours (faces y-/y+)
+  if (j > 1) nb += (double)W[o - g.n0];
+  else { const int64_t q = g.face(1, 0, i, 0, 0); nb += io.Q[q] / io.afac[q]; }
+  if (j < g.N[1] - 1) nb += (double)W[o + g.n0];
+  else { const int64_t q = g.face(1, 1, i, g.N[1], 0); nb += io.Q[q] / io.afac[q]; }
+  return (T)(acc + io.Mn * nb);
+}
+
+template <typename T, int LOAD, int STORE>
+__global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<T> io,
+                                               const typename Cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ sn, T scale, int logN, int TPL, int LPC) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
@@ -203,19 +236,24 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, const 
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
   const int64_t r0 = (int64_t)blockIdx.x * LPC;
   using C = typename Cplx<T>::t;
-  // load (vectorised pairs); slot 0 of each line is the zero pad
   const int tot2 = (LPC * N) >> 1;
   for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
     const int l = (2 * e) >> logN;
     const int pos = (2 * e) & (N - 1);
     const int64_t r = r0 + l;
     C v;
-    v.x = 0; v.y = 0;
+    v.x = 0;
+    v.y = 0;
     if (r < nrows) {
       const int j = 1 + (int)(r % (g.N[1] - 1));
       const int k = g.kmin + (int)(r / (g.N[1] - 1));
-      v = *reinterpret_cast<const C*>(a + g.pad(pos, j, k));
-      if (pos == 0) v.x = 0;
+      if (LOAD == 0) {
+        v = *reinterpret_cast<const C*>(io.src + g.pad(pos, j, k));
+        if (pos == 0) v.x = 0;
+      } else {
+        if (pos > 0) v.x = mstencil2d<T>(g, io, pos, j);
+        v.y = mstencil2d<T>(g, io, pos + 1, j);
+      }
     }
     *reinterpret_cast<C*>(s + l * N + pos) = v;
   }
@@ -229,8 +267,14 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, const 
       const int j = 1 + (int)(r % (g.N[1] - 1));
       const int k = g.kmin + (int)(r / (g.N[1] - 1));
       C v = *reinterpret_cast<const C*>(s + l * N + pos);
-      v.x *= scale;
-      v.y *= scale;
+      if (STORE == 0) {
+        v.x *= scale;
+        v.y *= scale;
+      } else {
+        const int64_t f = g.full(pos, j, k);
+        v.x = (pos == 0) ? (T)0 : (T)((double)v.x * io.ainv[f]);
+        v.y = (T)((double)v.y * io.ainv[f + 1]);
+      }
       if (pos == 0) v.x = 0;
       *reinterpret_cast<C*>(a + g.pad(pos, j, k)) = v;
     }
@@ -314,8 +358,9 @@ static inline int ilog2(int n) {
   return l;
 }
 
-template <typename T>
-cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
+template <typename T, int LOAD, int STORE>
+static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const void* tw, const T* sn, T scale,
+                              cudaStream_t st) {
   const int N = (int)g.n0;
   const int logN = ilog2(N);
   const int TPL = N / 8;
@@ -325,13 +370,41 @@ cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T sca
   const int64_t blocks = (nrows + LPC - 1) / LPC;
   const size_t smem = ((size_t)LPC * N + 32) * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_dst_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dst_x<T, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_dst_x<T><<<(unsigned)blocks, threads, smem, st>>>(g, a, reinterpret_cast<const typename Cplx<T>::t*>(tw), sn,
-                                                       scale, logN, TPL, LPC);
+  k_dst_x<T, LOAD, STORE><<<(unsigned)blocks, threads, smem, st>>>(
+      g, dst, io, reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, scale, logN, TPL, LPC);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
+  DstIO<T> io{a, nullptr, nullptr, nullptr, 0.0, 0.0};
+  return dst_x_impl<T, 0, 0>(g, a, io, tw, sn, scale, st);
+}
+
+// in place, storing X / alpha (the inverse transform of V, giving W = V/alpha)
+template <typename T>
+cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
+                                    cudaStream_t st) {
+  DstIO<T> io{a, nullptr, nullptr, ainv, 0.0, 0.0};
+  return dst_x_impl<T, 0, 1>(g, a, io, tw, sn, (T)1, st);
+}
+
+// dst = DST_x( M(W) + boundary Q/alpha terms ), 2D, src = W must not alias dst
+template <typename T>
+cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
+                               double Mn, const void* tw, const T* sn, cudaStream_t st) {
+  DstIO<T> io{W, Q, afac, nullptr, Mc, Mn};
+  return dst_x_impl<T, 1, 0>(g, dst, io, tw, sn, (T)1, st);
+}
+
+template cudaError_t launch_dst_x_store_ainv<double>(const Geom&, double*, const double*, const void*, const double*,
+                                                     cudaStream_t);
+template cudaError_t launch_dst_x_mload<double>(const Geom&, double*, const double*, const double*, const double*,
+                                                double, double, const void*, const double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {

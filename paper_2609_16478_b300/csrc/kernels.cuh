@@ -9,6 +9,37 @@ template <typename T>
 cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
+                                    cudaStream_t st);
+template <typename T>
+cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
+                               double Mn, const void* tw, const T* sn, cudaStream_t st);
+
+// Generated right-hand side of the homogeneous v-equation in the x-spectral
+// domain (2D): d(k, j) = sin(k pi/N0) (rxm_j + (-1)^(k+1) rxp_j)
+//                        - b_k (Qh-_k [j = 1] + Qh+_k [j = N1-1]),  b_k = L_y + 2 cos(k pi/N0) L_xy
+struct VGen2D {
+  const double* rxm;  // index j (1..N1-1)
+  const double* rxp;
+  const double* qhm;  // index k - 1
+  const double* qhp;
+  const double* sk;   // sin(k pi / N0), index k
+  const double* ck;   // cos(k pi / N0), index k
+  double Ly, Lxy;
+};
+template <typename T>
+cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, const VGen2D& G,
+                                   cudaStream_t st);
+
+// fused 2D matvec helpers (fused2d.cu)
+cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
+                            cudaStream_t st);
+cudaError_t launch_trace2d_x(const Geom& g, double* y, const double* Uh, const double* Q, const double* afac,
+                             const double* tau, cudaStream_t st);
+cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const double* Uh, cudaStream_t st);
+cudaError_t launch_trace2d_y(const Geom& g, double* y, const double* R, const double* Q, const double* afac,
+                             cudaStream_t st);
 
 // DST-I of generic strided lines (see dst.cu, k_dst_gen)
 template <typename T>

@@ -225,7 +225,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
-      tmp, z, pre, stab[3], ctab[3], tri, total;
+      tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -268,6 +268,12 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.pre = take(face);
   L.z = take(face);
   L.tri = take(tri_ncols(g) < kChunkedBelow ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  // fused 2D matvec scratch
+  L.rxm = take(((size_t)g.N[1] + 1) * sizeof(double));
+  L.rxp = take(((size_t)g.N[1] + 1) * sizeof(double));
+  L.qy = take(2 * (size_t)g.N[0] * sizeof(double));
+  L.R2 = take(2 * (size_t)g.N[0] * sizeof(double));
+  L.tau = take(((size_t)g.N[0] + 1) * sizeof(double));
   const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
   L.modes = take(nmodes * sizeof(Mode<double>));
   L.b = take(face);
@@ -294,6 +300,7 @@ struct ahoc_plan {
   double *W1, *W2, *ainv, *afac, *gD = nullptr, *vedge = nullptr, *gN = nullptr, *lapt = nullptr;
   double *twx, *snx, *twy, *sny, *twz, *snz, *b, *Q, *r, *tmp, *Kry, *partial, *hdev, *z, *pre, *tri;
   double *stab[3], *ctab[3];
+  double *rxm, *rxp, *qy, *R2, *tau;
   Mode<double>* modes;
   double* hhost = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -380,7 +387,30 @@ ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) 
   return AHOC_OK;
 }
 
+// SchurMatVec in 2D without full-field right-hand sides or inverse transforms:
+// V-hat from the generated spectrum (tri), W = V/alpha by one inverse DST,
+// G-hat = DST(M(W) + face terms) by one forward DST, U-hat by tri, then the
+// traces from U-hat directly.
+ahoc_status matvec_fused2d(ahoc_plan* p, const double* q, double* y) {
+  const Geom& g = p->g;
+  const Coefs& cf = p->cf;
+  const int N0 = g.N[0];
+  RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
+  RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
+  VGen2D G{p->rxm, p->rxp, p->qy, p->qy + (N0 - 1), p->stab[0], p->ctab[0], cf.L[16], cf.L[17]};
+  RUN(AHOC_K_TRI, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->tri, tri_chunk_len(g), G, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<double>(g, p->W1, p->ainv, p->twx, p->snx, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_mload<double>(g, p->W2, p->W1, q, p->afac, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
+  RUN(AHOC_K_TRI, launch_tri_chunked<double>(g, p->W2, p->modes, p->tri, tri_chunk_len(g), p->st));
+  RUN(AHOC_K_TRACE, launch_trace2d_x(g, y, p->W2, q, p->afac, p->tau, p->st));
+  RUN(AHOC_K_TRACE, launch_trace2d_ylines(g, cf, p->R2, p->W2, p->st));
+  RUN(AHOC_K_TRACE, launch_dst_gen<double>(p->R2, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
+  RUN(AHOC_K_TRACE, launch_trace2d_y(g, y, p->R2, q, p->afac, p->st));
+  return AHOC_OK;
+}
+
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
+  if (p->g.dim == 2 && tri_ncols(p->g) < kChunkedBelow) return matvec_fused2d(p, q, y);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -532,6 +562,11 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->pre = at<double>(p, L.pre);
   p->z = at<double>(p, L.z);
   p->tri = at<double>(p, L.tri);
+  p->rxm = at<double>(p, L.rxm);
+  p->rxp = at<double>(p, L.rxp);
+  p->qy = at<double>(p, L.qy);
+  p->R2 = at<double>(p, L.R2);
+  p->tau = at<double>(p, L.tau);
   p->modes = at<Mode<double>>(p, L.modes);
   p->b = at<double>(p, L.b);
   p->Q = at<double>(p, L.Q);
@@ -585,6 +620,15 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
       CKC(cudaMemcpyAsync(p->ctab[a], ct.data(), ct.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
       CKC(cudaStreamSynchronize(p->st));
     }
+    // tau_k = sum_m w_m sin(m k pi / N0): one-sided x-face weights in x-modes (fused 2D trace)
+    std::vector<double> tau((size_t)g.N[0] + 1, 0.0);
+    for (int k = 1; k < g.N[0]; ++k) {
+      long double t = 0;
+      for (int m = 1; m <= 3; ++m) t += (long double)cf.w[0][m] * sinl(pi * (long double)(m * k) / g.N[0]);
+      tau[k] = (double)t;
+    }
+    CKC(cudaMemcpyAsync(p->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaStreamSynchronize(p->st));
   }
   CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
   CKC(launch_face_gather(g, p->afac, alpha, p->st));

@@ -138,9 +138,20 @@ __device__ __forceinline__ int64_t col_base(const Geom& g, int64_t m) {
   return ix + g.n0 * (int64_t)iy;
 }
 
-template <typename T, int L>
+// generated right-hand side of the homogeneous v-equation (2D), see VGen2D
+__device__ __forceinline__ double vgen(const VGen2D& G, int k, int j, int Nt) {
+  double v = G.sk[k] * (G.rxm[j] + ((k & 1) ? G.rxp[j] : -G.rxp[j]));
+  if (j == 1 || j == Nt - 1) {
+    const double bk = G.Ly + 2.0 * G.ck[k] * G.Lxy;
+    if (j == 1) v -= bk * G.qhm[k - 1];
+    if (j == Nt - 1) v -= bk * G.qhp[k - 1];
+  }
+  return v;
+}
+
+template <typename T, int L, bool GEN>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                T* __restrict__ E) {
+                                                T* __restrict__ E, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -152,7 +163,8 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   const T r = modes[m].r, s = modes[m].s;
   T d[L];
 #pragma unroll
-  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
+  for (int q = 0; q < L; ++q)
+    d[q] = (q < len) ? (GEN ? (T)vgen(G, (int)m + 1, s0 + q, sh.Nt) : col[(int64_t)(s0 + q) * sh.stride]) : (T)0;
   T w = 0;
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -175,9 +187,9 @@ __global__ void k_tri_t1b(Geom g, const Mode<T>* __restrict__ modes, const T* __
   }
 }
 
-template <typename T, int L>
+template <typename T, int L, bool GEN>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                const T* __restrict__ carry, T* __restrict__ B) {
+                                                const T* __restrict__ carry, T* __restrict__ B, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -189,7 +201,8 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
   const T r = modes[m].r, s = modes[m].s;
   T d[L];
 #pragma unroll
-  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
+  for (int q = 0; q < L; ++q)
+    d[q] = (q < len) ? (GEN ? (T)vgen(G, (int)m + 1, s0 + q, sh.Nt) : col[(int64_t)(s0 + q) * sh.stride]) : (T)0;
   T w = carry[(int64_t)c * sh.ncols + m];
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -277,8 +290,9 @@ size_t tri_chunked_scratch(const Geom& g, int L) {
   return (size_t)(4 * C + 1) * ncols;  // elements
 }
 
-template <typename T, int L>
-static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* scratch, cudaStream_t st) {
+template <typename T, int L, bool GEN>
+static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* scratch, const VGen2D& G,
+                                 cudaStream_t st) {
   const int nx = g.N[0] - 1;
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
@@ -291,9 +305,9 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* s
   const int64_t work = ncols * C;
   const unsigned gb = (unsigned)((work + 127) / 128);
   const unsigned cb = (unsigned)((ncols + 127) / 128);
-  k_tri_t1<T, L><<<gb, 128, 0, st>>>(g, a, modes, E);
+  k_tri_t1<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, G);
   k_tri_t1b<T><<<cb, 128, 0, st>>>(g, modes, E, carry, L);
-  k_tri_t2<T, L><<<gb, 128, 0, st>>>(g, a, modes, carry, B);
+  k_tri_t2<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
   k_tri_t2b<T><<<cb, 128, 0, st>>>(g, modes, B, bcarry, Cc, L);
   k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, bcarry, Cc);
   return cudaGetLastError();
@@ -301,10 +315,23 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* s
 
 template <typename T>
 cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, cudaStream_t st) {
-  if (L == 32) return tri_chunked_L<T, 32>(g, a, modes, scratch, st);
-  if (L == 16) return tri_chunked_L<T, 16>(g, a, modes, scratch, st);
+  VGen2D G{};
+  if (L == 32) return tri_chunked_L<T, 32, false>(g, a, modes, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, false>(g, a, modes, scratch, G, st);
   return cudaErrorInvalidValue;
 }
+
+// the same solve with the v-equation right-hand side generated on the fly (2D)
+template <typename T>
+cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, const VGen2D& G,
+                                   cudaStream_t st) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  if (L == 32) return tri_chunked_L<T, 32, true>(g, a, modes, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, true>(g, a, modes, scratch, G, st);
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, double*, int,
+                                                    const VGen2D&, cudaStream_t);
 
 template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, double*, int, cudaStream_t);
 
