@@ -166,6 +166,28 @@ ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, dou
  * interior arrays; they may alias. */
 ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w);
 
+/* Dirichlet HOC Poisson solve without a plan and without any device
+ * allocation (the paper has no counterpart: this is a deployment aid).
+ * It computes the same result as ahoc_poisson on a plan of this grid,
+ * L_h w = rhs at interior points with w = 0 on the boundary, for callers
+ * that cannot call cudaMalloc: code running under another component's
+ * memory pool, latency-critical loops where an allocation would
+ * synchronise the device, or hosts that forbid allocation after start-up.
+ *   dim, N, lo, hi  as for ahoc_plan_create (host arrays)
+ *   rhs, w          device interior arrays (caller-owned); may alias
+ *   stream          a cudaStream_t of the current device (NULL = legacy default)
+ * All scratch (the padded field, the DST and per-mode tables, the carries
+ * of the chunked tridiagonal solve) lives in one static device array of
+ * 16 MiB that every GPU loading this library holds until the process exits;
+ * grids needing more (e.g. beyond 1024 x 1024 in 2D or 64^3 in 3D) return
+ * AHOC_EUNSUPPORTED before any launch.  The first call on a device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  Every call shares the array: calls that
+ * overlap on the GPU (other streams or threads) race.  Calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
+ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const double* lo, const double* hi,
+                                 const double* rhs, double* w, void* stream);
+
 ahoc_status ahoc_plan_destroy(ahoc_plan* p);
 
 /* Static strings; never NULL. */

@@ -24,7 +24,7 @@ AHOC_FP64, AHOC_MIXED = 0, 1
 # every entry point declared in include/ahoc.h
 SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
            "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
-           "ahoc_last_error", "ahoc_n_gamma")
+           "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc")
 
 
 class ahoc_bdata(C.Structure):
@@ -80,6 +80,8 @@ def lib():
     L.ahoc_status_string.restype = C.c_char_p
     L.ahoc_last_error.argtypes = []
     L.ahoc_last_error.restype = C.c_char_p
+    L.ahoc_poisson_noalloc.argtypes = [C.c_int, i64p, dp, dp, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ahoc_poisson_noalloc.restype = C.c_int
     L.ahoc_n_gamma.argtypes = [C.c_void_p]
     L.ahoc_n_gamma.restype = C.c_int64
     for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",

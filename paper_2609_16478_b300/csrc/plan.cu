@@ -477,6 +477,17 @@ bool is_fin(double x) { return std::isfinite(x); }
 
 }  // namespace
 
+// host helpers shared with other translation units of the library
+namespace ahoc {
+ahoc_status host_make_geom(int dim, const int64_t* N, const double* lo, const double* hi, Geom* g) {
+  return make_geom(dim, N, lo, hi, g);
+}
+Coefs host_make_coefs(const Geom& g) { return make_coefs(g); }
+ahoc_status host_fail(ahoc_status s, const char* msg) { return fail(s, msg); }
+bool host_tri_chunked(const Geom& g) { return tri_ncols(g) < kChunkedBelow; }
+int host_tri_chunk_len(const Geom& g) { return tri_chunk_len(g); }
+}  // namespace ahoc
+
 extern "C" {
 
 const char* ahoc_status_string(ahoc_status s) {
