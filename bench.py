@@ -131,7 +131,7 @@ _SAMPLES = {}
 
 
 def cpu_oracle_sample(N_cpu: int):
-    """Time the CPU oracle (assembly + SuperLU) on cfg2 at N_cpu; returns (DOF/s, seconds, err).
+    """Time the CPU oracle (assembly + SuperLU) on the 2D Fourier-coefficient workload at N_cpu; returns (DOF/s, seconds, err).
 
     The synthetic inputs are generated once, outside the timed region."""
     import numpy as np
@@ -140,7 +140,7 @@ def cpu_oracle_sample(N_cpu: int):
     from paper_2609_16478_b300 import inputs
 
     if N_cpu not in _SAMPLES:
-        _SAMPLES[N_cpu] = inputs.sample(inputs.config_problem("cfg2_2d"), [N_cpu, N_cpu])
+        _SAMPLES[N_cpu] = inputs.sample(inputs.config_problem("fourier2d"), [N_cpu, N_cpu])
     d = _SAMPLES[N_cpu]
     t0 = time.perf_counter()
     sol = coupled.solve_direct(coupled.assemble(d), d)
@@ -168,7 +168,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2D variable-coefficient clamped biharmonic (cfg2), oracle sample N=%d" % N_cpu,
+        "config": {"workload": "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes), oracle sample N=%d" % N_cpu,
                    "dim": 2, "N": N_cpu, "err_inf_vs_exact": max(errs)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "direct solve of the assembled coupled system at N=%d per step "
@@ -188,7 +188,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(dev)
     N = args.n
     dim = 2
-    prob = inputs.config_problem("cfg2_2d")
+    prob = inputs.config_problem("fourier2d")
     data = inputs.sample(prob, [N, N], backend="torch", device=dev)
     plan = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters)
     f = data["f"].reshape(-1).contiguous()
@@ -275,7 +275,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2D variable-coefficient clamped biharmonic (cfg2) N=%d, FP64, GMRES tol %g"
+        "config": {"workload": "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%d, FP64, GMRES tol %g"
                                % (N, args.tol),
                    "dim": dim, "N": N, "dof_per_solve": dof, "tol": args.tol,
                    "gmres_iters": infos[-1]["iters"], "err_inf_vs_exact": err,

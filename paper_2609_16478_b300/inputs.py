@@ -36,7 +36,7 @@ X = sp.symbols("x y z", real=True)
 
 __all__ = [
     "Problem", "fourier_alpha", "config_problem", "sample", "face_sizes",
-    "n_gamma", "CONFIGS",
+    "n_gamma", "WORKLOADS",
 ]
 
 
@@ -123,16 +123,16 @@ def _sinsq(v):
 def config_problem(name: str) -> Problem:
     """The named synthetic workloads."""
     x, y, z = X
-    if name == "cfg1_2d":
+    if name == "smooth2d":
         # 2D, unit square, alpha = 1 + 0.5 sin(2 pi x) sin(2 pi y), u = sin^2 sin^2
         return Problem(name, 2, 1 + sp.Rational(1, 2) * sp.sin(2 * sp.pi * x) * sp.sin(2 * sp.pi * y),
                        _sinsq(x) * _sinsq(y))
-    if name == "cfg2_2d":
+    if name == "fourier2d":
         # 2D, alpha = 1 + 0.4 * (8 seeded modes, |k| <= 6), u = sin^2 sin^2 cos(pi x)
         return Problem(name, 2, fourier_alpha(2, 8, 6, 0.4, 1), _sinsq(x) * _sinsq(y) * sp.cos(sp.pi * x))
-    if name == "cfg3_3d":
+    if name == "fourier3d":
         return Problem(name, 3, fourier_alpha(3, 6, 4, 0.4, 2), _sinsq(x) * _sinsq(y) * _sinsq(z))
-    if name == "cfg4_3d":
+    if name == "fourier3d_k32":
         k = 32
         u = _sinsq(x) * _sinsq(y) * _sinsq(z) * sp.sin(k * sp.pi * x) * sp.sin(k * sp.pi * y) * sp.sin(k * sp.pi * z)
         return Problem(name, 3, fourier_alpha(3, 6, 4, 0.5, 3), u)
@@ -185,11 +185,11 @@ def _plate_f(N, lo, hi):
     return f
 
 
-CONFIGS = {
-    "cfg1_2d": dict(dim=2, Ns=[64]),
-    "cfg2_2d": dict(dim=2, Ns=[256, 512, 1024, 2048, 4096]),
-    "cfg3_3d": dict(dim=3, Ns=[256, 512]),
-    "cfg4_3d": dict(dim=3, Ns=[1024]),
+WORKLOADS = {
+    "smooth2d": dict(dim=2, Ns=[64]),
+    "fourier2d": dict(dim=2, Ns=[256, 512, 1024, 2048, 4096]),
+    "fourier3d": dict(dim=3, Ns=[256, 512]),
+    "fourier3d_k32": dict(dim=3, Ns=[1024]),
 }
 
 

@@ -73,8 +73,8 @@ def test_poisson_matches_sparse_solve(N, lo, hi):
 
 # --- Lemma 1: the Schur action and right-hand side ---------------------------
 
-@pytest.mark.parametrize("name,N", [("sincos2d", [8, 8]), ("cfg1_2d", [16, 16]), ("sincos2d", [16, 8]),
-                                    ("sincos3d", [8, 8, 8]), ("cfg3_3d", [8, 16, 8])])
+@pytest.mark.parametrize("name,N", [("sincos2d", [8, 8]), ("smooth2d", [16, 16]), ("sincos2d", [16, 8]),
+                                    ("sincos3d", [8, 8, 8]), ("fourier3d", [8, 16, 8])])
 def test_schur_matrix_columns(name, N):
     prob = inputs.config_problem(name)
     d = inputs.sample(prob, N)
@@ -96,14 +96,14 @@ def test_schur_matrix_columns(name, N):
 # --- full solves against the direct solve -------------------------------------
 
 @pytest.mark.parametrize("name,N,lo,hi", [
-    ("cfg1_2d", [64, 64], None, None),          # the small configuration, GMRES tol 1e-12
+    ("smooth2d", [64, 64], None, None),          # the small configuration, GMRES tol 1e-12
     ("sincos2d", [32, 32], None, None),         # nonzero g_D, g_N, tangential Laplacian, corner v
     ("sincos2d", [64, 16], (0.0, -0.2), (1.0, 0.4)),   # anisotropic box and grid
-    ("cfg2_2d", [128, 128], None, None),
+    ("fourier2d", [128, 128], None, None),
     ("cavity", [64, 64], None, None),
     ("plate", [64, 64], None, None),
     ("sincos3d", [16, 16, 16], None, None),
-    ("cfg3_3d", [16, 8, 16], None, None),
+    ("fourier3d", [16, 8, 16], None, None),
     ("poly2d", [8, 8], None, None),             # smallest grid
 ])
 def test_solve_matches_oracle(name, N, lo, hi):
@@ -175,7 +175,7 @@ def test_plate_point_load():
 
 # --- full-size configurations: properties that hold at any size ---------------
 
-@pytest.mark.parametrize("name,N", [("cfg2_2d", [4096, 4096]), ("cfg3_3d", [128, 128, 128])])
+@pytest.mark.parametrize("name,N", [("fourier2d", [4096, 4096]), ("fourier3d", [128, 128, 128])])
 def test_large_grid_certificate(name, N):
     """Beyond the direct solver's reach: the oracle's residual certificate of the
     coupled equations evaluated on the GPU solution, and fourth-order accuracy."""
@@ -207,7 +207,7 @@ def test_large_grid_certificate(name, N):
 
 # --- boundary-symbol preconditioner and the tridiagonal paths ------------------
 
-@pytest.mark.parametrize("name,N", [("cfg2_2d", [256, 256]), ("cavity", [128, 128]), ("sincos3d", [16, 16, 16])])
+@pytest.mark.parametrize("name,N", [("fourier2d", [256, 256]), ("cavity", [128, 128]), ("sincos3d", [16, 16, 16])])
 def test_preconditioner_same_solution_fewer_iterations(name, N):
     d = inputs.sample(inputs.config_problem(name), N)
     f = _dev(d["f"])

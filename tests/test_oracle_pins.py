@@ -210,7 +210,7 @@ def test_P4_lemma4_3d_two_roots():
 
 # --- P6: manufactured clamped solutions, fourth-order convergence -----------
 
-@pytest.mark.parametrize("name,Ns,lo_rate", [("sincos2d", [16, 32, 64], 3.8), ("cfg1_2d", [16, 32, 64], 3.8),
+@pytest.mark.parametrize("name,Ns,lo_rate", [("sincos2d", [16, 32, 64], 3.8), ("smooth2d", [16, 32, 64], 3.8),
                                              ("sincos3d", [6, 8, 12], 3.4)])
 def test_P6_convergence_order(name, Ns, lo_rate):
     prob = inputs.config_problem(name)
