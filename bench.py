@@ -190,7 +190,8 @@ def run_ours(args, rank, world, local):
     dim = 2
     prob = inputs.config_problem("fourier2d")
     data = inputs.sample(prob, [N, N], backend="torch", device=dev)
-    plan = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters)
+    plan = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters,
+                         levels=args.levels)
     f = data["f"].reshape(-1).contiguous()
     u = torch.empty_like(f)
     st = plan.stream
@@ -278,7 +279,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%d, FP64, GMRES tol %g"
                                % (N, args.tol),
                    "dim": dim, "N": N, "dof_per_solve": dof, "tol": args.tol,
-                   "gmres_iters": infos[-1]["iters"], "err_inf_vs_exact": err,
+                   "gmres_iters": infos[-1]["iters"], "coarse_levels": infos[-1]["levels"],
+                   "coarse_gmres_iters": infos[-1]["coarse_iters"], "err_inf_vs_exact": err,
                    "rel_resid": infos[-1]["rel_resid"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set (two 134 MB fields + coefficient/data arrays) larger than L2; no flush"},
         "clocks": clocks,
@@ -302,6 +304,7 @@ def main():
     ap.add_argument("--restart", type=int, default=300)
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cpu-n", type=int, default=256)
+    ap.add_argument("--levels", type=int, default=-1, help="coarse levels of the nested initial guess (-1 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -95,6 +95,12 @@ typedef struct {
                              ahoc_workspace_bytes() bytes, 256-byte aligned; NULL lets the
                              plan allocate its own with cudaMalloc                             */
   size_t workspace_bytes; /* size of the caller workspace                                      */
+  int levels;             /* [-1] coarse levels of the nested initial guess: the problem is
+                             solved on grids with N/2, N/4, ... (data injected), each
+                             solution's Q interpolated (cubic, along the faces) to the next
+                             finer grid as GMRES's initial guess (the coarse-grid
+                             interpolated guess of Sec. 4.1).  -1: automatic (halve while
+                             every axis keeps >= 128 intervals, at most 3 levels); 0: off */
 } ahoc_opts;
 
 typedef struct {
@@ -106,10 +112,13 @@ typedef struct {
   int64_t launches;       /* kernels this library launched during the last solve                */
   double kernel_ms[AHOC_NK];      /* with opts.timing: summed device time per kernel class      */
   int64_t kernel_launches[AHOC_NK];
+  int levels;             /* coarse levels used for the initial guess                           */
+  int coarse_iters;       /* GMRES iterations summed over the coarse levels                     */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:
- * two interior fields, coefficient and boundary copies, the Krylov basis).
+ * two interior fields, coefficient and boundary copies, the Krylov basis;
+ * plus the coarse levels of the nested initial guess).
  * Returns AHOC_EINVAL on a bad shape.  Allocates nothing. */
 ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opts, size_t* bytes);
 

@@ -38,13 +38,14 @@ KERNEL_NAMES = ("dst_x", "dst_y", "tri", "vrhs", "urhs", "trace", "krylov", "oth
 class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("levels", C.c_int)]
 
 
 class ahoc_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("rel_resid", C.c_double),
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("launches", C.c_int64),
-                ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK)]
+                ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK),
+                ("levels", C.c_int), ("coarse_iters", C.c_int)]
 
 
 class AhocError(RuntimeError):
@@ -108,9 +109,10 @@ def _ptr(t: Optional[torch.Tensor], numel: int, name: str):
     return C.c_void_p(t.data_ptr())
 
 
-def _opts(prec, max_iters, restart, precond, workspace=None, timing=0):
+def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1):
     o = ahoc_opts()
     o.timing = int(timing)
+    o.levels = int(levels)
     o.prec = prec
     o.max_iters = max_iters
     o.restart = restart
@@ -122,10 +124,10 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0):
     return o
 
 
-def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64) -> int:
+def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 1)
+    o = _opts(prec, 500, restart, 1, levels=levels)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -140,7 +142,8 @@ class Plan:
 
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
-                 max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False):
+                 max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
+                 levels: int = -1):
         L = lib()
         self.dim = dim
         self.N = [int(n) for n in N]
@@ -159,12 +162,12 @@ class Plan:
                     s *= self.N[b] - 1
             self.ngamma += 2 * s
         self.device = alpha.device
-        nb = workspace_bytes(dim, self.N, restart, prec)
+        nb = workspace_bytes(dim, self.N, restart, prec, levels)
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
                         _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
-        o = _opts(prec, max_iters, restart, precond, self._ws, timing)
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
@@ -187,7 +190,8 @@ class Plan:
         return u, dict(iters=info.iters, restarts=info.restarts, rel_resid=info.rel_resid,
                        ms_total=info.ms_total, ms_matvec=info.ms_matvec, status=st, launches=info.launches,
                        kernel_ms={k: info.kernel_ms[i] for i, k in enumerate(KERNEL_NAMES)},
-                       kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)})
+                       kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)},
+                       levels=info.levels, coarse_iters=info.coarse_iters)
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         if y is None:

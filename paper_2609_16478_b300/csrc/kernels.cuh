@@ -89,6 +89,11 @@ cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t 
 cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,
                           cudaStream_t st);
 
+// grid transfer for the nested initial guess (stencil.cu)
+cudaError_t launch_inject_full(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st);
+cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st);
+cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st);
+
 // GMRES level-1/2 kernels on face vectors (FP64).
 // partial[b * ncols + c] = sum over block b's rows of V[c*ld + i] * w[i]
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,

@@ -44,6 +44,7 @@ struct Opts {
   int restart = 100;
   int precond = 1;
   int timing = 0;
+  int levels = -1;  // coarse levels of the nested initial guess (-1: automatic)
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -56,12 +57,14 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     if (o->restart > 0) d.restart = o->restart;
     d.precond = o->precond < 0 ? 1 : o->precond;
     d.timing = o->timing;
+    d.levels = o->levels;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
   if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "only AHOC_FP64 is implemented");
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
+  if (d.levels < -1 || d.levels > 8) return fail(AHOC_EINVAL, "levels must be -1 (automatic) or 0..8");
   if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
     return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
   *out = d;
@@ -287,6 +290,40 @@ Layout make_layout(const Geom& g, const Opts& o) {
   return L;
 }
 
+// Nested initial guess: coarse grids halve every axis.  Automatic depth:
+// coarsen while every axis keeps at least kMinCoarse intervals, at most
+// kAutoLevels times (deeper levels cost more in fixed latency than they save).
+constexpr int kMinCoarse = 128;
+constexpr int kAutoLevels = 3;
+int coarse_levels(const Geom& g, int requested) {
+  int maxl = 0;
+  int n = 1 << 30;
+  for (int a = 0; a < g.dim; ++a) n = (g.N[a] < n) ? g.N[a] : n;
+  while ((n >> (maxl + 1)) >= kMinCoarse && (n >> (maxl + 1)) >= 8) ++maxl;
+  if (requested < 0) return maxl < kAutoLevels ? maxl : kAutoLevels;
+  // an explicit request may go down to 8 intervals per axis
+  int lim = 0;
+  while ((n >> (lim + 1)) >= 8) ++lim;
+  return requested < lim ? requested : lim;
+}
+
+// total workspace of a plan and its coarse levels
+size_t total_bytes(const Geom& g, const Opts& o) {
+  size_t b = make_layout(g, o).total;
+  const int lv = coarse_levels(g, o.levels);
+  if (lv > 0) {
+    int64_t Nc[3];
+    for (int a = 0; a < g.dim; ++a) Nc[a] = g.N[a] / 2;
+    Geom gc;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    make_geom(g.dim, Nc, lo, hi, &gc);
+    Opts oc = o;
+    oc.levels = lv - 1;
+    b += total_bytes(gc, oc);
+  }
+  return b;
+}
+
 }  // namespace
 
 struct ahoc_plan {
@@ -314,6 +351,9 @@ struct ahoc_plan {
   int64_t launches = 0;
   double kms[AHOC_NK] = {0};
   int64_t kn[AHOC_NK] = {0};
+  ahoc_plan* coarse = nullptr;  // next coarser level of the nested initial guess
+  int coarse_iters = 0;
+  int levels = 0;
 };
 
 namespace {
@@ -513,7 +553,7 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
   CKS(make_geom(dim, N, nullptr, nullptr, &g));
   Opts o;
   CKS(read_opts(opts, &o));
-  *bytes = make_layout(g, o).total;
+  *bytes = total_bytes(g, o);
   return AHOC_OK;
 }
 
@@ -532,7 +572,8 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   std::vector<Mode<double>> modes;
   CKS(mode_table(g, cf, modes));
   Layout L = make_layout(g, o);
-  if (o.workspace && o.workspace_bytes < L.total) return fail(AHOC_ENOMEM, "caller workspace too small");
+  const size_t need = total_bytes(g, o);
+  if (o.workspace && o.workspace_bytes < need) return fail(AHOC_ENOMEM, "caller workspace too small");
 
   ahoc_plan* p = new (std::nothrow) ahoc_plan();
   if (!p) return fail(AHOC_ENOMEM, "host allocation failed");
@@ -665,6 +706,50 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     CKC(cudaMemcpyAsync(p->lapt, bd->lapt_gD, face, cudaMemcpyDeviceToDevice, p->st));
   }
   CKC(cudaStreamSynchronize(p->st));
+  // coarse level for the nested initial guess: data injected into temporaries
+  // carved from this level's field buffers, then copied by the coarse plan
+  const int lv = coarse_levels(g, o.levels);
+  if (lv > 0) {
+    int64_t Nc[3];
+    double lo_[3], hi_[3];
+    for (int a = 0; a < dim; ++a) {
+      Nc[a] = g.N[a] / 2;
+      lo_[a] = lo ? lo[a] : 0.0;
+      hi_[a] = hi ? hi[a] : 1.0;
+    }
+    Geom gc;
+    {
+      ahoc_status sg = make_geom(dim, Nc, lo_, hi_, &gc);
+      if (sg != AHOC_OK) return cleanup(sg);
+    }
+    double* a_c = p->W1;
+    double* gD_c = bd && bd->g_D ? p->W2 : nullptr;
+    double* vE_c = bd && bd->v_edge ? p->W2 + gc.nfull : nullptr;
+    double* gN_c = bd && bd->g_N ? p->b : nullptr;
+    double* lt_c = bd && bd->lapt_gD ? p->r : nullptr;
+    CKC(launch_inject_full(gc, g, a_c, alpha, p->st));
+    if (gD_c) CKC(launch_inject_full(gc, g, gD_c, bd->g_D, p->st));
+    if (vE_c) CKC(launch_inject_full(gc, g, vE_c, bd->v_edge, p->st));
+    if (gN_c) CKC(launch_inject_face(gc, g, gN_c, bd->g_N, p->st));
+    if (lt_c) CKC(launch_inject_face(gc, g, lt_c, bd->lapt_gD, p->st));
+    ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c};
+    ahoc_opts oc;
+    std::memset(&oc, 0, sizeof(oc));
+    oc.prec = o.prec;
+    oc.max_iters = o.max_iters;
+    oc.restart = o.restart;
+    oc.precond = o.precond;
+    oc.timing = o.timing;
+    oc.levels = lv - 1;
+    oc.workspace = o.workspace ? (void*)(p->ws + L.total) : nullptr;
+    oc.workspace_bytes = o.workspace ? o.workspace_bytes - L.total : 0;
+    ahoc_status sc = ahoc_plan_create(&p->coarse, dim, Nc, lo_, hi_, a_c, &bc, &oc, stream);
+    if (sc != AHOC_OK) return cleanup(sc);
+    p->levels = lv;
+    CKC(cudaMemsetAsync(p->W1, 0, fld, p->st));
+    CKC(cudaMemsetAsync(p->W2, 0, fld, p->st));
+    CKC(cudaStreamSynchronize(p->st));
+  }
 #undef CKC
   *out = p;
   return AHOC_OK;
@@ -675,6 +760,10 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
   ahoc_status s = AHOC_OK;
   if (p->st) {
     if (cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "stream sync at destroy failed");
+  }
+  if (p->coarse) {
+    if (ahoc_plan_destroy(p->coarse) != AHOC_OK) s = AHOC_ECUDA;
+    p->coarse = nullptr;
   }
   if (p->own_ws && p->ws) cudaFree(p->ws);
   if (p->hhost) cudaFreeHost(p->hhost);
@@ -756,10 +845,45 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
   int iters = 0, restarts = 0;
   double rel = 0.0;
   ahoc_status status = AHOC_OK;
+  p->coarse_iters = 0;
   if (beta0 > 0) {
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-    CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
     double beta = beta0;
+    if (p->coarse) {
+      // nested initial guess: solve on the coarser grid (recursively), then
+      // prolong its Q to this grid's faces (the paper's coarse-grid
+      // interpolated initial guess, Sec. 4.1)
+      ahoc_plan* c = p->coarse;
+      double* f_c = p->W2;
+      double* u_c = p->W1;
+      RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
+      CK(cudaStreamSynchronize(p->st));
+      ahoc_info ci;
+      std::memset(&ci, 0, sizeof(ci));
+      ahoc_status cs_ = ahoc_solve(c, f_c, u_c, tol, &ci);
+      if (cs_ != AHOC_OK && cs_ != AHOC_ENOCONV) return cs_;
+      p->coarse_iters = ci.iters + c->coarse_iters;
+      p->launches += ci.launches;
+      for (int k = 0; k < AHOC_NK; ++k) {
+        p->kms[k] += ci.kernel_ms[k];
+        p->kn[k] += ci.kernel_launches[k];
+      }
+      ms_mv += ci.ms_matvec;
+      RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
+      // the fields were borrowed as temporaries: restore the zero padding
+      CK(cudaMemsetAsync(p->W1, 0, (size_t)g.npad * sizeof(double), p->st));
+      CK(cudaMemsetAsync(p->W2, 0, (size_t)g.npad * sizeof(double), p->st));
+      // r = b - S Q0
+      CKS(matvec_dev(p, p->Q, p->tmp));
+      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+      RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
+      CKS(mdot(p, p->r, 1, p->r, p->hdev));
+      CKS(fetch(p, 1));
+      beta = std::sqrt(p->hhost[0]);
+      if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite initial residual");
+    } else {
+      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    }
     bool done = false;
     while (!done) {
       rel = beta / beta0;
@@ -861,6 +985,8 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
     info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     info->ms_matvec = ms_mv;
     info->launches = p->launches;
+    info->levels = p->levels;
+    info->coarse_iters = p->coarse_iters;
     for (int k = 0; k < AHOC_NK; ++k) {
       info->kernel_ms[k] = p->kms[k];
       info->kernel_launches[k] = p->kn[k];

@@ -295,3 +295,106 @@ template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, con
                                          const double*, const double*, const double*, const double*, cudaStream_t);
 
 }  // namespace ahoc
+
+namespace ahoc {
+
+// ---------------------------------------------------------------------------
+// Grid transfer for the nested (coarse-to-fine) initial guess: coarse data
+// by injection (the coarse grid points are every other fine point), and the
+// coarse Q prolonged to the fine face points by cubic Lagrange interpolation
+// along each in-face axis (one-sided near the face edges).
+// ---------------------------------------------------------------------------
+__global__ void k_inject_full(Geom gc, Geom gf, double* __restrict__ out, const double* __restrict__ in) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.nfull) return;
+  const int i = (int)(t % gc.f0);
+  const int64_t r = t / gc.f0;
+  const int j = (int)(r % gc.f1);
+  const int k = (int)(r / gc.f1);
+  out[t] = in[gf.full(2 * i, 2 * j, 2 * k)];
+}
+
+__device__ __forceinline__ void face_coords(const Geom& g, int64_t q, int& a, int& side, int c[3]) {
+  int f = 0;
+  while (q >= g.face_off[f + 1]) ++f;
+  a = f >> 1;
+  side = f & 1;
+  int64_t r = q - g.face_off[f];
+  c[0] = c[1] = c[2] = 0;
+  for (int b = 0; b < g.dim; ++b) {
+    if (b == a) continue;
+    const int nb = g.N[b] - 1;
+    c[b] = 1 + (int)(r % nb);
+    r /= nb;
+  }
+  c[a] = side ? g.N[a] : 0;
+}
+
+__global__ void k_inject_face(Geom gc, Geom gf, double* __restrict__ out, const double* __restrict__ in) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= gc.ngamma) return;
+  int a, side, c[3];
+  face_coords(gc, q, a, side, c);
+  out[q] = in[gf.face(a, side, 2 * c[0], 2 * c[1], 2 * c[2])];
+}
+
+// nodes and weights of the fine coordinate cf on the coarse line 1..Nc-1
+__device__ __forceinline__ int prolong_weights(int cf, int Nc, int* node, double* w) {
+  if ((cf & 1) == 0) {
+    node[0] = cf >> 1;
+    w[0] = 1.0;
+    return 1;
+  }
+  const double t = 0.5 * cf;
+  int lo = (cf >> 1) - 1;  // floor(t) - 1
+  if (lo < 1) lo = 1;
+  if (lo > Nc - 4) lo = Nc - 4;
+  for (int m = 0; m < 4; ++m) {
+    double l = 1.0;
+    for (int n = 0; n < 4; ++n)
+      if (n != m) l *= (t - (lo + n)) / (double)(m - n);
+    node[m] = lo + m;
+    w[m] = l;
+  }
+  return 4;
+}
+
+__global__ void k_face_prolong(Geom gf, Geom gc, double* __restrict__ out, const double* __restrict__ in) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= gf.ngamma) return;
+  int a, side, c[3];
+  face_coords(gf, q, a, side, c);
+  int rem[2] = {-1, -1}, nr = 0;
+  for (int b = 0; b < gf.dim; ++b)
+    if (b != a) rem[nr++] = b;
+  int n0[4], n1[4] = {0, 0, 0, 0};
+  double w0[4], w1[4] = {1.0, 0, 0, 0};
+  const int k0 = prolong_weights(c[rem[0]], gc.N[rem[0]], n0, w0);
+  int k1 = 1;
+  if (nr == 2) k1 = prolong_weights(c[rem[1]], gc.N[rem[1]], n1, w1);
+  double acc = 0.0;
+  for (int u = 0; u < k0; ++u)
+    for (int v = 0; v < k1; ++v) {
+      int cc[3] = {0, 0, 0};
+      cc[a] = side ? gc.N[a] : 0;
+      cc[rem[0]] = n0[u];
+      if (nr == 2) cc[rem[1]] = n1[v];
+      acc += w0[u] * w1[v] * in[gc.face(a, side, cc[0], cc[1], cc[2])];
+    }
+  out[q] = acc;
+}
+
+cudaError_t launch_inject_full(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st) {
+  k_inject_full<<<nblk(gc.nfull, 256), 256, 0, st>>>(gc, gf, out, in);
+  return cudaGetLastError();
+}
+cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st) {
+  k_inject_face<<<nblk(gc.ngamma, 256), 256, 0, st>>>(gc, gf, out, in);
+  return cudaGetLastError();
+}
+cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st) {
+  k_face_prolong<<<nblk(gf.ngamma, 256), 256, 0, st>>>(gf, gc, out, in);
+  return cudaGetLastError();
+}
+
+}  // namespace ahoc

@@ -235,3 +235,22 @@ def test_poisson_residual_sequential_tri_path():
     shape2 = tuple(n - 1 for n in reversed(N2))
     r2 = rng.normal(size=shape2)
     assert _rel(_host(p2.poisson(_dev(r2)), shape2), coupled.poisson_solve(N2, r2)) < 1e-11
+
+
+# --- nested (coarse-to-fine) initial guess --------------------------------------
+
+@pytest.mark.parametrize("name,N,levels", [("fourier2d", [256, 256], -1), ("fourier2d", [256, 256], 3),
+                                           ("sincos2d", [64, 16], 1), ("sincos3d", [16, 16, 16], 1),
+                                           ("cavity", [64, 64], 2)])
+def test_nested_initial_guess_matches_oracle(name, N, levels):
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    f = _dev(d["f"])
+    u1, i1 = _plan(d, levels=levels).solve(f, tol=1e-12)
+    shape = tuple(n + 1 for n in reversed(N))
+    assert _rel(_host(u1, shape), sol.U) < TOL_SOLVE, i1
+    assert i1["levels"] >= 1 and i1["coarse_iters"] > 0
+    u0, i0 = _plan(d, levels=0).solve(f, tol=1e-12)
+    assert i0["levels"] == 0
+    if name != "cavity":   # smooth data: the interpolated coarse solution saves fine iterations
+        assert i1["iters"] < i0["iters"], (i0["iters"], i1["iters"])
