@@ -100,7 +100,7 @@ typedef struct {
                              solution's Q interpolated (cubic, along the faces) to the next
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
-                             every axis keeps >= 128 intervals, at most 3 levels); 0: off */
+                             every axis keeps >= 128 intervals, at most 2 levels); 0: off */
 } ahoc_opts;
 
 typedef struct {
@@ -114,6 +114,8 @@ typedef struct {
   int64_t kernel_launches[AHOC_NK];
   int levels;             /* coarse levels used for the initial guess                           */
   int coarse_iters;       /* GMRES iterations summed over the coarse levels                     */
+  double kernel_ms_top[AHOC_NK];      /* as kernel_ms, this grid's launches only (no coarse)  */
+  int64_t kernel_launches_top[AHOC_NK];
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:

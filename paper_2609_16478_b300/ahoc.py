@@ -45,7 +45,8 @@ class ahoc_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("rel_resid", C.c_double),
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("launches", C.c_int64),
                 ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK),
-                ("levels", C.c_int), ("coarse_iters", C.c_int)]
+                ("levels", C.c_int), ("coarse_iters", C.c_int),
+                ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK)]
 
 
 class AhocError(RuntimeError):
@@ -191,7 +192,9 @@ class Plan:
                        ms_total=info.ms_total, ms_matvec=info.ms_matvec, status=st, launches=info.launches,
                        kernel_ms={k: info.kernel_ms[i] for i, k in enumerate(KERNEL_NAMES)},
                        kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)},
-                       levels=info.levels, coarse_iters=info.coarse_iters)
+                       levels=info.levels, coarse_iters=info.coarse_iters,
+                       kernel_ms_top={k: info.kernel_ms_top[i] for i, k in enumerate(KERNEL_NAMES)},
+                       kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)})
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         if y is None:

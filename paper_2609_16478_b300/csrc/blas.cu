@@ -16,36 +16,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[b * ncols + c] = sum_{i in block b's rows} V[c * ld + i] * w[i]
+// partial[b * ncols + c] = sum over block-row b's rows of V[c * ld + i] * w[i];
+// blockIdx.y selects a group of kCols columns, so one pass over the rows
+// serves kCols dot products with one shared-memory reduction.
+constexpr int kCols = 4;
+
 __global__ void __launch_bounds__(kDotThreads) k_mdot(const double* __restrict__ V, int64_t ld, int ncols,
                                                       const double* __restrict__ w, int64_t n,
                                                       double* __restrict__ partial) {
-  __shared__ double red[kDotThreads / 32];
+  __shared__ double red[kCols][kDotThreads / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
-  for (int c = 0; c < ncols; ++c) {
-    const double* v = V + (int64_t)c * ld;
-    double acc = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc = fma(v[i], w[i], acc);
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double s = threadIdx.x < (kDotThreads / 32) ? red[threadIdx.x] : 0.0;
-      s = warp_sum(s);
-      if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ncols + c] = s;
+  const int c0 = blockIdx.y * kCols;
+  const int nc = (ncols - c0) < kCols ? (ncols - c0) : kCols;
+  double acc[kCols] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < kCols; ++q)
+      if (q < nc) acc[q] = fma(V[(int64_t)(c0 + q) * ld + i], wi, acc[q]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kCols; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < kCols; ++q) {
+      double v = threadIdx.x < (kDotThreads / 32) ? red[q][threadIdx.x] : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0 && q < nc) partial[(int64_t)blockIdx.x * ncols + c0 + q] = v;
     }
-    __syncthreads();
   }
 }
 
+// out[c] = sum_b partial[b * ncols + c]: one warp per column, fixed order
 __global__ void k_reduce_cols(const double* __restrict__ partial, int nblocks, int ncols, double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (c >= ncols) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * ncols + c];
-  out[c] = s;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * ncols + c];
+  s = warp_sum(s);
+  if (lane == 0) out[c] = s;
 }
 
 __global__ void k_gemv_sub(const double* __restrict__ V, int64_t ld, int ncols, const double* __restrict__ h,
@@ -63,13 +80,17 @@ __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, do
   y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
+// out[c] = <V_c, w> for c < ncols: block partials into `partial` (capacity
+// nblocks * ncols), then a fixed-order reduction per column into out
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
-                        int nblocks, cudaStream_t st) {
-  k_mdot<<<nblocks, kDotThreads, 0, st>>>(V, ld, ncols, w, n, partial);
-  return cudaGetLastError();
-}
-cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st) {
-  k_reduce_cols<<<(ncols + 127) / 128, 128, 0, st>>>(partial, nblocks, ncols, out);
+                        int nblocks, double* out, cudaStream_t st) {
+  const int64_t want = (n + 4095) / 4096;
+  const int nb = (int)(want < 1 ? 1 : (want > nblocks ? nblocks : want));
+  dim3 grid(nb, (ncols + kCols - 1) / kCols);
+  k_mdot<<<grid, kDotThreads, 0, st>>>(V, ld, ncols, w, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nb, ncols, out);
   return cudaGetLastError();
 }
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,

@@ -350,6 +350,46 @@ __global__ void __launch_bounds__(512) k_dst_gen(T* __restrict__ base, int nline
 }
 
 // ---------------------------------------------------------------------------
+// Boundary preconditioner on 2D face lines in one pass: out = alpha *
+// DST(pre * DST(in / alpha)) per line, the line kept in shared memory.
+// Line l holds N-1 contiguous face values at l * lstride; in and out may alias.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_precond_lines(double* out, const double* in, const double* __restrict__ afac,
+                                                       const double* __restrict__ pre, int nlines, int64_t lstride,
+                                                       int N, const double2* __restrict__ tw,
+                                                       const double* __restrict__ sn, int logN, int TPL, int LPC) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s = reinterpret_cast<double*>(smem_raw);
+  double* wsum = s + (int64_t)LPC * N;
+  const int l0 = blockIdx.x * LPC;
+  const int tot = LPC * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e >> logN, j = e & (N - 1), line = l0 + l;
+    double v = 0.0;
+    if (j > 0 && line < nlines) {
+      const int64_t q = (int64_t)line * lstride + (j - 1);
+      v = in[q] / afac[q];
+    }
+    s[e] = v;
+  }
+  __syncthreads();
+  dst_lines<double>(s, N, N, logN, TPL, tw, sn, wsum);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e >> logN, j = e & (N - 1), line = l0 + l;
+    if (j > 0 && line < nlines) s[e] *= pre[(int64_t)line * lstride + (j - 1)];
+  }
+  __syncthreads();
+  dst_lines<double>(s, N, N, logN, TPL, tw, sn, wsum);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e >> logN, j = e & (N - 1), line = l0 + l;
+    if (j > 0 && line < nlines) {
+      const int64_t q = (int64_t)line * lstride + (j - 1);
+      out[q] = s[e] * afac[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline int ilog2(int n) {
@@ -445,6 +485,23 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
 }
 template cudaError_t launch_dst_gen<double>(double*, int, int, int64_t, int64_t, int64_t, int, const void*,
                                             const double*, cudaStream_t);
+
+cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
+                                 int64_t lstride, int N, const void* tw, const double* sn, cudaStream_t st) {
+  const int logN = ilog2(N);
+  const int TPL = N / 8;
+  const int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  const int threads = TPL * LPC;
+  const int blocks = (nlines + LPC - 1) / LPC;
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_precond_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_precond_lines<<<blocks, threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,
+                                                 reinterpret_cast<const double2*>(tw), sn, logN, TPL, LPC);
+  return cudaGetLastError();
+}
 
 template cudaError_t launch_dst_x<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
 template cudaError_t launch_dst_y<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);

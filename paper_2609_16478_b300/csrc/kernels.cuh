@@ -46,6 +46,10 @@ template <typename T>
 cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_t lstride, int64_t estride, int N,
                            const void* tw, const T* sn, cudaStream_t st);
 
+// Boundary preconditioner on 2D face lines, one pass (dst.cu)
+cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
+                                 int64_t lstride, int N, const void* tw, const double* sn, cudaStream_t st);
+
 // Boundary preconditioner (precond.cu)
 struct SymAxis {
   const double* stab;  // sin(j pi / N_a), j < 2 N_a
@@ -95,10 +99,10 @@ cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, cons
 cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st);
 
 // GMRES level-1/2 kernels on face vectors (FP64).
-// partial[b * ncols + c] = sum over block b's rows of V[c*ld + i] * w[i]
+// out[c] = <V_c, w>, c < ncols (deterministic two-stage reduction through
+// `partial`, which holds nblocks * ncols doubles)
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
-                        int nblocks, cudaStream_t st);
-cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st);
+                        int nblocks, double* out, cudaStream_t st);
 // w -= V h (h on device, ncols entries)
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
                             cudaStream_t st);

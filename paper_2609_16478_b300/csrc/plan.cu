@@ -294,7 +294,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
 // coarsen while every axis keeps at least kMinCoarse intervals, at most
 // kAutoLevels times (deeper levels cost more in fixed latency than they save).
 constexpr int kMinCoarse = 128;
-constexpr int kAutoLevels = 3;
+constexpr int kAutoLevels = 2;
 int coarse_levels(const Geom& g, int requested) {
   int maxl = 0;
   int n = 1 << 30;
@@ -354,6 +354,8 @@ struct ahoc_plan {
   ahoc_plan* coarse = nullptr;  // next coarser level of the nested initial guess
   int coarse_iters = 0;
   int levels = 0;
+  double kms_top[AHOC_NK] = {0};  // this level only (no coarse levels)
+  int64_t kn_top[AHOC_NK] = {0};
 };
 
 namespace {
@@ -366,7 +368,7 @@ P* at(ahoc_plan* p, size_t off) {
 // Launch one kernel through `f`, counting it and, when timing is on,
 // bracketing it with CUDA events on the plan's stream.
 template <class F>
-ahoc_status run(ahoc_plan* p, int kid, const char* what, F&& f) {
+ahoc_status run(ahoc_plan* p, int kid, const char* what, F&& f, int nkernels = 1) {
   ahoc_plan::EvPair ev{nullptr, nullptr, kid};
   if (p->o.timing) {
     if (!p->pool.empty()) {
@@ -385,8 +387,8 @@ ahoc_status run(ahoc_plan* p, int kid, const char* what, F&& f) {
     CK(cudaEventRecord(ev.b, p->st));
     p->pending.push_back(ev);
   }
-  ++p->launches;
-  ++p->kn[kid];
+  p->launches += nkernels;
+  p->kn[kid] += nkernels;
   return AHOC_OK;
 }
 
@@ -403,13 +405,15 @@ ahoc_status harvest(ahoc_plan* p) {
 }
 
 #define RUN(kid, call) CKS(run(p, kid, #call, [&]() { return (call); }))
+// a launcher that issues n kernels
+#define RUNN(kid, n, call) CKS(run(p, kid, #call, [&]() { return (call); }, n))
 
 ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
   const Geom& g = p->g;
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUN(AHOC_K_TRI, launch_tri_chunked<double>(g, W, p->modes, p->tri, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
@@ -438,10 +442,10 @@ ahoc_status matvec_fused2d(ahoc_plan* p, const double* q, double* y) {
   RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
   RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
   VGen2D G{p->rxm, p->rxp, p->qy, p->qy + (N0 - 1), p->stab[0], p->ctab[0], cf.L[16], cf.L[17]};
-  RUN(AHOC_K_TRI, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->tri, tri_chunk_len(g), G, p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->tri, tri_chunk_len(g), G, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<double>(g, p->W1, p->ainv, p->twx, p->snx, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x_mload<double>(g, p->W2, p->W1, q, p->afac, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
-  RUN(AHOC_K_TRI, launch_tri_chunked<double>(g, p->W2, p->modes, p->tri, tri_chunk_len(g), p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, p->W2, p->modes, p->tri, tri_chunk_len(g), p->st));
   RUN(AHOC_K_TRACE, launch_trace2d_x(g, y, p->W2, q, p->afac, p->tau, p->st));
   RUN(AHOC_K_TRACE, launch_trace2d_ylines(g, cf, p->R2, p->W2, p->st));
   RUN(AHOC_K_TRACE, launch_dst_gen<double>(p->R2, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
@@ -485,6 +489,16 @@ ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
     if (in != out) CK(cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
     return AHOC_OK;
   }
+  if (p->g.dim == 2) {
+    // x-faces are lines of N1 - 1 points (DST length N1), y-faces of N0 - 1
+    const Geom& g = p->g;
+    const int64_t ox = g.face_off[0], oy = g.face_off[2];
+    RUN(AHOC_K_KRYLOV, launch_precond_lines(out + ox, in + ox, p->afac + ox, p->pre + ox, 2, g.N[1] - 1, g.N[1],
+                                            p->twy, p->sny, p->st));
+    RUN(AHOC_K_KRYLOV, launch_precond_lines(out + oy, in + oy, p->afac + oy, p->pre + oy, 2, g.N[0] - 1, g.N[0],
+                                            p->twx, p->snx, p->st));
+    return AHOC_OK;
+  }
   RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, in, nullptr, p->afac, n, p->st));
   for (int a = 0; a < p->g.dim; ++a) CKS(face_dsts(p, out, a));
   RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->pre, nullptr, n, p->st));
@@ -502,8 +516,7 @@ ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
 
 // dots: out[c] = <V_c, w>, c < ncols (device); returns via hdev+off
 ahoc_status mdot(ahoc_plan* p, const double* V, int ncols, const double* w, double* out) {
-  RUN(AHOC_K_KRYLOV, launch_mdot(V, p->g.ngamma, ncols, w, p->g.ngamma, p->partial, kDotBlocks, p->st));
-  RUN(AHOC_K_KRYLOV, launch_reduce_cols(p->partial, kDotBlocks, ncols, out, p->st));
+  RUNN(AHOC_K_KRYLOV, 2, launch_mdot(V, p->g.ngamma, ncols, w, p->g.ngamma, p->partial, kDotBlocks, out, p->st));
   return AHOC_OK;
 }
 
@@ -830,6 +843,8 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
   for (int k = 0; k < AHOC_NK; ++k) {
     p->kms[k] = 0;
     p->kn[k] = 0;
+    p->kms_top[k] = 0;
+    p->kn_top[k] = 0;
   }
   const Geom& g = p->g;
   const int64_t n = g.ngamma;
@@ -863,6 +878,12 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
       ahoc_status cs_ = ahoc_solve(c, f_c, u_c, tol, &ci);
       if (cs_ != AHOC_OK && cs_ != AHOC_ENOCONV) return cs_;
       p->coarse_iters = ci.iters + c->coarse_iters;
+      CKS(harvest(p));
+      for (int k = 0; k < AHOC_NK; ++k) {
+        // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
+        p->kms_top[k] -= ci.kernel_ms[k];
+        p->kn_top[k] -= ci.kernel_launches[k];
+      }
       p->launches += ci.launches;
       for (int k = 0; k < AHOC_NK; ++k) {
         p->kms[k] += ci.kernel_ms[k];
@@ -986,6 +1007,10 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
     info->ms_matvec = ms_mv;
     info->launches = p->launches;
     info->levels = p->levels;
+    for (int k = 0; k < AHOC_NK; ++k) {
+      info->kernel_ms_top[k] = p->kms[k] + p->kms_top[k];
+      info->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
+    }
     info->coarse_iters = p->coarse_iters;
     for (int k = 0; k < AHOC_NK; ++k) {
       info->kernel_ms[k] = p->kms[k];

@@ -181,9 +181,22 @@ __global__ void k_tri_t1b(Geom g, const Mode<T>* __restrict__ modes, const T* __
   const T r = modes[m].r;
   const T rL = ipow(r, L);
   T cy = 0;
-  for (int c = 0; c < sh.C; ++c) {
+  // only the last chunk may be shorter; its carry-out is unused
+  constexpr int B = 8;
+  int c = 0;
+  for (; c + B <= sh.C; c += B) {
+    T e[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) e[q] = E[(int64_t)(c + q) * sh.ncols + m];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      carry[(int64_t)(c + q) * sh.ncols + m] = cy;
+      cy = e[q] + rL * cy;
+    }
+  }
+  for (; c < sh.C; ++c) {
     carry[(int64_t)c * sh.ncols + m] = cy;
-    cy = E[(int64_t)c * sh.ncols + m] + rL * cy;  // only the last chunk may be shorter; its carry-out is unused
+    cy = E[(int64_t)c * sh.ncols + m] + rL * cy;
   }
 }
 
@@ -232,11 +245,26 @@ __global__ void k_tri_t2b(Geom g, const Mode<T>* __restrict__ modes, const T* __
   const T r = modes[m].r;
   const T rL = ipow(r, L);
   const int lastlen = sh.nt - (sh.C - 1) * L;
+  // last (possibly shorter) chunk first, then the full ones in batches
   T bc = 0;
-  for (int c = sh.C - 1; c >= 0; --c) {
+  int c = sh.C - 1;
+  bcarry[(int64_t)c * sh.ncols + m] = bc;
+  bc = B[(int64_t)c * sh.ncols + m] + ipow(r, lastlen) * bc;  // p at the chunk start
+  --c;
+  constexpr int NB = 8;
+  for (; c - NB + 1 >= 0; c -= NB) {
+    T bv[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) bv[q] = B[(int64_t)(c - q) * sh.ncols + m];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      bcarry[(int64_t)(c - q) * sh.ncols + m] = bc;
+      bc = bv[q] + rL * bc;
+    }
+  }
+  for (; c >= 0; --c) {
     bcarry[(int64_t)c * sh.ncols + m] = bc;
-    const T rlen = (c == sh.C - 1) ? ipow(r, lastlen) : rL;
-    bc = B[(int64_t)c * sh.ncols + m] + rlen * bc;  // p at the chunk start
+    bc = B[(int64_t)c * sh.ncols + m] + rL * bc;
   }
   Cc[m] = modes[m].kapC * bc;  // bc = p_1
 }
@@ -259,15 +287,14 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
-  // descending: r^(e0 + 1 - j) * bc and - C r^(2N - j), both shrinking as j decreases
-  T rb = r * bc;
-  T Bj = Cm * ipow(r, 2 * sh.Nt - e0);
+  // descending: r^(e0 + 1 - j) bc - C r^(2N - j) = X_j, one geometric term
+  // (X_{j-1} = r X_j) that shrinks as j decreases
+  T X = r * bc - Cm * ipow(r, 2 * sh.Nt - e0);
 #pragma unroll
   for (int q = L - 1; q >= 0; --q)
     if (q < len) {
-      d[q] += rb - Bj;
-      rb *= r;
-      Bj *= r;
+      d[q] += X;
+      X *= r;
     }
   // ascending: + C r^j, shrinking as j increases
   T Aj = Cm * ipow(r, s0);
