@@ -268,6 +268,30 @@ def run_ours(args, rank, world, local):
             "hbm_peak_GBs": _peaks().get("hbm_gbs"),
             "share_of_step": kms["dst_x"] / sum(kms.values()), "top_kernel_by_time": top,
             "fp64_instr_note": "FFT mix is ~1.2 flops per FP64 instruction; ncu pipe utilisation in profiles/"}
+    # the same workload through the mixed-precision path (FP32 inner solves, FP64 refinement)
+    variants = {}
+    if not args.no_mixed:
+        pm = ahoc.plan_for(data, device=dev, timing=False, restart=args.restart, max_iters=args.max_iters,
+                           prec="mixed")
+        um = torch.empty_like(f)
+        for _ in range(args.warmup):
+            pm.solve(f, um, tol=args.tol)
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(pm.stream)
+        for _ in range(args.steps):
+            _, im = pm.solve(f, um, tol=args.tol)
+        m1.record(pm.stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        variants["mixed"] = {
+            "value": args.steps * dof / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / args.steps,
+            "dtype": "f32 inner solves, f64 refinement", "refine_steps": im["refine_steps"],
+            "gmres_iters_total": im["iters"],
+            "err_inf_vs_exact": float((um.reshape(N + 1, N + 1) - data["u_exact"]).abs().max()),
+            "rel_l2_vs_fp64": float(torch.linalg.norm(um - u) / torch.linalg.norm(u))}
+        pm.close()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, dt, _ = cpu_oracle_sample(args.cpu_n)
@@ -293,6 +317,7 @@ def run_ours(args, rank, world, local):
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
 
@@ -310,6 +335,7 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=256)
     ap.add_argument("--levels", type=int, default=-1, help="coarse levels of the nested initial guess (-1 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

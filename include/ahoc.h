@@ -81,14 +81,20 @@ typedef struct {
 
 /* Options; a NULL pointer selects the defaults given in brackets. */
 typedef struct {
-  ahoc_precision prec;    /* [AHOC_FP64] arithmetic of the Poisson solves                      */
+  ahoc_precision prec;    /* [AHOC_FP64] arithmetic of the Poisson solves.  AHOC_MIXED: FP32
+                             inner solves (DST, tridiagonal, stencils) inside FP64 iterative
+                             refinement of the coupled system (FP64 residual of all three
+                             block rows, FP64 GMRES vectors, Hessenberg and updates); the
+                             stopping test is the same relative Schur residual.  In a MIXED
+                             plan ahoc_matvec runs the FP32 inner solves.                     */
   int max_iters;          /* [500] total GMRES iterations allowed                               */
   int restart;            /* [100] Krylov basis size before a restart (the paper's GMRES is not
                              restarted; the cap only bounds memory)                            */
   int precond;            /* [1] 1: right-precondition GMRES with the boundary-symbol operator
                              (inverse single-face Schur symbol per face, coefficient frozen
                              pointwise on the face); 0: no preconditioner                    */
-  double refine_tol;      /* [0] reserved                                                      */
+  double refine_tol;      /* [3e-6] AHOC_MIXED: relative residual each FP32 correction GMRES
+                             aims for (<= 0 selects the default)                               */
   int timing;             /* [0] nonzero: time every kernel launch of ahoc_solve with CUDA
                              events on the plan's stream (ahoc_info.kernel_ms)               */
   void* workspace;        /* [NULL] caller-owned device workspace of at least
@@ -116,6 +122,7 @@ typedef struct {
   int coarse_iters;       /* GMRES iterations summed over the coarse levels                     */
   double kernel_ms_top[AHOC_NK];      /* as kernel_ms, this grid's launches only (no coarse)  */
   int64_t kernel_launches_top[AHOC_NK];
+  int refine_steps;       /* AHOC_MIXED: FP32 correction solves taken                           */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:

@@ -46,7 +46,8 @@ class ahoc_info(C.Structure):
                 ("ms_total", C.c_double), ("ms_matvec", C.c_double), ("launches", C.c_int64),
                 ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK),
                 ("levels", C.c_int), ("coarse_iters", C.c_int),
-                ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK)]
+                ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK),
+                ("refine_steps", C.c_int)]
 
 
 class AhocError(RuntimeError):
@@ -162,6 +163,9 @@ class Plan:
                 if b != a:
                     s *= self.N[b] - 1
             self.ngamma += 2 * s
+        if isinstance(prec, str):
+            prec = {"fp64": AHOC_FP64, "mixed": AHOC_MIXED}[prec]
+        self.prec = prec
         self.device = alpha.device
         nb = workspace_bytes(dim, self.N, restart, prec, levels)
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
@@ -194,7 +198,8 @@ class Plan:
                        kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)},
                        levels=info.levels, coarse_iters=info.coarse_iters,
                        kernel_ms_top={k: info.kernel_ms_top[i] for i, k in enumerate(KERNEL_NAMES)},
-                       kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)})
+                       kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)},
+                       refine_steps=info.refine_steps)
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         if y is None:

@@ -73,17 +73,25 @@ cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t s
 //   rhs = -M f - L_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
-                        const double* vedge, cudaStream_t st);
+                        const double* vedge, cudaStream_t st, const T* srcv = nullptr);
 // u-equation right-hand side for L_h U_int = rhs:
 //   rhs = M(V / alpha) - L_bdry(g_D),  V = Q on face points (M reaches no edges).
 template <typename T>
 cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
-                        const double* gD, cudaStream_t st);
+                        const double* gD, cudaStream_t st, const T* srcu = nullptr);
 // Boundary residual R_p = alpha_p [u_nn(U)_p + lapt_p] - Q_p at every face point.
 template <typename T>
 cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
                          const double* afac, const double* gD, const double* gN, const double* lapt,
-                         cudaStream_t st);
+                         cudaStream_t st, const double* srcq = nullptr);
+
+// mixed precision: FP64 residual of the coupled system (r_u, r_v in FP32, r_q in FP64)
+cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
+                            const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
+                            const double* gN, const double* lapt, const double* ainv, const double* afac,
+                            cudaStream_t st);
+cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
+                              cudaStream_t st);
 
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st);
 cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st);

@@ -45,6 +45,7 @@ struct Opts {
   int precond = 1;
   int timing = 0;
   int levels = -1;  // coarse levels of the nested initial guess (-1: automatic)
+  double refine_tol = 3e-6;  // mixed precision: relative residual of each FP32 correction solve
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -58,10 +59,12 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.precond = o->precond < 0 ? 1 : o->precond;
     d.timing = o->timing;
     d.levels = o->levels;
+    if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
-  if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "only AHOC_FP64 is implemented");
+  if (d.prec != AHOC_FP64 && d.prec != AHOC_MIXED) return fail(AHOC_EUNSUPPORTED, "prec must be AHOC_FP64 or AHOC_MIXED");
+  if (d.prec == AHOC_MIXED) d.levels = 0;  // the nested initial guess belongs to the FP64 path
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.levels < -1 || d.levels > 8) return fail(AHOC_EINVAL, "levels must be -1 (automatic) or 0..8");
@@ -174,7 +177,12 @@ void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
 }
 
 // Per-mode factors of the tridiagonal solve along the last axis (tri.cu).
-ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<double>>& out) {
+// log10 of the smallest power of r the sequential kernel may scale back up
+template <typename T> constexpr long double pow_floor() { return -290.0L; }
+template <> constexpr long double pow_floor<float>() { return -36.0L; }
+
+template <typename T>
+ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int nx = g.N[0] - 1;
   const int ny = (g.dim == 3) ? g.N[1] - 1 : 1;
@@ -200,22 +208,22 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<double>>
       if (!(fabsl(gam) < 0.5L)) return fail(AHOC_EUNSUPPORTED, "tridiagonal factor not diagonally dominant (mesh aspect ratio)");
       const long double r = 2 * gam / (1 + sqrtl(1 - 4 * gam * gam));
       const long double sigma = a / (1 + r * r);
-      Mode<double> m;
-      m.r = (double)r;
-      m.s = (double)(scale / sigma);
+      Mode<T> m;
+      m.r = (T)r;
+      m.s = (T)(scale / sigma);
       const long double r2N = powl(r, 2.0L * Nt);
-      m.kap = (double)(-r * (1 - r * r) / (1 - r2N));
-      m.kapC = (double)(-r / (1 - r2N));
+      m.kap = (T)(-r * (1 - r * r) / (1 - r2N));
+      m.kapC = (T)(-r / (1 - r2N));
       if (r == 0.0L) {
         m.rinv = 0;
         m.rj0 = 0;
         m.j0 = 0;
       } else {
-        long double lim = -290.0L * logl(10.0L) / logl(fabsl(r));
+        long double lim = pow_floor<T>() * logl(10.0L) / logl(fabsl(r));
         int j0 = (lim >= nt) ? nt : (int)lim;
         if (j0 < 0) j0 = 0;
-        m.rinv = (double)(1.0L / r);
-        m.rj0 = (double)powl(r, (long double)j0);
+        m.rinv = (T)(1.0L / r);
+        m.rj0 = (T)powl(r, (long double)j0);
         m.j0 = j0;
       }
       out[(size_t)(ky - 1) * nx + (kx - 1)] = m;
@@ -228,7 +236,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
-      tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, total;
+      tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau,
+      // mixed precision (AHOC_MIXED only)
+      F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -286,6 +296,23 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.Kry = take(face * (size_t)(o.restart + 1));
   L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
   L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
+  const bool mixed = (o.prec == AHOC_MIXED);
+  const size_t ffl = mixed ? (size_t)g.npad * sizeof(float) : 0;
+  L.F1 = take(ffl);
+  L.F2 = take(ffl);
+  L.Ru = take(ffl);
+  L.Rv = take(ffl);
+  L.U64 = take(mixed ? fld : 0);
+  L.V64 = take(mixed ? fld : 0);
+  for (int a = 0; a < 3; ++a) {
+    L.twf[a] = take(mixed ? 2 * (size_t)g.N[a] * sizeof(float) : 0);
+    L.snf[a] = take(mixed ? ((size_t)g.N[a] / 2 + 1) * sizeof(float) : 0);
+  }
+  L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
+  L.trif = take(mixed && tri_ncols(g) < kChunkedBelow ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(float) : 0);
+  L.Rq = take(mixed ? face : 0);
+  L.dQ = take(mixed ? face : 0);
+  L.b2 = take(mixed ? face : 0);
   L.total = off;
   return L;
 }
@@ -339,6 +366,12 @@ struct ahoc_plan {
   double *stab[3], *ctab[3];
   double *rxm, *rxp, *qy, *R2, *tau;
   Mode<double>* modes;
+  // mixed precision
+  float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
+        *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
+  double *U64 = nullptr, *V64 = nullptr, *Rq = nullptr, *dQ = nullptr, *b2 = nullptr;
+  Mode<float>* modesf = nullptr;
+  int refine_steps = 0;
   double* hhost = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool have_last = false;
@@ -431,6 +464,31 @@ ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) 
   return AHOC_OK;
 }
 
+// FP32 Dirichlet Poisson solve in place (mixed precision inner solves)
+ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
+  const Geom& g = p->g;
+  RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
+  if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
+  if (tri_ncols(g) < kChunkedBelow)
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->trif, tri_chunk_len(g), p->st));
+  else
+    RUN(AHOC_K_TRI, launch_tri<float>(g, W, p->modesf, p->st));
+  if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
+  return AHOC_OK;
+}
+
+// FP32 correction solves of the coupled system with residual sources:
+// L_h dV = -r_v - L_bdry(dQ)  ->  F1;   L_h dU = r_u + M(dV/alpha)  ->  F2
+ahoc_status solve_VU_f(ahoc_plan* p, const double* Q, const float* srcv, const float* srcu) {
+  const Geom& g = p->g;
+  RUN(AHOC_K_VRHS, launch_vrhs<float>(g, p->cf, p->F1, Q, nullptr, nullptr, p->st, srcv));
+  CKS(poisson_inplace_f(p, p->F1));
+  RUN(AHOC_K_URHS, launch_urhs<float>(g, p->cf, p->F2, p->F1, p->ainv, Q, nullptr, p->st, srcu));
+  CKS(poisson_inplace_f(p, p->F2));
+  return AHOC_OK;
+}
+
 // SchurMatVec in 2D without full-field right-hand sides or inverse transforms:
 // V-hat from the generated spectrum (tri), W = V/alpha by one inverse DST,
 // G-hat = DST(M(W) + face terms) by one forward DST, U-hat by tri, then the
@@ -454,6 +512,11 @@ ahoc_status matvec_fused2d(ahoc_plan* p, const double* q, double* y) {
 }
 
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
+  if (p->o.prec == AHOC_MIXED) {
+    CKS(solve_VU_f(p, q, nullptr, nullptr));
+    RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
+    return AHOC_OK;
+  }
   if (p->g.dim == 2 && tri_ncols(p->g) < kChunkedBelow) return matvec_fused2d(p, q, y);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
@@ -583,7 +646,9 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   CKS(read_opts(opts, &o));
   Coefs cf = make_coefs(g);
   std::vector<Mode<double>> modes;
-  CKS(mode_table(g, cf, modes));
+  CKS(mode_table<double>(g, cf, modes));
+  std::vector<Mode<float>> modesf;
+  if (o.prec == AHOC_MIXED) CKS(mode_table<float>(g, cf, modesf));
   Layout L = make_layout(g, o);
   const size_t need = total_bytes(g, o);
   if (o.workspace && o.workspace_bytes < need) return fail(AHOC_ENOMEM, "caller workspace too small");
@@ -632,6 +697,23 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->qy = at<double>(p, L.qy);
   p->R2 = at<double>(p, L.R2);
   p->tau = at<double>(p, L.tau);
+  if (o.prec == AHOC_MIXED) {
+    p->F1 = at<float>(p, L.F1);
+    p->F2 = at<float>(p, L.F2);
+    p->Ru = at<float>(p, L.Ru);
+    p->Rv = at<float>(p, L.Rv);
+    p->U64 = at<double>(p, L.U64);
+    p->V64 = at<double>(p, L.V64);
+    for (int a = 0; a < 3; ++a) {
+      p->twf[a] = at<float>(p, L.twf[a]);
+      p->snf[a] = at<float>(p, L.snf[a]);
+    }
+    p->modesf = at<Mode<float>>(p, L.modesf);
+    p->trif = at<float>(p, L.trif);
+    p->Rq = at<double>(p, L.Rq);
+    p->dQ = at<double>(p, L.dQ);
+    p->b2 = at<double>(p, L.b2);
+  }
   p->modes = at<Mode<double>>(p, L.modes);
   p->b = at<double>(p, L.b);
   p->Q = at<double>(p, L.Q);
@@ -665,6 +747,20 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   CKC(cudaMemcpyAsync(p->sny, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
   CKC(cudaMemcpyAsync(p->modes, modes.data(), modes.size() * sizeof(Mode<double>), cudaMemcpyHostToDevice, p->st));
   CKC(cudaStreamSynchronize(p->st));
+  if (o.prec == AHOC_MIXED) {
+    const size_t ffl = (size_t)g.npad * sizeof(float);
+    CKC(cudaMemsetAsync(p->F1, 0, ffl, p->st));
+    CKC(cudaMemsetAsync(p->F2, 0, ffl, p->st));
+    CKC(cudaMemcpyAsync(p->modesf, modesf.data(), modesf.size() * sizeof(Mode<float>), cudaMemcpyHostToDevice,
+                        p->st));
+    for (int a = 0; a < g.dim; ++a) {
+      dst_tables(g.N[a], tw, sn);
+      std::vector<float> twf(tw.begin(), tw.end()), snf(sn.begin(), sn.end());
+      CKC(cudaMemcpyAsync(p->twf[a], twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+      CKC(cudaMemcpyAsync(p->snf[a], snf.data(), snf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+      CKC(cudaStreamSynchronize(p->st));
+    }
+  }
   if (g.dim == 3) {
     dst_tables(g.N[2], tw, sn);
     CKC(cudaMemcpyAsync(p->twz, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
@@ -827,11 +923,250 @@ ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
   if (!p || !q) return fail(AHOC_EINVAL, "NULL argument");
   if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
   CK(cudaMemcpyAsync(q, p->Q, p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-  if (v) RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->W1, p->Q, p->vedge, p->st));
+  if (v) RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->o.prec == AHOC_MIXED ? p->V64 : p->W1, p->Q, p->vedge, p->st));
   return AHOC_OK;
 }
 
-// Algorithm 1, Main procedure, with GMRES (CGS2 Arnoldi, Givens rotations).
+}  // extern "C"
+
+namespace {
+
+struct GmresOut {
+  int iters = 0, restarts = 0;
+  double rel = 0.0, ms_mv = 0.0;
+  ahoc_status status = AHOC_OK;
+};
+
+// GMRES on S X = b (right-preconditioned with the boundary-symbol operator,
+// CGS2 Arnoldi on the device, Givens rotations and the least-squares solve
+// on the host in FP64).  X holds the initial guess on entry when `guess`
+// (else it is zeroed) and the iterate on exit; tol is relative to beta0 =
+// ||b||.  Restarts (an explicit residual) only when the basis is full.
+ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool guess, double tol, int max_iters,
+                  GmresOut* go) {
+  const int64_t n = p->g.ngamma;
+  const int m = p->o.restart;
+  double beta = beta0;
+  if (guess) {
+    CKS(matvec_dev(p, X, p->tmp));
+    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
+    CKS(mdot(p, p->r, 1, p->r, p->hdev));
+    CKS(fetch(p, 1));
+    beta = std::sqrt(p->hhost[0]);
+    if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite initial residual");
+  } else {
+    CK(cudaMemsetAsync(X, 0, n * sizeof(double), p->st));
+    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  bool done = false;
+  while (!done) {
+    go->rel = beta / beta0;
+    if (go->rel <= tol) break;
+    if (go->iters >= max_iters) {
+      go->status = AHOC_ENOCONV;
+      break;
+    }
+    double* V = p->Kry;
+    RUN(AHOC_K_KRYLOV, launch_axpby(V, p->r, 1.0 / beta, 0.0, n, p->st));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      double* w = V + (int64_t)(j + 1) * n;
+      CK(cudaEventRecord(p->ev0, p->st));
+      CKS(precond_apply(p, V + (int64_t)j * n, p->z));
+      CKS(matvec_dev(p, p->z, w));
+      CK(cudaEventRecord(p->ev1, p->st));
+      // CGS2
+      double* h1 = p->hdev;
+      double* h2 = p->hdev + (j + 1);
+      double* nr = p->hdev + 2 * (j + 1);
+      CKS(mdot(p, V, j + 1, w, h1));
+      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h1, w, n, p->st));
+      CKS(mdot(p, V, j + 1, w, h2));
+      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h2, w, n, p->st));
+      CKS(mdot(p, w, 1, w, nr));
+      CKS(fetch(p, 2 * (j + 1) + 1));
+      float evms = 0.f;
+      if (cudaEventElapsedTime(&evms, p->ev0, p->ev1) == cudaSuccess) go->ms_mv += evms;
+      ++go->iters;
+      double* Hc = &H[(size_t)j * (m + 1)];
+      for (int i = 0; i <= j; ++i) Hc[i] = p->hhost[i] + p->hhost[j + 1 + i];
+      const double hn = std::sqrt(p->hhost[2 * (j + 1)]);
+      if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
+      Hc[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = Hc[i], bb = Hc[i + 1];
+        Hc[i] = cs[i] * a + sn[i] * bb;
+        Hc[i + 1] = -sn[i] * a + cs[i] * bb;
+      }
+      const double den = std::hypot(Hc[j], Hc[j + 1]);
+      cs[j] = (den > 0) ? Hc[j] / den : 1.0;
+      sn[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
+      Hc[j] = den;
+      Hc[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      jend = j + 1;
+      go->rel = std::fabs(gv[j + 1]) / beta0;
+      if (go->rel <= tol || hn == 0.0 || go->iters >= max_iters) {
+        done = (go->rel <= tol || hn == 0.0);
+        break;
+      }
+      RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 1.0 / hn, 0.0, n, p->st));
+    }
+    // y = H^-1 g (upper triangular), X += P^-1 (V y)
+    for (int i = jend - 1; i >= 0; --i) {
+      double sacc = gv[i];
+      for (int k = i + 1; k < jend; ++k) sacc -= H[(size_t)k * (m + 1) + i] * y[k];
+      y[i] = sacc / H[(size_t)i * (m + 1) + i];
+    }
+    for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
+    CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemsetAsync(p->tmp, 0, n * sizeof(double), p->st));
+    RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->tmp, n, p->st));
+    CKS(precond_apply(p, p->tmp, p->z));
+    RUN(AHOC_K_KRYLOV, launch_axpby(X, p->z, 1.0, 1.0, n, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    CKS(harvest(p));
+    if (done) break;
+    if (go->iters >= max_iters) {
+      go->status = AHOC_ENOCONV;
+      break;
+    }
+    // restart: explicit residual r = b - S X
+    ++go->restarts;
+    CKS(matvec_dev(p, X, p->tmp));
+    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
+    CKS(mdot(p, p->r, 1, p->r, p->hdev));
+    CKS(fetch(p, 1));
+    beta = std::sqrt(p->hhost[0]);
+    if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite restart residual");
+  }
+  return AHOC_OK;
+}
+
+ahoc_status norm2(ahoc_plan* p, const double* v, double* out) {
+  CKS(mdot(p, v, 1, v, p->hdev));
+  CKS(fetch(p, 1));
+  *out = std::sqrt(p->hhost[0]);
+  if (!is_fin(*out)) return fail(AHOC_ENUMERIC, "non-finite norm");
+  return AHOC_OK;
+}
+
+// Algorithm 1 in FP64: b = -R(0), GMRES on S_h Q = b (from the nested
+// coarse-grid guess when the plan has coarse levels), recovery of V and U.
+ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol, GmresOut* go) {
+  const Geom& g = p->g;
+  CKS(schur_rhs_dev(p, f, p->b));
+  double beta0 = 0.0;
+  CKS(norm2(p, p->b, &beta0));
+  bool guess = false;
+  p->coarse_iters = 0;
+  if (beta0 > 0 && p->coarse) {
+    // nested initial guess: solve on the coarser grid (recursively), then
+    // prolong its Q to this grid's faces (the coarse-grid interpolated
+    // initial guess of Sec. 4.1)
+    ahoc_plan* c = p->coarse;
+    double* f_c = p->W2;
+    double* u_c = p->W1;
+    RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    ahoc_info ci;
+    std::memset(&ci, 0, sizeof(ci));
+    ahoc_status cs_ = ahoc_solve(c, f_c, u_c, tol, &ci);
+    if (cs_ != AHOC_OK && cs_ != AHOC_ENOCONV) return cs_;
+    p->coarse_iters = ci.iters + c->coarse_iters;
+    CKS(harvest(p));
+    for (int k = 0; k < AHOC_NK; ++k) {
+      // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
+      p->kms_top[k] -= ci.kernel_ms[k];
+      p->kn_top[k] -= ci.kernel_launches[k];
+      p->kms[k] += ci.kernel_ms[k];
+      p->kn[k] += ci.kernel_launches[k];
+    }
+    p->launches += ci.launches;
+    go->ms_mv += ci.ms_matvec;
+    RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
+    // the fields were borrowed as temporaries: restore the zero padding
+    CK(cudaMemsetAsync(p->W1, 0, (size_t)g.npad * sizeof(double), p->st));
+    CK(cudaMemsetAsync(p->W2, 0, (size_t)g.npad * sizeof(double), p->st));
+    guess = true;
+  }
+  if (beta0 > 0) CKS(gmres(p, p->b, beta0, p->Q, guess, tol, p->o.max_iters, go));
+  else CK(cudaMemsetAsync(p->Q, 0, g.ngamma * sizeof(double), p->st));
+  // recovery: V and U with the converged Q (and the data)
+  CKS(solve_VU(p, p->Q, f, true));
+  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->gD, p->st));
+  return AHOC_OK;
+}
+
+// Mixed precision: iterative refinement of the coupled system.  Each step
+// takes the FP64 residual of all three block rows at x = (U, V, Q), solves
+// the coupled correction system with FP32 Poisson solves (the same Schur
+// method: b = -R_d(0), GMRES on S dQ = b to refine_tol, recovery of dV, dU)
+// and adds the correction in FP64.  The relative size of the correction
+// right-hand side -- the Schur residual of the current iterate, evaluated
+// from the FP64 residual -- is the stopping test, so tol has the meaning it
+// has on the FP64 path.
+constexpr int kMaxRefine = 8;
+ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, GmresOut* go) {
+  const Geom& g = p->g;
+  const int64_t n = g.ngamma;
+  CK(cudaMemsetAsync(p->U64, 0, (size_t)g.npad * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->V64, 0, (size_t)g.npad * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->Q, 0, n * sizeof(double), p->st));
+  double bref = 0.0;
+  p->refine_steps = 0;
+  for (int step = 0; step <= kMaxRefine; ++step) {
+    RUNN(AHOC_K_OTHER, 2,
+         launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->gD, p->vedge, p->gN, p->lapt,
+                         p->ainv, p->afac, p->st));
+    // correction right-hand side b = -R_d(0)
+    CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
+    RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
+                                          p->st, p->Rq));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st));
+    double bn = 0.0;
+    CKS(norm2(p, p->b2, &bn));
+    if (step == 0) bref = bn;
+    go->rel = (bref > 0) ? bn / bref : 0.0;
+    if (bn == 0.0 || go->rel <= tol) break;
+    if (step == kMaxRefine) {
+      go->status = AHOC_ENOCONV;
+      break;
+    }
+    // inner tolerance: refine_tol, but no tighter than the outer goal needs
+    double itol = p->o.refine_tol;
+    const double need = 0.5 * tol * bref / bn;
+    if (need > itol) itol = need;
+    GmresOut gi;
+    CKS(gmres(p, p->b2, bn, p->dQ, false, itol, p->o.max_iters - go->iters, &gi));
+    go->iters += gi.iters;
+    go->restarts += gi.restarts;
+    go->ms_mv += gi.ms_mv;
+    // recovery of the correction and the FP64 update
+    CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
+    RUN(AHOC_K_OTHER, launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->dQ, 1.0, 1.0, n, p->st));
+    ++p->refine_steps;
+    if (go->iters >= p->o.max_iters) {
+      go->status = AHOC_ENOCONV;
+      break;
+    }
+  }
+  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->U64, p->gD, p->st));
+  return AHOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Algorithm 1, Main procedure (FP64, or FP32 inner solves with FP64 refinement).
 ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info) {
   if (!p || !f || !u) return fail(AHOC_EINVAL, "NULL argument");
   if (!(tol > 0) || !std::isfinite(tol)) return fail(AHOC_EINVAL, "tol must be positive");
@@ -846,178 +1181,30 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
     p->kms_top[k] = 0;
     p->kn_top[k] = 0;
   }
-  const Geom& g = p->g;
-  const int64_t n = g.ngamma;
-  const int m = p->o.restart;
-  double ms_mv = 0.0;
-  // b = -R(0)
-  CKS(schur_rhs_dev(p, f, p->b));
-  CKS(mdot(p, p->b, 1, p->b, p->hdev));
-  CKS(fetch(p, 1));
-  const double beta0 = std::sqrt(p->hhost[0]);
-  if (!is_fin(beta0)) return fail(AHOC_ENUMERIC, "non-finite ||b||");
-  CK(cudaMemsetAsync(p->Q, 0, n * sizeof(double), p->st));
-  int iters = 0, restarts = 0;
-  double rel = 0.0;
-  ahoc_status status = AHOC_OK;
-  p->coarse_iters = 0;
-  if (beta0 > 0) {
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-    double beta = beta0;
-    if (p->coarse) {
-      // nested initial guess: solve on the coarser grid (recursively), then
-      // prolong its Q to this grid's faces (the paper's coarse-grid
-      // interpolated initial guess, Sec. 4.1)
-      ahoc_plan* c = p->coarse;
-      double* f_c = p->W2;
-      double* u_c = p->W1;
-      RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
-      CK(cudaStreamSynchronize(p->st));
-      ahoc_info ci;
-      std::memset(&ci, 0, sizeof(ci));
-      ahoc_status cs_ = ahoc_solve(c, f_c, u_c, tol, &ci);
-      if (cs_ != AHOC_OK && cs_ != AHOC_ENOCONV) return cs_;
-      p->coarse_iters = ci.iters + c->coarse_iters;
-      CKS(harvest(p));
-      for (int k = 0; k < AHOC_NK; ++k) {
-        // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
-        p->kms_top[k] -= ci.kernel_ms[k];
-        p->kn_top[k] -= ci.kernel_launches[k];
-      }
-      p->launches += ci.launches;
-      for (int k = 0; k < AHOC_NK; ++k) {
-        p->kms[k] += ci.kernel_ms[k];
-        p->kn[k] += ci.kernel_launches[k];
-      }
-      ms_mv += ci.ms_matvec;
-      RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
-      // the fields were borrowed as temporaries: restore the zero padding
-      CK(cudaMemsetAsync(p->W1, 0, (size_t)g.npad * sizeof(double), p->st));
-      CK(cudaMemsetAsync(p->W2, 0, (size_t)g.npad * sizeof(double), p->st));
-      // r = b - S Q0
-      CKS(matvec_dev(p, p->Q, p->tmp));
-      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-      RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
-      CKS(mdot(p, p->r, 1, p->r, p->hdev));
-      CKS(fetch(p, 1));
-      beta = std::sqrt(p->hhost[0]);
-      if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite initial residual");
-    } else {
-      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-    }
-    bool done = false;
-    while (!done) {
-      rel = beta / beta0;
-      if (rel <= tol) break;
-      if (iters >= p->o.max_iters) {
-        status = AHOC_ENOCONV;
-        break;
-      }
-      double* V = p->Kry;
-      RUN(AHOC_K_KRYLOV, launch_axpby(V, p->r, 1.0 / beta, 0.0, n, p->st));
-      std::fill(gv.begin(), gv.end(), 0.0);
-      gv[0] = beta;
-      int jend = 0;
-      for (int j = 0; j < m; ++j) {
-        double* w = V + (int64_t)(j + 1) * n;
-        CK(cudaEventRecord(p->ev0, p->st));
-        CKS(precond_apply(p, V + (int64_t)j * n, p->z));
-        CKS(matvec_dev(p, p->z, w));
-        CK(cudaEventRecord(p->ev1, p->st));
-        // CGS2
-        double* h1 = p->hdev;
-        double* h2 = p->hdev + (j + 1);
-        double* nr = p->hdev + 2 * (j + 1);
-        CKS(mdot(p, V, j + 1, w, h1));
-        RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h1, w, n, p->st));
-        CKS(mdot(p, V, j + 1, w, h2));
-        RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h2, w, n, p->st));
-        CKS(mdot(p, w, 1, w, nr));
-        CKS(fetch(p, 2 * (j + 1) + 1));
-        float evms = 0.f;
-        if (cudaEventElapsedTime(&evms, p->ev0, p->ev1) == cudaSuccess) ms_mv += evms;
-        ++iters;
-        double* Hc = &H[(size_t)j * (m + 1)];
-        for (int i = 0; i <= j; ++i) Hc[i] = p->hhost[i] + p->hhost[j + 1 + i];
-        const double hn = std::sqrt(p->hhost[2 * (j + 1)]);
-        if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
-        Hc[j + 1] = hn;
-        for (int i = 0; i < j; ++i) {
-          const double a = Hc[i], bb = Hc[i + 1];
-          Hc[i] = cs[i] * a + sn[i] * bb;
-          Hc[i + 1] = -sn[i] * a + cs[i] * bb;
-        }
-        const double den = std::hypot(Hc[j], Hc[j + 1]);
-        cs[j] = (den > 0) ? Hc[j] / den : 1.0;
-        sn[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
-        Hc[j] = den;
-        Hc[j + 1] = 0.0;
-        gv[j + 1] = -sn[j] * gv[j];
-        gv[j] = cs[j] * gv[j];
-        jend = j + 1;
-        rel = std::fabs(gv[j + 1]) / beta0;
-        if (rel <= tol || hn == 0.0 || iters >= p->o.max_iters) {
-          done = (rel <= tol || hn == 0.0);
-          break;
-        }
-        RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 1.0 / hn, 0.0, n, p->st));
-      }
-      // y = H^-1 g (upper triangular), Q += V y
-      for (int i = jend - 1; i >= 0; --i) {
-        double s = gv[i];
-        for (int k = i + 1; k < jend; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
-        y[i] = s / H[(size_t)i * (m + 1) + i];
-      }
-      for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
-      CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
-      // Q += P^-1 (V y)
-      CK(cudaMemsetAsync(p->tmp, 0, n * sizeof(double), p->st));
-      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->tmp, n, p->st));
-      CKS(precond_apply(p, p->tmp, p->z));
-      RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->z, 1.0, 1.0, n, p->st));
-      CK(cudaStreamSynchronize(p->st));
-      CKS(harvest(p));
-      if (done) break;
-      if (iters >= p->o.max_iters) {
-        status = AHOC_ENOCONV;
-        break;
-      }
-      // restart: explicit residual r = b - S Q
-      ++restarts;
-      CKS(matvec_dev(p, p->Q, p->tmp));
-      CK(cudaMemcpyAsync(p->r, p->b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-      RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
-      CKS(mdot(p, p->r, 1, p->r, p->hdev));
-      CKS(fetch(p, 1));
-      beta = std::sqrt(p->hhost[0]);
-      if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite restart residual");
-    }
-  }
-  // recovery: V and U with the converged Q (and the data)
-  CKS(solve_VU(p, p->Q, f, true));
-  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->gD, p->st));
+  GmresOut go;
+  if (p->o.prec == AHOC_MIXED) CKS(solve_mixed(p, f, u, tol, &go));
+  else CKS(solve_fp64(p, f, u, tol, &go));
   CK(cudaStreamSynchronize(p->st));
   CKS(harvest(p));
   p->have_last = true;
   if (info) {
-    info->iters = iters;
-    info->restarts = restarts;
-    info->rel_resid = rel;
+    info->iters = go.iters;
+    info->restarts = go.restarts;
+    info->rel_resid = go.rel;
     info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    info->ms_matvec = ms_mv;
+    info->ms_matvec = go.ms_mv;
     info->launches = p->launches;
     info->levels = p->levels;
-    for (int k = 0; k < AHOC_NK; ++k) {
-      info->kernel_ms_top[k] = p->kms[k] + p->kms_top[k];
-      info->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
-    }
     info->coarse_iters = p->coarse_iters;
+    info->refine_steps = p->refine_steps;
     for (int k = 0; k < AHOC_NK; ++k) {
       info->kernel_ms[k] = p->kms[k];
       info->kernel_launches[k] = p->kn[k];
+      info->kernel_ms_top[k] = p->kms[k] + p->kms_top[k];
+      info->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
     }
   }
-  if (status != AHOC_OK) return fail(status, "GMRES reached max_iters");
+  if (go.status != AHOC_OK) return fail(go.status, "GMRES reached max_iters (or refinement did not converge)");
   return AHOC_OK;
 }
 

@@ -41,7 +41,8 @@ __device__ __forceinline__ bool near_bdry(const Geom& g, int i, int j, int k) {
 
 template <typename T>
 __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __restrict__ Q,
-                       const double* __restrict__ f, const double* __restrict__ vedge) {
+                       const double* __restrict__ f, const double* __restrict__ vedge,
+                       const T* __restrict__ srcv) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.npad) return;
   int i, j, k;
@@ -74,13 +75,14 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
     if (g.dim == 3) m += cf.Mn * (f[g.full(i, j, k - 1)] + f[g.full(i, j, k + 1)]);
     acc -= m;
   }
+  if (srcv) acc -= (double)srcv[t];
   out[t] = (T)acc;
 }
 
 template <typename T>
 __global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restrict__ V,
                        const double* __restrict__ ainv, const double* __restrict__ Q,
-                       const double* __restrict__ gD) {
+                       const double* __restrict__ gD, const T* __restrict__ srcu) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.npad) return;
   int i, j, k;
@@ -115,6 +117,7 @@ __global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restric
           acc -= c * gD[g.full(ii, jj, kk)];
         }
   }
+  if (srcu) acc += (double)srcu[t];
   out[t] = (T)acc;
 }
 
@@ -122,7 +125,7 @@ template <typename T>
 __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __restrict__ U,
                         const double* __restrict__ Q, const double* __restrict__ afac,
                         const double* __restrict__ gD, const double* __restrict__ gN,
-                        const double* __restrict__ lapt) {
+                        const double* __restrict__ lapt, const double* __restrict__ srcq) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.ngamma) return;
   int f = 0;
@@ -156,6 +159,7 @@ __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __res
   if (lapt) unn += lapt[q];
   double res = afac[q] * unn;
   if (Q) res -= Q[q];
+  if (srcq) res -= srcq[q];
   y[q] = res;
 }
 
@@ -238,21 +242,21 @@ static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) 
 
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
-                        const double* vedge, cudaStream_t st) {
-  k_vrhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, Q, f, vedge);
+                        const double* vedge, cudaStream_t st, const T* srcv) {
+  k_vrhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
-                        const double* gD, cudaStream_t st) {
-  k_urhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, V, ainv, Q, gD);
+                        const double* gD, cudaStream_t st, const T* srcu) {
+  k_urhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, V, ainv, Q, gD, srcu);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
                          const double* afac, const double* gD, const double* gN, const double* lapt,
-                         cudaStream_t st) {
-  k_trace<T><<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt);
+                         cudaStream_t st, const double* srcq) {
+  k_trace<T><<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq);
   return cudaGetLastError();
 }
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st) {
@@ -282,17 +286,19 @@ cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t 
 }
 
 template cudaError_t launch_vrhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
-                                         const double*, cudaStream_t);
+                                         const double*, cudaStream_t, const double*);
 template cudaError_t launch_urhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
-                                         const double*, const double*, cudaStream_t);
+                                         const double*, const double*, cudaStream_t, const double*);
 template cudaError_t launch_trace<double>(const Geom&, const Coefs&, double*, const double*, const double*,
-                                          const double*, const double*, const double*, const double*, cudaStream_t);
+                                          const double*, const double*, const double*, const double*, cudaStream_t,
+                                          const double*);
 template cudaError_t launch_vrhs<float>(const Geom&, const Coefs&, float*, const double*, const double*,
-                                        const double*, cudaStream_t);
+                                        const double*, cudaStream_t, const float*);
 template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const double*,
-                                        const double*, const double*, cudaStream_t);
+                                        const double*, const double*, cudaStream_t, const float*);
 template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, const float*, const double*,
-                                         const double*, const double*, const double*, const double*, cudaStream_t);
+                                         const double*, const double*, const double*, const double*, cudaStream_t,
+                                         const double*);
 
 }  // namespace ahoc
 
@@ -394,6 +400,126 @@ cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, cons
 }
 cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st) {
   k_face_prolong<<<nblk(gf.ngamma, 256), 256, 0, st>>>(gf, gc, out, in);
+  return cudaGetLastError();
+}
+
+}  // namespace ahoc
+
+namespace ahoc {
+
+// ---------------------------------------------------------------------------
+// Iterative refinement of the coupled system (mixed precision): the FP64
+// residual r = F - A x of the three block rows of Sec. 2.2 at the current
+// iterate x = (U, V, Q), U and V padded FP64 fields, boundary values from the
+// data (U = g_D, V = Q on faces, v_edge on edges and corners):
+//   r_u = -(L_h U - M(V/alpha))            (u-equation, right-hand side 0)
+//   r_v = M f - (-L_h V)                    (v-equation)
+//   r_q = -(alpha (delta_nn U + lapt) - Q)  (augmented equation, Lemma 1's R)
+// r_u and r_v are stored in FP32 (they are the sources of an FP32 correction
+// solve), r_q in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ufull(const Geom& g, const double* U, const double* gD, int i, int j, int k) {
+  int ax, sd;
+  if (bclass(g, i, j, k, ax, sd) == 0) return U[g.pad(i, j, k)];
+  return gD ? gD[g.full(i, j, k)] : 0.0;
+}
+__device__ __forceinline__ double vfull(const Geom& g, const double* V, const double* Q, const double* vedge, int i,
+                                        int j, int k) {
+  int ax, sd;
+  const int nb = bclass(g, i, j, k, ax, sd);
+  if (nb == 0) return V[g.pad(i, j, k)];
+  if (nb == 1) return Q[g.face(ax, sd, i, j, k)];
+  return vedge ? vedge[g.full(i, j, k)] : 0.0;
+}
+
+__global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __restrict__ rv,
+                           const double* __restrict__ U, const double* __restrict__ V, const double* __restrict__ Q,
+                           const double* __restrict__ f, const double* __restrict__ gD,
+                           const double* __restrict__ vedge, const double* __restrict__ ainv) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.npad) return;
+  int i, j, k;
+  decompose(g, t, i, j, k);
+  if (is_pad(g, i, j, k)) {
+    ru[t] = 0.f;
+    rv[t] = 0.f;
+    return;
+  }
+  const bool near = near_bdry(g, i, j, k);
+  double lu = 0.0, lv = 0.0;
+  const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
+  for (int dz = dzlo; dz <= dzhi; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const double c = cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (c == 0.0) continue;
+        const int ii = i + dx, jj = j + dy, kk = k + dz;
+        if (near) {
+          lu += c * ufull(g, U, gD, ii, jj, kk);
+          lv += c * vfull(g, V, Q, vedge, ii, jj, kk);
+        } else {
+          const int64_t o = g.pad(ii, jj, kk);
+          lu += c * U[o];
+          lv += c * V[o];
+        }
+      }
+  // M(V/alpha) and M f: centre and the axis neighbours
+  double mv = cf.Mc * V[t] * ainv[g.full(i, j, k)];
+  double mf = f ? cf.Mc * f[g.full(i, j, k)] : 0.0;
+  for (int a = 0; a < g.dim; ++a)
+    for (int s = -1; s <= 1; s += 2) {
+      const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
+      mv += cf.Mn * vfull(g, V, Q, vedge, ii, jj, kk) * ainv[g.full(ii, jj, kk)];
+      if (f) mf += cf.Mn * f[g.full(ii, jj, kk)];
+    }
+  ru[t] = (float)(-(lu - mv));
+  rv[t] = (float)(mf + lv);
+}
+
+// r_q at every face point (FP64)
+__global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const double* __restrict__ U,
+                             const double* __restrict__ Q, const double* __restrict__ afac,
+                             const double* __restrict__ gD, const double* __restrict__ gN,
+                             const double* __restrict__ lapt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.ngamma) return;
+  int a, side, c[3];
+  face_coords(g, q, a, side, c);
+  const int step = side ? -1 : 1;
+  int p[3] = {c[0], c[1], c[2]};
+  double unn = gD ? cf.w[a][0] * gD[g.full(c[0], c[1], c[2])] : 0.0;
+  for (int m = 1; m <= 3; ++m) {
+    p[a] = c[a] + m * step;
+    unn += cf.w[a][m] * U[g.pad(p[0], p[1], p[2])];
+  }
+  if (gN) unn += cf.wg[a] * gN[q];
+  if (lapt) unn += lapt[q];
+  rq[q] = -(afac[q] * unn - Q[q]);
+}
+
+// x += correction: U += dU, V += dV (FP32 padded fields)
+__global__ void k_accumulate(int64_t n, double* __restrict__ U, const float* __restrict__ dU, double* __restrict__ V,
+                             const float* __restrict__ dV) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  U[t] += (double)dU[t];
+  V[t] += (double)dV[t];
+}
+
+cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
+                            const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
+                            const double* gN, const double* lapt, const double* ainv, const double* afac,
+                            cudaStream_t st) {
+  k_residual<<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, ru, rv, U, V, Q, f, gD, vedge, ainv);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_residual_q<<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
+                              cudaStream_t st) {
+  k_accumulate<<<nblk(g.npad, 256), 256, 0, st>>>(g.npad, U, dU, V, dV);
   return cudaGetLastError();
 }
 

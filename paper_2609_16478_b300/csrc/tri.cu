@@ -361,6 +361,7 @@ template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const 
                                                     const VGen2D&, cudaStream_t);
 
 template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, double*, int, cudaStream_t);
+template cudaError_t launch_tri_chunked<float>(const Geom&, float*, const Mode<float>*, float*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st) {

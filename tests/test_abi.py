@@ -79,3 +79,10 @@ def test_plan_create_rejects_before_allocating():
     assert L.ahoc_solve(None, None, None, C.c_double(1e-12), None) == ahoc.AHOC_EINVAL
     assert L.ahoc_plan_destroy(None) == ahoc.AHOC_OK
     assert L.ahoc_n_gamma(None) == -1
+
+
+def test_no_unresolved_library_symbols():
+    """Every symbol of the library's own namespace is defined (templates instantiated)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", ahoc.LIB_PATH], capture_output=True, text=True).stdout
+    assert "ahoc" not in out, out

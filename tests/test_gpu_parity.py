@@ -254,3 +254,50 @@ def test_nested_initial_guess_matches_oracle(name, N, levels):
     assert i0["levels"] == 0
     if name != "cavity":   # smooth data: the interpolated coarse solution saves fine iterations
         assert i1["iters"] < i0["iters"], (i0["iters"], i1["iters"])
+
+
+# --- mixed precision: FP32 inner solves, FP64 iterative refinement -------------
+
+TOL_MIXED = 1e-9
+
+
+@pytest.mark.parametrize("name,N", [("smooth2d", [64, 64]), ("fourier2d", [256, 256]), ("sincos2d", [32, 32]),
+                                    ("cavity", [64, 64]), ("sincos3d", [16, 16, 16]), ("fourier3d", [16, 8, 16]),
+                                    ("sincos2d", [64, 16])])
+def test_mixed_solve_matches_oracle(name, N):
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    p = _plan(d, prec="mixed")
+    u, info = p.solve(_dev(d["f"]), tol=1e-12)
+    shape = tuple(n + 1 for n in reversed(N))
+    assert _rel(_host(u, shape), sol.U) < TOL_MIXED, info
+    assert info["refine_steps"] >= 2
+    q, v = p.last_qv()
+    assert _rel(q.cpu().numpy(), sol.Q) < 1e-8 and _rel(_host(v, shape), sol.V) < 1e-8
+
+
+@pytest.mark.parametrize("name,N", [("sincos2d", [16, 16]), ("sincos3d", [8, 8, 8])])
+def test_mixed_matvec_is_fp32_accurate(name, N):
+    d = inputs.sample(inputs.config_problem(name), N)
+    p = _plan(d, prec="mixed")
+    S = coupled.Blocks(coupled.assemble(d)).schur_dense()
+    ng = p.ngamma
+    Sg = np.empty((ng, ng))
+    e = torch.zeros(ng, dtype=torch.float64, device="cuda")
+    for j in range(ng):
+        e.zero_()
+        e[j] = 1.0
+        Sg[:, j] = p.matvec(e).cpu().numpy()
+    assert _rel(Sg, S) < 1e-5
+
+
+def test_mixed_equals_fp64_at_1024():
+    d = inputs.sample(inputs.config_problem("fourier2d"), [1024, 1024], backend="torch", device="cuda")
+    f = d["f"].reshape(-1).contiguous()
+    u64, i64 = _plan(d).solve(f, tol=1e-12)
+    umx, imx = _plan(d, prec="mixed").solve(f, tol=1e-12)
+    rel = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    assert rel < TOL_MIXED, (rel, imx)
+    err = float((umx.reshape(1025, 1025) - d["u_exact"]).abs().max())
+    err64 = float((u64.reshape(1025, 1025) - d["u_exact"]).abs().max())
+    assert err < 1.05 * err64 + 1e-15
