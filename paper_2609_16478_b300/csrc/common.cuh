@@ -53,6 +53,8 @@ template <typename T>
 struct alignas(16) Mode {
   T r, rinv, s, kap, rj0;
   T kapC;  // -r / (1 - r^(2N)): coefficient of the boundary correction r^j - r^(2N-j)
+  T q1;    // 1 - r, rounded on its own: r x is formed as x - q1 x, so the effective r
+           // of the slowest modes (r close to 1) keeps full relative accuracy
   int j0;
 };
 

@@ -29,8 +29,8 @@ struct VGen2D {
   double Ly, Lxy;
 };
 template <typename T>
-cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, const VGen2D& G,
-                                   cudaStream_t st);
+cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                                   double* scratch, int L, const VGen2D& G, cudaStream_t st);
 
 // fused 2D matvec helpers (fused2d.cu)
 cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
@@ -62,8 +62,11 @@ cudaError_t launch_face_muldiv(double* out, const double* in, const double* mul,
                                cudaStream_t st);
 
 // chunked tridiagonal solve (2D: few columns, many chunks per column)
+// modes: the element-wise factors (precision T); md64: the FP64 factors used
+// for the chunk carries; scratch: tri_chunked_scratch() doubles
 template <typename T>
-cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, cudaStream_t st);
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64, double* scratch,
+                               int L, cudaStream_t st);
 size_t tri_chunked_scratch(const Geom& g, int L);
 
 template <typename T>

@@ -117,6 +117,7 @@ __global__ void k_na_modes(Geom g, Coefs cf, Mode<double>* modes) {
   const double r2N = na_ipow(r, 2 * Nt);
   md.kap = -r * (1 - r * r) / (1 - r2N);
   md.kapC = -r / (1 - r2N);
+  md.q1 = 1.0 - r;
   if (r == 0.0) {
     md.rinv = 0;
     md.rj0 = 0;
@@ -227,7 +228,7 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
   NA_CK(launch_unpack(g, field, rhs, st));
   NA_CK(launch_dst_x<double>(g, field, twx, snx, 1.0, st));
   if (g.dim == 3) NA_CK(launch_dst_y<double>(g, field, twy, sny, 1.0, st));
-  if (chunked) NA_CK(launch_tri_chunked<double>(g, field, modes, tri, L, st));
+  if (chunked) NA_CK(launch_tri_chunked<double>(g, field, modes, modes, tri, L, st));
   else NA_CK(launch_tri<double>(g, field, modes, st));
   if (g.dim == 3) NA_CK(launch_dst_y<double>(g, field, twy, sny, 1.0, st));
   NA_CK(launch_dst_x<double>(g, field, twx, snx, 1.0, st));

@@ -214,6 +214,7 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out
       const long double r2N = powl(r, 2.0L * Nt);
       m.kap = (T)(-r * (1 - r * r) / (1 - r2N));
       m.kapC = (T)(-r / (1 - r2N));
+      m.q1 = (T)(1.0L - r);
       if (r == 0.0L) {
         m.rinv = 0;
         m.rj0 = 0;
@@ -309,7 +310,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
     L.snf[a] = take(mixed ? ((size_t)g.N[a] / 2 + 1) * sizeof(float) : 0);
   }
   L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
-  L.trif = take(mixed && tri_ncols(g) < kChunkedBelow ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(float) : 0);
+  L.trif = take(0);  // the chunked solve's carries are FP64 in both precisions (shared scratch L.tri)
   L.Rq = take(mixed ? face : 0);
   L.dQ = take(mixed ? face : 0);
   L.b2 = take(mixed ? face : 0);
@@ -446,7 +447,7 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->tri, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->modes, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
@@ -470,7 +471,7 @@ ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->trif, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<float>(g, W, p->modesf, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
@@ -500,10 +501,10 @@ ahoc_status matvec_fused2d(ahoc_plan* p, const double* q, double* y) {
   RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
   RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
   VGen2D G{p->rxm, p->rxp, p->qy, p->qy + (N0 - 1), p->stab[0], p->ctab[0], cf.L[16], cf.L[17]};
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->tri, tri_chunk_len(g), G, p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->modes, p->tri, tri_chunk_len(g), G, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<double>(g, p->W1, p->ainv, p->twx, p->snx, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x_mload<double>(g, p->W2, p->W1, q, p->afac, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, p->W2, p->modes, p->tri, tri_chunk_len(g), p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, p->W2, p->modes, p->modes, p->tri, tri_chunk_len(g), p->st));
   RUN(AHOC_K_TRACE, launch_trace2d_x(g, y, p->W2, q, p->afac, p->tau, p->st));
   RUN(AHOC_K_TRACE, launch_trace2d_ylines(g, cf, p->R2, p->W2, p->st));
   RUN(AHOC_K_TRACE, launch_dst_gen<double>(p->R2, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));

@@ -22,6 +22,10 @@
 
 namespace ahoc {
 
+// r x formed as x - (1 - r) x with 1 - r stored on its own (see Mode::q1)
+__device__ __forceinline__ double rmul(double q1, double x) { return fma(-q1, x, x); }
+__device__ __forceinline__ float rmul(float q1, float x) { return fmaf(-q1, x, x); }
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes) {
   const int nx = g.N[0] - 1;
@@ -46,9 +50,9 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
     for (int q = 0; q < B; ++q) d[q] = col[(int64_t)(j + q) * stride];
 #pragma unroll
     for (int q = 0; q < B; ++q) {
-      w = md.r * w + md.s * d[q];
+      w = rmul(md.q1, w) + md.s * d[q];
       P += rp * w;
-      rp *= md.r;
+      rp = rmul(md.q1, rp);
       d[q] = w;
     }
 #pragma unroll
@@ -56,9 +60,9 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   }
   for (; j <= nt; ++j) {
     T d = col[(int64_t)j * stride];
-    w = md.r * w + md.s * d;
+    w = rmul(md.q1, w) + md.s * d;
     P += rp * w;
-    rp *= md.r;
+    rp = rmul(md.q1, rp);
     col[(int64_t)j * stride] = w;
   }
 
@@ -73,7 +77,7 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
 #pragma unroll
     for (int q = 0; q < B; ++q) {
       if (j - q == md.j0) e = K * md.rj0;
-      u = md.r * u + (d[q] + e);
+      u = rmul(md.q1, u) + (d[q] + e);
       e *= md.rinv;
       d[q] = u;
     }
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   for (; j >= 1; --j) {
     T d = col[(int64_t)j * stride];
     if (j == md.j0) e = K * md.rj0;
-    u = md.r * u + (d + e);
+    u = rmul(md.q1, u) + (d + e);
     e *= md.rinv;
     col[(int64_t)j * stride] = u;
   }
@@ -151,7 +155,7 @@ __device__ __forceinline__ double vgen(const VGen2D& G, int k, int j, int Nt) {
 
 template <typename T, int L, bool GEN>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                T* __restrict__ E, VGen2D G) {
+                                                double* __restrict__ E, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   const int s0 = 1 + c * L;
   const int len = min(L, sh.nt - s0 + 1);
   const T* col = a + col_base(g, m);
-  const T r = modes[m].r, s = modes[m].s;
+  const T q1 = modes[m].q1, s = modes[m].s;
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -168,24 +172,23 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   T w = 0;
 #pragma unroll
   for (int q = 0; q < L; ++q)
-    if (q < len) w = r * w + s * d[q];
-  E[(int64_t)c * sh.ncols + m] = w;
+    if (q < len) w = rmul(q1, w) + s * d[q];
+  E[(int64_t)c * sh.ncols + m] = (double)w;
 }
 
-template <typename T>
-__global__ void k_tri_t1b(Geom g, const Mode<T>* __restrict__ modes, const T* __restrict__ E, T* __restrict__ carry,
-                          int L) {
+__global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ E,
+                          double* __restrict__ carry, int L) {
   const TriShape sh = tri_shape(g, L);
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= sh.ncols) return;
-  const T r = modes[m].r;
-  const T rL = ipow(r, L);
-  T cy = 0;
+  const double r = modes[m].r;
+  const double rL = ipow(r, L);
+  double cy = 0;
   // only the last chunk may be shorter; its carry-out is unused
   constexpr int B = 8;
   int c = 0;
   for (; c + B <= sh.C; c += B) {
-    T e[B];
+    double e[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) e[q] = E[(int64_t)(c + q) * sh.ncols + m];
 #pragma unroll
@@ -202,7 +205,7 @@ __global__ void k_tri_t1b(Geom g, const Mode<T>* __restrict__ modes, const T* __
 
 template <typename T, int L, bool GEN>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                const T* __restrict__ carry, T* __restrict__ B, VGen2D G) {
+                                                const double* __restrict__ carry, double* __restrict__ B, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -211,49 +214,48 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
   const int s0 = 1 + c * L;
   const int len = min(L, sh.nt - s0 + 1);
   T* col = a + col_base(g, m);
-  const T r = modes[m].r, s = modes[m].s;
+  const T q1 = modes[m].q1, s = modes[m].s;
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
     d[q] = (q < len) ? (GEN ? (T)vgen(G, (int)m + 1, s0 + q, sh.Nt) : col[(int64_t)(s0 + q) * sh.stride]) : (T)0;
-  T w = carry[(int64_t)c * sh.ncols + m];
+  T w = (T)carry[(int64_t)c * sh.ncols + m];
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) {
-      w = r * w + s * d[q];
+      w = rmul(q1, w) + s * d[q];
       d[q] = w;
     }
   T p = 0;
 #pragma unroll
   for (int q = L - 1; q >= 0; --q)
     if (q < len) {
-      p = r * p + d[q];
+      p = rmul(q1, p) + d[q];
       d[q] = p;
     }
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
-  B[(int64_t)c * sh.ncols + m] = p;
+  B[(int64_t)c * sh.ncols + m] = (double)p;
 }
 
-template <typename T>
-__global__ void k_tri_t2b(Geom g, const Mode<T>* __restrict__ modes, const T* __restrict__ B, T* __restrict__ bcarry,
-                          T* __restrict__ Cc, int L) {
+__global__ void k_tri_t2b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ B,
+                          double* __restrict__ bcarry, double* __restrict__ Cc, int L) {
   const TriShape sh = tri_shape(g, L);
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= sh.ncols) return;
-  const T r = modes[m].r;
-  const T rL = ipow(r, L);
+  const double r = modes[m].r;
+  const double rL = ipow(r, L);
   const int lastlen = sh.nt - (sh.C - 1) * L;
   // last (possibly shorter) chunk first, then the full ones in batches
-  T bc = 0;
+  double bc = 0;
   int c = sh.C - 1;
   bcarry[(int64_t)c * sh.ncols + m] = bc;
   bc = B[(int64_t)c * sh.ncols + m] + ipow(r, lastlen) * bc;  // p at the chunk start
   --c;
   constexpr int NB = 8;
   for (; c - NB + 1 >= 0; c -= NB) {
-    T bv[NB];
+    double bv[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) bv[q] = B[(int64_t)(c - q) * sh.ncols + m];
 #pragma unroll
@@ -271,7 +273,8 @@ __global__ void k_tri_t2b(Geom g, const Mode<T>* __restrict__ modes, const T* __
 
 template <typename T, int L>
 __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                const T* __restrict__ bcarry, const T* __restrict__ Cc) {
+                                                const Mode<double>* __restrict__ md64,
+                                                const double* __restrict__ bcarry, const double* __restrict__ Cc) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -281,28 +284,29 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
   const int len = min(L, sh.nt - s0 + 1);
   const int e0 = s0 + len - 1;
   T* col = a + col_base(g, m);
-  const T r = modes[m].r;
-  const T bc = bcarry[(int64_t)c * sh.ncols + m];
-  const T Cm = Cc[m];
+  const T q1 = modes[m].q1;
+  const double r = md64[m].r;
+  const double bc = bcarry[(int64_t)c * sh.ncols + m];
+  const double Cm = Cc[m];
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
   // descending: r^(e0 + 1 - j) bc - C r^(2N - j) = X_j, one geometric term
   // (X_{j-1} = r X_j) that shrinks as j decreases
-  T X = r * bc - Cm * ipow(r, 2 * sh.Nt - e0);
+  T X = (T)(r * bc - Cm * ipow(r, 2 * sh.Nt - e0));
 #pragma unroll
   for (int q = L - 1; q >= 0; --q)
     if (q < len) {
       d[q] += X;
-      X *= r;
+      X = rmul(q1, X);
     }
   // ascending: + C r^j, shrinking as j increases
-  T Aj = Cm * ipow(r, s0);
+  T Aj = (T)(Cm * ipow(r, s0));
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) {
       d[q] += Aj;
-      Aj *= r;
+      Aj = rmul(q1, Aj);
     }
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -314,54 +318,59 @@ size_t tri_chunked_scratch(const Geom& g, int L) {
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
   const int C = (nt + L - 1) / L;
-  return (size_t)(4 * C + 1) * ncols;  // elements
+  return (size_t)(4 * C + 1) * ncols;  // doubles (the carries are FP64 for every T)
 }
 
 template <typename T, int L, bool GEN>
-static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, T* scratch, const VGen2D& G,
-                                 cudaStream_t st) {
+static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                                 double* scratch, const VGen2D& G, cudaStream_t st) {
   const int nx = g.N[0] - 1;
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
   const int C = (nt + L - 1) / L;
-  T* E = scratch;
-  T* carry = E + (int64_t)C * ncols;
-  T* B = carry + (int64_t)C * ncols;
-  T* bcarry = B + (int64_t)C * ncols;
-  T* Cc = bcarry + (int64_t)C * ncols;
+  double* E = scratch;
+  double* carry = E + (int64_t)C * ncols;
+  double* B = carry + (int64_t)C * ncols;
+  double* bcarry = B + (int64_t)C * ncols;
+  double* Cc = bcarry + (int64_t)C * ncols;
   const int64_t work = ncols * C;
   const unsigned gb = (unsigned)((work + 127) / 128);
   const unsigned cb = (unsigned)((ncols + 127) / 128);
   k_tri_t1<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, G);
-  k_tri_t1b<T><<<cb, 128, 0, st>>>(g, modes, E, carry, L);
+  k_tri_t1b<<<cb, 128, 0, st>>>(g, md64, E, carry, L);
   k_tri_t2<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
-  k_tri_t2b<T><<<cb, 128, 0, st>>>(g, modes, B, bcarry, Cc, L);
-  k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, bcarry, Cc);
+  k_tri_t2b<<<cb, 128, 0, st>>>(g, md64, B, bcarry, Cc, L);
+  k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, md64, bcarry, Cc);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, cudaStream_t st) {
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64, double* scratch,
+                               int L, cudaStream_t st) {
   VGen2D G{};
-  if (L == 32) return tri_chunked_L<T, 32, false>(g, a, modes, scratch, G, st);
-  if (L == 16) return tri_chunked_L<T, 16, false>(g, a, modes, scratch, G, st);
+  if (L == 32) return tri_chunked_L<T, 32, false>(g, a, modes, md64, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, false>(g, a, modes, md64, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 
 // the same solve with the v-equation right-hand side generated on the fly (2D)
 template <typename T>
-cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, T* scratch, int L, const VGen2D& G,
-                                   cudaStream_t st) {
+cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                                   double* scratch, int L, const VGen2D& G, cudaStream_t st) {
   if (g.dim != 2) return cudaErrorInvalidValue;
-  if (L == 32) return tri_chunked_L<T, 32, true>(g, a, modes, scratch, G, st);
-  if (L == 16) return tri_chunked_L<T, 16, true>(g, a, modes, scratch, G, st);
+  if (L == 32) return tri_chunked_L<T, 32, true>(g, a, modes, md64, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, true>(g, a, modes, md64, scratch, G, st);
   return cudaErrorInvalidValue;
 }
-template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, double*, int,
-                                                    const VGen2D&, cudaStream_t);
+template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
+                                                    double*, int, const VGen2D&, cudaStream_t);
+template cudaError_t launch_tri_chunked_gen<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*,
+                                                   double*, int, const VGen2D&, cudaStream_t);
 
-template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, double*, int, cudaStream_t);
-template cudaError_t launch_tri_chunked<float>(const Geom&, float*, const Mode<float>*, float*, int, cudaStream_t);
+template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
+                                                double*, int, cudaStream_t);
+template cudaError_t launch_tri_chunked<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*, double*,
+                                               int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st) {
