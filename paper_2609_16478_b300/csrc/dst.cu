@@ -202,27 +202,34 @@ struct DstIO {
   const T* src;
   const double* Q;      // LOAD 1: face values
   const double* afac;   // LOAD 1: alpha at face points
-  const double* ainv;   // STORE 1: 1/alpha on the full grid
+  const double* ainv;   // STORE 1: 1/alpha on the full grid; LOAD 1: if set, src holds V, not V/alpha
   double Mc, Mn;        // LOAD 1: weighting M
+  const T* src2;        // LOAD 1: a source field added to M(W) (may be NULL)
+  double lscale;        // LOAD 0: factor applied on load
 };
 
 template <typename T>
+__device__ __forceinline__ double wval(const Geom& g, const DstIO<T>& io, int i, int j) {
+  const double v = (double)io.src[g.pad(i, j, 0)];
+  return io.ainv ? v * io.ainv[g.full(i, j, 0)] : v;
+}
+__device__ __forceinline__ double qval(const double* Q, const double* afac, int64_t q) {
+  return Q ? Q[q] / afac[q] : 0.0;
+}
+
+template <typename T>
 __device__ __forceinline__ T mstencil2d(const Geom& g, const DstIO<T>& io, int i, int j) {
-  const T* W = io.src;
-  const int64_t o = g.pad(i, j, 0);
-  double acc = io.Mc * (double)W[o];
+  double acc = io.Mc * wval(g, io, i, j);
   double nb = 0.0;
-  // x neighbours (i-1 = 0 and i+1 = N0 are faces x-/x+)
-  if (i > 1) nb += (double)W[o - 1];
-  else { const int64_t q = g.face(0, 0, 0, j, 0); nb += io.Q[q] / io.afac[q]; }
-  if (i < g.N[0] - 1) nb += (double)W[o + 1];
-  else { const int64_t q = g.face(0, 1, g.N[0], j, 0); nb += io.Q[q] / io.afac[q]; }
+  // x neighbours (i-1 = 0 and i+1 = N0 are faces x-/x+, holding Q)
+  nb += (i > 1) ? wval(g, io, i - 1, j) : qval(io.Q, io.afac, g.face(0, 0, 0, j, 0));
+  nb += (i < g.N[0] - 1) ? wval(g, io, i + 1, j) : qval(io.Q, io.afac, g.face(0, 1, g.N[0], j, 0));
   // y neighbours (faces y-/y+)
-  if (j > 1) nb += (double)W[o - g.n0];
-  else { const int64_t q = g.face(1, 0, i, 0, 0); nb += io.Q[q] / io.afac[q]; }
-  if (j < g.N[1] - 1) nb += (double)W[o + g.n0];
-  else { const int64_t q = g.face(1, 1, i, g.N[1], 0); nb += io.Q[q] / io.afac[q]; }
-  return (T)(acc + io.Mn * nb);
+  nb += (j > 1) ? wval(g, io, i, j - 1) : qval(io.Q, io.afac, g.face(1, 0, i, 0, 0));
+  nb += (j < g.N[1] - 1) ? wval(g, io, i, j + 1) : qval(io.Q, io.afac, g.face(1, 1, i, g.N[1], 0));
+  double v = acc + io.Mn * nb;
+  if (io.src2) v += (double)io.src2[g.pad(i, j, 0)];
+  return (T)v;
 }
 
 template <typename T, int LOAD, int STORE>
@@ -249,6 +256,10 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
       const int k = g.kmin + (int)(r / (g.N[1] - 1));
       if (LOAD == 0) {
         v = *reinterpret_cast<const C*>(io.src + g.pad(pos, j, k));
+        if (io.lscale != 1.0) {
+          v.x = (T)(io.lscale * (double)v.x);
+          v.y = (T)(io.lscale * (double)v.y);
+        }
         if (pos == 0) v.x = 0;
       } else {
         if (pos > 0) v.x = mstencil2d<T>(g, io, pos, j);
@@ -351,40 +362,42 @@ __global__ void __launch_bounds__(512) k_dst_gen(T* __restrict__ base, int nline
 
 // ---------------------------------------------------------------------------
 // Boundary preconditioner on 2D face lines in one pass: out = alpha *
-// DST(pre * DST(in / alpha)) per line, the line kept in shared memory.
+// DST(pre * DST(in / alpha)) per line, the line kept in shared memory in
+// precision T (FP32 is enough: GMRES is flexible, and stores P^-1 v).
 // Line l holds N-1 contiguous face values at l * lstride; in and out may alias.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(512) k_precond_lines(double* out, const double* in, const double* __restrict__ afac,
                                                        const double* __restrict__ pre, int nlines, int64_t lstride,
-                                                       int N, const double2* __restrict__ tw,
-                                                       const double* __restrict__ sn, int logN, int TPL, int LPC) {
+                                                       int N, const typename Cplx<T>::t* __restrict__ tw,
+                                                       const T* __restrict__ sn, int logN, int TPL, int LPC) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* s = reinterpret_cast<double*>(smem_raw);
-  double* wsum = s + (int64_t)LPC * N;
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* wsum = s + (int64_t)LPC * N;
   const int l0 = blockIdx.x * LPC;
   const int tot = LPC * N;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int l = e >> logN, j = e & (N - 1), line = l0 + l;
-    double v = 0.0;
+    T v = 0;
     if (j > 0 && line < nlines) {
       const int64_t q = (int64_t)line * lstride + (j - 1);
-      v = in[q] / afac[q];
+      v = (T)(in[q] / afac[q]);
     }
     s[e] = v;
   }
   __syncthreads();
-  dst_lines<double>(s, N, N, logN, TPL, tw, sn, wsum);
+  dst_lines<T>(s, N, N, logN, TPL, tw, sn, wsum);
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int l = e >> logN, j = e & (N - 1), line = l0 + l;
-    if (j > 0 && line < nlines) s[e] *= pre[(int64_t)line * lstride + (j - 1)];
+    if (j > 0 && line < nlines) s[e] = (T)((double)s[e] * pre[(int64_t)line * lstride + (j - 1)]);
   }
   __syncthreads();
-  dst_lines<double>(s, N, N, logN, TPL, tw, sn, wsum);
+  dst_lines<T>(s, N, N, logN, TPL, tw, sn, wsum);
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int l = e >> logN, j = e & (N - 1), line = l0 + l;
     if (j > 0 && line < nlines) {
       const int64_t q = (int64_t)line * lstride + (j - 1);
-      out[q] = s[e] * afac[q];
+      out[q] = (double)s[e] * afac[q];
     }
   }
 }
@@ -421,30 +434,49 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
 
 template <typename T>
 cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
-  DstIO<T> io{a, nullptr, nullptr, nullptr, 0.0, 0.0};
+  DstIO<T> io{a, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, 1.0};
   return dst_x_impl<T, 0, 0>(g, a, io, tw, sn, scale, st);
 }
+
+// dst = DST_x(lscale * src) (src may alias dst)
+template <typename T>
+cudaError_t launch_dst_x_from(const Geom& g, T* dst, const T* src, double lscale, const void* tw, const T* sn,
+                              cudaStream_t st) {
+  DstIO<T> io{src, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, lscale};
+  return dst_x_impl<T, 0, 0>(g, dst, io, tw, sn, (T)1, st);
+}
+template cudaError_t launch_dst_x_from<float>(const Geom&, float*, const float*, double, const void*, const float*,
+                                              cudaStream_t);
+template cudaError_t launch_dst_x_from<double>(const Geom&, double*, const double*, double, const void*,
+                                               const double*, cudaStream_t);
 
 // in place, storing X / alpha (the inverse transform of V, giving W = V/alpha)
 template <typename T>
 cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
                                     cudaStream_t st) {
-  DstIO<T> io{a, nullptr, nullptr, ainv, 0.0, 0.0};
+  DstIO<T> io{a, nullptr, nullptr, ainv, 0.0, 0.0, nullptr, 1.0};
   return dst_x_impl<T, 0, 1>(g, a, io, tw, sn, (T)1, st);
 }
 
 // dst = DST_x( M(W) + boundary Q/alpha terms ), 2D, src = W must not alias dst
 template <typename T>
 cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
-                               double Mn, const void* tw, const T* sn, cudaStream_t st) {
-  DstIO<T> io{W, Q, afac, nullptr, Mc, Mn};
+                               double Mn, const void* tw, const T* sn, cudaStream_t st, const T* src2,
+                               const double* ainv_load) {
+  DstIO<T> io{W, Q, afac, ainv_load, Mc, Mn, src2, 1.0};
   return dst_x_impl<T, 1, 0>(g, dst, io, tw, sn, (T)1, st);
 }
 
 template cudaError_t launch_dst_x_store_ainv<double>(const Geom&, double*, const double*, const void*, const double*,
                                                      cudaStream_t);
+template cudaError_t launch_dst_x_store_ainv<float>(const Geom&, float*, const double*, const void*, const float*,
+                                                    cudaStream_t);
 template cudaError_t launch_dst_x_mload<double>(const Geom&, double*, const double*, const double*, const double*,
-                                                double, double, const void*, const double*, cudaStream_t);
+                                                double, double, const void*, const double*, cudaStream_t,
+                                                const double*, const double*);
+template cudaError_t launch_dst_x_mload<float>(const Geom&, float*, const float*, const double*, const double*,
+                                               double, double, const void*, const float*, cudaStream_t, const float*,
+                                               const double*);
 
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
@@ -486,22 +518,28 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
 template cudaError_t launch_dst_gen<double>(double*, int, int, int64_t, int64_t, int64_t, int, const void*,
                                             const double*, cudaStream_t);
 
+template <typename T>
 cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
-                                 int64_t lstride, int N, const void* tw, const double* sn, cudaStream_t st) {
+                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st) {
   const int logN = ilog2(N);
   const int TPL = N / 8;
   const int LPC = TPL >= 512 ? 1 : 512 / TPL;
   const int threads = TPL * LPC;
   const int blocks = (nlines + LPC - 1) / LPC;
-  const size_t smem = ((size_t)LPC * N + 32) * sizeof(double);
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_precond_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_precond_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_precond_lines<<<blocks, threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,
-                                                 reinterpret_cast<const double2*>(tw), sn, logN, TPL, LPC);
+  k_precond_lines<T><<<blocks, threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,
+                                                    reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, logN, TPL,
+                                                    LPC);
   return cudaGetLastError();
 }
+template cudaError_t launch_precond_lines<float>(double*, const double*, const double*, const double*, int, int64_t,
+                                                 int, const void*, const float*, cudaStream_t);
+template cudaError_t launch_precond_lines<double>(double*, const double*, const double*, const double*, int, int64_t,
+                                                  int, const void*, const double*, cudaStream_t);
 
 template cudaError_t launch_dst_x<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
 template cudaError_t launch_dst_y<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);

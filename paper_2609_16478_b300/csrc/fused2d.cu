@@ -44,17 +44,19 @@ __global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, doubl
 
 constexpr int kRowThreads = 256;
 
+template <typename T>
 __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __restrict__ y,
-                                                           const double* __restrict__ Uh,
+                                                           const T* __restrict__ Uh,
                                                            const double* __restrict__ Q,
                                                            const double* __restrict__ afac,
-                                                           const double* __restrict__ tau) {
+                                                           const double* __restrict__ tau,
+                                                           const double* __restrict__ srcq) {
   __shared__ double red[2][kRowThreads / 32];
   const int j = blockIdx.x + 1;
   const int N0 = g.N[0];
-  const double* row = Uh + g.pad(0, j, 0);
+  const T* row = Uh + g.pad(0, j, 0);
   double acc = 0.0;  // k = 1 + tid + 256 m has the parity of 1 + tid
-  for (int k = 1 + threadIdx.x; k < N0; k += kRowThreads) acc = fma(row[k], tau[k], acc);
+  for (int k = 1 + threadIdx.x; k < N0; k += kRowThreads) acc = fma((double)row[k], tau[k], acc);
   // sum lanes of equal parity: lane 0 gets the odd-k sum, lane 1 the even-k sum
 #pragma unroll
   for (int o = 16; o >= 2; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -68,28 +70,49 @@ __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __res
       O += red[1][w];
     }
     const int64_t qm = g.face(0, 0, 0, j, 0), qp = g.face(0, 1, N0, j, 0);
-    y[qm] = afac[qm] * (E + O) - Q[qm];
-    y[qp] = afac[qp] * (E - O) - Q[qp];
+    double ym = afac[qm] * (E + O), yp = afac[qp] * (E - O);
+    if (Q) {
+      ym -= Q[qm];
+      yp -= Q[qp];
+    }
+    if (srcq) {
+      ym -= srcq[qm];
+      yp -= srcq[qp];
+    }
+    y[qm] = ym;
+    y[qp] = yp;
   }
 }
 
-__global__ void k_trace2d_ylines(Geom g, Coefs cf, double* __restrict__ R, const double* __restrict__ Uh) {
+template <typename T>
+__global__ void k_trace2d_ylines(Geom g, Coefs cf, double* __restrict__ R, const T* __restrict__ Uh) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0], N1 = g.N[1];
   if (k >= N0) return;
   const double w1 = cf.w[1][1], w2 = cf.w[1][2], w3 = cf.w[1][3];
-  R[k - 1] = w1 * Uh[g.pad(k, 1, 0)] + w2 * Uh[g.pad(k, 2, 0)] + w3 * Uh[g.pad(k, 3, 0)];
-  R[(N0 - 1) + k - 1] = w1 * Uh[g.pad(k, N1 - 1, 0)] + w2 * Uh[g.pad(k, N1 - 2, 0)] + w3 * Uh[g.pad(k, N1 - 3, 0)];
+  R[k - 1] = w1 * (double)Uh[g.pad(k, 1, 0)] + w2 * (double)Uh[g.pad(k, 2, 0)] + w3 * (double)Uh[g.pad(k, 3, 0)];
+  R[(N0 - 1) + k - 1] = w1 * (double)Uh[g.pad(k, N1 - 1, 0)] + w2 * (double)Uh[g.pad(k, N1 - 2, 0)] +
+                        w3 * (double)Uh[g.pad(k, N1 - 3, 0)];
 }
 
 __global__ void k_trace2d_y(Geom g, double* __restrict__ y, const double* __restrict__ R,
-                            const double* __restrict__ Q, const double* __restrict__ afac) {
+                            const double* __restrict__ Q, const double* __restrict__ afac,
+                            const double* __restrict__ srcq) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0];
   if (i >= N0) return;
   const int64_t qm = g.face(1, 0, i, 0, 0), qp = g.face(1, 1, i, g.N[1], 0);
-  y[qm] = afac[qm] * R[i - 1] - Q[qm];
-  y[qp] = afac[qp] * R[(N0 - 1) + i - 1] - Q[qp];
+  double ym = afac[qm] * R[i - 1], yp = afac[qp] * R[(N0 - 1) + i - 1];
+  if (Q) {
+    ym -= Q[qm];
+    yp -= Q[qp];
+  }
+  if (srcq) {
+    ym -= srcq[qm];
+    yp -= srcq[qp];
+  }
+  y[qm] = ym;
+  y[qp] = yp;
 }
 
 cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
@@ -98,19 +121,27 @@ cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, dou
   k_v2d_prep<<<(n + 255) / 256, 256, 0, st>>>(g, cf, Q, rxm, rxp, qy);
   return cudaGetLastError();
 }
-cudaError_t launch_trace2d_x(const Geom& g, double* y, const double* Uh, const double* Q, const double* afac,
-                             const double* tau, cudaStream_t st) {
-  k_trace2d_x<<<g.N[1] - 1, kRowThreads, 0, st>>>(g, y, Uh, Q, afac, tau);
+template <typename T>
+cudaError_t launch_trace2d_x(const Geom& g, double* y, const T* Uh, const double* Q, const double* afac,
+                             const double* tau, cudaStream_t st, const double* srcq) {
+  k_trace2d_x<T><<<g.N[1] - 1, kRowThreads, 0, st>>>(g, y, Uh, Q, afac, tau, srcq);
   return cudaGetLastError();
 }
-cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const double* Uh, cudaStream_t st) {
-  k_trace2d_ylines<<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, cf, R, Uh);
+template <typename T>
+cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const T* Uh, cudaStream_t st) {
+  k_trace2d_ylines<T><<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, cf, R, Uh);
   return cudaGetLastError();
 }
 cudaError_t launch_trace2d_y(const Geom& g, double* y, const double* R, const double* Q, const double* afac,
-                             cudaStream_t st) {
-  k_trace2d_y<<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, y, R, Q, afac);
+                             cudaStream_t st, const double* srcq) {
+  k_trace2d_y<<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, y, R, Q, afac, srcq);
   return cudaGetLastError();
 }
+template cudaError_t launch_trace2d_x<double>(const Geom&, double*, const double*, const double*, const double*,
+                                              const double*, cudaStream_t, const double*);
+template cudaError_t launch_trace2d_x<float>(const Geom&, double*, const float*, const double*, const double*,
+                                             const double*, cudaStream_t, const double*);
+template cudaError_t launch_trace2d_ylines<double>(const Geom&, const Coefs&, double*, const double*, cudaStream_t);
+template cudaError_t launch_trace2d_ylines<float>(const Geom&, const Coefs&, double*, const float*, cudaStream_t);
 
 }  // namespace ahoc

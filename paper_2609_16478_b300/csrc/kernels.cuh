@@ -12,9 +12,16 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
 template <typename T>
 cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
                                     cudaStream_t st);
+// dst = DST_x( M(W) + face Q/alpha terms + src2 ), 2D; W = V/alpha, or V when
+// ainv_load is given (then W = V * ainv on load); W must not alias dst
 template <typename T>
 cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
-                               double Mn, const void* tw, const T* sn, cudaStream_t st);
+                               double Mn, const void* tw, const T* sn, cudaStream_t st, const T* src2 = nullptr,
+                               const double* ainv_load = nullptr);
+// dst = DST_x(lscale * src)
+template <typename T>
+cudaError_t launch_dst_x_from(const Geom& g, T* dst, const T* src, double lscale, const void* tw, const T* sn,
+                              cudaStream_t st);
 
 // Generated right-hand side of the homogeneous v-equation in the x-spectral
 // domain (2D): d(k, j) = sin(k pi/N0) (rxm_j + (-1)^(k+1) rxp_j)
@@ -28,18 +35,22 @@ struct VGen2D {
   const double* ck;   // cos(k pi / N0), index k
   double Ly, Lxy;
 };
+// generated right-hand side; with `add` the generated terms are added to the
+// right-hand side already in a (x-spectral), otherwise they replace it
 template <typename T>
 cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                   double* scratch, int L, const VGen2D& G, cudaStream_t st);
+                                   double* scratch, int L, const VGen2D& G, cudaStream_t st, bool add = false);
 
 // fused 2D matvec helpers (fused2d.cu)
 cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
                             cudaStream_t st);
-cudaError_t launch_trace2d_x(const Geom& g, double* y, const double* Uh, const double* Q, const double* afac,
-                             const double* tau, cudaStream_t st);
-cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const double* Uh, cudaStream_t st);
+template <typename T>
+cudaError_t launch_trace2d_x(const Geom& g, double* y, const T* Uh, const double* Q, const double* afac,
+                             const double* tau, cudaStream_t st, const double* srcq = nullptr);
+template <typename T>
+cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const T* Uh, cudaStream_t st);
 cudaError_t launch_trace2d_y(const Geom& g, double* y, const double* R, const double* Q, const double* afac,
-                             cudaStream_t st);
+                             cudaStream_t st, const double* srcq = nullptr);
 
 // DST-I of generic strided lines (see dst.cu, k_dst_gen)
 template <typename T>
@@ -47,8 +58,9 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
                            const void* tw, const T* sn, cudaStream_t st);
 
 // Boundary preconditioner on 2D face lines, one pass (dst.cu)
+template <typename T>
 cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
-                                 int64_t lstride, int N, const void* tw, const double* sn, cudaStream_t st);
+                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st);
 
 // Boundary preconditioner (precond.cu)
 struct SymAxis {

@@ -239,7 +239,7 @@ struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
       tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau,
       // mixed precision (AHOC_MIXED only)
-      F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, total;
+      F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -295,6 +295,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.r = take(face);
   L.tmp = take(face);
   L.Kry = take(face * (size_t)(o.restart + 1));
+  L.Zb = take(face * (size_t)o.restart);
   L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
   L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
   const bool mixed = (o.prec == AHOC_MIXED);
@@ -305,9 +306,9 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.Rv = take(ffl);
   L.U64 = take(mixed ? fld : 0);
   L.V64 = take(mixed ? fld : 0);
-  for (int a = 0; a < 3; ++a) {
-    L.twf[a] = take(mixed ? 2 * (size_t)g.N[a] * sizeof(float) : 0);
-    L.snf[a] = take(mixed ? ((size_t)g.N[a] / 2 + 1) * sizeof(float) : 0);
+  for (int a = 0; a < 3; ++a) {  // FP32 DST tables: mixed inner solves and the preconditioner
+    L.twf[a] = take(2 * (size_t)g.N[a] * sizeof(float));
+    L.snf[a] = take(((size_t)g.N[a] / 2 + 1) * sizeof(float));
   }
   L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
   L.trif = take(0);  // the chunked solve's carries are FP64 in both precisions (shared scratch L.tri)
@@ -371,6 +372,7 @@ struct ahoc_plan {
   float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
   double *U64 = nullptr, *V64 = nullptr, *Rq = nullptr, *dQ = nullptr, *b2 = nullptr;
+  double* Zb = nullptr;  // flexible GMRES: the preconditioned directions z_j = P^-1 v_j
   Mode<float>* modesf = nullptr;
   int refine_steps = 0;
   double* hhost = nullptr;  // pinned
@@ -490,35 +492,67 @@ ahoc_status solve_VU_f(ahoc_plan* p, const double* Q, const float* srcv, const f
   return AHOC_OK;
 }
 
-// SchurMatVec in 2D without full-field right-hand sides or inverse transforms:
-// V-hat from the generated spectrum (tri), W = V/alpha by one inverse DST,
-// G-hat = DST(M(W) + face terms) by one forward DST, U-hat by tri, then the
-// traces from U-hat directly.
-ahoc_status matvec_fused2d(ahoc_plan* p, const double* q, double* y) {
+// The fused 2D solves (DST-I along x, exact tridiagonal solve along y) in
+// precision T, with the v-equation right-hand side generated in x-modes from
+// q and the traces taken from U-hat without a full inverse transform:
+//   q      face values: the v-equation boundary data and M's face terms (may be NULL)
+//   srcv   r_v field (FP32 correction solves; NULL in the Schur action)
+//   srcu   r_u field added to the u-equation right-hand side (may be NULL)
+//   srcq   r_q face array subtracted from the trace (may be NULL)
+//   recover == false: y = alpha delta_nn U - q - srcq (SchurMatVec, Algorithm 1)
+//   recover == true:  W1 <- V, W2 <- U, both physical (the recovery step)
+template <typename T>
+ahoc_status fused2d(ahoc_plan* p, T* W1, T* W2, const Mode<T>* modes, const void* twx, const T* snx,
+                    const double* q, const T* srcv, const T* srcu, const double* srcq, double* y, bool recover) {
   const Geom& g = p->g;
   const Coefs& cf = p->cf;
   const int N0 = g.N[0];
-  RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
-  RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
+  const int L = tri_chunk_len(g);
   VGen2D G{p->rxm, p->rxp, p->qy, p->qy + (N0 - 1), p->stab[0], p->ctab[0], cf.L[16], cf.L[17]};
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<double>(g, p->W1, p->modes, p->modes, p->tri, tri_chunk_len(g), G, p->st));
-  RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<double>(g, p->W1, p->ainv, p->twx, p->snx, p->st));
-  RUN(AHOC_K_DST_X, launch_dst_x_mload<double>(g, p->W2, p->W1, q, p->afac, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, p->W2, p->modes, p->modes, p->tri, tri_chunk_len(g), p->st));
-  RUN(AHOC_K_TRACE, launch_trace2d_x(g, y, p->W2, q, p->afac, p->tau, p->st));
-  RUN(AHOC_K_TRACE, launch_trace2d_ylines(g, cf, p->R2, p->W2, p->st));
+  if (q) {
+    RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
+    RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
+  }
+  // V-hat: L_h V = -r_v - L_bdry(q) in x-modes
+  if (srcv) {
+    RUN(AHOC_K_DST_X, launch_dst_x_from<T>(g, W1, srcv, -1.0, twx, snx, p->st));
+    if (q) RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, W1, modes, p->modes, p->tri, L, G, p->st, true));
+    else RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, W1, modes, p->modes, p->tri, L, p->st));
+  } else {
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, W1, modes, p->modes, p->tri, L, G, p->st, false));
+  }
+  // U-hat: L_h U = M(V/alpha) + face terms + r_u, by one forward DST of the fused right-hand side
+  if (!recover) {
+    RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<T>(g, W1, p->ainv, twx, snx, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, W2, W1, q, p->afac, cf.Mc, cf.Mn, twx, snx, p->st, srcu, nullptr));
+  } else {
+    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, W1, twx, snx, (T)1, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, W2, W1, q, p->afac, cf.Mc, cf.Mn, twx, snx, p->st, srcu, p->ainv));
+  }
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, W2, modes, p->modes, p->tri, L, p->st));
+  if (recover) {
+    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, W2, twx, snx, (T)1, p->st));
+    return AHOC_OK;
+  }
+  RUN(AHOC_K_TRACE, launch_trace2d_x<T>(g, y, W2, q, p->afac, p->tau, p->st, srcq));
+  RUN(AHOC_K_TRACE, launch_trace2d_ylines<T>(g, cf, p->R2, W2, p->st));
   RUN(AHOC_K_TRACE, launch_dst_gen<double>(p->R2, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
-  RUN(AHOC_K_TRACE, launch_trace2d_y(g, y, p->R2, q, p->afac, p->st));
+  RUN(AHOC_K_TRACE, launch_trace2d_y(g, y, p->R2, q, p->afac, p->st, srcq));
   return AHOC_OK;
 }
 
+bool fused_ok(const Geom& g) { return g.dim == 2 && tri_ncols(g) < kChunkedBelow; }
+
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
   if (p->o.prec == AHOC_MIXED) {
+    if (fused_ok(p->g))
+      return fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], q, nullptr, nullptr, nullptr, y, false);
     CKS(solve_VU_f(p, q, nullptr, nullptr));
     RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
     return AHOC_OK;
   }
-  if (p->g.dim == 2 && tri_ncols(p->g) < kChunkedBelow) return matvec_fused2d(p, q, y);
+  if (fused_ok(p->g))
+    return fused2d<double>(p, p->W1, p->W2, p->modes, p->twx, p->snx, q, nullptr, nullptr, nullptr, y, false);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -557,10 +591,10 @@ ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
     // x-faces are lines of N1 - 1 points (DST length N1), y-faces of N0 - 1
     const Geom& g = p->g;
     const int64_t ox = g.face_off[0], oy = g.face_off[2];
-    RUN(AHOC_K_KRYLOV, launch_precond_lines(out + ox, in + ox, p->afac + ox, p->pre + ox, 2, g.N[1] - 1, g.N[1],
-                                            p->twy, p->sny, p->st));
-    RUN(AHOC_K_KRYLOV, launch_precond_lines(out + oy, in + oy, p->afac + oy, p->pre + oy, 2, g.N[0] - 1, g.N[0],
-                                            p->twx, p->snx, p->st));
+    RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + ox, in + ox, p->afac + ox, p->pre + ox, 2, g.N[1] - 1,
+                                                   g.N[1], p->twf[1], p->snf[1], p->st));
+    RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + oy, in + oy, p->afac + oy, p->pre + oy, 2, g.N[0] - 1,
+                                                   g.N[0], p->twf[0], p->snf[0], p->st));
     return AHOC_OK;
   }
   RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, in, nullptr, p->afac, n, p->st));
@@ -698,6 +732,10 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->qy = at<double>(p, L.qy);
   p->R2 = at<double>(p, L.R2);
   p->tau = at<double>(p, L.tau);
+  for (int a = 0; a < 3; ++a) {
+    p->twf[a] = at<float>(p, L.twf[a]);
+    p->snf[a] = at<float>(p, L.snf[a]);
+  }
   if (o.prec == AHOC_MIXED) {
     p->F1 = at<float>(p, L.F1);
     p->F2 = at<float>(p, L.F2);
@@ -705,10 +743,6 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     p->Rv = at<float>(p, L.Rv);
     p->U64 = at<double>(p, L.U64);
     p->V64 = at<double>(p, L.V64);
-    for (int a = 0; a < 3; ++a) {
-      p->twf[a] = at<float>(p, L.twf[a]);
-      p->snf[a] = at<float>(p, L.snf[a]);
-    }
     p->modesf = at<Mode<float>>(p, L.modesf);
     p->trif = at<float>(p, L.trif);
     p->Rq = at<double>(p, L.Rq);
@@ -721,6 +755,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->r = at<double>(p, L.r);
   p->tmp = at<double>(p, L.tmp);
   p->Kry = at<double>(p, L.Kry);
+  p->Zb = at<double>(p, L.Zb);
   p->partial = at<double>(p, L.partial);
   p->hdev = at<double>(p, L.hdev);
   const size_t fld = (size_t)g.npad * sizeof(double);
@@ -754,13 +789,13 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     CKC(cudaMemsetAsync(p->F2, 0, ffl, p->st));
     CKC(cudaMemcpyAsync(p->modesf, modesf.data(), modesf.size() * sizeof(Mode<float>), cudaMemcpyHostToDevice,
                         p->st));
-    for (int a = 0; a < g.dim; ++a) {
-      dst_tables(g.N[a], tw, sn);
-      std::vector<float> twf(tw.begin(), tw.end()), snf(sn.begin(), sn.end());
-      CKC(cudaMemcpyAsync(p->twf[a], twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
-      CKC(cudaMemcpyAsync(p->snf[a], snf.data(), snf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
-      CKC(cudaStreamSynchronize(p->st));
-    }
+  }
+  for (int a = 0; a < g.dim; ++a) {
+    dst_tables(g.N[a], tw, sn);
+    std::vector<float> twf(tw.begin(), tw.end()), snf(sn.begin(), sn.end());
+    CKC(cudaMemcpyAsync(p->twf[a], twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaMemcpyAsync(p->snf[a], snf.data(), snf.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaStreamSynchronize(p->st));
   }
   if (g.dim == 3) {
     dst_tables(g.N[2], tw, sn);
@@ -938,9 +973,10 @@ struct GmresOut {
   ahoc_status status = AHOC_OK;
 };
 
-// GMRES on S X = b (right-preconditioned with the boundary-symbol operator,
-// CGS2 Arnoldi on the device, Givens rotations and the least-squares solve
-// on the host in FP64).  X holds the initial guess on entry when `guess`
+// Flexible GMRES on S X = b (right-preconditioned with the boundary-symbol
+// operator, whose inexact FP32 application is absorbed by storing the
+// directions z_j = P^-1 v_j; CGS2 Arnoldi on the device, Givens rotations and
+// the least-squares solve on the host in FP64).  X holds the initial guess on entry when `guess`
 // (else it is zeroed) and the iterate on exit; tol is relative to beta0 =
 // ||b||.  Restarts (an explicit residual) only when the basis is full.
 ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool guess, double tol, int max_iters,
@@ -977,8 +1013,9 @@ ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool g
     for (int j = 0; j < m; ++j) {
       double* w = V + (int64_t)(j + 1) * n;
       CK(cudaEventRecord(p->ev0, p->st));
-      CKS(precond_apply(p, V + (int64_t)j * n, p->z));
-      CKS(matvec_dev(p, p->z, w));
+      double* zj = p->Zb + (int64_t)j * n;
+      CKS(precond_apply(p, V + (int64_t)j * n, zj));
+      CKS(matvec_dev(p, zj, w));
       CK(cudaEventRecord(p->ev1, p->st));
       // CGS2
       double* h1 = p->hdev;
@@ -1018,7 +1055,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool g
       }
       RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 1.0 / hn, 0.0, n, p->st));
     }
-    // y = H^-1 g (upper triangular), X += P^-1 (V y)
+    // y = H^-1 g (upper triangular), X += Z y
     for (int i = jend - 1; i >= 0; --i) {
       double sacc = gv[i];
       for (int k = i + 1; k < jend; ++k) sacc -= H[(size_t)k * (m + 1) + i] * y[k];
@@ -1026,10 +1063,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool g
     }
     for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
     CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    CK(cudaMemsetAsync(p->tmp, 0, n * sizeof(double), p->st));
-    RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, jend, p->hdev, p->tmp, n, p->st));
-    CKS(precond_apply(p, p->tmp, p->z));
-    RUN(AHOC_K_KRYLOV, launch_axpby(X, p->z, 1.0, 1.0, n, p->st));
+    RUN(AHOC_K_KRYLOV, launch_gemv_sub(p->Zb, n, jend, p->hdev, X, n, p->st));
     CK(cudaStreamSynchronize(p->st));
     CKS(harvest(p));
     if (done) break;
@@ -1127,9 +1161,14 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
          launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->gD, p->vedge, p->gN, p->lapt,
                          p->ainv, p->afac, p->st));
     // correction right-hand side b = -R_d(0)
-    CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
-    RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
-                                          p->st, p->Rq));
+    if (fused_ok(g)) {
+      CKS(fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], nullptr, p->Rv, p->Ru, p->Rq, p->b2,
+                         false));
+    } else {
+      CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
+      RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
+                                            p->st, p->Rq));
+    }
     RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st));
     double bn = 0.0;
     CKS(norm2(p, p->b2, &bn));
@@ -1150,7 +1189,11 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
     go->restarts += gi.restarts;
     go->ms_mv += gi.ms_mv;
     // recovery of the correction and the FP64 update
-    CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
+    if (fused_ok(g))
+      CKS(fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], p->dQ, p->Rv, p->Ru, nullptr, nullptr,
+                         true));
+    else
+      CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
     RUN(AHOC_K_OTHER, launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->st));
     RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->dQ, 1.0, 1.0, n, p->st));
     ++p->refine_steps;

@@ -153,7 +153,15 @@ __device__ __forceinline__ double vgen(const VGen2D& G, int k, int j, int Nt) {
   return v;
 }
 
-template <typename T, int L, bool GEN>
+// right-hand side element: GEN 0 loaded, 1 generated, 2 loaded + generated
+template <typename T, int GEN>
+__device__ __forceinline__ T rhs_elem(const T* col, const VGen2D& G, int k, int j, const TriShape& sh) {
+  if (GEN == 0) return col[(int64_t)j * sh.stride];
+  if (GEN == 1) return (T)vgen(G, k, j, sh.Nt);
+  return (T)((double)col[(int64_t)j * sh.stride] + vgen(G, k, j, sh.Nt));
+}
+
+template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
                                                 double* __restrict__ E, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
-    d[q] = (q < len) ? (GEN ? (T)vgen(G, (int)m + 1, s0 + q, sh.Nt) : col[(int64_t)(s0 + q) * sh.stride]) : (T)0;
+    d[q] = (q < len) ? rhs_elem<T, GEN>(col, G, (int)m + 1, s0 + q, sh) : (T)0;
   T w = 0;
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -203,7 +211,7 @@ __global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const 
   }
 }
 
-template <typename T, int L, bool GEN>
+template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
                                                 const double* __restrict__ carry, double* __restrict__ B, VGen2D G) {
   const TriShape sh = tri_shape(g, L);
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
-    d[q] = (q < len) ? (GEN ? (T)vgen(G, (int)m + 1, s0 + q, sh.Nt) : col[(int64_t)(s0 + q) * sh.stride]) : (T)0;
+    d[q] = (q < len) ? rhs_elem<T, GEN>(col, G, (int)m + 1, s0 + q, sh) : (T)0;
   T w = (T)carry[(int64_t)c * sh.ncols + m];
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -321,7 +329,7 @@ size_t tri_chunked_scratch(const Geom& g, int L) {
   return (size_t)(4 * C + 1) * ncols;  // doubles (the carries are FP64 for every T)
 }
 
-template <typename T, int L, bool GEN>
+template <typename T, int L, int GEN>
 static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
                                  double* scratch, const VGen2D& G, cudaStream_t st) {
   const int nx = g.N[0] - 1;
@@ -348,24 +356,26 @@ template <typename T>
 cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64, double* scratch,
                                int L, cudaStream_t st) {
   VGen2D G{};
-  if (L == 32) return tri_chunked_L<T, 32, false>(g, a, modes, md64, scratch, G, st);
-  if (L == 16) return tri_chunked_L<T, 16, false>(g, a, modes, md64, scratch, G, st);
+  if (L == 32) return tri_chunked_L<T, 32, 0>(g, a, modes, md64, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, 0>(g, a, modes, md64, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 
 // the same solve with the v-equation right-hand side generated on the fly (2D)
 template <typename T>
 cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                   double* scratch, int L, const VGen2D& G, cudaStream_t st) {
+                                   double* scratch, int L, const VGen2D& G, cudaStream_t st, bool add) {
   if (g.dim != 2) return cudaErrorInvalidValue;
-  if (L == 32) return tri_chunked_L<T, 32, true>(g, a, modes, md64, scratch, G, st);
-  if (L == 16) return tri_chunked_L<T, 16, true>(g, a, modes, md64, scratch, G, st);
+  if (L == 32) return add ? tri_chunked_L<T, 32, 2>(g, a, modes, md64, scratch, G, st)
+                          : tri_chunked_L<T, 32, 1>(g, a, modes, md64, scratch, G, st);
+  if (L == 16) return add ? tri_chunked_L<T, 16, 2>(g, a, modes, md64, scratch, G, st)
+                          : tri_chunked_L<T, 16, 1>(g, a, modes, md64, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
-                                                    double*, int, const VGen2D&, cudaStream_t);
+                                                    double*, int, const VGen2D&, cudaStream_t, bool);
 template cudaError_t launch_tri_chunked_gen<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*,
-                                                   double*, int, const VGen2D&, cudaStream_t);
+                                                   double*, int, const VGen2D&, cudaStream_t, bool);
 
 template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
                                                 double*, int, cudaStream_t);
