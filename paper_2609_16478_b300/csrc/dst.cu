@@ -200,36 +200,38 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
 template <typename T>
 struct DstIO {
   const T* src;
-  const double* Q;      // LOAD 1: face values
-  const double* afac;   // LOAD 1: alpha at face points
-  const double* ainv;   // STORE 1: 1/alpha on the full grid; LOAD 1: if set, src holds V, not V/alpha
-  double Mc, Mn;        // LOAD 1: weighting M
+  const T* qa;          // LOAD 1: Q / alpha at the face points (precision T; may be NULL)
+  const T* ainv;        // STORE 1: 1/alpha on the full grid; LOAD 1: if set, src holds V, not V/alpha
+  T Mc, Mn;             // LOAD 1: weighting M
   const T* src2;        // LOAD 1: a source field added to M(W) (may be NULL)
-  double lscale;        // LOAD 0: factor applied on load
+  T lscale;             // LOAD 0: factor applied on load
 };
 
+// All arithmetic of the fused loads and stores is in T: on this GPU a single
+// FP64 operation per element would bound an FP32 pass by the FP64 pipe.
 template <typename T>
-__device__ __forceinline__ double wval(const Geom& g, const DstIO<T>& io, int i, int j) {
-  const double v = (double)io.src[g.pad(i, j, 0)];
+__device__ __forceinline__ T wval(const Geom& g, const DstIO<T>& io, int i, int j) {
+  const T v = io.src[g.pad(i, j, 0)];
   return io.ainv ? v * io.ainv[g.full(i, j, 0)] : v;
 }
-__device__ __forceinline__ double qval(const double* Q, const double* afac, int64_t q) {
-  return Q ? Q[q] / afac[q] : 0.0;
+template <typename T>
+__device__ __forceinline__ T qval(const DstIO<T>& io, int64_t q) {
+  return io.qa ? io.qa[q] : (T)0;
 }
 
 template <typename T>
 __device__ __forceinline__ T mstencil2d(const Geom& g, const DstIO<T>& io, int i, int j) {
-  double acc = io.Mc * wval(g, io, i, j);
-  double nb = 0.0;
+  const T acc = io.Mc * wval(g, io, i, j);
+  T nb = 0;
   // x neighbours (i-1 = 0 and i+1 = N0 are faces x-/x+, holding Q)
-  nb += (i > 1) ? wval(g, io, i - 1, j) : qval(io.Q, io.afac, g.face(0, 0, 0, j, 0));
-  nb += (i < g.N[0] - 1) ? wval(g, io, i + 1, j) : qval(io.Q, io.afac, g.face(0, 1, g.N[0], j, 0));
+  nb += (i > 1) ? wval(g, io, i - 1, j) : qval(io, g.face(0, 0, 0, j, 0));
+  nb += (i < g.N[0] - 1) ? wval(g, io, i + 1, j) : qval(io, g.face(0, 1, g.N[0], j, 0));
   // y neighbours (faces y-/y+)
-  nb += (j > 1) ? wval(g, io, i, j - 1) : qval(io.Q, io.afac, g.face(1, 0, i, 0, 0));
-  nb += (j < g.N[1] - 1) ? wval(g, io, i, j + 1) : qval(io.Q, io.afac, g.face(1, 1, i, g.N[1], 0));
-  double v = acc + io.Mn * nb;
-  if (io.src2) v += (double)io.src2[g.pad(i, j, 0)];
-  return (T)v;
+  nb += (j > 1) ? wval(g, io, i, j - 1) : qval(io, g.face(1, 0, i, 0, 0));
+  nb += (j < g.N[1] - 1) ? wval(g, io, i, j + 1) : qval(io, g.face(1, 1, i, g.N[1], 0));
+  T v = acc + io.Mn * nb;
+  if (io.src2) v += io.src2[g.pad(i, j, 0)];
+  return v;
 }
 
 template <typename T, int LOAD, int STORE>
@@ -239,29 +241,43 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   T* wsum = s + (int64_t)LPC * g.n0;
+  // per-line row data, computed once (no per-element division)
+  int64_t* rbase = reinterpret_cast<int64_t*>(wsum + 32);
+  int64_t* fbase = rbase + LPC;
+  int* rj = reinterpret_cast<int*>(fbase + LPC);
   const int N = (int)g.n0;
-  const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
-  const int64_t r0 = (int64_t)blockIdx.x * LPC;
+  const int nj = g.N[1] - 1;
+  const int nrows = nj * (g.kmax - g.kmin);
+  const int r0 = blockIdx.x * LPC;
+  for (int l = threadIdx.x; l < LPC; l += blockDim.x) {
+    const int r = r0 + l;
+    if (r < nrows) {
+      const int j = 1 + r % nj, k = g.kmin + r / nj;
+      rbase[l] = g.pad(0, j, k);
+      fbase[l] = g.full(0, j, k);
+      rj[l] = j;
+    } else {
+      rbase[l] = -1;
+    }
+  }
+  __syncthreads();
   using C = typename Cplx<T>::t;
   const int tot2 = (LPC * N) >> 1;
   for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
     const int l = (2 * e) >> logN;
     const int pos = (2 * e) & (N - 1);
-    const int64_t r = r0 + l;
+    const int64_t rb = rbase[l];
     C v;
     v.x = 0;
     v.y = 0;
-    if (r < nrows) {
-      const int j = 1 + (int)(r % (g.N[1] - 1));
-      const int k = g.kmin + (int)(r / (g.N[1] - 1));
+    if (rb >= 0) {
       if (LOAD == 0) {
-        v = *reinterpret_cast<const C*>(io.src + g.pad(pos, j, k));
-        if (io.lscale != 1.0) {
-          v.x = (T)(io.lscale * (double)v.x);
-          v.y = (T)(io.lscale * (double)v.y);
-        }
+        v = *reinterpret_cast<const C*>(io.src + rb + pos);
+        v.x *= io.lscale;
+        v.y *= io.lscale;
         if (pos == 0) v.x = 0;
       } else {
+        const int j = rj[l];
         if (pos > 0) v.x = mstencil2d<T>(g, io, pos, j);
         v.y = mstencil2d<T>(g, io, pos + 1, j);
       }
@@ -273,21 +289,19 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
   for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
     const int l = (2 * e) >> logN;
     const int pos = (2 * e) & (N - 1);
-    const int64_t r = r0 + l;
-    if (r < nrows) {
-      const int j = 1 + (int)(r % (g.N[1] - 1));
-      const int k = g.kmin + (int)(r / (g.N[1] - 1));
+    const int64_t rb = rbase[l];
+    if (rb >= 0) {
       C v = *reinterpret_cast<const C*>(s + l * N + pos);
       if (STORE == 0) {
         v.x *= scale;
         v.y *= scale;
       } else {
-        const int64_t f = g.full(pos, j, k);
-        v.x = (pos == 0) ? (T)0 : (T)((double)v.x * io.ainv[f]);
-        v.y = (T)((double)v.y * io.ainv[f + 1]);
+        const int64_t f = fbase[l] + pos;
+        v.x *= io.ainv[f];
+        v.y *= io.ainv[f + 1];
       }
       if (pos == 0) v.x = 0;
-      *reinterpret_cast<C*>(a + g.pad(pos, j, k)) = v;
+      *reinterpret_cast<C*>(a + rb + pos) = v;
     }
   }
 }
@@ -421,7 +435,7 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
   const int threads = TPL * LPC;
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
   const int64_t blocks = (nrows + LPC - 1) / LPC;
-  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T);
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T) + (size_t)LPC * (2 * sizeof(int64_t) + sizeof(int));
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_dst_x<T, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -434,7 +448,7 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
 
 template <typename T>
 cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
-  DstIO<T> io{a, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, 1.0};
+  DstIO<T> io{a, nullptr, nullptr, (T)0, (T)0, nullptr, (T)1};
   return dst_x_impl<T, 0, 0>(g, a, io, tw, sn, scale, st);
 }
 
@@ -442,7 +456,7 @@ cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T sca
 template <typename T>
 cudaError_t launch_dst_x_from(const Geom& g, T* dst, const T* src, double lscale, const void* tw, const T* sn,
                               cudaStream_t st) {
-  DstIO<T> io{src, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, lscale};
+  DstIO<T> io{src, nullptr, nullptr, (T)0, (T)0, nullptr, (T)lscale};
   return dst_x_impl<T, 0, 0>(g, dst, io, tw, sn, (T)1, st);
 }
 template cudaError_t launch_dst_x_from<float>(const Geom&, float*, const float*, double, const void*, const float*,
@@ -450,33 +464,32 @@ template cudaError_t launch_dst_x_from<float>(const Geom&, float*, const float*,
 template cudaError_t launch_dst_x_from<double>(const Geom&, double*, const double*, double, const void*,
                                                const double*, cudaStream_t);
 
-// in place, storing X / alpha (the inverse transform of V, giving W = V/alpha)
+// in place, storing X / alpha (the inverse transform of V, giving W = V/alpha);
+// ainv: 1/alpha on the full grid in precision T
 template <typename T>
-cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
+cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const T* ainv, const void* tw, const T* sn,
                                     cudaStream_t st) {
-  DstIO<T> io{a, nullptr, nullptr, ainv, 0.0, 0.0, nullptr, 1.0};
+  DstIO<T> io{a, nullptr, ainv, (T)0, (T)0, nullptr, (T)1};
   return dst_x_impl<T, 0, 1>(g, a, io, tw, sn, (T)1, st);
 }
 
-// dst = DST_x( M(W) + boundary Q/alpha terms ), 2D, src = W must not alias dst
+// dst = DST_x( M(W) + qa terms at the faces + src2 ), 2D, src = W must not alias dst
 template <typename T>
-cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
-                               double Mn, const void* tw, const T* sn, cudaStream_t st, const T* src2,
-                               const double* ainv_load) {
-  DstIO<T> io{W, Q, afac, ainv_load, Mc, Mn, src2, 1.0};
+cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const T* qa, T Mc, T Mn, const void* tw,
+                               const T* sn, cudaStream_t st, const T* src2, const T* ainv_load) {
+  DstIO<T> io{W, qa, ainv_load, Mc, Mn, src2, (T)1};
   return dst_x_impl<T, 1, 0>(g, dst, io, tw, sn, (T)1, st);
 }
 
 template cudaError_t launch_dst_x_store_ainv<double>(const Geom&, double*, const double*, const void*, const double*,
                                                      cudaStream_t);
-template cudaError_t launch_dst_x_store_ainv<float>(const Geom&, float*, const double*, const void*, const float*,
+template cudaError_t launch_dst_x_store_ainv<float>(const Geom&, float*, const float*, const void*, const float*,
                                                     cudaStream_t);
-template cudaError_t launch_dst_x_mload<double>(const Geom&, double*, const double*, const double*, const double*,
-                                                double, double, const void*, const double*, cudaStream_t,
-                                                const double*, const double*);
-template cudaError_t launch_dst_x_mload<float>(const Geom&, float*, const float*, const double*, const double*,
-                                               double, double, const void*, const float*, cudaStream_t, const float*,
-                                               const double*);
+template cudaError_t launch_dst_x_mload<double>(const Geom&, double*, const double*, const double*, double, double,
+                                                const void*, const double*, cudaStream_t, const double*,
+                                                const double*);
+template cudaError_t launch_dst_x_mload<float>(const Geom&, float*, const float*, const float*, float, float,
+                                               const void*, const float*, cudaStream_t, const float*, const float*);
 
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st) {
@@ -517,6 +530,8 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
 }
 template cudaError_t launch_dst_gen<double>(double*, int, int, int64_t, int64_t, int64_t, int, const void*,
                                             const double*, cudaStream_t);
+template cudaError_t launch_dst_gen<float>(float*, int, int, int64_t, int64_t, int64_t, int, const void*, const float*,
+                                           cudaStream_t);
 
 template <typename T>
 cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,

@@ -17,10 +17,12 @@
 
 namespace ahoc {
 
-__global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, double* __restrict__ rxm,
-                           double* __restrict__ rxp, double* __restrict__ qy) {
+template <typename T>
+__global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, const double* __restrict__ afinv,
+                           T* __restrict__ rxm, T* __restrict__ rxp, T* __restrict__ qy, T* __restrict__ qa) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N0 = g.N[0], N1 = g.N[1];
+  if (t < g.ngamma) qa[t] = (T)(Q[t] * afinv[t]);
   if (t <= N1) {
     const int j = t;
     double am = 0.0, ap = 0.0;
@@ -35,11 +37,11 @@ __global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, doubl
       }
     }
     if (j < N1) {
-      rxm[j] = am;
-      rxp[j] = ap;
+      rxm[j] = (T)am;
+      rxp[j] = (T)ap;
     }
   }
-  if (t < 2 * (N0 - 1)) qy[t] = Q[g.face_off[2] + t];
+  if (t < 2 * (N0 - 1)) qy[t] = (T)Q[g.face_off[2] + t];
 }
 
 constexpr int kRowThreads = 256;
@@ -49,14 +51,15 @@ __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __res
                                                            const T* __restrict__ Uh,
                                                            const double* __restrict__ Q,
                                                            const double* __restrict__ afac,
-                                                           const double* __restrict__ tau,
+                                                           const T* __restrict__ tau,
                                                            const double* __restrict__ srcq) {
   __shared__ double red[2][kRowThreads / 32];
   const int j = blockIdx.x + 1;
   const int N0 = g.N[0];
   const T* row = Uh + g.pad(0, j, 0);
-  double acc = 0.0;  // k = 1 + tid + 256 m has the parity of 1 + tid
-  for (int k = 1 + threadIdx.x; k < N0; k += kRowThreads) acc = fma((double)row[k], tau[k], acc);
+  T part = 0;  // k = 1 + tid + 256 m has the parity of 1 + tid; at most N0/256 terms in T
+  for (int k = 1 + threadIdx.x; k < N0; k += kRowThreads) part += row[k] * tau[k];
+  double acc = (double)part;
   // sum lanes of equal parity: lane 0 gets the odd-k sum, lane 1 the even-k sum
 #pragma unroll
   for (int o = 16; o >= 2; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -85,24 +88,24 @@ __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __res
 }
 
 template <typename T>
-__global__ void k_trace2d_ylines(Geom g, Coefs cf, double* __restrict__ R, const T* __restrict__ Uh) {
+__global__ void k_trace2d_ylines(Geom g, Coefs cf, T* __restrict__ R, const T* __restrict__ Uh) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0], N1 = g.N[1];
   if (k >= N0) return;
-  const double w1 = cf.w[1][1], w2 = cf.w[1][2], w3 = cf.w[1][3];
-  R[k - 1] = w1 * (double)Uh[g.pad(k, 1, 0)] + w2 * (double)Uh[g.pad(k, 2, 0)] + w3 * (double)Uh[g.pad(k, 3, 0)];
-  R[(N0 - 1) + k - 1] = w1 * (double)Uh[g.pad(k, N1 - 1, 0)] + w2 * (double)Uh[g.pad(k, N1 - 2, 0)] +
-                        w3 * (double)Uh[g.pad(k, N1 - 3, 0)];
+  const T w1 = (T)cf.w[1][1], w2 = (T)cf.w[1][2], w3 = (T)cf.w[1][3];
+  R[k - 1] = w1 * Uh[g.pad(k, 1, 0)] + w2 * Uh[g.pad(k, 2, 0)] + w3 * Uh[g.pad(k, 3, 0)];
+  R[(N0 - 1) + k - 1] = w1 * Uh[g.pad(k, N1 - 1, 0)] + w2 * Uh[g.pad(k, N1 - 2, 0)] + w3 * Uh[g.pad(k, N1 - 3, 0)];
 }
 
-__global__ void k_trace2d_y(Geom g, double* __restrict__ y, const double* __restrict__ R,
+template <typename T>
+__global__ void k_trace2d_y(Geom g, double* __restrict__ y, const T* __restrict__ R,
                             const double* __restrict__ Q, const double* __restrict__ afac,
                             const double* __restrict__ srcq) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0];
   if (i >= N0) return;
   const int64_t qm = g.face(1, 0, i, 0, 0), qp = g.face(1, 1, i, g.N[1], 0);
-  double ym = afac[qm] * R[i - 1], yp = afac[qp] * R[(N0 - 1) + i - 1];
+  double ym = afac[qm] * (double)R[i - 1], yp = afac[qp] * (double)R[(N0 - 1) + i - 1];
   if (Q) {
     ym -= Q[qm];
     yp -= Q[qp];
@@ -115,33 +118,51 @@ __global__ void k_trace2d_y(Geom g, double* __restrict__ y, const double* __rest
   y[qp] = yp;
 }
 
-cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
-                            cudaStream_t st) {
-  const int n = (g.N[1] + 1 > 2 * (g.N[0] - 1)) ? g.N[1] + 1 : 2 * (g.N[0] - 1);
-  k_v2d_prep<<<(n + 255) / 256, 256, 0, st>>>(g, cf, Q, rxm, rxp, qy);
+template <typename T>
+cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, const double* afinv, T* rxm, T* rxp,
+                            T* qy, T* qa, cudaStream_t st) {
+  int64_t n = (g.N[1] + 1 > 2 * (g.N[0] - 1)) ? g.N[1] + 1 : 2 * (g.N[0] - 1);
+  if (g.ngamma > n) n = g.ngamma;
+  k_v2d_prep<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, cf, Q, afinv, rxm, rxp, qy, qa);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_trace2d_x(const Geom& g, double* y, const T* Uh, const double* Q, const double* afac,
-                             const double* tau, cudaStream_t st, const double* srcq) {
+                             const T* tau, cudaStream_t st, const double* srcq) {
   k_trace2d_x<T><<<g.N[1] - 1, kRowThreads, 0, st>>>(g, y, Uh, Q, afac, tau, srcq);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const T* Uh, cudaStream_t st) {
+cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, T* R, const T* Uh, cudaStream_t st) {
   k_trace2d_ylines<T><<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, cf, R, Uh);
   return cudaGetLastError();
 }
-cudaError_t launch_trace2d_y(const Geom& g, double* y, const double* R, const double* Q, const double* afac,
+template <typename T>
+cudaError_t launch_trace2d_y(const Geom& g, double* y, const T* R, const double* Q, const double* afac,
                              cudaStream_t st, const double* srcq) {
-  k_trace2d_y<<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, y, R, Q, afac, srcq);
+  k_trace2d_y<T><<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, y, R, Q, afac, srcq);
   return cudaGetLastError();
 }
-template cudaError_t launch_trace2d_x<double>(const Geom&, double*, const double*, const double*, const double*,
-                                              const double*, cudaStream_t, const double*);
-template cudaError_t launch_trace2d_x<float>(const Geom&, double*, const float*, const double*, const double*,
-                                             const double*, cudaStream_t, const double*);
-template cudaError_t launch_trace2d_ylines<double>(const Geom&, const Coefs&, double*, const double*, cudaStream_t);
-template cudaError_t launch_trace2d_ylines<float>(const Geom&, const Coefs&, double*, const float*, cudaStream_t);
+
+__global__ void k_to_float(float* __restrict__ out, const double* __restrict__ in, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+cudaError_t launch_to_float(float* out, const double* in, int64_t n, cudaStream_t st) {
+  k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, in, n);
+  return cudaGetLastError();
+}
+
+#define AHOC_FUSED2D_INST(T)                                                                                    \
+  template cudaError_t launch_v2d_prep<T>(const Geom&, const Coefs&, const double*, const double*, T*, T*, T*, \
+                                          T*, cudaStream_t);                                                   \
+  template cudaError_t launch_trace2d_x<T>(const Geom&, double*, const T*, const double*, const double*,       \
+                                           const T*, cudaStream_t, const double*);                             \
+  template cudaError_t launch_trace2d_ylines<T>(const Geom&, const Coefs&, T*, const T*, cudaStream_t);        \
+  template cudaError_t launch_trace2d_y<T>(const Geom&, double*, const T*, const double*, const double*,       \
+                                           cudaStream_t, const double*);
+AHOC_FUSED2D_INST(double)
+AHOC_FUSED2D_INST(float)
+#undef AHOC_FUSED2D_INST
 
 }  // namespace ahoc

@@ -10,14 +10,14 @@ cudaError_t launch_dst_x(const Geom& g, T* a, const void* tw, const T* sn, T sca
 template <typename T>
 cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T scale, cudaStream_t st);
 template <typename T>
-cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const double* ainv, const void* tw, const T* sn,
+cudaError_t launch_dst_x_store_ainv(const Geom& g, T* a, const T* ainv, const void* tw, const T* sn,
                                     cudaStream_t st);
-// dst = DST_x( M(W) + face Q/alpha terms + src2 ), 2D; W = V/alpha, or V when
-// ainv_load is given (then W = V * ainv on load); W must not alias dst
+// dst = DST_x( M(W) + face terms qa = Q/alpha + src2 ), 2D; W = V/alpha, or V
+// when ainv_load is given (then W = V * ainv on load); W must not alias dst;
+// every array in precision T
 template <typename T>
-cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const double* Q, const double* afac, double Mc,
-                               double Mn, const void* tw, const T* sn, cudaStream_t st, const T* src2 = nullptr,
-                               const double* ainv_load = nullptr);
+cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const T* qa, T Mc, T Mn, const void* tw,
+                               const T* sn, cudaStream_t st, const T* src2 = nullptr, const T* ainv_load = nullptr);
 // dst = DST_x(lscale * src)
 template <typename T>
 cudaError_t launch_dst_x_from(const Geom& g, T* dst, const T* src, double lscale, const void* tw, const T* sn,
@@ -26,31 +26,42 @@ cudaError_t launch_dst_x_from(const Geom& g, T* dst, const T* src, double lscale
 // Generated right-hand side of the homogeneous v-equation in the x-spectral
 // domain (2D): d(k, j) = sin(k pi/N0) (rxm_j + (-1)^(k+1) rxp_j)
 //                        - b_k (Qh-_k [j = 1] + Qh+_k [j = N1-1]),  b_k = L_y + 2 cos(k pi/N0) L_xy
+template <typename T>
 struct VGen2D {
-  const double* rxm;  // index j (1..N1-1)
-  const double* rxp;
-  const double* qhm;  // index k - 1
-  const double* qhp;
-  const double* sk;   // sin(k pi / N0), index k
-  const double* ck;   // cos(k pi / N0), index k
-  double Ly, Lxy;
+  const T* rxm;  // index j (1..N1-1)
+  const T* rxp;
+  const T* qhm;  // index k - 1
+  const T* qhp;
+  const T* sk;   // sin(k pi / N0), index k
+  const T* ck;   // cos(k pi / N0), index k
+  T Ly, Lxy;
 };
 // generated right-hand side; with `add` the generated terms are added to the
 // right-hand side already in a (x-spectral), otherwise they replace it
+// rpow: per chunk c and mode m, r^(1 + cL) at [c][m] and r^(2N - e_c) at [C + c][m]
 template <typename T>
 cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                   double* scratch, int L, const VGen2D& G, cudaStream_t st, bool add = false);
+                                   const double* rpow, double* scratch, int L, const VGen2D<T>& G, cudaStream_t st,
+                                   bool add = false);
 
 // fused 2D matvec helpers (fused2d.cu)
-cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, double* rxm, double* rxp, double* qy,
-                            cudaStream_t st);
+// from the face values Q (FP64): rxm, rxp (boundary stencil on the first
+// interior columns), qy (y-face data) and qa = Q/alpha (all faces), in T
+template <typename T>
+cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, const double* afinv, T* rxm, T* rxp,
+                            T* qy, T* qa, cudaStream_t st);
 template <typename T>
 cudaError_t launch_trace2d_x(const Geom& g, double* y, const T* Uh, const double* Q, const double* afac,
-                             const double* tau, cudaStream_t st, const double* srcq = nullptr);
+                             const T* tau, cudaStream_t st, const double* srcq = nullptr);
 template <typename T>
-cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, double* R, const T* Uh, cudaStream_t st);
-cudaError_t launch_trace2d_y(const Geom& g, double* y, const double* R, const double* Q, const double* afac,
+cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, T* R, const T* Uh, cudaStream_t st);
+template <typename T>
+cudaError_t launch_trace2d_y(const Geom& g, double* y, const T* R, const double* Q, const double* afac,
                              cudaStream_t st, const double* srcq = nullptr);
+// chunk-start powers of r for the chunked tridiagonal solve (tri.cu)
+cudaError_t launch_tri_powers(const Geom& g, const Mode<double>* md64, double* rpow, int L, cudaStream_t st);
+size_t tri_powers_size(const Geom& g, int L);
+cudaError_t launch_to_float(float* out, const double* in, int64_t n, cudaStream_t st);
 
 // DST-I of generic strided lines (see dst.cu, k_dst_gen)
 template <typename T>
@@ -77,8 +88,8 @@ cudaError_t launch_face_muldiv(double* out, const double* in, const double* mul,
 // modes: the element-wise factors (precision T); md64: the FP64 factors used
 // for the chunk carries; scratch: tri_chunked_scratch() doubles
 template <typename T>
-cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64, double* scratch,
-                               int L, cudaStream_t st);
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                               const double* rpow, double* scratch, int L, cudaStream_t st);
 size_t tri_chunked_scratch(const Geom& g, int L);
 
 template <typename T>

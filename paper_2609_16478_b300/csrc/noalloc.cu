@@ -180,6 +180,7 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
   const size_t o_sny = take(((size_t)g.N[1] / 2 + 1) * sizeof(double));
   const size_t o_modes = take((size_t)ncols * sizeof(Mode<double>));
   const size_t o_tri = take(chunked ? tri_chunked_scratch(g, L) * sizeof(double) : 0);
+  const size_t o_rpow = take(chunked ? tri_powers_size(g, L) * sizeof(double) : 0);
   if (off > kNoAllocBytes) {
     const std::string msg = "ahoc_poisson_noalloc: this grid needs " + std::to_string(off) +
                             " bytes of scratch; the static scratch holds " + std::to_string(kNoAllocBytes) +
@@ -210,6 +211,7 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
   double* sny = reinterpret_cast<double*>(base + o_sny);
   Mode<double>* modes = reinterpret_cast<Mode<double>*>(base + o_modes);
   double* tri = reinterpret_cast<double*>(base + o_tri);
+  double* rpow = reinterpret_cast<double*>(base + o_rpow);
 #define NA_CK(call)                                                                              \
   do {                                                                                           \
     cudaError_t e_ = (call);                                                                     \
@@ -225,10 +227,11 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
   }
   k_na_modes<<<(unsigned)((ncols + 127) / 128), 128, 0, st>>>(g, cf, modes);
   NA_CK(cudaGetLastError());
+  if (chunked) NA_CK(launch_tri_powers(g, modes, rpow, L, st));
   NA_CK(launch_unpack(g, field, rhs, st));
   NA_CK(launch_dst_x<double>(g, field, twx, snx, 1.0, st));
   if (g.dim == 3) NA_CK(launch_dst_y<double>(g, field, twy, sny, 1.0, st));
-  if (chunked) NA_CK(launch_tri_chunked<double>(g, field, modes, modes, tri, L, st));
+  if (chunked) NA_CK(launch_tri_chunked<double>(g, field, modes, modes, rpow, tri, L, st));
   else NA_CK(launch_tri<double>(g, field, modes, st));
   if (g.dim == 3) NA_CK(launch_dst_y<double>(g, field, twy, sny, 1.0, st));
   NA_CK(launch_dst_x<double>(g, field, twx, snx, 1.0, st));

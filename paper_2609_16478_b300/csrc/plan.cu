@@ -239,7 +239,9 @@ struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
       tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau,
       // mixed precision (AHOC_MIXED only)
-      F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb, total;
+      F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
+      // per-precision side arrays of the fused 2D path
+      afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -296,6 +298,9 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.tmp = take(face);
   L.Kry = take(face * (size_t)(o.restart + 1));
   L.Zb = take(face * (size_t)o.restart);
+  L.afinv = take(face);
+  L.qa = take(face);
+  L.rpow = take(tri_ncols(g) < kChunkedBelow ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
   L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
   L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
   const bool mixed = (o.prec == AHOC_MIXED);
@@ -315,6 +320,16 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.Rq = take(mixed ? face : 0);
   L.dQ = take(mixed ? face : 0);
   L.b2 = take(mixed ? face : 0);
+  const size_t fface = (size_t)g.ngamma * sizeof(float);
+  L.ainvf = take(mixed ? (size_t)g.nfull * sizeof(float) : 0);
+  L.rxmf = take(mixed ? ((size_t)g.N[1] + 1) * sizeof(float) : 0);
+  L.rxpf = take(mixed ? ((size_t)g.N[1] + 1) * sizeof(float) : 0);
+  L.qyf = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
+  L.qaf = take(mixed ? fface : 0);
+  L.R2f = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
+  L.tauf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
+  L.skf = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
+  L.ckf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
   L.total = off;
   return L;
 }
@@ -373,6 +388,9 @@ struct ahoc_plan {
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
   double *U64 = nullptr, *V64 = nullptr, *Rq = nullptr, *dQ = nullptr, *b2 = nullptr;
   double* Zb = nullptr;  // flexible GMRES: the preconditioned directions z_j = P^-1 v_j
+  double *afinv = nullptr, *qa = nullptr, *rpow = nullptr;
+  float *ainvf = nullptr, *rxmf = nullptr, *rxpf = nullptr, *qyf = nullptr, *qaf = nullptr, *R2f = nullptr,
+        *tauf = nullptr, *skf = nullptr, *ckf = nullptr;
   Mode<float>* modesf = nullptr;
   int refine_steps = 0;
   double* hhost = nullptr;  // pinned
@@ -449,7 +467,7 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->modes, p->tri, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
@@ -473,7 +491,7 @@ ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->tri, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<float>(g, W, p->modesf, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
@@ -502,42 +520,62 @@ ahoc_status solve_VU_f(ahoc_plan* p, const double* Q, const float* srcv, const f
 //   recover == false: y = alpha delta_nn U - q - srcq (SchurMatVec, Algorithm 1)
 //   recover == true:  W1 <- V, W2 <- U, both physical (the recovery step)
 template <typename T>
-ahoc_status fused2d(ahoc_plan* p, T* W1, T* W2, const Mode<T>* modes, const void* twx, const T* snx,
-                    const double* q, const T* srcv, const T* srcu, const double* srcq, double* y, bool recover) {
+struct F2Arrays {
+  T *W1, *W2;
+  const Mode<T>* modes;
+  const void* tw;
+  const T *sn, *ainv, *tau, *sk, *ck;
+  T *rxm, *rxp, *qy, *qa, *R2;
+};
+F2Arrays<double> f2arrays_d(ahoc_plan* p) {
+  return F2Arrays<double>{p->W1, p->W2, p->modes, p->twx, p->snx, p->ainv, p->tau, p->stab[0], p->ctab[0],
+                          p->rxm, p->rxp, p->qy, p->qa, p->R2};
+}
+F2Arrays<float> f2arrays_f(ahoc_plan* p) {
+  return F2Arrays<float>{p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], p->ainvf, p->tauf, p->skf, p->ckf,
+                         p->rxmf, p->rxpf, p->qyf, p->qaf, p->R2f};
+}
+
+template <typename T>
+ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T* srcv, const T* srcu,
+                    const double* srcq, double* y, bool recover) {
   const Geom& g = p->g;
   const Coefs& cf = p->cf;
   const int N0 = g.N[0];
   const int L = tri_chunk_len(g);
-  VGen2D G{p->rxm, p->rxp, p->qy, p->qy + (N0 - 1), p->stab[0], p->ctab[0], cf.L[16], cf.L[17]};
+  VGen2D<T> G{A.rxm, A.rxp, A.qy, A.qy + (N0 - 1), A.sk, A.ck, (T)cf.L[16], (T)cf.L[17]};
   if (q) {
-    RUN(AHOC_K_VRHS, launch_v2d_prep(g, cf, q, p->rxm, p->rxp, p->qy, p->st));
-    RUN(AHOC_K_VRHS, launch_dst_gen<double>(p->qy, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
+    RUN(AHOC_K_VRHS, launch_v2d_prep<T>(g, cf, q, p->afinv, A.rxm, A.rxp, A.qy, A.qa, p->st));
+    RUN(AHOC_K_VRHS, launch_dst_gen<T>(A.qy, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st));
   }
+  const T* qa = q ? A.qa : nullptr;
   // V-hat: L_h V = -r_v - L_bdry(q) in x-modes
   if (srcv) {
-    RUN(AHOC_K_DST_X, launch_dst_x_from<T>(g, W1, srcv, -1.0, twx, snx, p->st));
-    if (q) RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, W1, modes, p->modes, p->tri, L, G, p->st, true));
-    else RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, W1, modes, p->modes, p->tri, L, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x_from<T>(g, A.W1, srcv, -1.0, A.tw, A.sn, p->st));
+    if (q)
+      RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, G, p->st, true));
+    else
+      RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, p->st));
   } else {
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, W1, modes, p->modes, p->tri, L, G, p->st, false));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, G, p->st, false));
   }
   // U-hat: L_h U = M(V/alpha) + face terms + r_u, by one forward DST of the fused right-hand side
   if (!recover) {
-    RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<T>(g, W1, p->ainv, twx, snx, p->st));
-    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, W2, W1, q, p->afac, cf.Mc, cf.Mn, twx, snx, p->st, srcu, nullptr));
+    RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<T>(g, A.W1, A.ainv, A.tw, A.sn, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, A.W2, A.W1, qa, (T)cf.Mc, (T)cf.Mn, A.tw, A.sn, p->st, srcu, nullptr));
   } else {
-    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, W1, twx, snx, (T)1, p->st));
-    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, W2, W1, q, p->afac, cf.Mc, cf.Mn, twx, snx, p->st, srcu, p->ainv));
+    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, A.W1, A.tw, A.sn, (T)1, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, A.W2, A.W1, qa, (T)cf.Mc, (T)cf.Mn, A.tw, A.sn, p->st, srcu, A.ainv));
   }
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, W2, modes, p->modes, p->tri, L, p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W2, A.modes, p->modes, p->rpow, p->tri, L, p->st));
   if (recover) {
-    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, W2, twx, snx, (T)1, p->st));
+    RUN(AHOC_K_DST_X, launch_dst_x<T>(g, A.W2, A.tw, A.sn, (T)1, p->st));
     return AHOC_OK;
   }
-  RUN(AHOC_K_TRACE, launch_trace2d_x<T>(g, y, W2, q, p->afac, p->tau, p->st, srcq));
-  RUN(AHOC_K_TRACE, launch_trace2d_ylines<T>(g, cf, p->R2, W2, p->st));
-  RUN(AHOC_K_TRACE, launch_dst_gen<double>(p->R2, 2, 1, N0 - 1, 0, 1, N0, p->twx, p->snx, p->st));
-  RUN(AHOC_K_TRACE, launch_trace2d_y(g, y, p->R2, q, p->afac, p->st, srcq));
+  RUN(AHOC_K_TRACE, launch_trace2d_x<T>(g, y, A.W2, q, p->afac, A.tau, p->st, srcq));
+  RUN(AHOC_K_TRACE, launch_trace2d_ylines<T>(g, cf, A.R2, A.W2, p->st));
+  RUN(AHOC_K_TRACE, launch_dst_gen<T>(A.R2, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st));
+  RUN(AHOC_K_TRACE, launch_trace2d_y<T>(g, y, A.R2, q, p->afac, p->st, srcq));
   return AHOC_OK;
 }
 
@@ -545,14 +583,12 @@ bool fused_ok(const Geom& g) { return g.dim == 2 && tri_ncols(g) < kChunkedBelow
 
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
   if (p->o.prec == AHOC_MIXED) {
-    if (fused_ok(p->g))
-      return fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], q, nullptr, nullptr, nullptr, y, false);
+    if (fused_ok(p->g)) return fused2d<float>(p, f2arrays_f(p), q, nullptr, nullptr, nullptr, y, false);
     CKS(solve_VU_f(p, q, nullptr, nullptr));
     RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
     return AHOC_OK;
   }
-  if (fused_ok(p->g))
-    return fused2d<double>(p, p->W1, p->W2, p->modes, p->twx, p->snx, q, nullptr, nullptr, nullptr, y, false);
+  if (fused_ok(p->g)) return fused2d<double>(p, f2arrays_d(p), q, nullptr, nullptr, nullptr, y, false);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -591,6 +627,11 @@ ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
     // x-faces are lines of N1 - 1 points (DST length N1), y-faces of N0 - 1
     const Geom& g = p->g;
     const int64_t ox = g.face_off[0], oy = g.face_off[2];
+    if (g.N[0] == g.N[1]) {  // the four faces are four consecutive lines of equal length
+      RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out, in, p->afac, p->pre, 4, g.N[0] - 1, g.N[0], p->twf[0],
+                                                     p->snf[0], p->st));
+      return AHOC_OK;
+    }
     RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + ox, in + ox, p->afac + ox, p->pre + ox, 2, g.N[1] - 1,
                                                    g.N[1], p->twf[1], p->snf[1], p->st));
     RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + oy, in + oy, p->afac + oy, p->pre + oy, 2, g.N[0] - 1,
@@ -756,6 +797,20 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   p->tmp = at<double>(p, L.tmp);
   p->Kry = at<double>(p, L.Kry);
   p->Zb = at<double>(p, L.Zb);
+  p->afinv = at<double>(p, L.afinv);
+  p->qa = at<double>(p, L.qa);
+  p->rpow = at<double>(p, L.rpow);
+  if (o.prec == AHOC_MIXED) {
+    p->ainvf = at<float>(p, L.ainvf);
+    p->rxmf = at<float>(p, L.rxmf);
+    p->rxpf = at<float>(p, L.rxpf);
+    p->qyf = at<float>(p, L.qyf);
+    p->qaf = at<float>(p, L.qaf);
+    p->R2f = at<float>(p, L.R2f);
+    p->tauf = at<float>(p, L.tauf);
+    p->skf = at<float>(p, L.skf);
+    p->ckf = at<float>(p, L.ckf);
+  }
   p->partial = at<double>(p, L.partial);
   p->hdev = at<double>(p, L.hdev);
   const size_t fld = (size_t)g.npad * sizeof(double);
@@ -829,6 +884,14 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   }
   CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
   CKC(launch_face_gather(g, p->afac, alpha, p->st));
+  CKC(launch_recip(p->afinv, p->afac, g.ngamma, p->st));
+  if (tri_ncols(g) < kChunkedBelow) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
+  if (o.prec == AHOC_MIXED) {
+    CKC(launch_to_float(p->ainvf, p->ainv, g.nfull, p->st));
+    CKC(launch_to_float(p->tauf, p->tau, g.N[0] + 1, p->st));
+    CKC(launch_to_float(p->skf, p->stab[0], 2 * (int64_t)g.N[0], p->st));
+    CKC(launch_to_float(p->ckf, p->ctab[0], g.N[0] + 1, p->st));
+  }
   if (o.precond) {
     const double* stp[3] = {p->stab[0], p->stab[1], g.dim == 3 ? p->stab[2] : nullptr};
     const double* ctp[3] = {p->ctab[0], p->ctab[1], g.dim == 3 ? p->ctab[2] : nullptr};
@@ -1162,8 +1225,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
                          p->ainv, p->afac, p->st));
     // correction right-hand side b = -R_d(0)
     if (fused_ok(g)) {
-      CKS(fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], nullptr, p->Rv, p->Ru, p->Rq, p->b2,
-                         false));
+      CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));
     } else {
       CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
       RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
@@ -1190,8 +1252,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
     go->ms_mv += gi.ms_mv;
     // recovery of the correction and the FP64 update
     if (fused_ok(g))
-      CKS(fused2d<float>(p, p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], p->dQ, p->Rv, p->Ru, nullptr, nullptr,
-                         true));
+      CKS(fused2d<float>(p, f2arrays_f(p), p->dQ, p->Rv, p->Ru, nullptr, nullptr, true));
     else
       CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
     RUN(AHOC_K_OTHER, launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->st));

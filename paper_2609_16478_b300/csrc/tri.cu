@@ -143,10 +143,11 @@ __device__ __forceinline__ int64_t col_base(const Geom& g, int64_t m) {
 }
 
 // generated right-hand side of the homogeneous v-equation (2D), see VGen2D
-__device__ __forceinline__ double vgen(const VGen2D& G, int k, int j, int Nt) {
-  double v = G.sk[k] * (G.rxm[j] + ((k & 1) ? G.rxp[j] : -G.rxp[j]));
+template <typename T>
+__device__ __forceinline__ T vgen(const VGen2D<T>& G, int k, int j, int Nt) {
+  T v = G.sk[k] * (G.rxm[j] + ((k & 1) ? G.rxp[j] : -G.rxp[j]));
   if (j == 1 || j == Nt - 1) {
-    const double bk = G.Ly + 2.0 * G.ck[k] * G.Lxy;
+    const T bk = G.Ly + (T)2 * G.ck[k] * G.Lxy;
     if (j == 1) v -= bk * G.qhm[k - 1];
     if (j == Nt - 1) v -= bk * G.qhp[k - 1];
   }
@@ -155,15 +156,15 @@ __device__ __forceinline__ double vgen(const VGen2D& G, int k, int j, int Nt) {
 
 // right-hand side element: GEN 0 loaded, 1 generated, 2 loaded + generated
 template <typename T, int GEN>
-__device__ __forceinline__ T rhs_elem(const T* col, const VGen2D& G, int k, int j, const TriShape& sh) {
+__device__ __forceinline__ T rhs_elem(const T* col, const VGen2D<T>& G, int k, int j, const TriShape& sh) {
   if (GEN == 0) return col[(int64_t)j * sh.stride];
-  if (GEN == 1) return (T)vgen(G, k, j, sh.Nt);
-  return (T)((double)col[(int64_t)j * sh.stride] + vgen(G, k, j, sh.Nt));
+  if (GEN == 1) return vgen(G, k, j, sh.Nt);
+  return col[(int64_t)j * sh.stride] + vgen(G, k, j, sh.Nt);
 }
 
 template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                double* __restrict__ E, VGen2D G) {
+                                                double* __restrict__ E, VGen2D<T> G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -213,7 +214,7 @@ __global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const 
 
 template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                const double* __restrict__ carry, double* __restrict__ B, VGen2D G) {
+                                                const double* __restrict__ carry, double* __restrict__ B, VGen2D<T> G) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
@@ -282,6 +283,7 @@ __global__ void k_tri_t2b(Geom g, const Mode<double>* __restrict__ modes, const 
 template <typename T, int L>
 __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
                                                 const Mode<double>* __restrict__ md64,
+                                                const double* __restrict__ rpow,
                                                 const double* __restrict__ bcarry, const double* __restrict__ Cc) {
   const TriShape sh = tri_shape(g, L);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
   for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : (T)0;
   // descending: r^(e0 + 1 - j) bc - C r^(2N - j) = X_j, one geometric term
   // (X_{j-1} = r X_j) that shrinks as j decreases
-  T X = (T)(r * bc - Cm * ipow(r, 2 * sh.Nt - e0));
+  T X = (T)(r * bc - Cm * rpow[(int64_t)(sh.C + c) * sh.ncols + m]);  // r^(2N - e0) tabulated
 #pragma unroll
   for (int q = L - 1; q >= 0; --q)
     if (q < len) {
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
       X = rmul(q1, X);
     }
   // ascending: + C r^j, shrinking as j increases
-  T Aj = (T)(Cm * ipow(r, s0));
+  T Aj = (T)(Cm * rpow[(int64_t)c * sh.ncols + m]);  // r^(s0) tabulated
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) {
@@ -331,7 +333,7 @@ size_t tri_chunked_scratch(const Geom& g, int L) {
 
 template <typename T, int L, int GEN>
 static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                 double* scratch, const VGen2D& G, cudaStream_t st) {
+                                 const double* rpow, double* scratch, const VGen2D<T>& G, cudaStream_t st) {
   const int nx = g.N[0] - 1;
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
@@ -348,39 +350,74 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, cons
   k_tri_t1b<<<cb, 128, 0, st>>>(g, md64, E, carry, L);
   k_tri_t2<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
   k_tri_t2b<<<cb, 128, 0, st>>>(g, md64, B, bcarry, Cc, L);
-  k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, md64, bcarry, Cc);
+  k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, md64, rpow, bcarry, Cc);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64, double* scratch,
-                               int L, cudaStream_t st) {
-  VGen2D G{};
-  if (L == 32) return tri_chunked_L<T, 32, 0>(g, a, modes, md64, scratch, G, st);
-  if (L == 16) return tri_chunked_L<T, 16, 0>(g, a, modes, md64, scratch, G, st);
+cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                               const double* rpow, double* scratch, int L, cudaStream_t st) {
+  VGen2D<T> G{};
+  if (L == 32) return tri_chunked_L<T, 32, 0>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, 0>(g, a, modes, md64, rpow, scratch, G, st);
   return cudaErrorInvalidValue;
+}
+
+// rpow[c][m] = r_m^(1 + cL) and rpow[C + c][m] = r_m^(2N - e_c), by binary powering in FP64
+__global__ void k_tri_powers(Geom g, const Mode<double>* __restrict__ md64, double* __restrict__ rpow, int L) {
+  const TriShape sh = tri_shape(g, L);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int e0 = min(s0 + L - 1, sh.nt);
+  const double r = md64[m].r;
+  rpow[(int64_t)c * sh.ncols + m] = ipow(r, s0);
+  rpow[(int64_t)(sh.C + c) * sh.ncols + m] = ipow(r, 2 * sh.Nt - e0);
+}
+
+size_t tri_powers_size(const Geom& g, int L) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  return (size_t)2 * C * ncols;  // doubles
+}
+
+cudaError_t launch_tri_powers(const Geom& g, const Mode<double>* md64, double* rpow, int L, cudaStream_t st) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  const int64_t work = ncols * C;
+  k_tri_powers<<<(unsigned)((work + 127) / 128), 128, 0, st>>>(g, md64, rpow, L);
+  return cudaGetLastError();
 }
 
 // the same solve with the v-equation right-hand side generated on the fly (2D)
 template <typename T>
 cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                   double* scratch, int L, const VGen2D& G, cudaStream_t st, bool add) {
+                                   const double* rpow, double* scratch, int L, const VGen2D<T>& G, cudaStream_t st,
+                                   bool add) {
   if (g.dim != 2) return cudaErrorInvalidValue;
-  if (L == 32) return add ? tri_chunked_L<T, 32, 2>(g, a, modes, md64, scratch, G, st)
-                          : tri_chunked_L<T, 32, 1>(g, a, modes, md64, scratch, G, st);
-  if (L == 16) return add ? tri_chunked_L<T, 16, 2>(g, a, modes, md64, scratch, G, st)
-                          : tri_chunked_L<T, 16, 1>(g, a, modes, md64, scratch, G, st);
+  if (L == 32) return add ? tri_chunked_L<T, 32, 2>(g, a, modes, md64, rpow, scratch, G, st)
+                          : tri_chunked_L<T, 32, 1>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 16) return add ? tri_chunked_L<T, 16, 2>(g, a, modes, md64, rpow, scratch, G, st)
+                          : tri_chunked_L<T, 16, 1>(g, a, modes, md64, rpow, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
-                                                    double*, int, const VGen2D&, cudaStream_t, bool);
+                                                    const double*, double*, int, const VGen2D<double>&, cudaStream_t,
+                                                    bool);
 template cudaError_t launch_tri_chunked_gen<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*,
-                                                   double*, int, const VGen2D&, cudaStream_t, bool);
+                                                   const double*, double*, int, const VGen2D<float>&, cudaStream_t,
+                                                   bool);
 
 template cudaError_t launch_tri_chunked<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
-                                                double*, int, cudaStream_t);
-template cudaError_t launch_tri_chunked<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*, double*,
-                                               int, cudaStream_t);
+                                                const double*, double*, int, cudaStream_t);
+template cudaError_t launch_tri_chunked<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*,
+                                               const double*, double*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st) {
