@@ -123,6 +123,8 @@ typedef struct {
   double kernel_ms_top[AHOC_NK];      /* as kernel_ms, this grid's launches only (no coarse)  */
   int64_t kernel_launches_top[AHOC_NK];
   int refine_steps;       /* AHOC_MIXED: FP32 correction solves taken                           */
+  double refine_hist[16]; /* AHOC_MIXED: relative Schur residual before each correction, then at exit */
+  int inner_iters[16];    /* AHOC_MIXED: GMRES iterations of each correction solve              */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:

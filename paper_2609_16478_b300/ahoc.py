@@ -47,7 +47,7 @@ class ahoc_info(C.Structure):
                 ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK),
                 ("levels", C.c_int), ("coarse_iters", C.c_int),
                 ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK),
-                ("refine_steps", C.c_int)]
+                ("refine_steps", C.c_int), ("refine_hist", C.c_double * 16), ("inner_iters", C.c_int * 16)]
 
 
 class AhocError(RuntimeError):
@@ -199,7 +199,9 @@ class Plan:
                        levels=info.levels, coarse_iters=info.coarse_iters,
                        kernel_ms_top={k: info.kernel_ms_top[i] for i, k in enumerate(KERNEL_NAMES)},
                        kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)},
-                       refine_steps=info.refine_steps)
+                       refine_steps=info.refine_steps,
+                       refine_hist=[info.refine_hist[i] for i in range(min(16, info.refine_steps + 1))],
+                       inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))])
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         if y is None:

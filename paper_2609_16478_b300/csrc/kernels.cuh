@@ -101,9 +101,10 @@ template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
                         const double* vedge, cudaStream_t st, const T* srcv = nullptr);
 // u-equation right-hand side for L_h U_int = rhs:
-//   rhs = M(V / alpha) - L_bdry(g_D),  V = Q on face points (M reaches no edges).
+//   rhs = M(V / alpha) - L_bdry(g_D),  V = Q on face points (M reaches no edges);
+//   ainv = 1/alpha on the full grid, in T.
 template <typename T>
-cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
+cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const T* ainv, const double* Q,
                         const double* gD, cudaStream_t st, const T* srcu = nullptr);
 // Boundary residual R_p = alpha_p [u_nn(U)_p + lapt_p] - Q_p at every face point.
 template <typename T>

@@ -247,8 +247,14 @@ struct Layout {
 // The chunked tridiagonal form is used when the transverse modes alone give
 // too few threads (2D, small 3D grids).
 constexpr int64_t kChunkedBelow = 65536;
+// FP32 solves always take the chunked form: its carries are FP64, and the
+// one-thread-per-column form accumulates the whole column in FP32, which
+// loses the near-boundary cancellation u = p + C phi on large grids.
 int tri_chunk_len(const Geom& g) { return ((g.dim == 3 ? g.N[2] : g.N[1]) >= 1024) ? 32 : 16; }
 int64_t tri_ncols(const Geom& g) { return (int64_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1); }
+bool chunked_for(const Geom& g, ahoc_precision prec) {
+  return prec == AHOC_MIXED || tri_ncols(g) < kChunkedBelow;
+}
 
 constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 
@@ -283,7 +289,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
   }
   L.pre = take(face);
   L.z = take(face);
-  L.tri = take(tri_ncols(g) < kChunkedBelow ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.tri = take(chunked_for(g, o.prec) ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
   // fused 2D matvec scratch
   L.rxm = take(((size_t)g.N[1] + 1) * sizeof(double));
   L.rxp = take(((size_t)g.N[1] + 1) * sizeof(double));
@@ -300,7 +306,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.Zb = take(face * (size_t)o.restart);
   L.afinv = take(face);
   L.qa = take(face);
-  L.rpow = take(tri_ncols(g) < kChunkedBelow ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.rpow = take(chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
   L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
   L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
   const bool mixed = (o.prec == AHOC_MIXED);
@@ -393,6 +399,8 @@ struct ahoc_plan {
         *tauf = nullptr, *skf = nullptr, *ckf = nullptr;
   Mode<float>* modesf = nullptr;
   int refine_steps = 0;
+  double refine_hist[16] = {0};
+  int inner_iters[16] = {0};
   double* hhost = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool have_last = false;
@@ -490,10 +498,7 @@ ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
   const Geom& g = p->g;
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
-  if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
-  else
-    RUN(AHOC_K_TRI, launch_tri<float>(g, W, p->modesf, p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   return AHOC_OK;
@@ -505,7 +510,7 @@ ahoc_status solve_VU_f(ahoc_plan* p, const double* Q, const float* srcv, const f
   const Geom& g = p->g;
   RUN(AHOC_K_VRHS, launch_vrhs<float>(g, p->cf, p->F1, Q, nullptr, nullptr, p->st, srcv));
   CKS(poisson_inplace_f(p, p->F1));
-  RUN(AHOC_K_URHS, launch_urhs<float>(g, p->cf, p->F2, p->F1, p->ainv, Q, nullptr, p->st, srcu));
+  RUN(AHOC_K_URHS, launch_urhs<float>(g, p->cf, p->F2, p->F1, p->ainvf, Q, nullptr, p->st, srcu));
   CKS(poisson_inplace_f(p, p->F2));
   return AHOC_OK;
 }
@@ -885,7 +890,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
   CKC(launch_face_gather(g, p->afac, alpha, p->st));
   CKC(launch_recip(p->afinv, p->afac, g.ngamma, p->st));
-  if (tri_ncols(g) < kChunkedBelow) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
+  if (chunked_for(g, o.prec)) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
   if (o.prec == AHOC_MIXED) {
     CKC(launch_to_float(p->ainvf, p->ainv, g.nfull, p->st));
     CKC(launch_to_float(p->tauf, p->tau, g.N[0] + 1, p->st));
@@ -1219,6 +1224,10 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
   CK(cudaMemsetAsync(p->Q, 0, n * sizeof(double), p->st));
   double bref = 0.0;
   p->refine_steps = 0;
+  for (int k = 0; k < 16; ++k) {
+    p->refine_hist[k] = 0.0;
+    p->inner_iters[k] = 0;
+  }
   for (int step = 0; step <= kMaxRefine; ++step) {
     RUNN(AHOC_K_OTHER, 2,
          launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->gD, p->vedge, p->gN, p->lapt,
@@ -1236,8 +1245,12 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
     CKS(norm2(p, p->b2, &bn));
     if (step == 0) bref = bn;
     go->rel = (bref > 0) ? bn / bref : 0.0;
+    if (step < 16) p->refine_hist[step] = go->rel;
     if (bn == 0.0 || go->rel <= tol) break;
-    if (step == kMaxRefine) {
+    // a correction that removes less than half of the residual means the FP32
+    // solves have reached their accuracy floor on this grid: stop rather than
+    // spend the remaining steps at that floor
+    if (step == kMaxRefine || (step >= 2 && go->rel > 0.5 * p->refine_hist[step - 1])) {
       go->status = AHOC_ENOCONV;
       break;
     }
@@ -1248,6 +1261,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
     GmresOut gi;
     CKS(gmres(p, p->b2, bn, p->dQ, false, itol, p->o.max_iters - go->iters, &gi));
     go->iters += gi.iters;
+    if (step < 16) p->inner_iters[step] = gi.iters;
     go->restarts += gi.restarts;
     go->ms_mv += gi.ms_mv;
     // recovery of the correction and the FP64 update
@@ -1302,6 +1316,10 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
     info->levels = p->levels;
     info->coarse_iters = p->coarse_iters;
     info->refine_steps = p->refine_steps;
+    for (int k = 0; k < 16; ++k) {
+      info->refine_hist[k] = p->refine_hist[k];
+      info->inner_iters[k] = p->inner_iters[k];
+    }
     for (int k = 0; k < AHOC_NK; ++k) {
       info->kernel_ms[k] = p->kms[k];
       info->kernel_launches[k] = p->kn[k];

@@ -39,16 +39,20 @@ __device__ __forceinline__ bool near_bdry(const Geom& g, int i, int j, int k) {
          (g.dim == 3 && (k == 1 || k == g.N[2] - 1));
 }
 
+// The right-hand-side kernels run on a (ceil(n0/256), n1, n2) grid: thread
+// (i, j, k) of the padded interior, no 64-bit index division.  Arithmetic is
+// in T; the FP64 face data (Q, v on the edges) is rounded to T on the
+// boundary-adjacent points that read it.
 template <typename T>
 __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __restrict__ Q,
                        const double* __restrict__ f, const double* __restrict__ vedge,
                        const T* __restrict__ srcv) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.npad) return;
-  int i, j, k;
-  decompose(g, t, i, j, k);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n0) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int64_t t = g.pad(i, j, k);
   if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
-  double acc = 0.0;
+  T acc = 0;
   if ((Q || vedge) && near_bdry(g, i, j, k)) {
     const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
     for (int dz = dzlo; dz <= dzhi; ++dz)
@@ -66,42 +70,46 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
           } else if (vedge) {
             vb = vedge[g.full(ii, jj, kk)];
           }
-          acc -= c * vb;
+          acc -= (T)c * (T)vb;
         }
   }
   if (f) {
-    double m = cf.Mc * f[g.full(i, j, k)];
-    m += cf.Mn * (f[g.full(i - 1, j, k)] + f[g.full(i + 1, j, k)] + f[g.full(i, j - 1, k)] + f[g.full(i, j + 1, k)]);
-    if (g.dim == 3) m += cf.Mn * (f[g.full(i, j, k - 1)] + f[g.full(i, j, k + 1)]);
+    T m = (T)cf.Mc * (T)f[g.full(i, j, k)];
+    m += (T)cf.Mn * (T)(f[g.full(i - 1, j, k)] + f[g.full(i + 1, j, k)] + f[g.full(i, j - 1, k)] + f[g.full(i, j + 1, k)]);
+    if (g.dim == 3) m += (T)cf.Mn * (T)(f[g.full(i, j, k - 1)] + f[g.full(i, j, k + 1)]);
     acc -= m;
   }
-  if (srcv) acc -= (double)srcv[t];
-  out[t] = (T)acc;
+  if (srcv) acc -= srcv[t];
+  out[t] = acc;
 }
 
+// ainv: 1/alpha on the full grid, in T
 template <typename T>
 __global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restrict__ V,
-                       const double* __restrict__ ainv, const double* __restrict__ Q,
+                       const T* __restrict__ ainv, const double* __restrict__ Q,
                        const double* __restrict__ gD, const T* __restrict__ srcu) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.npad) return;
-  int i, j, k;
-  decompose(g, t, i, j, k);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n0) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int64_t t = g.pad(i, j, k);
   if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
   // M(V / alpha): centre and the axis neighbours; a neighbour on a face holds Q
-  double acc = cf.Mc * (double)V[t] * ainv[g.full(i, j, k)];
-  const int nd = g.dim;
-  for (int a = 0; a < nd; ++a) {
+  const int64_t fc = g.full(i, j, k);
+  const T Mn = (T)cf.Mn;
+  T acc = (T)cf.Mc * V[t] * ainv[fc];
+  const int64_t pst[3] = {1, g.n0, g.n0 * g.n1}, fst[3] = {1, g.f0, g.f0 * g.f1};
+  const int idx[3] = {i, j, k};
+  for (int a = 0; a < g.dim; ++a) {
     for (int s = -1; s <= 1; s += 2) {
-      const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
-      const int ia = (a == 0) ? ii : (a == 1) ? jj : kk;
-      double v;
+      const int ia = idx[a] + s;
+      T v;
       if (ia == 0 || ia == g.N[a]) {
-        v = Q ? Q[g.face(a, ia != 0, ii, jj, kk)] : 0.0;
+        const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
+        v = Q ? (T)Q[g.face(a, ia != 0, ii, jj, kk)] : (T)0;
       } else {
-        v = (double)V[g.pad(ii, jj, kk)];
+        v = V[t + s * pst[a]];
       }
-      acc += cf.Mn * v * ainv[g.full(ii, jj, kk)];
+      acc += Mn * v * ainv[fc + s * fst[a]];
     }
   }
   if (gD && near_bdry(g, i, j, k)) {
@@ -114,11 +122,11 @@ __global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restric
           const int ii = i + dx, jj = j + dy, kk = k + dz;
           int ax, sd;
           if (bclass(g, ii, jj, kk, ax, sd) == 0) continue;
-          acc -= c * gD[g.full(ii, jj, kk)];
+          acc -= (T)c * (T)gD[g.full(ii, jj, kk)];
         }
   }
-  if (srcu) acc += (double)srcu[t];
-  out[t] = (T)acc;
+  if (srcu) acc += srcu[t];
+  out[t] = acc;
 }
 
 template <typename T>
@@ -243,13 +251,15 @@ static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) 
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
                         const double* vedge, cudaStream_t st, const T* srcv) {
-  k_vrhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv);
+  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)g.n2);
+  k_vrhs<T><<<grid, 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const double* ainv, const double* Q,
+cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const T* ainv, const double* Q,
                         const double* gD, cudaStream_t st, const T* srcu) {
-  k_urhs<T><<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, out, V, ainv, Q, gD, srcu);
+  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)g.n2);
+  k_urhs<T><<<grid, 256, 0, st>>>(g, cf, out, V, ainv, Q, gD, srcu);
   return cudaGetLastError();
 }
 template <typename T>
@@ -294,7 +304,7 @@ template cudaError_t launch_trace<double>(const Geom&, const Coefs&, double*, co
                                           const double*);
 template cudaError_t launch_vrhs<float>(const Geom&, const Coefs&, float*, const double*, const double*,
                                         const double*, cudaStream_t, const float*);
-template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const double*,
+template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const float*,
                                         const double*, const double*, cudaStream_t, const float*);
 template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, const float*, const double*,
                                          const double*, const double*, const double*, const double*, cudaStream_t,

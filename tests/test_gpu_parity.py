@@ -301,3 +301,23 @@ def test_mixed_equals_fp64_at_1024():
     err = float((umx.reshape(1025, 1025) - d["u_exact"]).abs().max())
     err64 = float((u64.reshape(1025, 1025) - d["u_exact"]).abs().max())
     assert err < 1.05 * err64 + 1e-15
+
+
+def test_mixed_equals_fp64_3d_512():
+    # 511^2 transverse modes: the grid on which a column-wise FP32 tridiagonal
+    # recurrence stalled the refinement at ~1e-5; the chunked form with FP64
+    # carries must take the mixed solve to the FP64 answer
+    N = [512, 512, 512]
+    d = inputs.sample(inputs.config_problem("fourier3d"), N, backend="torch", device="cuda")
+    f = d["f"].reshape(-1).contiguous()
+    p64 = _plan(d)
+    u64, i64 = p64.solve(f, tol=1e-12)
+    p64.close()
+    del p64
+    pmx = _plan(d, prec="mixed")
+    umx, imx = pmx.solve(f, tol=1e-12)
+    assert imx["status"] == 0 and imx["refine_steps"] <= 6, imx
+    hist = imx["refine_hist"]
+    assert all(hist[k + 1] < 0.5 * hist[k] for k in range(imx["refine_steps"]))
+    rel = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    assert rel < TOL_MIXED, (rel, imx)
