@@ -85,8 +85,13 @@ typedef struct {
                              inner solves (DST, tridiagonal, stencils) inside FP64 iterative
                              refinement of the coupled system (FP64 residual of all three
                              block rows, FP64 GMRES vectors, Hessenberg and updates); the
-                             stopping test is the same relative Schur residual.  In a MIXED
-                             plan ahoc_matvec runs the FP32 inner solves.                     */
+                             stopping test is the same relative Schur residual, evaluated
+                             from the FP64 residual of the iterate.  When a step removes
+                             less than a tenth of it (limiting accuracy), the solve has converged if the
+                             last correction changed U by at most tol (relative 2-norm;
+                             rel_resid may then exceed tol) and returns AHOC_ENOCONV
+                             otherwise.  In a MIXED plan ahoc_matvec runs the FP32 inner
+                             solves.                                                           */
   int max_iters;          /* [500] total GMRES iterations allowed                               */
   int restart;            /* [100] Krylov basis size before a restart (the paper's GMRES is not
                              restarted; the cap only bounds memory)                            */
@@ -107,7 +112,15 @@ typedef struct {
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
                              every axis keeps >= 128 intervals, at most 2 levels); 0: off */
+  double coarse_tol;      /* [0] relative Schur residual the coarse levels of the nested guess
+                             solve to (never tighter than the solve's tol).  The prolonged
+                             guess is only as good as the coarse grid's discretisation and
+                             the interpolation, so a coarse solve past that is wasted.
+                             <= 0: automatic (AHOC_COARSE_TOL_AUTO)                         */
 } ahoc_opts;
+
+/* automatic coarse-level tolerance of the nested initial guess */
+#define AHOC_COARSE_TOL_AUTO 1e-10
 
 typedef struct {
   int iters;              /* GMRES iterations (matrix-vector products) of the last solve        */
@@ -125,6 +138,7 @@ typedef struct {
   int refine_steps;       /* AHOC_MIXED: FP32 correction solves taken                           */
   double refine_hist[16]; /* AHOC_MIXED: relative Schur residual before each correction, then at exit */
   int inner_iters[16];    /* AHOC_MIXED: GMRES iterations of each correction solve              */
+  double refine_du[16];   /* AHOC_MIXED: ||dU||_2 / ||U||_2 of each correction (U after it)    */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:

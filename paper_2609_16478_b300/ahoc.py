@@ -38,7 +38,7 @@ KERNEL_NAMES = ("dst_x", "dst_y", "tri", "vrhs", "urhs", "trace", "krylov", "oth
 class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("levels", C.c_int)]
+                ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double)]
 
 
 class ahoc_info(C.Structure):
@@ -47,7 +47,8 @@ class ahoc_info(C.Structure):
                 ("kernel_ms", C.c_double * AHOC_NK), ("kernel_launches", C.c_int64 * AHOC_NK),
                 ("levels", C.c_int), ("coarse_iters", C.c_int),
                 ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK),
-                ("refine_steps", C.c_int), ("refine_hist", C.c_double * 16), ("inner_iters", C.c_int * 16)]
+                ("refine_steps", C.c_int), ("refine_hist", C.c_double * 16), ("inner_iters", C.c_int * 16),
+                ("refine_du", C.c_double * 16)]
 
 
 class AhocError(RuntimeError):
@@ -111,15 +112,23 @@ def _ptr(t: Optional[torch.Tensor], numel: int, name: str):
     return C.c_void_p(t.data_ptr())
 
 
-def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1):
+def _prec(prec) -> int:
+    """AHOC_FP64 / AHOC_MIXED from an int or "fp64" / "mixed"."""
+    if isinstance(prec, str):
+        return {"fp64": AHOC_FP64, "mixed": AHOC_MIXED}[prec]
+    return int(prec)
+
+
+def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0):
     o = ahoc_opts()
+    o.coarse_tol = float(coarse_tol)
     o.timing = int(timing)
     o.levels = int(levels)
-    o.prec = prec
+    o.prec = _prec(prec)
     o.max_iters = max_iters
     o.restart = restart
     o.precond = precond
-    o.refine_tol = 0.0
+    o.refine_tol = float(refine_tol)
     if workspace is not None:
         o.workspace = C.c_void_p(workspace.data_ptr())
         o.workspace_bytes = workspace.numel()
@@ -145,7 +154,7 @@ class Plan:
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
-                 levels: int = -1):
+                 levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0):
         L = lib()
         self.dim = dim
         self.N = [int(n) for n in N]
@@ -163,8 +172,7 @@ class Plan:
                 if b != a:
                     s *= self.N[b] - 1
             self.ngamma += 2 * s
-        if isinstance(prec, str):
-            prec = {"fp64": AHOC_FP64, "mixed": AHOC_MIXED}[prec]
+        prec = _prec(prec)
         self.prec = prec
         self.device = alpha.device
         nb = workspace_bytes(dim, self.N, restart, prec, levels)
@@ -172,7 +180,7 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
                         _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
-        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels)
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
@@ -201,7 +209,8 @@ class Plan:
                        kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)},
                        refine_steps=info.refine_steps,
                        refine_hist=[info.refine_hist[i] for i in range(min(16, info.refine_steps + 1))],
-                       inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))])
+                       inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))],
+                       refine_du=[info.refine_du[i] for i in range(min(16, info.refine_steps))])
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         if y is None:

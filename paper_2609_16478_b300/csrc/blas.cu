@@ -93,6 +93,10 @@ cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w,
   k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nb, ncols, out);
   return cudaGetLastError();
 }
+cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st) {
+  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nblocks, ncols, out);
+  return cudaGetLastError();
+}
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
                             cudaStream_t st) {
   k_gemv_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ld, ncols, h, w, n);

@@ -117,8 +117,10 @@ cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
                             cudaStream_t st);
+// U += dU, V += dV; out[0] = sum dU^2, out[1] = sum U^2 after the update
+// (deterministic: nblocks fixed partials in `partial`, 2 * nblocks doubles)
 cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
-                              cudaStream_t st);
+                              double* partial, int nblocks, double* out, cudaStream_t st);
 
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st);
 cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st);
@@ -138,6 +140,8 @@ cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, con
 // `partial`, which holds nblocks * ncols doubles)
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
                         int nblocks, double* out, cudaStream_t st);
+// out[c] = sum_b partial[b * ncols + c] in block order
+cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st);
 // w -= V h (h on device, ncols entries)
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
                             cudaStream_t st);

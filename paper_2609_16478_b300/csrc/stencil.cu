@@ -507,13 +507,43 @@ __global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const do
   rq[q] = -(afac[q] * unn - Q[q]);
 }
 
-// x += correction: U += dU, V += dV (FP32 padded fields)
-__global__ void k_accumulate(int64_t n, double* __restrict__ U, const float* __restrict__ dU, double* __restrict__ V,
-                             const float* __restrict__ dV) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  U[t] += (double)dU[t];
-  V[t] += (double)dV[t];
+// x += correction: U += dU, V += dV (FP32 padded fields), with the block
+// partial sums of dU^2 and of the updated U^2 (the size of the correction
+// relative to the iterate, for the refinement's stopping test)
+constexpr int kAccThreads = 512;
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(int64_t n, double* __restrict__ U, const float* __restrict__ dU,
+                                                            double* __restrict__ V, const float* __restrict__ dV,
+                                                            double* __restrict__ partial) {
+  __shared__ double red[2][kAccThreads / 32];
+  double sdu = 0.0, su = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double du = (double)dU[t];
+    const double u = U[t] + du;
+    U[t] = u;
+    V[t] += (double)dV[t];
+    sdu = fma(du, du, sdu);
+    su = fma(u, u, su);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sdu += __shfl_down_sync(0xffffffffu, sdu, o);
+    su += __shfl_down_sync(0xffffffffu, su, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = sdu;
+    red[1][warp] = su;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kAccThreads / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partial[2 * (int64_t)blockIdx.x] = a;
+    partial[2 * (int64_t)blockIdx.x + 1] = b;
+  }
 }
 
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
@@ -528,9 +558,11 @@ cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv
 }
 
 cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
-                              cudaStream_t st) {
-  k_accumulate<<<nblk(g.npad, 256), 256, 0, st>>>(g.npad, U, dU, V, dV);
-  return cudaGetLastError();
+                              double* partial, int nblocks, double* out, cudaStream_t st) {
+  k_accumulate<<<nblocks, kAccThreads, 0, st>>>(g.npad, U, dU, V, dV, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_cols(partial, nblocks, 2, out, st);
 }
 
 }  // namespace ahoc

@@ -321,3 +321,21 @@ def test_mixed_equals_fp64_3d_512():
     assert all(hist[k + 1] < 0.5 * hist[k] for k in range(imx["refine_steps"]))
     rel = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
     assert rel < TOL_MIXED, (rel, imx)
+
+
+def test_mixed_limiting_accuracy_k32():
+    # u = prod sin^2(pi x_a) sin(32 pi x_a): v = alpha Laplace u vanishes on every
+    # face, so the Schur right-hand side is at discretisation level while the
+    # interior fields are O(1e4); the refinement's residual then stops at the
+    # floor of its FP64 evaluation, and the solve ends on the size of the last
+    # correction.  It must agree with the FP64 solve all the same.
+    N = [256, 256, 256]
+    d = inputs.sample(inputs.config_problem("fourier3d_k32"), N, backend="torch", device="cuda")
+    f = d["f"].reshape(-1).contiguous()
+    u64, _ = _plan(d).solve(f, tol=1e-12)
+    umx, imx = _plan(d, prec="mixed").solve(f, tol=1e-12)
+    assert imx["status"] == 0, imx
+    k = imx["refine_steps"]
+    assert imx["refine_hist"][k] <= 1e-12 or imx["refine_du"][k - 1] <= 1e-12, imx
+    rel = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    assert rel < TOL_MIXED, (rel, imx)
