@@ -117,6 +117,12 @@ typedef struct {
                              guess is only as good as the coarse grid's discretisation and
                              the interpolation, so a coarse solve past that is wasted.
                              <= 0: automatic (AHOC_COARSE_TOL_AUTO)                         */
+  int batch;              /* [1] problems of this shape held by the plan and solved together:
+                             every launch covers all of them (one grid dimension per problem),
+                             GMRES runs in lockstep and a problem that has converged is masked
+                             out of later launches, so each result is the one a single-problem
+                             plan gives.  Per-problem arguments (alpha, data, f, u, q, y, b)
+                             hold `batch` arrays of their single-problem size back to back.  */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -139,6 +145,7 @@ typedef struct {
   double refine_hist[16]; /* AHOC_MIXED: relative Schur residual before each correction, then at exit */
   int inner_iters[16];    /* AHOC_MIXED: GMRES iterations of each correction solve              */
   double refine_du[16];   /* AHOC_MIXED: ||dU||_2 / ||U||_2 of each correction (U after it)    */
+  ahoc_status status;     /* this problem's outcome (AHOC_OK or AHOC_ENOCONV)                   */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:
@@ -149,8 +156,10 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
 
 /* Create a plan (Sec. 2.2 discretisation on the box [lo, hi]).
  *   dim      2 or 3;  N, lo, hi: host arrays of length dim, lo[a] < hi[a]
- *   alpha    device, full grid, alpha > 0 (not checked on the device)
- *   bd       host struct of device pointers (NULL = homogeneous data)
+ *   alpha    device, full grid, alpha > 0 (not checked on the device);
+ *            opts->batch grids back to back for a batched plan
+ *   bd       host struct of device pointers (NULL = homogeneous data); each
+ *            array holds opts->batch copies back to back
  *   opts     host struct (NULL = defaults)
  *   stream   a cudaStream_t (NULL = the legacy default stream)
  * Precomputes the DST twiddle tables, the per-mode tridiagonal factors of
@@ -166,7 +175,10 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
  *   f     device, full grid (boundary entries are used by M near the boundary)
  *   u     device, full grid output; boundary entries = g_D
  *   tol   relative residual of the Schur system, > 0
- *   info  host, may be NULL
+ *   info  host, may be NULL; a batched plan fills info[b] for every problem b
+ *         taking part (see ahoc_set_active)
+ * A batched plan solves the problems taking part; f and u hold one grid per
+ * problem of the plan (the others are neither read nor written).
  * Synchronises the plan's stream (it reads residual norms) and returns when
  * u is written.  AHOC_ENOCONV: u holds the solution for the best iterate. */
 ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info);
@@ -223,6 +235,21 @@ ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const double* lo, co
                                  const double* rhs, double* w, void* stream);
 
 ahoc_status ahoc_plan_destroy(ahoc_plan* p);
+
+/* Batched plans (serving) ---------------------------------------------------- */
+
+/* Replace problem b's coefficient and boundary data (single-problem sizes,
+ * device) in an existing plan, coarse levels included; the shape tables and
+ * the workspace are kept.  Synchronises the plan's stream. */
+ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd);
+
+/* Problems taking part in the next solves, matvecs and Schur right-hand
+ * sides: mask[b] != 0 (host array of ahoc_batch(p) flags; NULL = all).
+ * The others are skipped by every launch and their outputs are untouched. */
+ahoc_status ahoc_set_active(ahoc_plan* p, const int* mask);
+
+/* Number of problems a plan holds (opts.batch). */
+int ahoc_batch(const ahoc_plan* p);
 
 /* Static strings; never NULL. */
 const char* ahoc_status_string(ahoc_status s);

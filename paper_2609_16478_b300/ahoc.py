@@ -24,7 +24,8 @@ AHOC_FP64, AHOC_MIXED = 0, 1
 # every entry point declared in include/ahoc.h
 SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
            "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
-           "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc")
+           "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc", "ahoc_plan_load", "ahoc_set_active",
+           "ahoc_batch")
 
 
 class ahoc_bdata(C.Structure):
@@ -38,7 +39,8 @@ KERNEL_NAMES = ("dst_x", "dst_y", "tri", "vrhs", "urhs", "trace", "krylov", "oth
 class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double)]
+                ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
+                ("batch", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -48,7 +50,7 @@ class ahoc_info(C.Structure):
                 ("levels", C.c_int), ("coarse_iters", C.c_int),
                 ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK),
                 ("refine_steps", C.c_int), ("refine_hist", C.c_double * 16), ("inner_iters", C.c_int * 16),
-                ("refine_du", C.c_double * 16)]
+                ("refine_du", C.c_double * 16), ("status", C.c_int)]
 
 
 class AhocError(RuntimeError):
@@ -88,8 +90,13 @@ def lib():
     L.ahoc_poisson_noalloc.restype = C.c_int
     L.ahoc_n_gamma.argtypes = [C.c_void_p]
     L.ahoc_n_gamma.restype = C.c_int64
+    L.ahoc_plan_load.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(ahoc_bdata)]
+    L.ahoc_set_active.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    L.ahoc_batch.argtypes = [C.c_void_p]
+    L.ahoc_batch.restype = C.c_int
     for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
-                 "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy"):
+                 "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_plan_load",
+                 "ahoc_set_active"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -119,8 +126,10 @@ def _prec(prec) -> int:
     return int(prec)
 
 
-def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0):
+def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
+          batch=1):
     o = ahoc_opts()
+    o.batch = int(batch)
     o.coarse_tol = float(coarse_tol)
     o.timing = int(timing)
     o.levels = int(levels)
@@ -135,28 +144,46 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1
     return o
 
 
-def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1) -> int:
+def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1,
+                    batch: int = 1) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 1, levels=levels)
+    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
 
 
-class Plan:
-    """A solver plan for one grid, coefficient and boundary data (``ahoc_plan_create``).
+def _info_dict(info: "ahoc_info", st: int) -> Dict:
+    return dict(iters=info.iters, restarts=info.restarts, rel_resid=info.rel_resid,
+                ms_total=info.ms_total, ms_matvec=info.ms_matvec, status=st, launches=info.launches,
+                kernel_ms={k: info.kernel_ms[i] for i, k in enumerate(KERNEL_NAMES)},
+                kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)},
+                levels=info.levels, coarse_iters=info.coarse_iters,
+                kernel_ms_top={k: info.kernel_ms_top[i] for i, k in enumerate(KERNEL_NAMES)},
+                kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)},
+                refine_steps=info.refine_steps,
+                refine_hist=[info.refine_hist[i] for i in range(min(16, info.refine_steps + 1))],
+                inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))],
+                refine_du=[info.refine_du[i] for i in range(min(16, info.refine_steps))])
 
-    The device workspace is a torch uint8 tensor handed to the library, so
-    device memory comes from PyTorch's allocator.
+
+class Plan:
+    """A solver plan for one grid shape and ``batch`` problems of it (``ahoc_plan_create``).
+
+    With batch > 1, alpha, the boundary data, f and u hold ``batch`` arrays
+    of their single-problem size back to back, and ``solve`` returns one info
+    dict per problem.  The device workspace is a torch uint8 tensor handed to
+    the library, so device memory comes from PyTorch's allocator.
     """
 
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
-                 levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0):
+                 levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1):
         L = lib()
         self.dim = dim
+        self.batch = int(batch)
         self.N = [int(n) for n in N]
         self.lo = list(lo) if lo is not None else [0.0] * dim
         self.hi = list(hi) if hi is not None else [1.0] * dim
@@ -175,59 +202,77 @@ class Plan:
         prec = _prec(prec)
         self.prec = prec
         self.device = alpha.device
-        nb = workspace_bytes(dim, self.N, restart, prec, levels)
+        B = self.batch
+        nb = workspace_bytes(dim, self.N, restart, prec, levels, B)
+        self.workspace_bytes = nb
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
-                        _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
-        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol)
+        bd = ahoc_bdata(_ptr(g_D, B * self.nfull, "g_D"), _ptr(g_N, B * self.ngamma, "g_N"),
+                        _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"))
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
         hi_ = (C.c_double * dim)(*self.hi)
-        _check(L.ahoc_plan_create(C.byref(h), dim, n, lo_, hi_, _ptr(alpha, self.nfull, "alpha"), C.byref(bd),
+        _check(L.ahoc_plan_create(C.byref(h), dim, n, lo_, hi_, _ptr(alpha, B * self.nfull, "alpha"), C.byref(bd),
                                   C.byref(o), C.c_void_p(self.stream.cuda_stream)), "ahoc_plan_create")
         self._h = h
         assert L.ahoc_n_gamma(h) == self.ngamma
+        assert L.ahoc_batch(h) == B
+        self.active = [1] * B
 
     # -- Algorithm 1 ---------------------------------------------------------
     def solve(self, f: torch.Tensor, u: Optional[torch.Tensor] = None, tol: float = 1e-12,
-              check: bool = True) -> (torch.Tensor, Dict):
+              check: bool = True):
+        """u for f (one grid per problem of the plan); returns (u, info) with
+        info a dict, or for a batched plan a list of dicts (None for problems
+        not taking part)."""
+        B = self.batch
         if u is None:
-            u = torch.empty(self.nfull, dtype=torch.float64, device=self.device)
-        info = ahoc_info()
-        st = lib().ahoc_solve(self._h, _ptr(f, self.nfull, "f"), _ptr(u, self.nfull, "u"), float(tol),
-                              C.byref(info))
+            u = torch.empty(B * self.nfull, dtype=torch.float64, device=self.device)
+        infos = (ahoc_info * B)()
+        st = lib().ahoc_solve(self._h, _ptr(f, B * self.nfull, "f"), _ptr(u, B * self.nfull, "u"), float(tol),
+                              infos)
         if check:
             _check(st, "ahoc_solve")
-        return u, dict(iters=info.iters, restarts=info.restarts, rel_resid=info.rel_resid,
-                       ms_total=info.ms_total, ms_matvec=info.ms_matvec, status=st, launches=info.launches,
-                       kernel_ms={k: info.kernel_ms[i] for i, k in enumerate(KERNEL_NAMES)},
-                       kernel_launches={k: info.kernel_launches[i] for i, k in enumerate(KERNEL_NAMES)},
-                       levels=info.levels, coarse_iters=info.coarse_iters,
-                       kernel_ms_top={k: info.kernel_ms_top[i] for i, k in enumerate(KERNEL_NAMES)},
-                       kernel_launches_top={k: info.kernel_launches_top[i] for i, k in enumerate(KERNEL_NAMES)},
-                       refine_steps=info.refine_steps,
-                       refine_hist=[info.refine_hist[i] for i in range(min(16, info.refine_steps + 1))],
-                       inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))],
-                       refine_du=[info.refine_du[i] for i in range(min(16, info.refine_steps))])
+        out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
+        return u, (out[0] if B == 1 else out)
+
+    def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None):
+        """Replace problem b's coefficient and boundary data (``ahoc_plan_load``)."""
+        bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
+                        _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
+        _check(lib().ahoc_plan_load(self._h, int(b), _ptr(alpha, self.nfull, "alpha"), C.byref(bd)), "ahoc_plan_load")
+
+    def set_active(self, mask: Sequence[int]):
+        """Problems taking part in the next calls (``ahoc_set_active``)."""
+        m = [1 if v else 0 for v in mask]
+        if len(m) != self.batch:
+            raise ValueError("mask needs %d entries" % self.batch)
+        _check(lib().ahoc_set_active(self._h, (C.c_int * self.batch)(*m)), "ahoc_set_active")
+        self.active = m
 
     def matvec(self, q: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        n = self.batch * self.ngamma
         if y is None:
-            y = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
-        _check(lib().ahoc_matvec(self._h, _ptr(q, self.ngamma, "q"), _ptr(y, self.ngamma, "y")), "ahoc_matvec")
+            y = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(lib().ahoc_matvec(self._h, _ptr(q, n, "q"), _ptr(y, n, "y")), "ahoc_matvec")
         return y
 
     def schur_rhs(self, f: torch.Tensor, b: Optional[torch.Tensor] = None) -> torch.Tensor:
+        n = self.batch * self.ngamma
         if b is None:
-            b = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
-        _check(lib().ahoc_schur_rhs(self._h, _ptr(f, self.nfull, "f"), _ptr(b, self.ngamma, "b")), "ahoc_schur_rhs")
+            b = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(lib().ahoc_schur_rhs(self._h, _ptr(f, self.batch * self.nfull, "f"), _ptr(b, n, "b")),
+               "ahoc_schur_rhs")
         return b
 
     def last_qv(self, with_v: bool = True):
-        q = torch.empty(self.ngamma, dtype=torch.float64, device=self.device)
-        v = torch.empty(self.nfull, dtype=torch.float64, device=self.device) if with_v else None
-        _check(lib().ahoc_last_qv(self._h, _ptr(q, self.ngamma, "q"), _ptr(v, self.nfull, "v")), "ahoc_last_qv")
+        B = self.batch
+        q = torch.empty(B * self.ngamma, dtype=torch.float64, device=self.device)
+        v = torch.empty(B * self.nfull, dtype=torch.float64, device=self.device) if with_v else None
+        _check(lib().ahoc_last_qv(self._h, _ptr(q, B * self.ngamma, "q"), _ptr(v, B * self.nfull, "v")),
+               "ahoc_last_qv")
         return q, v
 
     # -- components -------------------------------------------------------------

@@ -2,7 +2,10 @@
 //
 // Reductions are deterministic: every block writes one partial per column in
 // a fixed order (warp shuffles, then shared memory), and a second kernel sums
-// the partials of each column in block order.
+// the partials of each column in block order.  A batch of problems runs in
+// one launch (the problem on the last grid dimension, each problem's vectors
+// at its own stride); the block split depends on the vector length only, so
+// a problem's sums are the same bits alone and in a batch.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -23,7 +26,12 @@ constexpr int kCols = 4;
 
 __global__ void __launch_bounds__(kDotThreads) k_mdot(const double* __restrict__ V, int64_t ld, int ncols,
                                                       const double* __restrict__ w, int64_t n,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial, BatchDot bd) {
+  const int bi = blockIdx.z;
+  if (bd.act && !bd.act[bi]) return;
+  V += (int64_t)bi * bd.vstride;
+  w += (int64_t)bi * bd.wstride;
+  partial += (int64_t)bi * bd.pstride;
   __shared__ double red[kCols][kDotThreads / 32];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
@@ -55,7 +63,11 @@ __global__ void __launch_bounds__(kDotThreads) k_mdot(const double* __restrict__
 }
 
 // out[c] = sum_b partial[b * ncols + c]: one warp per column, fixed order
-__global__ void k_reduce_cols(const double* __restrict__ partial, int nblocks, int ncols, double* __restrict__ out) {
+__global__ void k_reduce_cols(const double* __restrict__ partial, int nblocks, int ncols, double* __restrict__ out,
+                              int64_t pstride, int64_t ostride, const int* act) {
+  if (act && !act[blockIdx.y]) return;
+  partial += (int64_t)blockIdx.y * pstride;
+  out += (int64_t)blockIdx.y * ostride;
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= ncols) return;
@@ -66,44 +78,57 @@ __global__ void k_reduce_cols(const double* __restrict__ partial, int nblocks, i
 }
 
 __global__ void k_gemv_sub(const double* __restrict__ V, int64_t ld, int ncols, const double* __restrict__ h,
-                           double* __restrict__ w, int64_t n) {
+                           double* __restrict__ w, int64_t n, BatchDot bd, int64_t hstride, const int* ncols_b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int bi = blockIdx.y;
+  if (i >= n || (bd.act && !bd.act[bi])) return;
+  if (ncols_b) ncols = ncols_b[bi];
+  V += (int64_t)bi * bd.vstride;
+  w += (int64_t)bi * bd.wstride;
+  h += (int64_t)bi * hstride;
   double acc = w[i];
   for (int c = 0; c < ncols; ++c) acc = fma(-V[(int64_t)c * ld + i], h[c], acc);
   w[i] = acc;
 }
 
-__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n,
+                        const double* __restrict__ a_b, const int* act, int64_t ystride, int64_t xstride) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int bi = blockIdx.y;
+  if (i >= n || (act && !act[bi])) return;
+  if (a_b) a = a_b[bi];
+  y += (int64_t)bi * ystride;
+  x += (int64_t)bi * xstride;
   y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
 // out[c] = <V_c, w> for c < ncols: block partials into `partial` (capacity
 // nblocks * ncols), then a fixed-order reduction per column into out
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
-                        int nblocks, double* out, cudaStream_t st) {
+                        int nblocks, double* out, cudaStream_t st, int nbat, const BatchDot& bd, int64_t ostride) {
   const int64_t want = (n + 4095) / 4096;
   const int nb = (int)(want < 1 ? 1 : (want > nblocks ? nblocks : want));
-  dim3 grid(nb, (ncols + kCols - 1) / kCols);
-  k_mdot<<<grid, kDotThreads, 0, st>>>(V, ld, ncols, w, n, partial);
+  dim3 grid(nb, (ncols + kCols - 1) / kCols, nbat);
+  k_mdot<<<grid, kDotThreads, 0, st>>>(V, ld, ncols, w, n, partial, bd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nb, ncols, out);
+  k_reduce_cols<<<dim3((ncols + 7) / 8, nbat), 256, 0, st>>>(partial, nb, ncols, out, bd.pstride, ostride, bd.act);
   return cudaGetLastError();
 }
 cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st) {
-  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nblocks, ncols, out);
+  k_reduce_cols<<<(ncols + 7) / 8, 256, 0, st>>>(partial, nblocks, ncols, out, 0, 0, nullptr);
   return cudaGetLastError();
 }
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
-                            cudaStream_t st) {
-  k_gemv_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, ld, ncols, h, w, n);
+                            cudaStream_t st, int nbat, const BatchDot& bd, int64_t hstride, const int* ncols_b) {
+  k_gemv_sub<<<dim3((unsigned)((n + 255) / 256), nbat), 256, 0, st>>>(V, ld, ncols, h, w, n, bd, hstride, ncols_b);
   return cudaGetLastError();
 }
-cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st) {
-  k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, x, a, b, n);
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st, int nbat,
+                         const double* a_b, const int* act, int64_t ystride, int64_t xstride) {
+  if (ystride < 0) ystride = n;
+  if (xstride < 0) xstride = n;
+  k_axpby<<<dim3((unsigned)((n + 255) / 256), nbat), 256, 0, st>>>(y, x, a, b, n, a_b, act, ystride, xstride);
   return cudaGetLastError();
 }
 

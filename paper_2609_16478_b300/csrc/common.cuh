@@ -27,6 +27,15 @@ struct Geom {
   int64_t ngamma;
   int kmin, kmax;     // layers holding interior points: 3D [1, N2), 2D [0, 1)
   int64_t nint;       // interior points
+  // Batch of nb problems of this shape: every per-problem array holds nb
+  // copies back to back (fields npad apart, full-grid arrays nfull apart,
+  // face arrays ngamma apart); kernels take the problem from a grid
+  // dimension.  act (device, nb flags; NULL = all) masks problems out of a
+  // launch: their blocks return at once.
+  int nb;
+  const int* act;
+
+  __host__ __device__ inline bool skip(int b) const { return act != nullptr && act[b] == 0; }
 
   __host__ __device__ inline int64_t pad(int i, int j, int k) const { return i + n0 * (j + n1 * (int64_t)k); }
   __host__ __device__ inline int64_t full(int i, int j, int k) const { return i + f0 * (j + f1 * (int64_t)k); }

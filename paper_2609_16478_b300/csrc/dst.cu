@@ -238,6 +238,13 @@ template <typename T, int LOAD, int STORE>
 __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<T> io,
                                                const typename Cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ sn, T scale, int logN, int TPL, int LPC) {
+  const int bi = blockIdx.y;  // problem of the batch
+  if (g.skip(bi)) return;
+  a += (int64_t)bi * g.npad;
+  if (io.src) io.src += (int64_t)bi * g.npad;
+  if (io.src2) io.src2 += (int64_t)bi * g.npad;
+  if (io.qa) io.qa += (int64_t)bi * g.ngamma;
+  if (io.ainv) io.ainv += (int64_t)bi * g.nfull;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   T* wsum = s + (int64_t)LPC * g.n0;
@@ -313,6 +320,9 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
 template <typename T>
 __global__ void __launch_bounds__(512) k_dst_y(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ sn, T scale, int logN, int TPL, int LPC, int LS) {
+  const int bi = blockIdx.z;
+  if (g.skip(bi)) return;
+  a += (int64_t)bi * g.npad;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   T* wsum = s + (int64_t)LPC * LS;
@@ -348,7 +358,9 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_dst_gen(T* __restrict__ base, int nlines, int lpg, int64_t gstride,
                                                  int64_t lstride, int64_t estride, int N,
                                                  const typename Cplx<T>::t* __restrict__ tw, const T* __restrict__ sn,
-                                                 int logN, int TPL, int LPC) {
+                                                 int logN, int TPL, int LPC, int64_t bstride, const int* act) {
+  if (act && !act[blockIdx.y]) return;
+  base += (int64_t)blockIdx.y * bstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   T* wsum = s + (int64_t)LPC * N;
@@ -384,7 +396,12 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_precond_lines(double* out, const double* in, const double* __restrict__ afac,
                                                        const double* __restrict__ pre, int nlines, int64_t lstride,
                                                        int N, const typename Cplx<T>::t* __restrict__ tw,
-                                                       const T* __restrict__ sn, int logN, int TPL, int LPC) {
+                                                       const T* __restrict__ sn, int logN, int TPL, int LPC,
+                                                       int64_t bstride, const int* act) {
+  if (act && !act[blockIdx.y]) return;
+  out += (int64_t)blockIdx.y * bstride;
+  in += (int64_t)blockIdx.y * bstride;
+  afac += (int64_t)blockIdx.y * bstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   T* wsum = s + (int64_t)LPC * N;
@@ -441,7 +458,7 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
         cudaFuncSetAttribute(k_dst_x<T, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_dst_x<T, LOAD, STORE><<<(unsigned)blocks, threads, smem, st>>>(
+  k_dst_x<T, LOAD, STORE><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, smem, st>>>(
       g, dst, io, reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, scale, logN, TPL, LPC);
   return cudaGetLastError();
 }
@@ -500,7 +517,7 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
   if (LPC > g.n0) LPC = (int)g.n0;
   const int threads = TPL * LPC;
   const int LS = N + (int)(16 / sizeof(T));
-  dim3 grid((unsigned)((g.n0 + LPC - 1) / LPC), (unsigned)(g.kmax - g.kmin));
+  dim3 grid((unsigned)((g.n0 + LPC - 1) / LPC), (unsigned)(g.kmax - g.kmin), (unsigned)g.nb);
   const size_t smem = ((size_t)LPC * LS + 32) * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_dst_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -513,7 +530,7 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
 
 template <typename T>
 cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_t lstride, int64_t estride, int N,
-                           const void* tw, const T* sn, cudaStream_t st) {
+                           const void* tw, const T* sn, cudaStream_t st, int nb, int64_t bstride, const int* act) {
   const int logN = ilog2(N);
   const int TPL = N / 8;
   const int LPC = TPL >= 512 ? 1 : 512 / TPL;
@@ -524,18 +541,20 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
     cudaError_t e = cudaFuncSetAttribute(k_dst_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_dst_gen<T><<<blocks, threads, smem, st>>>(base, nlines, lpg, gstride, lstride, estride, N,
-                                               reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, logN, TPL, LPC);
+  k_dst_gen<T><<<dim3(blocks, nb), threads, smem, st>>>(base, nlines, lpg, gstride, lstride, estride, N,
+                                                         reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, logN,
+                                                         TPL, LPC, bstride, act);
   return cudaGetLastError();
 }
 template cudaError_t launch_dst_gen<double>(double*, int, int, int64_t, int64_t, int64_t, int, const void*,
-                                            const double*, cudaStream_t);
+                                            const double*, cudaStream_t, int, int64_t, const int*);
 template cudaError_t launch_dst_gen<float>(float*, int, int, int64_t, int64_t, int64_t, int, const void*, const float*,
-                                           cudaStream_t);
+                                           cudaStream_t, int, int64_t, const int*);
 
 template <typename T>
 cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
-                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st) {
+                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st, int nb,
+                                 int64_t bstride, const int* act) {
   const int logN = ilog2(N);
   const int TPL = N / 8;
   const int LPC = TPL >= 512 ? 1 : 512 / TPL;
@@ -546,15 +565,17 @@ cudaError_t launch_precond_lines(double* out, const double* in, const double* af
     cudaError_t e = cudaFuncSetAttribute(k_precond_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_precond_lines<T><<<blocks, threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,
-                                                    reinterpret_cast<const typename Cplx<T>::t*>(tw), sn, logN, TPL,
-                                                    LPC);
+  k_precond_lines<T><<<dim3(blocks, nb), threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,
+                                                               reinterpret_cast<const typename Cplx<T>::t*>(tw), sn,
+                                                               logN, TPL, LPC, bstride, act);
   return cudaGetLastError();
 }
 template cudaError_t launch_precond_lines<float>(double*, const double*, const double*, const double*, int, int64_t,
-                                                 int, const void*, const float*, cudaStream_t);
+                                                 int, const void*, const float*, cudaStream_t, int, int64_t,
+                                                 const int*);
 template cudaError_t launch_precond_lines<double>(double*, const double*, const double*, const double*, int, int64_t,
-                                                  int, const void*, const double*, cudaStream_t);
+                                                  int, const void*, const double*, cudaStream_t, int, int64_t,
+                                                  const int*);
 
 template cudaError_t launch_dst_x<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);
 template cudaError_t launch_dst_y<double>(const Geom&, double*, const void*, const double*, double, cudaStream_t);

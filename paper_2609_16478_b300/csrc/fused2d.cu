@@ -22,6 +22,14 @@ __global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, const
                            T* __restrict__ rxm, T* __restrict__ rxp, T* __restrict__ qy, T* __restrict__ qa) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N0 = g.N[0], N1 = g.N[1];
+  const int bi = blockIdx.y;
+  if (g.skip(bi)) return;
+  Q += (int64_t)bi * g.ngamma;
+  afinv += (int64_t)bi * g.ngamma;
+  qa += (int64_t)bi * g.ngamma;
+  rxm += (int64_t)bi * (N1 + 1);
+  rxp += (int64_t)bi * (N1 + 1);
+  qy += (int64_t)bi * 2 * N0;
   if (t < g.ngamma) qa[t] = (T)(Q[t] * afinv[t]);
   if (t <= N1) {
     const int j = t;
@@ -56,6 +64,16 @@ __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __res
   __shared__ double red[2][kRowThreads / 32];
   const int j = blockIdx.x + 1;
   const int N0 = g.N[0];
+  const int bi = blockIdx.y;
+  if (g.skip(bi)) return;
+  {
+    const int64_t fo = (int64_t)bi * g.ngamma;
+    y += fo;
+    Uh += (int64_t)bi * g.npad;
+    if (Q) Q += fo;
+    afac += fo;
+    if (srcq) srcq += fo;
+  }
   const T* row = Uh + g.pad(0, j, 0);
   T part = 0;  // k = 1 + tid + 256 m has the parity of 1 + tid; at most N0/256 terms in T
   for (int k = 1 + threadIdx.x; k < N0; k += kRowThreads) part += row[k] * tau[k];
@@ -91,7 +109,10 @@ template <typename T>
 __global__ void k_trace2d_ylines(Geom g, Coefs cf, T* __restrict__ R, const T* __restrict__ Uh) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0], N1 = g.N[1];
-  if (k >= N0) return;
+  const int bi = blockIdx.y;
+  if (k >= N0 || g.skip(bi)) return;
+  R += (int64_t)bi * 2 * N0;
+  Uh += (int64_t)bi * g.npad;
   const T w1 = (T)cf.w[1][1], w2 = (T)cf.w[1][2], w3 = (T)cf.w[1][3];
   R[k - 1] = w1 * Uh[g.pad(k, 1, 0)] + w2 * Uh[g.pad(k, 2, 0)] + w3 * Uh[g.pad(k, 3, 0)];
   R[(N0 - 1) + k - 1] = w1 * Uh[g.pad(k, N1 - 1, 0)] + w2 * Uh[g.pad(k, N1 - 2, 0)] + w3 * Uh[g.pad(k, N1 - 3, 0)];
@@ -103,7 +124,16 @@ __global__ void k_trace2d_y(Geom g, double* __restrict__ y, const T* __restrict_
                             const double* __restrict__ srcq) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int N0 = g.N[0];
-  if (i >= N0) return;
+  const int bi = blockIdx.y;
+  if (i >= N0 || g.skip(bi)) return;
+  {
+    const int64_t fo = (int64_t)bi * g.ngamma;
+    y += fo;
+    R += (int64_t)bi * 2 * N0;
+    if (Q) Q += fo;
+    afac += fo;
+    if (srcq) srcq += fo;
+  }
   const int64_t qm = g.face(1, 0, i, 0, 0), qp = g.face(1, 1, i, g.N[1], 0);
   double ym = afac[qm] * (double)R[i - 1], yp = afac[qp] * (double)R[(N0 - 1) + i - 1];
   if (Q) {
@@ -123,24 +153,24 @@ cudaError_t launch_v2d_prep(const Geom& g, const Coefs& cf, const double* Q, con
                             T* qy, T* qa, cudaStream_t st) {
   int64_t n = (g.N[1] + 1 > 2 * (g.N[0] - 1)) ? g.N[1] + 1 : 2 * (g.N[0] - 1);
   if (g.ngamma > n) n = g.ngamma;
-  k_v2d_prep<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, cf, Q, afinv, rxm, rxp, qy, qa);
+  k_v2d_prep<T><<<dim3((unsigned)((n + 255) / 256), g.nb), 256, 0, st>>>(g, cf, Q, afinv, rxm, rxp, qy, qa);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_trace2d_x(const Geom& g, double* y, const T* Uh, const double* Q, const double* afac,
                              const T* tau, cudaStream_t st, const double* srcq) {
-  k_trace2d_x<T><<<g.N[1] - 1, kRowThreads, 0, st>>>(g, y, Uh, Q, afac, tau, srcq);
+  k_trace2d_x<T><<<dim3(g.N[1] - 1, g.nb), kRowThreads, 0, st>>>(g, y, Uh, Q, afac, tau, srcq);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_trace2d_ylines(const Geom& g, const Coefs& cf, T* R, const T* Uh, cudaStream_t st) {
-  k_trace2d_ylines<T><<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, cf, R, Uh);
+  k_trace2d_ylines<T><<<dim3((g.N[0] + 255) / 256, g.nb), 256, 0, st>>>(g, cf, R, Uh);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_trace2d_y(const Geom& g, double* y, const T* R, const double* Q, const double* afac,
                              cudaStream_t st, const double* srcq) {
-  k_trace2d_y<T><<<(g.N[0] + 255) / 256, 256, 0, st>>>(g, y, R, Q, afac, srcq);
+  k_trace2d_y<T><<<dim3((g.N[0] + 255) / 256, g.nb), 256, 0, st>>>(g, y, R, Q, afac, srcq);
   return cudaGetLastError();
 }
 

@@ -65,13 +65,17 @@ cudaError_t launch_to_float(float* out, const double* in, int64_t n, cudaStream_
 
 // DST-I of generic strided lines (see dst.cu, k_dst_gen)
 template <typename T>
+// (nb problems: base + b * bstride for problem b; act masks problems out, may be NULL)
 cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_t lstride, int64_t estride, int N,
-                           const void* tw, const T* sn, cudaStream_t st);
+                           const void* tw, const T* sn, cudaStream_t st, int nb = 1, int64_t bstride = 0,
+                           const int* act = nullptr);
 
 // Boundary preconditioner on 2D face lines, one pass (dst.cu)
 template <typename T>
+// (out, in, afac of problem b at + b * bstride; pre is shared)
 cudaError_t launch_precond_lines(double* out, const double* in, const double* afac, const double* pre, int nlines,
-                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st);
+                                 int64_t lstride, int N, const void* tw, const T* sn, cudaStream_t st, int nb = 1,
+                                 int64_t bstride = 0, const int* act = nullptr);
 
 // Boundary preconditioner (precond.cu)
 struct SymAxis {
@@ -80,9 +84,11 @@ struct SymAxis {
 };
 cudaError_t launch_face_symbols(const Geom& g, const Coefs& cf, double* pre, const double* const* stab,
                                 const double* const* ctab, cudaStream_t st);
-// out[q] = in[q] * (mul ? mul[q] : 1) / (div ? div[q] : 1)
+// out[q] = in[q] * (mul ? mul[q] : 1) / (div ? div[q] : 1); nb problems of n
+// entries each, mul and div advancing by mstride / dstride per problem (0: shared)
 cudaError_t launch_face_muldiv(double* out, const double* in, const double* mul, const double* div, int64_t n,
-                               cudaStream_t st);
+                               cudaStream_t st, int nb = 1, int64_t mstride = 0, int64_t dstride = 0,
+                               const int* act = nullptr);
 
 // chunked tridiagonal solve (2D: few columns, many chunks per column)
 // modes: the element-wise factors (precision T); md64: the FP64 factors used
@@ -117,8 +123,9 @@ cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
                             cudaStream_t st);
-// U += dU, V += dV; out[0] = sum dU^2, out[1] = sum U^2 after the update
-// (deterministic: nblocks fixed partials in `partial`, 2 * nblocks doubles)
+// U += dU, V += dV; for problem b, out[2b] = sum dU^2 and out[2b + 1] = sum U^2
+// after the update (deterministic: nblocks fixed partials per problem in
+// `partial`, 2 * nb * nblocks doubles)
 cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
                               double* partial, int nblocks, double* out, cudaStream_t st);
 
@@ -135,17 +142,30 @@ cudaError_t launch_inject_full(const Geom& gc, const Geom& gf, double* out, cons
 cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st);
 cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st);
 
-// GMRES level-1/2 kernels on face vectors (FP64).
+// GMRES level-1/2 kernels on face vectors (FP64), over a batch of nbat
+// problems: problem b's V, w and partials start at b * vstride, wstride,
+// pstride; act masks problems out (NULL: all).
+struct BatchDot {
+  int64_t vstride = 0, wstride = 0, pstride = 0;
+  const int* act = nullptr;
+};
 // out[c] = <V_c, w>, c < ncols (deterministic two-stage reduction through
-// `partial`, which holds nblocks * ncols doubles)
+// `partial`, which holds nblocks * ncols doubles per problem); problem b's
+// results at out + b * ostride
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
-                        int nblocks, double* out, cudaStream_t st);
+                        int nblocks, double* out, cudaStream_t st, int nbat = 1, const BatchDot& bd = BatchDot{},
+                        int64_t ostride = 0);
 // out[c] = sum_b partial[b * ncols + c] in block order
 cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st);
-// w -= V h (h on device, ncols entries)
+// w -= V h (h on device, ncols entries; problem b's h at + b * hstride and,
+// when ncols_b is set, ncols_b[b] columns)
 cudaError_t launch_gemv_sub(const double* V, int64_t ld, int ncols, const double* h, double* w, int64_t n,
-                            cudaStream_t st);
-// y = a * x (+ y if accumulate)
-cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
+                            cudaStream_t st, int nbat = 1, const BatchDot& bd = BatchDot{}, int64_t hstride = 0,
+                            const int* ncols_b = nullptr);
+// y = a * x + b * y (b == 0: y = a * x); nbat problems of n entries, problem
+// b's y and x at + b * ystride, xstride (-1: n), a taken from a_b[b] when set
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st, int nbat = 1,
+                         const double* a_b = nullptr, const int* act = nullptr, int64_t ystride = -1,
+                         int64_t xstride = -1);
 
 }  // namespace ahoc

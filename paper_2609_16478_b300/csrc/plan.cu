@@ -47,6 +47,7 @@ struct Opts {
   int levels = -1;  // coarse levels of the nested initial guess (-1: automatic)
   double refine_tol = 3e-6;  // mixed precision: relative residual of each FP32 correction solve
   double coarse_tol = AHOC_COARSE_TOL_AUTO;  // relative Schur residual of the coarse levels
+  int batch = 1;  // problems of this shape solved together
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -62,6 +63,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.levels = o->levels;
     if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
     if (o->coarse_tol > 0) d.coarse_tol = o->coarse_tol;
+    if (o->batch > 0) d.batch = o->batch;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -69,6 +71,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
   if (d.prec == AHOC_MIXED) d.levels = 0;  // the nested initial guess belongs to the FP64 path
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
+  if (d.batch > 4096) return fail(AHOC_EINVAL, "batch > 4096");
   if (d.levels < -1 || d.levels > 8) return fail(AHOC_EINVAL, "levels must be -1 (automatic) or 0..8");
   if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
     return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
@@ -115,6 +118,8 @@ ahoc_status make_geom(int dim, const int64_t* N, const double* lo, const double*
     g->face_off[2 * a + 2] = g->face_off[2 * a + 1] + s;
   }
   g->ngamma = g->face_off[6];
+  g->nb = 1;
+  g->act = nullptr;
   return AHOC_OK;
 }
 
@@ -239,7 +244,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
-      tmp, z, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau,
+      tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb,
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
@@ -260,6 +265,17 @@ bool chunked_for(const Geom& g, ahoc_precision prec) {
 
 constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 
+// per-problem sizes of the GMRES scratch: dot partials and the device side
+// of the Hessenberg column exchange
+int64_t pstride(const Opts& o) { return (int64_t)kDotBlocks * (2 * (o.restart + 1) + 2); }
+int hstride(const Opts& o) { return 2 * (o.restart + 1) + 4; }
+
+// Workspace layout.  Per-problem arrays hold g.nb copies back to back at the
+// element strides the kernels assume (fields npad, full-grid arrays nfull,
+// face arrays ngamma, the 2D generator lines N1 + 1 and 2 N0, the chunked
+// tridiagonal scratch (4C + 1) ncols); the Krylov bases are laid out
+// [column][problem][face point], so column j of every problem is one batched
+// face array.  Tables that depend on the shape alone are held once.
 Layout make_layout(const Geom& g, const Opts& o) {
   Layout L;
   size_t off = 0;
@@ -268,17 +284,19 @@ Layout make_layout(const Geom& g, const Opts& o) {
     off += align256(bytes);
     return p;
   };
+  const size_t B = (size_t)g.nb;
   const size_t fld = (size_t)g.npad * sizeof(double);
   const size_t full = (size_t)g.nfull * sizeof(double);
   const size_t face = (size_t)g.ngamma * sizeof(double);
-  L.W1 = take(fld);
-  L.W2 = take(fld);
-  L.ainv = take(full);
-  L.afac = take(face);
-  L.gD = take(full);
-  L.vedge = take(full);
-  L.gN = take(face);
-  L.lapt = take(face);
+  const size_t rxn = (size_t)g.N[1] + 1, qyn = 2 * (size_t)g.N[0];
+  L.W1 = take(B * fld);
+  L.W2 = take(B * fld);
+  L.ainv = take(B * full);
+  L.afac = take(B * face);
+  L.gD = take(B * full);
+  L.vedge = take(B * full);
+  L.gN = take(B * face);
+  L.lapt = take(B * face);
   L.twx = take(2 * (size_t)g.N[0] * sizeof(double));
   L.snx = take(((size_t)g.N[0] / 2 + 1) * sizeof(double));
   L.twy = take(2 * (size_t)g.N[1] * sizeof(double));
@@ -290,51 +308,53 @@ Layout make_layout(const Geom& g, const Opts& o) {
     L.ctab[a] = take(((size_t)g.N[a] + 1) * sizeof(double));
   }
   L.pre = take(face);
-  L.z = take(face);
-  L.tri = take(chunked_for(g, o.prec) ? tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.tri = take(chunked_for(g, o.prec) ? B * tri_chunked_scratch(g, tri_chunk_len(g)) * sizeof(double) : 0);
   // fused 2D matvec scratch
-  L.rxm = take(((size_t)g.N[1] + 1) * sizeof(double));
-  L.rxp = take(((size_t)g.N[1] + 1) * sizeof(double));
-  L.qy = take(2 * (size_t)g.N[0] * sizeof(double));
-  L.R2 = take(2 * (size_t)g.N[0] * sizeof(double));
+  L.rxm = take(B * rxn * sizeof(double));
+  L.rxp = take(B * rxn * sizeof(double));
+  L.qy = take(B * qyn * sizeof(double));
+  L.R2 = take(B * qyn * sizeof(double));
   L.tau = take(((size_t)g.N[0] + 1) * sizeof(double));
   const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
   L.modes = take(nmodes * sizeof(Mode<double>));
-  L.b = take(face);
-  L.Q = take(face);
-  L.r = take(face);
-  L.tmp = take(face);
-  L.Kry = take(face * (size_t)(o.restart + 1));
-  L.Zb = take(face * (size_t)o.restart);
-  L.afinv = take(face);
-  L.qa = take(face);
+  L.b = take(B * face);
+  L.Q = take(B * face);
+  L.r = take(B * face);
+  L.tmp = take(B * face);
+  L.Kry = take(B * face * (size_t)(o.restart + 1));
+  L.Zb = take(B * face * (size_t)o.restart);
+  L.afinv = take(B * face);
+  L.qa = take(B * face);
   L.rpow = take(chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
-  L.partial = take((size_t)kDotBlocks * (2 * (o.restart + 1) + 2) * sizeof(double));
-  L.hdev = take((size_t)(2 * (o.restart + 1) + 4) * sizeof(double));
+  L.partial = take(B * (size_t)pstride(o) * sizeof(double));
+  L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
+  L.act = take(B * sizeof(int));
+  L.scal = take(B * sizeof(double));
+  L.ncolsb = take(B * sizeof(int));
   const bool mixed = (o.prec == AHOC_MIXED);
-  const size_t ffl = mixed ? (size_t)g.npad * sizeof(float) : 0;
+  const size_t ffl = mixed ? B * (size_t)g.npad * sizeof(float) : 0;
   L.F1 = take(ffl);
   L.F2 = take(ffl);
   L.Ru = take(ffl);
   L.Rv = take(ffl);
-  L.U64 = take(mixed ? fld : 0);
-  L.V64 = take(mixed ? fld : 0);
+  L.U64 = take(mixed ? B * fld : 0);
+  L.V64 = take(mixed ? B * fld : 0);
   for (int a = 0; a < 3; ++a) {  // FP32 DST tables: mixed inner solves and the preconditioner
     L.twf[a] = take(2 * (size_t)g.N[a] * sizeof(float));
     L.snf[a] = take(((size_t)g.N[a] / 2 + 1) * sizeof(float));
   }
   L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
   L.trif = take(0);  // the chunked solve's carries are FP64 in both precisions (shared scratch L.tri)
-  L.Rq = take(mixed ? face : 0);
-  L.dQ = take(mixed ? face : 0);
-  L.b2 = take(mixed ? face : 0);
+  L.Rq = take(mixed ? B * face : 0);
+  L.dQ = take(mixed ? B * face : 0);
+  L.b2 = take(mixed ? B * face : 0);
   const size_t fface = (size_t)g.ngamma * sizeof(float);
-  L.ainvf = take(mixed ? (size_t)g.nfull * sizeof(float) : 0);
-  L.rxmf = take(mixed ? ((size_t)g.N[1] + 1) * sizeof(float) : 0);
-  L.rxpf = take(mixed ? ((size_t)g.N[1] + 1) * sizeof(float) : 0);
-  L.qyf = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
-  L.qaf = take(mixed ? fface : 0);
-  L.R2f = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
+  L.ainvf = take(mixed ? B * (size_t)g.nfull * sizeof(float) : 0);
+  L.rxmf = take(mixed ? B * rxn * sizeof(float) : 0);
+  L.rxpf = take(mixed ? B * rxn * sizeof(float) : 0);
+  L.qyf = take(mixed ? B * qyn * sizeof(float) : 0);
+  L.qaf = take(mixed ? B * fface : 0);
+  L.R2f = take(mixed ? B * qyn * sizeof(float) : 0);
   L.tauf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
   L.skf = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
   L.ckf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
@@ -369,6 +389,7 @@ size_t total_bytes(const Geom& g, const Opts& o) {
     Geom gc;
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     make_geom(g.dim, Nc, lo, hi, &gc);
+    gc.nb = g.nb;
     Opts oc = o;
     oc.levels = lv - 1;
     b += total_bytes(gc, oc);
@@ -377,6 +398,15 @@ size_t total_bytes(const Geom& g, const Opts& o) {
 }
 
 }  // namespace
+
+// Per-problem outcome of a solve.
+struct ProbStat {
+  int iters = 0, restarts = 0, coarse_iters = 0, refine_steps = 0;
+  double rel = 0.0, ms_mv = 0.0;
+  ahoc_status status = AHOC_OK;
+  double hist[16] = {0}, du[16] = {0};
+  int inner[16] = {0};
+};
 
 struct ahoc_plan {
   Geom g;
@@ -387,7 +417,7 @@ struct ahoc_plan {
   bool own_ws = false;
   Layout L;
   double *W1, *W2, *ainv, *afac, *gD = nullptr, *vedge = nullptr, *gN = nullptr, *lapt = nullptr;
-  double *twx, *snx, *twy, *sny, *twz, *snz, *b, *Q, *r, *tmp, *Kry, *partial, *hdev, *z, *pre, *tri;
+  double *twx, *snx, *twy, *sny, *twz, *snz, *b, *Q, *r, *tmp, *Kry, *partial, *hdev, *pre, *tri;
   double *stab[3], *ctab[3];
   double *rxm, *rxp, *qy, *R2, *tau;
   Mode<double>* modes;
@@ -400,10 +430,13 @@ struct ahoc_plan {
   float *ainvf = nullptr, *rxmf = nullptr, *rxpf = nullptr, *qyf = nullptr, *qaf = nullptr, *R2f = nullptr,
         *tauf = nullptr, *skf = nullptr, *ckf = nullptr;
   Mode<float>* modesf = nullptr;
-  int refine_steps = 0;
-  double refine_hist[16] = {0};
-  double refine_du[16] = {0};
-  int inner_iters[16] = {0};
+  // batch state: the device mask g.act points to `act`; act_now mirrors it
+  int* act = nullptr;
+  double* scal = nullptr;  // per-problem scalars of the batched axpy
+  int* ncolsb = nullptr;   // per-problem column counts of the batched update
+  std::vector<int> act_now, part;  // current mask; problems taking part in solves
+  std::vector<ProbStat> ps;
+  bool has_gD = false, has_vedge = false, has_gN = false, has_lapt = false;
   double* hhost = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool have_last = false;
@@ -417,7 +450,6 @@ struct ahoc_plan {
   double kms[AHOC_NK] = {0};
   int64_t kn[AHOC_NK] = {0};
   ahoc_plan* coarse = nullptr;  // next coarser level of the nested initial guess
-  int coarse_iters = 0;
   int levels = 0;
   double kms_top[AHOC_NK] = {0};  // this level only (no coarse levels)
   int64_t kn_top[AHOC_NK] = {0};
@@ -489,9 +521,10 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
 // V-solve then U-solve (Algorithm 1, two FFT-based solves); leaves V in W1, U in W2.
 ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) {
   const Geom& g = p->g;
-  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data ? p->vedge : nullptr, p->st));
+  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data && p->has_vedge ? p->vedge : nullptr, p->st));
   CKS(poisson_inplace(p, p->W1));
-  RUN(AHOC_K_URHS, launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data ? p->gD : nullptr, p->st));
+  RUN(AHOC_K_URHS,
+      launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data && p->has_gD ? p->gD : nullptr, p->st));
   CKS(poisson_inplace(p, p->W2));
   return AHOC_OK;
 }
@@ -554,7 +587,7 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
   VGen2D<T> G{A.rxm, A.rxp, A.qy, A.qy + (N0 - 1), A.sk, A.ck, (T)cf.L[16], (T)cf.L[17]};
   if (q) {
     RUN(AHOC_K_VRHS, launch_v2d_prep<T>(g, cf, q, p->afinv, A.rxm, A.rxp, A.qy, A.qa, p->st));
-    RUN(AHOC_K_VRHS, launch_dst_gen<T>(A.qy, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st));
+    RUN(AHOC_K_VRHS, launch_dst_gen<T>(A.qy, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st, g.nb, 2 * N0, g.act));
   }
   const T* qa = q ? A.qa : nullptr;
   // V-hat: L_h V = -r_v - L_bdry(q) in x-modes
@@ -582,7 +615,7 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
   }
   RUN(AHOC_K_TRACE, launch_trace2d_x<T>(g, y, A.W2, q, p->afac, A.tau, p->st, srcq));
   RUN(AHOC_K_TRACE, launch_trace2d_ylines<T>(g, cf, A.R2, A.W2, p->st));
-  RUN(AHOC_K_TRACE, launch_dst_gen<T>(A.R2, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st));
+  RUN(AHOC_K_TRACE, launch_dst_gen<T>(A.R2, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st, g.nb, 2 * N0, g.act));
   RUN(AHOC_K_TRACE, launch_trace2d_y<T>(g, y, A.R2, q, p->afac, p->st, srcq));
   return AHOC_OK;
 }
@@ -614,63 +647,105 @@ ahoc_status face_dsts(ahoc_plan* p, double* v, int a) {
   const double* sn[3] = {p->snx, p->sny, p->snz};
   if (nr == 1) {
     const int b = rem[0];
-    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2, 1, fs, 0, 1, g.N[b], tw[b], sn[b], p->st));
+    RUN(AHOC_K_KRYLOV,
+        launch_dst_gen<double>(base, 2, 1, fs, 0, 1, g.N[b], tw[b], sn[b], p->st, g.nb, g.ngamma, g.act));
   } else {
     const int b0 = rem[0], b1 = rem[1];
     const int n0 = g.N[b0] - 1, n1 = g.N[b1] - 1;
-    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n1, n1, fs, n0, 1, g.N[b0], tw[b0], sn[b0], p->st));
-    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n0, n0, fs, 1, n0, g.N[b1], tw[b1], sn[b1], p->st));
+    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n1, n1, fs, n0, 1, g.N[b0], tw[b0], sn[b0], p->st, g.nb,
+                                              g.ngamma, g.act));
+    RUN(AHOC_K_KRYLOV, launch_dst_gen<double>(base, 2 * n0, n0, fs, 1, n0, g.N[b1], tw[b1], sn[b1], p->st, g.nb,
+                                              g.ngamma, g.act));
   }
   return AHOC_OK;
 }
 
 // out = P^-1 in: the boundary-symbol preconditioner (precond.cu); in, out may alias.
 ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
-  const int64_t n = p->g.ngamma;
+  const Geom& g = p->g;
+  const int64_t n = g.ngamma;
   if (!p->o.precond) {
-    if (in != out) CK(cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    if (in != out) RUN(AHOC_K_KRYLOV, launch_axpby(out, in, 1.0, 0.0, n, p->st, g.nb, nullptr, g.act));
     return AHOC_OK;
   }
-  if (p->g.dim == 2) {
+  if (g.dim == 2) {
     // x-faces are lines of N1 - 1 points (DST length N1), y-faces of N0 - 1
-    const Geom& g = p->g;
     const int64_t ox = g.face_off[0], oy = g.face_off[2];
     if (g.N[0] == g.N[1]) {  // the four faces are four consecutive lines of equal length
       RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out, in, p->afac, p->pre, 4, g.N[0] - 1, g.N[0], p->twf[0],
-                                                     p->snf[0], p->st));
+                                                     p->snf[0], p->st, g.nb, n, g.act));
       return AHOC_OK;
     }
     RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + ox, in + ox, p->afac + ox, p->pre + ox, 2, g.N[1] - 1,
-                                                   g.N[1], p->twf[1], p->snf[1], p->st));
+                                                   g.N[1], p->twf[1], p->snf[1], p->st, g.nb, n, g.act));
     RUN(AHOC_K_KRYLOV, launch_precond_lines<float>(out + oy, in + oy, p->afac + oy, p->pre + oy, 2, g.N[0] - 1,
-                                                   g.N[0], p->twf[0], p->snf[0], p->st));
+                                                   g.N[0], p->twf[0], p->snf[0], p->st, g.nb, n, g.act));
     return AHOC_OK;
   }
-  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, in, nullptr, p->afac, n, p->st));
-  for (int a = 0; a < p->g.dim; ++a) CKS(face_dsts(p, out, a));
-  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->pre, nullptr, n, p->st));
-  for (int a = 0; a < p->g.dim; ++a) CKS(face_dsts(p, out, a));
-  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->afac, nullptr, n, p->st));
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, in, nullptr, p->afac, n, p->st, g.nb, 0, n, g.act));
+  for (int a = 0; a < g.dim; ++a) CKS(face_dsts(p, out, a));
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->pre, nullptr, n, p->st, g.nb, 0, 0, g.act));
+  for (int a = 0; a < g.dim; ++a) CKS(face_dsts(p, out, a));
+  RUN(AHOC_K_KRYLOV, launch_face_muldiv(out, out, p->afac, nullptr, n, p->st, g.nb, n, 0, g.act));
   return AHOC_OK;
 }
 
 ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
+  const Geom& g = p->g;
   CKS(solve_VU(p, nullptr, f, true));
-  RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, b, p->W2, nullptr, p->afac, p->gD, p->gN, p->lapt, p->st));
-  RUN(AHOC_K_KRYLOV, launch_axpby(b, b, -1.0, 0.0, p->g.ngamma, p->st));
+  RUN(AHOC_K_TRACE, launch_trace<double>(g, p->cf, b, p->W2, nullptr, p->afac, p->has_gD ? p->gD : nullptr,
+                                         p->has_gN ? p->gN : nullptr, p->has_lapt ? p->lapt : nullptr, p->st));
+  RUN(AHOC_K_KRYLOV, launch_axpby(b, b, -1.0, 0.0, g.ngamma, p->st, g.nb, nullptr, g.act));
   return AHOC_OK;
 }
 
-// dots: out[c] = <V_c, w>, c < ncols (device); returns via hdev+off
-ahoc_status mdot(ahoc_plan* p, const double* V, int ncols, const double* w, double* out) {
-  RUNN(AHOC_K_KRYLOV, 2, launch_mdot(V, p->g.ngamma, ncols, w, p->g.ngamma, p->partial, kDotBlocks, out, p->st));
+// dots of every active problem: out[b * hstride + c] = <V_c, w> (problem b's
+// V_c at V + b * ngamma + c * ld, its w at w + b * ngamma), c < ncols
+ahoc_status mdot(ahoc_plan* p, const double* V, int64_t ld, int ncols, const double* w, double* out) {
+  const Geom& g = p->g;
+  BatchDot bd;
+  bd.vstride = g.ngamma;
+  bd.wstride = g.ngamma;
+  bd.pstride = pstride(p->o);
+  bd.act = g.act;
+  RUNN(AHOC_K_KRYLOV, 2,
+       launch_mdot(V, ld, ncols, w, g.ngamma, p->partial, kDotBlocks, out, p->st, g.nb, bd, hstride(p->o)));
   return AHOC_OK;
 }
 
-ahoc_status fetch(ahoc_plan* p, int n) {
-  CK(cudaMemcpyAsync(p->hhost, p->hdev, n * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+// w -= V h per active problem (h at hdev + b * hstride; ncols_b: per-problem counts or NULL)
+ahoc_status gemv_sub(ahoc_plan* p, const double* V, int64_t ld, int ncols, const double* h, double* w,
+                     const int* ncols_b) {
+  const Geom& g = p->g;
+  BatchDot bd;
+  bd.vstride = g.ngamma;
+  bd.wstride = g.ngamma;
+  bd.act = g.act;
+  RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, ld, ncols, h, w, g.ngamma, p->st, g.nb, bd, hstride(p->o), ncols_b));
+  return AHOC_OK;
+}
+
+// the Hessenberg exchange area of every problem, device to host (synchronises)
+ahoc_status fetch(ahoc_plan* p) {
+  CK(cudaMemcpyAsync(p->hhost, p->hdev, (size_t)p->g.nb * hstride(p->o) * sizeof(double), cudaMemcpyDeviceToHost,
+                     p->st));
   CK(cudaStreamSynchronize(p->st));
   return harvest(p);
+}
+
+// Set the problem mask of the next launches (uploaded only when it changes;
+// the host array is pageable, so the copy has consumed it on return).
+ahoc_status set_act(ahoc_plan* p, const std::vector<int>& m) {
+  if (m == p->act_now) return AHOC_OK;
+  CK(cudaMemcpyAsync(p->act, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice, p->st));
+  p->act_now = m;
+  return AHOC_OK;
+}
+
+bool any(const std::vector<int>& m) {
+  for (int v : m)
+    if (v) return true;
+  return false;
 }
 
 bool is_fin(double x) { return std::isfinite(x); }
@@ -713,21 +788,33 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
   CKS(make_geom(dim, N, nullptr, nullptr, &g));
   Opts o;
   CKS(read_opts(opts, &o));
+  g.nb = o.batch;
   *bytes = total_bytes(g, o);
   return AHOC_OK;
 }
 
 int64_t ahoc_n_gamma(const ahoc_plan* p) { return p ? p->g.ngamma : -1; }
 
-ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi,
-                             const double* alpha, const ahoc_bdata* bd, const ahoc_opts* opts, void* stream) {
-  if (!out) return fail(AHOC_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!alpha) return fail(AHOC_EINVAL, "alpha is NULL");
+}  // extern "C"
+
+namespace {
+
+#define CKC(call)                                                                                  \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(AHOC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Shape-only part of a plan: workspace, shared tables (DST twiddles, per-mode
+// tridiagonal factors, preconditioner symbols, trace weights) and the coarse
+// levels of the nested guess; the per-problem arrays are filled by
+// plan_load.  On failure *out may hold a partial plan for the caller to destroy.
+ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi, const Opts& o,
+                       cudaStream_t stream) {
   Geom g;
   CKS(make_geom(dim, N, lo, hi, &g));
-  Opts o;
-  CKS(read_opts(opts, &o));
+  g.nb = o.batch;
+  if (g.n2 * g.nb > 65535) return fail(AHOC_EUNSUPPORTED, "batch too large for this grid (N2 * batch > 65535)");
   Coefs cf = make_coefs(g);
   std::vector<Mode<double>> modes;
   CKS(mode_table<double>(g, cf, modes));
@@ -739,30 +826,31 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
 
   ahoc_plan* p = new (std::nothrow) ahoc_plan();
   if (!p) return fail(AHOC_ENOMEM, "host allocation failed");
+  *out = p;
   p->g = g;
   p->cf = cf;
   p->o = o;
   p->L = L;
-  p->st = reinterpret_cast<cudaStream_t>(stream);
+  p->st = stream;
   if (o.workspace) {
     p->ws = reinterpret_cast<char*>(o.workspace);
   } else {
     cudaError_t e = cudaMalloc(&p->ws, L.total);
     if (e != cudaSuccess) {
-      delete p;
+      p->ws = nullptr;
       cudaGetLastError();
       return fail(AHOC_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
     }
     p->own_ws = true;
   }
-  auto cleanup = [&](ahoc_status s) {
-    ahoc_plan_destroy(p);
-    return s;
-  };
   p->W1 = at<double>(p, L.W1);
   p->W2 = at<double>(p, L.W2);
   p->ainv = at<double>(p, L.ainv);
   p->afac = at<double>(p, L.afac);
+  p->gD = at<double>(p, L.gD);
+  p->vedge = at<double>(p, L.vedge);
+  p->gN = at<double>(p, L.gN);
+  p->lapt = at<double>(p, L.lapt);
   p->twx = at<double>(p, L.twx);
   p->snx = at<double>(p, L.snx);
   p->twy = at<double>(p, L.twy);
@@ -772,19 +860,32 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   for (int a = 0; a < 3; ++a) {
     p->stab[a] = at<double>(p, L.stab[a]);
     p->ctab[a] = at<double>(p, L.ctab[a]);
+    p->twf[a] = at<float>(p, L.twf[a]);
+    p->snf[a] = at<float>(p, L.snf[a]);
   }
   p->pre = at<double>(p, L.pre);
-  p->z = at<double>(p, L.z);
   p->tri = at<double>(p, L.tri);
   p->rxm = at<double>(p, L.rxm);
   p->rxp = at<double>(p, L.rxp);
   p->qy = at<double>(p, L.qy);
   p->R2 = at<double>(p, L.R2);
   p->tau = at<double>(p, L.tau);
-  for (int a = 0; a < 3; ++a) {
-    p->twf[a] = at<float>(p, L.twf[a]);
-    p->snf[a] = at<float>(p, L.snf[a]);
-  }
+  p->modes = at<Mode<double>>(p, L.modes);
+  p->b = at<double>(p, L.b);
+  p->Q = at<double>(p, L.Q);
+  p->r = at<double>(p, L.r);
+  p->tmp = at<double>(p, L.tmp);
+  p->Kry = at<double>(p, L.Kry);
+  p->Zb = at<double>(p, L.Zb);
+  p->afinv = at<double>(p, L.afinv);
+  p->qa = at<double>(p, L.qa);
+  p->rpow = at<double>(p, L.rpow);
+  p->partial = at<double>(p, L.partial);
+  p->hdev = at<double>(p, L.hdev);
+  p->act = at<int>(p, L.act);
+  p->scal = at<double>(p, L.scal);
+  p->ncolsb = at<int>(p, L.ncolsb);
+  p->g.act = p->act;
   if (o.prec == AHOC_MIXED) {
     p->F1 = at<float>(p, L.F1);
     p->F2 = at<float>(p, L.F2);
@@ -797,18 +898,6 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     p->Rq = at<double>(p, L.Rq);
     p->dQ = at<double>(p, L.dQ);
     p->b2 = at<double>(p, L.b2);
-  }
-  p->modes = at<Mode<double>>(p, L.modes);
-  p->b = at<double>(p, L.b);
-  p->Q = at<double>(p, L.Q);
-  p->r = at<double>(p, L.r);
-  p->tmp = at<double>(p, L.tmp);
-  p->Kry = at<double>(p, L.Kry);
-  p->Zb = at<double>(p, L.Zb);
-  p->afinv = at<double>(p, L.afinv);
-  p->qa = at<double>(p, L.qa);
-  p->rpow = at<double>(p, L.rpow);
-  if (o.prec == AHOC_MIXED) {
     p->ainvf = at<float>(p, L.ainvf);
     p->rxmf = at<float>(p, L.rxmf);
     p->rxpf = at<float>(p, L.rxpf);
@@ -819,23 +908,23 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     p->skf = at<float>(p, L.skf);
     p->ckf = at<float>(p, L.ckf);
   }
-  p->partial = at<double>(p, L.partial);
-  p->hdev = at<double>(p, L.hdev);
+  const size_t B = (size_t)g.nb;
   const size_t fld = (size_t)g.npad * sizeof(double);
   const size_t full = (size_t)g.nfull * sizeof(double);
   const size_t face = (size_t)g.ngamma * sizeof(double);
-  cudaError_t e;
-#define CKC(call)                                                                                        \
-  do {                                                                                                   \
-    e = (call);                                                                                          \
-    if (e != cudaSuccess)                                                                                \
-      return cleanup(fail(AHOC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e)));               \
-  } while (0)
-  CKC(cudaMallocHost(&p->hhost, (size_t)(2 * (o.restart + 1) + 4) * sizeof(double)));
+  p->part.assign(g.nb, 1);
+  p->ps.assign(g.nb, ProbStat{});
+  CKC(cudaMallocHost(&p->hhost, B * (size_t)hstride(o) * sizeof(double)));
   CKC(cudaEventCreate(&p->ev0));
   CKC(cudaEventCreate(&p->ev1));
-  CKC(cudaMemsetAsync(p->W1, 0, fld, p->st));
-  CKC(cudaMemsetAsync(p->W2, 0, fld, p->st));
+  // zero padding of the fields and zero boundary data until a problem brings its own
+  CKC(cudaMemsetAsync(p->W1, 0, B * fld, p->st));
+  CKC(cudaMemsetAsync(p->W2, 0, B * fld, p->st));
+  CKC(cudaMemsetAsync(p->gD, 0, B * full, p->st));
+  CKC(cudaMemsetAsync(p->vedge, 0, B * full, p->st));
+  CKC(cudaMemsetAsync(p->gN, 0, B * face, p->st));
+  CKC(cudaMemsetAsync(p->lapt, 0, B * face, p->st));
+  CKS(set_act(p, p->part));
   std::vector<double> tw, sn;
   dst_tables(g.N[0], tw, sn);
   CKC(cudaMemcpyAsync(p->twx, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
@@ -848,8 +937,8 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   CKC(cudaStreamSynchronize(p->st));
   if (o.prec == AHOC_MIXED) {
     const size_t ffl = (size_t)g.npad * sizeof(float);
-    CKC(cudaMemsetAsync(p->F1, 0, ffl, p->st));
-    CKC(cudaMemsetAsync(p->F2, 0, ffl, p->st));
+    CKC(cudaMemsetAsync(p->F1, 0, B * ffl, p->st));
+    CKC(cudaMemsetAsync(p->F2, 0, B * ffl, p->st));
     CKC(cudaMemcpyAsync(p->modesf, modesf.data(), modesf.size() * sizeof(Mode<float>), cudaMemcpyHostToDevice,
                         p->st));
   }
@@ -890,12 +979,8 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     CKC(cudaMemcpyAsync(p->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
     CKC(cudaStreamSynchronize(p->st));
   }
-  CKC(launch_recip(p->ainv, alpha, g.nfull, p->st));
-  CKC(launch_face_gather(g, p->afac, alpha, p->st));
-  CKC(launch_recip(p->afinv, p->afac, g.ngamma, p->st));
   if (chunked_for(g, o.prec)) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
   if (o.prec == AHOC_MIXED) {
-    CKC(launch_to_float(p->ainvf, p->ainv, g.nfull, p->st));
     CKC(launch_to_float(p->tauf, p->tau, g.N[0] + 1, p->st));
     CKC(launch_to_float(p->skf, p->stab[0], 2 * (int64_t)g.N[0], p->st));
     CKC(launch_to_float(p->ckf, p->ctab[0], g.N[0] + 1, p->st));
@@ -905,25 +990,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     const double* ctp[3] = {p->ctab[0], p->ctab[1], g.dim == 3 ? p->ctab[2] : nullptr};
     CKC(launch_face_symbols(g, cf, p->pre, stp, ctp, p->st));
   }
-  if (bd && bd->g_D) {
-    p->gD = at<double>(p, L.gD);
-    CKC(cudaMemcpyAsync(p->gD, bd->g_D, full, cudaMemcpyDeviceToDevice, p->st));
-  }
-  if (bd && bd->v_edge) {
-    p->vedge = at<double>(p, L.vedge);
-    CKC(cudaMemcpyAsync(p->vedge, bd->v_edge, full, cudaMemcpyDeviceToDevice, p->st));
-  }
-  if (bd && bd->g_N) {
-    p->gN = at<double>(p, L.gN);
-    CKC(cudaMemcpyAsync(p->gN, bd->g_N, face, cudaMemcpyDeviceToDevice, p->st));
-  }
-  if (bd && bd->lapt_gD) {
-    p->lapt = at<double>(p, L.lapt);
-    CKC(cudaMemcpyAsync(p->lapt, bd->lapt_gD, face, cudaMemcpyDeviceToDevice, p->st));
-  }
   CKC(cudaStreamSynchronize(p->st));
-  // coarse level for the nested initial guess: data injected into temporaries
-  // carved from this level's field buffers, then copied by the coarse plan
   const int lv = coarse_levels(g, o.levels);
   if (lv > 0) {
     int64_t Nc[3];
@@ -933,44 +1000,119 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
       lo_[a] = lo ? lo[a] : 0.0;
       hi_[a] = hi ? hi[a] : 1.0;
     }
-    Geom gc;
-    {
-      ahoc_status sg = make_geom(dim, Nc, lo_, hi_, &gc);
-      if (sg != AHOC_OK) return cleanup(sg);
+    Opts oc = o;
+    oc.levels = lv - 1;
+    oc.workspace = o.workspace ? (void*)(p->ws + L.total) : nullptr;
+    oc.workspace_bytes = o.workspace ? o.workspace_bytes - L.total : 0;
+    CKS(plan_alloc(&p->coarse, dim, Nc, lo_, hi_, oc, stream));
+    p->levels = lv;
+  }
+  return AHOC_OK;
+}
+
+// Problem b's coefficient and boundary data (device, single-problem sizes):
+// 1/alpha, the face alpha and its inverse, the FP32 copies of the mixed
+// path, the data arrays (zero where bd gives none) and, recursively, the
+// injected data of the coarse levels.
+ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd) {
+  Geom g = p->g;
+  g.nb = 1;
+  g.act = nullptr;
+  const size_t full = (size_t)g.nfull * sizeof(double);
+  const size_t face = (size_t)g.ngamma * sizeof(double);
+  const int64_t pf = (int64_t)b * g.nfull, pg = (int64_t)b * g.ngamma, pp = (int64_t)b * g.npad;
+  CKC(launch_recip(p->ainv + pf, alpha, g.nfull, p->st));
+  CKC(launch_face_gather(g, p->afac + pg, alpha, p->st));
+  CKC(launch_recip(p->afinv + pg, p->afac + pg, g.ngamma, p->st));
+  if (p->o.prec == AHOC_MIXED) CKC(launch_to_float(p->ainvf + pf, p->ainv + pf, g.nfull, p->st));
+  auto put = [&](double* dst, const double* src, size_t bytes, bool& flag) -> ahoc_status {
+    if (src) {
+      CKC(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, p->st));
+      flag = true;
+    } else {
+      CKC(cudaMemsetAsync(dst, 0, bytes, p->st));
     }
-    double* a_c = p->W1;
-    double* gD_c = bd && bd->g_D ? p->W2 : nullptr;
-    double* vE_c = bd && bd->v_edge ? p->W2 + gc.nfull : nullptr;
-    double* gN_c = bd && bd->g_N ? p->b : nullptr;
-    double* lt_c = bd && bd->lapt_gD ? p->r : nullptr;
+    return AHOC_OK;
+  };
+  CKS(put(p->gD + pf, bd ? bd->g_D : nullptr, full, p->has_gD));
+  CKS(put(p->vedge + pf, bd ? bd->v_edge : nullptr, full, p->has_vedge));
+  CKS(put(p->gN + pg, bd ? bd->g_N : nullptr, face, p->has_gN));
+  CKS(put(p->lapt + pg, bd ? bd->lapt_gD : nullptr, face, p->has_lapt));
+  if (p->coarse) {
+    // coarse data by injection, staged in this problem's field and face buffers
+    Geom gc = p->coarse->g;
+    gc.nb = 1;
+    gc.act = nullptr;
+    double* a_c = p->W1 + pp;
+    double* gD_c = bd && bd->g_D ? p->W2 + pp : nullptr;
+    double* vE_c = bd && bd->v_edge ? p->W2 + pp + gc.nfull : nullptr;
+    double* gN_c = bd && bd->g_N ? p->b + pg : nullptr;
+    double* lt_c = bd && bd->lapt_gD ? p->r + pg : nullptr;
     CKC(launch_inject_full(gc, g, a_c, alpha, p->st));
     if (gD_c) CKC(launch_inject_full(gc, g, gD_c, bd->g_D, p->st));
     if (vE_c) CKC(launch_inject_full(gc, g, vE_c, bd->v_edge, p->st));
     if (gN_c) CKC(launch_inject_face(gc, g, gN_c, bd->g_N, p->st));
     if (lt_c) CKC(launch_inject_face(gc, g, lt_c, bd->lapt_gD, p->st));
     ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c};
-    ahoc_opts oc;
-    std::memset(&oc, 0, sizeof(oc));
-    oc.prec = o.prec;
-    oc.max_iters = o.max_iters;
-    oc.restart = o.restart;
-    oc.precond = o.precond;
-    oc.timing = o.timing;
-    oc.levels = lv - 1;
-    oc.coarse_tol = o.coarse_tol;
-    oc.workspace = o.workspace ? (void*)(p->ws + L.total) : nullptr;
-    oc.workspace_bytes = o.workspace ? o.workspace_bytes - L.total : 0;
-    ahoc_status sc = ahoc_plan_create(&p->coarse, dim, Nc, lo_, hi_, a_c, &bc, &oc, stream);
-    if (sc != AHOC_OK) return cleanup(sc);
-    p->levels = lv;
-    CKC(cudaMemsetAsync(p->W1, 0, fld, p->st));
-    CKC(cudaMemsetAsync(p->W2, 0, fld, p->st));
+    CKS(plan_load(p->coarse, b, a_c, &bc));
     CKC(cudaStreamSynchronize(p->st));
+    CKC(cudaMemsetAsync(p->W1 + pp, 0, (size_t)g.npad * sizeof(double), p->st));
+    CKC(cudaMemsetAsync(p->W2 + pp, 0, (size_t)g.npad * sizeof(double), p->st));
   }
+  return AHOC_OK;
+}
 #undef CKC
+
+}  // namespace
+
+extern "C" {
+
+ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi,
+                             const double* alpha, const ahoc_bdata* bd, const ahoc_opts* opts, void* stream) {
+  if (!out) return fail(AHOC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!alpha) return fail(AHOC_EINVAL, "alpha is NULL");
+  Geom g;
+  CKS(make_geom(dim, N, lo, hi, &g));
+  Opts o;
+  CKS(read_opts(opts, &o));
+  ahoc_plan* p = nullptr;
+  ahoc_status s = plan_alloc(&p, dim, N, lo, hi, o, reinterpret_cast<cudaStream_t>(stream));
+  for (int b = 0; s == AHOC_OK && b < o.batch; ++b) {
+    ahoc_bdata bb{};
+    if (bd) {
+      bb.g_D = bd->g_D ? bd->g_D + (int64_t)b * g.nfull : nullptr;
+      bb.g_N = bd->g_N ? bd->g_N + (int64_t)b * g.ngamma : nullptr;
+      bb.lapt_gD = bd->lapt_gD ? bd->lapt_gD + (int64_t)b * g.ngamma : nullptr;
+      bb.v_edge = bd->v_edge ? bd->v_edge + (int64_t)b * g.nfull : nullptr;
+    }
+    s = plan_load(p, b, alpha + (int64_t)b * g.nfull, &bb);
+  }
+  if (s == AHOC_OK && cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "plan setup failed");
+  if (s != AHOC_OK) {
+    if (p) ahoc_plan_destroy(p);
+    return s;
+  }
   *out = p;
   return AHOC_OK;
 }
+
+ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd) {
+  if (!p || !alpha) return fail(AHOC_EINVAL, "NULL argument");
+  if (b < 0 || b >= p->g.nb) return fail(AHOC_EINVAL, "problem index out of range");
+  p->have_last = false;
+  CKS(plan_load(p, b, alpha, bd));
+  CK(cudaStreamSynchronize(p->st));
+  return AHOC_OK;
+}
+
+ahoc_status ahoc_set_active(ahoc_plan* p, const int* mask) {
+  if (!p) return fail(AHOC_EINVAL, "NULL argument");
+  for (int b = 0; b < p->g.nb; ++b) p->part[b] = mask ? (mask[b] != 0) : 1;
+  return AHOC_OK;
+}
+
+int ahoc_batch(const ahoc_plan* p) { return p ? p->g.nb : -1; }
 
 ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
   if (!p) return AHOC_OK;
@@ -1001,17 +1143,21 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
 ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y) {
   if (!p || !q || !y) return fail(AHOC_EINVAL, "NULL argument");
   if (q == y) return fail(AHOC_EINVAL, "q and y may not alias");
+  CKS(set_act(p, p->part));
   return matvec_dev(p, q, y);
 }
 
 ahoc_status ahoc_schur_rhs(ahoc_plan* p, const double* f, double* b) {
   if (!p || !f || !b) return fail(AHOC_EINVAL, "NULL argument");
+  CKS(set_act(p, p->part));
   return schur_rhs_dev(p, f, b);
 }
 
 ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, double scale) {
   if (!p || !in || !out) return fail(AHOC_EINVAL, "NULL argument");
+  if (p->g.nb != 1) return fail(AHOC_EINVAL, "ahoc_dst1 takes a single-problem plan");
   if (axis < 0 || axis >= p->g.dim - 1) return fail(AHOC_EINVAL, "axis must be < dim - 1");
+  CKS(set_act(p, p->part));
   RUN(AHOC_K_OTHER, launch_unpack(p->g, p->W1, in, p->st));
   if (axis == 0) RUN(AHOC_K_DST_X, launch_dst_x<double>(p->g, p->W1, p->twx, p->snx, scale, p->st));
   else RUN(AHOC_K_DST_Y, launch_dst_y<double>(p->g, p->W1, p->twy, p->sny, scale, p->st));
@@ -1021,6 +1167,8 @@ ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, dou
 
 ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
   if (!p || !rhs || !w) return fail(AHOC_EINVAL, "NULL argument");
+  if (p->g.nb != 1) return fail(AHOC_EINVAL, "ahoc_poisson takes a single-problem plan");
+  CKS(set_act(p, p->part));
   RUN(AHOC_K_OTHER, launch_unpack(p->g, p->W1, rhs, p->st));
   CKS(poisson_inplace(p, p->W1));
   RUN(AHOC_K_OTHER, launch_pack(p->g, w, p->W1, p->st));
@@ -1030,8 +1178,11 @@ ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
 ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
   if (!p || !q) return fail(AHOC_EINVAL, "NULL argument");
   if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
-  CK(cudaMemcpyAsync(q, p->Q, p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-  if (v) RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->o.prec == AHOC_MIXED ? p->V64 : p->W1, p->Q, p->vedge, p->st));
+  CK(cudaMemcpyAsync(q, p->Q, (size_t)p->g.nb * p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  CKS(set_act(p, p->part));
+  if (v)
+    RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->o.prec == AHOC_MIXED ? p->V64 : p->W1, p->Q,
+                                    p->has_vedge ? p->vedge : nullptr, p->st));
   return AHOC_OK;
 }
 
@@ -1039,205 +1190,278 @@ ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
 
 namespace {
 
-struct GmresOut {
-  int iters = 0, restarts = 0;
-  double rel = 0.0, ms_mv = 0.0;
-  ahoc_status status = AHOC_OK;
-};
-
-// Flexible GMRES on S X = b (right-preconditioned with the boundary-symbol
-// operator, whose inexact FP32 application is absorbed by storing the
-// directions z_j = P^-1 v_j; CGS2 Arnoldi on the device, Givens rotations and
-// the least-squares solve on the host in FP64).  X holds the initial guess on entry when `guess`
-// (else it is zeroed) and the iterate on exit; tol is relative to beta0 =
-// ||b||.  Restarts (an explicit residual) only when the basis is full.
-ahoc_status gmres(ahoc_plan* p, const double* b, double beta0, double* X, bool guess, double tol, int max_iters,
-                  GmresOut* go) {
-  const int64_t n = p->g.ngamma;
+// Flexible GMRES on S X = b for every problem of the batch in lockstep
+// (right-preconditioned with the boundary-symbol operator, whose inexact
+// FP32 application is absorbed by storing the directions z_j = P^-1 v_j;
+// CGS2 Arnoldi on the device, Givens rotations and the least-squares solve
+// on the host in FP64, per problem).  live: the problems to solve; a problem
+// that converges (relative residual <= tol[b]) or exhausts maxit[b] is
+// masked out of every later launch, so its arithmetic -- and its result --
+// is the same as in a solve of its own.  X holds the initial guess on entry
+// when `guess` (else it is zeroed) and the iterate on exit; tolerances are
+// relative to beta0[b] = ||b_b||.  Restarts (an explicit residual) only when
+// the basis is full.
+ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta0, double* X, bool guess,
+                  const std::vector<double>& tol, const std::vector<int>& maxit, std::vector<int> live,
+                  std::vector<ProbStat>& go) {
+  const Geom& g = p->g;
+  const int nb = g.nb;
+  const int64_t n = g.ngamma;
+  const int64_t ld = (int64_t)nb * n;  // Krylov column stride: [column][problem][point]
   const int m = p->o.restart;
-  double beta = beta0;
-  if (guess) {
-    CKS(matvec_dev(p, X, p->tmp));
-    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
-    CKS(mdot(p, p->r, 1, p->r, p->hdev));
-    CKS(fetch(p, 1));
-    beta = std::sqrt(p->hhost[0]);
-    if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite initial residual");
-  } else {
-    CK(cudaMemsetAsync(X, 0, n * sizeof(double), p->st));
-    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  const int hs = hstride(p->o);
+  for (int i = 0; i < nb; ++i) {
+    go[i].status = AHOC_OK;
+    if (live[i] && !(beta0[i] > 0)) live[i] = 0;
   }
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-  bool done = false;
-  while (!done) {
-    go->rel = beta / beta0;
-    if (go->rel <= tol) break;
-    if (go->iters >= max_iters) {
-      go->status = AHOC_ENOCONV;
-      break;
+  std::vector<double> beta(beta0);
+  if (guess) {
+    CKS(set_act(p, live));
+    CKS(matvec_dev(p, X, p->tmp));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st, nb, nullptr, g.act));
+    CKS(mdot(p, p->r, n, 1, p->r, p->hdev));
+    CKS(fetch(p));
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) {
+        beta[i] = std::sqrt(p->hhost[(size_t)i * hs]);
+        if (!is_fin(beta[i])) return fail(AHOC_ENUMERIC, "non-finite initial residual");
+      }
+  } else {
+    CK(cudaMemsetAsync(X, 0, (size_t)nb * n * sizeof(double), p->st));
+    CKS(set_act(p, live));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
+  }
+  for (int i = 0; i < nb; ++i)
+    if (live[i]) {
+      go[i].rel = beta[i] / beta0[i];
+      if (go[i].rel <= tol[i]) live[i] = 0;
     }
-    double* V = p->Kry;
-    RUN(AHOC_K_KRYLOV, launch_axpby(V, p->r, 1.0 / beta, 0.0, n, p->st));
-    std::fill(gv.begin(), gv.end(), 0.0);
-    gv[0] = beta;
-    int jend = 0;
+  std::vector<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), gv((size_t)nb * (m + 1)),
+      y(m), sc(nb, 0.0), hy((size_t)nb * hs, 0.0);
+  std::vector<int> jend(nb, 0), cyc(nb, 0), nc(nb, 0);
+  while (any(live)) {
+    for (int i = 0; i < nb; ++i)
+      if (live[i] && go[i].iters >= maxit[i]) {
+        go[i].status = AHOC_ENOCONV;
+        live[i] = 0;
+      }
+    if (!any(live)) break;
+    cyc = live;
+    CKS(set_act(p, live));
+    for (int i = 0; i < nb; ++i) {
+      sc[i] = live[i] ? 1.0 / beta[i] : 0.0;
+      jend[i] = 0;
+      std::fill(gv.begin() + (size_t)i * (m + 1), gv.begin() + (size_t)(i + 1) * (m + 1), 0.0);
+      gv[(size_t)i * (m + 1)] = beta[i];
+    }
+    CK(cudaMemcpyAsync(p->scal, sc.data(), nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->Kry, p->r, 0.0, 0.0, n, p->st, nb, p->scal, g.act));
     for (int j = 0; j < m; ++j) {
-      double* w = V + (int64_t)(j + 1) * n;
+      double* vj = p->Kry + (int64_t)j * ld;
+      double* w = p->Kry + (int64_t)(j + 1) * ld;
+      double* zj = p->Zb + (int64_t)j * ld;
       CK(cudaEventRecord(p->ev0, p->st));
-      double* zj = p->Zb + (int64_t)j * n;
-      CKS(precond_apply(p, V + (int64_t)j * n, zj));
+      CKS(precond_apply(p, vj, zj));
       CKS(matvec_dev(p, zj, w));
       CK(cudaEventRecord(p->ev1, p->st));
       // CGS2
-      double* h1 = p->hdev;
-      double* h2 = p->hdev + (j + 1);
-      double* nr = p->hdev + 2 * (j + 1);
-      CKS(mdot(p, V, j + 1, w, h1));
-      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h1, w, n, p->st));
-      CKS(mdot(p, V, j + 1, w, h2));
-      RUN(AHOC_K_KRYLOV, launch_gemv_sub(V, n, j + 1, h2, w, n, p->st));
-      CKS(mdot(p, w, 1, w, nr));
-      CKS(fetch(p, 2 * (j + 1) + 1));
+      CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev));
+      CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev, w, nullptr));
+      CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev + (j + 1)));
+      CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev + (j + 1), w, nullptr));
+      CKS(mdot(p, w, n, 1, w, p->hdev + 2 * (j + 1)));
+      CKS(fetch(p));
       float evms = 0.f;
-      if (cudaEventElapsedTime(&evms, p->ev0, p->ev1) == cudaSuccess) go->ms_mv += evms;
-      ++go->iters;
-      double* Hc = &H[(size_t)j * (m + 1)];
-      for (int i = 0; i <= j; ++i) Hc[i] = p->hhost[i] + p->hhost[j + 1 + i];
-      const double hn = std::sqrt(p->hhost[2 * (j + 1)]);
-      if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
-      Hc[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double a = Hc[i], bb = Hc[i + 1];
-        Hc[i] = cs[i] * a + sn[i] * bb;
-        Hc[i + 1] = -sn[i] * a + cs[i] * bb;
+      cudaEventElapsedTime(&evms, p->ev0, p->ev1);
+      for (int i = 0; i < nb; ++i) {
+        if (!live[i]) continue;
+        ProbStat& gi = go[i];
+        gi.ms_mv += evms;
+        ++gi.iters;
+        const double* hh = p->hhost + (size_t)i * hs;
+        double* Hc = &H[((size_t)i * m + j) * (m + 1)];
+        double* csi = &cs[(size_t)i * m];
+        double* sni = &sn[(size_t)i * m];
+        double* gvi = &gv[(size_t)i * (m + 1)];
+        for (int k = 0; k <= j; ++k) Hc[k] = hh[k] + hh[j + 1 + k];
+        const double hn = std::sqrt(hh[2 * (j + 1)]);
+        if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
+        Hc[j + 1] = hn;
+        for (int k = 0; k < j; ++k) {
+          const double a = Hc[k], bb = Hc[k + 1];
+          Hc[k] = csi[k] * a + sni[k] * bb;
+          Hc[k + 1] = -sni[k] * a + csi[k] * bb;
+        }
+        const double den = std::hypot(Hc[j], Hc[j + 1]);
+        csi[j] = (den > 0) ? Hc[j] / den : 1.0;
+        sni[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
+        Hc[j] = den;
+        Hc[j + 1] = 0.0;
+        gvi[j + 1] = -sni[j] * gvi[j];
+        gvi[j] = csi[j] * gvi[j];
+        jend[i] = j + 1;
+        gi.rel = std::fabs(gvi[j + 1]) / beta0[i];
+        if (gi.rel <= tol[i] || hn == 0.0) {
+          live[i] = 0;  // converged
+        } else if (gi.iters >= maxit[i]) {
+          live[i] = 0;
+          gi.status = AHOC_ENOCONV;
+        } else {
+          sc[i] = 1.0 / hn;
+        }
       }
-      const double den = std::hypot(Hc[j], Hc[j + 1]);
-      cs[j] = (den > 0) ? Hc[j] / den : 1.0;
-      sn[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
-      Hc[j] = den;
-      Hc[j + 1] = 0.0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = cs[j] * gv[j];
-      jend = j + 1;
-      go->rel = std::fabs(gv[j + 1]) / beta0;
-      if (go->rel <= tol || hn == 0.0 || go->iters >= max_iters) {
-        done = (go->rel <= tol || hn == 0.0);
-        break;
+      if (!any(live)) break;
+      CKS(set_act(p, live));
+      CK(cudaMemcpyAsync(p->scal, sc.data(), nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 0.0, 0.0, n, p->st, nb, p->scal, g.act));
+    }
+    // y = H^-1 g (upper triangular), X += Z y, per problem of this cycle
+    for (int i = 0; i < nb; ++i) {
+      nc[i] = cyc[i] ? jend[i] : 0;
+      if (!cyc[i]) continue;
+      const double* gvi = &gv[(size_t)i * (m + 1)];
+      const int je = jend[i];
+      for (int k = je - 1; k >= 0; --k) {
+        double sacc = gvi[k];
+        for (int l = k + 1; l < je; ++l) sacc -= H[((size_t)i * m + l) * (m + 1) + k] * y[l];
+        y[k] = sacc / H[((size_t)i * m + k) * (m + 1) + k];
       }
-      RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 1.0 / hn, 0.0, n, p->st));
+      for (int k = 0; k < je; ++k) hy[(size_t)i * hs + k] = -y[k];
     }
-    // y = H^-1 g (upper triangular), X += Z y
-    for (int i = jend - 1; i >= 0; --i) {
-      double sacc = gv[i];
-      for (int k = i + 1; k < jend; ++k) sacc -= H[(size_t)k * (m + 1) + i] * y[k];
-      y[i] = sacc / H[(size_t)i * (m + 1) + i];
-    }
-    for (int i = 0; i < jend; ++i) p->hhost[i] = -y[i];
-    CK(cudaMemcpyAsync(p->hdev, p->hhost, jend * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    RUN(AHOC_K_KRYLOV, launch_gemv_sub(p->Zb, n, jend, p->hdev, X, n, p->st));
+    CK(cudaMemcpyAsync(p->hdev, hy.data(), hy.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->ncolsb, nc.data(), nb * sizeof(int), cudaMemcpyHostToDevice, p->st));
+    CKS(set_act(p, cyc));
+    CKS(gemv_sub(p, p->Zb, ld, 0, p->hdev, X, p->ncolsb));
     CK(cudaStreamSynchronize(p->st));
     CKS(harvest(p));
-    if (done) break;
-    if (go->iters >= max_iters) {
-      go->status = AHOC_ENOCONV;
-      break;
-    }
-    // restart: explicit residual r = b - S X
-    ++go->restarts;
+    if (!any(live)) break;
+    // restart the problems whose basis filled: explicit residual r = b - S X
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) ++go[i].restarts;
+    CKS(set_act(p, live));
     CKS(matvec_dev(p, X, p->tmp));
-    CK(cudaMemcpyAsync(p->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st));
-    CKS(mdot(p, p->r, 1, p->r, p->hdev));
-    CKS(fetch(p, 1));
-    beta = std::sqrt(p->hhost[0]);
-    if (!is_fin(beta)) return fail(AHOC_ENUMERIC, "non-finite restart residual");
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st, nb, nullptr, g.act));
+    CKS(mdot(p, p->r, n, 1, p->r, p->hdev));
+    CKS(fetch(p));
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) {
+        beta[i] = std::sqrt(p->hhost[(size_t)i * hs]);
+        if (!is_fin(beta[i])) return fail(AHOC_ENUMERIC, "non-finite restart residual");
+        go[i].rel = beta[i] / beta0[i];
+        if (go[i].rel <= tol[i]) live[i] = 0;
+      }
   }
   return AHOC_OK;
 }
 
-ahoc_status norm2(ahoc_plan* p, const double* v, double* out) {
-  CKS(mdot(p, v, 1, v, p->hdev));
-  CKS(fetch(p, 1));
-  *out = std::sqrt(p->hhost[0]);
-  if (!is_fin(*out)) return fail(AHOC_ENUMERIC, "non-finite norm");
+// ||v_b|| of every problem in the current mask (others: 0)
+ahoc_status norms(ahoc_plan* p, const double* v, std::vector<double>& out) {
+  CKS(mdot(p, v, p->g.ngamma, 1, v, p->hdev));
+  CKS(fetch(p));
+  out.assign(p->g.nb, 0.0);
+  for (int i = 0; i < p->g.nb; ++i)
+    if (p->act_now[i]) {
+      out[i] = std::sqrt(p->hhost[(size_t)i * hstride(p->o)]);
+      if (!is_fin(out[i])) return fail(AHOC_ENUMERIC, "non-finite norm");
+    }
   return AHOC_OK;
 }
 
+ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol);
+
 // Algorithm 1 in FP64: b = -R(0), GMRES on S_h Q = b (from the nested
 // coarse-grid guess when the plan has coarse levels), recovery of V and U.
-ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol, GmresOut* go) {
+ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
   const Geom& g = p->g;
+  const int nb = g.nb;
+  std::vector<int> live = p->part;
+  CKS(set_act(p, live));
   CKS(schur_rhs_dev(p, f, p->b));
-  double beta0 = 0.0;
-  CKS(norm2(p, p->b, &beta0));
+  std::vector<double> beta0;
+  CKS(norms(p, p->b, beta0));
   bool guess = false;
-  p->coarse_iters = 0;
-  if (beta0 > 0 && p->coarse) {
+  bool any_rhs = false;
+  for (int i = 0; i < nb; ++i) any_rhs = any_rhs || (live[i] && beta0[i] > 0);
+  if (any_rhs && p->coarse) {
     // nested initial guess: solve on the coarser grid (recursively), then
     // prolong its Q to this grid's faces (the coarse-grid interpolated
     // initial guess of Sec. 4.1)
     ahoc_plan* c = p->coarse;
     double* f_c = p->W2;
     double* u_c = p->W1;
+    CKS(set_act(c, live));
     RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
     CK(cudaStreamSynchronize(p->st));
-    ahoc_info ci;
-    std::memset(&ci, 0, sizeof(ci));
+    c->part = live;
     const double ctol = p->o.coarse_tol > tol ? p->o.coarse_tol : tol;
-    ahoc_status cs_ = ahoc_solve(c, f_c, u_c, ctol, &ci);
-    if (cs_ != AHOC_OK && cs_ != AHOC_ENOCONV) return cs_;
-    p->coarse_iters = ci.iters + c->coarse_iters;
+    ahoc_status cs_ = solve_internal(c, f_c, u_c, ctol);
+    if (cs_ != AHOC_OK) return cs_;  // ENOCONV of a coarse level is kept in its stats, not an error
     CKS(harvest(p));
     for (int k = 0; k < AHOC_NK; ++k) {
       // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
-      p->kms_top[k] -= ci.kernel_ms[k];
-      p->kn_top[k] -= ci.kernel_launches[k];
-      p->kms[k] += ci.kernel_ms[k];
-      p->kn[k] += ci.kernel_launches[k];
+      const double cms = c->kms[k];
+      const int64_t cn = c->kn[k];
+      p->kms_top[k] -= cms;
+      p->kn_top[k] -= cn;
+      p->kms[k] += cms;
+      p->kn[k] += cn;
     }
-    p->launches += ci.launches;
-    go->ms_mv += ci.ms_matvec;
+    p->launches += c->launches;
+    for (int i = 0; i < nb; ++i) {
+      p->ps[i].coarse_iters = c->ps[i].iters + c->ps[i].coarse_iters;
+      p->ps[i].ms_mv += c->ps[i].ms_mv;
+    }
+    CKS(set_act(p, live));
     RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
     // the fields were borrowed as temporaries: restore the zero padding
-    CK(cudaMemsetAsync(p->W1, 0, (size_t)g.npad * sizeof(double), p->st));
-    CK(cudaMemsetAsync(p->W2, 0, (size_t)g.npad * sizeof(double), p->st));
+    CK(cudaMemsetAsync(p->W1, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+    CK(cudaMemsetAsync(p->W2, 0, (size_t)nb * g.npad * sizeof(double), p->st));
     guess = true;
   }
-  if (beta0 > 0) CKS(gmres(p, p->b, beta0, p->Q, guess, tol, p->o.max_iters, go));
-  else CK(cudaMemsetAsync(p->Q, 0, g.ngamma * sizeof(double), p->st));
+  std::vector<ProbStat> go(nb);
+  CKS(gmres(p, p->b, beta0, p->Q, guess, std::vector<double>(nb, tol), std::vector<int>(nb, p->o.max_iters), live,
+            go));
+  for (int i = 0; i < nb; ++i) {
+    ProbStat& s = p->ps[i];
+    s.iters = go[i].iters;
+    s.restarts = go[i].restarts;
+    s.rel = live[i] && beta0[i] > 0 ? go[i].rel : 0.0;
+    s.status = go[i].status;
+    s.ms_mv += go[i].ms_mv;
+  }
   // recovery: V and U with the converged Q (and the data)
+  CKS(set_act(p, p->part));
   CKS(solve_VU(p, p->Q, f, true));
-  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->gD, p->st));
+  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->has_gD ? p->gD : nullptr, p->st));
   return AHOC_OK;
 }
 
-// Mixed precision: iterative refinement of the coupled system.  Each step
-// takes the FP64 residual of all three block rows at x = (U, V, Q), solves
-// the coupled correction system with FP32 Poisson solves (the same Schur
-// method: b = -R_d(0), GMRES on S dQ = b to refine_tol, recovery of dV, dU)
-// and adds the correction in FP64.  The relative size of the correction
-// right-hand side -- the Schur residual of the current iterate, evaluated
-// from the FP64 residual -- is the stopping test, so tol has the meaning it
-// has on the FP64 path.
+// Mixed precision: iterative refinement of the coupled system, every problem
+// of the batch in lockstep.  Each step takes the FP64 residual of all three
+// block rows at x = (U, V, Q), solves the coupled correction system with FP32
+// Poisson solves (the same Schur method: b = -R_d(0), GMRES on S dQ = b to
+// refine_tol, recovery of dV, dU) and adds the correction in FP64.  The
+// relative size of the correction right-hand side -- the Schur residual of
+// the current iterate, evaluated from the FP64 residual -- is the stopping
+// test, so tol has the meaning it has on the FP64 path.
 constexpr int kMaxRefine = 8;
-ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, GmresOut* go) {
+ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
   const Geom& g = p->g;
+  const int nb = g.nb;
   const int64_t n = g.ngamma;
-  CK(cudaMemsetAsync(p->U64, 0, (size_t)g.npad * sizeof(double), p->st));
-  CK(cudaMemsetAsync(p->V64, 0, (size_t)g.npad * sizeof(double), p->st));
-  CK(cudaMemsetAsync(p->Q, 0, n * sizeof(double), p->st));
-  double bref = 0.0;
-  p->refine_steps = 0;
-  for (int k = 0; k < 16; ++k) {
-    p->refine_hist[k] = 0.0;
-    p->refine_du[k] = 0.0;
-    p->inner_iters[k] = 0;
-  }
-  for (int step = 0; step <= kMaxRefine; ++step) {
+  CK(cudaMemsetAsync(p->U64, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->V64, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->Q, 0, (size_t)nb * n * sizeof(double), p->st));
+  std::vector<int> live = p->part;
+  std::vector<double> bref(nb, 0.0), bn;
+  for (int step = 0; step <= kMaxRefine && any(live); ++step) {
+    CKS(set_act(p, live));
     RUNN(AHOC_K_OTHER, 2,
-         launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->gD, p->vedge, p->gN, p->lapt,
-                         p->ainv, p->afac, p->st));
+         launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->has_gD ? p->gD : nullptr,
+                         p->has_vedge ? p->vedge : nullptr, p->has_gN ? p->gN : nullptr,
+                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st));
     // correction right-hand side b = -R_d(0)
     if (fused_ok(g)) {
       CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));
@@ -1246,55 +1470,99 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol, Gm
       RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
                                             p->st, p->Rq));
     }
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st));
-    double bn = 0.0;
-    CKS(norm2(p, p->b2, &bn));
-    if (step == 0) bref = bn;
-    go->rel = (bref > 0) ? bn / bref : 0.0;
-    if (step < 16) p->refine_hist[step] = go->rel;
-    if (bn == 0.0 || go->rel <= tol) break;
-    // Stagnation (a step that removes less than a tenth of the residual): the refinement
-    // has reached its limiting accuracy.  If the last correction changed U by
-    // at most tol (relative 2-norm), the iterate is settled to the accuracy
-    // asked for and the residual sits at the floor of its FP64 evaluation --
-    // the case of data whose Schur right-hand side is tiny next to the
-    // solution -- and the solve has converged.  Otherwise the FP32 solves are
-    // too inaccurate for this grid and the solve has not converged.
-    if (step >= 2 && go->rel > 0.9 * p->refine_hist[step - 1]) {
-      if (!(p->refine_du[step - 1] <= tol)) go->status = AHOC_ENOCONV;
-      break;
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st, nb, nullptr, g.act));
+    CKS(norms(p, p->b2, bn));
+    std::vector<double> itol(nb, 0.0);
+    std::vector<int> maxit(nb, 0);
+    for (int i = 0; i < nb; ++i) {
+      if (!live[i]) continue;
+      ProbStat& s = p->ps[i];
+      if (step == 0) bref[i] = bn[i];
+      s.rel = (bref[i] > 0) ? bn[i] / bref[i] : 0.0;
+      s.hist[step] = s.rel;
+      if (bn[i] == 0.0 || s.rel <= tol) {
+        live[i] = 0;
+        continue;
+      }
+      // Stagnation (a step that removes less than a tenth of the residual):
+      // the refinement has reached its limiting accuracy.  If the last
+      // correction changed U by at most tol (relative 2-norm), the iterate is
+      // settled to the accuracy asked for and the residual sits at the floor
+      // of its FP64 evaluation -- the case of data whose Schur right-hand
+      // side is tiny next to the solution -- and the solve has converged.
+      // Otherwise the FP32 solves are too inaccurate for this grid and the
+      // solve has not converged.
+      if (step >= 2 && s.rel > 0.9 * s.hist[step - 1]) {
+        if (!(s.du[step - 1] <= tol)) s.status = AHOC_ENOCONV;
+        live[i] = 0;
+        continue;
+      }
+      if (step == kMaxRefine) {
+        s.status = AHOC_ENOCONV;
+        live[i] = 0;
+        continue;
+      }
+      // inner tolerance: refine_tol, but no tighter than the outer goal needs
+      itol[i] = p->o.refine_tol;
+      const double need = 0.5 * tol * bref[i] / bn[i];
+      if (need > itol[i]) itol[i] = need;
+      maxit[i] = p->o.max_iters - s.iters;
     }
-    if (step == kMaxRefine) {
-      go->status = AHOC_ENOCONV;
-      break;
+    if (!any(live)) break;
+    std::vector<ProbStat> gi(nb);
+    CKS(gmres(p, p->b2, bn, p->dQ, false, itol, maxit, live, gi));
+    for (int i = 0; i < nb; ++i) {
+      if (!live[i]) continue;
+      ProbStat& s = p->ps[i];
+      s.iters += gi[i].iters;
+      s.restarts += gi[i].restarts;
+      s.ms_mv += gi[i].ms_mv;
+      s.inner[step] = gi[i].iters;
     }
-    // inner tolerance: refine_tol, but no tighter than the outer goal needs
-    double itol = p->o.refine_tol;
-    const double need = 0.5 * tol * bref / bn;
-    if (need > itol) itol = need;
-    GmresOut gi;
-    CKS(gmres(p, p->b2, bn, p->dQ, false, itol, p->o.max_iters - go->iters, &gi));
-    go->iters += gi.iters;
-    if (step < 16) p->inner_iters[step] = gi.iters;
-    go->restarts += gi.restarts;
-    go->ms_mv += gi.ms_mv;
     // recovery of the correction and the FP64 update
+    CKS(set_act(p, live));
     if (fused_ok(g))
       CKS(fused2d<float>(p, f2arrays_f(p), p->dQ, p->Rv, p->Ru, nullptr, nullptr, true));
     else
       CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
-    RUNN(AHOC_K_OTHER, 2,
-         launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->partial, kDotBlocks, p->hdev, p->st));
-    CKS(fetch(p, 2));
-    if (step < 16) p->refine_du[step] = p->hhost[1] > 0 ? std::sqrt(p->hhost[0] / p->hhost[1]) : 0.0;
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->dQ, 1.0, 1.0, n, p->st));
-    ++p->refine_steps;
-    if (go->iters >= p->o.max_iters) {
-      go->status = AHOC_ENOCONV;
-      break;
+    RUNN(AHOC_K_OTHER, 2, launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->partial, kDotBlocks, p->hdev, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->dQ, 1.0, 1.0, n, p->st, nb, nullptr, g.act));
+    CKS(fetch(p));
+    for (int i = 0; i < nb; ++i) {
+      if (!live[i]) continue;
+      ProbStat& s = p->ps[i];
+      const double su = p->hhost[2 * i + 1], sdu = p->hhost[2 * i];
+      s.du[step] = su > 0 ? std::sqrt(sdu / su) : 0.0;
+      ++s.refine_steps;
+      if (s.iters >= p->o.max_iters) {
+        s.status = AHOC_ENOCONV;
+        live[i] = 0;
+      }
     }
   }
-  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->U64, p->gD, p->st));
+  CKS(set_act(p, p->part));
+  RUN(AHOC_K_OTHER, launch_write_full(g, u, p->U64, p->has_gD ? p->gD : nullptr, p->st));
+  return AHOC_OK;
+}
+
+// One solve of the problems in p->part (statistics in p->ps).
+ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol) {
+  p->have_last = false;
+  CK(cudaStreamSynchronize(p->st));
+  CKS(harvest(p));
+  p->launches = 0;
+  for (int k = 0; k < AHOC_NK; ++k) {
+    p->kms[k] = 0;
+    p->kn[k] = 0;
+    p->kms_top[k] = 0;
+    p->kn_top[k] = 0;
+  }
+  p->ps.assign(p->g.nb, ProbStat{});
+  if (p->o.prec == AHOC_MIXED) CKS(solve_mixed(p, f, u, tol));
+  else CKS(solve_fp64(p, f, u, tol));
+  CK(cudaStreamSynchronize(p->st));
+  CKS(harvest(p));
+  p->have_last = true;
   return AHOC_OK;
 }
 
@@ -1307,45 +1575,38 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
   if (!p || !f || !u) return fail(AHOC_EINVAL, "NULL argument");
   if (!(tol > 0) || !std::isfinite(tol)) return fail(AHOC_EINVAL, "tol must be positive");
   const auto t0 = std::chrono::steady_clock::now();
-  p->have_last = false;
-  CK(cudaStreamSynchronize(p->st));
-  CKS(harvest(p));
-  p->launches = 0;
-  for (int k = 0; k < AHOC_NK; ++k) {
-    p->kms[k] = 0;
-    p->kn[k] = 0;
-    p->kms_top[k] = 0;
-    p->kn_top[k] = 0;
-  }
-  GmresOut go;
-  if (p->o.prec == AHOC_MIXED) CKS(solve_mixed(p, f, u, tol, &go));
-  else CKS(solve_fp64(p, f, u, tol, &go));
-  CK(cudaStreamSynchronize(p->st));
-  CKS(harvest(p));
-  p->have_last = true;
-  if (info) {
-    info->iters = go.iters;
-    info->restarts = go.restarts;
-    info->rel_resid = go.rel;
-    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    info->ms_matvec = go.ms_mv;
-    info->launches = p->launches;
-    info->levels = p->levels;
-    info->coarse_iters = p->coarse_iters;
-    info->refine_steps = p->refine_steps;
+  CKS(solve_internal(p, f, u, tol));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  ahoc_status st = AHOC_OK;
+  for (int i = 0; i < p->g.nb; ++i) {
+    if (!p->part[i]) continue;
+    const ProbStat& s = p->ps[i];
+    if (s.status != AHOC_OK) st = s.status;
+    if (!info) continue;
+    ahoc_info* in = info + i;
+    in->status = s.status;
+    in->iters = s.iters;
+    in->restarts = s.restarts;
+    in->rel_resid = s.rel;
+    in->ms_total = ms;
+    in->ms_matvec = s.ms_mv;
+    in->launches = p->launches;
+    in->levels = p->levels;
+    in->coarse_iters = s.coarse_iters;
+    in->refine_steps = s.refine_steps;
     for (int k = 0; k < 16; ++k) {
-      info->refine_hist[k] = p->refine_hist[k];
-      info->refine_du[k] = p->refine_du[k];
-      info->inner_iters[k] = p->inner_iters[k];
+      in->refine_hist[k] = s.hist[k];
+      in->refine_du[k] = s.du[k];
+      in->inner_iters[k] = s.inner[k];
     }
     for (int k = 0; k < AHOC_NK; ++k) {
-      info->kernel_ms[k] = p->kms[k];
-      info->kernel_launches[k] = p->kn[k];
-      info->kernel_ms_top[k] = p->kms[k] + p->kms_top[k];
-      info->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
+      in->kernel_ms[k] = p->kms[k];
+      in->kernel_launches[k] = p->kn[k];
+      in->kernel_ms_top[k] = p->kms[k] + p->kms_top[k];
+      in->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
     }
   }
-  if (go.status != AHOC_OK) return fail(go.status, "GMRES reached max_iters (or refinement did not converge)");
+  if (st != AHOC_OK) return fail(st, "GMRES reached max_iters (or refinement did not converge)");
   return AHOC_OK;
 }
 

@@ -87,9 +87,15 @@ __global__ void k_face_symbols(Geom g, Coefs cf, double* __restrict__ pre, const
 }
 
 __global__ void k_face_muldiv(double* __restrict__ out, const double* __restrict__ in, const double* __restrict__ mul,
-                              const double* __restrict__ div, int64_t n) {
+                              const double* __restrict__ div, int64_t n, int64_t mstride, int64_t dstride,
+                              const int* act) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int bi = blockIdx.y;
+  if (i >= n || (act && !act[bi])) return;
+  out += (int64_t)bi * n;
+  in += (int64_t)bi * n;
+  if (mul) mul += (int64_t)bi * mstride;
+  if (div) div += (int64_t)bi * dstride;
   double v = in[i];
   if (mul) v *= mul[i];
   if (div) v /= div[i];
@@ -104,8 +110,8 @@ cudaError_t launch_face_symbols(const Geom& g, const Coefs& cf, double* pre, con
 }
 
 cudaError_t launch_face_muldiv(double* out, const double* in, const double* mul, const double* div, int64_t n,
-                               cudaStream_t st) {
-  k_face_muldiv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, in, mul, div, n);
+                               cudaStream_t st, int nb, int64_t mstride, int64_t dstride, const int* act) {
+  k_face_muldiv<<<dim3((unsigned)((n + 255) / 256), nb), 256, 0, st>>>(out, in, mul, div, n, mstride, dstride, act);
   return cudaGetLastError();
 }
 

@@ -48,8 +48,14 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
                        const double* __restrict__ f, const double* __restrict__ vedge,
                        const T* __restrict__ srcv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n0) return;
-  const int j = blockIdx.y, k = blockIdx.z;
+  const int bi = blockIdx.z / (int)g.n2;
+  if (i >= g.n0 || g.skip(bi)) return;
+  const int j = blockIdx.y, k = blockIdx.z - bi * (int)g.n2;
+  out += (int64_t)bi * g.npad;
+  if (srcv) srcv += (int64_t)bi * g.npad;
+  if (Q) Q += (int64_t)bi * g.ngamma;
+  if (f) f += (int64_t)bi * g.nfull;
+  if (vedge) vedge += (int64_t)bi * g.nfull;
   const int64_t t = g.pad(i, j, k);
   if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
   T acc = 0;
@@ -89,8 +95,15 @@ __global__ void k_urhs(Geom g, Coefs cf, T* __restrict__ out, const T* __restric
                        const T* __restrict__ ainv, const double* __restrict__ Q,
                        const double* __restrict__ gD, const T* __restrict__ srcu) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n0) return;
-  const int j = blockIdx.y, k = blockIdx.z;
+  const int bi = blockIdx.z / (int)g.n2;
+  if (i >= g.n0 || g.skip(bi)) return;
+  const int j = blockIdx.y, k = blockIdx.z - bi * (int)g.n2;
+  out += (int64_t)bi * g.npad;
+  V += (int64_t)bi * g.npad;
+  if (srcu) srcu += (int64_t)bi * g.npad;
+  ainv += (int64_t)bi * g.nfull;
+  if (Q) Q += (int64_t)bi * g.ngamma;
+  if (gD) gD += (int64_t)bi * g.nfull;
   const int64_t t = g.pad(i, j, k);
   if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
   // M(V / alpha): centre and the axis neighbours; a neighbour on a face holds Q
@@ -135,7 +148,19 @@ __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __res
                         const double* __restrict__ gD, const double* __restrict__ gN,
                         const double* __restrict__ lapt, const double* __restrict__ srcq) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= g.ngamma) return;
+  const int bi = blockIdx.y;
+  if (q >= g.ngamma || g.skip(bi)) return;
+  {
+    const int64_t fo = (int64_t)bi * g.ngamma;
+    y += fo;
+    U += (int64_t)bi * g.npad;
+    if (Q) Q += fo;
+    afac += fo;
+    if (gD) gD += (int64_t)bi * g.nfull;
+    if (gN) gN += fo;
+    if (lapt) lapt += fo;
+    if (srcq) srcq += fo;
+  }
   int f = 0;
   while (q >= g.face_off[f + 1]) ++f;
   const int a = f >> 1, side = f & 1;
@@ -175,7 +200,11 @@ __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __res
 __global__ void k_write_full(Geom g, double* __restrict__ out, const double* __restrict__ Uin,
                              const double* __restrict__ bnd) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nfull) return;
+  const int bi = blockIdx.y;
+  if (t >= g.nfull || g.skip(bi)) return;
+  out += (int64_t)bi * g.nfull;
+  Uin += (int64_t)bi * g.npad;
+  if (bnd) bnd += (int64_t)bi * g.nfull;
   const int i = (int)(t % g.f0);
   const int64_t r = t / g.f0;
   const int j = (int)(r % g.f1);
@@ -189,7 +218,12 @@ __global__ void k_write_full(Geom g, double* __restrict__ out, const double* __r
 __global__ void k_v_full(Geom g, double* __restrict__ out, const double* __restrict__ Vin,
                          const double* __restrict__ Q, const double* __restrict__ vedge) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nfull) return;
+  const int bi = blockIdx.y;
+  if (t >= g.nfull || g.skip(bi)) return;
+  out += (int64_t)bi * g.nfull;
+  Vin += (int64_t)bi * g.npad;
+  if (Q) Q += (int64_t)bi * g.ngamma;
+  if (vedge) vedge += (int64_t)bi * g.nfull;
   const int i = (int)(t % g.f0);
   const int64_t r = t / g.f0;
   const int j = (int)(r % g.f1);
@@ -226,6 +260,8 @@ __global__ void k_unpack(Geom g, double* __restrict__ padded, const double* __re
 __global__ void k_face_gather(Geom g, double* __restrict__ face, const double* __restrict__ full) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.ngamma) return;
+  face += (int64_t)blockIdx.y * g.ngamma;
+  full += (int64_t)blockIdx.y * g.nfull;
   int f = 0;
   while (q >= g.face_off[f + 1]) ++f;
   const int a = f >> 1, side = f & 1;
@@ -251,14 +287,14 @@ static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) 
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
                         const double* vedge, cudaStream_t st, const T* srcv) {
-  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)g.n2);
+  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)(g.n2 * g.nb));
   k_vrhs<T><<<grid, 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const T* ainv, const double* Q,
                         const double* gD, cudaStream_t st, const T* srcu) {
-  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)g.n2);
+  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)(g.n2 * g.nb));
   k_urhs<T><<<grid, 256, 0, st>>>(g, cf, out, V, ainv, Q, gD, srcu);
   return cudaGetLastError();
 }
@@ -266,16 +302,16 @@ template <typename T>
 cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
                          const double* afac, const double* gD, const double* gN, const double* lapt,
                          cudaStream_t st, const double* srcq) {
-  k_trace<T><<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq);
+  k_trace<T><<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq);
   return cudaGetLastError();
 }
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st) {
-  k_write_full<<<nblk(g.nfull, 256), 256, 0, st>>>(g, out, Uin, bnd);
+  k_write_full<<<dim3(nblk(g.nfull, 256), g.nb), 256, 0, st>>>(g, out, Uin, bnd);
   return cudaGetLastError();
 }
 cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,
                           cudaStream_t st) {
-  k_v_full<<<nblk(g.nfull, 256), 256, 0, st>>>(g, vfull, Vpad, Q, vedge);
+  k_v_full<<<dim3(nblk(g.nfull, 256), g.nb), 256, 0, st>>>(g, vfull, Vpad, Q, vedge);
   return cudaGetLastError();
 }
 cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st) {
@@ -287,7 +323,7 @@ cudaError_t launch_unpack(const Geom& g, double* padded, const double* dense, cu
   return cudaGetLastError();
 }
 cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, cudaStream_t st) {
-  k_face_gather<<<nblk(g.ngamma, 256), 256, 0, st>>>(g, face, full);
+  k_face_gather<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, face, full);
   return cudaGetLastError();
 }
 cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st) {
@@ -322,7 +358,9 @@ namespace ahoc {
 // ---------------------------------------------------------------------------
 __global__ void k_inject_full(Geom gc, Geom gf, double* __restrict__ out, const double* __restrict__ in) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= gc.nfull) return;
+  if (t >= gc.nfull || gc.skip(blockIdx.y)) return;
+  out += (int64_t)blockIdx.y * gc.nfull;
+  in += (int64_t)blockIdx.y * gf.nfull;
   const int i = (int)(t % gc.f0);
   const int64_t r = t / gc.f0;
   const int j = (int)(r % gc.f1);
@@ -348,7 +386,9 @@ __device__ __forceinline__ void face_coords(const Geom& g, int64_t q, int& a, in
 
 __global__ void k_inject_face(Geom gc, Geom gf, double* __restrict__ out, const double* __restrict__ in) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= gc.ngamma) return;
+  if (q >= gc.ngamma || gc.skip(blockIdx.y)) return;
+  out += (int64_t)blockIdx.y * gc.ngamma;
+  in += (int64_t)blockIdx.y * gf.ngamma;
   int a, side, c[3];
   face_coords(gc, q, a, side, c);
   out[q] = in[gf.face(a, side, 2 * c[0], 2 * c[1], 2 * c[2])];
@@ -377,7 +417,9 @@ __device__ __forceinline__ int prolong_weights(int cf, int Nc, int* node, double
 
 __global__ void k_face_prolong(Geom gf, Geom gc, double* __restrict__ out, const double* __restrict__ in) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= gf.ngamma) return;
+  if (q >= gf.ngamma || gf.skip(blockIdx.y)) return;
+  out += (int64_t)blockIdx.y * gf.ngamma;
+  in += (int64_t)blockIdx.y * gc.ngamma;
   int a, side, c[3];
   face_coords(gf, q, a, side, c);
   int rem[2] = {-1, -1}, nr = 0;
@@ -401,15 +443,15 @@ __global__ void k_face_prolong(Geom gf, Geom gc, double* __restrict__ out, const
 }
 
 cudaError_t launch_inject_full(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st) {
-  k_inject_full<<<nblk(gc.nfull, 256), 256, 0, st>>>(gc, gf, out, in);
+  k_inject_full<<<dim3(nblk(gc.nfull, 256), gc.nb), 256, 0, st>>>(gc, gf, out, in);
   return cudaGetLastError();
 }
 cudaError_t launch_inject_face(const Geom& gc, const Geom& gf, double* out, const double* in, cudaStream_t st) {
-  k_inject_face<<<nblk(gc.ngamma, 256), 256, 0, st>>>(gc, gf, out, in);
+  k_inject_face<<<dim3(nblk(gc.ngamma, 256), gc.nb), 256, 0, st>>>(gc, gf, out, in);
   return cudaGetLastError();
 }
 cudaError_t launch_face_prolong(const Geom& gf, const Geom& gc, double* out, const double* in, cudaStream_t st) {
-  k_face_prolong<<<nblk(gf.ngamma, 256), 256, 0, st>>>(gf, gc, out, in);
+  k_face_prolong<<<dim3(nblk(gf.ngamma, 256), gf.nb), 256, 0, st>>>(gf, gc, out, in);
   return cudaGetLastError();
 }
 
@@ -447,7 +489,20 @@ __global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __re
                            const double* __restrict__ f, const double* __restrict__ gD,
                            const double* __restrict__ vedge, const double* __restrict__ ainv) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.npad) return;
+  const int bi = blockIdx.y;
+  if (t >= g.npad || g.skip(bi)) return;
+  {
+    const int64_t po = (int64_t)bi * g.npad, fo = (int64_t)bi * g.nfull;
+    ru += po;
+    rv += po;
+    U += po;
+    V += po;
+    Q += (int64_t)bi * g.ngamma;
+    if (f) f += fo;
+    if (gD) gD += fo;
+    if (vedge) vedge += fo;
+    ainv += fo;
+  }
   int i, j, k;
   decompose(g, t, i, j, k);
   if (is_pad(g, i, j, k)) {
@@ -492,7 +547,18 @@ __global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const do
                              const double* __restrict__ gD, const double* __restrict__ gN,
                              const double* __restrict__ lapt) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= g.ngamma) return;
+  const int bi = blockIdx.y;
+  if (q >= g.ngamma || g.skip(bi)) return;
+  {
+    const int64_t fo = (int64_t)bi * g.ngamma;
+    rq += fo;
+    U += (int64_t)bi * g.npad;
+    Q += fo;
+    afac += fo;
+    if (gD) gD += (int64_t)bi * g.nfull;
+    if (gN) gN += fo;
+    if (lapt) lapt += fo;
+  }
   int a, side, c[3];
   face_coords(g, q, a, side, c);
   const int step = side ? -1 : 1;
@@ -511,11 +577,20 @@ __global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const do
 // partial sums of dU^2 and of the updated U^2 (the size of the correction
 // relative to the iterate, for the refinement's stopping test)
 constexpr int kAccThreads = 512;
-__global__ void __launch_bounds__(kAccThreads) k_accumulate(int64_t n, double* __restrict__ U, const float* __restrict__ dU,
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(Geom g, double* __restrict__ U, const float* __restrict__ dU,
                                                             double* __restrict__ V, const float* __restrict__ dV,
                                                             double* __restrict__ partial) {
   __shared__ double red[2][kAccThreads / 32];
   double sdu = 0.0, su = 0.0;
+  const int bi = blockIdx.y;
+  const int64_t n = g.skip(bi) ? 0 : g.npad;  // a masked problem contributes zero partials
+  {
+    const int64_t po = (int64_t)bi * g.npad;
+    U += po;
+    dU += po;
+    V += po;
+    dV += po;
+  }
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const double du = (double)dU[t];
     const double u = U[t] + du;
@@ -541,8 +616,10 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(int64_t n, double* _
       a += red[0][w];
       b += red[1][w];
     }
-    partial[2 * (int64_t)blockIdx.x] = a;
-    partial[2 * (int64_t)blockIdx.x + 1] = b;
+    // partial[block][problem][2]: column 2 bi + c of a (2 nb)-column reduction
+    const int64_t o = 2 * ((int64_t)blockIdx.x * g.nb + bi);
+    partial[o] = a;
+    partial[o + 1] = b;
   }
 }
 
@@ -550,19 +627,19 @@ cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
                             cudaStream_t st) {
-  k_residual<<<nblk(g.npad, 256), 256, 0, st>>>(g, cf, ru, rv, U, V, Q, f, gD, vedge, ainv);
+  k_residual<<<dim3(nblk(g.npad, 256), g.nb), 256, 0, st>>>(g, cf, ru, rv, U, V, Q, f, gD, vedge, ainv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_q<<<nblk(g.ngamma, 256), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt);
+  k_residual_q<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double* V, const float* dV,
                               double* partial, int nblocks, double* out, cudaStream_t st) {
-  k_accumulate<<<nblocks, kAccThreads, 0, st>>>(g.npad, U, dU, V, dV, partial);
+  k_accumulate<<<dim3(nblocks, g.nb), kAccThreads, 0, st>>>(g, U, dU, V, dV, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_reduce_cols(partial, nblocks, 2, out, st);
+  return launch_reduce_cols(partial, nblocks, 2 * g.nb, out, st);
 }
 
 }  // namespace ahoc

@@ -28,6 +28,8 @@ __device__ __forceinline__ float rmul(float q1, float x) { return fmaf(-q1, x, x
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes) {
+  if (g.skip(blockIdx.y)) return;
+  a += (int64_t)blockIdx.y * g.npad;
   const int nx = g.N[0] - 1;
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,6 +144,20 @@ __device__ __forceinline__ int64_t col_base(const Geom& g, int64_t m) {
   return ix + g.n0 * (int64_t)iy;
 }
 
+// per-problem scratch of the chunked solve: (4C + 1) ncols doubles
+__device__ __forceinline__ int64_t tri_sstride(const TriShape& sh) { return (4 * (int64_t)sh.C + 1) * sh.ncols; }
+
+// the generator arrays of problem b (rx: N1 + 1 apart, qy: 2 N0 apart)
+template <typename T>
+__device__ __forceinline__ void vgen_at(VGen2D<T>& G, const Geom& g, int b) {
+  if (!G.rxm) return;
+  const int64_t rs = (int64_t)b * (g.N[1] + 1), qs = (int64_t)b * 2 * g.N[0];
+  G.rxm += rs;
+  G.rxp += rs;
+  G.qhm += qs;
+  G.qhp += qs;
+}
+
 // generated right-hand side of the homogeneous v-equation (2D), see VGen2D
 template <typename T>
 __device__ __forceinline__ T vgen(const VGen2D<T>& G, int k, int j, int Nt) {
@@ -165,7 +181,11 @@ __device__ __forceinline__ T rhs_elem(const T* col, const VGen2D<T>& G, int k, i
 template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
                                                 double* __restrict__ E, VGen2D<T> G) {
+  if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
+  a += (int64_t)blockIdx.y * g.npad;
+  E += (int64_t)blockIdx.y * tri_sstride(sh);
+  vgen_at(G, g, blockIdx.y);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
   const int64_t m = t % sh.ncols;
@@ -187,7 +207,10 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
 
 __global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ E,
                           double* __restrict__ carry, int L) {
+  if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
+  E += (int64_t)blockIdx.y * tri_sstride(sh);
+  carry += (int64_t)blockIdx.y * tri_sstride(sh);
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= sh.ncols) return;
   const double r = modes[m].r;
@@ -215,7 +238,12 @@ __global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const 
 template <typename T, int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
                                                 const double* __restrict__ carry, double* __restrict__ B, VGen2D<T> G) {
+  if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
+  a += (int64_t)blockIdx.y * g.npad;
+  carry += (int64_t)blockIdx.y * tri_sstride(sh);
+  B += (int64_t)blockIdx.y * tri_sstride(sh);
+  vgen_at(G, g, blockIdx.y);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
   const int64_t m = t % sh.ncols;
@@ -250,7 +278,11 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
 
 __global__ void k_tri_t2b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ B,
                           double* __restrict__ bcarry, double* __restrict__ Cc, int L) {
+  if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
+  B += (int64_t)blockIdx.y * tri_sstride(sh);
+  bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
+  Cc += (int64_t)blockIdx.y * tri_sstride(sh);
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= sh.ncols) return;
   const double r = modes[m].r;
@@ -285,7 +317,11 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
                                                 const Mode<double>* __restrict__ md64,
                                                 const double* __restrict__ rpow,
                                                 const double* __restrict__ bcarry, const double* __restrict__ Cc) {
+  if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
+  a += (int64_t)blockIdx.y * g.npad;
+  bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
+  Cc += (int64_t)blockIdx.y * tri_sstride(sh);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
   const int64_t m = t % sh.ncols;
@@ -344,8 +380,8 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, cons
   double* bcarry = B + (int64_t)C * ncols;
   double* Cc = bcarry + (int64_t)C * ncols;
   const int64_t work = ncols * C;
-  const unsigned gb = (unsigned)((work + 127) / 128);
-  const unsigned cb = (unsigned)((ncols + 127) / 128);
+  const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
+  const dim3 cb((unsigned)((ncols + 127) / 128), (unsigned)g.nb);
   k_tri_t1<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, G);
   k_tri_t1b<<<cb, 128, 0, st>>>(g, md64, E, carry, L);
   k_tri_t2<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
@@ -425,7 +461,7 @@ cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t s
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int threads = 128;
   const int64_t blocks = (ncols + threads - 1) / threads;
-  k_tri<T><<<(unsigned)blocks, threads, 0, st>>>(g, a, modes);
+  k_tri<T><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, 0, st>>>(g, a, modes);
   return cudaGetLastError();
 }
 

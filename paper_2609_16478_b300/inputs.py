@@ -379,3 +379,159 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
 def _to_t(a, device):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+
+
+# ----------------------------------------------------------------------------
+# serving workload: a seeded stream of requests with closed-form data
+# ----------------------------------------------------------------------------
+#
+# Request r (r = 0, 1, ...) draws its grid, its coefficient and its exact
+# solution from numpy's default_rng(seed) stream (the shape mix) and from its
+# own id (the coefficient: the Fourier recipe above with M = 6, K = 4, A = 0.5
+# and seed r):
+#   * dim 2 with probability 0.7, N uniform in {128, 256, 512, 1024, 2048};
+#     dim 3 otherwise, N uniform in {64, 128, 256};
+#   * u = prod_a sin^2(pi x_a) cos(m_a pi x_a), m_a uniform in {0, ..., 4};
+#   * arrivals: a Poisson process (exponential gaps) of the given rate.
+# u vanishes with its normal derivative on every face, and alpha * Laplace u
+# vanishes on every edge, so all boundary data are zero; f is
+# -Laplace(alpha Laplace u) = -(alpha Lap^2 u + 2 grad alpha . grad Lap u +
+# Lap alpha Lap u), evaluated from closed-form derivatives (no symbolic work
+# per request).
+
+SERVE_2D = (128, 256, 512, 1024, 2048)
+SERVE_3D = (64, 128, 256)
+
+
+@dataclass
+class RequestSpec:
+    rid: int
+    dim: int
+    N: int
+    m: Tuple[int, ...]
+    arrival: float  # seconds from the start of the stream
+
+
+def request_stream(n: int, rate: float, seed: int = 5, p2d: float = 0.7,
+                   sizes2d: Sequence[int] = SERVE_2D, sizes3d: Sequence[int] = SERVE_3D) -> List[RequestSpec]:
+    """n requests with Poisson arrivals of `rate` per second."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(n):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        if rng.uniform() < p2d:
+            dim, N = 2, int(rng.choice(sizes2d))
+        else:
+            dim, N = 3, int(rng.choice(sizes3d))
+        m = tuple(int(v) for v in rng.integers(0, 5, size=dim))
+        out.append(RequestSpec(r, dim, N, m, t))
+    return out
+
+
+def _cos_terms(m: int):
+    """sin^2(pi x) cos(m pi x) as a sum of a_j cos(w_j x)."""
+    return [(0.5, m * math.pi), (-0.25, (m + 2) * math.pi), (-0.25, (m - 2) * math.pi)]
+
+
+def _g_derivs(x, m: int):
+    """g, g', g'', g''', g'''' of g(x) = sin^2(pi x) cos(m pi x) at x (torch)."""
+    import torch
+    out = [torch.zeros_like(x) for _ in range(5)]
+    for a, w in _cos_terms(m):
+        c, s = torch.cos(w * x), torch.sin(w * x)
+        out[0] += a * c
+        out[1] += -a * w * s
+        out[2] += -a * w ** 2 * c
+        out[3] += a * w ** 3 * s
+        out[4] += a * w ** 4 * c
+    return out
+
+
+_ALPHA_MAX: Dict[Tuple[int, int], float] = {}
+
+
+def _alpha_norm(dim: int, modes, device) -> float:
+    import torch
+    L = 1024 if dim == 2 else 128
+    t = torch.linspace(0.0, 1.0, L + 1, dtype=torch.float64, device=device)
+    grids = torch.meshgrid(*([t] * dim), indexing="ij")
+    val = torch.zeros_like(grids[0])
+    for k, c, th in modes:
+        val += c * torch.cos(2 * math.pi * sum(k[a] * grids[a] for a in range(dim)) + th)
+    return float(val.abs().max())
+
+
+def sample_request(spec: RequestSpec, device="cuda", out_alpha=None, out_f=None, with_exact: bool = False,
+                   M: int = 6, K: int = 4, A: float = 0.5) -> Dict[str, object]:
+    """alpha and f of a request on its full grid (float64 tensors on device);
+    written into out_alpha / out_f (flat views) when given."""
+    import torch
+    dim, N = spec.dim, spec.N
+    modes = fourier_modes(dim, M, K, spec.rid)
+    mx = _alpha_norm(dim, modes, device)
+    x = torch.arange(N + 1, dtype=torch.float64, device=device) / N
+    g = [_g_derivs(x, spec.m[a]) for a in range(dim)]
+
+    def axis(v, a):  # 1D array along axis a of the (reversed) full-grid shape
+        shp = [1] * dim
+        shp[dim - 1 - a] = N + 1
+        return v.reshape(shp)
+
+    G = [[axis(g[a][k], a) for k in range(5)] for a in range(dim)]
+    shape = (N + 1,) * dim
+
+    def prod(parts):
+        out = parts[0]
+        for q in parts[1:]:
+            out = out * q
+        return out.expand(shape) if out.shape != shape else out
+
+    # alpha and its derivatives
+    al = torch.ones(shape, dtype=torch.float64, device=device)
+    dal = [torch.zeros(shape, dtype=torch.float64, device=device) for _ in range(dim)]
+    lal = torch.zeros(shape, dtype=torch.float64, device=device)
+    X_ = [axis(x, a) for a in range(dim)]
+    for k, c, th in modes:
+        ph = 2 * math.pi * sum(k[a] * X_[a] for a in range(dim)) + th
+        cph, sph = torch.cos(ph), torch.sin(ph)
+        s = A * c / mx
+        al = al + s * cph
+        for a in range(dim):
+            dal[a] = dal[a] - s * 2 * math.pi * k[a] * sph
+        lal = lal - s * (2 * math.pi) ** 2 * sum(kk * kk for kk in k) * cph
+    # Laplace u, its gradient and the bi-Laplacian of the separable u
+    def term(sel):  # product over axes of G[a][sel[a]]
+        return prod([G[a][sel[a]] for a in range(dim)])
+    lap = sum(term([2 if b == a else 0 for b in range(dim)]) for a in range(dim))
+    glap = []
+    for c in range(dim):
+        acc = 0
+        for a in range(dim):
+            sel = [2 if b == a else 0 for b in range(dim)]
+            sel[c] += 1
+            acc = acc + term(sel)
+        glap.append(acc)
+    bil = 0
+    for a in range(dim):
+        for c in range(dim):
+            sel = [0] * dim
+            sel[a] += 2
+            sel[c] += 2
+            bil = bil + term(sel)
+    f = -(al * bil + 2 * sum(dal[c] * glap[c] for c in range(dim)) + lal * lap)
+    res: Dict[str, object] = {"dim": dim, "N": [N] * dim, "lo": (0.0,) * dim, "hi": (1.0,) * dim,
+                              "name": "request%d" % spec.rid}
+    if out_alpha is not None:
+        out_alpha.copy_(al.reshape(-1))
+        res["alpha"] = out_alpha
+    else:
+        res["alpha"] = al.reshape(-1).contiguous()
+    if out_f is not None:
+        out_f.copy_(f.reshape(-1))
+        res["f"] = out_f
+    else:
+        res["f"] = f.reshape(-1).contiguous()
+    if with_exact:
+        res["u_exact"] = term([0] * dim).reshape(-1).contiguous()
+    return res
