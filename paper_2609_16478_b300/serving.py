@@ -1,0 +1,355 @@
+"""Continuous-batching request server for the augmented HOC solver.
+
+Requests (a grid, a coefficient and a right-hand side; see
+``inputs.request_stream``) arrive over time.  The server keeps, per grid
+shape (dim, N), a pool of batched plans resident on the device -- the DST
+twiddles, the per-mode tridiagonal factors, the preconditioner symbols and
+the Krylov bases stay allocated between requests -- and admits work by an
+HBM budget:
+
+  * every shape has a FIFO queue; a worker takes up to B queued requests of
+    one shape (B: the shape's batch size, from the tuner or a default) as
+    soon as a plan of that shape is idle, loads each request's coefficient
+    into a slot of the plan (``ahoc_plan_load``), masks the unused slots
+    (``ahoc_set_active``) and solves the batch in one set of launches;
+  * a new plan is allocated only if the pool's device bytes stay within the
+    budget, after evicting idle plans of other shapes (least recently used
+    first); otherwise the request waits for a plan to free up;
+  * several workers, each with its own CUDA stream, run batches of different
+    (or the same) shapes at once, so requests that arrive while others are
+    on the GPU are admitted as slots free up and their work overlaps.
+
+A problem's result does not depend on the batch it was solved in: batched
+plans give every problem the bits of its own single-problem solve.
+
+The admission and batching policy (``Scheduler``) is plain host code with no
+device work, so it can be exercised without a GPU.
+"""
+
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Callable, Deque, Dict, List, Optional, Sequence, Tuple
+
+Key = Tuple[int, int]  # (dim, N)
+
+
+# ----------------------------------------------------------------------------
+# host-side policy
+# ----------------------------------------------------------------------------
+
+@dataclass
+class SlotState:
+    key: Key
+    batch: int
+    nbytes: int
+    busy: bool = False
+    last_used: float = 0.0
+    handle: object = None  # the executor's plan object (None until created)
+
+
+@dataclass
+class Work:
+    key: Key
+    slot: SlotState
+    reqs: list
+    new_slot: bool  # the executor must create the slot's plan first
+
+
+class Scheduler:
+    """Admission and batching by shape under a device-memory budget.
+
+    batch_for(key) gives a shape's batch size, plan_bytes(key, batch) the
+    device bytes of one plan with its buffers.  Not thread-safe: the caller
+    holds a lock around every call.
+    """
+
+    def __init__(self, budget_bytes: int, batch_for: Callable[[Key], int],
+                 plan_bytes: Callable[[Key, int], int], max_slots_per_key: int = 4):
+        self.budget = int(budget_bytes)
+        self.batch_for = batch_for
+        self.plan_bytes = plan_bytes
+        self.max_slots = max_slots_per_key
+        self.queues: Dict[Key, Deque] = {}
+        self.slots: Dict[Key, List[SlotState]] = {}
+        self.used = 0
+        self.evicted: List[SlotState] = []  # plans the executor must free
+
+    @staticmethod
+    def key_of(req) -> Key:
+        return (req.dim, req.N)
+
+    def arrive(self, req) -> None:
+        self.queues.setdefault(self.key_of(req), deque()).append(req)
+
+    def pending(self) -> int:
+        return sum(len(q) for q in self.queues.values())
+
+    def _evict_for(self, need: int, keep: Key) -> bool:
+        """Evict idle plans of other shapes (LRU) until `need` more bytes fit."""
+        if self.used + need <= self.budget:
+            return True
+        idle = [s for k, ss in self.slots.items() if k != keep for s in ss if not s.busy]
+        idle.sort(key=lambda s: s.last_used)
+        freed = 0
+        victims = []
+        for s in idle:
+            if self.used - freed + need <= self.budget:
+                break
+            victims.append(s)
+            freed += s.nbytes
+        if self.used - freed + need > self.budget:
+            return False
+        for s in victims:
+            self.slots[s.key].remove(s)
+            self.used -= s.nbytes
+            self.evicted.append(s)
+        return True
+
+    def next_work(self, now: float) -> Optional[Work]:
+        """The batch to run next: the shape whose oldest request has waited
+        longest among shapes with an idle plan or room for a new one."""
+        order = sorted((q[0].arrival, k) for k, q in self.queues.items() if q)
+        for _, k in order:
+            ss = self.slots.setdefault(k, [])
+            slot = next((s for s in ss if not s.busy), None)
+            new = False
+            if slot is None:
+                if len(ss) >= self.max_slots:
+                    continue
+                B = max(1, int(self.batch_for(k)))
+                nb = int(self.plan_bytes(k, B))
+                while nb > self.budget and B > 1:  # a smaller batch when one plan would not fit
+                    B //= 2
+                    nb = int(self.plan_bytes(k, B))
+                if not self._evict_for(nb, k):
+                    # nothing else resident and still too large: run it over budget rather than starve
+                    if self.used != 0:
+                        continue
+                slot = SlotState(k, B, nb)
+                ss.append(slot)
+                self.used += nb
+                new = True
+            q = self.queues[k]
+            reqs = [q.popleft() for _ in range(min(slot.batch, len(q)))]
+            slot.busy = True
+            slot.last_used = now
+            return Work(k, slot, reqs, new)
+        return None
+
+    def release(self, work: Work, now: float) -> None:
+        work.slot.busy = False
+        work.slot.last_used = now
+
+    def take_evicted(self) -> List[SlotState]:
+        out, self.evicted = self.evicted, []
+        return out
+
+
+# ----------------------------------------------------------------------------
+# device executor
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Record:
+    rid: int
+    dim: int
+    N: int
+    arrival: float
+    start: float = 0.0
+    done: float = 0.0
+    batch: int = 0       # requests solved together with this one (itself included)
+    status: int = -1
+    iters: int = 0
+    refine_steps: int = 0
+    err_inf: Optional[float] = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+    @property
+    def dof(self) -> int:
+        return (self.N - 1) ** self.dim
+
+
+def default_batch(key: Key) -> int:
+    """Problems per launch: enough grid points to fill the GPU (about 4M
+    interior points per batch), at most 16."""
+    dim, N = key
+    pts = (N - 1) ** dim
+    return int(max(1, min(16, (4 << 20) // max(pts, 1))))
+
+
+class Server:
+    """Solve a request stream with batched plans on several CUDA streams.
+
+    prec: "mixed" (FP32 inner solves, FP64 refinement) or "fp64";
+    tol: relative Schur residual of every solve; workers: concurrent batches;
+    batch_for: per-shape batch size (default ``default_batch``; 1 gives the
+    plain one-request-per-solve server).
+    """
+
+    def __init__(self, device="cuda", prec="mixed", tol: float = 1e-10, workers: int = 4,
+                 budget_bytes: Optional[int] = None, batch_for: Optional[Callable[[Key], int]] = None,
+                 restart: int = 60, keep_results: bool = False, check_exact: bool = False):
+        import torch
+
+        from . import ahoc
+        self.torch = torch
+        self.ahoc = ahoc
+        self.device = torch.device(device)
+        self.prec = prec
+        self.tol = tol
+        self.workers = workers
+        self.restart = restart
+        self.keep = keep_results
+        self.check_exact = check_exact
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(0.6 * free)
+        self.sched = Scheduler(budget_bytes, batch_for or default_batch, self._plan_bytes)
+        self.results: Dict[int, object] = {}
+        self.records: Dict[int, Record] = {}
+        self.cv = threading.Condition()
+        self.error: Optional[BaseException] = None
+
+    def _plan_bytes(self, key: Key, B: int) -> int:
+        dim, N = key
+        ws = self.ahoc.workspace_bytes(dim, [N] * dim, self.restart, self.prec, -1, B)
+        return ws + 3 * B * (N + 1) ** dim * 8  # + alpha, f, u buffers
+
+    # one plan of a shape, with its buffers and stream
+    class _Slot:
+        def __init__(self, srv: "Server", key: Key, B: int):
+            torch = srv.torch
+            dim, N = key
+            self.stream = torch.cuda.Stream(device=srv.device)
+            nf = (N + 1) ** dim
+            self.nf = nf
+            with torch.cuda.stream(self.stream):
+                self.alpha = torch.ones(B * nf, dtype=torch.float64, device=srv.device)
+                self.f = torch.zeros(B * nf, dtype=torch.float64, device=srv.device)
+                self.u = torch.zeros(B * nf, dtype=torch.float64, device=srv.device)
+                self.plan = srv.ahoc.Plan(dim, [N] * dim, self.alpha, prec=srv.prec, restart=srv.restart,
+                                          batch=B, stream=self.stream, max_iters=2000)
+            self.stream.synchronize()
+
+        def close(self):
+            self.plan.close()
+
+    def _run_work(self, w: Work) -> None:
+        from . import inputs
+        torch = self.torch
+        if w.new_slot:
+            w.slot.handle = Server._Slot(self, w.key, w.slot.batch)
+        sl: Server._Slot = w.slot.handle
+        t0 = time.perf_counter()
+        B = w.slot.batch
+        nf = sl.nf
+        with torch.cuda.stream(sl.stream):
+            for i, spec in enumerate(w.reqs):
+                inputs.sample_request(spec, device=self.device, out_alpha=sl.alpha[i * nf:(i + 1) * nf],
+                                      out_f=sl.f[i * nf:(i + 1) * nf])
+                sl.plan.load(i, sl.alpha[i * nf:(i + 1) * nf])
+            sl.plan.set_active([1 if i < len(w.reqs) else 0 for i in range(B)])
+            _, infos = sl.plan.solve(sl.f, sl.u, tol=self.tol, check=False)
+            if B == 1:
+                infos = [infos]
+            outs = []
+            for i, spec in enumerate(w.reqs):
+                ui = sl.u[i * nf:(i + 1) * nf]
+                err = None
+                if self.check_exact:
+                    ex = inputs.sample_request(spec, device=self.device, with_exact=True)["u_exact"]
+                    err = float((ui - ex).abs().max())
+                outs.append((ui.clone() if self.keep else None, err))
+            sl.stream.synchronize()
+        t1 = time.perf_counter()
+        for i, spec in enumerate(w.reqs):
+            r = self.records[spec.rid]
+            r.start, r.done, r.batch = t0, t1, len(w.reqs)
+            r.status, r.iters, r.refine_steps = infos[i]["status"], infos[i]["iters"], infos[i]["refine_steps"]
+            r.err_inf = outs[i][1]
+            if self.keep:
+                self.results[spec.rid] = outs[i][0]
+
+    def _worker(self, t_start: float) -> None:
+        try:
+            while True:
+                with self.cv:
+                    while True:
+                        if self.error is not None:
+                            return
+                        if self._fed and self.sched.pending() == 0:
+                            return  # every request is taken; in-flight batches finish on their workers
+                        w = self.sched.next_work(time.perf_counter() - t_start)
+                        if w is not None:
+                            evicted = self.sched.take_evicted()
+                            break
+                        self.cv.wait(timeout=0.05)
+                for s in evicted:
+                    if s.handle is not None:
+                        s.handle.close()
+                        s.handle = None
+                self._run_work(w)
+                with self.cv:
+                    self.sched.release(w, time.perf_counter() - t_start)
+                    self.cv.notify_all()
+        except BaseException as e:  # surface worker failures to run()
+            with self.cv:
+                self.error = e
+                self.cv.notify_all()
+
+    def run(self, specs: Sequence, realtime: bool = True) -> List[Record]:
+        """Feed the requests at their arrival times (or all at once) and solve them."""
+        self.records = {s.rid: Record(s.rid, s.dim, s.N, s.arrival) for s in specs}
+        self._fed = False
+        t_start = time.perf_counter()
+        threads = [threading.Thread(target=self._worker, args=(t_start,), daemon=True)
+                   for _ in range(self.workers)]
+        for t in threads:
+            t.start()
+        for s in sorted(specs, key=lambda r: r.arrival):
+            if realtime:
+                dt = s.arrival - (time.perf_counter() - t_start)
+                if dt > 0:
+                    time.sleep(dt)
+            with self.cv:
+                self.sched.arrive(s)
+                self.records[s.rid].arrival = s.arrival if realtime else 0.0
+                self.cv.notify_all()
+        with self.cv:
+            self._fed = True
+            self.cv.notify_all()
+        for t in threads:
+            t.join()
+        if self.error is not None:
+            raise self.error
+        for r in self.records.values():
+            r.start -= t_start
+            r.done -= t_start
+        return [self.records[s.rid] for s in specs]
+
+    def close(self) -> None:
+        for ss in self.sched.slots.values():
+            for s in ss:
+                if s.handle is not None:
+                    s.handle.close()
+                    s.handle = None
+
+
+def summarize(records: Sequence[Record]) -> Dict[str, float]:
+    """p50/p99 latency (ms), aggregate DOF/s over the makespan, batch sizes."""
+    import numpy as np
+    lat = np.array([r.latency for r in records]) * 1e3
+    t0 = min(r.arrival for r in records)
+    t1 = max(r.done for r in records)
+    dof = sum(r.dof for r in records)
+    return dict(requests=len(records), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                mean_ms=float(lat.mean()), makespan_s=t1 - t0, dof_per_s=dof / (t1 - t0),
+                mean_batch=float(np.mean([r.batch for r in records])),
+                failed=int(sum(1 for r in records if r.status != 0)))
