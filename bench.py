@@ -178,6 +178,71 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serving_variant(args, dev):
+    """The serving workload: a seeded Poisson stream of requests of mixed
+    dimension, size, coefficient and right-hand side, at 80% of the measured
+    sequential mixed-path capacity; the batched mixed-precision server
+    against one-at-a-time plain FP64 solves of the same stream."""
+    import numpy as np
+    import torch
+
+    from paper_2609_16478_b300 import ahoc, inputs, serving
+
+    tol = args.serve_tol
+    p3 = 0.3
+    mix = {(2, n): (1 - p3) / len(inputs.SERVE_2D) for n in inputs.SERVE_2D}
+    mix.update({(3, n): p3 / len(inputs.SERVE_3D) for n in inputs.SERVE_3D})
+    # sequential capacity of the mixed path, one warm solve per shape
+    t_seq = {}
+    for (dim, n) in mix:
+        d = inputs.sample_request(inputs.RequestSpec(10 ** 6, dim, n, (1,) * dim, 0.0), device=dev)
+        p = ahoc.Plan(dim, [n] * dim, d["alpha"], prec="mixed", restart=60, max_iters=2000)
+        p.solve(d["f"], tol=tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.solve(d["f"], tol=tol)
+        t_seq[(dim, n)] = time.perf_counter() - t0
+        p.close()
+    cap = 1.0 / sum(mix[k] * t_seq[k] for k in mix)
+    rate = 0.8 * cap
+    specs = inputs.request_stream(args.serve_requests, rate, seed=5)
+
+    def warm_specs(batch_for):
+        out, rid = [], 10 ** 7
+        for (dim, n) in mix:
+            for _ in range(batch_for((dim, n))):
+                out.append(inputs.RequestSpec(rid, dim, n, (0,) * dim, 0.0))
+                rid += 1
+        return out
+
+    def arm(prec, workers, batch_for):
+        srv = serving.Server(device=dev, prec=prec, tol=tol, workers=workers, batch_for=batch_for,
+                             check_exact=True)
+        srv.run(warm_specs(batch_for or serving.default_batch), realtime=False)  # plans resident
+        recs = srv.run(specs, realtime=True)
+        srv.close()
+        torch.cuda.empty_cache()
+        return recs, serving.summarize(recs)
+
+    ra, sa = arm("mixed", args.serve_workers, None)
+    rb, sb = arm("fp64", 1, lambda k: 1)
+    ea = {r.rid: r.err_inf for r in ra}
+    eb = {r.rid: r.err_inf for r in rb}
+    ratio = max(ea[i] / eb[i] for i in ea if eb[i] > 0)
+    return {
+        "workload": "%d requests, Poisson arrivals (seed 5) at %.1f req/s = 80%% of the sequential mixed-path "
+                    "capacity %.1f req/s; 2D N in %s (p=0.7), 3D N in %s; per-request Fourier coefficient "
+                    "(M=6, K=4, A=0.5, seed = request id) and u = prod sin^2(pi x) cos(m pi x), m in 0..4; "
+                    "Schur tol %g" % (len(specs), rate, cap, list(inputs.SERVE_2D), list(inputs.SERVE_3D), tol),
+        "batched_mixed": dict(sa, workers=args.serve_workers, batch="default_batch (about 4M points, <= 16)"),
+        "sequential_fp64": dict(sb, workers=1, batch=1),
+        "p99_speedup": sb["p99_ms"] / sa["p99_ms"], "dof_per_s_ratio": sa["dof_per_s"] / sb["dof_per_s"],
+        "max_err_ratio_mixed_over_fp64": ratio,
+        "max_err_inf": max(max(ea.values()), max(eb.values())),
+        "seq_mixed_ms_per_shape": {"%dD N=%d" % k: 1e3 * v for k, v in t_seq.items()},
+    }
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -296,6 +361,10 @@ def run_ours(args, rank, world, local):
             "kernel_ms_per_step": {k: sum(i["kernel_ms"][k] for i in ims) / args.steps for k in ahoc.KERNEL_NAMES},
             "launches_per_step": sum(i["launches"] for i in ims) // args.steps}
         pm.close()
+    if not args.no_serve and world == 1:
+        del plan
+        torch.cuda.empty_cache()
+        variants["serving"] = serving_variant(args, dev)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, dt, _ = cpu_oracle_sample(args.cpu_n)
@@ -340,6 +409,10 @@ def main():
     ap.add_argument("--levels", type=int, default=-1, help="coarse levels of the nested initial guess (-1 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-tol", type=float, default=1e-12)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

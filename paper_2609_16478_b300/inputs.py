@@ -462,6 +462,20 @@ def _alpha_norm(dim: int, modes, device) -> float:
     return float(val.abs().max())
 
 
+def exact_request(spec: RequestSpec, device="cuda"):
+    """The exact u of a request on its full grid (flat float64 tensor)."""
+    import torch
+    dim, N = spec.dim, spec.N
+    x = torch.arange(N + 1, dtype=torch.float64, device=device) / N
+    out = None
+    for a in range(dim):
+        shp = [1] * dim
+        shp[dim - 1 - a] = N + 1
+        g = _g_derivs(x, spec.m[a])[0].reshape(shp)
+        out = g if out is None else out * g
+    return out.expand((N + 1,) * dim).reshape(-1).contiguous()
+
+
 def sample_request(spec: RequestSpec, device="cuda", out_alpha=None, out_f=None, with_exact: bool = False,
                    M: int = 6, K: int = 4, A: float = 0.5) -> Dict[str, object]:
     """alpha and f of a request on its full grid (float64 tensors on device);

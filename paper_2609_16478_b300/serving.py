@@ -264,8 +264,7 @@ class Server:
                 ui = sl.u[i * nf:(i + 1) * nf]
                 err = None
                 if self.check_exact:
-                    ex = inputs.sample_request(spec, device=self.device, with_exact=True)["u_exact"]
-                    err = float((ui - ex).abs().max())
+                    err = float((ui - inputs.exact_request(spec, self.device)).abs().max())
                 outs.append((ui.clone() if self.keep else None, err))
             sl.stream.synchronize()
         t1 = time.perf_counter()
