@@ -87,9 +87,10 @@ typedef struct {
                              block rows, FP64 GMRES vectors, Hessenberg and updates); the
                              stopping test is the same relative Schur residual, evaluated
                              from the FP64 residual of the iterate.  When a step removes
-                             less than a tenth of it (limiting accuracy), the solve has converged if the
-                             last correction changed U by at most tol (relative 2-norm;
-                             rel_resid may then exceed tol) and returns AHOC_ENOCONV
+                             less than a tenth of it (limiting accuracy), the solve has
+                             converged if the last correction changed U by at most tol
+                             (relative 2-norm; rel_resid may then exceed tol), refines on
+                             while the corrections at least halve, and returns AHOC_ENOCONV
                              otherwise.  In a MIXED plan ahoc_matvec runs the FP32 inner
                              solves.                                                           */
   int max_iters;          /* [500] total GMRES iterations allowed                               */
@@ -123,6 +124,12 @@ typedef struct {
                              out of later launches, so each result is the one a single-problem
                              plan gives.  Per-problem arguments (alpha, data, f, u, q, y, b)
                              hold `batch` arrays of their single-problem size back to back.  */
+  int no_graphs;          /* [0] 0: each GMRES iteration (mask and scalar uploads, the
+                             normalisation of v_j, the preconditioner, the Schur matvec, CGS2
+                             and the read-back of the Hessenberg column) is captured once as a
+                             CUDA graph per iteration index and replayed; needs a stream other
+                             than the legacy default stream and timing == 0.  nonzero: plain
+                             launches.                                                         */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -133,7 +140,7 @@ typedef struct {
   int restarts;
   double rel_resid;       /* ||b - S_h Q|| / ||b|| estimated by GMRES at exit                   */
   double ms_total;        /* wall time of the last ahoc_solve, host clock                       */
-  double ms_matvec;       /* device time of the matvecs of the last solve (CUDA events)         */
+  double ms_matvec;       /* device time of the Arnoldi steps (preconditioner, matvec, CGS2)   */
   int64_t launches;       /* kernels this library launched during the last solve                */
   double kernel_ms[AHOC_NK];      /* with opts.timing: summed device time per kernel class      */
   int64_t kernel_launches[AHOC_NK];

@@ -40,7 +40,7 @@ class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
-                ("batch", C.c_int)]
+                ("batch", C.c_int), ("no_graphs", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -127,9 +127,10 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1):
+          batch=1, graphs=True):
     o = ahoc_opts()
     o.batch = int(batch)
+    o.no_graphs = 0 if graphs else 1
     o.coarse_tol = float(coarse_tol)
     o.timing = int(timing)
     o.levels = int(levels)
@@ -180,7 +181,8 @@ class Plan:
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
-                 levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1):
+                 levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
+                 graphs: bool = True):
         L = lib()
         self.dim = dim
         self.batch = int(batch)
@@ -209,7 +211,7 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, B * self.nfull, "g_D"), _ptr(g_N, B * self.ngamma, "g_N"),
                         _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"))
-        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B)
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)

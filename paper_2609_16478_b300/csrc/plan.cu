@@ -48,6 +48,7 @@ struct Opts {
   double refine_tol = 3e-6;  // mixed precision: relative residual of each FP32 correction solve
   double coarse_tol = AHOC_COARSE_TOL_AUTO;  // relative Schur residual of the coarse levels
   int batch = 1;  // problems of this shape solved together
+  int graphs = 1;  // replay GMRES iterations as CUDA graphs
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -64,6 +65,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
     if (o->coarse_tol > 0) d.coarse_tol = o->coarse_tol;
     if (o->batch > 0) d.batch = o->batch;
+    d.graphs = o->no_graphs ? 0 : 1;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -438,6 +440,18 @@ struct ahoc_plan {
   std::vector<ProbStat> ps;
   bool has_gD = false, has_vedge = false, has_gN = false, has_lapt = false;
   double* hhost = nullptr;  // pinned
+  // CUDA graphs of the GMRES iterations, one per iteration index, captured on
+  // first use; the per-problem scalars and the mask reach them through
+  // pinned host arrays copied inside the graph
+  struct GCount {
+    int64_t launches = 0;
+    int64_t kn[AHOC_NK] = {0};
+  };
+  bool use_graphs = false;
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<GCount> gcount;
+  double* scal_h = nullptr;  // pinned
+  int* act_h = nullptr;      // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool have_last = false;
   // launch accounting (and, with opts.timing, per-launch CUDA events)
@@ -915,6 +929,11 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->part.assign(g.nb, 1);
   p->ps.assign(g.nb, ProbStat{});
   CKC(cudaMallocHost(&p->hhost, B * (size_t)hstride(o) * sizeof(double)));
+  CKC(cudaMallocHost(&p->scal_h, B * sizeof(double)));
+  CKC(cudaMallocHost(&p->act_h, B * sizeof(int)));
+  p->use_graphs = o.graphs && !o.timing && stream != nullptr && stream != cudaStreamLegacy;
+  p->gexec.assign(o.restart, nullptr);
+  p->gcount.assign(o.restart, ahoc_plan::GCount{});
   CKC(cudaEventCreate(&p->ev0));
   CKC(cudaEventCreate(&p->ev1));
   // zero padding of the fields and zero boundary data until a problem brings its own
@@ -1126,6 +1145,10 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
   }
   if (p->own_ws && p->ws) cudaFree(p->ws);
   if (p->hhost) cudaFreeHost(p->hhost);
+  if (p->scal_h) cudaFreeHost(p->scal_h);
+  if (p->act_h) cudaFreeHost(p->act_h);
+  for (auto& ge : p->gexec)
+    if (ge) cudaGraphExecDestroy(ge);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   for (auto& ev : p->pool) {
@@ -1190,6 +1213,79 @@ ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
 
 namespace {
 
+// One Arnoldi step j for every problem in the mask: v_j = src * scal[b]
+// (src = r at j = 0, v_j itself after), z_j = P^-1 v_j, w = v_{j+1} = S z_j,
+// CGS2 of w against v_0..v_j (the coefficients of both passes and ||w||^2 in
+// the Hessenberg exchange area), then that area to the pinned host copy.
+ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
+  const Geom& g = p->g;
+  const int64_t n = g.ngamma;
+  double* vj = p->Kry + (int64_t)j * ld;
+  double* w = p->Kry + (int64_t)(j + 1) * ld;
+  double* zj = p->Zb + (int64_t)j * ld;
+  RUN(AHOC_K_KRYLOV, launch_axpby(vj, src, 0.0, 0.0, n, p->st, g.nb, p->scal, g.act));
+  CKS(precond_apply(p, vj, zj));
+  CKS(matvec_dev(p, zj, w));
+  CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev));
+  CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev, w, nullptr));
+  CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev + (j + 1)));
+  CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev + (j + 1), w, nullptr));
+  CKS(mdot(p, w, n, 1, w, p->hdev + 2 * (j + 1)));
+  CK(cudaMemcpyAsync(p->hhost, p->hdev, (size_t)g.nb * hstride(p->o) * sizeof(double), cudaMemcpyDeviceToHost,
+                     p->st));
+  return AHOC_OK;
+}
+
+// Run Arnoldi step j with the mask in act_h and the scalars in scal_h: as a
+// replay of its CUDA graph (captured here the first time), or as plain
+// launches.  Returns after the host copy of the Hessenberg area is complete.
+ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
+  const int nb = p->g.nb;
+  if (p->use_graphs && !p->gexec[j]) {
+    const int64_t l0 = p->launches;
+    int64_t k0[AHOC_NK];
+    for (int k = 0; k < AHOC_NK; ++k) k0[k] = p->kn[k];
+    CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+    ahoc_status s = AHOC_OK;
+    if (cudaMemcpyAsync(p->act, p->act_h, nb * sizeof(int), cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
+        cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st) != cudaSuccess)
+      s = fail(AHOC_ECUDA, "copy in graph capture");
+    if (s == AHOC_OK) s = arnoldi_step(p, j, ld, src);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+    cudaError_t ei = cudaSuccess;
+    if (s == AHOC_OK && e == cudaSuccess) ei = cudaGraphInstantiate(&p->gexec[j], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    // the capture issued nothing: count the graph's launches per replay instead
+    ahoc_plan::GCount& gc = p->gcount[j];
+    gc.launches = p->launches - l0;
+    p->launches = l0;
+    for (int k = 0; k < AHOC_NK; ++k) {
+      gc.kn[k] = p->kn[k] - k0[k];
+      p->kn[k] = k0[k];
+    }
+    if (s != AHOC_OK) return s;
+    if (e != cudaSuccess) return fail(AHOC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (ei != cudaSuccess) {
+      p->gexec[j] = nullptr;
+      return fail(AHOC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+  }
+  if (p->use_graphs) {
+    CK(cudaGraphLaunch(p->gexec[j], p->st));
+    const ahoc_plan::GCount& gc = p->gcount[j];
+    p->launches += gc.launches;
+    for (int k = 0; k < AHOC_NK; ++k) p->kn[k] += gc.kn[k];
+    p->act_now.assign(p->act_h, p->act_h + nb);
+  } else {
+    CKS(set_act(p, std::vector<int>(p->act_h, p->act_h + nb)));
+    CK(cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CKS(arnoldi_step(p, j, ld, src));
+  }
+  CK(cudaStreamSynchronize(p->st));
+  return harvest(p);
+}
+
 // Flexible GMRES on S X = b for every problem of the batch in lockstep
 // (right-preconditioned with the boundary-symbol operator, whose inexact
 // FP32 application is absorbed by storing the directions z_j = P^-1 v_j;
@@ -1238,7 +1334,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       if (go[i].rel <= tol[i]) live[i] = 0;
     }
   std::vector<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), gv((size_t)nb * (m + 1)),
-      y(m), sc(nb, 0.0), hy((size_t)nb * hs, 0.0);
+      y(m), hy((size_t)nb * hs, 0.0);
   std::vector<int> jend(nb, 0), cyc(nb, 0), nc(nb, 0);
   while (any(live)) {
     for (int i = 0; i < nb; ++i)
@@ -1248,30 +1344,18 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       }
     if (!any(live)) break;
     cyc = live;
-    CKS(set_act(p, live));
     for (int i = 0; i < nb; ++i) {
-      sc[i] = live[i] ? 1.0 / beta[i] : 0.0;
+      p->scal_h[i] = live[i] ? 1.0 / beta[i] : 0.0;
       jend[i] = 0;
       std::fill(gv.begin() + (size_t)i * (m + 1), gv.begin() + (size_t)(i + 1) * (m + 1), 0.0);
       gv[(size_t)i * (m + 1)] = beta[i];
     }
-    CK(cudaMemcpyAsync(p->scal, sc.data(), nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->Kry, p->r, 0.0, 0.0, n, p->st, nb, p->scal, g.act));
     for (int j = 0; j < m; ++j) {
-      double* vj = p->Kry + (int64_t)j * ld;
-      double* w = p->Kry + (int64_t)(j + 1) * ld;
-      double* zj = p->Zb + (int64_t)j * ld;
+      for (int i = 0; i < nb; ++i) p->act_h[i] = live[i];
       CK(cudaEventRecord(p->ev0, p->st));
-      CKS(precond_apply(p, vj, zj));
-      CKS(matvec_dev(p, zj, w));
+      CKS(arnoldi_launch(p, j, ld, j == 0 ? p->r : p->Kry + (int64_t)j * ld));
       CK(cudaEventRecord(p->ev1, p->st));
-      // CGS2
-      CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev));
-      CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev, w, nullptr));
-      CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev + (j + 1)));
-      CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev + (j + 1), w, nullptr));
-      CKS(mdot(p, w, n, 1, w, p->hdev + 2 * (j + 1)));
-      CKS(fetch(p));
+      CK(cudaEventSynchronize(p->ev1));
       float evms = 0.f;
       cudaEventElapsedTime(&evms, p->ev0, p->ev1);
       for (int i = 0; i < nb; ++i) {
@@ -1308,13 +1392,10 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
           live[i] = 0;
           gi.status = AHOC_ENOCONV;
         } else {
-          sc[i] = 1.0 / hn;
+          p->scal_h[i] = 1.0 / hn;  // v_{j+1} = w / ||w||, applied by the next step
         }
       }
       if (!any(live)) break;
-      CKS(set_act(p, live));
-      CK(cudaMemcpyAsync(p->scal, sc.data(), nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
-      RUN(AHOC_K_KRYLOV, launch_axpby(w, w, 0.0, 0.0, n, p->st, nb, p->scal, g.act));
     }
     // y = H^-1 g (upper triangular), X += Z y, per problem of this cycle
     for (int i = 0; i < nb; ++i) {
@@ -1485,17 +1566,24 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
         continue;
       }
       // Stagnation (a step that removes less than a tenth of the residual):
-      // the refinement has reached its limiting accuracy.  If the last
-      // correction changed U by at most tol (relative 2-norm), the iterate is
-      // settled to the accuracy asked for and the residual sits at the floor
-      // of its FP64 evaluation -- the case of data whose Schur right-hand
-      // side is tiny next to the solution -- and the solve has converged.
-      // Otherwise the FP32 solves are too inaccurate for this grid and the
-      // solve has not converged.
+      // the residual has reached the floor of its FP64 evaluation (data
+      // whose Schur right-hand side is tiny next to the solution, or a tol
+      // at that floor).  If the last correction changed U by at most tol
+      // (relative 2-norm), the iterate is settled to the accuracy asked for
+      // and the solve has converged; if the corrections still shrink (at
+      // least halve), the next step settles it further; otherwise the FP32
+      // solves are too inaccurate for this grid and the solve has not
+      // converged.
       if (step >= 2 && s.rel > 0.9 * s.hist[step - 1]) {
-        if (!(s.du[step - 1] <= tol)) s.status = AHOC_ENOCONV;
-        live[i] = 0;
-        continue;
+        if (s.du[step - 1] <= tol) {
+          live[i] = 0;
+          continue;
+        }
+        if (!(s.du[step - 1] < 0.5 * s.du[step - 2])) {
+          s.status = AHOC_ENOCONV;
+          live[i] = 0;
+          continue;
+        }
       }
       if (step == kMaxRefine) {
         s.status = AHOC_ENOCONV;

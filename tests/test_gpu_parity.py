@@ -339,3 +339,17 @@ def test_mixed_limiting_accuracy_k32():
     assert imx["refine_hist"][k] <= 1e-12 or imx["refine_du"][k - 1] <= 1e-12, imx
     rel = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
     assert rel < TOL_MIXED, (rel, imx)
+
+
+def test_mixed_refines_on_at_the_floor():
+    # a serving request whose Schur residual stalls just above tol = 1e-12
+    # while its corrections still shrink: the refinement must go on and
+    # converge (and agree with the FP64 solve)
+    spec = inputs.RequestSpec(704, 2, 2048, (4, 2), 0.0)
+    d = inputs.sample_request(spec, device="cuda")
+    pm = ahoc.Plan(2, [2048, 2048], d["alpha"], prec="mixed", restart=60, max_iters=2000)
+    um, im = pm.solve(d["f"], tol=1e-12)
+    assert im["status"] == 0, im
+    p64 = ahoc.Plan(2, [2048, 2048], d["alpha"], restart=60, max_iters=2000)
+    u64, _ = p64.solve(d["f"], tol=1e-12)
+    assert float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)) < TOL_MIXED
