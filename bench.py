@@ -343,7 +343,10 @@ def run_ours(args, rank, world, local):
     roof = {"kernel": "k_dst_x<double> (DST-I along x, FP64)", "bound": "alu", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
             "peak_source": "nominal B300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
-            "traffic": None, "avg_launch_ms": avg_ms, "launches": kn_top["dst_x"],
+            # DRAM bytes per launch of k_dst_x<double,1,0> (forward transform with the fused M load, the
+            # kernel's most frequent form in GMRES) from the ncu capture summarised in
+            # profiles/k_dst_x_fp64_2d4096.md: 134.6 MB read + 93.0 MB written
+            "traffic": 227.5e6, "avg_launch_ms": avg_ms, "launches": kn_top["dst_x"],
             "algorithmic_bytes_per_launch": 16 * N * (N - 1), "flops_per_launch": flops,
             "hbm_achieved_GBs": 16 * N * (N - 1) / (avg_ms / 1e3) / 1e9,
             "hbm_peak_GBs": _peaks().get("hbm_gbs"),
