@@ -5,20 +5,23 @@ and v = alpha * Lap u, interleaved per interior point (U_p, V_p) to limit
 fill, followed by the augmented boundary unknowns Q (the values of v on the
 relative interiors of the clamped faces; fully clamped: every face).
 
-Equations, one block row each (beta = 0):
+Equations, one block row each:
   (i)   L_h U - M(V / alpha) = 0 at interior points            (Sec. 2.2, u-equation)
         boundary U = g_D moves to the right-hand side; V / alpha at a face
         point is Q / alpha there.  (Reading: the block zero in the first
         block row of the printed system hides only the Q columns that M does
         not reach; at the first interior layer M reaches the boundary value
         of v, which is Q.)
-  (ii)  -L_h V = M f at interior points                          (Sec. 2.2, v-equation)
+  (ii)  -L_h V + M(beta V / alpha) = M f at interior points     (Sec. 2.2, v-equation)
         V at face points is Q; V at edges and corners is the data v_edge
         (the Remark after the one-sided formula: there all of Lap u follows
         from g_D by tangential differentiation).
-  (iii) alpha_p [ (delta_nn U)_p + lapt_gD_p ] - Q_p = 0 at face points p
+  (iii) on a clamped face (u_n = g_N, Eq. 2):
+        alpha_p [ (delta_nn U)_p + lapt_gD_p ] - Q_p = 0 at face points p
         (Lemma 1's residual R_p), with the one-sided delta_nn of Sec. 2.2
-        using U0 = g_D, U1..U3 interior and the outward g_N.
+        using U0 = g_D, U1..U3 interior and the outward g_N;
+        on a Navier face (Lap u = g_L, Eq. 2): v = alpha g_L is data, the row
+        is alpha_p g_L,p - Q_p = 0.
 
 With this sign of block row (iii) the identity block is -I, so that the
 algebraic residual R(Q) = A22 Q + A21 U(Q) - F2 of Lemma 1's proof equals the
@@ -172,7 +175,10 @@ def assemble(data: Dict, N=None, lo=None, hi=None) -> Coupled:
     """Assemble the coupled system for sampled data (see ``inputs.sample``).
 
     data holds full-grid arrays alpha, f, g_D, v_edge and face arrays g_N and
-    lapt_gD (any of the data arrays may be None, meaning zero).
+    lapt_gD (any of the data arrays may be None, meaning zero); optionally
+    beta (a number or a full-grid array; default 0), navier (the face ids
+    2 * axis + side of the Navier faces; default none) and the face array
+    g_L (Lap u on the faces; read on Navier faces).
     """
     N = list(N if N is not None else data["N"])
     lo = list(lo if lo is not None else data["lo"])
@@ -202,6 +208,12 @@ def assemble(data: Dict, N=None, lo=None, hi=None) -> Coupled:
     vE = zero_full if vE is None else vE
     gN = np.zeros(ng) if gN is None else gN
     lapt = np.zeros(ng) if lapt is None else lapt
+    beta = data.get("beta", 0.0)
+    beta = np.broadcast_to(np.asarray(beta if beta is not None else 0.0, dtype=np.float64).reshape(-1)
+                           if np.ndim(beta) else np.float64(beta), zero_full.shape)
+    navier = set(data.get("navier") or ())
+    gL = flat("g_L")
+    gL = np.zeros(ng) if gL is None else gL
 
     L = laplacian(h)
     Mw = weighting(d)
@@ -243,6 +255,10 @@ def assemble(data: Dict, N=None, lo=None, hi=None) -> Coupled:
         add(ru[inter], 2 * grid.interior_flat([jj[inter] for jj in j]) + 1, -c / alpha[jf[inter]])
         qf = _face_of(grid, j, face)
         add(ru[face], 2 * n + qf[face], -c / alpha[jf[face]])
+        # (ii) + M(beta V / alpha)
+        ba = beta[jf] / alpha[jf]
+        add(rv[inter], 2 * grid.interior_flat([jj[inter] for jj in j]) + 1, c * ba[inter])
+        add(rv[face], 2 * n + qf[face], c * ba[face])
         # (ii) right-hand side M f (f sampled on the full grid, boundary included)
         np.add.at(F, rv, c * f[jf])
 
@@ -255,6 +271,10 @@ def assemble(data: Dict, N=None, lo=None, hi=None) -> Coupled:
             r = 2 * n + q
             pf = grid.full_flat(P)
             al = alpha[pf]
+            if 2 * a + side in navier:
+                add(r, r, -1.0)
+                F[r] = -al * gL[q]
+                continue
             step = 1 if side == 0 else -1
             for m, w in ((1, w1), (2, w2), (3, w3)):
                 jm = [P[b] if b != a else P[a] + step * m for b in range(d)]

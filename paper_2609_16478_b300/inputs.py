@@ -98,6 +98,8 @@ class Problem:
     lo: Tuple[float, ...] = (0.0, 0.0, 0.0)
     hi: Tuple[float, ...] = (1.0, 1.0, 1.0)
     note: str = ""
+    beta: float = 0.0                          # constant beta of Eq. 1
+    navier: Tuple[int, ...] = ()               # Navier faces (2 * axis + side): Lap u = g_L there
 
     def exprs(self) -> Dict[str, sp.Expr]:
         xs = X[: self.dim]
@@ -109,7 +111,7 @@ class Problem:
             out["u"] = u
             out["lap"] = lap
             out["v"] = w
-            out["f"] = -sum(sp.diff(w, v, 2) for v in xs)
+            out["f"] = -sum(sp.diff(w, v, 2) for v in xs) + sp.Float(self.beta) * lap
             for a, v in enumerate(xs):
                 out[f"du{a}"] = sp.diff(u, v)
                 out[f"d2u{a}"] = sp.diff(u, v, 2)
@@ -145,6 +147,24 @@ def config_problem(name: str) -> Problem:
     if name == "poly2d":
         # degree-4 polynomial with nonzero data everywhere and constant alpha
         return Problem(name, 2, sp.Integer(1), x ** 4 + x * y ** 3 - 2 * x ** 2 * y + y + 1)
+    if name.startswith("singular2d"):
+        # Example 1 (Sec. 4.1, Table 1): -eps Lap^2 u + Lap u = f on the unit
+        # square, alpha = eps, beta = 1, clamped on x = 0 and Navier on the
+        # other faces; name "singular2d" (eps = 1e-4) or "singular2d_eps1e-5"
+        eps = sp.Float(name.split("_eps")[1]) if "_eps" in name else sp.Float("1e-4")
+        u = 256 * (x ** 2 + eps * (1 - sp.exp(-x / sp.sqrt(eps))) ** 2) * (x - 1) ** 2 * y ** 2 * (y - 1) ** 2
+        return Problem(name, 2, eps, u, beta=1.0, navier=(1, 2, 3))
+    if name == "navier2d":
+        # variable coefficient, beta = 0, clamped on x- and y-, Navier on x+ and y+
+        return Problem(name, 2, 1 + x ** 2 + y ** 2, sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)), navier=(1, 3))
+    if name == "navier3d":
+        return Problem(name, 3, 1 + x ** 2 + y ** 2 + z ** 2,
+                       sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)) * sp.sin(2 * z + sp.Rational(1, 2)),
+                       beta=0.0, navier=(0, 3, 5))
+    if name == "shift2d":
+        # constant alpha and beta (the shifted-eigenvalue case) with nonzero data on every face
+        return Problem(name, 2, sp.Float(2.0), sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)), beta=50.0,
+                       navier=(2,))
     if name == "cavity":
         # lid-driven cavity streamfunction: f = 0, u = 0, u_y = 1 on y = 1 (Sec. 4, Table 6)
         def gN(axis, side, coords):
@@ -328,6 +348,7 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
     fs = []
     gN = []
     lapt = []
+    gL = []
     for a in range(dim):
         for side in (0, 1):
             pc = face_coords(N, lo, hi, a, side)
@@ -341,11 +362,14 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
                     if b != a:
                         lt += np.broadcast_to(np.asarray(_lamb(ex[f"d2u{b}"], dim, "numpy")(*pc), float), lt.shape)
                 lapt.append(lt)
+                gL.append(np.broadcast_to(np.asarray(_lamb(ex["lap"], dim, "numpy")(*pc), float), lt.shape).copy())
             else:
                 gN.append(np.asarray(prob.gN_face(a, side, pc), dtype=float))
                 lapt.append(np.zeros(pc[0].size))
+                gL.append(np.zeros(pc[0].size))
     gN = np.concatenate(gN)
     lapt = np.concatenate(lapt)
+    gL = np.concatenate(gL)
 
     cnt = _edge_mask(N, dim)
     if prob.u is not None:
@@ -373,6 +397,10 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
     out["v_edge"] = vE
     out["g_N"] = gN if backend == "numpy" else _to_t(gN, device)
     out["lapt_gD"] = lapt if backend == "numpy" else _to_t(lapt, device)
+    out["beta"] = float(prob.beta)
+    out["navier"] = tuple(prob.navier)
+    if prob.navier:
+        out["g_L"] = gL if backend == "numpy" else _to_t(gL, device)
     return out
 
 

@@ -324,3 +324,73 @@ def test_P9_cavity_table6_n1024():
     assert abs(U[k] - float(rows[0][1])) < 1e-9
     assert abs(k[1] / N - float(rows[0][2])) < 1e-12
     assert abs(k[0] / N - float(rows[0][3])) < 1e-4
+
+
+# --- beta term and Navier faces (Sec. 2.2 v-equation; Eq. 2; Example 1) --------
+
+def _lam_M(N, k, h):
+    # the weighting M on the sine basis: 1 + (1/12) sum_a h_a^2 sigma_a
+    s = [-(4.0 / h[a] ** 2) * math.sin(k[a] * math.pi / (2 * N[a])) ** 2 for a in range(len(N))]
+    return 1.0 + sum(h[a] ** 2 * s[a] for a in range(len(N))) / 12.0
+
+
+@pytest.mark.parametrize("N", [(8, 8), (6, 10, 8)])
+def test_shifted_v_operator_eigenpairs(N):
+    """The assembled v-equation block -L_h + M(beta / alpha .) with constant
+    alpha and beta returns -lam_L + (beta / alpha) lam_M on sine vectors."""
+    d = len(N)
+    alpha, beta = 2.5, 40.0
+    data = {"N": list(N), "lo": [0.0] * d, "hi": [1.0, 0.7, 1.3][:d], "alpha": np.full([n + 1 for n in N], alpha),
+            "f": None, "g_D": None, "v_edge": None, "g_N": None, "lapt_gD": None, "beta": beta}
+    sys_ = coupled.assemble(data)
+    Avv = sys_.A[sys_.iv][:, sys_.iv]
+    h = sys_.grid.h
+    idx = [np.arange(1, n) for n in N]
+    g = np.meshgrid(*reversed(idx), indexing="ij")
+    for _ in range(5):
+        k = [int(rng.integers(1, N[a])) for a in range(d)]
+        v = np.ones_like(g[0], dtype=float)
+        for a in range(d):
+            v = v * np.sin(k[a] * math.pi * g[d - 1 - a] / N[a])
+        lam = -_lam_L(N, k, h) + (beta / alpha) * _lam_M(N, k, h)
+        assert np.allclose(Avv @ v.reshape(-1), lam * v.reshape(-1), rtol=1e-11, atol=1e-9 * abs(lam))
+
+
+@pytest.mark.parametrize("col,name", [(1, "singular2d"), (2, "singular2d_eps1e-5")])
+def test_example1_table1_n256(col, name):
+    """Example 1 (Table 1): the oracle's error at 256^2 equals the printed value
+    to the printed three digits (beta term, Navier faces and the clamped face together)."""
+    row = golden("singular2d_table1.txt")[0]
+    assert int(row[0]) == 256
+    d = inputs.sample(inputs.config_problem(name), [256, 256])
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    err = np.max(np.abs(sol.U - d["u_exact"]))
+    assert abs(err / float(row[col]) - 1) < 0.005, (err, row[col])
+
+
+@pytest.mark.parametrize("name,Ns,lo_rate", [("navier2d", [16, 32, 64], 3.6), ("shift2d", [16, 32, 64], 3.6),
+                                             ("navier3d", [6, 8, 12], 3.2)])
+def test_navier_and_shift_convergence_order(name, Ns, lo_rate):
+    prob = inputs.config_problem(name)
+    errs = []
+    for N in Ns:
+        d = inputs.sample(prob, [N] * prob.dim)
+        sol = coupled.solve_direct(coupled.assemble(d), d)
+        errs.append(np.max(np.abs(sol.U - d["u_exact"])))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert min(rates) > lo_rate, rates
+    assert max(rates) < 5.6, rates
+
+
+def test_navier_face_carries_the_data():
+    """On a Navier face the augmented unknown is v = alpha Lap u from the data exactly."""
+    d = inputs.sample(inputs.config_problem("navier2d"), [16, 16])
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    off = coupled.Grid([16, 16], [0, 0], [1, 1]).face_offsets()
+    g = coupled.Grid([16, 16], [0.0, 0.0], [1.0, 1.0])
+    for fid in (1, 3):
+        a, side = fid // 2, fid % 2
+        P = g.face_point_indices(a, side)
+        al = d["alpha"].reshape(-1)[g.full_flat(P)]
+        q = sol.Q[off[fid]:off[fid + 1]]
+        assert np.allclose(q, al * d["g_L"][off[fid]:off[fid + 1]], rtol=1e-10, atol=1e-12)
