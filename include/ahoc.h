@@ -77,6 +77,8 @@ typedef struct {
   const double* lapt_gD; /* face array: sum of the tangential second derivatives of g_D          */
   const double* v_edge;  /* full grid; only edge and corner entries are read: alpha * Laplace u,
                             known there from g_D by tangential differentiation (Remark, Sec. 2.2) */
+  const double* g_L;     /* face array: Laplace u on the face interiors; read on Navier faces
+                            only (opts.navier), where v = alpha g_L is data (Eq. 2)              */
 } ahoc_bdata;
 
 /* Options; a NULL pointer selects the defaults given in brackets. */
@@ -124,6 +126,16 @@ typedef struct {
                              out of later launches, so each result is the one a single-problem
                              plan gives.  Per-problem arguments (alpha, data, f, u, q, y, b)
                              hold `batch` arrays of their single-problem size back to back.  */
+  int navier;             /* [0] problem class: bit 2a + side set makes face (axis a, side) a
+                             Navier face (Eq. 2, Laplace u = g_L, so v = alpha g_L is data and
+                             the face carries no augmented unknown: its rows of the Schur
+                             system are -I, right-hand side -alpha g_L); other faces clamped */
+  double shift;           /* [0] problem class: the constant ratio gamma = beta / alpha of the
+                             beta term of Eq. 1.  The v-equation is -L_h V + gamma M V = M f
+                             (Sec. 2.2 with beta / alpha constant, e.g. constant alpha and
+                             beta): its Poisson solves take the shifted eigenvalues
+                             -lambda_L + gamma lambda_M.  gamma >= 0; variable beta / alpha
+                             is not supported (the v-equation would need an iterative solve) */
   int no_graphs;          /* [0] 0: each GMRES iteration (mask and scalar uploads, the
                              normalisation of v_j, the preconditioner, the Schur matvec, CGS2
                              and the read-back of the Hessenberg column) is captured once as a

@@ -29,7 +29,8 @@ SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matve
 
 
 class ahoc_bdata(C.Structure):
-    _fields_ = [("g_D", C.c_void_p), ("g_N", C.c_void_p), ("lapt_gD", C.c_void_p), ("v_edge", C.c_void_p)]
+    _fields_ = [("g_D", C.c_void_p), ("g_N", C.c_void_p), ("lapt_gD", C.c_void_p), ("v_edge", C.c_void_p),
+                ("g_L", C.c_void_p)]
 
 
 AHOC_NK = 8
@@ -40,7 +41,7 @@ class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
-                ("batch", C.c_int), ("no_graphs", C.c_int)]
+                ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -127,9 +128,11 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1, graphs=True):
+          batch=1, graphs=True, navier=0, shift=0.0):
     o = ahoc_opts()
     o.batch = int(batch)
+    o.navier = int(navier)
+    o.shift = float(shift)
     o.no_graphs = 0 if graphs else 1
     o.coarse_tol = float(coarse_tol)
     o.timing = int(timing)
@@ -146,10 +149,10 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1
 
 
 def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1,
-                    batch: int = 1) -> int:
+                    batch: int = 1, shift: float = 0.0) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch)
+    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -179,7 +182,8 @@ class Plan:
     """
 
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
-                 g_D=None, g_N=None, lapt_gD=None, v_edge=None, prec: int = AHOC_FP64,
+                 g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None, navier: int = 0, shift: float = 0.0,
+                 prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
                  graphs: bool = True):
@@ -205,13 +209,15 @@ class Plan:
         self.prec = prec
         self.device = alpha.device
         B = self.batch
-        nb = workspace_bytes(dim, self.N, restart, prec, levels, B)
+        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift)
         self.workspace_bytes = nb
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, B * self.nfull, "g_D"), _ptr(g_N, B * self.ngamma, "g_N"),
-                        _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"))
-        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs)
+                        _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"),
+                        _ptr(g_L, B * self.ngamma, "g_L"))
+        o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
+                  navier, shift)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
@@ -240,10 +246,11 @@ class Plan:
         out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
         return u, (out[0] if B == 1 else out)
 
-    def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None):
+    def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None):
         """Replace problem b's coefficient and boundary data (``ahoc_plan_load``)."""
         bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
-                        _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"))
+                        _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"),
+                        _ptr(g_L, self.ngamma, "g_L"))
         _check(lib().ahoc_plan_load(self._h, int(b), _ptr(alpha, self.nfull, "alpha"), C.byref(bd)), "ahoc_plan_load")
 
     def set_active(self, mask: Sequence[int]):
@@ -304,12 +311,27 @@ class Plan:
 
 
 def plan_for(data: Dict, device="cuda", **kw) -> "Plan":
-    """Create a plan from a sampled problem (see ``paper_2609_16478_b300.inputs.sample``)."""
+    """Create a plan from a sampled problem (see ``paper_2609_16478_b300.inputs.sample``).
+
+    The problem's Navier faces become the plan's mask, and a nonzero beta the
+    shift gamma = beta / alpha, which must then be constant (a constant alpha).
+    """
     def dev(key):
         v = data.get(key)
         if v is None:
             return None
         t = torch.as_tensor(v, dtype=torch.float64)
         return t.reshape(-1).contiguous().to(device)
-    return Plan(data["dim"], data["N"], dev("alpha"), lo=data["lo"], hi=data["hi"], g_D=dev("g_D"),
-                g_N=dev("g_N"), lapt_gD=dev("lapt_gD"), v_edge=dev("v_edge"), **kw)
+    alpha = dev("alpha")
+    navier = sum(1 << int(f) for f in (data.get("navier") or ()))
+    beta = float(data.get("beta") or 0.0)
+    shift = 0.0
+    if beta != 0.0:
+        lo_, hi_ = float(alpha.min()), float(alpha.max())
+        if lo_ != hi_:
+            raise ValueError("beta != 0 needs a constant alpha (the shift beta / alpha must be constant)")
+        shift = beta / lo_
+    kw.setdefault("navier", navier)
+    kw.setdefault("shift", shift)
+    return Plan(data["dim"], data["N"], alpha, lo=data["lo"], hi=data["hi"], g_D=dev("g_D"),
+                g_N=dev("g_N"), lapt_gD=dev("lapt_gD"), v_edge=dev("v_edge"), g_L=dev("g_L"), **kw)

@@ -34,6 +34,9 @@ struct Geom {
   // launch: their blocks return at once.
   int nb;
   const int* act;
+  int navier;  // bit 2a + side: Navier face (v = alpha g_L is data); other faces clamped
+
+  __host__ __device__ inline bool is_navier(int face_id) const { return (navier >> face_id) & 1; }
 
   __host__ __device__ inline bool skip(int b) const { return act != nullptr && act[b] == 0; }
 
@@ -55,6 +58,7 @@ struct Coefs {
   double Mc, Mn;          // weighting M: centre and each axis neighbour
   double w[3][4];         // one-sided u_nn weights on U0..U3 per normal axis (1/h^2 scaled)
   double wg[3];           // weight on g_N per normal axis (11/(3h))
+  double gam;             // constant beta / alpha: the v-equation is -L_h V + gam M V = M f
 };
 
 // Per-mode factors of the tridiagonal solve along the last axis (see tri.cu).

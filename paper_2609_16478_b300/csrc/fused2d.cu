@@ -40,8 +40,10 @@ __global__ void k_v2d_prep(Geom g, Coefs cf, const double* __restrict__ Q, const
       for (int dy = -1; dy <= 1; ++dy) {
         const int jj = j + dy;
         if (jj < 1 || jj > N1 - 1) continue;  // corners carry no unknown (zero in the homogeneous part)
-        am -= cf.L[9 + (dy + 1) * 3 + 0] * Qm[jj - 1];
-        ap -= cf.L[9 + (dy + 1) * 3 + 2] * Qp[jj - 1];
+        // (L - gam M)_bdry: the shift reaches the face point of the same row only
+        const double sm = dy == 0 ? cf.gam * cf.Mn : 0.0;
+        am -= (cf.L[9 + (dy + 1) * 3 + 0] - sm) * Qm[jj - 1];
+        ap -= (cf.L[9 + (dy + 1) * 3 + 2] - sm) * Qp[jj - 1];
       }
     }
     if (j < N1) {
@@ -91,7 +93,8 @@ __global__ void __launch_bounds__(kRowThreads) k_trace2d_x(Geom g, double* __res
       O += red[1][w];
     }
     const int64_t qm = g.face(0, 0, 0, j, 0), qp = g.face(0, 1, N0, j, 0);
-    double ym = afac[qm] * (E + O), yp = afac[qp] * (E - O);
+    // Navier faces carry v as data: the homogeneous R_p there is -Q_p
+    double ym = g.is_navier(0) ? 0.0 : afac[qm] * (E + O), yp = g.is_navier(1) ? 0.0 : afac[qp] * (E - O);
     if (Q) {
       ym -= Q[qm];
       yp -= Q[qp];
@@ -135,7 +138,8 @@ __global__ void k_trace2d_y(Geom g, double* __restrict__ y, const T* __restrict_
     if (srcq) srcq += fo;
   }
   const int64_t qm = g.face(1, 0, i, 0, 0), qp = g.face(1, 1, i, g.N[1], 0);
-  double ym = afac[qm] * (double)R[i - 1], yp = afac[qp] * (double)R[(N0 - 1) + i - 1];
+  double ym = g.is_navier(2) ? 0.0 : afac[qm] * (double)R[i - 1];
+  double yp = g.is_navier(3) ? 0.0 : afac[qp] * (double)R[(N0 - 1) + i - 1];
   if (Q) {
     ym -= Q[qm];
     yp -= Q[qp];

@@ -101,8 +101,8 @@ size_t tri_chunked_scratch(const Geom& g, int L);
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st);
 
-// V-equation right-hand side for L_h V_int = rhs:
-//   rhs = -M f - L_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
+// V-equation right-hand side for (L_h - gam M) V_int = rhs:
+//   rhs = -M f - (L - gam M)_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
                         const double* vedge, cudaStream_t st, const T* srcv = nullptr);
@@ -112,17 +112,18 @@ cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q,
 template <typename T>
 cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, const T* ainv, const double* Q,
                         const double* gD, cudaStream_t st, const T* srcu = nullptr);
-// Boundary residual R_p = alpha_p [u_nn(U)_p + lapt_p] - Q_p at every face point.
+// Boundary residual R_p = alpha_p [u_nn(U)_p + lapt_p] - Q_p at every point of a
+// clamped face, R_p = alpha_p g_L,p - Q_p on a Navier face (minus srcq if given).
 template <typename T>
 cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
                          const double* afac, const double* gD, const double* gN, const double* lapt,
-                         cudaStream_t st, const double* srcq = nullptr);
+                         cudaStream_t st, const double* srcq = nullptr, const double* gL = nullptr);
 
 // mixed precision: FP64 residual of the coupled system (r_u, r_v in FP32, r_q in FP64)
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
-                            cudaStream_t st);
+                            cudaStream_t st, const double* gL = nullptr);
 // U += dU, V += dV; for problem b, out[2b] = sum dU^2 and out[2b + 1] = sum U^2
 // after the update (deterministic: nblocks fixed partials per problem in
 // `partial`, 2 * nb * nblocks doubles)

@@ -49,6 +49,8 @@ struct Opts {
   double coarse_tol = AHOC_COARSE_TOL_AUTO;  // relative Schur residual of the coarse levels
   int batch = 1;  // problems of this shape solved together
   int graphs = 1;  // replay GMRES iterations as CUDA graphs
+  int navier = 0;        // Navier faces (bit 2a + side)
+  double shift = 0.0;    // constant beta / alpha of the v-equation
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -66,6 +68,8 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     if (o->coarse_tol > 0) d.coarse_tol = o->coarse_tol;
     if (o->batch > 0) d.batch = o->batch;
     d.graphs = o->no_graphs ? 0 : 1;
+    d.navier = o->navier;
+    d.shift = o->shift;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -74,6 +78,8 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.batch > 4096) return fail(AHOC_EINVAL, "batch > 4096");
+  if (d.navier < 0 || d.navier > 63) return fail(AHOC_EINVAL, "navier must be a mask of faces 0..5");
+  if (!(d.shift >= 0) || !std::isfinite(d.shift)) return fail(AHOC_EINVAL, "shift must be finite and >= 0");
   if (d.levels < -1 || d.levels > 8) return fail(AHOC_EINVAL, "levels must be -1 (automatic) or 0..8");
   if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
     return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
@@ -190,8 +196,9 @@ void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
 template <typename T> constexpr long double pow_floor() { return -290.0L; }
 template <> constexpr long double pow_floor<float>() { return -36.0L; }
 
+// gam: shift of the operator, L_h - gam M (0: L_h itself)
 template <typename T>
-ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out) {
+ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out, double gam = 0.0) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int nx = g.N[0] - 1;
   const int ny = (g.dim == 3) ? g.N[1] - 1 : 1;
@@ -206,12 +213,14 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out
     for (int kx = 1; kx <= nx; ++kx) {
       const long double cx = cosl(pi * kx / g.N[0]);
       long double a, b;
+      const long double gm = gam, mc = cf.Mc, mn = cf.Mn;
       if (g.dim == 2) {
-        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0);
-        b = L(0, 1, 0) + 2 * cx * L(1, 1, 0);
+        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0) - gm * (mc + 2 * cx * mn);
+        b = L(0, 1, 0) + 2 * cx * L(1, 1, 0) - gm * mn;
       } else {
-        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0) + 2 * cy * L(0, 1, 0) + 4 * cx * cy * L(1, 1, 0);
-        b = L(0, 0, 1) + 2 * cx * L(1, 0, 1) + 2 * cy * L(0, 1, 1);
+        a = L(0, 0, 0) + 2 * cx * L(1, 0, 0) + 2 * cy * L(0, 1, 0) + 4 * cx * cy * L(1, 1, 0) -
+            gm * (mc + 2 * (cx + cy) * mn);
+        b = L(0, 0, 1) + 2 * cx * L(1, 0, 1) + 2 * cy * L(0, 1, 1) - gm * mn;
       }
       const long double gam = -b / a;
       if (!(fabsl(gam) < 0.5L)) return fail(AHOC_EUNSUPPORTED, "tridiagonal factor not diagonally dominant (mesh aspect ratio)");
@@ -246,7 +255,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
-      tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb,
+      tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb, modes_v, modesf_v, rpow_v, gL,
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
@@ -319,6 +328,8 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.tau = take(((size_t)g.N[0] + 1) * sizeof(double));
   const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
   L.modes = take(nmodes * sizeof(Mode<double>));
+  const bool shifted = o.shift != 0.0;  // the V solves take their own (shifted) mode tables
+  L.modes_v = take(shifted ? nmodes * sizeof(Mode<double>) : 0);
   L.b = take(B * face);
   L.Q = take(B * face);
   L.r = take(B * face);
@@ -328,6 +339,8 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.afinv = take(B * face);
   L.qa = take(B * face);
   L.rpow = take(chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.rpow_v = take(shifted && chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.gL = take(B * face);
   L.partial = take(B * (size_t)pstride(o) * sizeof(double));
   L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
   L.act = take(B * sizeof(int));
@@ -346,6 +359,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
     L.snf[a] = take(((size_t)g.N[a] / 2 + 1) * sizeof(float));
   }
   L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
+  L.modesf_v = take(mixed && shifted ? nmodes * sizeof(Mode<float>) : 0);
   L.trif = take(0);  // the chunked solve's carries are FP64 in both precisions (shared scratch L.tri)
   L.Rq = take(mixed ? B * face : 0);
   L.dQ = take(mixed ? B * face : 0);
@@ -423,6 +437,13 @@ struct ahoc_plan {
   double *stab[3], *ctab[3];
   double *rxm, *rxp, *qy, *R2, *tau;
   Mode<double>* modes;
+  // the V solves' tables: the shifted operator L_h - gam M (aliases of the
+  // U tables when gam = 0)
+  Mode<double>* modes_v = nullptr;
+  Mode<float>* modesf_v = nullptr;
+  double* rpow_v = nullptr;
+  double* gL = nullptr;
+  bool has_gL = false;
   // mixed precision
   float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
@@ -519,14 +540,17 @@ ahoc_status harvest(ahoc_plan* p) {
 // a launcher that issues n kernels
 #define RUNN(kid, n, call) CKS(run(p, kid, #call, [&]() { return (call); }, n))
 
-ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
+// vsolve: the operator of the v-equation, L_h - gam M (the shifted tables)
+ahoc_status poisson_inplace(ahoc_plan* p, double* W, bool vsolve = false) {
   const Geom& g = p->g;
+  const Mode<double>* md = vsolve ? p->modes_v : p->modes;
+  const double* rp = vsolve ? p->rpow_v : p->rpow;
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, p->modes, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
+    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, md, md, rp, p->tri, tri_chunk_len(g), p->st));
   else
-    RUN(AHOC_K_TRI, launch_tri<double>(g, W, p->modes, p->st));
+    RUN(AHOC_K_TRI, launch_tri<double>(g, W, md, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   return AHOC_OK;
@@ -536,7 +560,7 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W) {
 ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) {
   const Geom& g = p->g;
   RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data && p->has_vedge ? p->vedge : nullptr, p->st));
-  CKS(poisson_inplace(p, p->W1));
+  CKS(poisson_inplace(p, p->W1, true));
   RUN(AHOC_K_URHS,
       launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data && p->has_gD ? p->gD : nullptr, p->st));
   CKS(poisson_inplace(p, p->W2));
@@ -544,11 +568,14 @@ ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) 
 }
 
 // FP32 Dirichlet Poisson solve in place (mixed precision inner solves)
-ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
+ahoc_status poisson_inplace_f(ahoc_plan* p, float* W, bool vsolve = false) {
   const Geom& g = p->g;
+  const Mode<float>* mf = vsolve ? p->modesf_v : p->modesf;
+  const Mode<double>* md = vsolve ? p->modes_v : p->modes;
+  const double* rp = vsolve ? p->rpow_v : p->rpow;
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, p->modesf, p->modes, p->rpow, p->tri, tri_chunk_len(g), p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, W, mf, md, rp, p->tri, tri_chunk_len(g), p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, W, p->twf[1], p->snf[1], 1.0f, p->st));
   RUN(AHOC_K_DST_X, launch_dst_x<float>(g, W, p->twf[0], p->snf[0], 1.0f, p->st));
   return AHOC_OK;
@@ -559,7 +586,7 @@ ahoc_status poisson_inplace_f(ahoc_plan* p, float* W) {
 ahoc_status solve_VU_f(ahoc_plan* p, const double* Q, const float* srcv, const float* srcu) {
   const Geom& g = p->g;
   RUN(AHOC_K_VRHS, launch_vrhs<float>(g, p->cf, p->F1, Q, nullptr, nullptr, p->st, srcv));
-  CKS(poisson_inplace_f(p, p->F1));
+  CKS(poisson_inplace_f(p, p->F1, true));
   RUN(AHOC_K_URHS, launch_urhs<float>(g, p->cf, p->F2, p->F1, p->ainvf, Q, nullptr, p->st, srcu));
   CKS(poisson_inplace_f(p, p->F2));
   return AHOC_OK;
@@ -578,16 +605,17 @@ template <typename T>
 struct F2Arrays {
   T *W1, *W2;
   const Mode<T>* modes;
+  const Mode<T>* modes_v;  // the V solve's (shifted) tables
   const void* tw;
   const T *sn, *ainv, *tau, *sk, *ck;
   T *rxm, *rxp, *qy, *qa, *R2;
 };
 F2Arrays<double> f2arrays_d(ahoc_plan* p) {
-  return F2Arrays<double>{p->W1, p->W2, p->modes, p->twx, p->snx, p->ainv, p->tau, p->stab[0], p->ctab[0],
+  return F2Arrays<double>{p->W1, p->W2, p->modes, p->modes_v, p->twx, p->snx, p->ainv, p->tau, p->stab[0], p->ctab[0],
                           p->rxm, p->rxp, p->qy, p->qa, p->R2};
 }
 F2Arrays<float> f2arrays_f(ahoc_plan* p) {
-  return F2Arrays<float>{p->F1, p->F2, p->modesf, p->twf[0], p->snf[0], p->ainvf, p->tauf, p->skf, p->ckf,
+  return F2Arrays<float>{p->F1, p->F2, p->modesf, p->modesf_v, p->twf[0], p->snf[0], p->ainvf, p->tauf, p->skf, p->ckf,
                          p->rxmf, p->rxpf, p->qyf, p->qaf, p->R2f};
 }
 
@@ -598,7 +626,8 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
   const Coefs& cf = p->cf;
   const int N0 = g.N[0];
   const int L = tri_chunk_len(g);
-  VGen2D<T> G{A.rxm, A.rxp, A.qy, A.qy + (N0 - 1), A.sk, A.ck, (T)cf.L[16], (T)cf.L[17]};
+  // y-face terms of (L - gam M)_bdry: the shift reaches the face point of the same column
+  VGen2D<T> G{A.rxm, A.rxp, A.qy, A.qy + (N0 - 1), A.sk, A.ck, (T)(cf.L[16] - cf.gam * cf.Mn), (T)cf.L[17]};
   if (q) {
     RUN(AHOC_K_VRHS, launch_v2d_prep<T>(g, cf, q, p->afinv, A.rxm, A.rxp, A.qy, A.qa, p->st));
     RUN(AHOC_K_VRHS, launch_dst_gen<T>(A.qy, 2, 1, N0 - 1, 0, 1, N0, A.tw, A.sn, p->st, g.nb, 2 * N0, g.act));
@@ -608,11 +637,13 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
   if (srcv) {
     RUN(AHOC_K_DST_X, launch_dst_x_from<T>(g, A.W1, srcv, -1.0, A.tw, A.sn, p->st));
     if (q)
-      RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, G, p->st, true));
+      RUNN(AHOC_K_TRI, 5,
+           launch_tri_chunked_gen<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, G, p->st, true));
     else
-      RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, p->st));
+      RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, p->st));
   } else {
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen<T>(g, A.W1, A.modes, p->modes, p->rpow, p->tri, L, G, p->st, false));
+    RUNN(AHOC_K_TRI, 5,
+         launch_tri_chunked_gen<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, G, p->st, false));
   }
   // U-hat: L_h U = M(V/alpha) + face terms + r_u, by one forward DST of the fused right-hand side
   if (!recover) {
@@ -708,7 +739,8 @@ ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
   const Geom& g = p->g;
   CKS(solve_VU(p, nullptr, f, true));
   RUN(AHOC_K_TRACE, launch_trace<double>(g, p->cf, b, p->W2, nullptr, p->afac, p->has_gD ? p->gD : nullptr,
-                                         p->has_gN ? p->gN : nullptr, p->has_lapt ? p->lapt : nullptr, p->st));
+                                         p->has_gN ? p->gN : nullptr, p->has_lapt ? p->lapt : nullptr, p->st,
+                                         nullptr, p->has_gL ? p->gL : nullptr));
   RUN(AHOC_K_KRYLOV, launch_axpby(b, b, -1.0, 0.0, g.ngamma, p->st, g.nb, nullptr, g.act));
   return AHOC_OK;
 }
@@ -829,11 +861,17 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKS(make_geom(dim, N, lo, hi, &g));
   g.nb = o.batch;
   if (g.n2 * g.nb > 65535) return fail(AHOC_EUNSUPPORTED, "batch too large for this grid (N2 * batch > 65535)");
+  if (o.navier >> (2 * dim)) return fail(AHOC_EINVAL, "navier names a face beyond 2 * dim");
+  g.navier = o.navier;
   Coefs cf = make_coefs(g);
-  std::vector<Mode<double>> modes;
+  cf.gam = o.shift;
+  const bool shifted = o.shift != 0.0;
+  std::vector<Mode<double>> modes, modes_v;
   CKS(mode_table<double>(g, cf, modes));
-  std::vector<Mode<float>> modesf;
+  if (shifted) CKS(mode_table<double>(g, cf, modes_v, o.shift));
+  std::vector<Mode<float>> modesf, modesf_v;
   if (o.prec == AHOC_MIXED) CKS(mode_table<float>(g, cf, modesf));
+  if (o.prec == AHOC_MIXED && shifted) CKS(mode_table<float>(g, cf, modesf_v, o.shift));
   Layout L = make_layout(g, o);
   const size_t need = total_bytes(g, o);
   if (o.workspace && o.workspace_bytes < need) return fail(AHOC_ENOMEM, "caller workspace too small");
@@ -885,6 +923,8 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->R2 = at<double>(p, L.R2);
   p->tau = at<double>(p, L.tau);
   p->modes = at<Mode<double>>(p, L.modes);
+  p->modes_v = shifted ? at<Mode<double>>(p, L.modes_v) : p->modes;
+  p->gL = at<double>(p, L.gL);
   p->b = at<double>(p, L.b);
   p->Q = at<double>(p, L.Q);
   p->r = at<double>(p, L.r);
@@ -894,6 +934,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->afinv = at<double>(p, L.afinv);
   p->qa = at<double>(p, L.qa);
   p->rpow = at<double>(p, L.rpow);
+  p->rpow_v = shifted ? at<double>(p, L.rpow_v) : p->rpow;
   p->partial = at<double>(p, L.partial);
   p->hdev = at<double>(p, L.hdev);
   p->act = at<int>(p, L.act);
@@ -908,6 +949,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     p->U64 = at<double>(p, L.U64);
     p->V64 = at<double>(p, L.V64);
     p->modesf = at<Mode<float>>(p, L.modesf);
+    p->modesf_v = shifted ? at<Mode<float>>(p, L.modesf_v) : p->modesf;
     p->trif = at<float>(p, L.trif);
     p->Rq = at<double>(p, L.Rq);
     p->dQ = at<double>(p, L.dQ);
@@ -943,6 +985,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMemsetAsync(p->vedge, 0, B * full, p->st));
   CKC(cudaMemsetAsync(p->gN, 0, B * face, p->st));
   CKC(cudaMemsetAsync(p->lapt, 0, B * face, p->st));
+  CKC(cudaMemsetAsync(p->gL, 0, B * face, p->st));
   CKS(set_act(p, p->part));
   std::vector<double> tw, sn;
   dst_tables(g.N[0], tw, sn);
@@ -953,6 +996,9 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMemcpyAsync(p->twy, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
   CKC(cudaMemcpyAsync(p->sny, sn.data(), sn.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
   CKC(cudaMemcpyAsync(p->modes, modes.data(), modes.size() * sizeof(Mode<double>), cudaMemcpyHostToDevice, p->st));
+  if (shifted)
+    CKC(cudaMemcpyAsync(p->modes_v, modes_v.data(), modes_v.size() * sizeof(Mode<double>), cudaMemcpyHostToDevice,
+                        p->st));
   CKC(cudaStreamSynchronize(p->st));
   if (o.prec == AHOC_MIXED) {
     const size_t ffl = (size_t)g.npad * sizeof(float);
@@ -960,6 +1006,9 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     CKC(cudaMemsetAsync(p->F2, 0, B * ffl, p->st));
     CKC(cudaMemcpyAsync(p->modesf, modesf.data(), modesf.size() * sizeof(Mode<float>), cudaMemcpyHostToDevice,
                         p->st));
+    if (shifted)
+      CKC(cudaMemcpyAsync(p->modesf_v, modesf_v.data(), modesf_v.size() * sizeof(Mode<float>),
+                          cudaMemcpyHostToDevice, p->st));
   }
   for (int a = 0; a < g.dim; ++a) {
     dst_tables(g.N[a], tw, sn);
@@ -999,6 +1048,8 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     CKC(cudaStreamSynchronize(p->st));
   }
   if (chunked_for(g, o.prec)) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
+  if (chunked_for(g, o.prec) && shifted)
+    CKC(launch_tri_powers(g, p->modes_v, p->rpow_v, tri_chunk_len(g), p->st));
   if (o.prec == AHOC_MIXED) {
     CKC(launch_to_float(p->tauf, p->tau, g.N[0] + 1, p->st));
     CKC(launch_to_float(p->skf, p->stab[0], 2 * (int64_t)g.N[0], p->st));
@@ -1057,6 +1108,7 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
   CKS(put(p->vedge + pf, bd ? bd->v_edge : nullptr, full, p->has_vedge));
   CKS(put(p->gN + pg, bd ? bd->g_N : nullptr, face, p->has_gN));
   CKS(put(p->lapt + pg, bd ? bd->lapt_gD : nullptr, face, p->has_lapt));
+  CKS(put(p->gL + pg, bd ? bd->g_L : nullptr, face, p->has_gL));
   if (p->coarse) {
     // coarse data by injection, staged in this problem's field and face buffers
     Geom gc = p->coarse->g;
@@ -1067,12 +1119,14 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
     double* vE_c = bd && bd->v_edge ? p->W2 + pp + gc.nfull : nullptr;
     double* gN_c = bd && bd->g_N ? p->b + pg : nullptr;
     double* lt_c = bd && bd->lapt_gD ? p->r + pg : nullptr;
+    double* gL_c = bd && bd->g_L ? p->tmp + pg : nullptr;
     CKC(launch_inject_full(gc, g, a_c, alpha, p->st));
     if (gD_c) CKC(launch_inject_full(gc, g, gD_c, bd->g_D, p->st));
     if (vE_c) CKC(launch_inject_full(gc, g, vE_c, bd->v_edge, p->st));
     if (gN_c) CKC(launch_inject_face(gc, g, gN_c, bd->g_N, p->st));
     if (lt_c) CKC(launch_inject_face(gc, g, lt_c, bd->lapt_gD, p->st));
-    ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c};
+    if (gL_c) CKC(launch_inject_face(gc, g, gL_c, bd->g_L, p->st));
+    ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c, gL_c};
     CKS(plan_load(p->coarse, b, a_c, &bc));
     CKC(cudaStreamSynchronize(p->st));
     CKC(cudaMemsetAsync(p->W1 + pp, 0, (size_t)g.npad * sizeof(double), p->st));
@@ -1104,6 +1158,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
       bb.g_N = bd->g_N ? bd->g_N + (int64_t)b * g.ngamma : nullptr;
       bb.lapt_gD = bd->lapt_gD ? bd->lapt_gD + (int64_t)b * g.ngamma : nullptr;
       bb.v_edge = bd->v_edge ? bd->v_edge + (int64_t)b * g.nfull : nullptr;
+      bb.g_L = bd->g_L ? bd->g_L + (int64_t)b * g.ngamma : nullptr;
     }
     s = plan_load(p, b, alpha + (int64_t)b * g.nfull, &bb);
   }
@@ -1542,7 +1597,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
     RUNN(AHOC_K_OTHER, 2,
          launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->has_gD ? p->gD : nullptr,
                          p->has_vedge ? p->vedge : nullptr, p->has_gN ? p->gN : nullptr,
-                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st));
+                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st, p->has_gL ? p->gL : nullptr));
     // correction right-hand side b = -R_d(0)
     if (fused_ok(g)) {
       CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));

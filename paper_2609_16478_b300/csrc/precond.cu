@@ -14,7 +14,13 @@
 //
 // where (a_l, b_l) are the centre and normal-neighbour weights of L_h and
 // (m_d, m_o) those of M in the transverse mode l, and w_m the one-sided
-// weights along the normal a.  The preconditioner applies, face by face,
+// weights along the normal a.  With the shift gam = beta/alpha of the
+// v-equation the V extension solves with L_h - gam M, whose weights are
+// aV_l = a_l - gam m_d, bV_l = b_l - gam m_o, and the summand becomes
+//   (m_o lamV_k - bV_l Mhat_k) / (lamV_k lam_k),  Mhat_k = m_d + 2 m_o cos(k pi/N_a),
+// lamV_k = aV_l + 2 bV_l cos(k pi/N_a) (the form above at gam = 0).  A Navier
+// face has the symbol -1: its augmented rows are -I.  The preconditioner
+// applies, face by face,
 //   P^-1 q = D_alpha  DST^-1 [ DST(D_alpha^-1 q) / s ],
 // i.e. the inverse of that single-face symbol with the coefficient frozen
 // pointwise on the face (for constant alpha the scaling cancels exactly).
@@ -67,7 +73,14 @@ __global__ void k_face_symbols(Geom g, Coefs cf, double* __restrict__ pre, const
   for (int b = 0; b < g.dim; ++b)
     if (b != a) md += 2.0 * cf.Mn * c[b];
   const double mo = cf.Mn;
-  const double num = mo * al - bl * md;
+  double norm = 1.0;
+  for (int b = 0; b < g.dim; ++b)
+    if (b != a) norm *= 2.0 / g.N[b];
+  if (g.is_navier(f)) {
+    pre[q] = -norm;
+    return;
+  }
+  const double av = al - cf.gam * md, bv = bl - cf.gam * mo;
   const int Na = g.N[a];
   const double* ca = ct[a];
   double kap = 0.0;
@@ -76,13 +89,12 @@ __global__ void k_face_symbols(Geom g, Coefs cf, double* __restrict__ pre, const
     const double s2 = stab[(2 * k) % (2 * Na)];
     const double s3 = stab[(3 * k) % (2 * Na)];
     const double lam = al + 2.0 * bl * ca[k];
+    const double lamv = av + 2.0 * bv * ca[k];
+    const double mhat = md + 2.0 * mo * ca[k];
     const double tr = cf.w[a][1] * s1 + cf.w[a][2] * s2 + cf.w[a][3] * s3;
-    kap += s1 * num / (lam * lam) * tr;
+    kap += s1 * (mo * lamv - bv * mhat) / (lamv * lam) * tr;
   }
   kap *= 2.0 / Na;
-  double norm = 1.0;
-  for (int b = 0; b < g.dim; ++b)
-    if (b != a) norm *= 2.0 / g.N[b];
   pre[q] = norm / (kap - 1.0);
 }
 

@@ -76,7 +76,9 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
           } else if (vedge) {
             vb = vedge[g.full(ii, jj, kk)];
           }
-          acc -= (T)c * (T)vb;
+          // the shift gam M V reaches the axis neighbours (weight Mn): (L - gam M) V = ...
+          const double ce = (dx * dx + dy * dy + dz * dz == 1) ? c - cf.gam * cf.Mn : c;
+          acc -= (T)ce * (T)vb;
         }
   }
   if (f) {
@@ -146,7 +148,8 @@ template <typename T>
 __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __restrict__ U,
                         const double* __restrict__ Q, const double* __restrict__ afac,
                         const double* __restrict__ gD, const double* __restrict__ gN,
-                        const double* __restrict__ lapt, const double* __restrict__ srcq) {
+                        const double* __restrict__ lapt, const double* __restrict__ srcq,
+                        const double* __restrict__ gL) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int bi = blockIdx.y;
   if (q >= g.ngamma || g.skip(bi)) return;
@@ -160,9 +163,17 @@ __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __res
     if (gN) gN += fo;
     if (lapt) lapt += fo;
     if (srcq) srcq += fo;
+    if (gL) gL += fo;
   }
   int f = 0;
   while (q >= g.face_off[f + 1]) ++f;
+  if (g.is_navier(f)) {  // R_p = alpha_p g_L,p - Q_p: v is data on a Navier face
+    double res = gL ? afac[q] * gL[q] : 0.0;
+    if (Q) res -= Q[q];
+    if (srcq) res -= srcq[q];
+    y[q] = res;
+    return;
+  }
   const int a = f >> 1, side = f & 1;
   const int64_t loc = q - g.face_off[f];
   int c[3] = {0, 0, 0};
@@ -301,8 +312,8 @@ cudaError_t launch_urhs(const Geom& g, const Coefs& cf, T* out, const T* V, cons
 template <typename T>
 cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, const double* Q,
                          const double* afac, const double* gD, const double* gN, const double* lapt,
-                         cudaStream_t st, const double* srcq) {
-  k_trace<T><<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq);
+                         cudaStream_t st, const double* srcq, const double* gL) {
+  k_trace<T><<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq, gL);
   return cudaGetLastError();
 }
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st) {
@@ -337,14 +348,14 @@ template cudaError_t launch_urhs<double>(const Geom&, const Coefs&, double*, con
                                          const double*, const double*, cudaStream_t, const double*);
 template cudaError_t launch_trace<double>(const Geom&, const Coefs&, double*, const double*, const double*,
                                           const double*, const double*, const double*, const double*, cudaStream_t,
-                                          const double*);
+                                          const double*, const double*);
 template cudaError_t launch_vrhs<float>(const Geom&, const Coefs&, float*, const double*, const double*,
                                         const double*, cudaStream_t, const float*);
 template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const float*,
                                         const double*, const double*, cudaStream_t, const float*);
 template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, const float*, const double*,
                                          const double*, const double*, const double*, const double*, cudaStream_t,
-                                         const double*);
+                                         const double*, const double*);
 
 }  // namespace ahoc
 
@@ -465,8 +476,9 @@ namespace ahoc {
 // iterate x = (U, V, Q), U and V padded FP64 fields, boundary values from the
 // data (U = g_D, V = Q on faces, v_edge on edges and corners):
 //   r_u = -(L_h U - M(V/alpha))            (u-equation, right-hand side 0)
-//   r_v = M f - (-L_h V)                    (v-equation)
-//   r_q = -(alpha (delta_nn U + lapt) - Q)  (augmented equation, Lemma 1's R)
+//   r_v = M f - (-L_h V + gam M V)          (v-equation, gam = beta / alpha constant)
+//   r_q = -(alpha (delta_nn U + lapt) - Q)  (augmented equation, Lemma 1's R; on a
+//                                            Navier face -(alpha g_L - Q))
 // r_u and r_v are stored in FP32 (they are the sources of an FP32 correction
 // solve), r_q in FP64.
 // ---------------------------------------------------------------------------
@@ -528,24 +540,27 @@ __global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __re
           lv += c * V[o];
         }
       }
-  // M(V/alpha) and M f: centre and the axis neighbours
+  // M(V/alpha), M V (the shift term) and M f: centre and the axis neighbours
   double mv = cf.Mc * V[t] * ainv[g.full(i, j, k)];
+  double mvv = cf.Mc * V[t];
   double mf = f ? cf.Mc * f[g.full(i, j, k)] : 0.0;
   for (int a = 0; a < g.dim; ++a)
     for (int s = -1; s <= 1; s += 2) {
       const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
-      mv += cf.Mn * vfull(g, V, Q, vedge, ii, jj, kk) * ainv[g.full(ii, jj, kk)];
+      const double vn = vfull(g, V, Q, vedge, ii, jj, kk);
+      mv += cf.Mn * vn * ainv[g.full(ii, jj, kk)];
+      mvv += cf.Mn * vn;
       if (f) mf += cf.Mn * f[g.full(ii, jj, kk)];
     }
   ru[t] = (float)(-(lu - mv));
-  rv[t] = (float)(mf + lv);
+  rv[t] = (float)(mf + lv - cf.gam * mvv);
 }
 
 // r_q at every face point (FP64)
 __global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const double* __restrict__ U,
                              const double* __restrict__ Q, const double* __restrict__ afac,
                              const double* __restrict__ gD, const double* __restrict__ gN,
-                             const double* __restrict__ lapt) {
+                             const double* __restrict__ lapt, const double* __restrict__ gL) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int bi = blockIdx.y;
   if (q >= g.ngamma || g.skip(bi)) return;
@@ -558,9 +573,14 @@ __global__ void k_residual_q(Geom g, Coefs cf, double* __restrict__ rq, const do
     if (gD) gD += (int64_t)bi * g.nfull;
     if (gN) gN += fo;
     if (lapt) lapt += fo;
+    if (gL) gL += fo;
   }
   int a, side, c[3];
   face_coords(g, q, a, side, c);
+  if (g.is_navier(2 * a + side)) {
+    rq[q] = -((gL ? afac[q] * gL[q] : 0.0) - Q[q]);
+    return;
+  }
   const int step = side ? -1 : 1;
   int p[3] = {c[0], c[1], c[2]};
   double unn = gD ? cf.w[a][0] * gD[g.full(c[0], c[1], c[2])] : 0.0;
@@ -626,11 +646,11 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Geom g, double* __re
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
-                            cudaStream_t st) {
+                            cudaStream_t st, const double* gL) {
   k_residual<<<dim3(nblk(g.npad, 256), g.nb), 256, 0, st>>>(g, cf, ru, rv, U, V, Q, f, gD, vedge, ainv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual_q<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt);
+  k_residual_q<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt, gL);
   return cudaGetLastError();
 }
 
