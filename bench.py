@@ -186,7 +186,7 @@ def serving_variant(args, dev):
     import numpy as np
     import torch
 
-    from paper_2609_16478_b300 import ahoc, inputs, serving
+    from paper_2609_16478_b300 import ahoc, autotune, inputs, serving
 
     tol = args.serve_tol
     p3 = 0.3
@@ -207,10 +207,12 @@ def serving_variant(args, dev):
     rate = 0.8 * cap
     specs = inputs.request_stream(args.serve_requests, rate, seed=5)
 
-    def warm_specs(batch_for):
-        out, rid = [], 10 ** 7
+    def warm_specs(batch_for, size, rid0):
+        # `size` requests of every shape at once (at most the shape's batch):
+        # the pool then holds a plan of that size per shape
+        out, rid = [], rid0
         for (dim, n) in mix:
-            for _ in range(batch_for((dim, n))):
+            for _ in range(min(size, batch_for((dim, n)))):
                 out.append(inputs.RequestSpec(rid, dim, n, (0,) * dim, 0.0))
                 rid += 1
         return out
@@ -218,13 +220,24 @@ def serving_variant(args, dev):
     def arm(prec, workers, batch_for):
         srv = serving.Server(device=dev, prec=prec, tol=tol, workers=workers, batch_for=batch_for,
                              check_exact=True)
-        srv.run(warm_specs(batch_for or serving.default_batch), realtime=False)  # plans resident
+        srv.sched.max_slots = args.serve_slots
+        size = 1
+        while size <= max(batch_for(k) for k in mix):  # plans of every power-of-two size resident
+            srv.run(warm_specs(batch_for, size, 10 ** 7 + 1000 * size), realtime=False)
+            size *= 2
         recs = srv.run(specs, realtime=True)
         srv.close()
         torch.cuda.empty_cache()
         return recs, serving.summarize(recs)
 
-    ra, sa = arm("mixed", args.serve_workers, None)
+    # the mixed server takes the tuner's batch sizes and launch shapes
+    cache = autotune.load(args.tune_cache)
+    autotune.apply(cache)
+    ra, sa = arm("mixed", args.serve_workers, autotune.batch_for(cache, "mixed", serving.default_batch))
+    for k in cache:  # the FP64 arm runs with the built-in shapes
+        dim, n, _ = k.split(":")
+        for kind in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS):
+            ahoc.lib().ahoc_tune_set(kind, int(dim), int(n), ahoc.AHOC_MIXED, 0)
     rb, sb = arm("fp64", 1, lambda k: 1)
     ea = {r.rid: r.err_inf for r in ra}
     eb = {r.rid: r.err_inf for r in rb}
@@ -234,7 +247,8 @@ def serving_variant(args, dev):
                     "capacity %.1f req/s; 2D N in %s (p=0.7), 3D N in %s; per-request Fourier coefficient "
                     "(M=6, K=4, A=0.5, seed = request id) and u = prod sin^2(pi x) cos(m pi x), m in 0..4; "
                     "Schur tol %g" % (len(specs), rate, cap, list(inputs.SERVE_2D), list(inputs.SERVE_3D), tol),
-        "batched_mixed": dict(sa, workers=args.serve_workers, batch="default_batch (about 4M points, <= 16)"),
+        "batched_mixed": dict(sa, workers=args.serve_workers, plan_slots_per_shape=args.serve_slots,
+                              batch="per shape from the autotuner: %s" % {k: v["batch"] for k, v in cache.items()}),
         "sequential_fp64": dict(sb, workers=1, batch=1),
         "p99_speedup": sb["p99_ms"] / sa["p99_ms"], "dof_per_s_ratio": sa["dof_per_s"] / sb["dof_per_s"],
         "max_err_ratio_mixed_over_fp64": ratio,
@@ -434,7 +448,12 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-tol", type=float, default=1e-12)
+    ap.add_argument("--serve-slots", type=int, default=8, help="plans per shape in the serving pool")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache (default: the shipped B300 choices)")
     args = ap.parse_args()
+    if args.tune_cache is None:
+        from paper_2609_16478_b300 import autotune
+        args.tune_cache = autotune.SHIPPED_MIXED
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -139,9 +139,11 @@ typedef struct {
   int no_graphs;          /* [0] 0: each GMRES iteration (mask and scalar uploads, the
                              normalisation of v_j, the preconditioner, the Schur matvec, CGS2
                              and the read-back of the Hessenberg column) is captured once as a
-                             CUDA graph per iteration index and replayed; needs a stream other
-                             than the legacy default stream and timing == 0.  nonzero: plain
-                             launches.                                                         */
+                             CUDA graph per iteration index and replayed on a stream the plan
+                             owns, ordered after and before the caller's stream by events (no
+                             graphs with timing != 0; a capture that another thread's CUDA
+                             call invalidates leaves the plan on plain launches).  nonzero:
+                             plain launches.                                                   */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -269,6 +271,23 @@ ahoc_status ahoc_set_active(ahoc_plan* p, const int* mask);
 
 /* Number of problems a plan holds (opts.batch). */
 int ahoc_batch(const ahoc_plan* p);
+
+/* Launch-shape tuning (no paper counterpart) ------------------------------ */
+
+/* Tunable launch shapes, kept in a process-wide table per (kind, dim, N,
+ * precision) and fixed into a plan when it is created (and read by
+ * ahoc_workspace_bytes, so set them before both):
+ *   AHOC_TUNE_TRI_CHUNK    rows per thread of the chunked tridiagonal solve
+ *                          along the last axis: 8, 16 or 32 (key N: that axis)
+ *   AHOC_TUNE_DST_THREADS  threads per CTA of the line DSTs along x and y:
+ *                          128, 256 or 512 (key N: the x axis)
+ * value 0 restores the built-in choice.  The shapes change rounding, not the
+ * discrete problem: results stay within the solver's tolerance.  The FFT
+ * radix is fixed (radix 4, one radix-2 stage when log2(N/2) is odd). */
+enum { AHOC_TUNE_TRI_CHUNK = 0, AHOC_TUNE_DST_THREADS = 1, AHOC_TUNE_NKINDS = 2 };
+ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value);
+/* the table entry (0: built-in), or -1 for arguments out of range */
+int ahoc_tune_get(int kind, int dim, int64_t N, int prec);
 
 /* Static strings; never NULL. */
 const char* ahoc_status_string(ahoc_status s);

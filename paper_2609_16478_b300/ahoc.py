@@ -20,12 +20,13 @@ LIB_PATH = os.path.join(_HERE, "libahoc.so")
 AHOC_OK, AHOC_EINVAL, AHOC_ENOMEM, AHOC_ECUDA, AHOC_ENOCONV, AHOC_ENUMERIC, AHOC_ETIMEOUT, \
     AHOC_EUNSUPPORTED, AHOC_EINTERNAL = range(9)
 AHOC_FP64, AHOC_MIXED = 0, 1
+AHOC_TUNE_TRI_CHUNK, AHOC_TUNE_DST_THREADS = 0, 1
 
 # every entry point declared in include/ahoc.h
 SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
            "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
            "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc", "ahoc_plan_load", "ahoc_set_active",
-           "ahoc_batch")
+           "ahoc_batch", "ahoc_tune_set", "ahoc_tune_get")
 
 
 class ahoc_bdata(C.Structure):
@@ -95,6 +96,10 @@ def lib():
     L.ahoc_set_active.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
     L.ahoc_batch.argtypes = [C.c_void_p]
     L.ahoc_batch.restype = C.c_int
+    L.ahoc_tune_set.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_int]
+    L.ahoc_tune_set.restype = C.c_int
+    L.ahoc_tune_get.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int]
+    L.ahoc_tune_get.restype = C.c_int
     for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
                  "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_plan_load",
                  "ahoc_set_active"):

@@ -35,6 +35,8 @@ struct Geom {
   int nb;
   const int* act;
   int navier;  // bit 2a + side: Navier face (v = alpha g_L is data); other faces clamped
+  int triL;     // rows per chunk of the chunked tridiagonal solve (0: default)
+  int dst_cta;  // threads per CTA of the line DSTs along x and y (0: default 512)
 
   __host__ __device__ inline bool is_navier(int face_id) const { return (navier >> face_id) & 1; }
 

@@ -448,7 +448,8 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
   const int N = (int)g.n0;
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  const int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  const int cta = g.dst_cta ? g.dst_cta : 512;
+  const int LPC = TPL >= cta ? 1 : cta / TPL;
   const int threads = TPL * LPC;
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
   const int64_t blocks = (nrows + LPC - 1) / LPC;
@@ -513,7 +514,8 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
   const int N = g.N[1];
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  int LPC = TPL >= 512 ? 1 : 512 / TPL;
+  const int cta = g.dst_cta ? g.dst_cta : 512;
+  int LPC = TPL >= cta ? 1 : cta / TPL;
   if (LPC > g.n0) LPC = (int)g.n0;
   const int threads = TPL * LPC;
   const int LS = N + (int)(16 / sizeof(T));

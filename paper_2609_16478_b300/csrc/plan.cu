@@ -1,9 +1,11 @@
 // Plan, solver engine and C ABI of the augmented HOC method (Sec. 2.3,
 // Algorithm 1): ConstructSchurRHS, SchurMatVec, GMRES on S_h Q = b, recovery.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -21,6 +23,15 @@ thread_local std::string g_err;
 ahoc_status fail(ahoc_status s, const std::string& msg) {
   g_err = msg;
   return s;
+}
+
+// Serialises CUDA graph captures with the library's own synchronising entry
+// points (plan creation, loading, destruction: pinned allocations, frees,
+// stream synchronisations), which would otherwise invalidate a capture open
+// in another thread.
+std::recursive_mutex& capture_mutex() {
+  static std::recursive_mutex m;
+  return m;
 }
 
 #define CK(call)                                                                             \
@@ -268,7 +279,28 @@ constexpr int64_t kChunkedBelow = 65536;
 // FP32 solves always take the chunked form: its carries are FP64, and the
 // one-thread-per-column form accumulates the whole column in FP32, which
 // loses the near-boundary cancellation u = p + C phi on large grids.
-int tri_chunk_len(const Geom& g) { return ((g.dim == 3 ? g.N[2] : g.N[1]) >= 1024) ? 32 : 16; }
+int tri_chunk_len(const Geom& g) {
+  if (g.triL) return g.triL;
+  return ((g.dim == 3 ? g.N[2] : g.N[1]) >= 1024) ? 32 : 16;
+}
+
+// Tuned launch shapes (ahoc_tune_set), per kind, dim, precision and log2 N
+// (N of the last axis for the chunk length, of x for the DST CTA); 0 = default.
+std::atomic<int> g_tune[AHOC_TUNE_NKINDS][2][2][13];
+
+int ilog2i(int64_t n) {
+  int l = 0;
+  while ((int64_t(1) << l) < n) ++l;
+  return l;
+}
+
+// a plan's tuned shapes, fixed at its creation
+void apply_tuning(Geom& g, const Opts& o) {
+  const int pi = o.prec == AHOC_MIXED ? 1 : 0, di = g.dim - 2;
+  const int nt = g.dim == 3 ? g.N[2] : g.N[1];
+  g.triL = g_tune[AHOC_TUNE_TRI_CHUNK][di][pi][ilog2i(nt)].load();
+  g.dst_cta = g_tune[AHOC_TUNE_DST_THREADS][di][pi][ilog2i(g.N[0])].load();
+}
 int64_t tri_ncols(const Geom& g) { return (int64_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1); }
 bool chunked_for(const Geom& g, ahoc_precision prec) {
   return prec == AHOC_MIXED || tri_ncols(g) < kChunkedBelow;
@@ -408,6 +440,7 @@ size_t total_bytes(const Geom& g, const Opts& o) {
     gc.nb = g.nb;
     Opts oc = o;
     oc.levels = lv - 1;
+    apply_tuning(gc, oc);
     b += total_bytes(gc, oc);
   }
   return b;
@@ -474,6 +507,11 @@ struct ahoc_plan {
   double* scal_h = nullptr;  // pinned
   int* act_h = nullptr;      // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // the graphs are captured and replayed on a stream of the plan's own, so
+  // that no other work can land on a stream while it is capturing; two
+  // events order it with the caller's stream
+  cudaStream_t gst = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   bool have_last = false;
   // launch accounting (and, with opts.timing, per-launch CUDA events)
   struct EvPair {
@@ -835,6 +873,7 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
   Opts o;
   CKS(read_opts(opts, &o));
   g.nb = o.batch;
+  apply_tuning(g, o);
   *bytes = total_bytes(g, o);
   return AHOC_OK;
 }
@@ -860,6 +899,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   Geom g;
   CKS(make_geom(dim, N, lo, hi, &g));
   g.nb = o.batch;
+  apply_tuning(g, o);
   if (g.n2 * g.nb > 65535) return fail(AHOC_EUNSUPPORTED, "batch too large for this grid (N2 * batch > 65535)");
   if (o.navier >> (2 * dim)) return fail(AHOC_EINVAL, "navier names a face beyond 2 * dim");
   g.navier = o.navier;
@@ -973,11 +1013,16 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMallocHost(&p->hhost, B * (size_t)hstride(o) * sizeof(double)));
   CKC(cudaMallocHost(&p->scal_h, B * sizeof(double)));
   CKC(cudaMallocHost(&p->act_h, B * sizeof(int)));
-  p->use_graphs = o.graphs && !o.timing && stream != nullptr && stream != cudaStreamLegacy;
+  p->use_graphs = o.graphs && !o.timing;
   p->gexec.assign(o.restart, nullptr);
   p->gcount.assign(o.restart, ahoc_plan::GCount{});
   CKC(cudaEventCreate(&p->ev0));
   CKC(cudaEventCreate(&p->ev1));
+  if (p->use_graphs) {
+    CKC(cudaStreamCreateWithFlags(&p->gst, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&p->gev_out, cudaEventDisableTiming));
+  }
   // zero padding of the fields and zero boundary data until a problem brings its own
   CKC(cudaMemsetAsync(p->W1, 0, B * fld, p->st));
   CKC(cudaMemsetAsync(p->W2, 0, B * fld, p->st));
@@ -1142,6 +1187,7 @@ extern "C" {
 
 ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi,
                              const double* alpha, const ahoc_bdata* bd, const ahoc_opts* opts, void* stream) {
+  std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   if (!out) return fail(AHOC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!alpha) return fail(AHOC_EINVAL, "alpha is NULL");
@@ -1172,6 +1218,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
 }
 
 ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd) {
+  std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   if (!p || !alpha) return fail(AHOC_EINVAL, "NULL argument");
   if (b < 0 || b >= p->g.nb) return fail(AHOC_EINVAL, "problem index out of range");
   p->have_last = false;
@@ -1188,8 +1235,28 @@ ahoc_status ahoc_set_active(ahoc_plan* p, const int* mask) {
 
 int ahoc_batch(const ahoc_plan* p) { return p ? p->g.nb : -1; }
 
+ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value) {
+  if (kind < 0 || kind >= AHOC_TUNE_NKINDS) return fail(AHOC_EINVAL, "unknown tuning kind");
+  if (dim != 2 && dim != 3) return fail(AHOC_EINVAL, "dim must be 2 or 3");
+  if (N < 8 || N > kMaxN || !pow2(N)) return fail(AHOC_EINVAL, "N must be a power of two in [8, 4096]");
+  if (prec != AHOC_FP64 && prec != AHOC_MIXED) return fail(AHOC_EINVAL, "prec must be AHOC_FP64 or AHOC_MIXED");
+  const bool ok = value == 0 || (kind == AHOC_TUNE_TRI_CHUNK ? (value == 8 || value == 16 || value == 32)
+                                                             : (value == 128 || value == 256 || value == 512));
+  if (!ok) return fail(AHOC_EINVAL, "value not offered for this kind");
+  g_tune[kind][dim - 2][prec][ilog2i(N)].store(value);
+  return AHOC_OK;
+}
+
+int ahoc_tune_get(int kind, int dim, int64_t N, int prec) {
+  if (kind < 0 || kind >= AHOC_TUNE_NKINDS || (dim != 2 && dim != 3) || N < 8 || N > kMaxN || !pow2(N) ||
+      (prec != AHOC_FP64 && prec != AHOC_MIXED))
+    return -1;
+  return g_tune[kind][dim - 2][prec][ilog2i(N)].load();
+}
+
 ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
   if (!p) return AHOC_OK;
+  std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   ahoc_status s = AHOC_OK;
   if (p->st) {
     if (cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "stream sync at destroy failed");
@@ -1206,6 +1273,9 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
     if (ge) cudaGraphExecDestroy(ge);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->gev_in) cudaEventDestroy(p->gev_in);
+  if (p->gev_out) cudaEventDestroy(p->gev_out);
+  if (p->gst) cudaStreamDestroy(p->gst);
   for (auto& ev : p->pool) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);
@@ -1296,21 +1366,36 @@ ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
 // launches.  Returns after the host copy of the Hessenberg area is complete.
 ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
   const int nb = p->g.nb;
+  cudaStream_t user = p->st;
+  if (p->use_graphs) {
+    // the caller's stream hands over to the plan's graph stream
+    CK(cudaEventRecord(p->gev_in, user));
+    CK(cudaStreamWaitEvent(p->gst, p->gev_in, 0));
+    p->st = p->gst;
+  }
   if (p->use_graphs && !p->gexec[j]) {
     const int64_t l0 = p->launches;
     int64_t k0[AHOC_NK];
     for (int k = 0; k < AHOC_NK; ++k) k0[k] = p->kn[k];
-    CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
-    ahoc_status s = AHOC_OK;
-    if (cudaMemcpyAsync(p->act, p->act_h, nb * sizeof(int), cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
-        cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st) != cudaSuccess)
-      s = fail(AHOC_ECUDA, "copy in graph capture");
-    if (s == AHOC_OK) s = arnoldi_step(p, j, ld, src);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
-    cudaError_t ei = cudaSuccess;
-    if (s == AHOC_OK && e == cudaSuccess) ei = cudaGraphInstantiate(&p->gexec[j], graph, 0);
-    if (graph) cudaGraphDestroy(graph);
+    bool captured = false;
+    {
+      // no plan of this process allocates or frees (synchronising calls)
+      // while a capture is open
+      std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+      if (cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        ahoc_status s = AHOC_OK;
+        if (cudaMemcpyAsync(p->act, p->act_h, nb * sizeof(int), cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
+            cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st) != cudaSuccess)
+          s = AHOC_ECUDA;
+        if (s == AHOC_OK) s = arnoldi_step(p, j, ld, src);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+        if (s == AHOC_OK && e == cudaSuccess && graph &&
+            cudaGraphInstantiate(&p->gexec[j], graph, 0) == cudaSuccess)
+          captured = true;
+        if (graph) cudaGraphDestroy(graph);
+      }
+    }
     // the capture issued nothing: count the graph's launches per replay instead
     ahoc_plan::GCount& gc = p->gcount[j];
     gc.launches = p->launches - l0;
@@ -1319,20 +1404,32 @@ ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
       gc.kn[k] = p->kn[k] - k0[k];
       p->kn[k] = k0[k];
     }
-    if (s != AHOC_OK) return s;
-    if (e != cudaSuccess) return fail(AHOC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    if (ei != cudaSuccess) {
+    if (!captured) {
+      // a capture can be invalidated by another thread's synchronising CUDA
+      // call (outside this library); drop the error it left and run this
+      // plan with plain launches from now on
+      cudaGetLastError();
       p->gexec[j] = nullptr;
-      return fail(AHOC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+      p->use_graphs = false;
+      g_err.clear();
     }
   }
   if (p->use_graphs) {
-    CK(cudaGraphLaunch(p->gexec[j], p->st));
+    const cudaError_t e = cudaGraphLaunch(p->gexec[j], p->st);
+    p->st = user;
+    CK(e);
+    CK(cudaEventRecord(p->gev_out, p->gst));
+    CK(cudaStreamWaitEvent(user, p->gev_out, 0));
     const ahoc_plan::GCount& gc = p->gcount[j];
     p->launches += gc.launches;
     for (int k = 0; k < AHOC_NK; ++k) p->kn[k] += gc.kn[k];
     p->act_now.assign(p->act_h, p->act_h + nb);
   } else {
+    if (p->st != user) {  // the capture failed: hand back to the caller's stream
+      CK(cudaEventRecord(p->gev_out, p->st));
+      p->st = user;
+      CK(cudaStreamWaitEvent(user, p->gev_out, 0));
+    }
     CKS(set_act(p, std::vector<int>(p->act_h, p->act_h + nb)));
     CK(cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
     CKS(arnoldi_step(p, j, ld, src));

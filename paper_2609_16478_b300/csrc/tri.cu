@@ -396,6 +396,7 @@ cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const 
   VGen2D<T> G{};
   if (L == 32) return tri_chunked_L<T, 32, 0>(g, a, modes, md64, rpow, scratch, G, st);
   if (L == 16) return tri_chunked_L<T, 16, 0>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 8) return tri_chunked_L<T, 8, 0>(g, a, modes, md64, rpow, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 
@@ -441,6 +442,8 @@ cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, co
                           : tri_chunked_L<T, 32, 1>(g, a, modes, md64, rpow, scratch, G, st);
   if (L == 16) return add ? tri_chunked_L<T, 16, 2>(g, a, modes, md64, rpow, scratch, G, st)
                           : tri_chunked_L<T, 16, 1>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 8) return add ? tri_chunked_L<T, 8, 2>(g, a, modes, md64, rpow, scratch, G, st)
+                         : tri_chunked_L<T, 8, 1>(g, a, modes, md64, rpow, scratch, G, st);
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,

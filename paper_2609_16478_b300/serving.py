@@ -8,10 +8,13 @@ the Krylov bases stay allocated between requests -- and admits work by an
 HBM budget:
 
   * every shape has a FIFO queue; a worker takes up to B queued requests of
-    one shape (B: the shape's batch size, from the tuner or a default) as
-    soon as a plan of that shape is idle, loads each request's coefficient
-    into a slot of the plan (``ahoc_plan_load``), masks the unused slots
-    (``ahoc_set_active``) and solves the batch in one set of launches;
+    one shape (B: the shape's largest batch, from the tuner or a default),
+    runs them on the smallest idle plan of that shape whose batch is the
+    power of two at or above their number (creating it if the pool has room),
+    loads each request's coefficient into a slot of the plan
+    (``ahoc_plan_load``), masks the unused slots (``ahoc_set_active``) and
+    solves the batch in one set of launches (a plan much larger than its
+    batch would launch mostly masked blocks);
   * a new plan is allocated only if the pool's device bytes stay within the
     budget, after evicting idle plans of other shapes (least recently used
     first); otherwise the request waits for a plan to free up;
@@ -115,25 +118,34 @@ class Scheduler:
         order = sorted((q[0].arrival, k) for k, q in self.queues.items() if q)
         for _, k in order:
             ss = self.slots.setdefault(k, [])
-            slot = next((s for s in ss if not s.busy), None)
+            q = self.queues[k]
+            bmax = max(1, int(self.batch_for(k)))
+            n = min(bmax, len(q))
+            want = 1
+            while want < n:
+                want *= 2
+            want = min(want, bmax)
+            idle = [s for s in ss if not s.busy]
+            # the smallest idle plan that holds all n, else a new plan of size `want`
+            fit = sorted((s for s in idle if s.batch >= n), key=lambda s: s.batch)
+            slot = fit[0] if fit and fit[0].batch <= 2 * want else None
             new = False
-            if slot is None:
-                if len(ss) >= self.max_slots:
-                    continue
-                B = max(1, int(self.batch_for(k)))
+            if slot is None and len(ss) < self.max_slots:
+                B = want
                 nb = int(self.plan_bytes(k, B))
                 while nb > self.budget and B > 1:  # a smaller batch when one plan would not fit
                     B //= 2
                     nb = int(self.plan_bytes(k, B))
-                if not self._evict_for(nb, k):
-                    # nothing else resident and still too large: run it over budget rather than starve
-                    if self.used != 0:
-                        continue
-                slot = SlotState(k, B, nb)
-                ss.append(slot)
-                self.used += nb
-                new = True
-            q = self.queues[k]
+                fits = self._evict_for(nb, k)
+                if fits or self.used == 0:  # nothing else resident: run over budget rather than starve
+                    slot = SlotState(k, B, nb)
+                    ss.append(slot)
+                    self.used += nb
+                    new = True
+            if slot is None and idle:  # no room for a new plan: the largest idle one
+                slot = max(idle, key=lambda s: s.batch)
+            if slot is None:
+                continue
             reqs = [q.popleft() for _ in range(min(slot.batch, len(q)))]
             slot.busy = True
             slot.last_used = now
@@ -348,7 +360,12 @@ def summarize(records: Sequence[Record]) -> Dict[str, float]:
     t0 = min(r.arrival for r in records)
     t1 = max(r.done for r in records)
     dof = sum(r.dof for r in records)
+    shapes = {}
+    for k in sorted({(r.dim, r.N) for r in records}):
+        ls = np.array([r.latency for r in records if (r.dim, r.N) == k]) * 1e3
+        shapes["%dD N=%d" % k] = {"n": int(ls.size), "p50_ms": float(np.percentile(ls, 50)),
+                                  "p99_ms": float(np.percentile(ls, 99))}
     return dict(requests=len(records), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 mean_ms=float(lat.mean()), makespan_s=t1 - t0, dof_per_s=dof / (t1 - t0),
                 mean_batch=float(np.mean([r.batch for r in records])),
-                failed=int(sum(1 for r in records if r.status != 0)))
+                failed=int(sum(1 for r in records if r.status != 0)), by_shape=shapes)

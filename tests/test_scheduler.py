@@ -18,21 +18,26 @@ def test_fifo_batches_by_shape():
     s = _sched(10_000 * MB)
     for rid, (dim, N) in enumerate([(2, 128), (3, 64), (2, 128), (2, 128), (2, 128), (2, 128), (3, 64)]):
         s.arrive(_req(rid, dim, N, 0.1 * rid))
-    w = s.next_work(1.0)
-    assert w.key == (2, 128) and [r.rid for r in w.reqs] == [0, 2, 3, 4] and w.new_slot
-    w2 = s.next_work(1.0)  # oldest waiting head is now request 1 (3D)
-    assert w2.key == (3, 64) and [r.rid for r in w2.reqs] == [1, 6]
-    w3 = s.next_work(1.0)  # a second plan of the busy 2D shape
-    assert w3.key == (2, 128) and [r.rid for r in w3.reqs] == [5] and w3.new_slot
+    w = s.next_work(1.0)  # 5 queued, at most 4 per batch: a plan of 4
+    assert w.key == (2, 128) and [r.rid for r in w.reqs] == [0, 2, 3, 4] and w.new_slot and w.slot.batch == 4
+    w2 = s.next_work(1.0)  # oldest waiting head is now request 1 (3D): a plan of 2 for two requests
+    assert w2.key == (3, 64) and [r.rid for r in w2.reqs] == [1, 6] and w2.slot.batch == 2
+    w3 = s.next_work(1.0)  # a second plan of the busy 2D shape, sized to its one request
+    assert w3.key == (2, 128) and [r.rid for r in w3.reqs] == [5] and w3.new_slot and w3.slot.batch == 1
     assert s.next_work(1.0) is None and s.pending() == 0
+    s.release(w3, 2.0)
     s.release(w, 2.0)
     s.arrive(_req(9, 2, 128, 2.5))
-    w4 = s.next_work(3.0)
-    assert w4.slot is w.slot and not w4.new_slot and [r.rid for r in w4.reqs] == [9]
+    w4 = s.next_work(3.0)  # the idle plan of 1 fits exactly: reused, the plan of 4 stays idle
+    assert w4.slot is w3.slot and not w4.new_slot and [r.rid for r in w4.reqs] == [9]
+    for rid in range(10, 13):
+        s.arrive(_req(rid, 2, 128, 3.0))
+    w5 = s.next_work(3.5)  # three requests: the idle plan of 4
+    assert w5.slot is w.slot and [r.rid for r in w5.reqs] == [10, 11, 12]
 
 
 def test_budget_waits_then_evicts_lru():
-    s = _sched(250 * MB)  # room for two 100 MB plans
+    s = _sched(250 * MB, nbytes=400 * MB)  # single-request plans of 100 MB: room for two
     s.arrive(_req(0, 2, 128, 0.0))
     s.arrive(_req(1, 2, 256, 0.1))
     s.arrive(_req(2, 3, 64, 0.2))
