@@ -79,6 +79,7 @@ typedef struct {
                             known there from g_D by tangential differentiation (Remark, Sec. 2.2) */
   const double* g_L;     /* face array: Laplace u on the face interiors; read on Navier faces
                             only (opts.navier), where v = alpha g_L is data (Eq. 2)              */
+  const double* beta;    /* full grid: beta of Eq. 1, read when opts.variable_beta is set        */
 } ahoc_bdata;
 
 /* Options; a NULL pointer selects the defaults given in brackets. */
@@ -144,6 +145,15 @@ typedef struct {
                              graphs with timing != 0; a capture that another thread's CUDA
                              call invalidates leaves the plan on plain launches).  nonzero:
                              plain launches.                                                   */
+  int variable_beta;      /* [0] problem class: nonzero makes beta / alpha variable, with beta
+                             from each problem's bd->beta.  FP64: every v-solve is a
+                             right-preconditioned BiCGSTAB on (L_h - M(beta/alpha .)) V = rhs,
+                             preconditioned by (and started from) the FFT solve with the
+                             constant shift opts.shift (a representative beta/alpha), as in the
+                             paper's solver settings (Sec. 4); no CUDA graphs.  MIXED: the FP32
+                             corrections use the constant shift and the FP64 residual the
+                             exact beta/alpha, so the refinement converges to the same
+                             discrete solution                                                 */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -167,6 +177,7 @@ typedef struct {
   int inner_iters[16];    /* AHOC_MIXED: GMRES iterations of each correction solve              */
   double refine_du[16];   /* AHOC_MIXED: ||dU||_2 / ||U||_2 of each correction (U after it)    */
   ahoc_status status;     /* this problem's outcome (AHOC_OK or AHOC_ENOCONV)                   */
+  int vsolve_iters;       /* opts.variable_beta, FP64: BiCGSTAB iterations over all v-solves   */
 } ahoc_info;
 
 /* Bytes of device workspace a plan of this shape needs (Sec. 2.3, Algorithm 1:

@@ -12,6 +12,7 @@ import ctypes as C
 import os
 from typing import Dict, Optional, Sequence
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -31,7 +32,7 @@ SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matve
 
 class ahoc_bdata(C.Structure):
     _fields_ = [("g_D", C.c_void_p), ("g_N", C.c_void_p), ("lapt_gD", C.c_void_p), ("v_edge", C.c_void_p),
-                ("g_L", C.c_void_p)]
+                ("g_L", C.c_void_p), ("beta", C.c_void_p)]
 
 
 AHOC_NK = 8
@@ -42,7 +43,8 @@ class ahoc_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_iters", C.c_int), ("restart", C.c_int), ("precond", C.c_int),
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
-                ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int)]
+                ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int),
+                ("variable_beta", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -52,7 +54,7 @@ class ahoc_info(C.Structure):
                 ("levels", C.c_int), ("coarse_iters", C.c_int),
                 ("kernel_ms_top", C.c_double * AHOC_NK), ("kernel_launches_top", C.c_int64 * AHOC_NK),
                 ("refine_steps", C.c_int), ("refine_hist", C.c_double * 16), ("inner_iters", C.c_int * 16),
-                ("refine_du", C.c_double * 16), ("status", C.c_int)]
+                ("refine_du", C.c_double * 16), ("status", C.c_int), ("vsolve_iters", C.c_int)]
 
 
 class AhocError(RuntimeError):
@@ -133,8 +135,9 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1, graphs=True, navier=0, shift=0.0):
+          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False):
     o = ahoc_opts()
+    o.variable_beta = 1 if variable_beta else 0
     o.batch = int(batch)
     o.navier = int(navier)
     o.shift = float(shift)
@@ -154,10 +157,10 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1
 
 
 def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1,
-                    batch: int = 1, shift: float = 0.0) -> int:
+                    batch: int = 1, shift: float = 0.0, variable_beta: bool = False) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift)
+    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift, variable_beta=variable_beta)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -174,7 +177,8 @@ def _info_dict(info: "ahoc_info", st: int) -> Dict:
                 refine_steps=info.refine_steps,
                 refine_hist=[info.refine_hist[i] for i in range(min(16, info.refine_steps + 1))],
                 inner_iters=[info.inner_iters[i] for i in range(min(16, info.refine_steps))],
-                refine_du=[info.refine_du[i] for i in range(min(16, info.refine_steps))])
+                refine_du=[info.refine_du[i] for i in range(min(16, info.refine_steps))],
+                vsolve_iters=info.vsolve_iters)
 
 
 class Plan:
@@ -188,6 +192,7 @@ class Plan:
 
     def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None, navier: int = 0, shift: float = 0.0,
+                 beta=None,
                  prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
@@ -214,15 +219,16 @@ class Plan:
         self.prec = prec
         self.device = alpha.device
         B = self.batch
-        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift)
+        variable_beta = beta is not None
+        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift, variable_beta)
         self.workspace_bytes = nb
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, B * self.nfull, "g_D"), _ptr(g_N, B * self.ngamma, "g_N"),
                         _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"),
-                        _ptr(g_L, B * self.ngamma, "g_L"))
+                        _ptr(g_L, B * self.ngamma, "g_L"), _ptr(beta, B * self.nfull, "beta"))
         o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
-                  navier, shift)
+                  navier, shift, variable_beta)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
@@ -251,11 +257,11 @@ class Plan:
         out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
         return u, (out[0] if B == 1 else out)
 
-    def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None):
+    def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None, beta=None):
         """Replace problem b's coefficient and boundary data (``ahoc_plan_load``)."""
         bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
                         _ptr(lapt_gD, self.ngamma, "lapt_gD"), _ptr(v_edge, self.nfull, "v_edge"),
-                        _ptr(g_L, self.ngamma, "g_L"))
+                        _ptr(g_L, self.ngamma, "g_L"), _ptr(beta, self.nfull, "beta"))
         _check(lib().ahoc_plan_load(self._h, int(b), _ptr(alpha, self.nfull, "alpha"), C.byref(bd)), "ahoc_plan_load")
 
     def set_active(self, mask: Sequence[int]):
@@ -329,13 +335,19 @@ def plan_for(data: Dict, device="cuda", **kw) -> "Plan":
         return t.reshape(-1).contiguous().to(device)
     alpha = dev("alpha")
     navier = sum(1 << int(f) for f in (data.get("navier") or ()))
-    beta = float(data.get("beta") or 0.0)
+    beta = data.get("beta")
     shift = 0.0
-    if beta != 0.0:
+    if beta is not None and np.ndim(beta) > 0:
+        # variable beta: BiCGSTAB v-solves preconditioned by the FFT solve with the mean of beta/alpha
+        kw.setdefault("beta", dev("beta"))
+        shift = float((kw["beta"] / alpha).mean())
+    elif beta:
         lo_, hi_ = float(alpha.min()), float(alpha.max())
         if lo_ != hi_:
-            raise ValueError("beta != 0 needs a constant alpha (the shift beta / alpha must be constant)")
-        shift = beta / lo_
+            kw.setdefault("beta", torch.full_like(alpha, float(beta)))
+            shift = float((kw["beta"] / alpha).mean())
+        else:
+            shift = float(beta) / lo_
     kw.setdefault("navier", navier)
     kw.setdefault("shift", shift)
     return Plan(data["dim"], data["N"], alpha, lo=data["lo"], hi=data["hi"], g_D=dev("g_D"),

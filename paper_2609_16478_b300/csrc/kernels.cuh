@@ -105,7 +105,8 @@ cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t s
 //   rhs = -M f - (L - gam M)_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
-                        const double* vedge, cudaStream_t st, const T* srcv = nullptr);
+                        const double* vedge, cudaStream_t st, const T* srcv = nullptr,
+                        const double* gam = nullptr);
 // u-equation right-hand side for L_h U_int = rhs:
 //   rhs = M(V / alpha) - L_bdry(g_D),  V = Q on face points (M reaches no edges);
 //   ainv = 1/alpha on the full grid, in T.
@@ -123,7 +124,17 @@ cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, 
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
-                            cudaStream_t st, const double* gL = nullptr);
+                            cudaStream_t st, const double* gL = nullptr, const double* gam = nullptr);
+// variable beta/alpha (gam on the full grid): y = L_h x - M(gam x) on interior
+// points, x = 0 on the boundary (stencil.cu)
+cudaError_t launch_vop(const Geom& g, const Coefs& cf, double* y, const double* x, const double* gam,
+                       cudaStream_t st);
+// y = c[3b] x0 + c[3b+1] x1 + c[3b+2] x2 per problem b of g.nb (n entries each;
+// x1, x2 may be NULL; c on the device, 3 g.nb entries); masked by g.act
+cudaError_t launch_comb(const Geom& g, int64_t n, double* y, const double* x0, const double* x1, const double* x2,
+                        const double* c, cudaStream_t st);
+// out = a * b elementwise
+cudaError_t launch_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);
 // U += dU, V += dV; for problem b, out[2b] = sum dU^2 and out[2b + 1] = sum U^2
 // after the update (deterministic: nblocks fixed partials per problem in
 // `partial`, 2 * nb * nblocks doubles)

@@ -61,7 +61,8 @@ struct Opts {
   int batch = 1;  // problems of this shape solved together
   int graphs = 1;  // replay GMRES iterations as CUDA graphs
   int navier = 0;        // Navier faces (bit 2a + side)
-  double shift = 0.0;    // constant beta / alpha of the v-equation
+  double shift = 0.0;    // constant beta / alpha of the v-equation (reference value if variable)
+  int varb = 0;          // variable beta / alpha (problems bring beta)
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -81,6 +82,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.graphs = o->no_graphs ? 0 : 1;
     d.navier = o->navier;
     d.shift = o->shift;
+    d.varb = o->variable_beta ? 1 : 0;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -267,6 +269,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
       tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb, modes_v, modesf_v, rpow_v, gL,
+      gam, bcg, bcoef,
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
@@ -372,6 +375,10 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.qa = take(B * face);
   L.rpow = take(chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
   L.rpow_v = take(shifted && chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  // variable beta/alpha: gam = beta/alpha per problem; the BiCGSTAB v-solve's 9 fields (FP64 path)
+  L.gam = take(o.varb ? B * full : 0);
+  L.bcg = take(o.varb && o.prec == AHOC_FP64 ? 9 * B * fld : 0);
+  L.bcoef = take(o.varb ? 3 * B * sizeof(double) : 0);
   L.gL = take(B * face);
   L.partial = take(B * (size_t)pstride(o) * sizeof(double));
   L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
@@ -477,6 +484,12 @@ struct ahoc_plan {
   double* rpow_v = nullptr;
   double* gL = nullptr;
   bool has_gL = false;
+  // variable beta/alpha: gam = beta/alpha per problem (full grid) and the
+  // BiCGSTAB fields (rhs, x is W1, r, r-hat, p, v, s, t, p-hat, s-hat)
+  double* gam = nullptr;
+  double* bcg = nullptr;
+  double* bcoef = nullptr;
+  int bicg_iters = 0;  // BiCGSTAB iterations of the last solve (summed over v-solves)
   // mixed precision
   float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
@@ -595,10 +608,16 @@ ahoc_status poisson_inplace(ahoc_plan* p, double* W, bool vsolve = false) {
 }
 
 // V-solve then U-solve (Algorithm 1, two FFT-based solves); leaves V in W1, U in W2.
+ahoc_status bicgstab_v(ahoc_plan* p);
+
 ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) {
   const Geom& g = p->g;
-  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data && p->has_vedge ? p->vedge : nullptr, p->st));
-  CKS(poisson_inplace(p, p->W1, true));
+  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data && p->has_vedge ? p->vedge : nullptr, p->st,
+                                       nullptr, p->gam));
+  if (p->o.varb)
+    CKS(bicgstab_v(p));  // variable beta/alpha: (L_h - M(gam .)) V = rhs iteratively
+  else
+    CKS(poisson_inplace(p, p->W1, true));
   RUN(AHOC_K_URHS,
       launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data && p->has_gD ? p->gD : nullptr, p->st));
   CKS(poisson_inplace(p, p->W2));
@@ -712,7 +731,7 @@ ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
     RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
     return AHOC_OK;
   }
-  if (fused_ok(p->g)) return fused2d<double>(p, f2arrays_d(p), q, nullptr, nullptr, nullptr, y, false);
+  if (fused_ok(p->g) && !p->o.varb) return fused2d<double>(p, f2arrays_d(p), q, nullptr, nullptr, nullptr, y, false);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -830,6 +849,146 @@ bool any(const std::vector<int>& m) {
   for (int v : m)
     if (v) return true;
   return false;
+}
+
+// The v-solve with variable beta/alpha (Sec. 2.2 v-equation; Sec. 4 solver
+// settings: BiCGSTAB preconditioned by an FFT solver): B V = rhs with
+// B = L_h - M(gam .) and V = 0 on the boundary, rhs in W1 on entry, V in W1 on
+// exit.  Right-preconditioned BiCGSTAB; the preconditioner and the initial
+// guess are the FFT solve with the constant shift gam0 = opts.shift, so
+// B P^-1 = I - M((gam - gam0) .) P^-1, a lower-order perturbation of the
+// identity.  Every problem of the batch in lockstep, each stopping on its own
+// at ||r|| <= 1e-14 ||rhs|| (or on stagnation); the caller's mask is restored.
+constexpr double kBicgTol = 1e-14;
+constexpr int kBicgMaxIters = 200;
+ahoc_status bicgstab_v(ahoc_plan* p) {
+  const Geom& g = p->g;
+  const int nb = g.nb, hs = hstride(p->o);
+  const int64_t n = g.npad;
+  double* b = p->bcg;
+  double* r = b + (int64_t)nb * n;
+  double* rh = r + (int64_t)nb * n;
+  double* pv = rh + (int64_t)nb * n;
+  double* v = pv + (int64_t)nb * n;
+  double* s = v + (int64_t)nb * n;
+  double* t = s + (int64_t)nb * n;
+  double* ph = t + (int64_t)nb * n;
+  double* sh = ph + (int64_t)nb * n;
+  double* x = p->W1;
+  const std::vector<int> caller = p->act_now;
+  std::vector<int> live = caller;
+  std::vector<double> c(3 * (size_t)nb, 0.0);
+  auto comb = [&](double* y, const double* x0, const double* x1, const double* x2) -> ahoc_status {
+    CK(cudaMemcpyAsync(p->bcoef, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    RUN(AHOC_K_OTHER, launch_comb(g, n, y, x0, x1, x2, p->bcoef, p->st));
+    return AHOC_OK;
+  };
+  auto set3 = [&](double a0, const std::vector<double>* a1, double s1, const std::vector<double>* a2, double s2) {
+    for (int i = 0; i < nb; ++i) {
+      c[3 * i] = a0;
+      c[3 * i + 1] = a1 ? s1 * (*a1)[i] : s1;
+      c[3 * i + 2] = a2 ? s2 * (*a2)[i] : s2;
+    }
+  };
+  // <a_b, x_b> of every problem in the mask into the exchange area at off
+  auto fdot = [&](const double* a, const double* w, int off) -> ahoc_status {
+    BatchDot bd;
+    bd.vstride = n;
+    bd.wstride = n;
+    bd.pstride = pstride(p->o);
+    bd.act = g.act;
+    RUNN(AHOC_K_KRYLOV, 2, launch_mdot(a, n, 1, w, n, p->partial, kDotBlocks, p->hdev + off, p->st, nb, bd, hs));
+    return AHOC_OK;
+  };
+  auto h = [&](int i, int off) { return p->hhost[(size_t)i * hs + off]; };
+  std::vector<double> bn(nb), rho(nb, 1.0), rho1(nb), alpha(nb, 1.0), omega(nb, 1.0), beta(nb), best(nb);
+  std::vector<int> stall(nb, 0);
+  set3(1.0, nullptr, 0.0, nullptr, 0.0);
+  CKS(comb(b, x, nullptr, nullptr));  // b = rhs
+  CKS(poisson_inplace(p, x, true));    // x0 = P^-1 rhs
+  RUN(AHOC_K_OTHER, launch_vop(g, p->cf, v, x, p->gam, p->st));
+  set3(1.0, nullptr, -1.0, nullptr, 0.0);
+  CKS(comb(r, b, v, nullptr));  // r = rhs - B x0
+  set3(1.0, nullptr, 0.0, nullptr, 0.0);
+  CKS(comb(rh, r, nullptr, nullptr));
+  CK(cudaMemsetAsync(pv, 0, (size_t)nb * n * sizeof(double), p->st));
+  CK(cudaMemsetAsync(v, 0, (size_t)nb * n * sizeof(double), p->st));
+  CKS(fdot(b, b, 0));
+  CKS(fdot(rh, r, 1));
+  CKS(fetch(p));
+  for (int i = 0; i < nb; ++i) {
+    if (!live[i]) continue;
+    bn[i] = std::sqrt(h(i, 0));
+    rho1[i] = h(i, 1);
+    best[i] = std::sqrt(std::fabs(rho1[i]));
+    if (!(bn[i] > 0) || best[i] <= kBicgTol * bn[i]) live[i] = 0;
+  }
+  for (int it = 0; it < kBicgMaxIters && any(live); ++it) {
+    CKS(set_act(p, live));
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) {
+        beta[i] = (rho1[i] / rho[i]) * (alpha[i] / omega[i]);
+        rho[i] = rho1[i];
+      }
+    // p = r + beta (p - omega v)
+    for (int i = 0; i < nb; ++i) {
+      c[3 * i] = 1.0;
+      c[3 * i + 1] = beta[i];
+      c[3 * i + 2] = -beta[i] * omega[i];
+    }
+    CKS(comb(pv, r, pv, v));
+    set3(1.0, nullptr, 0.0, nullptr, 0.0);
+    CKS(comb(ph, pv, nullptr, nullptr));
+    CKS(poisson_inplace(p, ph, true));
+    RUN(AHOC_K_OTHER, launch_vop(g, p->cf, v, ph, p->gam, p->st));
+    CKS(fdot(rh, v, 0));
+    CKS(fetch(p));
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) {
+        const double d = h(i, 0);
+        alpha[i] = d != 0.0 ? rho[i] / d : 0.0;
+        if (!std::isfinite(alpha[i])) return fail(AHOC_ENUMERIC, "BiCGSTAB breakdown in the v-solve");
+      }
+    // s = r - alpha v
+    set3(1.0, &alpha, -1.0, nullptr, 0.0);
+    CKS(comb(s, r, v, nullptr));
+    set3(1.0, nullptr, 0.0, nullptr, 0.0);
+    CKS(comb(sh, s, nullptr, nullptr));
+    CKS(poisson_inplace(p, sh, true));
+    RUN(AHOC_K_OTHER, launch_vop(g, p->cf, t, sh, p->gam, p->st));
+    CKS(fdot(t, s, 0));
+    CKS(fdot(t, t, 1));
+    CKS(fetch(p));
+    for (int i = 0; i < nb; ++i)
+      if (live[i]) omega[i] = h(i, 1) > 0 ? h(i, 0) / h(i, 1) : 0.0;
+    // x += alpha p-hat + omega s-hat;  r = s - omega t
+    set3(1.0, &alpha, 1.0, &omega, 1.0);
+    CKS(comb(x, x, ph, sh));
+    set3(1.0, &omega, -1.0, nullptr, 0.0);
+    CKS(comb(r, s, t, nullptr));
+    CKS(fdot(r, r, 0));
+    CKS(fdot(rh, r, 1));
+    CKS(fetch(p));
+    ++p->bicg_iters;
+    for (int i = 0; i < nb; ++i) {
+      if (!live[i]) continue;
+      const double rn = std::sqrt(h(i, 0));
+      rho1[i] = h(i, 1);
+      if (!std::isfinite(rn)) return fail(AHOC_ENUMERIC, "non-finite residual in the v-solve");
+      if (rn <= kBicgTol * bn[i] || omega[i] == 0.0 || rho1[i] == 0.0) {
+        live[i] = 0;
+        continue;
+      }
+      // stagnation at the rounding floor: three steps without a new best
+      if (rn < 0.5 * best[i]) {
+        best[i] = rn;
+        stall[i] = 0;
+      } else if (++stall[i] >= 3) {
+        live[i] = 0;
+      }
+    }
+  }
+  return set_act(p, caller);
 }
 
 bool is_fin(double x) { return std::isfinite(x); }
@@ -965,6 +1124,11 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->modes = at<Mode<double>>(p, L.modes);
   p->modes_v = shifted ? at<Mode<double>>(p, L.modes_v) : p->modes;
   p->gL = at<double>(p, L.gL);
+  if (o.varb) {
+    p->gam = at<double>(p, L.gam);
+    p->bcoef = at<double>(p, L.bcoef);
+    if (o.prec == AHOC_FP64) p->bcg = at<double>(p, L.bcg);
+  }
   p->b = at<double>(p, L.b);
   p->Q = at<double>(p, L.Q);
   p->r = at<double>(p, L.r);
@@ -1013,7 +1177,8 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMallocHost(&p->hhost, B * (size_t)hstride(o) * sizeof(double)));
   CKC(cudaMallocHost(&p->scal_h, B * sizeof(double)));
   CKC(cudaMallocHost(&p->act_h, B * sizeof(int)));
-  p->use_graphs = o.graphs && !o.timing;
+  // the BiCGSTAB v-solves read residual norms on the host inside the matvec
+  p->use_graphs = o.graphs && !o.timing && !(o.varb && o.prec == AHOC_FP64);
   p->gexec.assign(o.restart, nullptr);
   p->gcount.assign(o.restart, ahoc_plan::GCount{});
   CKC(cudaEventCreate(&p->ev0));
@@ -1154,6 +1319,10 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
   CKS(put(p->gN + pg, bd ? bd->g_N : nullptr, face, p->has_gN));
   CKS(put(p->lapt + pg, bd ? bd->lapt_gD : nullptr, face, p->has_lapt));
   CKS(put(p->gL + pg, bd ? bd->g_L : nullptr, face, p->has_gL));
+  if (p->o.varb) {
+    if (!bd || !bd->beta) return fail(AHOC_EINVAL, "variable_beta needs beta for every problem");
+    CKC(launch_mul(p->gam + pf, bd->beta, p->ainv + pf, g.nfull, p->st));
+  }
   if (p->coarse) {
     // coarse data by injection, staged in this problem's field and face buffers
     Geom gc = p->coarse->g;
@@ -1165,13 +1334,15 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
     double* gN_c = bd && bd->g_N ? p->b + pg : nullptr;
     double* lt_c = bd && bd->lapt_gD ? p->r + pg : nullptr;
     double* gL_c = bd && bd->g_L ? p->tmp + pg : nullptr;
+    double* be_c = bd && bd->beta ? p->W2 + pp + 2 * gc.nfull : nullptr;
     CKC(launch_inject_full(gc, g, a_c, alpha, p->st));
     if (gD_c) CKC(launch_inject_full(gc, g, gD_c, bd->g_D, p->st));
     if (vE_c) CKC(launch_inject_full(gc, g, vE_c, bd->v_edge, p->st));
     if (gN_c) CKC(launch_inject_face(gc, g, gN_c, bd->g_N, p->st));
     if (lt_c) CKC(launch_inject_face(gc, g, lt_c, bd->lapt_gD, p->st));
     if (gL_c) CKC(launch_inject_face(gc, g, gL_c, bd->g_L, p->st));
-    ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c, gL_c};
+    if (be_c) CKC(launch_inject_full(gc, g, be_c, bd->beta, p->st));
+    ahoc_bdata bc{gD_c, gN_c, lt_c, vE_c, gL_c, be_c};
     CKS(plan_load(p->coarse, b, a_c, &bc));
     CKC(cudaStreamSynchronize(p->st));
     CKC(cudaMemsetAsync(p->W1 + pp, 0, (size_t)g.npad * sizeof(double), p->st));
@@ -1205,6 +1376,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
       bb.lapt_gD = bd->lapt_gD ? bd->lapt_gD + (int64_t)b * g.ngamma : nullptr;
       bb.v_edge = bd->v_edge ? bd->v_edge + (int64_t)b * g.nfull : nullptr;
       bb.g_L = bd->g_L ? bd->g_L + (int64_t)b * g.ngamma : nullptr;
+      bb.beta = bd->beta ? bd->beta + (int64_t)b * g.nfull : nullptr;
     }
     s = plan_load(p, b, alpha + (int64_t)b * g.nfull, &bb);
   }
@@ -1694,7 +1866,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
     RUNN(AHOC_K_OTHER, 2,
          launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->has_gD ? p->gD : nullptr,
                          p->has_vedge ? p->vedge : nullptr, p->has_gN ? p->gN : nullptr,
-                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st, p->has_gL ? p->gL : nullptr));
+                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st, p->has_gL ? p->gL : nullptr, p->gam));
     // correction right-hand side b = -R_d(0)
     if (fused_ok(g)) {
       CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));
@@ -1798,6 +1970,7 @@ ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol)
     p->kn_top[k] = 0;
   }
   p->ps.assign(p->g.nb, ProbStat{});
+  p->bicg_iters = 0;
   if (p->o.prec == AHOC_MIXED) CKS(solve_mixed(p, f, u, tol));
   else CKS(solve_fp64(p, f, u, tol));
   CK(cudaStreamSynchronize(p->st));
@@ -1825,6 +1998,7 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
     if (!info) continue;
     ahoc_info* in = info + i;
     in->status = s.status;
+    in->vsolve_iters = p->bicg_iters;
     in->iters = s.iters;
     in->restarts = s.restarts;
     in->rel_resid = s.rel;

@@ -46,7 +46,7 @@ __device__ __forceinline__ bool near_bdry(const Geom& g, int i, int j, int k) {
 template <typename T>
 __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __restrict__ Q,
                        const double* __restrict__ f, const double* __restrict__ vedge,
-                       const T* __restrict__ srcv) {
+                       const T* __restrict__ srcv, const double* __restrict__ gam) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int bi = blockIdx.z / (int)g.n2;
   if (i >= g.n0 || g.skip(bi)) return;
@@ -56,6 +56,7 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
   if (Q) Q += (int64_t)bi * g.ngamma;
   if (f) f += (int64_t)bi * g.nfull;
   if (vedge) vedge += (int64_t)bi * g.nfull;
+  if (gam) gam += (int64_t)bi * g.nfull;
   const int64_t t = g.pad(i, j, k);
   if (is_pad(g, i, j, k)) { out[t] = (T)0; return; }
   T acc = 0;
@@ -77,7 +78,8 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
             vb = vedge[g.full(ii, jj, kk)];
           }
           // the shift gam M V reaches the axis neighbours (weight Mn): (L - gam M) V = ...
-          const double ce = (dx * dx + dy * dy + dz * dz == 1) ? c - cf.gam * cf.Mn : c;
+          const double gn = gam ? gam[g.full(ii, jj, kk)] : cf.gam;
+          const double ce = (dx * dx + dy * dy + dz * dz == 1) ? c - gn * cf.Mn : c;
           acc -= (T)ce * (T)vb;
         }
   }
@@ -297,9 +299,9 @@ static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) 
 
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
-                        const double* vedge, cudaStream_t st, const T* srcv) {
+                        const double* vedge, cudaStream_t st, const T* srcv, const double* gam) {
   const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)(g.n2 * g.nb));
-  k_vrhs<T><<<grid, 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv);
+  k_vrhs<T><<<grid, 256, 0, st>>>(g, cf, out, Q, f, vedge, srcv, gam);
   return cudaGetLastError();
 }
 template <typename T>
@@ -343,14 +345,14 @@ cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t 
 }
 
 template cudaError_t launch_vrhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
-                                         const double*, cudaStream_t, const double*);
+                                         const double*, cudaStream_t, const double*, const double*);
 template cudaError_t launch_urhs<double>(const Geom&, const Coefs&, double*, const double*, const double*,
                                          const double*, const double*, cudaStream_t, const double*);
 template cudaError_t launch_trace<double>(const Geom&, const Coefs&, double*, const double*, const double*,
                                           const double*, const double*, const double*, const double*, cudaStream_t,
                                           const double*, const double*);
 template cudaError_t launch_vrhs<float>(const Geom&, const Coefs&, float*, const double*, const double*,
-                                        const double*, cudaStream_t, const float*);
+                                        const double*, cudaStream_t, const float*, const double*);
 template cudaError_t launch_urhs<float>(const Geom&, const Coefs&, float*, const float*, const float*,
                                         const double*, const double*, cudaStream_t, const float*);
 template cudaError_t launch_trace<float>(const Geom&, const Coefs&, double*, const float*, const double*,
@@ -496,8 +498,8 @@ __device__ __forceinline__ double vfull(const Geom& g, const double* V, const do
   return vedge ? vedge[g.full(i, j, k)] : 0.0;
 }
 
-__global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __restrict__ rv,
-                           const double* __restrict__ U, const double* __restrict__ V, const double* __restrict__ Q,
+__global__ void k_residual(Geom g, Coefs cf, const double* __restrict__ gam, float* __restrict__ ru,
+                           float* __restrict__ rv, const double* __restrict__ U, const double* __restrict__ V, const double* __restrict__ Q,
                            const double* __restrict__ f, const double* __restrict__ gD,
                            const double* __restrict__ vedge, const double* __restrict__ ainv) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -514,6 +516,7 @@ __global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __re
     if (gD) gD += fo;
     if (vedge) vedge += fo;
     ainv += fo;
+    if (gam) gam += fo;
   }
   int i, j, k;
   decompose(g, t, i, j, k);
@@ -540,20 +543,22 @@ __global__ void k_residual(Geom g, Coefs cf, float* __restrict__ ru, float* __re
           lv += c * V[o];
         }
       }
-  // M(V/alpha), M V (the shift term) and M f: centre and the axis neighbours
-  double mv = cf.Mc * V[t] * ainv[g.full(i, j, k)];
-  double mvv = cf.Mc * V[t];
-  double mf = f ? cf.Mc * f[g.full(i, j, k)] : 0.0;
+  // M(V/alpha), M(gam V) (the shift term) and M f: centre and the axis neighbours
+  const int64_t fc = g.full(i, j, k);
+  double mv = cf.Mc * V[t] * ainv[fc];
+  double mgv = cf.Mc * (gam ? gam[fc] : cf.gam) * V[t];
+  double mf = f ? cf.Mc * f[fc] : 0.0;
   for (int a = 0; a < g.dim; ++a)
     for (int s = -1; s <= 1; s += 2) {
       const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
+      const int64_t fn = g.full(ii, jj, kk);
       const double vn = vfull(g, V, Q, vedge, ii, jj, kk);
-      mv += cf.Mn * vn * ainv[g.full(ii, jj, kk)];
-      mvv += cf.Mn * vn;
-      if (f) mf += cf.Mn * f[g.full(ii, jj, kk)];
+      mv += cf.Mn * vn * ainv[fn];
+      mgv += cf.Mn * (gam ? gam[fn] : cf.gam) * vn;
+      if (f) mf += cf.Mn * f[fn];
     }
   ru[t] = (float)(-(lu - mv));
-  rv[t] = (float)(mf + lv - cf.gam * mvv);
+  rv[t] = (float)(mf + lv - mgv);
 }
 
 // r_q at every face point (FP64)
@@ -646,8 +651,8 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(Geom g, double* __re
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
-                            cudaStream_t st, const double* gL) {
-  k_residual<<<dim3(nblk(g.npad, 256), g.nb), 256, 0, st>>>(g, cf, ru, rv, U, V, Q, f, gD, vedge, ainv);
+                            cudaStream_t st, const double* gL, const double* gam) {
+  k_residual<<<dim3(nblk(g.npad, 256), g.nb), 256, 0, st>>>(g, cf, gam, ru, rv, U, V, Q, f, gD, vedge, ainv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_residual_q<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt, gL);
@@ -660,6 +665,87 @@ cudaError_t launch_accumulate(const Geom& g, double* U, const float* dU, double*
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_cols(partial, nblocks, 2 * g.nb, out, st);
+}
+
+}  // namespace ahoc
+
+namespace ahoc {
+
+// ---------------------------------------------------------------------------
+// Variable beta / alpha (Sec. 2.2 v-equation, beta/alpha not constant): the
+// interior operator B V = L_h V - M(gam V) with V = 0 on the boundary
+// (gam = beta/alpha on the full grid), for the preconditioned BiCGSTAB
+// v-solve (Sec. 4, solver settings), and the linear combinations it needs.
+// ---------------------------------------------------------------------------
+__global__ void k_vop(Geom g, Coefs cf, double* __restrict__ y, const double* __restrict__ x,
+                      const double* __restrict__ gam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bi = blockIdx.z / (int)g.n2;
+  if (i >= g.n0 || g.skip(bi)) return;
+  const int j = blockIdx.y, k = blockIdx.z - bi * (int)g.n2;
+  y += (int64_t)bi * g.npad;
+  x += (int64_t)bi * g.npad;
+  gam += (int64_t)bi * g.nfull;
+  const int64_t t = g.pad(i, j, k);
+  if (is_pad(g, i, j, k)) {
+    y[t] = 0.0;
+    return;
+  }
+  auto xv = [&](int ii, int jj, int kk) -> double {
+    int ax, sd;
+    return bclass(g, ii, jj, kk, ax, sd) ? 0.0 : x[g.pad(ii, jj, kk)];
+  };
+  double acc = 0.0;
+  const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
+  for (int dz = dzlo; dz <= dzhi; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const double c = cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (c != 0.0) acc += c * xv(i + dx, j + dy, k + dz);
+      }
+  double m = cf.Mc * gam[g.full(i, j, k)] * x[t];
+  for (int a = 0; a < g.dim; ++a)
+    for (int s = -1; s <= 1; s += 2) {
+      const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
+      m += cf.Mn * gam[g.full(ii, jj, kk)] * xv(ii, jj, kk);
+    }
+  y[t] = acc - m;
+}
+
+// y = c[3b] x0 + c[3b + 1] x1 + c[3b + 2] x2 per problem b (x1, x2 may be NULL;
+// any x may alias y), over n entries per problem
+__global__ void k_comb(int64_t n, const int* act, double* __restrict__ y, const double* x0, const double* x1,
+                       const double* x2, const double* __restrict__ c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bi = blockIdx.y;
+  if (i >= n || (act && !act[bi])) return;
+  const int64_t o = (int64_t)bi * n + i;
+  double v = c[3 * bi] * x0[o];
+  if (x1) v += c[3 * bi + 1] * x1[o];
+  if (x2) v += c[3 * bi + 2] * x2[o];
+  y[o] = v;
+}
+
+__global__ void k_mul(double* __restrict__ out, const double* __restrict__ a, const double* __restrict__ b,
+                      int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = a[t] * b[t];
+}
+
+cudaError_t launch_vop(const Geom& g, const Coefs& cf, double* y, const double* x, const double* gam,
+                       cudaStream_t st) {
+  const dim3 grid((unsigned)((g.n0 + 255) / 256), (unsigned)g.n1, (unsigned)(g.n2 * g.nb));
+  k_vop<<<grid, 256, 0, st>>>(g, cf, y, x, gam);
+  return cudaGetLastError();
+}
+cudaError_t launch_comb(const Geom& g, int64_t n, double* y, const double* x0, const double* x1, const double* x2,
+                        const double* c, cudaStream_t st) {
+  k_comb<<<dim3(nblk(n, 256), g.nb), 256, 0, st>>>(n, g.act, y, x0, x1, x2, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st) {
+  k_mul<<<nblk(n, 256), 256, 0, st>>>(out, a, b, n);
+  return cudaGetLastError();
 }
 
 }  // namespace ahoc

@@ -98,7 +98,7 @@ class Problem:
     lo: Tuple[float, ...] = (0.0, 0.0, 0.0)
     hi: Tuple[float, ...] = (1.0, 1.0, 1.0)
     note: str = ""
-    beta: float = 0.0                          # constant beta of Eq. 1
+    beta: object = 0.0                         # beta of Eq. 1: a number or a sympy expression
     navier: Tuple[int, ...] = ()               # Navier faces (2 * axis + side): Lap u = g_L there
 
     def exprs(self) -> Dict[str, sp.Expr]:
@@ -111,7 +111,8 @@ class Problem:
             out["u"] = u
             out["lap"] = lap
             out["v"] = w
-            out["f"] = -sum(sp.diff(w, v, 2) for v in xs) + sp.Float(self.beta) * lap
+            out["f"] = -sum(sp.diff(w, v, 2) for v in xs) + sp.sympify(self.beta) * lap
+            out["beta"] = sp.sympify(self.beta)
             for a, v in enumerate(xs):
                 out[f"du{a}"] = sp.diff(u, v)
                 out[f"d2u{a}"] = sp.diff(u, v, 2)
@@ -154,6 +155,25 @@ def config_problem(name: str) -> Problem:
         eps = sp.Float(name.split("_eps")[1]) if "_eps" in name else sp.Float("1e-4")
         u = 256 * (x ** 2 + eps * (1 - sp.exp(-x / sp.sqrt(eps))) ** 2) * (x - 1) ** 2 * y ** 2 * (y - 1) ** 2
         return Problem(name, 2, eps, u, beta=1.0, navier=(1, 2, 3))
+    if name.startswith("peak3d") or name.startswith("sincos3d_var"):
+        # Examples 2 and 3 (Sec. 4.1, Tables 2-3): alpha = x^2 + y^2 + z^2 + 1,
+        # beta = x + y + z + 10, clamped on x = 0 and Navier on the other faces;
+        # "peak3d_q10_p0.2", "peak3d_q5_p1", "sincos3d_var_5_1_5", "sincos3d_var_25_5_25"
+        alpha = x ** 2 + y ** 2 + z ** 2 + 1
+        beta = x + y + z + 10
+        par = name.split("_")
+        if name.startswith("peak3d"):
+            q, p = sp.Rational(par[1][1:]), sp.Rational(par[2][1:])
+            u = (x ** 2 - x) * (y ** 2 - y) * (z ** 2 - z) * sp.exp(q * ((x - sp.Rational(1, 2)) ** 2 +
+                                                                         (y - sp.Rational(1, 2)) ** 2 + (z - p) ** 2))
+        else:
+            k1, k2, k3 = (int(v) for v in par[2:5])
+            u = sp.sin(k1 * x) * sp.cos(k2 * y) * sp.sin(k3 * z)
+        return Problem(name, 3, alpha, u, beta=beta, navier=(1, 2, 3, 4, 5))
+    if name == "varbeta2d":
+        # variable alpha and beta (beta/alpha not constant), one Navier face
+        return Problem(name, 2, 1 + x ** 2 + y ** 2, sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)),
+                       beta=5 + x + 2 * y, navier=(1,))
     if name == "navier2d":
         # variable coefficient, beta = 0, clamped on x- and y-, Navier on x+ and y+
         return Problem(name, 2, 1 + x ** 2 + y ** 2, sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)), navier=(1, 3))
@@ -397,7 +417,10 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
     out["v_edge"] = vE
     out["g_N"] = gN if backend == "numpy" else _to_t(gN, device)
     out["lapt_gD"] = lapt if backend == "numpy" else _to_t(lapt, device)
-    out["beta"] = float(prob.beta)
+    if isinstance(prob.beta, sp.Expr) and not prob.beta.is_number:
+        out["beta"] = full("beta")
+    else:
+        out["beta"] = float(prob.beta)
     out["navier"] = tuple(prob.navier)
     if prob.navier:
         out["g_L"] = gL if backend == "numpy" else _to_t(gL, device)

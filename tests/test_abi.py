@@ -86,3 +86,19 @@ def test_no_unresolved_library_symbols():
     import subprocess
     out = subprocess.run(["nm", "-D", "--undefined-only", ahoc.LIB_PATH], capture_output=True, text=True).stdout
     assert "ahoc" not in out, out
+
+
+def test_every_bdata_field_reaches_each_problem():
+    """ahoc_plan_create splits the batch's boundary-data arrays per problem:
+    every field of ahoc_bdata must be forwarded (a field missing there is
+    silently zero)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_2609_16478_b300", "csrc", "plan.cu")).read()
+    hdr = open(os.path.join(ROOT, "include", "ahoc.h")).read()
+    body = hdr[hdr.index("typedef struct {", hdr.index("Boundary data")):hdr.index("} ahoc_bdata;")]
+    fields = re.findall(r"const double\* (\w+);", body)
+    assert len(fields) >= 6
+    create = src[src.index("ahoc_status ahoc_plan_create("):]
+    create = create[:create.index("s = plan_load(")]
+    for f in fields:
+        assert "bb.%s = bd->%s" % (f, f) in create, f

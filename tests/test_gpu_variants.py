@@ -78,3 +78,53 @@ def test_example1_table1(prec):
             err = float((u.reshape(N + 1, N + 1) - d["u_exact"]).abs().max())
             assert abs(err / float(row[col]) - 1) < bar, (N, name, err, row[col], info["iters"])
             p.close()
+
+
+# --- variable beta / alpha: BiCGSTAB v-solves (FP64), constant-shift corrections (mixed) ---
+
+@pytest.mark.parametrize("name,N", [("varbeta2d", [64, 64]), ("sincos3d_var_5_1_5", [16, 16, 16]),
+                                    ("peak3d_q5_p1", [16, 16, 16])])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-9)])
+def test_variable_beta_matches_oracle(name, N, prec, tol):
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    p, U, info = _solve(d, prec)
+    assert _rel(U, sol.U) < tol, info
+    if prec == "fp64":
+        assert info["vsolve_iters"] > 0
+
+
+@pytest.mark.parametrize("name,N", [("varbeta2d", [8, 8]), ("sincos3d_var_5_1_5", [8, 8, 8])])
+def test_variable_beta_schur_columns(name, N):
+    d = inputs.sample(inputs.config_problem(name), N)
+    B = coupled.Blocks(coupled.assemble(d))
+    S = B.schur_dense()
+    p = ahoc.plan_for(d)
+    ng = p.ngamma
+    e = torch.zeros(ng, dtype=torch.float64, device="cuda")
+    Sg = np.empty((ng, ng))
+    for j in range(ng):
+        e.zero_()
+        e[j] = 1.0
+        Sg[:, j] = p.matvec(e).cpu().numpy()
+    assert _rel(Sg, S) < 1e-11
+    b = p.schur_rhs(torch.as_tensor(np.ascontiguousarray(d["f"]), dtype=torch.float64).reshape(-1).cuda())
+    assert _rel(b.cpu().numpy(), B.schur_rhs()) < 1e-11
+
+
+@pytest.mark.parametrize("prec,nmax", [("fp64", 256), ("mixed", 128)])
+def test_examples2_3_tables(prec, nmax):
+    """Tables 2-3 (Examples 2-3): the maximum error of U at 32^3 .. nmax^3
+    equals the printed values to their three digits."""
+    names = ["peak3d_q10_p0.2", "peak3d_q5_p1", "sincos3d_var_5_1_5", "sincos3d_var_25_5_25"]
+    for row in golden("varbeta3d_tables23.txt"):
+        N = int(row[0])
+        if N > nmax:
+            continue
+        for col, name in enumerate(names, start=1):
+            d = inputs.sample(inputs.config_problem(name), [N] * 3, backend="torch", device="cuda")
+            p = ahoc.plan_for(d, prec=prec, restart=100, max_iters=1000)
+            u, info = p.solve(d["f"].reshape(-1).contiguous(), tol=1e-12)
+            err = float((u.reshape(N + 1, N + 1, N + 1) - d["u_exact"]).abs().max())
+            assert abs(err / float(row[col]) - 1) < 0.006, (N, name, err, row[col], info["iters"])
+            p.close()

@@ -394,3 +394,33 @@ def test_navier_face_carries_the_data():
         al = d["alpha"].reshape(-1)[g.full_flat(P)]
         q = sol.Q[off[fid]:off[fid + 1]]
         assert np.allclose(q, al * d["g_L"][off[fid]:off[fid + 1]], rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,Ns,lo_rate", [("varbeta2d", [16, 32, 64], 3.6),
+                                             ("sincos3d_var_5_1_5", [8, 12, 16], 3.4)])
+def test_variable_beta_convergence_order(name, Ns, lo_rate):
+    """beta/alpha variable (Examples 2-3's coefficients in 3D): fourth order."""
+    prob = inputs.config_problem(name)
+    errs = []
+    for N in Ns:
+        d = inputs.sample(prob, [N] * prob.dim)
+        assert np.ndim(d["beta"]) > 0
+        sol = coupled.solve_direct(coupled.assemble(d), d)
+        errs.append(np.max(np.abs(sol.U - d["u_exact"])))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert min(rates) > lo_rate, rates
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not __import__("os").environ.get("AHOC_RUN_SLOW"),
+                    reason="about 2.5 minutes per case; set AHOC_RUN_SLOW=1")
+@pytest.mark.parametrize("col,name", [(1, "peak3d_q10_p0.2"), (2, "peak3d_q5_p1"), (3, "sincos3d_var_5_1_5"),
+                                      (4, "sincos3d_var_25_5_25")])
+def test_examples2_3_tables_n32(col, name):
+    """Tables 2-3 at 32^3: the oracle's error equals the printed value to its
+    three digits (variable beta/alpha, 3D Navier faces, clamped face)."""
+    row = golden("varbeta3d_tables23.txt")[0]
+    d = inputs.sample(inputs.config_problem(name), [32, 32, 32])
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    err = np.max(np.abs(sol.U - d["u_exact"]))
+    assert abs(err / float(row[col]) - 1) < 0.005, (err, row[col])
