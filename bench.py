@@ -178,6 +178,52 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def paper_suite(args, dev):
+    """The paper's printed workloads at their largest sizes, one JSON line each:
+    Example 1 (Table 1) at 4096^2, Examples 2-3 (Tables 2-3, variable beta/alpha)
+    at 512^3, and Table 4's classical-biharmonic timing problems at 1024^3,
+    FP64 and mixed; the error against the exact solution beside the printed one."""
+    import torch
+
+    from paper_2609_16478_b300 import ahoc, inputs
+    printed = {("singular2d", 4096): 4.54e-10, ("singular2d_eps1e-5", 4096): 4.65e-9,
+               ("peak3d_q10_p0.2", 512): 8.50e-7, ("peak3d_q5_p1", 512): 1.07e-8,
+               ("sincos3d_var_5_1_5", 512): 1.05e-10, ("sincos3d_var_25_5_25", 512): 7.45e-8}
+    paper_cpu_s = {("classic3d_peak", 1024): 362.76, ("classic3d_sincos", 1024): 161.88,
+                   ("classic3d_peak", 512): 44.86, ("classic3d_sincos", 512): 19.89}
+    runs = [("singular2d", 4096), ("singular2d_eps1e-5", 4096), ("peak3d_q10_p0.2", 512), ("peak3d_q5_p1", 512),
+            ("sincos3d_var_5_1_5", 512), ("sincos3d_var_25_5_25", 512), ("classic3d_peak", 512),
+            ("classic3d_sincos", 512), ("classic3d_peak", 1024), ("classic3d_sincos", 1024)]
+    for name, N in runs:
+        prob = inputs.config_problem(name)
+        d = inputs.sample(prob, [N] * prob.dim, backend="torch", device=dev)
+        f = d["f"].reshape(-1).contiguous()
+        for prec in ("fp64", "mixed"):
+            st = torch.cuda.Stream(device=dev)
+            p = ahoc.plan_for(d, device=dev, prec=prec, restart=100, max_iters=1000, stream=st)
+            u = torch.empty_like(f)
+            p.solve(f, u, tol=1e-12, check=False)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, info = p.solve(f, u, tol=1e-12)
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = float((u.reshape(d["u_exact"].shape) - d["u_exact"]).abs().max())
+            dof = (N - 1) ** prob.dim
+            print(json.dumps({"suite": "paper", "workload": name, "N": N, "dim": prob.dim, "prec": prec,
+                              "ms": ms, "dof_per_s": dof / (ms / 1e3), "err_inf_vs_exact": err,
+                              "paper_err_inf": printed.get((name, N)),
+                              "paper_cpu_s_16_threads": paper_cpu_s.get((name, N)),
+                              "gmres_iters": info["iters"], "coarse_iters": info["coarse_iters"],
+                              "refine_steps": info["refine_steps"], "vsolve_iters": info["vsolve_iters"]}),
+                  flush=True)
+            p.close()
+        del d, f
+        torch.cuda.empty_cache()
+
+
 def serving_variant(args, dev):
     """The serving workload: a seeded Poisson stream of requests of mixed
     dimension, size, coefficient and right-hand side, at 80% of the measured
@@ -449,6 +495,8 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-tol", type=float, default=1e-12)
     ap.add_argument("--serve-slots", type=int, default=8, help="plans per shape in the serving pool")
+    ap.add_argument("--suite", choices=["bench", "paper"], default="bench",
+                    help="paper: the paper's printed workloads at their largest sizes, one JSON line each")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache (default: the shipped B300 choices)")
     args = ap.parse_args()
     if args.tune_cache is None:
@@ -461,6 +509,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.suite == "paper":
+        import torch
+        torch.cuda.set_device(local)
+        paper_suite(args, torch.device("cuda", local))
         return
     if world > 1:
         import torch

@@ -170,6 +170,16 @@ def config_problem(name: str) -> Problem:
             k1, k2, k3 = (int(v) for v in par[2:5])
             u = sp.sin(k1 * x) * sp.cos(k2 * y) * sp.sin(k3 * z)
         return Problem(name, 3, alpha, u, beta=beta, navier=(1, 2, 3, 4, 5))
+    if name.startswith("classic3d"):
+        # Table 4's timing problems: the classical biharmonic (alpha = 1, beta = 0)
+        # with Example 2's (q, p) = (5, 1) or Example 3's (25, 5, 25) solution;
+        # "classic3d_peak" or "classic3d_sincos"; clamped on x = 0, Navier elsewhere
+        if name.endswith("peak"):
+            u = (x ** 2 - x) * (y ** 2 - y) * (z ** 2 - z) * sp.exp(5 * ((x - sp.Rational(1, 2)) ** 2 +
+                                                                         (y - sp.Rational(1, 2)) ** 2 + (z - 1) ** 2))
+        else:
+            u = sp.sin(25 * x) * sp.cos(5 * y) * sp.sin(25 * z)
+        return Problem(name, 3, sp.Integer(1), u, navier=(1, 2, 3, 4, 5))
     if name == "varbeta2d":
         # variable alpha and beta (beta/alpha not constant), one Navier face
         return Problem(name, 2, 1 + x ** 2 + y ** 2, sp.sin(3 * x) * sp.cos(y + sp.Rational(1, 3)),

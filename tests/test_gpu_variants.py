@@ -112,10 +112,11 @@ def test_variable_beta_schur_columns(name, N):
     assert _rel(b.cpu().numpy(), B.schur_rhs()) < 1e-11
 
 
-@pytest.mark.parametrize("prec,nmax", [("fp64", 256), ("mixed", 128)])
+@pytest.mark.parametrize("prec,nmax", [("fp64", 512), ("mixed", 128)])
 def test_examples2_3_tables(prec, nmax):
-    """Tables 2-3 (Examples 2-3): the maximum error of U at 32^3 .. nmax^3
-    equals the printed values to their three digits."""
+    """Tables 2-3 (Examples 2-3): the maximum error of U at 32^3 .. 256^3
+    equals the printed values to their three digits; at 512^3 (the paper's
+    GMRES stops at a tolerance proportional to h^3.5, Sec. 4.1) within 1%."""
     names = ["peak3d_q10_p0.2", "peak3d_q5_p1", "sincos3d_var_5_1_5", "sincos3d_var_25_5_25"]
     for row in golden("varbeta3d_tables23.txt"):
         N = int(row[0])
@@ -126,5 +127,5 @@ def test_examples2_3_tables(prec, nmax):
             p = ahoc.plan_for(d, prec=prec, restart=100, max_iters=1000)
             u, info = p.solve(d["f"].reshape(-1).contiguous(), tol=1e-12)
             err = float((u.reshape(N + 1, N + 1, N + 1) - d["u_exact"]).abs().max())
-            assert abs(err / float(row[col]) - 1) < 0.006, (N, name, err, row[col], info["iters"])
+            assert abs(err / float(row[col]) - 1) < (0.006 if N <= 256 else 0.01), (N, name, err, row[col], info["iters"])
             p.close()
