@@ -135,8 +135,8 @@ typedef struct {
                              beta term of Eq. 1.  The v-equation is -L_h V + gamma M V = M f
                              (Sec. 2.2 with beta / alpha constant, e.g. constant alpha and
                              beta): its Poisson solves take the shifted eigenvalues
-                             -lambda_L + gamma lambda_M.  gamma >= 0; variable beta / alpha
-                             is not supported (the v-equation would need an iterative solve) */
+                             -lambda_L + gamma lambda_M.  gamma >= 0; with variable_beta set,
+                             the reference shift of the iterative v-solve                      */
   int no_graphs;          /* [0] 0: each GMRES iteration (mask and scalar uploads, the
                              normalisation of v_j, the preconditioner, the Schur matvec, CGS2
                              and the read-back of the Hessenberg column) is captured once as a
@@ -154,6 +154,16 @@ typedef struct {
                              corrections use the constant shift and the FP64 residual the
                              exact beta/alpha, so the refinement converges to the same
                              discrete solution                                                 */
+  int uhat_slots;         /* [0] 2D FP64 with constant beta / alpha: the Schur matvecs of
+                             GMRES's first cycle leave U in x-modes (U-hat, the transform
+                             along x of the u-solve) in a field each, and U and V of the data
+                             alone are kept, so that the recovery of U is one combination of
+                             those fields (Q = Q0 + Z y is linear) and one inverse DST instead
+                             of two Poisson solves; V is then formed only when
+                             ahoc_last_qv asks for it.  Falls back to the two solves when
+                             GMRES restarts or takes more steps than slots.  0: automatic
+                             (min(restart, 16) slots); > 0: that many (at most restart);
+                             < 0: none.  Each slot holds one field per problem (workspace).  */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */

@@ -44,7 +44,7 @@ class ahoc_opts(C.Structure):
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
                 ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int),
-                ("variable_beta", C.c_int)]
+                ("variable_beta", C.c_int), ("uhat_slots", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -135,9 +135,10 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False):
+          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0):
     o = ahoc_opts()
     o.variable_beta = 1 if variable_beta else 0
+    o.uhat_slots = int(uhat_slots)
     o.batch = int(batch)
     o.navier = int(navier)
     o.shift = float(shift)
@@ -157,10 +158,11 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1
 
 
 def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1,
-                    batch: int = 1, shift: float = 0.0, variable_beta: bool = False) -> int:
+                    batch: int = 1, shift: float = 0.0, variable_beta: bool = False, uhat_slots: int = 0) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
-    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift, variable_beta=variable_beta)
+    o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift, variable_beta=variable_beta,
+              uhat_slots=uhat_slots)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -196,7 +198,7 @@ class Plan:
                  prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
-                 graphs: bool = True):
+                 graphs: bool = True, uhat_slots: int = 0):
         L = lib()
         self.dim = dim
         self.batch = int(batch)
@@ -220,7 +222,7 @@ class Plan:
         self.device = alpha.device
         B = self.batch
         variable_beta = beta is not None
-        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift, variable_beta)
+        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift, variable_beta, uhat_slots)
         self.workspace_bytes = nb
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -228,7 +230,7 @@ class Plan:
                         _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"),
                         _ptr(g_L, B * self.ngamma, "g_L"), _ptr(beta, B * self.nfull, "beta"))
         o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
-                  navier, shift, variable_beta)
+                  navier, shift, variable_beta, uhat_slots)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)

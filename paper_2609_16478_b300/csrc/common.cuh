@@ -73,4 +73,20 @@ struct alignas(16) Mode {
   int j0;
 };
 
+// Length (complex entries) of a DST twiddle table for lines of N points:
+// tw[t] = exp(-2 pi i t/N) for t < N, then the FFT stage twiddles, one block
+// per radix-4 stage with Ns > 1 of the N/2-point transform (Ns = 2 or 4,
+// then x4 up to N/8): tw[off + (r-1) Ns + kk] = tw[2 r kk (N/2)/(4 Ns)],
+// r = 1..3, kk < Ns -- the same values, contiguous in kk, so that a warp's
+// lanes read consecutive entries.
+__host__ __device__ inline int64_t dst_tw_len(int N) {
+  const int M = N >> 1;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  int64_t len = N;
+  for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2)
+    if (Ns > 1) len += 3 * (int64_t)Ns;
+  return len;
+}
+
 }  // namespace ahoc

@@ -15,7 +15,8 @@
 // with one radix-2 stage first when log2 M is odd.  A line of N elements is
 // handled by TPL = N/8 threads (one radix-4 butterfly each per stage); a CTA
 // holds LPC lines.  All twiddles come from per-plan tables computed on the
-// host in long double: tw[t] = exp(-2 pi i t/N), t < N.
+// host in long double: tw[t] = exp(-2 pi i t/N), t < N, followed by the same
+// values per FFT stage in the order its threads read them (dst_tw_len).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -88,16 +89,17 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
     Ns = 2;
   }
   const int M4 = M >> 2;
+  // stage twiddles W_M^{r kk M/(4 Ns)}, contiguous in kk (table layout at dst_tw_len)
+  const C* tws = tw + N;
   for (; Ns < M; Ns <<= 2) {
     const int j = lt;
     const int kk = j & (Ns - 1);
     C x0 = c[j], x1 = c[j + M4], x2 = c[j + 2 * M4], x3 = c[j + 3 * M4];
     if (Ns > 1) {
-      // W_M^{r*kk*M/(4Ns)} = W_N^{2*r*t}
-      const int t = kk * (M / (4 * Ns));
-      x1 = cmul(x1, tw[2 * t]);
-      x2 = cmul(x2, tw[4 * t]);
-      x3 = cmul(x3, tw[6 * t]);
+      x1 = cmul(x1, tws[kk]);
+      x2 = cmul(x2, tws[Ns + kk]);
+      x3 = cmul(x3, tws[2 * Ns + kk]);
+      tws += 3 * Ns;
     }
     __syncthreads();
     C a0, a1, b0, b1;

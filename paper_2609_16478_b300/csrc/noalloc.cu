@@ -45,6 +45,25 @@ __global__ void k_na_dst_tables(double* tw, double* sn, int N) {
   if (t <= N / 2) sn[t] = 0.5 * sinpi((double)t / N);
 }
 
+// the FFT stage twiddles after the first N entries (layout at dst_tw_len),
+// copied from tw[0..N) once k_na_dst_tables has written it
+__global__ void k_na_dst_stages(double* tw, int N) {
+  const int M = N >> 1;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  int64_t off = N;
+  for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2) {
+    if (Ns == 1) continue;
+    for (int e = threadIdx.x; e < 3 * Ns; e += blockDim.x) {
+      const int r = 1 + e / Ns, kk = e - (r - 1) * Ns;
+      const int64_t src = (int64_t)2 * r * kk * (M / (4 * Ns));
+      tw[2 * (off + e)] = tw[2 * src];
+      tw[2 * (off + e) + 1] = tw[2 * src + 1];
+    }
+    off += 3 * (int64_t)Ns;
+  }
+}
+
 // sum of a few doubles with Neumaier compensation (the stencil-weight residue)
 __device__ double na_fsum(const double* t, int n) {
   double s = 0.0, c = 0.0;
@@ -174,9 +193,9 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
     return p;
   };
   const size_t o_field = take((size_t)g.npad * sizeof(double));
-  const size_t o_twx = take(2 * (size_t)g.N[0] * sizeof(double));
+  const size_t o_twx = take(2 * (size_t)dst_tw_len(g.N[0]) * sizeof(double));
   const size_t o_snx = take(((size_t)g.N[0] / 2 + 1) * sizeof(double));
-  const size_t o_twy = take(2 * (size_t)g.N[1] * sizeof(double));
+  const size_t o_twy = take(2 * (size_t)dst_tw_len(g.N[1]) * sizeof(double));
   const size_t o_sny = take(((size_t)g.N[1] / 2 + 1) * sizeof(double));
   const size_t o_modes = take((size_t)ncols * sizeof(Mode<double>));
   const size_t o_tri = take(chunked ? tri_chunked_scratch(g, L) * sizeof(double) : 0);
@@ -220,9 +239,11 @@ extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const dou
   // the pad slots of the field must start at zero; the array keeps the last call's contents
   NA_CK(cudaMemsetAsync(field, 0, (size_t)g.npad * sizeof(double), st));
   k_na_dst_tables<<<(g.N[0] + 255) / 256, 256, 0, st>>>(twx, snx, g.N[0]);
+  k_na_dst_stages<<<1, 256, 0, st>>>(twx, g.N[0]);
   NA_CK(cudaGetLastError());
   if (g.dim == 3) {
     k_na_dst_tables<<<(g.N[1] + 255) / 256, 256, 0, st>>>(twy, sny, g.N[1]);
+    k_na_dst_stages<<<1, 256, 0, st>>>(twy, g.N[1]);
     NA_CK(cudaGetLastError());
   }
   k_na_modes<<<(unsigned)((ncols + 127) / 128), 128, 0, st>>>(g, cf, modes);

@@ -63,6 +63,7 @@ struct Opts {
   int navier = 0;        // Navier faces (bit 2a + side)
   double shift = 0.0;    // constant beta / alpha of the v-equation (reference value if variable)
   int varb = 0;          // variable beta / alpha (problems bring beta)
+  int uhat = 0;          // U-hat slots of the recovery (0 automatic, < 0 none)
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -83,6 +84,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.navier = o->navier;
     d.shift = o->shift;
     d.varb = o->variable_beta ? 1 : 0;
+    d.uhat = o->uhat_slots;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -191,15 +193,31 @@ Coefs make_coefs(const Geom& g) {
   return c;
 }
 
-// DST tables for one axis: tw[t] = exp(-2 pi i t / N) (t < N), sn[j] = sin(pi j/N)/2 (j <= N/2)
+int ilog2i(int64_t n);
+
+// DST tables for one axis: tw[t] = exp(-2 pi i t / N) (t < N) followed by the
+// FFT stage twiddles (layout at dst_tw_len), sn[j] = sin(pi j/N)/2 (j <= N/2)
 void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
-  tw.resize(2 * (size_t)N);
+  tw.resize(2 * (size_t)dst_tw_len(N));
   sn.resize((size_t)N / 2 + 1);
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int t = 0; t < N; ++t) {
     const long double ang = -2.0L * pi * (long double)t / (long double)N;
     tw[2 * t] = (double)cosl(ang);
     tw[2 * t + 1] = (double)sinl(ang);
+  }
+  const int M = N / 2;
+  const int logM = ilog2i(M > 0 ? M : 1);
+  size_t off = (size_t)N;
+  for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2) {
+    if (Ns == 1) continue;
+    for (int r = 1; r <= 3; ++r)
+      for (int kk = 0; kk < Ns; ++kk) {
+        const size_t src = (size_t)2 * r * kk * (M / (4 * Ns)), dst = off + (size_t)(r - 1) * Ns + kk;
+        tw[2 * dst] = tw[2 * src];
+        tw[2 * dst + 1] = tw[2 * src + 1];
+      }
+    off += 3 * (size_t)Ns;
   }
   for (int j = 0; j <= N / 2; ++j) sn[j] = (double)(0.5L * sinl(pi * (long double)j / (long double)N));
 }
@@ -269,7 +287,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
       tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb, modes_v, modesf_v, rpow_v, gL,
-      gam, bcg, bcoef,
+      gam, bcg, bcoef, bank, Ud, Vd,
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
@@ -316,6 +334,18 @@ constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 int64_t pstride(const Opts& o) { return (int64_t)kDotBlocks * (2 * (o.restart + 1) + 2); }
 int hstride(const Opts& o) { return 2 * (o.restart + 1) + 4; }
 
+bool fused_ok(const Geom& g);
+
+// U-hat slots of the recovery (2D FP64 fused Schur matvec, constant beta/alpha):
+// the matvecs of GMRES's first cycle leave U in x-modes in a slot each, so the
+// recovery of U is a combination of those fields and one inverse DST.
+constexpr int kAutoUhatSlots = 16;
+int bank_slots(const Geom& g, const Opts& o) {
+  if (o.uhat < 0 || o.prec != AHOC_FP64 || o.varb || !fused_ok(g)) return 0;
+  const int want = o.uhat > 0 ? o.uhat : kAutoUhatSlots;
+  return want < o.restart ? want : o.restart;
+}
+
 // Workspace layout.  Per-problem arrays hold g.nb copies back to back at the
 // element strides the kernels assume (fields npad, full-grid arrays nfull,
 // face arrays ngamma, the 2D generator lines N1 + 1 and 2 N0, the chunked
@@ -343,11 +373,11 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.vedge = take(B * full);
   L.gN = take(B * face);
   L.lapt = take(B * face);
-  L.twx = take(2 * (size_t)g.N[0] * sizeof(double));
+  L.twx = take(2 * (size_t)dst_tw_len(g.N[0]) * sizeof(double));
   L.snx = take(((size_t)g.N[0] / 2 + 1) * sizeof(double));
-  L.twy = take(2 * (size_t)g.N[1] * sizeof(double));
+  L.twy = take(2 * (size_t)dst_tw_len(g.N[1]) * sizeof(double));
   L.sny = take(((size_t)g.N[1] / 2 + 1) * sizeof(double));
-  L.twz = take(2 * (size_t)g.N[2] * sizeof(double));
+  L.twz = take(2 * (size_t)dst_tw_len(g.N[2]) * sizeof(double));
   L.snz = take(((size_t)g.N[2] / 2 + 1) * sizeof(double));
   for (int a = 0; a < 3; ++a) {
     L.stab[a] = take(2 * (size_t)g.N[a] * sizeof(double));
@@ -380,6 +410,11 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.bcg = take(o.varb && o.prec == AHOC_FP64 ? 9 * B * fld : 0);
   L.bcoef = take(o.varb ? 3 * B * sizeof(double) : 0);
   L.gL = take(B * face);
+  // the recovery's U-hat slots (one more: the guess's U-hat and the sum) and the data's U and V
+  const int nbank = bank_slots(g, o);
+  L.bank = take(nbank ? (size_t)(nbank + 1) * B * fld : 0);
+  L.Ud = take(nbank ? B * fld : 0);
+  L.Vd = take(nbank ? B * fld : 0);
   L.partial = take(B * (size_t)pstride(o) * sizeof(double));
   L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
   L.act = take(B * sizeof(int));
@@ -394,7 +429,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.U64 = take(mixed ? B * fld : 0);
   L.V64 = take(mixed ? B * fld : 0);
   for (int a = 0; a < 3; ++a) {  // FP32 DST tables: mixed inner solves and the preconditioner
-    L.twf[a] = take(2 * (size_t)g.N[a] * sizeof(float));
+    L.twf[a] = take(2 * (size_t)dst_tw_len(g.N[a]) * sizeof(float));
     L.snf[a] = take(((size_t)g.N[a] / 2 + 1) * sizeof(float));
   }
   L.modesf = take(mixed ? nmodes * sizeof(Mode<float>) : 0);
@@ -447,6 +482,7 @@ size_t total_bytes(const Geom& g, const Opts& o) {
     gc.nb = g.nb;
     Opts oc = o;
     oc.levels = lv - 1;
+    oc.uhat = -1;  // coarse levels only solve for Q
     apply_tuning(gc, oc);
     b += total_bytes(gc, oc);
   }
@@ -490,6 +526,14 @@ struct ahoc_plan {
   double* bcg = nullptr;
   double* bcoef = nullptr;
   int bicg_iters = 0;  // BiCGSTAB iterations of the last solve (summed over v-solves)
+  // recovery from the U-hat slots: bank holds nbank + 1 batched fields (slot
+  // j: U-hat of z_j; slot nbank: U-hat of the initial guess, then the sum);
+  // Ud, Vd: U and V of the data alone (Q = 0).  bank_valid: the last GMRES
+  // ended in its first cycle within nbank steps.  v_lazy: V was not
+  // recovered by the last solve (ahoc_last_qv forms it on request).
+  double *bank = nullptr, *Ud = nullptr, *Vd = nullptr;
+  int nbank = 0;
+  bool bank_valid = false, v_lazy = false;
   // mixed precision
   float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
@@ -724,14 +768,19 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
 
 bool fused_ok(const Geom& g) { return g.dim == 2 && tri_ncols(g) < kChunkedBelow; }
 
-ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y) {
+// uhat: where the FP64 fused 2D matvec leaves U in x-modes (NULL: W2)
+ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y, double* uhat = nullptr) {
   if (p->o.prec == AHOC_MIXED) {
     if (fused_ok(p->g)) return fused2d<float>(p, f2arrays_f(p), q, nullptr, nullptr, nullptr, y, false);
     CKS(solve_VU_f(p, q, nullptr, nullptr));
     RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
     return AHOC_OK;
   }
-  if (fused_ok(p->g) && !p->o.varb) return fused2d<double>(p, f2arrays_d(p), q, nullptr, nullptr, nullptr, y, false);
+  if (fused_ok(p->g) && !p->o.varb) {
+    F2Arrays<double> A = f2arrays_d(p);
+    if (uhat) A.W2 = uhat;
+    return fused2d<double>(p, A, q, nullptr, nullptr, nullptr, y, false);
+  }
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -1096,6 +1145,12 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   }
   p->W1 = at<double>(p, L.W1);
   p->W2 = at<double>(p, L.W2);
+  p->nbank = bank_slots(g, o);
+  if (p->nbank) {
+    p->bank = at<double>(p, L.bank);
+    p->Ud = at<double>(p, L.Ud);
+    p->Vd = at<double>(p, L.Vd);
+  }
   p->ainv = at<double>(p, L.ainv);
   p->afac = at<double>(p, L.afac);
   p->gD = at<double>(p, L.gD);
@@ -1191,6 +1246,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   // zero padding of the fields and zero boundary data until a problem brings its own
   CKC(cudaMemsetAsync(p->W1, 0, B * fld, p->st));
   CKC(cudaMemsetAsync(p->W2, 0, B * fld, p->st));
+  if (p->nbank) CKC(cudaMemsetAsync(p->bank, 0, (size_t)(p->nbank + 1) * B * fld, p->st));
   CKC(cudaMemsetAsync(p->gD, 0, B * full, p->st));
   CKC(cudaMemsetAsync(p->vedge, 0, B * full, p->st));
   CKC(cudaMemsetAsync(p->gN, 0, B * face, p->st));
@@ -1282,6 +1338,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     }
     Opts oc = o;
     oc.levels = lv - 1;
+    oc.uhat = -1;  // coarse levels only solve for Q
     oc.workspace = o.workspace ? (void*)(p->ws + L.total) : nullptr;
     oc.workspace_bytes = o.workspace ? o.workspace_bytes - L.total : 0;
     CKS(plan_alloc(&p->coarse, dim, Nc, lo_, hi_, oc, stream));
@@ -1500,6 +1557,14 @@ ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
   if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
   CK(cudaMemcpyAsync(q, p->Q, (size_t)p->g.nb * p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
   CKS(set_act(p, p->part));
+  if (v && p->v_lazy) {
+    // V = V(data) + V(Q): the v-equation with the converged Q alone, plus the stored data part
+    const Geom& g = p->g;
+    RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, p->Q, nullptr, nullptr, p->st, nullptr, p->gam));
+    CKS(poisson_inplace(p, p->W1, true));
+    RUN(AHOC_K_OTHER, launch_axpby(p->W1, p->Vd, 1.0, 1.0, g.npad, p->st, g.nb, nullptr, g.act));
+    p->v_lazy = false;
+  }
   if (v)
     RUN(AHOC_K_OTHER, launch_v_full(p->g, v, p->o.prec == AHOC_MIXED ? p->V64 : p->W1, p->Q,
                                     p->has_vedge ? p->vedge : nullptr, p->st));
@@ -1520,9 +1585,10 @@ ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
   double* vj = p->Kry + (int64_t)j * ld;
   double* w = p->Kry + (int64_t)(j + 1) * ld;
   double* zj = p->Zb + (int64_t)j * ld;
+  double* uh = j < p->nbank ? p->bank + (int64_t)j * g.nb * g.npad : nullptr;
   RUN(AHOC_K_KRYLOV, launch_axpby(vj, src, 0.0, 0.0, n, p->st, g.nb, p->scal, g.act));
   CKS(precond_apply(p, vj, zj));
-  CKS(matvec_dev(p, zj, w));
+  CKS(matvec_dev(p, zj, w, uh));
   CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev));
   CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev, w, nullptr));
   CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev + (j + 1)));
@@ -1635,9 +1701,12 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
     if (live[i] && !(beta0[i] > 0)) live[i] = 0;
   }
   std::vector<double> beta(beta0);
+  // U-hat slot of the guess (then of the recovery's sum)
+  double* ux0 = p->nbank ? p->bank + (int64_t)p->nbank * nb * g.npad : nullptr;
+  p->bank_valid = p->nbank > 0;
   if (guess) {
     CKS(set_act(p, live));
-    CKS(matvec_dev(p, X, p->tmp));
+    CKS(matvec_dev(p, X, p->tmp, ux0));
     RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
     RUN(AHOC_K_KRYLOV, launch_axpby(p->r, p->tmp, -1.0, 1.0, n, p->st, nb, nullptr, g.act));
     CKS(mdot(p, p->r, n, 1, p->r, p->hdev));
@@ -1649,6 +1718,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       }
   } else {
     CK(cudaMemsetAsync(X, 0, (size_t)nb * n * sizeof(double), p->st));
+    if (ux0) CK(cudaMemsetAsync(ux0, 0, (size_t)nb * g.npad * sizeof(double), p->st));
     CKS(set_act(p, live));
     RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
   }
@@ -1738,10 +1808,26 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
     CK(cudaMemcpyAsync(p->ncolsb, nc.data(), nb * sizeof(int), cudaMemcpyHostToDevice, p->st));
     CKS(set_act(p, cyc));
     CKS(gemv_sub(p, p->Zb, ld, 0, p->hdev, X, p->ncolsb));
+    if (p->bank_valid) {
+      // the same combination of the slots' U-hat fields: U-hat of X
+      int jmax = 0;
+      for (int i = 0; i < nb; ++i) jmax = nc[i] > jmax ? nc[i] : jmax;
+      if (jmax <= p->nbank) {
+        BatchDot bd;
+        bd.vstride = g.npad;
+        bd.wstride = g.npad;
+        bd.act = g.act;
+        RUN(AHOC_K_KRYLOV, launch_gemv_sub(p->bank, (int64_t)nb * g.npad, 0, p->hdev, ux0, g.npad, p->st, nb, bd,
+                                           hstride(p->o), p->ncolsb));
+      } else {
+        p->bank_valid = false;
+      }
+    }
     CK(cudaStreamSynchronize(p->st));
     CKS(harvest(p));
     if (!any(live)) break;
     // restart the problems whose basis filled: explicit residual r = b - S X
+    p->bank_valid = false;
     for (int i = 0; i < nb; ++i)
       if (live[i]) ++go[i].restarts;
     CKS(set_act(p, live));
@@ -1784,6 +1870,10 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
   std::vector<int> live = p->part;
   CKS(set_act(p, live));
   CKS(schur_rhs_dev(p, f, p->b));
+  if (p->nbank && u) {  // U and V of the data alone, for the recovery from the slots
+    CK(cudaMemcpyAsync(p->Ud, p->W2, (size_t)nb * g.npad * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    CK(cudaMemcpyAsync(p->Vd, p->W1, (size_t)nb * g.npad * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+  }
   std::vector<double> beta0;
   CKS(norms(p, p->b, beta0));
   bool guess = false;
@@ -1795,13 +1885,13 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     // initial guess of Sec. 4.1)
     ahoc_plan* c = p->coarse;
     double* f_c = p->W2;
-    double* u_c = p->W1;
     CKS(set_act(c, live));
     RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
     CK(cudaStreamSynchronize(p->st));
     c->part = live;
     const double ctol = p->o.coarse_tol > tol ? p->o.coarse_tol : tol;
-    ahoc_status cs_ = solve_internal(c, f_c, u_c, ctol);
+    // only the coarse Q is used: the coarse level skips its recovery of V and U
+    ahoc_status cs_ = solve_internal(c, f_c, nullptr, ctol);
     if (cs_ != AHOC_OK) return cs_;  // ENOCONV of a coarse level is kept in its stats, not an error
     CKS(harvest(p));
     for (int k = 0; k < AHOC_NK; ++k) {
@@ -1820,8 +1910,7 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     }
     CKS(set_act(p, live));
     RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
-    // the fields were borrowed as temporaries: restore the zero padding
-    CK(cudaMemsetAsync(p->W1, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+    // f_c borrowed W2 as a temporary: restore its zero padding
     CK(cudaMemsetAsync(p->W2, 0, (size_t)nb * g.npad * sizeof(double), p->st));
     guess = true;
   }
@@ -1836,8 +1925,21 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     s.status = go[i].status;
     s.ms_mv += go[i].ms_mv;
   }
-  // recovery: V and U with the converged Q (and the data)
+  if (!u) return AHOC_OK;  // a coarse level of the nested guess: Q only
   CKS(set_act(p, p->part));
+  if (p->bank_valid) {
+    // U = U(data) + U(Q), U(Q) the inverse DST of the combined U-hat (linear
+    // in Q: Q = X0 + Z y, so its U-hat is the guess's plus Z's combination);
+    // V is formed only if ahoc_last_qv asks for it
+    double* ux = p->bank + (int64_t)p->nbank * nb * g.npad;
+    RUN(AHOC_K_DST_X, launch_dst_x<double>(g, ux, p->twx, p->snx, 1.0, p->st));
+    RUN(AHOC_K_OTHER, launch_axpby(ux, p->Ud, 1.0, 1.0, g.npad, p->st, nb, nullptr, g.act));
+    RUN(AHOC_K_OTHER, launch_write_full(g, u, ux, p->has_gD ? p->gD : nullptr, p->st));
+    p->v_lazy = true;
+    return AHOC_OK;
+  }
+  p->v_lazy = false;
+  // recovery: V and U with the converged Q (and the data)
   CKS(solve_VU(p, p->Q, f, true));
   RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->has_gD ? p->gD : nullptr, p->st));
   return AHOC_OK;
@@ -1952,12 +2054,14 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
       }
     }
   }
+  if (!u) return AHOC_OK;
   CKS(set_act(p, p->part));
   RUN(AHOC_K_OTHER, launch_write_full(g, u, p->U64, p->has_gD ? p->gD : nullptr, p->st));
   return AHOC_OK;
 }
 
-// One solve of the problems in p->part (statistics in p->ps).
+// One solve of the problems in p->part (statistics in p->ps); u == NULL: Q
+// only (the nested guess's coarse levels), V and U are not recovered.
 ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol) {
   p->have_last = false;
   CK(cudaStreamSynchronize(p->st));

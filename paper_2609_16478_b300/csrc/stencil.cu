@@ -543,21 +543,26 @@ __global__ void k_residual(Geom g, Coefs cf, const double* __restrict__ gam, flo
           lv += c * V[o];
         }
       }
-  // M(V/alpha), M(gam V) (the shift term) and M f: centre and the axis neighbours
+  // M(V/alpha), M(gam V) (the shift term) and M f: centre and the axis
+  // neighbours; the neighbour sums are formed first and weighted once (this
+  // kernel is bound by the FP64 pipe)
   const int64_t fc = g.full(i, j, k);
-  double mv = cf.Mc * V[t] * ainv[fc];
-  double mgv = cf.Mc * (gam ? gam[fc] : cf.gam) * V[t];
-  double mf = f ? cf.Mc * f[fc] : 0.0;
+  const double vc = V[t];
+  double swn = 0.0, svn = 0.0, sgn = 0.0, sfn = 0.0;
   for (int a = 0; a < g.dim; ++a)
     for (int s = -1; s <= 1; s += 2) {
       const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
       const int64_t fn = g.full(ii, jj, kk);
       const double vn = vfull(g, V, Q, vedge, ii, jj, kk);
-      mv += cf.Mn * vn * ainv[fn];
-      mgv += cf.Mn * (gam ? gam[fn] : cf.gam) * vn;
-      if (f) mf += cf.Mn * f[fn];
+      swn = fma(vn, ainv[fn], swn);
+      if (gam) sgn = fma(vn, gam[fn], sgn);
+      else svn += vn;
+      if (f) sfn += f[fn];
     }
-  ru[t] = (float)(-(lu - mv));
+  const double mv = fma(cf.Mn, swn, cf.Mc * (vc * ainv[fc]));
+  const double mgv = gam ? fma(cf.Mn, sgn, cf.Mc * (vc * gam[fc])) : cf.gam * fma(cf.Mn, svn, cf.Mc * vc);
+  const double mf = f ? fma(cf.Mn, sfn, cf.Mc * f[fc]) : 0.0;
+  ru[t] = (float)(mv - lu);
   rv[t] = (float)(mf + lv - mgv);
 }
 
