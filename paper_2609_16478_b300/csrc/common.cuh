@@ -73,20 +73,30 @@ struct alignas(16) Mode {
   int j0;
 };
 
-// Length (complex entries) of a DST twiddle table for lines of N points:
-// tw[t] = exp(-2 pi i t/N) for t < N, then the FFT stage twiddles, one block
-// per radix-4 stage with Ns > 1 of the N/2-point transform (Ns = 2 or 4,
-// then x4 up to N/8): tw[off + (r-1) Ns + kk] = tw[2 r kk (N/2)/(4 Ns)],
-// r = 1..3, kk < Ns -- the same values, contiguous in kk, so that a warp's
-// lanes read consecutive entries.
+// DST twiddle table for lines of N points, in entries of two reals:
+//   [0, N)           tw[t] = exp(-2 pi i t/N)
+//   [N, N + N/2 + 1) pre-processing factors (sin(pi j/N)/2 + 1/4, sin(pi j/N)/2 - 1/4)
+//   then per radix-4 stage with Ns > 1 of the N/2-point FFT (Ns = 2 or 4,
+//   then x4 up to N/8): Ns entries (c, t) of w = W^kk, then Ns of w^2
+//   (W = exp(-2 pi i/(4 Ns))), contiguous in kk so a warp reads consecutive
+//   entries; then N/4 + 1 entries (c, t) of exp(-2 pi i k/N), k <= N/4, for the
+//   post-processing.
+// A factor zeta = exp(i theta) is held as (c, t) with zeta = c (1 + i t), or,
+// where the swap rule of dst_swap_* holds, zeta = i c (1 + i t); either way
+// |t| <= 1, and zeta q costs two FMAs plus a scaling that the butterfly's
+// additions absorb into FMAs.
+__host__ __device__ inline bool dst_swap_w1(int kk, int Ns) { return 2 * kk > Ns; }
+__host__ __device__ inline bool dst_swap_w2(int kk, int Ns) { return 4 * kk > Ns && 4 * kk < 3 * Ns; }
+__host__ __device__ inline bool dst_swap_post(int k, int N) { return 8 * k > N; }
+
 __host__ __device__ inline int64_t dst_tw_len(int N) {
   const int M = N >> 1;
   int logM = 0;
   while ((1 << logM) < M) ++logM;
-  int64_t len = N;
+  int64_t len = N + N / 2 + 1;
   for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2)
-    if (Ns > 1) len += 3 * (int64_t)Ns;
-  return len;
+    if (Ns > 1) len += 2 * (int64_t)Ns;
+  return len + M / 2 + 1;
 }
 
 }  // namespace ahoc

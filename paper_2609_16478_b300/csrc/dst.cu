@@ -37,6 +37,27 @@ __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
+// A factor zeta held as (c, t) (table layout at dst_tw_len): zeta q is c R,
+// R = rot(q + i t q), rot the identity or (when `swap`) multiplication by i.
+// The products c R enter the butterflies as FMAs: with
+//   Rx = swap ? T.y : T.x,  Ry = swap ? T.x : T.y,  cx = swap ? -c : c,
+// (c R).x = cx Rx and (c R).y = c Ry.  The selects and the sign flip are
+// integer operations, off the FP64 pipe.
+template <typename C>
+__device__ __forceinline__ C lf_rot(C q, decltype(C{}.x) t, bool swap) {
+  const auto tx = fmaT(-t, q.y, q.x), ty = fmaT(t, q.x, q.y);
+  C r;
+  r.x = swap ? ty : tx;
+  r.y = swap ? tx : ty;
+  return r;
+}
+__device__ __forceinline__ double negif(double x, bool f) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)f << 63));
+}
+__device__ __forceinline__ float negif(float x, bool f) {
+  return __int_as_float(__float_as_int(x) ^ ((int)f << 31));
+}
+
 // In-place DST-I of the LPC lines of this CTA.  Line l occupies s[l*LS .. l*LS+N)
 // with s[l*LS] == 0.  Every thread of the CTA must call this.  wsum: >= 32
 // elements of scratch for the cross-warp scan.
@@ -52,15 +73,14 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
   const int M = N >> 1;
   const int logM = logN - 1;
 
-  // 1. pre-processing, pairs (j, N-j)
+  // 1. pre-processing, pairs (j, N-j): z_j = (s_j + 1/4) x_j + (s_j - 1/4) x_{N-j}
+  //    and z_{N-j} the other way round, s_j = sin(pi j/N)/2 (tabulated sums)
+  const C* pm = tw + N;
   for (int j = lt + 1; j <= (N >> 1); j += TPL) {
-    T a = y[j], b = y[N - j];
-    T sum = a + b, dif = a - b;
-    T sj = sn[j];
-    T za = fmaT(sj, sum, (T)0.25 * dif);
-    T zb = fmaT(sj, sum, (T)-0.25 * dif);
-    y[j] = za;
-    if (j != (N >> 1)) y[N - j] = zb;
+    const T a = y[j], b = y[N - j];
+    const C f = pm[j];
+    y[j] = fmaT(f.x, a, f.y * b);
+    if (j != (N >> 1)) y[N - j] = fmaT(f.y, a, f.x * b);
   }
   __syncthreads();
 
@@ -89,30 +109,49 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
     Ns = 2;
   }
   const int M4 = M >> 2;
-  // stage twiddles W_M^{r kk M/(4 Ns)}, contiguous in kk (table layout at dst_tw_len)
-  const C* tws = tw + N;
+  // stage factors w = W^kk and w^2, W = exp(-2 pi i/(4 Ns)), contiguous in kk
+  const C* tws = tw + N + (N >> 1) + 1;
   for (; Ns < M; Ns <<= 2) {
     const int j = lt;
     const int kk = j & (Ns - 1);
-    C x0 = c[j], x1 = c[j + M4], x2 = c[j + 2 * M4], x3 = c[j + 3 * M4];
-    if (Ns > 1) {
-      x1 = cmul(x1, tws[kk]);
-      x2 = cmul(x2, tws[Ns + kk]);
-      x3 = cmul(x3, tws[2 * Ns + kk]);
-      tws += 3 * Ns;
-    }
-    __syncthreads();
-    C a0, a1, b0, b1;
-    a0.x = x0.x + x2.x; a0.y = x0.y + x2.y;
-    a1.x = x0.x - x2.x; a1.y = x0.y - x2.y;
-    b0.x = x1.x + x3.x; b0.y = x1.y + x3.y;
-    b1.x = x1.x - x3.x; b1.y = x1.y - x3.y;
+    const C x0 = c[j], x1 = c[j + M4], x2 = c[j + 2 * M4], x3 = c[j + 3 * M4];
     C y0, y1, y2, y3;
-    y0.x = a0.x + b0.x; y0.y = a0.y + b0.y;
-    y2.x = a0.x - b0.x; y2.y = a0.y - b0.y;
-    // -i * b1 = (b1.y, -b1.x)
-    y1.x = a1.x + b1.y; y1.y = a1.y - b1.x;
-    y3.x = a1.x - b1.y; y3.y = a1.y + b1.x;
+    if (Ns > 1) {
+      // y_r = sum_m (-i)^{rm} w^m x_m, factored as a = x0 +- w^2 x2,
+      // b = x1 +- w^2 x3, y = a +- w b (and a -+ i w b): every product with a
+      // factor becomes FMAs (24 FP64 operations instead of 28)
+      const C f1 = tws[kk], f2 = tws[Ns + kk];
+      const bool s1 = dst_swap_w1(kk, Ns), s2 = dst_swap_w2(kk, Ns);
+      const T c1 = f1.x, c1x = negif(f1.x, s1), c2 = f2.x, c2x = negif(f2.x, s2);
+      tws += 2 * Ns;
+      __syncthreads();
+      C r = lf_rot(x2, f2.y, s2);
+      C a0, a1, b0, b1;
+      a0.x = fmaT(c2x, r.x, x0.x); a0.y = fmaT(c2, r.y, x0.y);
+      a1.x = fmaT(-c2x, r.x, x0.x); a1.y = fmaT(-c2, r.y, x0.y);
+      r = lf_rot(x3, f2.y, s2);
+      b0.x = fmaT(c2x, r.x, x1.x); b0.y = fmaT(c2, r.y, x1.y);
+      b1.x = fmaT(-c2x, r.x, x1.x); b1.y = fmaT(-c2, r.y, x1.y);
+      r = lf_rot(b0, f1.y, s1);
+      y0.x = fmaT(c1x, r.x, a0.x); y0.y = fmaT(c1, r.y, a0.y);
+      y2.x = fmaT(-c1x, r.x, a0.x); y2.y = fmaT(-c1, r.y, a0.y);
+      // y1 = a1 - i w b1, y3 = a1 + i w b1; -i (c R) = (c R.y, -(cx R.x))
+      r = lf_rot(b1, f1.y, s1);
+      y1.x = fmaT(c1, r.y, a1.x); y1.y = fmaT(-c1x, r.x, a1.y);
+      y3.x = fmaT(-c1, r.y, a1.x); y3.y = fmaT(c1x, r.x, a1.y);
+    } else {
+      __syncthreads();
+      C a0, a1, b0, b1;
+      a0.x = x0.x + x2.x; a0.y = x0.y + x2.y;
+      a1.x = x0.x - x2.x; a1.y = x0.y - x2.y;
+      b0.x = x1.x + x3.x; b0.y = x1.y + x3.y;
+      b1.x = x1.x - x3.x; b1.y = x1.y - x3.y;
+      y0.x = a0.x + b0.x; y0.y = a0.y + b0.y;
+      y2.x = a0.x - b0.x; y2.y = a0.y - b0.y;
+      // -i * b1 = (b1.y, -b1.x)
+      y1.x = a1.x + b1.y; y1.y = a1.y - b1.x;
+      y3.x = a1.x - b1.y; y3.y = a1.y + b1.x;
+    }
     const int o = ((j - kk) << 2) + kk;
     c[o] = y0;
     c[o + Ns] = y1;
@@ -138,11 +177,15 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       E.x = A.x + B.x; E.y = A.y - B.y;
       D.x = A.x - B.x; D.y = A.y + B.y;
       O.x = D.y; O.y = -D.x;
-      C Tt = cmul(tw[k], O);
-      y[2 * k] = -(E.y + Tt.y);
-      y[2 * k + 1] = E.x + Tt.x;
-      y[2 * (M - k)] = E.y - Tt.y;
-      y[2 * (M - k) + 1] = E.x - Tt.x;
+      // Tt = exp(-2 pi i k/N) O = c R (factor table after the stages)
+      const C f = tws[k];
+      const bool sw = dst_swap_post(k, N);
+      const C r = lf_rot(O, f.y, sw);
+      const T cx = negif(f.x, sw);
+      y[2 * k] = fmaT(-f.x, r.y, -E.y);
+      y[2 * k + 1] = fmaT(cx, r.x, E.x);
+      y[2 * (M - k)] = fmaT(-f.x, r.y, E.y);
+      y[2 * (M - k) + 1] = fmaT(-cx, r.x, E.x);
     }
   }
   __syncthreads();
@@ -282,8 +325,10 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
     if (rb >= 0) {
       if (LOAD == 0) {
         v = *reinterpret_cast<const C*>(io.src + rb + pos);
-        v.x *= io.lscale;
-        v.y *= io.lscale;
+        if (io.lscale != (T)1) {  // uniform branch: no FP64 work for the common factor 1
+          v.x *= io.lscale;
+          v.y *= io.lscale;
+        }
         if (pos == 0) v.x = 0;
       } else {
         const int j = rj[l];
@@ -302,8 +347,10 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
     if (rb >= 0) {
       C v = *reinterpret_cast<const C*>(s + l * N + pos);
       if (STORE == 0) {
-        v.x *= scale;
-        v.y *= scale;
+        if (scale != (T)1) {
+          v.x *= scale;
+          v.y *= scale;
+        }
       } else {
         const int64_t f = fbase[l] + pos;
         v.x *= io.ainv[f];
@@ -346,7 +393,7 @@ __global__ void __launch_bounds__(512) k_dst_y(Geom g, T* __restrict__ a, const 
     const int c = e % LPC;
     const int j = e / LPC;
     const int i = i0 + c;
-    if (i < g.n0) a[g.pad(i, j, k)] = (j > 0) ? s[c * LS + j] * scale : (T)0;
+    if (i < g.n0) a[g.pad(i, j, k)] = (j > 0) ? (scale != (T)1 ? s[c * LS + j] * scale : s[c * LS + j]) : (T)0;
   }
 }
 

@@ -45,23 +45,37 @@ __global__ void k_na_dst_tables(double* tw, double* sn, int N) {
   if (t <= N / 2) sn[t] = 0.5 * sinpi((double)t / N);
 }
 
-// the FFT stage twiddles after the first N entries (layout at dst_tw_len),
-// copied from tw[0..N) once k_na_dst_tables has written it
+// (c, t) with exp(i pi x) = c (1 + i t), or = i c (1 + i t) when swap
+__device__ void na_factor(double x, bool swap, double* out) {
+  double sn, c;
+  sincospi(x, &sn, &c);
+  out[0] = swap ? sn : c;
+  out[1] = swap ? -c / sn : sn / c;
+}
+
+// the entries after the first N of a DST table (layout at dst_tw_len)
 __global__ void k_na_dst_stages(double* tw, int N) {
   const int M = N >> 1;
   int logM = 0;
   while ((1 << logM) < M) ++logM;
   int64_t off = N;
+  for (int j = threadIdx.x; j <= N / 2; j += blockDim.x) {
+    const double h = 0.5 * sinpi((double)j / N);
+    tw[2 * (off + j)] = h + 0.25;
+    tw[2 * (off + j) + 1] = h - 0.25;
+  }
+  off += N / 2 + 1;
   for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2) {
     if (Ns == 1) continue;
-    for (int e = threadIdx.x; e < 3 * Ns; e += blockDim.x) {
-      const int r = 1 + e / Ns, kk = e - (r - 1) * Ns;
-      const int64_t src = (int64_t)2 * r * kk * (M / (4 * Ns));
-      tw[2 * (off + e)] = tw[2 * src];
-      tw[2 * (off + e) + 1] = tw[2 * src + 1];
+    for (int kk = threadIdx.x; kk < Ns; kk += blockDim.x) {
+      const double x = -(double)kk / (2.0 * Ns);
+      na_factor(x, dst_swap_w1(kk, Ns), tw + 2 * (off + kk));
+      na_factor(2 * x, dst_swap_w2(kk, Ns), tw + 2 * (off + Ns + kk));
     }
-    off += 3 * (int64_t)Ns;
+    off += 2 * (int64_t)Ns;
   }
+  for (int k = threadIdx.x; k <= M / 2; k += blockDim.x)
+    na_factor(-2.0 * k / N, dst_swap_post(k, N), tw + 2 * (off + k));
 }
 
 // sum of a few doubles with Neumaier compensation (the stencil-weight residue)

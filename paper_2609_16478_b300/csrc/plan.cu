@@ -195,10 +195,16 @@ Coefs make_coefs(const Geom& g) {
 
 int ilog2i(int64_t n);
 
-// DST tables for one axis: tw[t] = exp(-2 pi i t / N) (t < N) followed by the
-// FFT stage twiddles (layout at dst_tw_len), sn[j] = sin(pi j/N)/2 (j <= N/2)
+// (c, t) with exp(i theta) = c (1 + i t), or = i c (1 + i t) when swap
+void dst_factor(long double theta, bool swap, double* out) {
+  const long double c = cosl(theta), sn = sinl(theta);
+  out[0] = (double)(swap ? sn : c);
+  out[1] = (double)(swap ? -c / sn : sn / c);
+}
+
+// DST tables for one axis (layout at dst_tw_len); sn[j] = sin(pi j/N)/2 (j <= N/2)
 void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
-  tw.resize(2 * (size_t)dst_tw_len(N));
+  tw.assign(2 * (size_t)dst_tw_len(N), 0.0);
   sn.resize((size_t)N / 2 + 1);
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int t = 0; t < N; ++t) {
@@ -206,19 +212,26 @@ void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
     tw[2 * t] = (double)cosl(ang);
     tw[2 * t + 1] = (double)sinl(ang);
   }
+  size_t off = (size_t)N;
+  for (int j = 0; j <= N / 2; ++j) {
+    const long double h = 0.5L * sinl(pi * (long double)j / (long double)N);
+    tw[2 * (off + j)] = (double)(h + 0.25L);
+    tw[2 * (off + j) + 1] = (double)(h - 0.25L);
+  }
+  off += (size_t)N / 2 + 1;
   const int M = N / 2;
   const int logM = ilog2i(M > 0 ? M : 1);
-  size_t off = (size_t)N;
   for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2) {
     if (Ns == 1) continue;
-    for (int r = 1; r <= 3; ++r)
-      for (int kk = 0; kk < Ns; ++kk) {
-        const size_t src = (size_t)2 * r * kk * (M / (4 * Ns)), dst = off + (size_t)(r - 1) * Ns + kk;
-        tw[2 * dst] = tw[2 * src];
-        tw[2 * dst + 1] = tw[2 * src + 1];
-      }
-    off += 3 * (size_t)Ns;
+    for (int kk = 0; kk < Ns; ++kk) {
+      const long double th = -pi * (long double)kk / (2.0L * Ns);  // W^kk, W = exp(-2 pi i/(4 Ns))
+      dst_factor(th, dst_swap_w1(kk, Ns), &tw[2 * (off + kk)]);
+      dst_factor(2 * th, dst_swap_w2(kk, Ns), &tw[2 * (off + Ns + kk)]);
+    }
+    off += 2 * (size_t)Ns;
   }
+  for (int k = 0; k <= M / 2; ++k)
+    dst_factor(-2.0L * pi * (long double)k / (long double)N, dst_swap_post(k, N), &tw[2 * (off + k)]);
   for (int j = 0; j <= N / 2; ++j) sn[j] = (double)(0.5L * sinl(pi * (long double)j / (long double)N));
 }
 

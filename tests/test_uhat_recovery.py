@@ -33,9 +33,9 @@ def _solve(data, N, **kw):
 def test_slots_match_two_solves(name, N, levels):
     prob = inputs.config_problem(name)
     data = inputs.sample(prob, [N, N], backend="torch", device="cuda")
-    ua, qa, va, ia = _solve(data, N, levels=levels, restart=100)
+    ua, qa, va, ia = _solve(data, N, levels=levels, restart=100, uhat_slots=64)
     ub, qb, vb, ib = _solve(data, N, levels=levels, restart=100, uhat_slots=-1)
-    assert ia["iters"] == ib["iters"] and ia["iters"] <= 16
+    assert ia["iters"] == ib["iters"] and ia["iters"] <= 64
     # the slot path replaces four DSTs of the recovery by one
     assert ib["kernel_launches"]["dst_x"] - ia["kernel_launches"]["dst_x"] == 3
     assert torch.equal(qa, qb)
