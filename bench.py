@@ -405,13 +405,15 @@ def run_ours(args, rank, world, local):
             "peak_source": "nominal B300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
             # DRAM bytes per launch of k_dst_x<double,1,0> (forward transform with the fused M load, the
             # kernel's most frequent form in GMRES) from the ncu capture summarised in
-            # profiles/k_dst_x_fp64_2d4096.md: 134.6 MB read + 93.0 MB written
-            "traffic": 227.5e6, "avg_launch_ms": avg_ms, "launches": kn_top["dst_x"],
+            # profiles/k_dst_x_fp64_2d4096.md: 134.5 MB read + 94.5 MB written
+            "traffic": 229.0e6, "avg_launch_ms": avg_ms, "launches": kn_top["dst_x"],
             "algorithmic_bytes_per_launch": 16 * N * (N - 1), "flops_per_launch": flops,
             "hbm_achieved_GBs": 16 * N * (N - 1) / (avg_ms / 1e3) / 1e9,
             "hbm_peak_GBs": _peaks().get("hbm_gbs"),
             "share_of_step": kms["dst_x"] / sum(kms.values()), "top_kernel_by_time": top,
-            "fp64_instr_note": "FFT mix is ~1.2 flops per FP64 instruction; ncu pipe utilisation in profiles/"}
+            "fp64_instr_note": "FP64 pipe 90-92% busy under ncu (profiles/); the FFT's additions cannot all be "
+                               "FMAs, so flops per FP64 operation stay below 2",
+            "fp64_probe_ops_per_s": 0.463e12}
     # the same workload through the mixed-precision path (FP32 inner solves, FP64 refinement)
     variants = {}
     if not args.no_mixed:
