@@ -43,7 +43,9 @@ def _peaks():
 
 
 def dst_flops_per_line(N: int) -> float:
-    """FP64 flops one DST-I line of the x-kernel executes (FMA = 2 flops).
+    """The algorithmic flop count of one DST-I line (N/2-point complex FFT
+    with pre- and post-processing), fixed independently of how a kernel fuses
+    the operations into FMAs: a complex product counts as 6 flops.
 
     pre-processing 8 per pair (N/2 pairs); radix-2 stage 4 per butterfly;
     radix-4 stage 34 per butterfly (16 without twiddles in the first stage);
