@@ -97,6 +97,14 @@ template <typename T>
 cudaError_t launch_tri_chunked(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
                                const double* rpow, double* scratch, int L, cudaStream_t st);
 size_t tri_chunked_scratch(const Geom& g, int L);
+// FP64 chunked solve in two passes over the field with exact tables (tri.cu):
+// tab holds tri2_table_size() doubles from tri2_table_fill (roots r[m] in
+// long double, mode order of the Mode tables); G (2D) generates the
+// v-equation right-hand side, added to the field when `add`
+size_t tri2_table_size(const Geom& g, int L);
+void tri2_table_fill(const Geom& g, int L, const long double* r, double* out);
+cudaError_t launch_tri2(const Geom& g, double* a, const Mode<double>* modes, const double* tab, double* scratch,
+                        int L, cudaStream_t st, const VGen2D<double>* G = nullptr, bool add = false);
 
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st);

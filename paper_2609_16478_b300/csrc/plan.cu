@@ -242,7 +242,8 @@ template <> constexpr long double pow_floor<float>() { return -36.0L; }
 
 // gam: shift of the operator, L_h - gam M (0: L_h itself)
 template <typename T>
-ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out, double gam = 0.0) {
+ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out, double gam = 0.0,
+                       std::vector<long double>* roots = nullptr) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int nx = g.N[0] - 1;
   const int ny = (g.dim == 3) ? g.N[1] - 1 : 1;
@@ -252,6 +253,7 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out
   if (g.dim == 3) scale *= 2.0L / g.N[1];
   auto L = [&](int dx, int dy, int dz) { return (long double)cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)]; };
   out.resize((size_t)nx * ny);
+  if (roots) roots->assign((size_t)nx * ny, 0.0L);
   for (int ky = 1; ky <= ny; ++ky) {
     const long double cy = (g.dim == 3) ? cosl(pi * ky / g.N[1]) : 0.0L;
     for (int kx = 1; kx <= nx; ++kx) {
@@ -269,6 +271,7 @@ ahoc_status mode_table(const Geom& g, const Coefs& cf, std::vector<Mode<T>>& out
       const long double gam = -b / a;
       if (!(fabsl(gam) < 0.5L)) return fail(AHOC_EUNSUPPORTED, "tridiagonal factor not diagonally dominant (mesh aspect ratio)");
       const long double r = 2 * gam / (1 + sqrtl(1 - 4 * gam * gam));
+      if (roots) (*roots)[(size_t)(ky - 1) * nx + (kx - 1)] = r;
       const long double sigma = a / (1 + r * r);
       Mode<T> m;
       m.r = (T)r;
@@ -304,7 +307,7 @@ struct Layout {
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
-      afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, total;
+      afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, tri2, tri2_v, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -339,6 +342,9 @@ int64_t tri_ncols(const Geom& g) { return (int64_t)(g.N[0] - 1) * (g.dim == 3 ? 
 bool chunked_for(const Geom& g, ahoc_precision prec) {
   return prec == AHOC_MIXED || tri_ncols(g) < kChunkedBelow;
 }
+// FP64 solves take the chunked form (two passes, tables of tri2_table_fill)
+// below kChunkedBelow columns, in either precision of the plan
+bool tri2_for(const Geom& g) { return tri_ncols(g) < kChunkedBelow; }
 
 constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 
@@ -418,6 +424,8 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.qa = take(B * face);
   L.rpow = take(chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
   L.rpow_v = take(shifted && chunked_for(g, o.prec) ? tri_powers_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.tri2 = take(tri2_for(g) ? tri2_table_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
+  L.tri2_v = take(shifted && tri2_for(g) ? tri2_table_size(g, tri_chunk_len(g)) * sizeof(double) : 0);
   // variable beta/alpha: gam = beta/alpha per problem; the BiCGSTAB v-solve's 9 fields (FP64 path)
   L.gam = take(o.varb ? B * full : 0);
   L.bcg = take(o.varb && o.prec == AHOC_FP64 ? 9 * B * fld : 0);
@@ -553,6 +561,7 @@ struct ahoc_plan {
   double *U64 = nullptr, *V64 = nullptr, *Rq = nullptr, *dQ = nullptr, *b2 = nullptr;
   double* Zb = nullptr;  // flexible GMRES: the preconditioned directions z_j = P^-1 v_j
   double *afinv = nullptr, *qa = nullptr, *rpow = nullptr;
+  double *tri2 = nullptr, *tri2_v = nullptr;  // tables of the FP64 chunked solve (U and shifted V operators)
   float *ainvf = nullptr, *rxmf = nullptr, *rxpf = nullptr, *qyf = nullptr, *qaf = nullptr, *R2f = nullptr,
         *tauf = nullptr, *skf = nullptr, *ckf = nullptr;
   Mode<float>* modesf = nullptr;
@@ -652,11 +661,10 @@ ahoc_status harvest(ahoc_plan* p) {
 ahoc_status poisson_inplace(ahoc_plan* p, double* W, bool vsolve = false) {
   const Geom& g = p->g;
   const Mode<double>* md = vsolve ? p->modes_v : p->modes;
-  const double* rp = vsolve ? p->rpow_v : p->rpow;
   RUN(AHOC_K_DST_X, launch_dst_x<double>(g, W, p->twx, p->snx, 1.0, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
-  if (tri_ncols(g) < kChunkedBelow)
-    RUNN(AHOC_K_TRI, 5, launch_tri_chunked<double>(g, W, md, md, rp, p->tri, tri_chunk_len(g), p->st));
+  if (tri2_for(g))
+    RUNN(AHOC_K_TRI, 4, launch_tri2(g, W, md, vsolve ? p->tri2_v : p->tri2, p->tri, tri_chunk_len(g), p->st));
   else
     RUN(AHOC_K_TRI, launch_tri<double>(g, W, md, p->st));
   if (g.dim == 3) RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, W, p->twy, p->sny, 1.0, p->st));
@@ -733,6 +741,23 @@ F2Arrays<float> f2arrays_f(ahoc_plan* p) {
                          p->rxmf, p->rxpf, p->qyf, p->qaf, p->R2f};
 }
 
+// The chunked tridiagonal solve of a fused 2D pass in precision T: FP64 in two
+// passes with the plan's tables (4 kernels), FP32 in three with FP64 carries
+// (5 kernels); vsolve selects the (shifted) V operator, G a generated
+// right-hand side (added to the field when `add`).
+cudaError_t tri_fused(ahoc_plan* p, double* W, const Mode<double>* mT, bool vsolve, const VGen2D<double>* G,
+                      bool add, int L) {
+  return launch_tri2(p->g, W, mT, vsolve ? p->tri2_v : p->tri2, p->tri, L, p->st, G, add);
+}
+cudaError_t tri_fused(ahoc_plan* p, float* W, const Mode<float>* mT, bool vsolve, const VGen2D<float>* G, bool add,
+                      int L) {
+  const Mode<double>* md = vsolve ? p->modes_v : p->modes;
+  const double* rp = vsolve ? p->rpow_v : p->rpow;
+  if (G) return launch_tri_chunked_gen<float>(p->g, W, mT, md, rp, p->tri, L, *G, p->st, add);
+  return launch_tri_chunked<float>(p->g, W, mT, md, rp, p->tri, L, p->st);
+}
+template <typename T> constexpr int tri_kernels() { return sizeof(T) == 8 ? 4 : 5; }
+
 template <typename T>
 ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T* srcv, const T* srcu,
                     const double* srcq, double* y, bool recover) {
@@ -750,14 +775,9 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
   // V-hat: L_h V = -r_v - L_bdry(q) in x-modes
   if (srcv) {
     RUN(AHOC_K_DST_X, launch_dst_x_from<T>(g, A.W1, srcv, -1.0, A.tw, A.sn, p->st));
-    if (q)
-      RUNN(AHOC_K_TRI, 5,
-           launch_tri_chunked_gen<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, G, p->st, true));
-    else
-      RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, p->st));
+    RUNN(AHOC_K_TRI, tri_kernels<T>(), tri_fused(p, A.W1, A.modes_v, true, q ? &G : nullptr, true, L));
   } else {
-    RUNN(AHOC_K_TRI, 5,
-         launch_tri_chunked_gen<T>(g, A.W1, A.modes_v, p->modes_v, p->rpow_v, p->tri, L, G, p->st, false));
+    RUNN(AHOC_K_TRI, tri_kernels<T>(), tri_fused(p, A.W1, A.modes_v, true, &G, false, L));
   }
   // U-hat: L_h U = M(V/alpha) + face terms + r_u, by one forward DST of the fused right-hand side
   if (!recover) {
@@ -767,7 +787,7 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
     RUN(AHOC_K_DST_X, launch_dst_x<T>(g, A.W1, A.tw, A.sn, (T)1, p->st));
     RUN(AHOC_K_DST_X, launch_dst_x_mload<T>(g, A.W2, A.W1, qa, (T)cf.Mc, (T)cf.Mn, A.tw, A.sn, p->st, srcu, A.ainv));
   }
-  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<T>(g, A.W2, A.modes, p->modes, p->rpow, p->tri, L, p->st));
+  RUNN(AHOC_K_TRI, tri_kernels<T>(), tri_fused(p, A.W2, A.modes, false, nullptr, false, L));
   if (recover) {
     RUN(AHOC_K_DST_X, launch_dst_x<T>(g, A.W2, A.tw, A.sn, (T)1, p->st));
     return AHOC_OK;
@@ -1128,8 +1148,9 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   cf.gam = o.shift;
   const bool shifted = o.shift != 0.0;
   std::vector<Mode<double>> modes, modes_v;
-  CKS(mode_table<double>(g, cf, modes));
-  if (shifted) CKS(mode_table<double>(g, cf, modes_v, o.shift));
+  std::vector<long double> roots, roots_v;
+  CKS(mode_table<double>(g, cf, modes, 0.0, &roots));
+  if (shifted) CKS(mode_table<double>(g, cf, modes_v, o.shift, &roots_v));
   std::vector<Mode<float>> modesf, modesf_v;
   if (o.prec == AHOC_MIXED) CKS(mode_table<float>(g, cf, modesf));
   if (o.prec == AHOC_MIXED && shifted) CKS(mode_table<float>(g, cf, modesf_v, o.shift));
@@ -1207,6 +1228,10 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->qa = at<double>(p, L.qa);
   p->rpow = at<double>(p, L.rpow);
   p->rpow_v = shifted ? at<double>(p, L.rpow_v) : p->rpow;
+  if (tri2_for(g)) {
+    p->tri2 = at<double>(p, L.tri2);
+    p->tri2_v = shifted ? at<double>(p, L.tri2_v) : p->tri2;
+  }
   p->partial = at<double>(p, L.partial);
   p->hdev = at<double>(p, L.hdev);
   p->act = at<int>(p, L.act);
@@ -1325,6 +1350,18 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     }
     CKC(cudaMemcpyAsync(p->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
     CKC(cudaStreamSynchronize(p->st));
+  }
+  if (tri2_for(g)) {
+    const int L2 = tri_chunk_len(g);
+    std::vector<double> t2(tri2_table_size(g, L2));
+    tri2_table_fill(g, L2, roots.data(), t2.data());
+    CKC(cudaMemcpyAsync(p->tri2, t2.data(), t2.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CKC(cudaStreamSynchronize(p->st));
+    if (shifted) {
+      tri2_table_fill(g, L2, roots_v.data(), t2.data());
+      CKC(cudaMemcpyAsync(p->tri2_v, t2.data(), t2.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+      CKC(cudaStreamSynchronize(p->st));
+    }
   }
   if (chunked_for(g, o.prec)) CKC(launch_tri_powers(g, p->modes, p->rpow, tri_chunk_len(g), p->st));
   if (chunked_for(g, o.prec) && shifted)

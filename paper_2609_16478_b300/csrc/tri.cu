@@ -17,6 +17,9 @@
 //
 // One thread owns one mode column; a warp covers 32 adjacent x-modes, so
 // every row access is a coalesced 32-element segment.
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -357,6 +360,261 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 chunked form in two passes over the field.  Per chunk of len rows from
+// zero carries: the forward recurrence wl and the backward recurrence pl of
+// wl (3 FP64 operations per row, pl stored in place).  With the forward carry
+// cf = w_{s0-1} and the backward carry cb = p_{e0+1},
+//   w_{s0+q} = wl_q + cf r^(q+1),
+//   p_{s0+q} = pl_q + cf G_q + cb r^(len-q),   G_q = sum_{q'=q}^{len-1} r^(2q'-q+1),
+//   u_{s0+q} = p_{s0+q} + C (r^(s0+q) - r^(2N-s0-q))
+//            = pl_q + cf G_q + X R_q + Y P_q,
+// R_q = r^(len-1-q), P_q = r^q, X = cb r - C r^(2N-e0), Y = C r^(s0): three
+// FMAs per row.  G, R, P, r^L and the chunk powers come from a table built
+// from the exact root in long double (tri2_table_size).  Within a chunk the
+// recurrences multiply by the rounded r directly: over len <= 32 rows its
+// representation error stays below 32 ulp.
+// ---------------------------------------------------------------------------
+struct Tri2Off {
+  int64_t Gf, Rf, Gl, Rl, P, rL, rlast, rp1, rp2, total;
+};
+__host__ __device__ inline Tri2Off tri2_offsets(int64_t ncols, int C, int L) {
+  Tri2Off o;
+  const int64_t blk = (int64_t)L * ncols;
+  o.Gf = 0;
+  o.Rf = blk;
+  o.Gl = 2 * blk;
+  o.Rl = 3 * blk;
+  o.P = 4 * blk;
+  o.rL = 5 * blk;
+  o.rlast = o.rL + ncols;
+  o.rp1 = o.rlast + ncols;
+  o.rp2 = o.rp1 + (int64_t)C * ncols;
+  o.total = o.rp2 + (int64_t)C * ncols;
+  return o;
+}
+
+size_t tri2_table_size(const Geom& g, int L) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  return (size_t)tri2_offsets(ncols, C, L).total;  // doubles
+}
+
+void tri2_table_fill(const Geom& g, int L, const long double* r, double* out) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int Nt = (g.dim == 3) ? g.N[2] : g.N[1];
+  const int nt = Nt - 1;
+  const int C = (nt + L - 1) / L;
+  const int lastlen = nt - (C - 1) * L;
+  const Tri2Off o = tri2_offsets(ncols, C, L);
+  std::vector<long double> pw(2 * L + 2);
+  for (int64_t m = 0; m < ncols; ++m) {
+    const long double rm = r[m];
+    pw[0] = 1.0L;
+    for (int k = 1; k < (int)pw.size(); ++k) pw[k] = pw[k - 1] * rm;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int len = pass ? lastlen : L;
+      const int64_t oG = pass ? o.Gl : o.Gf, oR = pass ? o.Rl : o.Rf;
+      for (int q = 0; q < L; ++q) {
+        long double G = 0.0L, R = 0.0L;
+        if (q < len) {
+          for (int qq = len - 1; qq >= q; --qq) G += pw[2 * qq - q + 1];
+          R = pw[len - 1 - q];
+        }
+        out[oG + (int64_t)q * ncols + m] = (double)G;
+        out[oR + (int64_t)q * ncols + m] = (double)R;
+      }
+    }
+    for (int q = 0; q < L; ++q) out[o.P + (int64_t)q * ncols + m] = (double)pw[q];
+    out[o.rL + m] = (double)pw[L];
+    out[o.rlast + m] = (double)pw[lastlen];
+    // r^(s0) = r^(1 + cL), ascending (shrinking); r^(2 Nt - e0), descending in c (shrinking)
+    long double a = rm;
+    for (int c = 0; c < C; ++c) {
+      out[o.rp1 + (int64_t)c * ncols + m] = (double)a;
+      a *= pw[L];
+    }
+    long double b = powl(rm, (long double)(2 * Nt - nt));  // chunk C-1 ends at e0 = nt
+    for (int c = C - 1; c >= 0; --c) {
+      out[o.rp2 + (int64_t)c * ncols + m] = (double)b;
+      b *= (c == C - 1) ? pw[lastlen] : pw[L];
+    }
+  }
+}
+
+template <int L, int GEN>
+__global__ void __launch_bounds__(128) k_tri2_t1(Geom g, double* __restrict__ a,
+                                                 const Mode<double>* __restrict__ modes, double* __restrict__ E,
+                                                 double* __restrict__ B, VGen2D<double> G) {
+  if (g.skip(blockIdx.y)) return;
+  const TriShape sh = tri_shape(g, L);
+  a += (int64_t)blockIdx.y * g.npad;
+  E += (int64_t)blockIdx.y * tri_sstride(sh);
+  B += (int64_t)blockIdx.y * tri_sstride(sh);
+  vgen_at(G, g, blockIdx.y);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int len = min(L, sh.nt - s0 + 1);
+  double* col = a + col_base(g, m);
+  const double r = modes[m].r, s = modes[m].s;
+  double d[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    d[q] = (q < len) ? rhs_elem<double, GEN>(col, G, (int)m + 1, s0 + q, sh) : 0.0;
+  double w = 0.0;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) {
+      w = fma(r, w, s * d[q]);
+      d[q] = w;
+    }
+  E[(int64_t)c * sh.ncols + m] = w;
+  double pl = 0.0;
+#pragma unroll
+  for (int q = L - 1; q >= 0; --q)
+    if (q < len) {
+      pl = fma(r, pl, d[q]);
+      d[q] = pl;
+    }
+  B[(int64_t)c * sh.ncols + m] = pl;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+}
+
+// forward carries cf_c = w_{s0(c)-1}
+__global__ void k_tri2_t1b(Geom g, const double* __restrict__ tab, const double* __restrict__ E,
+                           double* __restrict__ carry, int L) {
+  if (g.skip(blockIdx.y)) return;
+  const TriShape sh = tri_shape(g, L);
+  E += (int64_t)blockIdx.y * tri_sstride(sh);
+  carry += (int64_t)blockIdx.y * tri_sstride(sh);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= sh.ncols) return;
+  const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
+  const double rL = tab[o.rL + m];
+  double cy = 0.0;
+  for (int c = 0; c < sh.C; ++c) {
+    carry[(int64_t)c * sh.ncols + m] = cy;
+    cy = fma(rL, cy, E[(int64_t)c * sh.ncols + m]);
+  }
+}
+
+// backward carries cb_c = p_{e0(c)+1} and C = kapC p_1
+__global__ void k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ tab,
+                           const double* __restrict__ B, const double* __restrict__ carry,
+                           double* __restrict__ bcarry, double* __restrict__ Cc, int L) {
+  if (g.skip(blockIdx.y)) return;
+  const TriShape sh = tri_shape(g, L);
+  B += (int64_t)blockIdx.y * tri_sstride(sh);
+  carry += (int64_t)blockIdx.y * tri_sstride(sh);
+  bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
+  Cc += (int64_t)blockIdx.y * tri_sstride(sh);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= sh.ncols) return;
+  const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
+  const double rL = tab[o.rL + m], rlast = tab[o.rlast + m];
+  const double G0 = tab[o.Gf + m], G0l = tab[o.Gl + m];
+  double bc = 0.0;
+  for (int c = sh.C - 1; c >= 0; --c) {
+    const int64_t i = (int64_t)c * sh.ncols + m;
+    bcarry[i] = bc;
+    const bool last = (c == sh.C - 1);
+    bc = fma(last ? rlast : rL, bc, fma(carry[i], last ? G0l : G0, B[i]));  // p at the chunk start
+  }
+  Cc[m] = modes[m].kapC * bc;
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) k_tri2_t3(Geom g, double* __restrict__ a,
+                                                 const Mode<double>* __restrict__ modes,
+                                                 const double* __restrict__ tab, const double* __restrict__ carry,
+                                                 const double* __restrict__ bcarry, const double* __restrict__ Cc) {
+  if (g.skip(blockIdx.y)) return;
+  const TriShape sh = tri_shape(g, L);
+  a += (int64_t)blockIdx.y * g.npad;
+  carry += (int64_t)blockIdx.y * tri_sstride(sh);
+  bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
+  Cc += (int64_t)blockIdx.y * tri_sstride(sh);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sh.ncols * sh.C) return;
+  const int64_t m = t % sh.ncols;
+  const int c = (int)(t / sh.ncols);
+  const int s0 = 1 + c * L;
+  const int len = min(L, sh.nt - s0 + 1);
+  double* col = a + col_base(g, m);
+  const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
+  const bool last = (c == sh.C - 1);
+  const double* Gt = tab + (last ? o.Gl : o.Gf) + m;
+  const double* Rt = tab + (last ? o.Rl : o.Rf) + m;
+  const double* Pt = tab + o.P + m;
+  const int64_t i = (int64_t)c * sh.ncols + m;
+  const double cf = carry[i], Cm = Cc[m];
+  const double X = fma(bcarry[i], modes[m].r, -Cm * tab[o.rp2 + i]);
+  const double Y = Cm * tab[o.rp1 + i];
+  double d[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : 0.0;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) {
+      const int64_t k = (int64_t)q * sh.ncols;
+      double u = fma(cf, Gt[k], d[q]);
+      u = fma(X, Rt[k], u);
+      d[q] = fma(Y, Pt[k], u);
+    }
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+}
+
+template <int L, int GEN>
+static cudaError_t tri2_L(const Geom& g, double* a, const Mode<double>* modes, const double* tab, double* scratch,
+                          const VGen2D<double>& G, cudaStream_t st) {
+  const int nx = g.N[0] - 1;
+  const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
+  const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
+  const int C = (nt + L - 1) / L;
+  double* E = scratch;
+  double* carry = E + (int64_t)C * ncols;
+  double* B = carry + (int64_t)C * ncols;
+  double* bcarry = B + (int64_t)C * ncols;
+  double* Cc = bcarry + (int64_t)C * ncols;
+  const int64_t work = ncols * C;
+  const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
+  const dim3 cb((unsigned)((ncols + 127) / 128), (unsigned)g.nb);
+  k_tri2_t1<L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, B, G);
+  k_tri2_t1b<<<cb, 128, 0, st>>>(g, tab, E, carry, L);
+  k_tri2_t2b<<<cb, 128, 0, st>>>(g, modes, tab, B, carry, bcarry, Cc, L);
+  k_tri2_t3<L><<<gb, 128, 0, st>>>(g, a, modes, tab, carry, bcarry, Cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri2(const Geom& g, double* a, const Mode<double>* modes, const double* tab, double* scratch,
+                        int L, cudaStream_t st, const VGen2D<double>* G, bool add) {
+  if (G && g.dim != 2) return cudaErrorInvalidValue;
+  const VGen2D<double> Gz{};
+  const VGen2D<double>& Gv = G ? *G : Gz;
+  const int gen = G ? (add ? 2 : 1) : 0;
+#define AHOC_TRI2(LL)                                                  \
+  if (L == LL) {                                                       \
+    if (gen == 0) return tri2_L<LL, 0>(g, a, modes, tab, scratch, Gv, st); \
+    if (gen == 1) return tri2_L<LL, 1>(g, a, modes, tab, scratch, Gv, st); \
+    return tri2_L<LL, 2>(g, a, modes, tab, scratch, Gv, st);           \
+  }
+  AHOC_TRI2(32)
+  AHOC_TRI2(16)
+  AHOC_TRI2(8)
+#undef AHOC_TRI2
+  return cudaErrorInvalidValue;
 }
 
 size_t tri_chunked_scratch(const Geom& g, int L) {
