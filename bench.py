@@ -479,6 +479,7 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "kernel_ms_per_step_finest_level": {k: v / args.steps for k, v in kms_top.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
         "variants": variants,
