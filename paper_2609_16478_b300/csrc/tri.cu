@@ -365,32 +365,40 @@ __global__ void __launch_bounds__(128) k_tri_t3(Geom g, T* __restrict__ a, const
 // ---------------------------------------------------------------------------
 // FP64 chunked form in two passes over the field.  Per chunk of len rows from
 // zero carries: the forward recurrence wl and the backward recurrence pl of
-// wl (3 FP64 operations per row, pl stored in place).  With the forward carry
-// cf = w_{s0-1} and the backward carry cb = p_{e0+1},
+// wl (pl stored in place).  With the forward carry cf = w_{s0-1} and the
+// backward carry cb = p_{e0+1},
 //   w_{s0+q} = wl_q + cf r^(q+1),
 //   p_{s0+q} = pl_q + cf G_q + cb r^(len-q),   G_q = sum_{q'=q}^{len-1} r^(2q'-q+1),
-//   u_{s0+q} = p_{s0+q} + C (r^(s0+q) - r^(2N-s0-q))
-//            = pl_q + cf G_q + X R_q + Y P_q,
-// R_q = r^(len-1-q), P_q = r^q, X = cb r - C r^(2N-e0), Y = C r^(s0): three
-// FMAs per row.  G, R, P, r^L and the chunk powers come from a table built
-// from the exact root in long double (tri2_table_size).  Within a chunk the
-// recurrences multiply by the rounded r directly: over len <= 32 rows its
-// representation error stays below 32 ulp.
+//   u_{s0+q} = p_{s0+q} + C (r^(s0+q) - r^(2N-s0-q)).
+// With R_q = r^(len-1-q), P_q = r^q and G_q = (r P_q - r^(len+2) R_q)/(1 - r^2),
+//   u_{s0+q} = pl_q + X R_q + Y P_q,
+//   X = cb r - C r^(2N-e0) - cf r^(len+2)/(1-r^2),   Y = C r^(s0) + cf r/(1-r^2),
+// two FMAs per row.  (For r near 1 the two cf terms are each about
+// 1/(1 - r^2) times cf G_q and cancel: at most ~log10(1/((len+1)(1-r)))
+// digits of that term, about 1.3 at N = 4096.)  R, P, the per-mode factors
+// and the chunk powers come from a table built from the exact root in long
+// double (tri2_table_size).  Within a chunk the recurrences multiply by the
+// rounded r directly: over len <= 32 rows its representation error stays
+// below 32 ulp.  The carry passes run one thread per column with their loads
+// issued in batches of 8 chunks.
 // ---------------------------------------------------------------------------
 struct Tri2Off {
-  int64_t Gf, Rf, Gl, Rl, P, rL, rlast, rp1, rp2, total;
+  int64_t Rf, Rl, P, rL, rlast, G0f, G0l, K1, K2f, K2l, rp1, rp2, total;
 };
 __host__ __device__ inline Tri2Off tri2_offsets(int64_t ncols, int C, int L) {
   Tri2Off o;
   const int64_t blk = (int64_t)L * ncols;
-  o.Gf = 0;
-  o.Rf = blk;
-  o.Gl = 2 * blk;
-  o.Rl = 3 * blk;
-  o.P = 4 * blk;
-  o.rL = 5 * blk;
+  o.Rf = 0;
+  o.Rl = blk;
+  o.P = 2 * blk;
+  o.rL = 3 * blk;
   o.rlast = o.rL + ncols;
-  o.rp1 = o.rlast + ncols;
+  o.G0f = o.rlast + ncols;
+  o.G0l = o.G0f + ncols;
+  o.K1 = o.G0l + ncols;
+  o.K2f = o.K1 + ncols;
+  o.K2l = o.K2f + ncols;
+  o.rp1 = o.K2l + ncols;
   o.rp2 = o.rp1 + (int64_t)C * ncols;
   o.total = o.rp2 + (int64_t)C * ncols;
   return o;
@@ -412,27 +420,27 @@ void tri2_table_fill(const Geom& g, int L, const long double* r, double* out) {
   const int C = (nt + L - 1) / L;
   const int lastlen = nt - (C - 1) * L;
   const Tri2Off o = tri2_offsets(ncols, C, L);
-  std::vector<long double> pw(2 * L + 2);
+  std::vector<long double> pw(2 * L + 3);
   for (int64_t m = 0; m < ncols; ++m) {
     const long double rm = r[m];
     pw[0] = 1.0L;
     for (int k = 1; k < (int)pw.size(); ++k) pw[k] = pw[k - 1] * rm;
-    for (int pass = 0; pass < 2; ++pass) {
-      const int len = pass ? lastlen : L;
-      const int64_t oG = pass ? o.Gl : o.Gf, oR = pass ? o.Rl : o.Rf;
-      for (int q = 0; q < L; ++q) {
-        long double G = 0.0L, R = 0.0L;
-        if (q < len) {
-          for (int qq = len - 1; qq >= q; --qq) G += pw[2 * qq - q + 1];
-          R = pw[len - 1 - q];
-        }
-        out[oG + (int64_t)q * ncols + m] = (double)G;
-        out[oR + (int64_t)q * ncols + m] = (double)R;
-      }
+    for (int q = 0; q < L; ++q) {
+      out[o.Rf + (int64_t)q * ncols + m] = (double)pw[L - 1 - q];
+      out[o.Rl + (int64_t)q * ncols + m] = q < lastlen ? (double)pw[lastlen - 1 - q] : 0.0;
+      out[o.P + (int64_t)q * ncols + m] = (double)pw[q];
     }
-    for (int q = 0; q < L; ++q) out[o.P + (int64_t)q * ncols + m] = (double)pw[q];
+    long double g0 = 0.0L, g0l = 0.0L;  // G_0 = sum_{q'<len} r^(2q'+1)
+    for (int qq = 0; qq < L; ++qq) g0 += pw[2 * qq + 1];
+    for (int qq = 0; qq < lastlen; ++qq) g0l += pw[2 * qq + 1];
+    const long double inv = 1.0L / (1.0L - rm * rm);
     out[o.rL + m] = (double)pw[L];
     out[o.rlast + m] = (double)pw[lastlen];
+    out[o.G0f + m] = (double)g0;
+    out[o.G0l + m] = (double)g0l;
+    out[o.K1 + m] = (double)(rm * inv);
+    out[o.K2f + m] = (double)(pw[L + 2] * inv);
+    out[o.K2l + m] = (double)(pw[lastlen + 2] * inv);
     // r^(s0) = r^(1 + cL), ascending (shrinking); r^(2 Nt - e0), descending in c (shrinking)
     long double a = rm;
     for (int c = 0; c < C; ++c) {
@@ -447,6 +455,9 @@ void tri2_table_fill(const Geom& g, int L, const long double* r, double* out) {
   }
 }
 
+// Pass 1: local recurrences of a chunk.  GEN 1/2: the generated v-equation
+// right-hand side s sk (rxm_j +- rxp_j) (VGen2D) replaces / is added to the
+// field; its face rows (j = 1, N1 - 1) are corrected once outside the row loop.
 template <int L, int GEN>
 __global__ void __launch_bounds__(128) k_tri2_t1(Geom g, double* __restrict__ a,
                                                  const Mode<double>* __restrict__ modes, double* __restrict__ E,
@@ -465,15 +476,36 @@ __global__ void __launch_bounds__(128) k_tri2_t1(Geom g, double* __restrict__ a,
   const int len = min(L, sh.nt - s0 + 1);
   double* col = a + col_base(g, m);
   const double r = modes[m].r, s = modes[m].s;
-  double d[L];
+  double a1 = 0.0, a2 = 0.0;
+  if (GEN) {
+    const int k = (int)m + 1;
+    a1 = s * G.sk[k];
+    a2 = (k & 1) ? a1 : -a1;
+  }
+  double d[L];  // s times the right-hand side
 #pragma unroll
-  for (int q = 0; q < L; ++q)
-    d[q] = (q < len) ? rhs_elem<double, GEN>(col, G, (int)m + 1, s0 + q, sh) : 0.0;
+  for (int q = 0; q < L; ++q) {
+    double v = 0.0;
+    if (q < len) {
+      const int j = s0 + q;
+      if (GEN) v = fma(a1, G.rxm[j], a2 * G.rxp[j]);
+      if (GEN != 1) v = GEN ? fma(s, col[(int64_t)j * sh.stride], v) : s * col[(int64_t)j * sh.stride];
+    }
+    d[q] = v;
+  }
+  if (GEN && (s0 == 1 || s0 + len - 1 == sh.Nt - 1)) {
+    const int k = (int)m + 1;
+    const double bk = s * (G.Ly + 2.0 * G.ck[k] * G.Lxy);
+    if (s0 == 1) d[0] -= bk * G.qhm[k - 1];
+#pragma unroll
+    for (int q = 0; q < L; ++q)
+      if (q == len - 1 && s0 + q == sh.Nt - 1) d[q] -= bk * G.qhp[k - 1];
+  }
   double w = 0.0;
 #pragma unroll
   for (int q = 0; q < L; ++q)
     if (q < len) {
-      w = fma(r, w, s * d[q]);
+      w = fma(r, w, d[q]);
       d[q] = w;
     }
   E[(int64_t)c * sh.ncols + m] = w;
@@ -490,9 +522,13 @@ __global__ void __launch_bounds__(128) k_tri2_t1(Geom g, double* __restrict__ a,
     if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
 }
 
+constexpr int kCarryThreads = 32;  // one thread per column; small CTAs spread the columns over the SMs
+constexpr int kCarryBatch = 8;
+
 // forward carries cf_c = w_{s0(c)-1}
-__global__ void k_tri2_t1b(Geom g, const double* __restrict__ tab, const double* __restrict__ E,
-                           double* __restrict__ carry, int L) {
+__global__ void __launch_bounds__(kCarryThreads) k_tri2_t1b(Geom g, const double* __restrict__ tab,
+                                                            const double* __restrict__ E,
+                                                            double* __restrict__ carry, int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   E += (int64_t)blockIdx.y * tri_sstride(sh);
@@ -502,16 +538,30 @@ __global__ void k_tri2_t1b(Geom g, const double* __restrict__ tab, const double*
   const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
   const double rL = tab[o.rL + m];
   double cy = 0.0;
-  for (int c = 0; c < sh.C; ++c) {
+  int c = 0;
+  for (; c + kCarryBatch <= sh.C; c += kCarryBatch) {
+    double e[kCarryBatch];
+#pragma unroll
+    for (int q = 0; q < kCarryBatch; ++q) e[q] = E[(int64_t)(c + q) * sh.ncols + m];
+#pragma unroll
+    for (int q = 0; q < kCarryBatch; ++q) {
+      carry[(int64_t)(c + q) * sh.ncols + m] = cy;
+      cy = fma(rL, cy, e[q]);
+    }
+  }
+  for (; c < sh.C; ++c) {
     carry[(int64_t)c * sh.ncols + m] = cy;
     cy = fma(rL, cy, E[(int64_t)c * sh.ncols + m]);
   }
 }
 
 // backward carries cb_c = p_{e0(c)+1} and C = kapC p_1
-__global__ void k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ tab,
-                           const double* __restrict__ B, const double* __restrict__ carry,
-                           double* __restrict__ bcarry, double* __restrict__ Cc, int L) {
+__global__ void __launch_bounds__(kCarryThreads) k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes,
+                                                            const double* __restrict__ tab,
+                                                            const double* __restrict__ B,
+                                                            const double* __restrict__ carry,
+                                                            double* __restrict__ bcarry, double* __restrict__ Cc,
+                                                            int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   B += (int64_t)blockIdx.y * tri_sstride(sh);
@@ -521,16 +571,32 @@ __global__ void k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes, const
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= sh.ncols) return;
   const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
-  const double rL = tab[o.rL + m], rlast = tab[o.rlast + m];
-  const double G0 = tab[o.Gf + m], G0l = tab[o.Gl + m];
-  double bc = 0.0;
-  for (int c = sh.C - 1; c >= 0; --c) {
-    const int64_t i = (int64_t)c * sh.ncols + m;
-    bcarry[i] = bc;
-    const bool last = (c == sh.C - 1);
-    bc = fma(last ? rlast : rL, bc, fma(carry[i], last ? G0l : G0, B[i]));  // p at the chunk start
+  const double rL = tab[o.rL + m], G0 = tab[o.G0f + m];
+  // the last (possibly shorter) chunk, then the full ones in batches
+  int c = sh.C - 1;
+  int64_t i = (int64_t)c * sh.ncols + m;
+  bcarry[i] = 0.0;
+  double bc = fma(carry[i], tab[o.G0l + m], B[i]);  // p at the chunk start
+  --c;
+  for (; c - kCarryBatch + 1 >= 0; c -= kCarryBatch) {
+    double h[kCarryBatch];
+#pragma unroll
+    for (int q = 0; q < kCarryBatch; ++q) {
+      const int64_t k = (int64_t)(c - q) * sh.ncols + m;
+      h[q] = fma(carry[k], G0, B[k]);
+    }
+#pragma unroll
+    for (int q = 0; q < kCarryBatch; ++q) {
+      bcarry[(int64_t)(c - q) * sh.ncols + m] = bc;
+      bc = fma(rL, bc, h[q]);
+    }
   }
-  Cc[m] = modes[m].kapC * bc;
+  for (; c >= 0; --c) {
+    i = (int64_t)c * sh.ncols + m;
+    bcarry[i] = bc;
+    bc = fma(rL, bc, fma(carry[i], G0, B[i]));
+  }
+  Cc[m] = modes[m].kapC * bc;  // bc = p_1
 }
 
 template <int L>
@@ -553,13 +619,12 @@ __global__ void __launch_bounds__(128) k_tri2_t3(Geom g, double* __restrict__ a,
   double* col = a + col_base(g, m);
   const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
   const bool last = (c == sh.C - 1);
-  const double* Gt = tab + (last ? o.Gl : o.Gf) + m;
   const double* Rt = tab + (last ? o.Rl : o.Rf) + m;
   const double* Pt = tab + o.P + m;
   const int64_t i = (int64_t)c * sh.ncols + m;
   const double cf = carry[i], Cm = Cc[m];
-  const double X = fma(bcarry[i], modes[m].r, -Cm * tab[o.rp2 + i]);
-  const double Y = Cm * tab[o.rp1 + i];
+  const double X = fma(-cf, tab[(last ? o.K2l : o.K2f) + m], fma(bcarry[i], modes[m].r, -Cm * tab[o.rp2 + i]));
+  const double Y = fma(cf, tab[o.K1 + m], Cm * tab[o.rp1 + i]);
   double d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : 0.0;
@@ -567,9 +632,7 @@ __global__ void __launch_bounds__(128) k_tri2_t3(Geom g, double* __restrict__ a,
   for (int q = 0; q < L; ++q)
     if (q < len) {
       const int64_t k = (int64_t)q * sh.ncols;
-      double u = fma(cf, Gt[k], d[q]);
-      u = fma(X, Rt[k], u);
-      d[q] = fma(Y, Pt[k], u);
+      d[q] = fma(Y, Pt[k], fma(X, Rt[k], d[q]));
     }
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -590,10 +653,10 @@ static cudaError_t tri2_L(const Geom& g, double* a, const Mode<double>* modes, c
   double* Cc = bcarry + (int64_t)C * ncols;
   const int64_t work = ncols * C;
   const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
-  const dim3 cb((unsigned)((ncols + 127) / 128), (unsigned)g.nb);
+  const dim3 cb((unsigned)((ncols + kCarryThreads - 1) / kCarryThreads), (unsigned)g.nb);
   k_tri2_t1<L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, B, G);
-  k_tri2_t1b<<<cb, 128, 0, st>>>(g, tab, E, carry, L);
-  k_tri2_t2b<<<cb, 128, 0, st>>>(g, modes, tab, B, carry, bcarry, Cc, L);
+  k_tri2_t1b<<<cb, kCarryThreads, 0, st>>>(g, tab, E, carry, L);
+  k_tri2_t2b<<<cb, kCarryThreads, 0, st>>>(g, modes, tab, B, carry, bcarry, Cc, L);
   k_tri2_t3<L><<<gb, 128, 0, st>>>(g, a, modes, tab, carry, bcarry, Cc);
   return cudaGetLastError();
 }
