@@ -236,9 +236,11 @@ void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
 }
 
 // Per-mode factors of the tridiagonal solve along the last axis (tri.cu).
-// log10 of the smallest power of r the sequential kernel may scale back up
-template <typename T> constexpr long double pow_floor() { return -290.0L; }
-template <> constexpr long double pow_floor<float>() { return -36.0L; }
+// log10 of the smallest power of r that the one-thread-per-column kernel keeps
+// in the boundary-correction terms (K r^j and r^(j-1) w_j in P): below it they
+// are under the rounding of the solution (K is at most a few times |w|)
+template <typename T> constexpr long double pow_floor() { return -18.0L; }
+template <> constexpr long double pow_floor<float>() { return -9.0L; }
 
 // gam: shift of the operator, L_h - gam M (0: L_h itself)
 template <typename T>

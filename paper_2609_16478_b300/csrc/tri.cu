@@ -12,7 +12,8 @@
 //     u_j = r u_{j+1} + w_j + K r^j,  u_N = 0,   K = kap * P,
 // where kap = -r (1 - r^2) / (1 - r^{2N}) makes u_0 = 0 exactly.  No
 // division is done on the device.  K r^j is run downward from j0 (the last
-// index where |r|^j is representable) by multiplying with 1/r.  scale folds in
+// index where |r|^j is above 1e-18 in FP64, 1e-9 in FP32) by multiplying
+// with 1/r.  scale folds in
 // the (2/N)^(d-1) of the inverse DST-I.
 //
 // One thread owns one mode column; a warp covers 32 adjacent x-modes, so
@@ -29,6 +30,11 @@ namespace ahoc {
 __device__ __forceinline__ double rmul(double q1, double x) { return fma(-q1, x, x); }
 __device__ __forceinline__ float rmul(float q1, float x) { return fmaf(-q1, x, x); }
 
+// The terms that carry the boundary correction -- r^(j-1) w_j in P and K r^j --
+// fall below the rounding of the solution beyond j0 (Mode::j0: |r|^j0 ~ 1e-18
+// in FP64), so each recurrence runs in two phases: rows up to the warp's
+// largest j0 with the correction terms (4 operations per row), the rest
+// without them (2 per row).  The split is uniform across the warp.
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes) {
   if (g.skip(blockIdx.y)) return;
@@ -44,21 +50,30 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   T* col = a + ix + g.n0 * (int64_t)iy;
   const Mode<T> md = modes[m];
   const int nt = Nt - 1;
+  const int jw = __reduce_max_sync(__activemask(), md.j0);  // uniform phase boundary
   constexpr int B = 8;
 
-  // forward recurrence and the accumulated first value P
+  // forward recurrence and the accumulated first value P = sum r^(j-1) w_j
   T w = 0, P = 0, rp = 1;
   int j = 1;
   for (; j + B - 1 <= nt; j += B) {
     T d[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) d[q] = col[(int64_t)(j + q) * stride];
+    if (j <= jw) {
 #pragma unroll
-    for (int q = 0; q < B; ++q) {
-      w = rmul(md.q1, w) + md.s * d[q];
-      P += rp * w;
-      rp = rmul(md.q1, rp);
-      d[q] = w;
+      for (int q = 0; q < B; ++q) {
+        w = rmul(md.q1, w) + md.s * d[q];
+        P += rp * w;
+        rp = rmul(md.q1, rp);
+        d[q] = w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        w = rmul(md.q1, w) + md.s * d[q];
+        d[q] = w;
+      }
     }
 #pragma unroll
     for (int q = 0; q < B; ++q) col[(int64_t)(j + q) * stride] = d[q];
@@ -66,12 +81,14 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   for (; j <= nt; ++j) {
     T d = col[(int64_t)j * stride];
     w = rmul(md.q1, w) + md.s * d;
-    P += rp * w;
-    rp = rmul(md.q1, rp);
+    if (j <= jw) {
+      P += rp * w;
+      rp = rmul(md.q1, rp);
+    }
     col[(int64_t)j * stride] = w;
   }
 
-  // backward recurrence with the boundary correction K r^j
+  // backward recurrence with the boundary correction K r^j, started at j0
   const T K = md.kap * P;
   T u = 0, e = 0;
   j = nt;
@@ -79,12 +96,20 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
     T d[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) d[q] = col[(int64_t)(j - q) * stride];
+    if (j - B + 1 <= jw) {
 #pragma unroll
-    for (int q = 0; q < B; ++q) {
-      if (j - q == md.j0) e = K * md.rj0;
-      u = rmul(md.q1, u) + (d[q] + e);
-      e *= md.rinv;
-      d[q] = u;
+      for (int q = 0; q < B; ++q) {
+        if (j - q == md.j0) e = K * md.rj0;
+        u = rmul(md.q1, u) + (d[q] + e);
+        e *= md.rinv;
+        d[q] = u;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        u = rmul(md.q1, u) + d[q];
+        d[q] = u;
+      }
     }
 #pragma unroll
     for (int q = 0; q < B; ++q) col[(int64_t)(j - q) * stride] = d[q];
