@@ -115,7 +115,7 @@ typedef struct {
                              solution's Q interpolated (cubic, along the faces) to the next
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
-                             every axis keeps >= 128 intervals, at most 2 levels); 0: off */
+                             every axis keeps >= 128 intervals, at most 3 levels); 0: off */
   double coarse_tol;      /* [0] relative Schur residual the coarse levels of the nested guess
                              solve to (never tighter than the solve's tol).  The prolonged
                              guess is only as good as the coarse grid's discretisation and
@@ -167,7 +167,7 @@ typedef struct {
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
-#define AHOC_COARSE_TOL_AUTO 1e-10
+#define AHOC_COARSE_TOL_AUTO 3e-11
 
 typedef struct {
   int iters;              /* GMRES iterations (matrix-vector products) of the last solve        */

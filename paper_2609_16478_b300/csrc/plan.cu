@@ -479,7 +479,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
 // coarsen while every axis keeps at least kMinCoarse intervals, at most
 // kAutoLevels times (deeper levels cost more in fixed latency than they save).
 constexpr int kMinCoarse = 128;
-constexpr int kAutoLevels = 2;
+constexpr int kAutoLevels = 3;
 int coarse_levels(const Geom& g, int requested) {
   int maxl = 0;
   int n = 1 << 30;

@@ -650,18 +650,24 @@ __global__ void __launch_bounds__(128) k_tri2_t3(Geom g, double* __restrict__ a,
   const double cf = carry[i], Cm = Cc[m];
   const double X = fma(-cf, tab[(last ? o.K2l : o.K2f) + m], fma(bcarry[i], modes[m].r, -Cm * tab[o.rp2 + i]));
   const double Y = fma(cf, tab[o.K1 + m], Cm * tab[o.rp1 + i]);
-  double d[L];
+  // rows are independent here: batches of 8 keep the register count (and so
+  // the occupancy that hides the loads) at that of an 8-row chunk
+  constexpr int Q = L < 8 ? L : 8;
+#pragma unroll 1
+  for (int q0 = 0; q0 < L; q0 += Q) {
+    double d[Q], rr[Q], pp[Q];
 #pragma unroll
-  for (int q = 0; q < L; ++q) d[q] = (q < len) ? col[(int64_t)(s0 + q) * sh.stride] : 0.0;
-#pragma unroll
-  for (int q = 0; q < L; ++q)
-    if (q < len) {
-      const int64_t k = (int64_t)q * sh.ncols;
-      d[q] = fma(Y, Pt[k], fma(X, Rt[k], d[q]));
+    for (int q = 0; q < Q; ++q) {
+      const bool in = q0 + q < len;
+      const int64_t k = (int64_t)(q0 + q) * sh.ncols;
+      d[q] = in ? col[(int64_t)(s0 + q0 + q) * sh.stride] : 0.0;
+      rr[q] = in ? Rt[k] : 0.0;
+      pp[q] = in ? Pt[k] : 0.0;
     }
 #pragma unroll
-  for (int q = 0; q < L; ++q)
-    if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
+    for (int q = 0; q < Q; ++q)
+      if (q0 + q < len) col[(int64_t)(s0 + q0 + q) * sh.stride] = fma(Y, pp[q], fma(X, rr[q], d[q]));
+  }
 }
 
 template <int L, int GEN>
