@@ -77,6 +77,79 @@ __global__ void k_reduce_cols(const double* __restrict__ partial, int nblocks, i
   if (lane == 0) out[c] = s;
 }
 
+// Fused CGS pass: dst = src - V h (h: nh columns; no update when h is NULL,
+// dst then unused), then the partial dots of the updated vector with V's
+// columns c (self: with itself), and the last block of each column group
+// sums the partials in block order into out -- the same arithmetic and
+// order as k_gemv_sub, k_mdot and k_reduce_cols, so the bits are theirs.
+// Every block of a column group computes the update of its rows (reading
+// src only); the blocks of group 0 write it.  cnt: one zeroed counter per
+// (problem, column group); the last block resets it.
+__global__ void __launch_bounds__(kDotThreads) k_cgs(const double* __restrict__ V, int64_t ld, int ncols,
+                                                     const double* __restrict__ h, int nh,
+                                                     const double* __restrict__ src, double* __restrict__ dst,
+                                                     int64_t n, double* __restrict__ partial,
+                                                     double* __restrict__ out, BatchDot bd, int64_t hstride,
+                                                     int64_t ostride, int* __restrict__ cnt, int self) {
+  const int bi = blockIdx.z;
+  if (bd.act && !bd.act[bi]) return;
+  V += (int64_t)bi * bd.vstride;
+  src += (int64_t)bi * bd.wstride;
+  if (dst) dst += (int64_t)bi * bd.wstride;
+  partial += (int64_t)bi * bd.pstride;
+  out += (int64_t)bi * ostride;
+  if (h) h += (int64_t)bi * hstride;
+  cnt += (int64_t)bi * gridDim.y + blockIdx.y;
+  __shared__ double red[kCols][kDotThreads / 32];
+  __shared__ int last;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const int c0 = blockIdx.y * kCols;
+  const int nc = (ncols - c0) < kCols ? (ncols - c0) : kCols;
+  double acc[kCols] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double wi = src[i];
+    if (h) {
+      for (int c = 0; c < nh; ++c) wi = fma(-V[(int64_t)c * ld + i], h[c], wi);
+      if (blockIdx.y == 0) dst[i] = wi;
+    }
+#pragma unroll
+    for (int q = 0; q < kCols; ++q)
+      if (q < nc) acc[q] = fma(self ? wi : V[(int64_t)(c0 + q) * ld + i], wi, acc[q]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kCols; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < kCols; ++q) {
+      double v = threadIdx.x < (kDotThreads / 32) ? red[q][threadIdx.x] : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0 && q < nc) partial[(int64_t)blockIdx.x * ncols + c0 + q] = v;
+    }
+  }
+  // the last block of this column group reduces its columns
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (warp < nc) {
+    const int c = c0 + warp;
+    double sacc = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partial + (int64_t)b * ncols + c);
+    sacc = warp_sum(sacc);
+    if (lane == 0) out[c] = sacc;
+  }
+  if (threadIdx.x == 0) *cnt = 0;
+}
+
 __global__ void k_gemv_sub(const double* __restrict__ V, int64_t ld, int ncols, const double* __restrict__ h,
                            double* __restrict__ w, int64_t n, BatchDot bd, int64_t hstride, const int* ncols_b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,6 +186,16 @@ cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_reduce_cols<<<dim3((ncols + 7) / 8, nbat), 256, 0, st>>>(partial, nb, ncols, out, bd.pstride, ostride, bd.act);
+  return cudaGetLastError();
+}
+cudaError_t launch_cgs(const double* V, int64_t ld, int ncols, const double* h, int nh, const double* src,
+                       double* dst, int64_t n, double* partial, int nblocks, double* out, cudaStream_t st, int nbat,
+                       const BatchDot& bd, int64_t hstride, int64_t ostride, int* cnt, bool self) {
+  const int64_t want = (n + 4095) / 4096;
+  const int nb = (int)(want < 1 ? 1 : (want > nblocks ? nblocks : want));
+  dim3 grid(nb, self ? 1 : (ncols + kCols - 1) / kCols, nbat);
+  k_cgs<<<grid, kDotThreads, 0, st>>>(V, ld, self ? 1 : ncols, h, nh, src, dst, n, partial, out, bd, hstride, ostride,
+                                     cnt, self ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, cudaStream_t st) {

@@ -172,6 +172,14 @@ struct BatchDot {
 // out[c] = <V_c, w>, c < ncols (deterministic two-stage reduction through
 // `partial`, which holds nblocks * ncols doubles per problem); problem b's
 // results at out + b * ostride
+// One fused CGS pass (blas.cu, k_cgs): dst = src - V h over nh columns when
+// h is set (dst must not alias src), then out[c] = <V_c, dst> for c < ncols
+// (self: out[0] = <dst, dst>; without h the dots take src) in one launch,
+// with the block split, order and bits of launch_gemv_sub + launch_mdot.
+// cnt: zeroed ints, one per (problem, group of 4 columns), left zeroed.
+cudaError_t launch_cgs(const double* V, int64_t ld, int ncols, const double* h, int nh, const double* src,
+                       double* dst, int64_t n, double* partial, int nblocks, double* out, cudaStream_t st, int nbat,
+                       const BatchDot& bd, int64_t hstride, int64_t ostride, int* cnt, bool self);
 cudaError_t launch_mdot(const double* V, int64_t ld, int ncols, const double* w, int64_t n, double* partial,
                         int nblocks, double* out, cudaStream_t st, int nbat = 1, const BatchDot& bd = BatchDot{},
                         int64_t ostride = 0);

@@ -305,7 +305,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t W1, W2, ainv, afac, gD, vedge, gN, lapt, twx, snx, twy, sny, twz, snz, modes, b, Q, r, Kry, partial, hdev,
       tmp, pre, stab[3], ctab[3], tri, rxm, rxp, qy, R2, tau, act, scal, ncolsb, modes_v, modesf_v, rpow_v, gL,
-      gam, bcg, bcoef, bank, Ud, Vd,
+      gam, bcg, bcoef, bank, Ud, Vd, cgscnt,
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
@@ -354,6 +354,8 @@ constexpr int kDotBlocks = 296;  // 2 x 148 SMs
 // of the Hessenberg column exchange
 int64_t pstride(const Opts& o) { return (int64_t)kDotBlocks * (2 * (o.restart + 1) + 2); }
 int hstride(const Opts& o) { return 2 * (o.restart + 1) + 4; }
+// counters of the fused CGS passes: one per problem and group of 4 Krylov columns
+int cgs_groups(const Opts& o) { return (o.restart + 1 + 3) / 4 + 1; }
 
 bool fused_ok(const Geom& g);
 
@@ -440,6 +442,7 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.Vd = take(nbank ? B * fld : 0);
   L.partial = take(B * (size_t)pstride(o) * sizeof(double));
   L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
+  L.cgscnt = take(B * (size_t)cgs_groups(o) * sizeof(int));
   L.act = take(B * sizeof(int));
   L.scal = take(B * sizeof(double));
   L.ncolsb = take(B * sizeof(int));
@@ -571,6 +574,7 @@ struct ahoc_plan {
   int* act = nullptr;
   double* scal = nullptr;  // per-problem scalars of the batched axpy
   int* ncolsb = nullptr;   // per-problem column counts of the batched update
+  int* cgscnt = nullptr;   // zeroed counters of the fused CGS passes (launch_cgs)
   std::vector<int> act_now, part;  // current mask; problems taking part in solves
   std::vector<ProbStat> ps;
   bool has_gD = false, has_vedge = false, has_gN = false, has_lapt = false;
@@ -1239,6 +1243,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->act = at<int>(p, L.act);
   p->scal = at<double>(p, L.scal);
   p->ncolsb = at<int>(p, L.ncolsb);
+  p->cgscnt = at<int>(p, L.cgscnt);
   p->g.act = p->act;
   if (o.prec == AHOC_MIXED) {
     p->F1 = at<float>(p, L.F1);
@@ -1292,6 +1297,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMemsetAsync(p->gN, 0, B * face, p->st));
   CKC(cudaMemsetAsync(p->lapt, 0, B * face, p->st));
   CKC(cudaMemsetAsync(p->gL, 0, B * face, p->st));
+  CKC(cudaMemsetAsync(p->cgscnt, 0, B * (size_t)cgs_groups(o) * sizeof(int), p->st));
   CKS(set_act(p, p->part));
   std::vector<double> tw, sn;
   dst_tables(g.N[0], tw, sn);
@@ -1641,11 +1647,21 @@ ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
   RUN(AHOC_K_KRYLOV, launch_axpby(vj, src, 0.0, 0.0, n, p->st, g.nb, p->scal, g.act));
   CKS(precond_apply(p, vj, zj));
   CKS(matvec_dev(p, zj, w, uh));
-  CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev));
-  CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev, w, nullptr));
-  CKS(mdot(p, p->Kry, ld, j + 1, w, p->hdev + (j + 1)));
-  CKS(gemv_sub(p, p->Kry, ld, j + 1, p->hdev + (j + 1), w, nullptr));
-  CKS(mdot(p, w, n, 1, w, p->hdev + 2 * (j + 1)));
+  // CGS2 in three fused passes (the bits of separate dot, update and
+  // reduction kernels): h1 = V^T w; w' = w - V h1 (in tmp), h2 = V^T w';
+  // w = w' - V h2, ||w||^2
+  BatchDot bd;
+  bd.vstride = n;
+  bd.wstride = n;
+  bd.pstride = pstride(p->o);
+  bd.act = g.act;
+  const int hs = hstride(p->o);
+  RUN(AHOC_K_KRYLOV, launch_cgs(p->Kry, ld, j + 1, nullptr, 0, w, nullptr, n, p->partial, kDotBlocks, p->hdev, p->st,
+                                g.nb, bd, hs, hs, p->cgscnt, false));
+  RUN(AHOC_K_KRYLOV, launch_cgs(p->Kry, ld, j + 1, p->hdev, j + 1, w, p->tmp, n, p->partial, kDotBlocks,
+                                p->hdev + (j + 1), p->st, g.nb, bd, hs, hs, p->cgscnt, false));
+  RUN(AHOC_K_KRYLOV, launch_cgs(p->Kry, ld, 1, p->hdev + (j + 1), j + 1, p->tmp, w, n, p->partial, kDotBlocks,
+                                p->hdev + 2 * (j + 1), p->st, g.nb, bd, hs, hs, p->cgscnt, true));
   CK(cudaMemcpyAsync(p->hhost, p->hdev, (size_t)g.nb * hstride(p->o) * sizeof(double), cudaMemcpyDeviceToHost,
                      p->st));
   return AHOC_OK;
