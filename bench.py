@@ -129,6 +129,26 @@ class ClockSampler:
         return out
 
 
+def max_over_ranks(values, world, device):
+    """The largest of each value over the ranks (the slowest rank's time
+    decides a replicated run); one all-reduce on the initialised process
+    group when world > 1."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(world: int, steps: int, units_per_step: float, ms: float) -> float:
+    """Units all ranks processed per second: each rank runs `steps` steps of
+    `units_per_step` units, the job takes the slowest rank's `ms`."""
+    return world * steps * units_per_step / (ms / 1e3)
+
+
 _SAMPLES = {}
 
 
@@ -383,15 +403,12 @@ def run_ours(args, rank, world, local):
         tinfos.append(ti)
     plan_t.close()
 
-    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_s * 1e3], world, dev)
     if rank != 0:
         return
 
-    value = world * args.steps * dof / (ms / 1e3)
-    e2e_value = world * args.steps * dof / (e2e_ms / 1e3)
+    value = whole_job_rate(world, args.steps, dof, ms)
+    e2e_value = whole_job_rate(world, args.steps, dof, e2e_ms)
     launches = sum(i["launches"] for i in infos)
     kms = {k: sum(i["kernel_ms"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
     kn = {k: sum(i["kernel_launches"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
