@@ -1,17 +1,21 @@
 """Benchmark: biharmonic DOF/s to a fixed error on one or more B300s.
 
 A step is one whole solve (Algorithm 1: Schur right-hand side, GMRES on the
-Schur system to relative residual 1e-12, recovery of V and U) of the 2D
-variable-coefficient clamped problem on a 4096 x 4096 grid (coefficient
-1 + 0.4 * 8 seeded Fourier modes, u = sin^2(pi x) sin^2(pi y) cos(pi x)),
-FP64 throughout.  DOF = interior unknowns (N-1)^2 per solve.
+Schur system to relative residual 1e-12, recovery of V and U) of the 3D
+variable-coefficient clamped problem on a 1024^3 grid: u = prod_a
+sin^2(pi x_a) sin(32 pi x_a), coefficient 1 + 0.5 * (6 seeded Fourier modes,
+wavenumbers <= 4), FP64 throughout.  DOF = interior unknowns (N-1)^3 per
+solve.  Beside it: the same workload through the mixed path (FP32 inner
+solves, FP64 refinement), the 2D 4096^2 workload in both precisions, the
+serving stream, and the oracle's timing sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME --n N] [--prec fp64|mixed]
 
 Multi-GPU runs (torchrun) solve independent replicas, one per rank (the
 solve does not shard on this pool: every box has one GPU); value is the sum
 over ranks.  The reference arm times the CPU oracle (assembled coupled
-system + SuperLU) on a bounded sample of the same workload.
+system + SuperLU) on a bounded sample of the same workload (--cpu-n).
 """
 
 from __future__ import annotations
@@ -31,7 +35,14 @@ if ROOT not in sys.path:
 
 METRIC = "biharmonic DOF/s to fixed error"
 UNIT = "DOF/s"
-FP64_PEAK_TFLOPS = 1.25     # nominal dense FP64 rate of a B300 (no FP64 tensor path is used)
+# FP64 peak of the B300, derived from the FP64 pipe's issue rate (ncu: 2 FP64
+# thread operations per clock per SM, an FMA counting 2 flops) at the maximum
+# SM clock: 148 x 2 x 2 x 2.032e9 flop/s
+FP64_PEAK_TFLOPS_DERIVED = 148 * 2 * 2 * 2.032e9 / 1e12
+
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
+# capture, scaled to the bench's grid by the points processed (profiles/)
+PROFILED_TRAFFIC = {}
 
 
 def _peaks():
@@ -152,8 +163,9 @@ def whole_job_rate(world: int, steps: int, units_per_step: float, ms: float) -> 
 _SAMPLES = {}
 
 
-def cpu_oracle_sample(N_cpu: int):
-    """Time the CPU oracle (assembly + SuperLU) on the 2D Fourier-coefficient workload at N_cpu; returns (DOF/s, seconds, err).
+def cpu_oracle_sample(name: str, N_cpu: int):
+    """Time the CPU oracle (assembly + SuperLU) on workload `name` at N_cpu
+    intervals per axis; returns (DOF/s, seconds, err against the exact u).
 
     The synthetic inputs are generated once, outside the timed region."""
     import numpy as np
@@ -161,40 +173,51 @@ def cpu_oracle_sample(N_cpu: int):
     from oracle import coupled
     from paper_2609_16478_b300 import inputs
 
-    if N_cpu not in _SAMPLES:
-        _SAMPLES[N_cpu] = inputs.sample(inputs.config_problem("fourier2d"), [N_cpu, N_cpu])
-    d = _SAMPLES[N_cpu]
+    key = (name, N_cpu)
+    prob = inputs.config_problem(name)
+    if key not in _SAMPLES:
+        _SAMPLES[key] = inputs.sample(prob, [N_cpu] * prob.dim)
+    d = _SAMPLES[key]
     t0 = time.perf_counter()
     sol = coupled.solve_direct(coupled.assemble(d), d)
     dt = time.perf_counter() - t0
     err = float(np.max(np.abs(sol.U - d["u_exact"])))
-    return (N_cpu - 1) ** 2 / dt, dt, err
+    return (N_cpu - 1) ** prob.dim / dt, dt, err
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm (rank 0 only)."""
+    """The oracle as the reference arm (rank 0 only): each step one direct
+    solve of the bench's workload at the bounded size --cpu-n."""
     if rank != 0:
         return
-    N_cpu = args.cpu_n
+    from paper_2609_16478_b300 import inputs
+
+    name, N_cpu = args.workload, args.cpu_n
+    dim = inputs.config_problem(name).dim
     for _ in range(args.warmup):
-        cpu_oracle_sample(N_cpu)
+        cpu_oracle_sample(name, N_cpu)
     t0 = time.perf_counter()
     errs = []
     for _ in range(args.steps):
-        _, _, e = cpu_oracle_sample(N_cpu)
+        _, _, e = cpu_oracle_sample(name, N_cpu)
         errs.append(e)
     dt = time.perf_counter() - t0
-    value = args.steps * (N_cpu - 1) ** 2 / dt
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    value = args.steps * (N_cpu - 1) ** dim / dt
+    sample = ("direct solve of the assembled coupled system (SuperLU, single-threaded; %d host cores visible) of "
+              "the bench's workload at N=%d per step (the GPU arm solves N=%d)" % (_cores(), N_cpu, args.n))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes), oracle sample N=%d" % N_cpu,
-                   "dim": 2, "N": N_cpu, "err_inf_vs_exact": max(errs)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "direct solve of the assembled coupled system at N=%d per step "
-                                   "(SuperLU, single-threaded; %d host cores visible)" % (N_cpu, cores)},
+        "config": {"workload": _workload_name(name, args.n, dim) + ", oracle sample N=%d" % N_cpu,
+                   "dim": dim, "N": N_cpu, "err_inf_vs_exact": max(errs),
+                   "note": "a timing sample: the high-wavenumber u is not resolved at this N"
+                   if name == "fourier3d_k32" else ""},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -325,6 +348,141 @@ def serving_variant(args, dev):
     }
 
 
+HEADLINE = ("fourier3d_k32", 1024)   # 3D 1024^3, u = prod sin^2(pi x_a) sin(32 pi x_a), 6-mode coefficient in [0.5, 1.5]
+VARIANT_2D = ("fourier2d", 4096)      # 2D 4096^2, 8-mode coefficient in [0.6, 1.4]
+
+
+def _workload_name(name, N, dim):
+    if name == "fourier3d_k32":
+        return ("3D variable-coefficient clamped biharmonic, high wavenumber (u = prod sin^2(pi x_a) sin(32 pi x_a), "
+                "coefficient 1 + 0.5 * 6 seeded Fourier modes) N=%d^3" % N)
+    if name == "fourier3d":
+        return "3D variable-coefficient clamped biharmonic (Fourier coefficient, 6 modes) N=%d^3" % N
+    return "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%d^%d" % (N, dim)
+
+
+def _interior(N, dim):
+    return (N - 1) ** dim
+
+
+def _kernel_pass(data, dev, stream, prec, args):
+    """One solve on an event-timed plan (every launch bracketed by CUDA events
+    on the plan's stream, plain launches); the plan is closed on return."""
+    import torch
+
+    from paper_2609_16478_b300 import ahoc
+
+    f = data["f"].reshape(-1).contiguous()
+    p = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters,
+                      levels=args.levels if prec == "fp64" else -1, prec=prec, stream=stream)
+    u = torch.empty_like(f)
+    _, ti = p.solve(f, u, tol=args.tol)
+    p.close()
+    del u
+    torch.cuda.empty_cache()
+    return ti
+
+
+def _dst_rates(ti, N, dim, itemsize):
+    """Per DST class of the finest grid: average event-timed launch time and
+    the algorithmic HBM rate (one read and one write of every interior point
+    per launch)."""
+    out = {}
+    nbytes = 2 * itemsize * _interior(N, dim)
+    for k in ("dst_x", "dst_y"):
+        n = ti["kernel_launches_top"][k]
+        if n == 0:
+            continue
+        ms = ti["kernel_ms_top"][k] / n
+        out[k] = {"launches": n, "avg_launch_ms": ms, "algorithmic_bytes_per_launch": nbytes,
+                  "hbm_GBs": nbytes / (ms / 1e3) / 1e9}
+    return out
+
+
+def _timed_solves(plan, f, u, steps, args, clk=None):
+    import torch
+
+    st = plan.stream
+    infos = []
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        _, info = plan.solve(f, u, tol=args.tol)
+        infos.append(info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), infos
+
+
+def _mixed_variant(data, dev, stream, args, u_ref):
+    """The same workload through the mixed path (FP32 inner solves, FP64 refinement)."""
+    import torch
+
+    from paper_2609_16478_b300 import ahoc
+
+    N = data["N"][0]
+    dim = data["dim"]
+    f = data["f"].reshape(-1).contiguous()
+    pm = ahoc.plan_for(data, device=dev, restart=args.restart, max_iters=args.max_iters, prec="mixed",
+                       stream=stream)
+    um = torch.empty_like(f)
+    for _ in range(args.mixed_warmup):
+        pm.solve(f, um, tol=args.tol)
+    steps = args.mixed_steps
+    mms, ims = _timed_solves(pm, f, um, steps, args)
+    pm.close()
+    torch.cuda.empty_cache()
+    err = float((um.reshape(data["u_exact"].shape) - data["u_exact"]).abs().max())
+    rel = float(torch.linalg.norm(um - u_ref) / torch.linalg.norm(u_ref))
+    del um
+    torch.cuda.empty_cache()
+    tm = _kernel_pass(data, dev, stream, "mixed", args)
+    im = ims[-1]
+    return {
+        "value": steps * _interior(N, dim) / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / steps, "steps": steps,
+        "dtype": "f32 inner solves, f64 refinement", "refine_steps": im["refine_steps"],
+        "gmres_iters_total": im["iters"], "err_inf_vs_exact": err, "rel_l2_vs_fp64": rel,
+        "launches_per_step": sum(i["launches"] for i in ims) // steps,
+        "kernel_ms_per_step": tm["kernel_ms"], "kernel_launches_per_step": tm["kernel_launches"],
+        "dst_hbm_f32": _dst_rates(tm, N, dim, 4)}
+
+
+def _variant_2d(args, dev, stream):
+    """2D 4096^2, FP64 and mixed: K solves each, device-resident."""
+    import torch
+
+    from paper_2609_16478_b300 import ahoc, inputs
+
+    name, N = VARIANT_2D
+    data = inputs.sample(inputs.config_problem(name), [N, N], backend="torch", device=dev)
+    f = data["f"].reshape(-1).contiguous()
+    out = {"workload": _workload_name(name, N, 2)}
+    u64 = None
+    for prec in ("fp64", "mixed"):
+        p = ahoc.plan_for(data, device=dev, restart=300, max_iters=args.max_iters, prec=prec, stream=stream)
+        u = torch.empty_like(f)
+        for _ in range(args.warmup):
+            p.solve(f, u, tol=args.tol)
+        ms, infos = _timed_solves(p, f, u, args.steps, args)
+        p.close()
+        err = float((u.reshape(N + 1, N + 1) - data["u_exact"]).abs().max())
+        rec = {"value": args.steps * _interior(N, 2) / (ms / 1e3), "ms_per_step": ms / args.steps,
+               "err_inf_vs_exact": err, "gmres_iters": infos[-1]["iters"],
+               "coarse_gmres_iters": infos[-1]["coarse_iters"], "refine_steps": infos[-1]["refine_steps"],
+               "launches_per_step": infos[-1]["launches"]}
+        if prec == "fp64":
+            u64 = u
+        else:
+            rec["rel_l2_vs_fp64"] = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
+        out[prec] = rec
+        torch.cuda.empty_cache()
+    del data, f, u64
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -333,171 +491,133 @@ def run_ours(args, rank, world, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    N = args.n
-    dim = 2
-    prob = inputs.config_problem("fourier2d")
-    data = inputs.sample(prob, [N, N], backend="torch", device=dev)
-    # the plan's own stream: GMRES iterations are replayed as CUDA graphs (not
-    # possible on the legacy default stream); kernel timing uses a second,
-    # event-timed plan below, so that the timed solves run exactly as a user's
+    name, N = args.workload, args.n
+    prob = inputs.config_problem(name)
+    dim = prob.dim
+    data = inputs.sample(prob, [N] * dim, backend="torch", device=dev)
+    data.pop("v_exact", None)
+    # the plans' own stream: GMRES iterations are replayed as CUDA graphs (not
+    # possible on the legacy default stream); kernel timing uses separate,
+    # event-timed plans, so that the timed solves run exactly as a user's
     solve_stream = torch.cuda.Stream(device=dev)
     plan = ahoc.plan_for(data, device=dev, restart=args.restart, max_iters=args.max_iters,
-                         levels=args.levels, stream=solve_stream)
+                         levels=args.levels, stream=solve_stream, prec=args.prec)
     f = data["f"].reshape(-1).contiguous()
     u = torch.empty_like(f)
-    st = plan.stream
-    dof = (N - 1) ** dim
+    dof = _interior(N, dim)
 
     for _ in range(args.warmup):
         _, info = plan.solve(f, u, tol=args.tol)
     torch.cuda.synchronize()
-    err = float((u.reshape(N + 1, N + 1) - data["u_exact"]).abs().max())
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    # device-resident timed region
-    infos = []
+    # device-resident timed region: inputs in HBM, exactly `steps` solves
     with ClockSampler(local) as clk:
         barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(args.steps):
-            _, info = plan.solve(f, u, tol=args.tol)
-            infos.append(info)
-        e1.record(st)
-        torch.cuda.synchronize()
+        ms, infos = _timed_solves(plan, f, u, args.steps, args)
         barrier()
-    ms = e0.elapsed_time(e1)
     clocks = clk.summary()
+    err = float((u.reshape(data["u_exact"].shape) - data["u_exact"]).abs().max())
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # end to end through the C ABI with host buffers (ahoc_solve_host: pinned f
+    # in, u out, the copies inside the timed region)
     f_host = f.cpu().pin_memory()
     u_host = torch.empty(f.numel(), dtype=torch.float64).pin_memory()
-    f_dev = torch.empty_like(f)
+    e2e_steps = min(args.steps, args.e2e_steps)
+    plan.solve_host(f_host, u_host, tol=args.tol)  # first call allocates the staging grids
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        with torch.cuda.stream(st):
-            f_dev.copy_(f_host, non_blocking=True)
-        plan.solve(f_dev, u, tol=args.tol)
-        with torch.cuda.stream(st):
-            u_host.copy_(u, non_blocking=True)
-        st.synchronize()
+    for _ in range(e2e_steps):
+        plan.solve_host(f_host, u_host, tol=args.tol)
     e2e_s = time.perf_counter() - t0
     barrier()
+    e2e_err = float((u_host.reshape(data["u_exact"].shape) - data["u_exact"].cpu()).abs().max())
+    plan.close()
+    del plan, f_host, u_host
+    torch.cuda.empty_cache()
 
-    # kernel breakdown: the same solves on an event-timed plan (every launch
-    # bracketed by CUDA events on the plan's stream, plain launches)
-    plan_t = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters,
-                           levels=args.levels, stream=solve_stream)
-    u_t = torch.empty_like(f)
-    plan_t.solve(f, u_t, tol=args.tol)
-    tinfos = []
-    for _ in range(args.steps):
-        _, ti = plan_t.solve(f, u_t, tol=args.tol)
-        tinfos.append(ti)
-    plan_t.close()
-
-    ms, e2e_ms = max_over_ranks([ms, e2e_s * 1e3], world, dev)
+    ms, e2e_ms = max_over_ranks([ms, 1e3 * e2e_s * args.steps / e2e_steps], world, dev)
     if rank != 0:
         return
 
+    # kernel breakdown: one solve on an event-timed plan
+    ti = _kernel_pass(data, dev, solve_stream, args.prec, args)
     value = whole_job_rate(world, args.steps, dof, ms)
     e2e_value = whole_job_rate(world, args.steps, dof, e2e_ms)
     launches = sum(i["launches"] for i in infos)
-    kms = {k: sum(i["kernel_ms"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
-    kn = {k: sum(i["kernel_launches"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
-    top = max(kms, key=lambda k: kms[k])
-    # the roofline uses the N = 4096 grid's own launches (coarse levels have other N)
-    kms_top = {k: sum(i["kernel_ms_top"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
-    kn_top = {k: sum(i["kernel_launches_top"][k] for i in tinfos) for k in ahoc.KERNEL_NAMES}
-    avg_ms = kms_top["dst_x"] / max(1, kn_top["dst_x"])
-    flops = dst_flops_per_line(N) * (N - 1)          # one launch transforms N-1 lines of N
+    kms, kn = ti["kernel_ms"], ti["kernel_launches"]
+    kms_top, kn_top = ti["kernel_ms_top"], ti["kernel_launches_top"]
+    # the roofline is taken on the finest grid's dominant DST class (coarse levels have other N)
+    dk = max(("dst_x", "dst_y"), key=lambda k: kms_top[k])
+    avg_ms = kms_top[dk] / max(1, kn_top[dk])
+    lines = (N - 1) ** (dim - 1)
+    flops = dst_flops_per_line(N) * lines          # one launch transforms every line of the field along one axis
     achieved = flops / (avg_ms / 1e3) / 1e12
-    roof = {"kernel": "k_dst_x<double> (DST-I along x, FP64)", "bound": "alu", "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "nominal B300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
-            # DRAM bytes per launch of k_dst_x<double,1,0> (forward transform with the fused M load, the
-            # kernel's most frequent form in GMRES) from the ncu capture summarised in
-            # profiles/k_dst_x_fp64_2d4096.md: 134.5 MB read + 94.5 MB written
-            "traffic": 229.0e6, "avg_launch_ms": avg_ms, "launches": kn_top["dst_x"],
-            "algorithmic_bytes_per_launch": 16 * N * (N - 1), "flops_per_launch": flops,
-            "hbm_achieved_GBs": 16 * N * (N - 1) / (avg_ms / 1e3) / 1e9,
-            "hbm_peak_GBs": _peaks().get("hbm_gbs"),
-            "share_of_step": kms["dst_x"] / sum(kms.values()), "top_kernel_by_time": top,
-            "fp64_instr_note": "FP64 pipe 90-92% busy under ncu (profiles/); the FFT's additions cannot all be "
-                               "FMAs, so flops per FP64 operation stay below 2",
-            "fp64_probe_ops_per_s": 0.463e12}
-    # the same workload through the mixed-precision path (FP32 inner solves, FP64 refinement)
+    peak = FP64_PEAK_TFLOPS_DERIVED
+    roof = {"kernel": "k_%s<double> (DST-I along %s, FP64)" % (dk, dk[-1]), "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "derived, of the FP64 pipe: 148 SMs x 2 FP64 FMA lanes per clock (ncu's FP64 pipe "
+                           "peak) x 2 flop x 2.032 GHz; MEASURED_PEAKS.json has no FP64 figure",
+            "traffic": PROFILED_TRAFFIC.get((name, N, dk)), "avg_launch_ms": avg_ms, "launches": kn_top[dk],
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 16 * N * lines,
+            "hbm_achieved_GBs": 16 * N * lines / (avg_ms / 1e3) / 1e9, "hbm_peak_GBs": _peaks().get("hbm_gbs"),
+            "share_of_step": kms[dk] / sum(kms.values()),
+            "top_kernel_class_by_time": max(kms, key=lambda k: kms[k]),
+            "flop_count": "algorithmic flops of the N/2-point complex FFT with DST-I pre- and post-processing "
+                          "(complex product = 6 flops), independent of the kernel's FMA fusion"}
     variants = {}
-    if not args.no_mixed:
-        pm = ahoc.plan_for(data, device=dev, restart=args.restart, max_iters=args.max_iters,
-                           prec="mixed", stream=solve_stream)
-        um = torch.empty_like(f)
-        for _ in range(args.warmup):
-            pm.solve(f, um, tol=args.tol)
-        torch.cuda.synchronize()
-        m0 = torch.cuda.Event(enable_timing=True)
-        m1 = torch.cuda.Event(enable_timing=True)
-        m0.record(pm.stream)
-        ims = []
-        for _ in range(args.steps):
-            _, im = pm.solve(f, um, tol=args.tol)
-            ims.append(im)
-        m1.record(pm.stream)
-        torch.cuda.synchronize()
-        mms = m0.elapsed_time(m1)
-        pm_t = ahoc.plan_for(data, device=dev, timing=True, restart=args.restart, max_iters=args.max_iters,
-                             prec="mixed", stream=solve_stream)
-        pm_t.solve(f, um, tol=args.tol)
-        _, tm = pm_t.solve(f, um, tol=args.tol)
-        pm_t.close()
-        variants["mixed"] = {
-            "value": args.steps * dof / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / args.steps,
-            "dtype": "f32 inner solves, f64 refinement", "refine_steps": im["refine_steps"],
-            "gmres_iters_total": im["iters"],
-            "err_inf_vs_exact": float((um.reshape(N + 1, N + 1) - data["u_exact"]).abs().max()),
-            "rel_l2_vs_fp64": float(torch.linalg.norm(um - u) / torch.linalg.norm(u)),
-            "launches_per_step": sum(i["launches"] for i in ims) // args.steps,
-            "kernel_ms_per_step": tm["kernel_ms"], "kernel_launches_per_step": tm["kernel_launches"]}
-        pm.close()
+    if not args.no_mixed and args.prec == "fp64":
+        variants["mixed"] = _mixed_variant(data, dev, solve_stream, args, u)
+    del data, f, u
+    torch.cuda.empty_cache()
+    if not args.no_2d:
+        variants["2d_4096"] = _variant_2d(args, dev, solve_stream)
     if not args.no_serve and world == 1:
-        del plan
-        torch.cuda.empty_cache()
         variants["serving"] = serving_variant(args, dev)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, _ = cpu_oracle_sample(args.cpu_n)
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        reps, tot = 0, 0.0
+        while reps < 1 or (tot < 10.0 and reps < 5):  # about 10-30 s of CPU work
+            v, dt, _ = cpu_oracle_sample(name, args.cpu_n)
+            reps += 1
+            tot += dt
+        v = reps * (args.cpu_n - 1) ** dim / tot
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "direct solve (assembly + SuperLU) of the same workload at N=%d, %.1f s; "
-                         "single-threaded, %d host cores visible" % (args.cpu_n, dt, cores)}
-    nbytes = f.numel() * 8
+               "sample": "%d direct solves (assembly + SuperLU) of the same workload at N=%d, %.1f s in all; "
+                         "single-threaded, %d host cores visible" % (reps, args.cpu_n, tot, _cores())}
+    nbytes = f_numel = (N + 1) ** dim
+    nbytes = 8 * f_numel
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%d, FP64, GMRES tol %g"
-                               % (N, args.tol),
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32 inner solves, f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": _workload_name(name, N, dim) + ", %s, GMRES tol %g"
+                               % ("FP64" if args.prec == "fp64" else "mixed FP32/FP64", args.tol),
                    "dim": dim, "N": N, "dof_per_solve": dof, "tol": args.tol,
                    "gmres_iters": infos[-1]["iters"], "coarse_levels": infos[-1]["levels"],
                    "coarse_gmres_iters": infos[-1]["coarse_iters"], "err_inf_vs_exact": err,
                    "rel_resid": infos[-1]["rel_resid"], "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set (two 134 MB fields + coefficient/data arrays) larger than L2; no flush",
+                   "l2": "inputs larger than L2 (one FP64 field of this grid is %.1f GB); no flush"
+                         % (8 * N ** dim / 1e9),
                    "cuda_graphs": "GMRES iterations replayed as CUDA graphs on the plan's own stream",
-                   "kernel_timing": "kernel_ms_per_step and roofline from a second pass of the same solves with "
-                                    "every launch bracketed by CUDA events (plain launches)"},
+                   "kernel_timing": "kernel_ms_per_step and roofline from one more solve on a plan with every "
+                                    "launch bracketed by CUDA events (plain launches)"},
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": e2e_steps, "err_inf_vs_exact": e2e_err,
+                "how": "ahoc_solve_host through the C ABI: f from pinned host memory to the device, the solve, "
+                       "u back to pinned host memory, host clock around each call"},
         "gpu_launches": launches,
-        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-        "kernel_ms_per_step_finest_level": {k: v / args.steps for k, v in kms_top.items()},
+        "kernel_ms_per_step": kms,
+        "kernel_ms_per_step_finest_level": kms_top,
+        "kernel_launches_per_step": kn,
         "roofline": roof,
+        "dst_hbm_" + ("f64" if args.prec == "fp64" else "f32"): _dst_rates(ti, N, dim, 8 if args.prec == "fp64" else 4),
         "cpu_baseline": cpu,
         "variants": variants,
     }
@@ -510,14 +630,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--workload", default=HEADLINE[0])
+    ap.add_argument("--n", type=int, default=HEADLINE[1])
     ap.add_argument("--tol", type=float, default=1e-12)
-    ap.add_argument("--restart", type=int, default=300)
+    ap.add_argument("--prec", choices=["fp64", "mixed"], default="fp64", help="precision of the headline solves")
+    ap.add_argument("--restart", type=int, default=100)
     ap.add_argument("--max-iters", type=int, default=2000)
-    ap.add_argument("--cpu-n", type=int, default=256)
+    ap.add_argument("--cpu-n", type=int, default=20, help="grid of the oracle's timing sample")
     ap.add_argument("--levels", type=int, default=-1, help="coarse levels of the nested initial guess (-1 auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--mixed-steps", type=int, default=3, help="timed solves of the mixed variant")
+    ap.add_argument("--mixed-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="timed solves through ahoc_solve_host (at most --steps)")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D 4096^2 variant")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-workers", type=int, default=4)

@@ -225,6 +225,18 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
  * u is written.  AHOC_ENOCONV: u holds the solution for the best iterate. */
 ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info);
 
+/* ahoc_solve with HOST arrays (Algorithm 1, Main procedure, as ahoc_solve):
+ * f of every problem taking part is copied to the device, the problem is
+ * solved, and u is copied back, all on the plan's stream.
+ *   f_host  host, opts.batch full grids back to back (read for the problems
+ *           taking part); page-locked memory gives the fastest copies,
+ *           pageable memory works
+ *   u_host  host, same size, output (boundary entries = g_D)
+ * The first call allocates two device staging arrays of opts.batch full
+ * grids each with cudaMalloc (freed by ahoc_plan_destroy; AHOC_ENOMEM if that
+ * fails).  Returns when u_host is written; otherwise as ahoc_solve. */
+ahoc_status ahoc_solve_host(ahoc_plan* p, const double* f_host, double* u_host, double tol, ahoc_info* info);
+
 /* y = S_h q = R(q) - R(0) (Lemma 1; Algorithm 1, SchurMatVec), the
  * homogeneous part of the boundary residual: V(q) by the v-equation with
  * zero f and edge data, U(V) by the u-equation with zero g_D, then

@@ -24,7 +24,7 @@ AHOC_FP64, AHOC_MIXED = 0, 1
 AHOC_TUNE_TRI_CHUNK, AHOC_TUNE_DST_THREADS = 0, 1
 
 # every entry point declared in include/ahoc.h
-SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
+SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_matvec", "ahoc_schur_rhs",
            "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
            "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc", "ahoc_plan_load", "ahoc_set_active",
            "ahoc_batch", "ahoc_tune_set", "ahoc_tune_get")
@@ -80,6 +80,7 @@ def lib():
     L.ahoc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, i64p, dp, dp, C.c_void_p,
                                    C.POINTER(ahoc_bdata), C.POINTER(ahoc_opts), C.c_void_p]
     L.ahoc_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
+    L.ahoc_solve_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
     L.ahoc_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     L.ahoc_schur_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     L.ahoc_last_qv.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -102,7 +103,7 @@ def lib():
     L.ahoc_tune_set.restype = C.c_int
     L.ahoc_tune_get.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int]
     L.ahoc_tune_get.restype = C.c_int
-    for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_matvec", "ahoc_schur_rhs",
+    for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_matvec", "ahoc_schur_rhs",
                  "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_plan_load",
                  "ahoc_set_active"):
         getattr(L, name).restype = C.c_int
@@ -122,6 +123,14 @@ def _ptr(t: Optional[torch.Tensor], numel: int, name: str):
         return None
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("%s must be a contiguous CUDA float64 tensor" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(t: torch.Tensor, numel: int, name: str):
+    if not (t.device.type == "cpu" and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous host float64 tensor" % name)
     if t.numel() != numel:
         raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
     return C.c_void_p(t.data_ptr())
@@ -259,6 +268,18 @@ class Plan:
         out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
         return u, (out[0] if B == 1 else out)
 
+    def solve_host(self, f_host: torch.Tensor, u_host: torch.Tensor, tol: float = 1e-12, check: bool = True):
+        """``ahoc_solve_host``: f and u in host memory (float64, contiguous;
+        pinned for fast copies); returns the info as ``solve`` does."""
+        B = self.batch
+        infos = (ahoc_info * B)()
+        st = lib().ahoc_solve_host(self._h, _hptr(f_host, B * self.nfull, "f_host"),
+                                   _hptr(u_host, B * self.nfull, "u_host"), float(tol), infos)
+        if check:
+            _check(st, "ahoc_solve_host")
+        out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
+        return u_host, (out[0] if B == 1 else out)
+
     def load(self, b: int, alpha: torch.Tensor, g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None, beta=None):
         """Replace problem b's coefficient and boundary data (``ahoc_plan_load``)."""
         bd = ahoc_bdata(_ptr(g_D, self.nfull, "g_D"), _ptr(g_N, self.ngamma, "g_N"),
@@ -312,9 +333,11 @@ class Plan:
         return out
 
     def close(self):
+        """Destroy the plan and release its workspace tensor."""
         if getattr(self, "_h", None) is not None and self._h.value:
             _check(lib().ahoc_plan_destroy(self._h), "ahoc_plan_destroy")
             self._h = None
+        self._ws = None
 
     def __del__(self):
         try:

@@ -609,6 +609,8 @@ struct ahoc_plan {
   int64_t kn[AHOC_NK] = {0};
   ahoc_plan* coarse = nullptr;  // next coarser level of the nested initial guess
   int levels = 0;
+  // device staging grids of ahoc_solve_host (f in, u out), allocated on its first call
+  double *hf = nullptr, *hu = nullptr;
   double kms_top[AHOC_NK] = {0};  // this level only (no coarse levels)
   int64_t kn_top[AHOC_NK] = {0};
 };
@@ -1553,6 +1555,8 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
     p->coarse = nullptr;
   }
   if (p->own_ws && p->ws) cudaFree(p->ws);
+  if (p->hf) cudaFree(p->hf);
+  if (p->hu) cudaFree(p->hu);
   if (p->hhost) cudaFreeHost(p->hhost);
   if (p->scal_h) cudaFreeHost(p->scal_h);
   if (p->act_h) cudaFreeHost(p->act_h);
@@ -2194,6 +2198,39 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
   }
   if (st != AHOC_OK) return fail(st, "GMRES reached max_iters (or refinement did not converge)");
   return AHOC_OK;
+}
+
+// ahoc_solve with host arrays: f of every problem taking part is copied to a
+// device staging grid, the solve runs as ahoc_solve, and u comes back, all on
+// the plan's stream (one cudaMemcpyAsync per problem and direction).
+ahoc_status ahoc_solve_host(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info) {
+  if (!p || !f || !u) return fail(AHOC_EINVAL, "NULL argument");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(AHOC_EINVAL, "tol must be positive");
+  const size_t one = (size_t)p->g.nfull * sizeof(double);
+  const size_t bytes = (size_t)p->g.nb * one;
+  if (!p->hf || !p->hu) {
+    std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+    if (!p->hf && cudaMalloc(&p->hf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->hf = nullptr;
+      return fail(AHOC_ENOMEM, "cudaMalloc of the staging grid for f failed");
+    }
+    if (!p->hu && cudaMalloc(&p->hu, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->hu = nullptr;
+      return fail(AHOC_ENOMEM, "cudaMalloc of the staging grid for u failed");
+    }
+  }
+  for (int b = 0; b < p->g.nb; ++b)
+    if (p->part[b])
+      CK(cudaMemcpyAsync((char*)p->hf + b * one, (const char*)f + b * one, one, cudaMemcpyHostToDevice, p->st));
+  const ahoc_status s = ahoc_solve(p, p->hf, p->hu, tol, info);
+  if (s != AHOC_OK && s != AHOC_ENOCONV) return s;
+  for (int b = 0; b < p->g.nb; ++b)
+    if (p->part[b])
+      CK(cudaMemcpyAsync((char*)u + b * one, (const char*)p->hu + b * one, one, cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return s;
 }
 
 }  // extern "C"

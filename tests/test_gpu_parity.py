@@ -353,3 +353,24 @@ def test_mixed_refines_on_at_the_floor():
     p64 = ahoc.Plan(2, [2048, 2048], d["alpha"], restart=60, max_iters=2000)
     u64, _ = p64.solve(d["f"], tol=1e-12)
     assert float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64)) < TOL_MIXED
+
+
+# --- host-buffer entry point -----------------------------------------------------
+
+@pytest.mark.parametrize("name,N,prec", [("smooth2d", [64, 64], "fp64"), ("sincos3d", [16, 16, 16], "mixed")])
+def test_solve_host_matches_device_solve_and_oracle(name, N, prec):
+    """ahoc_solve_host (f and u in host memory, copies on the plan's stream)
+    gives the device-pointer solve's result bit for bit, and the oracle's."""
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    p = _plan(d, prec=prec)
+    f = _dev(d["f"])
+    u_dev, _ = p.solve(f, tol=1e-12)
+    f_host = torch.as_tensor(np.ascontiguousarray(d["f"]), dtype=torch.float64).reshape(-1).pin_memory()
+    u_host = torch.full_like(f_host, float("nan")).pin_memory()
+    for _ in range(2):
+        p.solve_host(f_host, u_host, tol=1e-12)
+        assert torch.equal(u_host, u_dev.cpu())
+    shape = tuple(n + 1 for n in reversed(N))
+    assert _rel(u_host.numpy().reshape(shape), sol.U) < (TOL_SOLVE if prec == "fp64" else 1e-9)
+    p.close()
