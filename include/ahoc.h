@@ -164,6 +164,13 @@ typedef struct {
                              GMRES restarts or takes more steps than slots.  0: automatic
                              (min(restart, 16) slots); > 0: that many (at most restart);
                              < 0: none.  Each slot holds one field per problem (workspace).  */
+  int unfused;            /* [0] 3D FP64 with constant beta / alpha: 0 runs the Schur matvec in
+                             four full DST passes (the v-equation's right-hand side generated
+                             in the transverse modes inside the solve along z, V/alpha stored
+                             by the last inverse DST, M(V/alpha) fused into the u-solve's first
+                             DST, the traces taken from U-hat); nonzero: the plain form, two
+                             full Poisson solves (eight DST passes) and the trace of physical
+                             U.  Both give the same discrete action.                           */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -282,9 +289,13 @@ ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w);
  * grids needing more (e.g. beyond 1024 x 1024 in 2D or 64^3 in 3D) return
  * AHOC_EUNSUPPORTED before any launch.  The first call on a device looks up
  * the array's device address with that device current; make that first call
- * before any stream capture.  Every call shares the array: calls that
- * overlap on the GPU (other streams or threads) race.  Calls no cudaMalloc,
- * cudaFree or allocating library routine. */
+ * before any stream capture.  Under CUDA's lazy module loading (the default)
+ * that first call is also what creates the 16 MiB array on the device, so a
+ * caller that hands the device's memory to a pool should make it first.
+ * The looked-up address is kept for the life of the process: do not call
+ * this entry point on a device after a cudaDeviceReset of it.  Every call
+ * shares the array: calls that overlap on the GPU (other streams or threads)
+ * race.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const double* lo, const double* hi,
                                  const double* rhs, double* w, void* stream);
 

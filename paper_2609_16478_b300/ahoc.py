@@ -44,7 +44,7 @@ class ahoc_opts(C.Structure):
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
                 ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int),
-                ("variable_beta", C.c_int), ("uhat_slots", C.c_int)]
+                ("variable_beta", C.c_int), ("uhat_slots", C.c_int), ("unfused", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -144,8 +144,9 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0):
+          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0, fused=True):
     o = ahoc_opts()
+    o.unfused = 0 if fused else 1
     o.variable_beta = 1 if variable_beta else 0
     o.uhat_slots = int(uhat_slots)
     o.batch = int(batch)
@@ -207,7 +208,7 @@ class Plan:
                  prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
-                 graphs: bool = True, uhat_slots: int = 0):
+                 graphs: bool = True, uhat_slots: int = 0, fused: bool = True):
         L = lib()
         self.dim = dim
         self.batch = int(batch)
@@ -239,7 +240,7 @@ class Plan:
                         _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"),
                         _ptr(g_L, B * self.ngamma, "g_L"), _ptr(beta, B * self.nfull, "beta"))
         o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
-                  navier, shift, variable_beta, uhat_slots)
+                  navier, shift, variable_beta, uhat_slots, fused)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)

@@ -279,6 +279,23 @@ __device__ __forceinline__ T mstencil2d(const Geom& g, const DstIO<T>& io, int i
   return v;
 }
 
+// LOAD 2 (3D): M(W) with the seven-point weighting M; W = V/alpha in src
+template <typename T>
+__device__ __forceinline__ T mstencil3d(const Geom& g, const DstIO<T>& io, int i, int j, int k) {
+  auto W = [&](int ii, int jj, int kk) { return io.src[g.pad(ii, jj, kk)]; };
+  const T acc = io.Mc * W(i, j, k);
+  T nb = 0;
+  nb += (i > 1) ? W(i - 1, j, k) : qval(io, g.face(0, 0, 0, j, k));
+  nb += (i < g.N[0] - 1) ? W(i + 1, j, k) : qval(io, g.face(0, 1, g.N[0], j, k));
+  nb += (j > 1) ? W(i, j - 1, k) : qval(io, g.face(1, 0, i, 0, k));
+  nb += (j < g.N[1] - 1) ? W(i, j + 1, k) : qval(io, g.face(1, 1, i, g.N[1], k));
+  nb += (k > 1) ? W(i, j, k - 1) : qval(io, g.face(2, 0, i, j, 0));
+  nb += (k < g.N[2] - 1) ? W(i, j, k + 1) : qval(io, g.face(2, 1, i, j, g.N[2]));
+  T v = acc + io.Mn * nb;
+  if (io.src2) v += io.src2[g.pad(i, j, k)];
+  return v;
+}
+
 template <typename T, int LOAD, int STORE>
 __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<T> io,
                                                const typename Cplx<T>::t* __restrict__ tw,
@@ -297,6 +314,7 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
   int64_t* rbase = reinterpret_cast<int64_t*>(wsum + 32);
   int64_t* fbase = rbase + LPC;
   int* rj = reinterpret_cast<int*>(fbase + LPC);
+  int* rk = rj + LPC;
   const int N = (int)g.n0;
   const int nj = g.N[1] - 1;
   const int nrows = nj * (g.kmax - g.kmin);
@@ -308,6 +326,7 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
       rbase[l] = g.pad(0, j, k);
       fbase[l] = g.full(0, j, k);
       rj[l] = j;
+      rk[l] = k;
     } else {
       rbase[l] = -1;
     }
@@ -330,10 +349,14 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
           v.y *= io.lscale;
         }
         if (pos == 0) v.x = 0;
-      } else {
+      } else if (LOAD == 1) {
         const int j = rj[l];
         if (pos > 0) v.x = mstencil2d<T>(g, io, pos, j);
         v.y = mstencil2d<T>(g, io, pos + 1, j);
+      } else {
+        const int j = rj[l], k = rk[l];
+        if (pos > 0) v.x = mstencil3d<T>(g, io, pos, j, k);
+        v.y = mstencil3d<T>(g, io, pos + 1, j, k);
       }
     }
     *reinterpret_cast<C*>(s + l * N + pos) = v;
@@ -502,7 +525,7 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
   const int threads = TPL * LPC;
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
   const int64_t blocks = (nrows + LPC - 1) / LPC;
-  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T) + (size_t)LPC * (2 * sizeof(int64_t) + sizeof(int));
+  const size_t smem = ((size_t)LPC * N + 32) * sizeof(T) + (size_t)LPC * (2 * sizeof(int64_t) + 2 * sizeof(int));
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_dst_x<T, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -547,6 +570,19 @@ cudaError_t launch_dst_x_mload(const Geom& g, T* dst, const T* W, const T* qa, T
   DstIO<T> io{W, qa, ainv_load, Mc, Mn, src2, (T)1};
   return dst_x_impl<T, 1, 0>(g, dst, io, tw, sn, (T)1, st);
 }
+
+// dst = DST_x( M(W) + qa terms at the faces + src2 ), 3D, src = W must not alias dst
+template <typename T>
+cudaError_t launch_dst_x_mload3d(const Geom& g, T* dst, const T* W, const T* qa, T Mc, T Mn, const void* tw,
+                                 const T* sn, cudaStream_t st, const T* src2) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  DstIO<T> io{W, qa, nullptr, Mc, Mn, src2, (T)1};
+  return dst_x_impl<T, 2, 0>(g, dst, io, tw, sn, (T)1, st);
+}
+template cudaError_t launch_dst_x_mload3d<double>(const Geom&, double*, const double*, const double*, double, double,
+                                                  const void*, const double*, cudaStream_t, const double*);
+template cudaError_t launch_dst_x_mload3d<float>(const Geom&, float*, const float*, const float*, float, float,
+                                                 const void*, const float*, cudaStream_t, const float*);
 
 template cudaError_t launch_dst_x_store_ainv<double>(const Geom&, double*, const double*, const void*, const double*,
                                                      cudaStream_t);

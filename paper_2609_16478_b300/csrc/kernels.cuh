@@ -109,6 +109,37 @@ cudaError_t launch_tri2(const Geom& g, double* a, const Mode<double>* modes, con
 template <typename T>
 cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t st);
 
+// Generated right-hand side of the homogeneous v-equation in the (x, y)-mode
+// domain (3D), for mode column (kx, ky) and row k of the solve along z:
+//   d = sx[kx] Ax(ky, k) + sy[ky] By(kx, k) + [k = 1] Zm(kx, ky) + [k = N2-1] Zp(kx, ky)
+// Ax: the x-face sum (odd kx) or difference (even kx) slot of `gen`, By the
+// same for y, Zm / Zp the z-face slots (face layout; fused3d.cu, v3d_prep).
+template <typename T>
+struct VGen3D {
+  const T* gen;  // face layout, problems ngamma apart
+  const T* sx;   // sin(k pi / N0), index k
+  const T* sy;   // sin(k pi / N1), index k
+};
+// the one-thread-per-column solve with the right-hand side generated from G
+template <typename T>
+cudaError_t launch_tri_gen3(const Geom& g, T* a, const Mode<T>* modes, const VGen3D<T>& G, cudaStream_t st);
+
+// fused 3D matvec helpers (fused3d.cu)
+template <typename T>
+cudaError_t launch_v3d_prep(const Geom& g, const Coefs& cf, const double* Q, const double* afinv, T* gen, T* qa,
+                            cudaStream_t st);
+// Tr (face layout, in-face modes) from U-hat; the in-face inverse DSTs follow
+template <typename T>
+cudaError_t launch_trace3d(const Geom& g, const Coefs& cf, const T* Uh, const T* taux, const T* tauy, double* Tr,
+                           cudaStream_t st);
+cudaError_t launch_trace3d_fin(const Geom& g, double* y, const double* Tr, const double* Q, const double* afac,
+                               const double* srcq, cudaStream_t st);
+bool trace3d_red_ok(const Geom& g);
+// dst = DST_x( M(W) + face terms qa + src2 ), 3D (seven-point M); W must not alias dst
+template <typename T>
+cudaError_t launch_dst_x_mload3d(const Geom& g, T* dst, const T* W, const T* qa, T Mc, T Mn, const void* tw,
+                                 const T* sn, cudaStream_t st, const T* src2 = nullptr);
+
 // V-equation right-hand side for (L_h - gam M) V_int = rhs:
 //   rhs = -M f - (L - gam M)_bdry(V_b),  V_b = Q on face points, v_edge on edges/corners.
 template <typename T>

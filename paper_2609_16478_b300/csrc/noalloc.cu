@@ -11,7 +11,10 @@
 // the library keeps until the process exits.  Tables are rebuilt on the
 // device at every call, so consecutive calls with different grids are fine;
 // calls that overlap on the GPU (other streams, other threads) share the
-// array and race.
+// array and race.  Under lazy module loading (CUDA's default) the array is
+// created on a device by the first call there, not when the library loads;
+// its address is looked up once per device and must not be used across a
+// cudaDeviceReset.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -141,7 +144,9 @@ __global__ void k_na_modes(Geom g, Coefs cf, Mode<double>* modes) {
   double scale = 2.0 / g.N[0];
   if (g.dim == 3) scale *= 2.0 / g.N[1];
   const double gam = -b / a;
-  const double disc = apb * (a - 2.0 * b) / (a * a);  // = 1 - 4 gam^2
+  // = 1 - 4 gam^2 >= 0 for the diagonally dominant factors the host admits;
+  // clamped so that rounding near |b/a| = 1/2 cannot give a NaN root
+  const double disc = fmax(apb * (a - 2.0 * b) / (a * a), 0.0);
   const double r = 2 * gam / (1 + sqrt(disc));
   const double sigma = a / (1 + r * r);
   Mode<double> md;
@@ -156,7 +161,10 @@ __global__ void k_na_modes(Geom g, Coefs cf, Mode<double>* modes) {
     md.rj0 = 0;
     md.j0 = 0;
   } else {
-    const double lim = -290.0 * log(10.0) / log(fabs(r));
+    // the plan's cutoff: the last row where |r|^j is above 1e-18, so that the
+    // seed K r^j0 of the boundary correction stays a normal number for any
+    // right-hand side the solve can scale linearly
+    const double lim = -18.0 * log(10.0) / log(fabs(r));
     const int j0 = (lim >= nt) ? nt : (lim < 0 ? 0 : (int)lim);
     md.rinv = 1.0 / r;
     md.rj0 = na_ipow(r, j0);

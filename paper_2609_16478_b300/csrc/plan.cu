@@ -64,6 +64,7 @@ struct Opts {
   double shift = 0.0;    // constant beta / alpha of the v-equation (reference value if variable)
   int varb = 0;          // variable beta / alpha (problems bring beta)
   int uhat = 0;          // U-hat slots of the recovery (0 automatic, < 0 none)
+  int unfused = 0;       // 3D: the plain Schur matvec (eight DST passes) instead of the fused one
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -85,6 +86,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.shift = o->shift;
     d.varb = o->variable_beta ? 1 : 0;
     d.uhat = o->uhat_slots;
+    d.unfused = o->unfused ? 1 : 0;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -309,7 +311,9 @@ struct Layout {
       // mixed precision (AHOC_MIXED only)
       F1, F2, Ru, Rv, U64, V64, twf[3], snf[3], modesf, trif, Rq, dQ, b2, Zb,
       // per-precision side arrays of the fused 2D path
-      afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, tri2, tri2_v, total;
+      afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, tri2, tri2_v,
+      // fused 3D matvec: generator and trace arrays (face layout), y-face trace weights
+      gen3, tr3, tauy, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -414,6 +418,9 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.qy = take(B * qyn * sizeof(double));
   L.R2 = take(B * qyn * sizeof(double));
   L.tau = take(((size_t)g.N[0] + 1) * sizeof(double));
+  L.tauy = take(((size_t)g.N[1] + 1) * sizeof(double));
+  L.gen3 = take(g.dim == 3 ? B * face : 0);
+  L.tr3 = take(g.dim == 3 ? B * face : 0);
   const size_t nmodes = (size_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1);
   L.modes = take(nmodes * sizeof(Mode<double>));
   const bool shifted = o.shift != 0.0;  // the V solves take their own (shifted) mode tables
@@ -538,6 +545,7 @@ struct ahoc_plan {
   double *twx, *snx, *twy, *sny, *twz, *snz, *b, *Q, *r, *tmp, *Kry, *partial, *hdev, *pre, *tri;
   double *stab[3], *ctab[3];
   double *rxm, *rxp, *qy, *R2, *tau;
+  double *tauy = nullptr, *gen3 = nullptr, *tr3 = nullptr;  // fused 3D matvec
   Mode<double>* modes;
   // the V solves' tables: the shifted operator L_h - gam M (aliases of the
   // U tables when gam = 0)
@@ -809,6 +817,52 @@ ahoc_status fused2d(ahoc_plan* p, const F2Arrays<T>& A, const double* q, const T
 
 bool fused_ok(const Geom& g) { return g.dim == 2 && tri_ncols(g) < kChunkedBelow; }
 
+// The fused 3D form (FP64, constant beta/alpha; both z-solves one thread per
+// mode column, whatever the number of columns): fused3d.cu's header gives
+// the algebra.
+bool fused3d_ok(const ahoc_plan* p) {
+  const Geom& g = p->g;
+  return g.dim == 3 && p->o.prec == AHOC_FP64 && !p->o.varb && !p->o.unfused && trace3d_red_ok(g);
+}
+
+// DST-I of face-layout arrays along the in-face axes other than z for the x-
+// and y-faces, along both for the z-faces (the generator and the traces)
+ahoc_status face_dsts3(ahoc_plan* p, double* v, int kid) {
+  const Geom& g = p->g;
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1, nz = g.N[2] - 1;
+  RUN(kid, launch_dst_gen<double>(v + g.face_off[0], 2 * nz, 1, ny, 0, 1, g.N[1], p->twy, p->sny, p->st, g.nb,
+                                  g.ngamma, g.act));
+  RUN(kid, launch_dst_gen<double>(v + g.face_off[2], 2 * nz, 1, nx, 0, 1, g.N[0], p->twx, p->snx, p->st, g.nb,
+                                  g.ngamma, g.act));
+  RUN(kid, launch_dst_gen<double>(v + g.face_off[4], 2 * ny, 1, nx, 0, 1, g.N[0], p->twx, p->snx, p->st, g.nb,
+                                  g.ngamma, g.act));
+  RUN(kid, launch_dst_gen<double>(v + g.face_off[4], 2 * nx, nx, (int64_t)nx * ny, 1, nx, g.N[1], p->twy, p->sny,
+                                  p->st, g.nb, g.ngamma, g.act));
+  return AHOC_OK;
+}
+
+// y = S q (Algorithm 1, SchurMatVec) in 4 full DST passes: the V solve's
+// right-hand side generated in (x, y)-modes inside the z-solve, V back to
+// physical space with V/alpha stored, M(V/alpha) fused into the U solve's
+// first DST, and the traces from U-hat without transforming U back
+ahoc_status fused3d(ahoc_plan* p, const double* q, double* y) {
+  const Geom& g = p->g;
+  const Coefs& cf = p->cf;
+  RUN(AHOC_K_VRHS, launch_v3d_prep<double>(g, cf, q, p->afinv, p->gen3, p->qa, p->st));
+  CKS(face_dsts3(p, p->gen3, AHOC_K_VRHS));
+  const VGen3D<double> G{p->gen3, p->stab[0], p->stab[1]};
+  RUN(AHOC_K_TRI, launch_tri_gen3<double>(g, p->W1, p->modes_v, G, p->st));
+  RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, p->W1, p->twy, p->sny, 1.0, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<double>(g, p->W1, p->ainv, p->twx, p->snx, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_mload3d<double>(g, p->W2, p->W1, p->qa, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
+  RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, p->W2, p->twy, p->sny, 1.0, p->st));
+  RUN(AHOC_K_TRI, launch_tri<double>(g, p->W2, p->modes, p->st));
+  RUNN(AHOC_K_TRACE, 2, launch_trace3d<double>(g, cf, p->W2, p->tau, p->tauy, p->tr3, p->st));
+  CKS(face_dsts3(p, p->tr3, AHOC_K_TRACE));
+  RUN(AHOC_K_TRACE, launch_trace3d_fin(g, y, p->tr3, q, p->afac, nullptr, p->st));
+  return AHOC_OK;
+}
+
 // uhat: where the FP64 fused 2D matvec leaves U in x-modes (NULL: W2)
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y, double* uhat = nullptr) {
   if (p->o.prec == AHOC_MIXED) {
@@ -822,6 +876,7 @@ ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y, double* uhat = 
     if (uhat) A.W2 = uhat;
     return fused2d<double>(p, A, q, nullptr, nullptr, nullptr, y, false);
   }
+  if (fused3d_ok(p)) return fused3d(p, q, y);
   CKS(solve_VU(p, q, nullptr, false));
   RUN(AHOC_K_TRACE, launch_trace<double>(p->g, p->cf, y, p->W2, q, p->afac, nullptr, nullptr, nullptr, p->st));
   return AHOC_OK;
@@ -1218,6 +1273,9 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->qy = at<double>(p, L.qy);
   p->R2 = at<double>(p, L.R2);
   p->tau = at<double>(p, L.tau);
+  p->tauy = at<double>(p, L.tauy);
+  p->gen3 = at<double>(p, L.gen3);
+  p->tr3 = at<double>(p, L.tr3);
   p->modes = at<Mode<double>>(p, L.modes);
   p->modes_v = shifted ? at<Mode<double>>(p, L.modes_v) : p->modes;
   p->gL = at<double>(p, L.gL);
@@ -1351,15 +1409,19 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
       CKC(cudaMemcpyAsync(p->ctab[a], ct.data(), ct.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
       CKC(cudaStreamSynchronize(p->st));
     }
-    // tau_k = sum_m w_m sin(m k pi / N0): one-sided x-face weights in x-modes (fused 2D trace)
-    std::vector<double> tau((size_t)g.N[0] + 1, 0.0);
-    for (int k = 1; k < g.N[0]; ++k) {
-      long double t = 0;
-      for (int m = 1; m <= 3; ++m) t += (long double)cf.w[0][m] * sinl(pi * (long double)(m * k) / g.N[0]);
-      tau[k] = (double)t;
+    // tau_k = sum_m w_m sin(m k pi / N_a): one-sided weights of the a-faces in
+    // a-modes (fused traces; x and, for 3D, y)
+    for (int a = 0; a < 2; ++a) {
+      std::vector<double> tau((size_t)g.N[a] + 1, 0.0);
+      for (int k = 1; k < g.N[a]; ++k) {
+        long double t = 0;
+        for (int m = 1; m <= 3; ++m) t += (long double)cf.w[a][m] * sinl(pi * (long double)(m * k) / g.N[a]);
+        tau[k] = (double)t;
+      }
+      CKC(cudaMemcpyAsync(a == 0 ? p->tau : p->tauy, tau.data(), tau.size() * sizeof(double),
+                          cudaMemcpyHostToDevice, p->st));
+      CKC(cudaStreamSynchronize(p->st));
     }
-    CKC(cudaMemcpyAsync(p->tau, tau.data(), tau.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    CKC(cudaStreamSynchronize(p->st));
   }
   if (tri2_for(g)) {
     const int L2 = tri_chunk_len(g);

@@ -35,8 +35,11 @@ __device__ __forceinline__ float rmul(float q1, float x) { return fmaf(-q1, x, x
 // in FP64), so each recurrence runs in two phases: rows up to the warp's
 // largest j0 with the correction terms (4 operations per row), the rest
 // without them (2 per row).  The split is uniform across the warp.
-template <typename T>
-__global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes) {
+// GEN: the right-hand side of the forward recurrence is generated from G
+// (VGen3D: the v-equation's face terms in (x, y)-modes) instead of read.
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
+                                             VGen3D<T> G) {
   if (g.skip(blockIdx.y)) return;
   a += (int64_t)blockIdx.y * g.npad;
   const int nx = g.N[0] - 1;
@@ -53,13 +56,32 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
   const int jw = __reduce_max_sync(__activemask(), md.j0);  // uniform phase boundary
   constexpr int B = 8;
 
+  // the generator: row j's value is ax A[j - 1] + ay Bv[j - 1] (+ the z-face
+  // terms on the first and last rows), A and Bv strided by ny and nx
+  T ax = 0, ay = 0;
+  const T *A = nullptr, *Bv = nullptr;
+  const int ny = g.N[1] - 1;
+  if (GEN) {
+    const T* gen = G.gen + (int64_t)blockIdx.y * g.ngamma;
+    ax = G.sx[ix];
+    ay = G.sy[iy];
+    A = gen + g.face_off[(ix & 1) ? 0 : 1] + (iy - 1);
+    Bv = gen + g.face_off[(iy & 1) ? 2 : 3] + (ix - 1);
+  }
+  auto rhs = [&](int jj) -> T {
+    if (!GEN) return col[(int64_t)jj * stride];
+    T v = ax * A[(int64_t)(jj - 1) * ny] + ay * Bv[(int64_t)(jj - 1) * nx];
+    if (jj == 1) v += G.gen[(int64_t)blockIdx.y * g.ngamma + g.face_off[4] + m];
+    if (jj == nt) v += G.gen[(int64_t)blockIdx.y * g.ngamma + g.face_off[5] + m];
+    return v;
+  };
   // forward recurrence and the accumulated first value P = sum r^(j-1) w_j
   T w = 0, P = 0, rp = 1;
   int j = 1;
   for (; j + B - 1 <= nt; j += B) {
     T d[B];
 #pragma unroll
-    for (int q = 0; q < B; ++q) d[q] = col[(int64_t)(j + q) * stride];
+    for (int q = 0; q < B; ++q) d[q] = rhs(j + q);
     if (j <= jw) {
 #pragma unroll
       for (int q = 0; q < B; ++q) {
@@ -79,7 +101,7 @@ __global__ void __launch_bounds__(128) k_tri(Geom g, T* __restrict__ a, const Mo
     for (int q = 0; q < B; ++q) col[(int64_t)(j + q) * stride] = d[q];
   }
   for (; j <= nt; ++j) {
-    T d = col[(int64_t)j * stride];
+    T d = rhs(j);
     w = rmul(md.q1, w) + md.s * d;
     if (j <= jw) {
       P += rp * w;
@@ -816,11 +838,23 @@ cudaError_t launch_tri(const Geom& g, T* a, const Mode<T>* modes, cudaStream_t s
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int threads = 128;
   const int64_t blocks = (ncols + threads - 1) / threads;
-  k_tri<T><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, 0, st>>>(g, a, modes);
+  k_tri<T, false><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, 0, st>>>(g, a, modes, VGen3D<T>{});
   return cudaGetLastError();
 }
 
 template cudaError_t launch_tri<double>(const Geom&, double*, const Mode<double>*, cudaStream_t);
 template cudaError_t launch_tri<float>(const Geom&, float*, const Mode<float>*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_tri_gen3(const Geom& g, T* a, const Mode<T>* modes, const VGen3D<T>& G, cudaStream_t st) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  const int64_t ncols = (int64_t)(g.N[0] - 1) * (g.N[1] - 1);
+  const int threads = 128;
+  const int64_t blocks = (ncols + threads - 1) / threads;
+  k_tri<T, true><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, 0, st>>>(g, a, modes, G);
+  return cudaGetLastError();
+}
+template cudaError_t launch_tri_gen3<double>(const Geom&, double*, const Mode<double>*, const VGen3D<double>&,
+                                             cudaStream_t);
 
 }  // namespace ahoc

@@ -537,6 +537,18 @@ def exact_request(spec: RequestSpec, device="cuda"):
     return out.expand((N + 1,) * dim).reshape(-1).contiguous()
 
 
+def request_numpy(spec: RequestSpec) -> Dict[str, object]:
+    """A request's alpha, f and exact u on the host (numpy, full-grid shape
+    reversed as ``sample`` returns it; every boundary datum of a request is
+    zero), for the CPU oracle."""
+    d = sample_request(spec, device="cpu", with_exact=True)
+    shape = (spec.N + 1,) * spec.dim
+    out = {k: d[k] for k in ("dim", "N", "lo", "hi", "name")}
+    for k in ("alpha", "f", "u_exact"):
+        out[k] = d[k].numpy().reshape(shape)
+    return out
+
+
 def sample_request(spec: RequestSpec, device="cuda", out_alpha=None, out_f=None, with_exact: bool = False,
                    M: int = 6, K: int = 4, A: float = 0.5) -> Dict[str, object]:
     """alpha and f of a request on its full grid (float64 tensors on device);

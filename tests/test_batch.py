@@ -7,9 +7,11 @@ batch, so results, iteration counts and residuals must be identical to a
 single-problem plan's.
 """
 
+import numpy as np
 import pytest
 import torch
 
+from oracle import coupled
 from paper_2609_16478_b300 import ahoc, inputs
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +47,24 @@ def test_batch_equals_solo(dim, N, prec):
         assert infos[b]["refine_steps"] == info["refine_steps"]
         q, _ = ps.last_qv(with_v=False)
         assert torch.equal(qb[b * pb.ngamma:(b + 1) * pb.ngamma], q)
+
+
+@pytest.mark.parametrize("dim,N,prec", [(2, 64, "fp64"), (2, 64, "mixed"), (3, 16, "fp64"), (3, 16, "mixed")])
+def test_batch_matches_oracle(dim, N, prec):
+    """Every problem of a batched solve against the CPU oracle's direct solve
+    of the same request (relative L2 on the full grid)."""
+    B = 3
+    specs = [inputs.RequestSpec(r, dim, N, MS[dim][r % 3], 0.0) for r in range(B)]
+    ds = [inputs.sample_request(s, device="cuda") for s in specs]
+    nf = (N + 1) ** dim
+    pb = ahoc.Plan(dim, [N] * dim, torch.cat([d["alpha"] for d in ds]), prec=prec, batch=B)
+    ub, infos = pb.solve(torch.cat([d["f"] for d in ds]), tol=1e-12)
+    for b, s in enumerate(specs):
+        h = inputs.request_numpy(s)
+        sol = coupled.solve_direct(coupled.assemble(h), h)
+        u = ub[b * nf:(b + 1) * nf].cpu().numpy().reshape(sol.U.shape)
+        rel = np.linalg.norm(u - sol.U) / np.linalg.norm(sol.U)
+        assert rel < (1e-10 if prec == "fp64" else 1e-9), (b, rel, infos[b])
 
 
 @pytest.mark.parametrize("dim,N,prec", [(2, 128, "fp64"), (3, 32, "mixed")])

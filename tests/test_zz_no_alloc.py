@@ -29,9 +29,16 @@ def _noalloc(dim, N, lo, hi, rhs, w):
                                   C.c_void_p(st.cuda_stream))
 
 
-@pytest.mark.parametrize("N,lo,hi", [((1024, 1024), (0.0, 0.0), (1.0, 1.0)),
-                                     ((32, 256), (0.0, -0.5), (1.0, 0.3)),
-                                     ((64, 32, 16), (0.0, 0.0, 0.0), (1.0, 2.0, 0.5))])
+KNOALLOC = 16 << 20
+CASES = [((1024, 1024), (0.0, 0.0), (1.0, 1.0)),
+         ((32, 256), (0.0, -0.5), (1.0, 0.3)),
+         ((64, 32, 16), (0.0, 0.0, 0.0), (1.0, 2.0, 0.5)),
+         # more than 65536 transverse modes (the one-thread-per-column
+         # tridiagonal kernel), equal spacing 1/4096 on every axis
+         ((4096, 32, 8), (0.0, 0.0, 0.0), (1.0, 1.0 / 128, 1.0 / 512))]
+
+
+@pytest.mark.parametrize("N,lo,hi", CASES)
 def test_noalloc_matches_plan_on_two_calls(N, lo, hi):
     dim = len(N)
     nfull = int(np.prod([n + 1 for n in N]))
@@ -46,11 +53,34 @@ def test_noalloc_matches_plan_on_two_calls(N, lo, hi):
         free0 = torch.cuda.mem_get_info()[0]
         assert _noalloc(dim, N, lo, hi, rhs, w) == ahoc.AHOC_OK
         torch.cuda.synchronize()
-        if call == 1:
-            # no device memory was taken by the call (the static array loaded with the library)
-            assert torch.cuda.mem_get_info()[0] == free0
+        grown = free0 - torch.cuda.mem_get_info()[0]
+        if call == 0:
+            # under lazy module loading the first call in the process creates
+            # the static array (and loads the module's code, in 2 MiB pages)
+            assert grown <= KNOALLOC + (4 << 20), grown
+        else:
+            # later calls take no device memory
+            assert grown == 0, grown
         rel = float(torch.linalg.norm(w - ref) / torch.linalg.norm(ref))
         assert rel < 1e-12, (call, rel)
+
+
+@pytest.mark.parametrize("N,lo,hi", [CASES[0], CASES[3]])
+def test_noalloc_tiny_rhs_matches_plan(N, lo, hi):
+    """The solve is linear: a right-hand side of size 1e-30 (a late correction
+    solve on a fine grid) gets the plan's result to the same relative accuracy."""
+    dim = len(N)
+    nfull = int(np.prod([n + 1 for n in N]))
+    nint = int(np.prod([n - 1 for n in N]))
+    plan = ahoc.Plan(dim, N, torch.ones(nfull, dtype=torch.float64, device="cuda"), lo=lo, hi=hi)
+    rng = np.random.default_rng(13)
+    rhs = torch.as_tensor(rng.normal(size=nint) * 1e-30, dtype=torch.float64).cuda()
+    ref = plan.poisson(rhs)
+    w = torch.full_like(rhs, float("nan"))
+    assert _noalloc(dim, N, lo, hi, rhs, w) == ahoc.AHOC_OK
+    torch.cuda.synchronize()
+    rel = float(torch.linalg.norm(w - ref) / torch.linalg.norm(ref))
+    assert rel < 1e-12, rel
 
 
 def test_noalloc_rejects_oversized_grid():
