@@ -352,16 +352,28 @@ HEADLINE = ("fourier3d_k32", 1024)   # 3D 1024^3, u = prod sin^2(pi x_a) sin(32 
 VARIANT_2D = ("fourier2d", 4096)      # 2D 4096^2, 8-mode coefficient in [0.6, 1.4]
 
 
+def _grid_str(N, dim):
+    if isinstance(N, (list, tuple)):
+        return "x".join(str(n) for n in N) if len(set(N)) > 1 else "%d^%d" % (N[0], dim)
+    return "%d^%d" % (N, dim)
+
+
 def _workload_name(name, N, dim):
+    gs = _grid_str(N, dim)
     if name == "fourier3d_k32":
         return ("3D variable-coefficient clamped biharmonic, high wavenumber (u = prod sin^2(pi x_a) sin(32 pi x_a), "
-                "coefficient 1 + 0.5 * 6 seeded Fourier modes) N=%d^3" % N)
+                "coefficient 1 + 0.5 * 6 seeded Fourier modes) N=%s" % gs)
     if name == "fourier3d":
-        return "3D variable-coefficient clamped biharmonic (Fourier coefficient, 6 modes) N=%d^3" % N
-    return "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%d^%d" % (N, dim)
+        return "3D variable-coefficient clamped biharmonic (Fourier coefficient, 6 modes) N=%s" % gs
+    return "2D variable-coefficient clamped biharmonic (Fourier coefficient, 8 modes) N=%s" % gs
 
 
 def _interior(N, dim):
+    if isinstance(N, (list, tuple)):
+        out = 1
+        for n in N:
+            out *= n - 1
+        return out
     return (N - 1) ** dim
 
 
@@ -422,7 +434,7 @@ def _mixed_variant(data, dev, stream, args, u_ref):
 
     from paper_2609_16478_b300 import ahoc
 
-    N = data["N"][0]
+    N = list(data["N"])
     dim = data["dim"]
     f = data["f"].reshape(-1).contiguous()
     pm = ahoc.plan_for(data, device=dev, restart=args.restart, max_iters=args.max_iters, prec="mixed",
@@ -491,10 +503,11 @@ def run_ours(args, rank, world, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    name, N = args.workload, args.n
+    name = args.workload
     prob = inputs.config_problem(name)
     dim = prob.dim
-    data = inputs.sample(prob, [N] * dim, backend="torch", device=dev)
+    N = [int(v) for v in args.shape.split("x")] if args.shape else [args.n] * dim
+    data = inputs.sample(prob, N, backend="torch", device=dev)
     data.pop("v_exact", None)
     # the plans' own stream: GMRES iterations are replayed as CUDA graphs (not
     # possible on the legacy default stream); kernel timing uses separate,
@@ -554,17 +567,19 @@ def run_ours(args, rank, world, local):
     # the roofline is taken on the finest grid's dominant DST class (coarse levels have other N)
     dk = max(("dst_x", "dst_y"), key=lambda k: kms_top[k])
     avg_ms = kms_top[dk] / max(1, kn_top[dk])
-    lines = (N - 1) ** (dim - 1)
-    flops = dst_flops_per_line(N) * lines          # one launch transforms every line of the field along one axis
+    ax = 0 if dk == "dst_x" else 1
+    Nl = N[ax]                                      # line length along the transform axis
+    lines = _interior(N, dim) // (Nl - 1)
+    flops = dst_flops_per_line(Nl) * lines         # one launch transforms every line of the field along one axis
     achieved = flops / (avg_ms / 1e3) / 1e12
     peak = FP64_PEAK_TFLOPS_DERIVED
     roof = {"kernel": "k_%s<double> (DST-I along %s, FP64)" % (dk, dk[-1]), "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_source": "derived, of the FP64 pipe: 148 SMs x 2 FP64 FMA lanes per clock (ncu's FP64 pipe "
                            "peak) x 2 flop x 2.032 GHz; MEASURED_PEAKS.json has no FP64 figure",
-            "traffic": PROFILED_TRAFFIC.get((name, N, dk)), "avg_launch_ms": avg_ms, "launches": kn_top[dk],
-            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 16 * N * lines,
-            "hbm_achieved_GBs": 16 * N * lines / (avg_ms / 1e3) / 1e9, "hbm_peak_GBs": _peaks().get("hbm_gbs"),
+            "traffic": PROFILED_TRAFFIC.get((name, tuple(N), dk)), "avg_launch_ms": avg_ms, "launches": kn_top[dk],
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 16 * Nl * lines,
+            "hbm_achieved_GBs": 16 * Nl * lines / (avg_ms / 1e3) / 1e9, "hbm_peak_GBs": _peaks().get("hbm_gbs"),
             "share_of_step": kms[dk] / sum(kms.values()),
             "top_kernel_class_by_time": max(kms, key=lambda k: kms[k]),
             "flop_count": "algorithmic flops of the N/2-point complex FFT with DST-I pre- and post-processing "
@@ -589,7 +604,9 @@ def run_ours(args, rank, world, local):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d direct solves (assembly + SuperLU) of the same workload at N=%d, %.1f s in all; "
                          "single-threaded, %d host cores visible" % (reps, args.cpu_n, tot, _cores())}
-    nbytes = f_numel = (N + 1) ** dim
+    f_numel = 1
+    for n in N:
+        f_numel *= n + 1
     nbytes = 8 * f_numel
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -598,12 +615,12 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": _workload_name(name, N, dim) + ", %s, GMRES tol %g"
                                % ("FP64" if args.prec == "fp64" else "mixed FP32/FP64", args.tol),
-                   "dim": dim, "N": N, "dof_per_solve": dof, "tol": args.tol,
+                   "dim": dim, "N": N[0] if len(set(N)) == 1 else N, "dof_per_solve": dof, "tol": args.tol,
                    "gmres_iters": infos[-1]["iters"], "coarse_levels": infos[-1]["levels"],
                    "coarse_gmres_iters": infos[-1]["coarse_iters"], "err_inf_vs_exact": err,
                    "rel_resid": infos[-1]["rel_resid"], "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (one FP64 field of this grid is %.1f GB); no flush"
-                         % (8 * N ** dim / 1e9),
+                   "l2": "inputs larger than L2 (one FP64 field of this grid is %.2f GB); no flush"
+                         % (8 * f_numel / 1e9),
                    "cuda_graphs": "GMRES iterations replayed as CUDA graphs on the plan's own stream",
                    "kernel_timing": "kernel_ms_per_step and roofline from one more solve on a plan with every "
                                     "launch bracketed by CUDA events (plain launches)"},
@@ -632,6 +649,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=HEADLINE[0])
     ap.add_argument("--n", type=int, default=HEADLINE[1])
+    ap.add_argument("--shape", default=None, help="grid as N0xN1[xN2] (profiling cases); overrides --n")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--prec", choices=["fp64", "mixed"], default="fp64", help="precision of the headline solves")
     ap.add_argument("--restart", type=int, default=100)

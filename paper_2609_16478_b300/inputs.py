@@ -36,7 +36,7 @@ X = sp.symbols("x y z", real=True)
 
 __all__ = [
     "Problem", "fourier_alpha", "config_problem", "sample", "face_sizes",
-    "n_gamma", "WORKLOADS",
+    "n_gamma", "WORKLOADS", "TriProblem", "triharmonic_problem", "sample_triharmonic",
 ]
 
 
@@ -440,6 +440,103 @@ def sample(prob: Problem, N: Sequence[int], lo=None, hi=None, backend: str = "nu
 def _to_t(a, device):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+
+
+# ----------------------------------------------------------------------------
+# triharmonic problems: Lap^3 u = f (the paper's triharmonic extension, Table 5)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class TriProblem:
+    """Lap^3 u = f in a box with u, u_n and u_nn given on the clamped faces and
+    u, Lap u and Lap^2 u given on the other (simply supported) faces; all data
+    are traces of the exact u."""
+
+    name: str
+    dim: int
+    u: sp.Expr
+    clamped: Tuple[int, ...] = (0,)            # face ids 2 * axis + side
+    lo: Tuple[float, ...] = (0.0, 0.0, 0.0)
+    hi: Tuple[float, ...] = (1.0, 1.0, 1.0)
+
+
+def triharmonic_problem(name: str) -> TriProblem:
+    """"tri3d_5_1_5", "tri3d_25_5_25": u = sin(k1 x) cos(k2 y) sin(k3 z),
+    clamped on x = 0 (the setting of Table 5); "tripoly3d", "tripoly2d":
+    polynomials of degree 5 with nonzero data of every kind, clamped on two
+    faces; "trisin2d": a smooth 2D solution clamped on x = 0."""
+    x, y, z = X
+    if name.startswith("tri3d_"):
+        k1, k2, k3 = (int(v) for v in name.split("_")[1:4])
+        return TriProblem(name, 3, sp.sin(k1 * x) * sp.cos(k2 * y) * sp.sin(k3 * z), clamped=(0,))
+    if name == "tripoly3d":
+        u = x ** 5 - 2 * x ** 3 * y ** 2 + x * y * z ** 3 + y ** 4 * z - z ** 5 / 3 + x ** 2 * z + y - 1
+        return TriProblem(name, 3, u, clamped=(0, 3))
+    if name == "tripoly2d":
+        u = x ** 5 - 3 * x ** 3 * y ** 2 + 2 * x * y ** 4 + y ** 5 / 5 + x ** 2 * y - x + 2
+        return TriProblem(name, 2, u, clamped=(0, 2))
+    if name == "trisin2d":
+        return TriProblem(name, 2, sp.sin(3 * x + sp.Rational(1, 4)) * sp.cos(2 * y), clamped=(0,))
+    raise KeyError(name)
+
+
+def sample_triharmonic(prob: TriProblem, N: Sequence[int], lo=None, hi=None, backend: str = "numpy",
+                       device=None) -> Dict[str, object]:
+    """Sample a triharmonic problem: full-grid arrays f (= Lap^3 u), u_exact, and
+    the boundary data g_D (u), lap_gD (Lap u) and bilap (Lap^2 u), each with
+    its interior entries 0; face arrays g_N (outward normal derivative), g_NN
+    (second normal derivative) and lapt_w (2 Lap_t u_nn + Lap_t^2 u, Lap_t the
+    sum of the tangential second derivatives), in the layouts of ``sample``."""
+    dim = prob.dim
+    N = [int(n) for n in N]
+    lo = tuple(lo) if lo is not None else prob.lo[:dim]
+    hi = tuple(hi) if hi is not None else prob.hi[:dim]
+    xs = X[:dim]
+    u = prob.u
+    lap = lambda e: sum(sp.diff(e, v, 2) for v in xs)  # noqa: E731
+    lu = lap(u)
+    l2u = lap(lu)
+    out: Dict[str, object] = {"dim": dim, "N": N, "lo": lo, "hi": hi, "name": prob.name,
+                              "clamped": tuple(prob.clamped), "triharmonic": True}
+
+    def full(expr):
+        return _eval_full(_lamb(expr, dim, backend), N, lo, hi, dim, backend, device)
+
+    out["f"] = full(lap(l2u))
+    u_full = full(u)
+    cnt = _edge_mask(N, dim)
+    if backend == "numpy":
+        bm = cnt > 0
+        out["g_D"] = np.where(bm, u_full, 0.0)
+        out["lap_gD"] = np.where(bm, full(lu), 0.0)
+        out["bilap"] = np.where(bm, full(l2u), 0.0)
+    else:
+        import torch
+        bm = torch.from_numpy(cnt).to(device) > 0
+        zero = torch.zeros_like(u_full)
+        out["g_D"] = torch.where(bm, u_full, zero)
+        out["lap_gD"] = torch.where(bm, full(lu), zero)
+        out["bilap"] = torch.where(bm, full(l2u), zero)
+    out["u_exact"] = u_full
+    gN, gNN, lw = [], [], []
+    for a in range(dim):
+        tang = [v for b, v in enumerate(xs) if b != a]
+        lt = lambda e: sum(sp.diff(e, v, 2) for v in tang)  # noqa: E731
+        unn = sp.diff(u, xs[a], 2)
+        w = 2 * lt(unn) + lt(lt(u))
+        for side in (0, 1):
+            pc = face_coords(N, lo, hi, a, side)
+
+            def ev(e):
+                return np.broadcast_to(np.asarray(_lamb(e, dim, "numpy")(*pc), dtype=float), pc[0].shape).copy()
+            du = ev(sp.diff(u, xs[a]))
+            gN.append(-du if side == 0 else du)
+            gNN.append(ev(unn))
+            lw.append(ev(w))
+    for key, arr in (("g_N", gN), ("g_NN", gNN), ("lapt_w", lw)):
+        v = np.concatenate(arr)
+        out[key] = v if backend == "numpy" else _to_t(v, device)
+    return out
 
 
 # ----------------------------------------------------------------------------
