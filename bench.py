@@ -272,9 +272,10 @@ def paper_suite(args, dev):
 def serving_variant(args, dev):
     """The serving workload: a seeded Poisson stream of requests of mixed
     dimension, size, coefficient and right-hand side, at 80% of the measured
-    sequential mixed-path capacity; the batched mixed-precision server
-    against one-at-a-time plain FP64 solves of the same stream."""
-    import numpy as np
+    sequential FP64 capacity (below the capacity of every arm), served three
+    ways: the batched mixed-precision server, the same server in FP64 (same
+    workers and batches: the precision gain apart from the batching gain),
+    and one-at-a-time FP64 solves."""
     import torch
 
     from paper_2609_16478_b300 import ahoc, autotune, inputs, serving
@@ -283,19 +284,20 @@ def serving_variant(args, dev):
     p3 = 0.3
     mix = {(2, n): (1 - p3) / len(inputs.SERVE_2D) for n in inputs.SERVE_2D}
     mix.update({(3, n): p3 / len(inputs.SERVE_3D) for n in inputs.SERVE_3D})
-    # sequential capacity of the mixed path, one warm solve per shape
-    t_seq = {}
-    for (dim, n) in mix:
-        d = inputs.sample_request(inputs.RequestSpec(10 ** 6, dim, n, (1,) * dim, 0.0), device=dev)
-        p = ahoc.Plan(dim, [n] * dim, d["alpha"], prec="mixed", restart=60, max_iters=2000)
-        p.solve(d["f"], tol=tol)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p.solve(d["f"], tol=tol)
-        t_seq[(dim, n)] = time.perf_counter() - t0
-        p.close()
-    cap = 1.0 / sum(mix[k] * t_seq[k] for k in mix)
-    rate = 0.8 * cap
+    # sequential capacity per precision, one warm solve per shape
+    t_seq = {"mixed": {}, "fp64": {}}
+    for prec in t_seq:
+        for (dim, n) in mix:
+            d = inputs.sample_request(inputs.RequestSpec(10 ** 6, dim, n, (1,) * dim, 0.0), device=dev)
+            p = ahoc.Plan(dim, [n] * dim, d["alpha"], prec=prec, restart=60, max_iters=2000)
+            p.solve(d["f"], tol=tol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.solve(d["f"], tol=tol)
+            t_seq[prec][(dim, n)] = time.perf_counter() - t0
+            p.close()
+    cap = {prec: 1.0 / sum(mix[k] * t_seq[prec][k] for k in mix) for prec in t_seq}
+    rate = 0.8 * min(cap.values())
     specs = inputs.request_stream(args.serve_requests, rate, seed=5)
 
     def warm_specs(batch_for, size, rid0):
@@ -321,30 +323,40 @@ def serving_variant(args, dev):
         torch.cuda.empty_cache()
         return recs, serving.summarize(recs)
 
-    # the mixed server takes the tuner's batch sizes and launch shapes
+    # the batched servers take the tuner's batch sizes (and, in mixed, its launch shapes)
     cache = autotune.load(args.tune_cache)
     autotune.apply(cache)
-    ra, sa = arm("mixed", args.serve_workers, autotune.batch_for(cache, "mixed", serving.default_batch))
-    for k in cache:  # the FP64 arm runs with the built-in shapes
+    bfor = autotune.batch_for(cache, "mixed", serving.default_batch)
+    ra, sa = arm("mixed", args.serve_workers, bfor)
+    for k in cache:  # the FP64 arms run with the built-in shapes
         dim, n, _ = k.split(":")
         for kind in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS):
             ahoc.lib().ahoc_tune_set(kind, int(dim), int(n), ahoc.AHOC_MIXED, 0)
-    rb, sb = arm("fp64", 1, lambda k: 1)
+    rb, sb = arm("fp64", args.serve_workers, bfor)
+    rc, sc = arm("fp64", 1, lambda k: 1)
     ea = {r.rid: r.err_inf for r in ra}
     eb = {r.rid: r.err_inf for r in rb}
-    ratio = max(ea[i] / eb[i] for i in ea if eb[i] > 0)
+    ec = {r.rid: r.err_inf for r in rc}
+    ratio = max(ea[i] / ec[i] for i in ea if ea[i] is not None and ec[i])
     return {
-        "workload": "%d requests, Poisson arrivals (seed 5) at %.1f req/s = 80%% of the sequential mixed-path "
-                    "capacity %.1f req/s; 2D N in %s (p=0.7), 3D N in %s; per-request Fourier coefficient "
-                    "(M=6, K=4, A=0.5, seed = request id) and u = prod sin^2(pi x) cos(m pi x), m in 0..4; "
-                    "Schur tol %g" % (len(specs), rate, cap, list(inputs.SERVE_2D), list(inputs.SERVE_3D), tol),
+        "workload": "%d requests, Poisson arrivals (seed 5) at %.1f req/s = 80%% of the sequential FP64 capacity "
+                    "%.1f req/s (sequential mixed capacity %.1f req/s); 2D N in %s (p=0.7), 3D N in %s; per-request "
+                    "Fourier coefficient (M=6, K=4, A=0.5, seed = request id) and u = prod sin^2(pi x) cos(m pi x), "
+                    "m in 0..4; Schur tol %g"
+                    % (len(specs), rate, cap["fp64"], cap["mixed"], list(inputs.SERVE_2D), list(inputs.SERVE_3D), tol),
+        "latency": "arrival to the solution in device memory; parts: queue wait, request data (synthesised on the "
+                   "worker's stream from closed forms and loaded into the plan), solve; the error check against the "
+                   "exact u runs after it",
         "batched_mixed": dict(sa, workers=args.serve_workers, plan_slots_per_shape=args.serve_slots,
                               batch="per shape from the autotuner: %s" % {k: v["batch"] for k, v in cache.items()}),
-        "sequential_fp64": dict(sb, workers=1, batch=1),
-        "p99_speedup": sb["p99_ms"] / sa["p99_ms"], "dof_per_s_ratio": sa["dof_per_s"] / sb["dof_per_s"],
+        "batched_fp64": dict(sb, workers=args.serve_workers, batch="as batched_mixed"),
+        "sequential_fp64": dict(sc, workers=1, batch=1),
+        "p99_speedup_mixed_over_batched_fp64": sb["p99_ms"] / sa["p99_ms"],
+        "p99_speedup_mixed_over_sequential_fp64": sc["p99_ms"] / sa["p99_ms"],
+        "dof_per_s_ratio_mixed_over_batched_fp64": sa["dof_per_s"] / sb["dof_per_s"],
         "max_err_ratio_mixed_over_fp64": ratio,
-        "max_err_inf": max(max(ea.values()), max(eb.values())),
-        "seq_mixed_ms_per_shape": {"%dD N=%d" % k: 1e3 * v for k, v in t_seq.items()},
+        "max_err_inf": max(max(v for v in e.values() if v is not None) for e in (ea, eb, ec)),
+        "seq_ms_per_shape": {prec: {"%dD N=%d" % k: 1e3 * v for k, v in t.items()} for prec, t in t_seq.items()},
     }
 
 
@@ -667,8 +679,9 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-tol", type=float, default=1e-12)
     ap.add_argument("--serve-slots", type=int, default=8, help="plans per shape in the serving pool")
-    ap.add_argument("--suite", choices=["bench", "paper"], default="bench",
-                    help="paper: the paper's printed workloads at their largest sizes, one JSON line each")
+    ap.add_argument("--suite", choices=["bench", "paper", "serving"], default="bench",
+                    help="paper: the paper's printed workloads at their largest sizes, one JSON line each; "
+                         "serving: the serving workload alone")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache (default: the shipped B300 choices)")
     args = ap.parse_args()
     if args.tune_cache is None:
@@ -686,6 +699,11 @@ def main():
         import torch
         torch.cuda.set_device(local)
         paper_suite(args, torch.device("cuda", local))
+        return
+    if args.suite == "serving":
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"suite": "serving", **serving_variant(args, torch.device("cuda", local))}), flush=True)
         return
     if world > 1:
         import torch

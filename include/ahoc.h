@@ -80,6 +80,13 @@ typedef struct {
   const double* g_L;     /* face array: Laplace u on the face interiors; read on Navier faces
                             only (opts.navier), where v = alpha g_L is data (Eq. 2)              */
   const double* beta;    /* full grid: beta of Eq. 1, read when opts.variable_beta is set        */
+  /* triharmonic class only (opts.triharmonic; the paper's triharmonic extension, Sec. 4.2): */
+  const double* lap_gD;  /* full grid; boundary entries read: Laplace u on the whole boundary    */
+  const double* bilap;   /* full grid; boundary entries read: Laplace^2 u on the simply
+                            supported faces and on every edge and corner                        */
+  const double* g_NN;    /* face array: second normal derivative of u on the clamped faces      */
+  const double* lapt_w;  /* face array: 2 Lap_t u_nn + Lap_t^2 u on the clamped faces, Lap_t the
+                            sum of the tangential second derivatives                            */
 } ahoc_bdata;
 
 /* Options; a NULL pointer selects the defaults given in brackets. */
@@ -171,6 +178,29 @@ typedef struct {
                              DST, the traces taken from U-hat); nonzero: the plain form, two
                              full Poisson solves (eight DST passes) and the trace of physical
                              U.  Both give the same discrete action.                           */
+  int triharmonic;        /* [0] problem class: nonzero solves Laplace^3 u = f (the paper's
+                             triharmonic extension, Sec. 4.2, Table 5) in the mixed form
+                             Laplace u = v, Laplace v = w, Laplace w = f, each discretised
+                             with the compact scheme (L_h X = M(Laplace x)); the augmented
+                             unknowns Q are w = Laplace^2 u on the faces.  The faces in
+                             opts.navier are simply supported (u, Laplace u, Laplace^2 u
+                             given: their Schur rows are -I, right-hand side -bilap), the
+                             others clamped (u, u_n, u_nn given; the augmented equation is
+                             Laplace^2 u = u_ssss + 2 Lap_t u_nn + Lap_t^2 u with u_ssss
+                             one-sided from U_0 = g_D, U_1..U_4, u_s = -g_N and u_nn = g_NN,
+                             exact for polynomials of degree 6 in s).  Each Schur action
+                             runs three Poisson solves.  FP64 only, alpha = 1 (alpha may be
+                             NULL), no beta, no preconditioner, no nested guess; f is the
+                             right-hand side of Laplace^3 u = f; ahoc_last_qv returns Q
+                             only.                                                             */
+  int auto_shift;         /* [0] nonzero: ahoc_plan_create derives the beta class of Eq. 1 from
+                             the data instead of opts.shift / opts.variable_beta: with
+                             gamma = beta / alpha over every point of every problem
+                             (bd->beta; none: beta = 0), one value everywhere gives the
+                             constant shift gamma, several give variable beta with the mean
+                             of gamma as the reference shift.  Uses a few KB of temporary
+                             device memory (cudaMalloc) and synchronises the stream; with it,
+                             ahoc_workspace_bytes sizes for the variable-beta class.          */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess */
@@ -193,7 +223,7 @@ typedef struct {
   double refine_hist[16]; /* AHOC_MIXED: relative Schur residual before each correction, then at exit */
   int inner_iters[16];    /* AHOC_MIXED: GMRES iterations of each correction solve              */
   double refine_du[16];   /* AHOC_MIXED: ||dU||_2 / ||U||_2 of each correction (U after it)    */
-  ahoc_status status;     /* this problem's outcome (AHOC_OK or AHOC_ENOCONV)                   */
+  ahoc_status status;     /* this problem's outcome (AHOC_OK, AHOC_ENOCONV or AHOC_ENUMERIC)    */
   int vsolve_iters;       /* opts.variable_beta, FP64: BiCGSTAB iterations over all v-solves   */
 } ahoc_info;
 
@@ -229,7 +259,11 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
  * A batched plan solves the problems taking part; f and u hold one grid per
  * problem of the plan (the others are neither read nor written).
  * Synchronises the plan's stream (it reads residual norms) and returns when
- * u is written.  AHOC_ENOCONV: u holds the solution for the best iterate. */
+ * u is written.  AHOC_ENOCONV: u holds the solution for the best iterate.
+ * A problem whose data or iterates turn NaN or Inf is masked out of the
+ * batch with info[b].status = AHOC_ENUMERIC (its u is not meaningful); the
+ * other problems are solved as if it were absent, and the call returns
+ * AHOC_ENUMERIC. */
 ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info);
 
 /* ahoc_solve with HOST arrays (Algorithm 1, Main procedure, as ahoc_solve):

@@ -32,7 +32,8 @@ SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve
 
 class ahoc_bdata(C.Structure):
     _fields_ = [("g_D", C.c_void_p), ("g_N", C.c_void_p), ("lapt_gD", C.c_void_p), ("v_edge", C.c_void_p),
-                ("g_L", C.c_void_p), ("beta", C.c_void_p)]
+                ("g_L", C.c_void_p), ("beta", C.c_void_p), ("lap_gD", C.c_void_p), ("bilap", C.c_void_p),
+                ("g_NN", C.c_void_p), ("lapt_w", C.c_void_p)]
 
 
 AHOC_NK = 8
@@ -44,7 +45,8 @@ class ahoc_opts(C.Structure):
                 ("refine_tol", C.c_double), ("timing", C.c_int), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
                 ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int),
-                ("variable_beta", C.c_int), ("uhat_slots", C.c_int), ("unfused", C.c_int)]
+                ("variable_beta", C.c_int), ("uhat_slots", C.c_int), ("unfused", C.c_int),
+                ("triharmonic", C.c_int), ("auto_shift", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -144,9 +146,12 @@ def _prec(prec) -> int:
 
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
-          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0, fused=True):
+          batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0, fused=True,
+          triharmonic=False, auto_shift=False):
     o = ahoc_opts()
+    o.auto_shift = 1 if auto_shift else 0
     o.unfused = 0 if fused else 1
+    o.triharmonic = 1 if triharmonic else 0
     o.variable_beta = 1 if variable_beta else 0
     o.uhat_slots = int(uhat_slots)
     o.batch = int(batch)
@@ -168,11 +173,12 @@ def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1
 
 
 def workspace_bytes(dim: int, N: Sequence[int], restart: int = 100, prec: int = AHOC_FP64, levels: int = -1,
-                    batch: int = 1, shift: float = 0.0, variable_beta: bool = False, uhat_slots: int = 0) -> int:
+                    batch: int = 1, shift: float = 0.0, variable_beta: bool = False, uhat_slots: int = 0,
+                    triharmonic: bool = False, auto_shift: bool = False) -> int:
     L = lib()
     n = (C.c_int64 * dim)(*N)
     o = _opts(prec, 500, restart, 1, levels=levels, batch=batch, shift=shift, variable_beta=variable_beta,
-              uhat_slots=uhat_slots)
+              uhat_slots=uhat_slots, triharmonic=triharmonic, auto_shift=auto_shift)
     out = C.c_size_t(0)
     _check(L.ahoc_workspace_bytes(dim, n, C.byref(o), C.byref(out)), "ahoc_workspace_bytes")
     return int(out.value)
@@ -202,9 +208,10 @@ class Plan:
     the library, so device memory comes from PyTorch's allocator.
     """
 
-    def __init__(self, dim: int, N: Sequence[int], alpha: torch.Tensor, lo=None, hi=None,
+    def __init__(self, dim: int, N: Sequence[int], alpha: Optional[torch.Tensor], lo=None, hi=None,
                  g_D=None, g_N=None, lapt_gD=None, v_edge=None, g_L=None, navier: int = 0, shift: float = 0.0,
-                 beta=None,
+                 beta=None, triharmonic: bool = False, lap_gD=None, bilap=None, g_NN=None, lapt_w=None,
+                 device=None, auto_shift: bool = False,
                  prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
@@ -229,18 +236,21 @@ class Plan:
             self.ngamma += 2 * s
         prec = _prec(prec)
         self.prec = prec
-        self.device = alpha.device
+        self.device = alpha.device if alpha is not None else torch.device(device or "cuda")
         B = self.batch
-        variable_beta = beta is not None
-        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift, variable_beta, uhat_slots)
+        variable_beta = beta is not None and not auto_shift
+        nb = workspace_bytes(dim, self.N, restart, prec, levels, B, shift, variable_beta, uhat_slots, triharmonic,
+                             auto_shift)
         self.workspace_bytes = nb
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         bd = ahoc_bdata(_ptr(g_D, B * self.nfull, "g_D"), _ptr(g_N, B * self.ngamma, "g_N"),
                         _ptr(lapt_gD, B * self.ngamma, "lapt_gD"), _ptr(v_edge, B * self.nfull, "v_edge"),
-                        _ptr(g_L, B * self.ngamma, "g_L"), _ptr(beta, B * self.nfull, "beta"))
+                        _ptr(g_L, B * self.ngamma, "g_L"), _ptr(beta, B * self.nfull, "beta"),
+                        _ptr(lap_gD, B * self.nfull, "lap_gD"), _ptr(bilap, B * self.nfull, "bilap"),
+                        _ptr(g_NN, B * self.ngamma, "g_NN"), _ptr(lapt_w, B * self.ngamma, "lapt_w"))
         o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
-                  navier, shift, variable_beta, uhat_slots, fused)
+                  navier, shift, variable_beta, uhat_slots, fused, triharmonic, auto_shift)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)
@@ -347,11 +357,27 @@ class Plan:
             pass
 
 
+def plan_for_triharmonic(data: Dict, device="cuda", **kw) -> "Plan":
+    """Create a triharmonic plan from a sampled problem (``inputs.sample_triharmonic``):
+    the faces not clamped are the simply supported faces of the plan's mask."""
+    def dev(key):
+        t = torch.as_tensor(data[key], dtype=torch.float64)
+        return t.reshape(-1).contiguous().to(device)
+    clamped = set(data.get("clamped") or ())
+    supported = sum(1 << f for f in range(2 * data["dim"]) if f not in clamped)
+    return Plan(data["dim"], data["N"], None, lo=data["lo"], hi=data["hi"], g_D=dev("g_D"), g_N=dev("g_N"),
+                navier=supported, triharmonic=True, lap_gD=dev("lap_gD"), bilap=dev("bilap"), g_NN=dev("g_NN"),
+                lapt_w=dev("lapt_w"), device=device, **kw)
+
+
 def plan_for(data: Dict, device="cuda", **kw) -> "Plan":
     """Create a plan from a sampled problem (see ``paper_2609_16478_b300.inputs.sample``).
 
-    The problem's Navier faces become the plan's mask, and a nonzero beta the
-    shift gamma = beta / alpha, which must then be constant (a constant alpha).
+    The problem's Navier faces become the plan's mask; a nonzero beta (a
+    number or a full-grid array) is passed as a full-grid array and the plan
+    derives the beta class from it (``opts.auto_shift``: constant
+    beta / alpha gives the shifted eigenvalues, otherwise the BiCGSTAB
+    v-solves).
     """
     def dev(key):
         v = data.get(key)
@@ -362,19 +388,12 @@ def plan_for(data: Dict, device="cuda", **kw) -> "Plan":
     alpha = dev("alpha")
     navier = sum(1 << int(f) for f in (data.get("navier") or ()))
     beta = data.get("beta")
-    shift = 0.0
-    if beta is not None and np.ndim(beta) > 0:
-        # variable beta: BiCGSTAB v-solves preconditioned by the FFT solve with the mean of beta/alpha
-        kw.setdefault("beta", dev("beta"))
-        shift = float((kw["beta"] / alpha).mean())
-    elif beta:
-        lo_, hi_ = float(alpha.min()), float(alpha.max())
-        if lo_ != hi_:
-            kw.setdefault("beta", torch.full_like(alpha, float(beta)))
-            shift = float((kw["beta"] / alpha).mean())
+    if beta is not None and (np.ndim(beta) > 0 or float(beta) != 0.0):
+        if np.ndim(beta) > 0:
+            kw.setdefault("beta", dev("beta"))
         else:
-            shift = float(beta) / lo_
+            kw.setdefault("beta", torch.full_like(alpha, float(beta)))
+        kw.setdefault("auto_shift", True)
     kw.setdefault("navier", navier)
-    kw.setdefault("shift", shift)
     return Plan(data["dim"], data["N"], alpha, lo=data["lo"], hi=data["hi"], g_D=dev("g_D"),
                 g_N=dev("g_N"), lapt_gD=dev("lapt_gD"), v_edge=dev("v_edge"), g_L=dev("g_L"), **kw)

@@ -61,6 +61,11 @@ struct Coefs {
   double w[3][4];         // one-sided u_nn weights on U0..U3 per normal axis (1/h^2 scaled)
   double wg[3];           // weight on g_N per normal axis (11/(3h))
   double gam;             // constant beta / alpha: the v-equation is -L_h V + gam M V = M f
+  double fsign;           // sign of M f in the right-hand side of the equation solved first:
+                          // -1 for the v-equation (-L_h V = M f), +1 for the triharmonic w-equation
+  // triharmonic class: one-sided fourth normal derivative at a clamped face,
+  // u_ssss ~ sum_m w4[a][m] U_m + w4s[a] u_s + w4ss[a] u_ss (s the inward normal)
+  double w4[3][5], w4s[3], w4ss[3];
 };
 
 // Per-mode factors of the tridiagonal solve along the last axis (see tri.cu).

@@ -17,12 +17,12 @@
 //                  z-, z+) generate the right-hand side inside the
 //                  tridiagonal solve (tri.cu, VGen3D).  Also Q/alpha on the
 //                  faces for the u-equation's M stencil.
-//   trace3d_red    the one-sided combination w1 U1 + w2 U2 + w3 U3 of an
+//   trace3d_x/y    the one-sided combination w1 U1 + w2 U2 + w3 U3 of an
 //                  x-face from U-hat(kx, ky, k) (the z-solve's output):
 //                  sum_kx tau_x(kx) U-hat, tau_x(kx) = sum_m w_m sin(m kx pi/N0),
 //                  odd and even kx apart (the x+ face takes (-1)^(kx+1));
-//                  likewise the y-faces over ky; one read of U-hat.  Written
-//                  in face layout, still in the in-face transverse modes.
+//                  likewise the y-faces over ky (a second read of U-hat).
+//                  Written in face layout, still in the in-face modes.
 //   trace3d_z      the z-faces' combinations of the planes k = 1, 2, 3 and
 //                  N2-1, N2-2, N2-3 in (kx, ky) modes.
 //   trace3d_fin    after the in-face inverse DSTs: R = alpha (.) - Q.
@@ -95,93 +95,76 @@ __global__ void k_v3d_prep(Geom g, Coefs cf, const double* __restrict__ Q, const
   }
 }
 
-// One CTA per (k plane, problem).  Thread t owns the x-mode columns
-// kx = 1 + t + c * blockDim.x; per row ky it adds tau_y(ky) U-hat into its
-// column sums (odd / even ky apart), and the warps reduce tau_x(kx) U-hat over
-// their lanes (odd / even kx apart) into shared memory, summed in warp order
-// once per batch of rows.
-constexpr int kRedThreads = 512;
-constexpr int kRedRows = 8;
-constexpr int kRedCols = 8;  // columns per thread: N0 <= kRedThreads * kRedCols
-
+// x-faces: one warp per row (ky, k) of U-hat sums tau_x(kx) U-hat over kx;
+// lane l takes kx = 1 + l + 32 t, so a lane sees one kx parity and the
+// xor-shuffles over lanes of equal parity leave the odd-kx sum in lane 0 and
+// the even-kx sum in lane 1.  Sums in T (an FP32 pass takes no FP64 operation
+// per element), the two results in FP64.
+constexpr int kRedThreads = 256;
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_trace3d_red(Geom g, const T* __restrict__ Uh,
-                                                             const T* __restrict__ taux,
-                                                             const T* __restrict__ tauy, double* __restrict__ out) {
-  __shared__ double red[kRedRows][2][kRedThreads / 32];
-  const int k = 1 + blockIdx.x;
+__global__ void __launch_bounds__(kRedThreads) k_trace3d_x(Geom g, const T* __restrict__ Uh,
+                                                           const T* __restrict__ taux, double* __restrict__ out) {
   const int bi = blockIdx.y;
   if (g.skip(bi)) return;
-  Uh += (int64_t)bi * g.npad + g.pad(0, 0, k);
-  out += (int64_t)bi * g.ngamma;
-  const int N0 = g.N[0], N1 = g.N[1];
-  const int nx = N0 - 1, ny = N1 - 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int ncol = (nx + blockDim.x - 1) / blockDim.x;
-  // sums in T: an FP32 pass must not take FP64 operations per element
-  T ys[kRedCols][2];
-  T tx[kRedCols];
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1;
+  const int64_t row = (int64_t)blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);  // (ky - 1) + ny (k - 1)
+  if (row >= (int64_t)ny * (g.N[2] - 1)) return;
+  const int lane = threadIdx.x & 31;
+  const int ky = 1 + (int)(row % ny), k = 1 + (int)(row / ny);
+  const T* r = Uh + (int64_t)bi * g.npad + g.pad(0, ky, k);
+  T acc = 0;
+  int kx = 1 + lane;
+  for (; kx + 96 <= nx; kx += 128)  // four loads in flight per lane
+    acc += taux[kx] * r[kx] + taux[kx + 32] * r[kx + 32] + taux[kx + 64] * r[kx + 64] + taux[kx + 96] * r[kx + 96];
+  for (; kx <= nx; kx += 32) acc += taux[kx] * r[kx];
+  double a = (double)acc;
 #pragma unroll
-  for (int c = 0; c < kRedCols; ++c) {
-    ys[c][0] = ys[c][1] = (T)0;
-    const int kx = 1 + threadIdx.x + c * blockDim.x;
-    tx[c] = (c < ncol && kx <= nx) ? taux[kx] : (T)0;
+  for (int o = 16; o >= 2; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  const double other = __shfl_down_sync(0xffffffffu, a, 1);  // lane 0 gets lane 1's even-kx sum
+  if (lane == 0) {
+    out += (int64_t)bi * g.ngamma;
+    out[g.face_off[0] + row] = a + other;  // x-: U(m) = sum U-hat sin(m kx pi/N0)
+    out[g.face_off[1] + row] = a - other;  // x+: U(N0 - m) picks up (-1)^(kx+1)
   }
-  for (int r0 = 1; r0 <= ny; r0 += kRedRows) {
-#pragma unroll
-    for (int rr = 0; rr < kRedRows; ++rr) {
-      const int ky = r0 + rr;
-      T xs = 0;
-      if (ky <= ny) {
-        const T* row = Uh + g.n0 * (int64_t)ky;
-        const T wy = tauy[ky];
-#pragma unroll
-        for (int c = 0; c < kRedCols; ++c) {
-          const int kx = 1 + threadIdx.x + c * blockDim.x;
-          if (c < ncol && kx <= nx) {
-            const T val = row[kx];
-            ys[c][ky & 1] += wy * val;
-            xs += tx[c] * val;
-          }
-        }
-      }
-      // lanes of equal kx parity: lane 0 ends with the sum over its warp's odd kx
-      // (kx = 1 + t + c * blockDim.x has the parity of 1 + lane), lane 1 with the even
-#pragma unroll
-      for (int o = 16; o >= 2; o >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o);
-      if (lane < 2) red[rr][lane][warp] = (double)xs;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * kRedRows) {
-      const int rr = threadIdx.x >> 1, par = threadIdx.x & 1;  // par 0: odd kx, 1: even kx
-      const int ky = r0 + rr;
-      if (ky <= ny) {
-        double s = 0.0;
-        for (int w = 0; w < nwarp; ++w) s += red[rr][par][w];
-        red[rr][par][0] = s;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < kRedRows) {
-      const int ky = r0 + threadIdx.x;
-      if (ky <= ny) {
-        const double O = red[threadIdx.x][0][0], E = red[threadIdx.x][1][0];
-        const int64_t loc = (ky - 1) + (int64_t)ny * (k - 1);
-        out[g.face_off[0] + loc] = O + E;  // x-: U(m) = sum U-hat sin(m kx pi/N0)
-        out[g.face_off[1] + loc] = O - E;  // x+: U(N0 - m) picks up (-1)^(kx+1)
-      }
-    }
-    __syncthreads();
+}
+
+// y-faces: a CTA takes a strip of 32 x-modes of one plane k; warp w sums
+// tau_y(ky) U-hat over the rows ky = 1 + w + W t (W warps, even: one ky parity
+// per warp), lane l over its column; the warps' sums are combined in shared
+// memory in warp order.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_trace3d_y(Geom g, const T* __restrict__ Uh,
+                                                           const T* __restrict__ tauy, double* __restrict__ out) {
+  __shared__ double part[kRedThreads / 32][32];
+  const int bi = blockIdx.z;
+  if (g.skip(bi)) return;
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1;
+  const int k = 1 + blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int W = kRedThreads / 32;
+  const int kx = 1 + blockIdx.x * 32 + lane;
+  const T* base = Uh + (int64_t)bi * g.npad + g.pad(0, 0, k);
+  T acc = 0;
+  if (kx <= nx) {
+    int ky = 1 + w;
+    for (; ky + 3 * W <= ny; ky += 4 * W)
+      acc += tauy[ky] * base[g.n0 * (int64_t)ky + kx] + tauy[ky + W] * base[g.n0 * (int64_t)(ky + W) + kx] +
+             tauy[ky + 2 * W] * base[g.n0 * (int64_t)(ky + 2 * W) + kx] +
+             tauy[ky + 3 * W] * base[g.n0 * (int64_t)(ky + 3 * W) + kx];
+    for (; ky <= ny; ky += W) acc += tauy[ky] * base[g.n0 * (int64_t)ky + kx];
   }
-#pragma unroll
-  for (int c = 0; c < kRedCols; ++c) {
-    const int kx = 1 + threadIdx.x + c * blockDim.x;
-    if (c < ncol && kx <= nx) {
-      const double O = (double)ys[c][1], E = (double)ys[c][0];  // ky odd, ky even
-      const int64_t loc = (kx - 1) + (int64_t)nx * (k - 1);
-      out[g.face_off[2] + loc] = O + E;
-      out[g.face_off[3] + loc] = O - E;
+  part[w][lane] = (double)acc;
+  __syncthreads();
+  if (w == 0 && kx <= nx) {
+    double O = 0.0, E = 0.0;  // warps of even w take odd ky
+    for (int v = 0; v < W; v += 2) {
+      O += part[v][lane];
+      E += part[v + 1][lane];
     }
+    out += (int64_t)bi * g.ngamma;
+    const int64_t loc = (kx - 1) + (int64_t)nx * (k - 1);
+    out[g.face_off[2] + loc] = O + E;
+    out[g.face_off[3] + loc] = O - E;
   }
 }
 
@@ -227,19 +210,22 @@ cudaError_t launch_v3d_prep(const Geom& g, const Coefs& cf, const double* Q, con
   return cudaGetLastError();
 }
 
-bool trace3d_red_ok(const Geom& g) { return g.dim == 3 && g.N[0] - 1 <= kRedThreads * kRedCols; }
+bool trace3d_red_ok(const Geom& g) { return g.dim == 3; }
 
+// three kernels: the x-face sums, the y-face sums, the z-face planes
 template <typename T>
 cudaError_t launch_trace3d(const Geom& g, const Coefs& cf, const T* Uh, const T* taux, const T* tauy,
                            double* Tr, cudaStream_t st) {
-  const int nx = g.N[0] - 1;
-  int th = nx < kRedThreads ? ((nx + 31) / 32) * 32 : kRedThreads;
-  if (th < 64) th = 64;
-  k_trace3d_red<T><<<dim3((unsigned)(g.N[2] - 1), g.nb), th, 0, st>>>(g, Uh, taux, tauy, Tr);
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1, nz = g.N[2] - 1;
+  const int64_t rows = (int64_t)ny * nz;
+  k_trace3d_x<T><<<dim3(nblk3(rows, kRedThreads / 32), g.nb), kRedThreads, 0, st>>>(g, Uh, taux, Tr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t nz = (int64_t)nx * (g.N[1] - 1);
-  k_trace3d_z<T><<<dim3(nblk3(nz, 256), g.nb), 256, 0, st>>>(g, cf, Uh, Tr);
+  k_trace3d_y<T><<<dim3((unsigned)((nx + 31) / 32), (unsigned)nz, g.nb), kRedThreads, 0, st>>>(g, Uh, tauy, Tr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t nzf = (int64_t)nx * ny;
+  k_trace3d_z<T><<<dim3(nblk3(nzf, 256), g.nb), 256, 0, st>>>(g, cf, Uh, Tr);
   return cudaGetLastError();
 }
 

@@ -123,6 +123,11 @@ struct VGen3D {
 // the one-thread-per-column solve with the right-hand side generated from G
 template <typename T>
 cudaError_t launch_tri_gen3(const Geom& g, T* a, const Mode<T>* modes, const VGen3D<T>& G, cudaStream_t st);
+// the chunked solve (FP64 carries) with the right-hand side generated from G
+template <typename T>
+cudaError_t launch_tri_chunked_gen3(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                                    const double* rpow, double* scratch, int L, const VGen3D<T>& G,
+                                    cudaStream_t st);
 
 // fused 3D matvec helpers (fused3d.cu)
 template <typename T>
@@ -159,6 +164,11 @@ cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, 
                          const double* afac, const double* gD, const double* gN, const double* lapt,
                          cudaStream_t st, const double* srcq = nullptr, const double* gL = nullptr);
 
+// Triharmonic class (Lap^3 u = f): R_p = u_ssss(U)_p + lapt_w_p - Q_p on clamped
+// faces (one-sided u_ssss with g_D, g_N, g_NN), bilap_p - Q_p on the others
+cudaError_t launch_trace_tri(const Geom& g, const Coefs& cf, double* y, const double* U, const double* Q,
+                             const double* gD, const double* gN, const double* gNN, const double* laptw,
+                             const double* bilap, cudaStream_t st);
 // mixed precision: FP64 residual of the coupled system (r_u, r_v in FP32, r_q in FP64)
 cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv, double* rq, const double* U,
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
@@ -184,6 +194,10 @@ cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, con
 cudaError_t launch_pack(const Geom& g, double* dense, const double* padded, cudaStream_t st);
 cudaError_t launch_unpack(const Geom& g, double* padded, const double* dense, cudaStream_t st);
 cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, cudaStream_t st);
+// per block b: out[3b] = min, out[3b+1] = max, out[3b+2] = sum of beta/alpha over n points
+cudaError_t launch_ratio_stats(const double* beta, const double* alpha, int64_t n, double* out, int blocks,
+                               cudaStream_t st);
+// out = 1 / in (in == NULL: out = 1)
 cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st);
 cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,
                           cudaStream_t st);

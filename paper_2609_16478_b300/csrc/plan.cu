@@ -65,6 +65,7 @@ struct Opts {
   int varb = 0;          // variable beta / alpha (problems bring beta)
   int uhat = 0;          // U-hat slots of the recovery (0 automatic, < 0 none)
   int unfused = 0;       // 3D: the plain Schur matvec (eight DST passes) instead of the fused one
+  int tri = 0;           // the triharmonic class: Lap^3 u = f, navier = the simply supported faces
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -87,11 +88,19 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.varb = o->variable_beta ? 1 : 0;
     d.uhat = o->uhat_slots;
     d.unfused = o->unfused ? 1 : 0;
+    d.tri = o->triharmonic ? 1 : 0;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
   if (d.prec != AHOC_FP64 && d.prec != AHOC_MIXED) return fail(AHOC_EUNSUPPORTED, "prec must be AHOC_FP64 or AHOC_MIXED");
   if (d.prec == AHOC_MIXED) d.levels = 0;  // the nested initial guess belongs to the FP64 path
+  if (d.tri) {
+    if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "the triharmonic class runs in FP64 only");
+    if (d.varb || d.shift != 0.0) return fail(AHOC_EINVAL, "the triharmonic class takes no beta");
+    d.precond = 0;  // the boundary-symbol preconditioner is the biharmonic's
+    d.levels = 0;
+    d.uhat = -1;
+  }
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.batch > 4096) return fail(AHOC_EINVAL, "batch > 4096");
@@ -148,6 +157,42 @@ ahoc_status make_geom(int dim, const int64_t* N, const double* lo, const double*
   return AHOC_OK;
 }
 
+// Weights of the one-sided fourth normal derivative at a clamped face of the
+// triharmonic class: with U_m = u(m h) along the inward normal s,
+//   sum_{m=0}^{4} c_m U_m + c_s h u_s + c_ss h^2 u_ss = h^4 u_ssss + O(h^7).
+// Expanding U_m = sum_k (m h)^k / k! u_k, the coefficients of u_3..u_6 give
+// four equations in c_1..c_4 (right-hand side 1 for u_4, 0 otherwise); those
+// of u_0, u_1, u_2 then give c_0, c_s, c_ss.  Solved here in long double.
+void fourth_weights(long double c[5], long double& cs, long double& css) {
+  long double A[4][5];
+  for (int k = 3; k <= 6; ++k) {
+    long double fact = 1;
+    for (int t = 2; t <= k; ++t) fact *= t;
+    for (int m = 1; m <= 4; ++m) A[k - 3][m - 1] = powl((long double)m, (long double)k) / fact;
+    A[k - 3][4] = (k == 4) ? 1.0L : 0.0L;
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (fabsl(A[r][col]) > fabsl(A[piv][col])) piv = r;
+    for (int t = 0; t < 5; ++t) std::swap(A[col][t], A[piv][t]);
+    for (int r = 0; r < 4; ++r) {
+      if (r == col) continue;
+      const long double f = A[r][col] / A[col][col];
+      for (int t = col; t < 5; ++t) A[r][t] -= f * A[col][t];
+    }
+  }
+  c[0] = 0;
+  cs = 0;
+  css = 0;
+  for (int m = 1; m <= 4; ++m) {
+    c[m] = A[m - 1][4] / A[m - 1][m - 1];
+    c[0] -= c[m];
+    cs -= c[m] * m;
+    css -= c[m] * m * m / 2.0L;
+  }
+}
+
 // Stencil coefficients (Sec. 2.2; prefactor 1/12; 2D nine-point operator).
 Coefs make_coefs(const Geom& g) {
   Coefs c;
@@ -191,6 +236,15 @@ Coefs make_coefs(const Geom& g) {
   for (int a = 0; a < g.dim; ++a) {
     for (int m = 0; m < 4; ++m) c.w[a][m] = os[m] * inv[a];
     c.wg[a] = (11.0 / 3.0) / g.h[a];
+  }
+  c.fsign = -1.0;
+  long double c4[5], cs, css;
+  fourth_weights(c4, cs, css);
+  for (int a = 0; a < g.dim; ++a) {
+    const long double h = g.h[a];
+    for (int m = 0; m < 5; ++m) c.w4[a][m] = (double)(c4[m] / (h * h * h * h));
+    c.w4s[a] = (double)(cs / (h * h * h));
+    c.w4ss[a] = (double)(css / (h * h));
   }
   return c;
 }
@@ -313,7 +367,12 @@ struct Layout {
       // per-precision side arrays of the fused 2D path
       afinv, qa, rpow, ainvf, rxmf, rxpf, qyf, qaf, R2f, tauf, skf, ckf, tri2, tri2_v,
       // fused 3D matvec: generator and trace arrays (face layout), y-face trace weights
-      gen3, tr3, tauy, total;
+      gen3, tr3, tauy,
+      // triharmonic class: Lap u and Lap^2 u on the boundary, u_nn and the tangential
+      // part of Lap^2 u on the faces, Lap u gathered on the faces
+      lapgD, bilap, gNN, laptw, vface,
+      // fused 3D matvec of the mixed path: FP32 generator, y sine table and y trace weights
+      gen3f, skyf, tauyf, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -368,7 +427,7 @@ bool fused_ok(const Geom& g);
 // recovery of U is a combination of those fields and one inverse DST.
 constexpr int kAutoUhatSlots = 16;
 int bank_slots(const Geom& g, const Opts& o) {
-  if (o.uhat < 0 || o.prec != AHOC_FP64 || o.varb || !fused_ok(g)) return 0;
+  if (o.uhat < 0 || o.prec != AHOC_FP64 || o.varb || o.tri || !fused_ok(g)) return 0;
   const int want = o.uhat > 0 ? o.uhat : kAutoUhatSlots;
   return want < o.restart ? want : o.restart;
 }
@@ -442,6 +501,11 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.bcg = take(o.varb && o.prec == AHOC_FP64 ? 9 * B * fld : 0);
   L.bcoef = take(o.varb ? 3 * B * sizeof(double) : 0);
   L.gL = take(B * face);
+  L.lapgD = take(o.tri ? B * full : 0);
+  L.bilap = take(o.tri ? B * full : 0);
+  L.gNN = take(o.tri ? B * face : 0);
+  L.laptw = take(o.tri ? B * face : 0);
+  L.vface = take(o.tri ? B * face : 0);
   // the recovery's U-hat slots (one more: the guess's U-hat and the sum) and the data's U and V
   const int nbank = bank_slots(g, o);
   L.bank = take(nbank ? (size_t)(nbank + 1) * B * fld : 0);
@@ -481,6 +545,9 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.tauf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
   L.skf = take(mixed ? 2 * (size_t)g.N[0] * sizeof(float) : 0);
   L.ckf = take(mixed ? ((size_t)g.N[0] + 1) * sizeof(float) : 0);
+  L.gen3f = take(mixed && g.dim == 3 ? B * fface : 0);
+  L.skyf = take(mixed ? 2 * (size_t)g.N[1] * sizeof(float) : 0);
+  L.tauyf = take(mixed ? ((size_t)g.N[1] + 1) * sizeof(float) : 0);
   L.total = off;
   return L;
 }
@@ -576,7 +643,7 @@ struct ahoc_plan {
   double *afinv = nullptr, *qa = nullptr, *rpow = nullptr;
   double *tri2 = nullptr, *tri2_v = nullptr;  // tables of the FP64 chunked solve (U and shifted V operators)
   float *ainvf = nullptr, *rxmf = nullptr, *rxpf = nullptr, *qyf = nullptr, *qaf = nullptr, *R2f = nullptr,
-        *tauf = nullptr, *skf = nullptr, *ckf = nullptr;
+        *tauf = nullptr, *skf = nullptr, *ckf = nullptr, *gen3f = nullptr, *skyf = nullptr, *tauyf = nullptr;
   Mode<float>* modesf = nullptr;
   // batch state: the device mask g.act points to `act`; act_now mirrors it
   int* act = nullptr;
@@ -586,6 +653,9 @@ struct ahoc_plan {
   std::vector<int> act_now, part;  // current mask; problems taking part in solves
   std::vector<ProbStat> ps;
   bool has_gD = false, has_vedge = false, has_gN = false, has_lapt = false;
+  // triharmonic class data (Lap u, Lap^2 u on the boundary; u_nn, tangential part of Lap^2 u; Lap u on the faces)
+  double *lapgD = nullptr, *bilap = nullptr, *gNN = nullptr, *laptw = nullptr, *vface = nullptr;
+  bool has_lapgD = false, has_bilap = false, has_gNN = false, has_laptw = false;
   double* hhost = nullptr;  // pinned
   // CUDA graphs of the GMRES iterations, one per iteration index, captured on
   // first use; the per-problem scalars and the mask reach them through
@@ -702,6 +772,28 @@ ahoc_status solve_VU(ahoc_plan* p, const double* Q, const double* f, bool data) 
   RUN(AHOC_K_URHS,
       launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q, data && p->has_gD ? p->gD : nullptr, p->st));
   CKS(poisson_inplace(p, p->W2));
+  return AHOC_OK;
+}
+
+// Triharmonic class (Sec. 4.2, triharmonic equation): the three sequential
+// Dirichlet solves of the mixed form Lap w = f, Lap v = w, Lap u = v with the
+// w boundary values Q on the faces.  Leaves U in W1 and V in W2.  data: with f
+// and the boundary data (edges and corners of w, v on the boundary, g_D);
+// otherwise the homogeneous part (Q alone).
+ahoc_status solve_tri(ahoc_plan* p, const double* Q, const double* f, bool data) {
+  const Geom& g = p->g;
+  // L_h W = M f - L_bdry(W_b): W_b = Q on the faces, Lap^2 u on edges and corners
+  RUN(AHOC_K_VRHS, launch_vrhs<double>(g, p->cf, p->W1, Q, f, data && p->has_bilap ? p->bilap : nullptr, p->st,
+                                       nullptr, nullptr));
+  CKS(poisson_inplace(p, p->W1));
+  // L_h V = M W - L_bdry(V_b): M reaches W = Q on the faces, V_b = Lap u (data)
+  RUN(AHOC_K_URHS, launch_urhs<double>(g, p->cf, p->W2, p->W1, p->ainv, Q,
+                                       data && p->has_lapgD ? p->lapgD : nullptr, p->st));
+  CKS(poisson_inplace(p, p->W2));
+  // L_h U = M V - L_bdry(g_D): M reaches V = Lap u on the faces
+  RUN(AHOC_K_URHS, launch_urhs<double>(g, p->cf, p->W1, p->W2, p->ainv, data && p->has_lapgD ? p->vface : nullptr,
+                                       data && p->has_gD ? p->gD : nullptr, p->st));
+  CKS(poisson_inplace(p, p->W1));
   return AHOC_OK;
 }
 
@@ -822,23 +914,27 @@ bool fused_ok(const Geom& g) { return g.dim == 2 && tri_ncols(g) < kChunkedBelow
 // the algebra.
 bool fused3d_ok(const ahoc_plan* p) {
   const Geom& g = p->g;
-  return g.dim == 3 && p->o.prec == AHOC_FP64 && !p->o.varb && !p->o.unfused && trace3d_red_ok(g);
+  return g.dim == 3 && !p->o.varb && !p->o.tri && !p->o.unfused && trace3d_red_ok(g);
 }
 
 // DST-I of face-layout arrays along the in-face axes other than z for the x-
 // and y-faces, along both for the z-faces (the generator and the traces)
-ahoc_status face_dsts3(ahoc_plan* p, double* v, int kid) {
+template <typename T>
+ahoc_status face_dsts3(ahoc_plan* p, T* v, const void* twx, const T* snx, const void* twy, const T* sny, int kid) {
   const Geom& g = p->g;
   const int nx = g.N[0] - 1, ny = g.N[1] - 1, nz = g.N[2] - 1;
-  RUN(kid, launch_dst_gen<double>(v + g.face_off[0], 2 * nz, 1, ny, 0, 1, g.N[1], p->twy, p->sny, p->st, g.nb,
-                                  g.ngamma, g.act));
-  RUN(kid, launch_dst_gen<double>(v + g.face_off[2], 2 * nz, 1, nx, 0, 1, g.N[0], p->twx, p->snx, p->st, g.nb,
-                                  g.ngamma, g.act));
-  RUN(kid, launch_dst_gen<double>(v + g.face_off[4], 2 * ny, 1, nx, 0, 1, g.N[0], p->twx, p->snx, p->st, g.nb,
-                                  g.ngamma, g.act));
-  RUN(kid, launch_dst_gen<double>(v + g.face_off[4], 2 * nx, nx, (int64_t)nx * ny, 1, nx, g.N[1], p->twy, p->sny,
-                                  p->st, g.nb, g.ngamma, g.act));
+  RUN(kid, launch_dst_gen<T>(v + g.face_off[0], 2 * nz, 1, ny, 0, 1, g.N[1], twy, sny, p->st, g.nb, g.ngamma,
+                             g.act));
+  RUN(kid, launch_dst_gen<T>(v + g.face_off[2], 2 * nz, 1, nx, 0, 1, g.N[0], twx, snx, p->st, g.nb, g.ngamma,
+                             g.act));
+  RUN(kid, launch_dst_gen<T>(v + g.face_off[4], 2 * ny, 1, nx, 0, 1, g.N[0], twx, snx, p->st, g.nb, g.ngamma,
+                             g.act));
+  RUN(kid, launch_dst_gen<T>(v + g.face_off[4], 2 * nx, nx, (int64_t)nx * ny, 1, nx, g.N[1], twy, sny, p->st,
+                             g.nb, g.ngamma, g.act));
   return AHOC_OK;
+}
+ahoc_status face_dsts3(ahoc_plan* p, double* v, int kid) {
+  return face_dsts3<double>(p, v, p->twx, p->snx, p->twy, p->sny, kid);
 }
 
 // y = S q (Algorithm 1, SchurMatVec) in 4 full DST passes: the V solve's
@@ -857,7 +953,31 @@ ahoc_status fused3d(ahoc_plan* p, const double* q, double* y) {
   RUN(AHOC_K_DST_X, launch_dst_x_mload3d<double>(g, p->W2, p->W1, p->qa, cf.Mc, cf.Mn, p->twx, p->snx, p->st));
   RUN(AHOC_K_DST_Y, launch_dst_y<double>(g, p->W2, p->twy, p->sny, 1.0, p->st));
   RUN(AHOC_K_TRI, launch_tri<double>(g, p->W2, p->modes, p->st));
-  RUNN(AHOC_K_TRACE, 2, launch_trace3d<double>(g, cf, p->W2, p->tau, p->tauy, p->tr3, p->st));
+  RUNN(AHOC_K_TRACE, 3, launch_trace3d<double>(g, cf, p->W2, p->tau, p->tauy, p->tr3, p->st));
+  CKS(face_dsts3(p, p->tr3, AHOC_K_TRACE));
+  RUN(AHOC_K_TRACE, launch_trace3d_fin(g, y, p->tr3, q, p->afac, nullptr, p->st));
+  return AHOC_OK;
+}
+
+// The same in FP32 (the mixed path's Schur action): the z-solves take the
+// chunked form with FP64 carries; the generator arrays, the fields and the
+// stencil in FP32, the traces summed in FP32 and finished in FP64.
+ahoc_status fused3d_f(ahoc_plan* p, const double* q, double* y) {
+  const Geom& g = p->g;
+  const Coefs& cf = p->cf;
+  const int L = tri_chunk_len(g);
+  RUN(AHOC_K_VRHS, launch_v3d_prep<float>(g, cf, q, p->afinv, p->gen3f, p->qaf, p->st));
+  CKS(face_dsts3<float>(p, p->gen3f, p->twf[0], p->snf[0], p->twf[1], p->snf[1], AHOC_K_VRHS));
+  const VGen3D<float> G{p->gen3f, p->skf, p->skyf};
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked_gen3<float>(g, p->F1, p->modesf_v, p->modes_v, p->rpow_v, p->tri, L, G,
+                                                      p->st));
+  RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, p->F1, p->twf[1], p->snf[1], 1.0f, p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_store_ainv<float>(g, p->F1, p->ainvf, p->twf[0], p->snf[0], p->st));
+  RUN(AHOC_K_DST_X, launch_dst_x_mload3d<float>(g, p->F2, p->F1, p->qaf, (float)cf.Mc, (float)cf.Mn, p->twf[0],
+                                                p->snf[0], p->st));
+  RUN(AHOC_K_DST_Y, launch_dst_y<float>(g, p->F2, p->twf[1], p->snf[1], 1.0f, p->st));
+  RUNN(AHOC_K_TRI, 5, launch_tri_chunked<float>(g, p->F2, p->modesf, p->modes, p->rpow, p->tri, L, p->st));
+  RUNN(AHOC_K_TRACE, 3, launch_trace3d<float>(g, cf, p->F2, p->tauf, p->tauyf, p->tr3, p->st));
   CKS(face_dsts3(p, p->tr3, AHOC_K_TRACE));
   RUN(AHOC_K_TRACE, launch_trace3d_fin(g, y, p->tr3, q, p->afac, nullptr, p->st));
   return AHOC_OK;
@@ -865,8 +985,14 @@ ahoc_status fused3d(ahoc_plan* p, const double* q, double* y) {
 
 // uhat: where the FP64 fused 2D matvec leaves U in x-modes (NULL: W2)
 ahoc_status matvec_dev(ahoc_plan* p, const double* q, double* y, double* uhat = nullptr) {
+  if (p->o.tri) {
+    CKS(solve_tri(p, q, nullptr, false));
+    RUN(AHOC_K_TRACE, launch_trace_tri(p->g, p->cf, y, p->W1, q, nullptr, nullptr, nullptr, nullptr, nullptr, p->st));
+    return AHOC_OK;
+  }
   if (p->o.prec == AHOC_MIXED) {
     if (fused_ok(p->g)) return fused2d<float>(p, f2arrays_f(p), q, nullptr, nullptr, nullptr, y, false);
+    if (fused3d_ok(p)) return fused3d_f(p, q, y);
     CKS(solve_VU_f(p, q, nullptr, nullptr));
     RUN(AHOC_K_TRACE, launch_trace<float>(p->g, p->cf, y, p->F2, q, p->afac, nullptr, nullptr, nullptr, p->st));
     return AHOC_OK;
@@ -939,6 +1065,14 @@ ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
 
 ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
   const Geom& g = p->g;
+  if (p->o.tri) {
+    CKS(solve_tri(p, nullptr, f, true));
+    RUN(AHOC_K_TRACE, launch_trace_tri(g, p->cf, b, p->W1, nullptr, p->has_gD ? p->gD : nullptr,
+                                       p->has_gN ? p->gN : nullptr, p->has_gNN ? p->gNN : nullptr,
+                                       p->has_laptw ? p->laptw : nullptr, p->has_bilap ? p->bilap : nullptr, p->st));
+    RUN(AHOC_K_KRYLOV, launch_axpby(b, b, -1.0, 0.0, g.ngamma, p->st, g.nb, nullptr, g.act));
+    return AHOC_OK;
+  }
   CKS(solve_VU(p, nullptr, f, true));
   RUN(AHOC_K_TRACE, launch_trace<double>(g, p->cf, b, p->W2, nullptr, p->afac, p->has_gD ? p->gD : nullptr,
                                          p->has_gN ? p->gN : nullptr, p->has_lapt ? p->lapt : nullptr, p->st,
@@ -1176,6 +1310,10 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
   CKS(make_geom(dim, N, nullptr, nullptr, &g));
   Opts o;
   CKS(read_opts(opts, &o));
+  if (opts && opts->auto_shift && !o.tri) {  // the data decide the beta class: size for the larger one
+    o.varb = 1;
+    o.shift = 1.0;
+  }
   g.nb = o.batch;
   apply_tuning(g, o);
   *bytes = total_bytes(g, o);
@@ -1209,6 +1347,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   g.navier = o.navier;
   Coefs cf = make_coefs(g);
   cf.gam = o.shift;
+  if (o.tri) cf.fsign = 1.0;  // the w-equation L_h W = M f
   const bool shifted = o.shift != 0.0;
   std::vector<Mode<double>> modes, modes_v;
   std::vector<long double> roots, roots_v;
@@ -1279,6 +1418,13 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->modes = at<Mode<double>>(p, L.modes);
   p->modes_v = shifted ? at<Mode<double>>(p, L.modes_v) : p->modes;
   p->gL = at<double>(p, L.gL);
+  if (o.tri) {
+    p->lapgD = at<double>(p, L.lapgD);
+    p->bilap = at<double>(p, L.bilap);
+    p->gNN = at<double>(p, L.gNN);
+    p->laptw = at<double>(p, L.laptw);
+    p->vface = at<double>(p, L.vface);
+  }
   if (o.varb) {
     p->gam = at<double>(p, L.gam);
     p->bcoef = at<double>(p, L.bcoef);
@@ -1327,6 +1473,9 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     p->tauf = at<float>(p, L.tauf);
     p->skf = at<float>(p, L.skf);
     p->ckf = at<float>(p, L.ckf);
+    p->gen3f = at<float>(p, L.gen3f);
+    p->skyf = at<float>(p, L.skyf);
+    p->tauyf = at<float>(p, L.tauyf);
   }
   const size_t B = (size_t)g.nb;
   const size_t fld = (size_t)g.npad * sizeof(double);
@@ -1442,6 +1591,8 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     CKC(launch_to_float(p->tauf, p->tau, g.N[0] + 1, p->st));
     CKC(launch_to_float(p->skf, p->stab[0], 2 * (int64_t)g.N[0], p->st));
     CKC(launch_to_float(p->ckf, p->ctab[0], g.N[0] + 1, p->st));
+    CKC(launch_to_float(p->skyf, p->stab[1], 2 * (int64_t)g.N[1], p->st));
+    CKC(launch_to_float(p->tauyf, p->tauy, g.N[1] + 1, p->st));
   }
   if (o.precond) {
     const double* stp[3] = {p->stab[0], p->stab[1], g.dim == 3 ? p->stab[2] : nullptr};
@@ -1481,7 +1632,8 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
   const size_t face = (size_t)g.ngamma * sizeof(double);
   const int64_t pf = (int64_t)b * g.nfull, pg = (int64_t)b * g.ngamma, pp = (int64_t)b * g.npad;
   CKC(launch_recip(p->ainv + pf, alpha, g.nfull, p->st));
-  CKC(launch_face_gather(g, p->afac + pg, alpha, p->st));
+  if (alpha) CKC(launch_face_gather(g, p->afac + pg, alpha, p->st));
+  else CKC(launch_recip(p->afac + pg, nullptr, g.ngamma, p->st));  // unit coefficient (triharmonic class)
   CKC(launch_recip(p->afinv + pg, p->afac + pg, g.ngamma, p->st));
   if (p->o.prec == AHOC_MIXED) CKC(launch_to_float(p->ainvf + pf, p->ainv + pf, g.nfull, p->st));
   auto put = [&](double* dst, const double* src, size_t bytes, bool& flag) -> ahoc_status {
@@ -1498,6 +1650,14 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
   CKS(put(p->gN + pg, bd ? bd->g_N : nullptr, face, p->has_gN));
   CKS(put(p->lapt + pg, bd ? bd->lapt_gD : nullptr, face, p->has_lapt));
   CKS(put(p->gL + pg, bd ? bd->g_L : nullptr, face, p->has_gL));
+  if (p->o.tri) {
+    CKS(put(p->lapgD + pf, bd ? bd->lap_gD : nullptr, full, p->has_lapgD));
+    CKS(put(p->bilap + pf, bd ? bd->bilap : nullptr, full, p->has_bilap));
+    CKS(put(p->gNN + pg, bd ? bd->g_NN : nullptr, face, p->has_gNN));
+    CKS(put(p->laptw + pg, bd ? bd->lapt_w : nullptr, face, p->has_laptw));
+    if (bd && bd->lap_gD) CKC(launch_face_gather(g, p->vface + pg, bd->lap_gD, p->st));
+    else CKC(cudaMemsetAsync(p->vface + pg, 0, face, p->st));
+  }
   if (p->o.varb) {
     if (!bd || !bd->beta) return fail(AHOC_EINVAL, "variable_beta needs beta for every problem");
     CKC(launch_mul(p->gam + pf, bd->beta, p->ainv + pf, g.nfull, p->st));
@@ -1531,6 +1691,44 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
 }
 #undef CKC
 
+// opts.auto_shift: the beta class from the data.  gamma = beta / alpha over
+// every point of every problem: one value everywhere -> the constant shift;
+// otherwise variable beta with the mean of gamma as the reference shift of the
+// v-solves' FFT preconditioner.  A few KB of device scratch, freed on return.
+ahoc_status derive_shift(const Geom& g, Opts& o, const double* alpha, const ahoc_bdata* bd, cudaStream_t st) {
+  o.varb = 0;
+  o.shift = 0.0;
+  if (!bd || !bd->beta) return AHOC_OK;
+  constexpr int kBlocks = 296;
+  const int64_t n = g.nfull * (int64_t)o.batch;
+  double* dev = nullptr;
+  if (cudaMalloc(&dev, 3 * kBlocks * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AHOC_ENOMEM, "cudaMalloc of the beta/alpha statistics failed");
+  }
+  std::vector<double> h(3 * kBlocks);
+  cudaError_t e = launch_ratio_stats(bd->beta, alpha, n, dev, kBlocks, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dev, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dev);
+  if (e != cudaSuccess) return fail(AHOC_ECUDA, std::string("beta/alpha statistics: ") + cudaGetErrorString(e));
+  double mn = INFINITY, mx = -INFINITY, sum = 0.0;
+  for (int b = 0; b < kBlocks; ++b) {
+    mn = std::fmin(mn, h[3 * b]);
+    mx = std::fmax(mx, h[3 * b + 1]);
+    sum += h[3 * b + 2];
+  }
+  if (!std::isfinite(mn) || !std::isfinite(mx) || !std::isfinite(sum)) return fail(AHOC_EINVAL, "beta/alpha not finite");
+  if (mn < 0) return fail(AHOC_EINVAL, "beta/alpha must be >= 0");
+  if (mn == mx) {
+    o.shift = mn;
+  } else {
+    o.varb = 1;
+    o.shift = sum / (double)n;
+  }
+  return AHOC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1540,11 +1738,12 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   if (!out) return fail(AHOC_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!alpha) return fail(AHOC_EINVAL, "alpha is NULL");
+  if (!alpha && !(opts && opts->triharmonic)) return fail(AHOC_EINVAL, "alpha is NULL");
   Geom g;
   CKS(make_geom(dim, N, lo, hi, &g));
   Opts o;
   CKS(read_opts(opts, &o));
+  if (opts && opts->auto_shift && !o.tri) CKS(derive_shift(g, o, alpha, bd, reinterpret_cast<cudaStream_t>(stream)));
   ahoc_plan* p = nullptr;
   ahoc_status s = plan_alloc(&p, dim, N, lo, hi, o, reinterpret_cast<cudaStream_t>(stream));
   for (int b = 0; s == AHOC_OK && b < o.batch; ++b) {
@@ -1556,8 +1755,12 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
       bb.v_edge = bd->v_edge ? bd->v_edge + (int64_t)b * g.nfull : nullptr;
       bb.g_L = bd->g_L ? bd->g_L + (int64_t)b * g.ngamma : nullptr;
       bb.beta = bd->beta ? bd->beta + (int64_t)b * g.nfull : nullptr;
+      bb.lap_gD = bd->lap_gD ? bd->lap_gD + (int64_t)b * g.nfull : nullptr;
+      bb.bilap = bd->bilap ? bd->bilap + (int64_t)b * g.nfull : nullptr;
+      bb.g_NN = bd->g_NN ? bd->g_NN + (int64_t)b * g.ngamma : nullptr;
+      bb.lapt_w = bd->lapt_w ? bd->lapt_w + (int64_t)b * g.ngamma : nullptr;
     }
-    s = plan_load(p, b, alpha + (int64_t)b * g.nfull, &bb);
+    s = plan_load(p, b, alpha ? alpha + (int64_t)b * g.nfull : nullptr, &bb);
   }
   if (s == AHOC_OK && cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "plan setup failed");
   if (s != AHOC_OK) {
@@ -1570,7 +1773,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
 
 ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd) {
   std::lock_guard<std::recursive_mutex> lk(capture_mutex());
-  if (!p || !alpha) return fail(AHOC_EINVAL, "NULL argument");
+  if (!p || (!alpha && !p->o.tri)) return fail(AHOC_EINVAL, "NULL argument");
   if (b < 0 || b >= p->g.nb) return fail(AHOC_EINVAL, "problem index out of range");
   p->have_last = false;
   CKS(plan_load(p, b, alpha, bd));
@@ -1679,6 +1882,7 @@ ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
 ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
   if (!p || !q) return fail(AHOC_EINVAL, "NULL argument");
   if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
+  if (v && p->o.tri) return fail(AHOC_EUNSUPPORTED, "a triharmonic plan returns Q only (v must be NULL)");
   CK(cudaMemcpyAsync(q, p->Q, (size_t)p->g.nb * p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
   CKS(set_act(p, p->part));
   if (v && p->v_lazy) {
@@ -1848,7 +2052,10 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
     for (int i = 0; i < nb; ++i)
       if (live[i]) {
         beta[i] = std::sqrt(p->hhost[(size_t)i * hs]);
-        if (!is_fin(beta[i])) return fail(AHOC_ENUMERIC, "non-finite initial residual");
+        if (!is_fin(beta[i])) {  // this problem fails alone: masked out, the others go on
+          go[i].status = AHOC_ENUMERIC;
+          live[i] = 0;
+        }
       }
   } else {
     CK(cudaMemsetAsync(X, 0, (size_t)nb * n * sizeof(double), p->st));
@@ -1861,6 +2068,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       go[i].rel = beta[i] / beta0[i];
       if (go[i].rel <= tol[i]) live[i] = 0;
     }
+  if (!any(live)) return AHOC_OK;
   std::vector<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), gv((size_t)nb * (m + 1)),
       y(m), hy((size_t)nb * hs, 0.0);
   std::vector<int> jend(nb, 0), cyc(nb, 0), nc(nb, 0);
@@ -1898,7 +2106,16 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
         double* gvi = &gv[(size_t)i * (m + 1)];
         for (int k = 0; k <= j; ++k) Hc[k] = hh[k] + hh[j + 1 + k];
         const double hn = std::sqrt(hh[2 * (j + 1)]);
-        if (!is_fin(hn)) return fail(AHOC_ENUMERIC, "non-finite Arnoldi norm");
+        bool bad = !is_fin(hn);
+        for (int k = 0; k <= j && !bad; ++k) bad = !is_fin(Hc[k]);
+        if (bad) {
+          // a NaN or Inf in this problem's Arnoldi step: it leaves the batch
+          // with its iterate as it was at the start of the cycle
+          gi.status = AHOC_ENUMERIC;
+          live[i] = 0;
+          jend[i] = 0;
+          continue;
+        }
         Hc[j + 1] = hn;
         for (int k = 0; k < j; ++k) {
           const double a = Hc[k], bb = Hc[k + 1];
@@ -1973,7 +2190,11 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
     for (int i = 0; i < nb; ++i)
       if (live[i]) {
         beta[i] = std::sqrt(p->hhost[(size_t)i * hs]);
-        if (!is_fin(beta[i])) return fail(AHOC_ENUMERIC, "non-finite restart residual");
+        if (!is_fin(beta[i])) {
+          go[i].status = AHOC_ENUMERIC;
+          live[i] = 0;
+          continue;
+        }
         go[i].rel = beta[i] / beta0[i];
         if (go[i].rel <= tol[i]) live[i] = 0;
       }
@@ -1981,16 +2202,14 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
   return AHOC_OK;
 }
 
-// ||v_b|| of every problem in the current mask (others: 0)
+// ||v_b|| of every problem in the current mask (others: 0); a problem whose
+// vector holds a NaN or Inf gets a non-finite norm (the caller masks it out)
 ahoc_status norms(ahoc_plan* p, const double* v, std::vector<double>& out) {
   CKS(mdot(p, v, p->g.ngamma, 1, v, p->hdev));
   CKS(fetch(p));
   out.assign(p->g.nb, 0.0);
   for (int i = 0; i < p->g.nb; ++i)
-    if (p->act_now[i]) {
-      out[i] = std::sqrt(p->hhost[(size_t)i * hstride(p->o)]);
-      if (!is_fin(out[i])) return fail(AHOC_ENUMERIC, "non-finite norm");
-    }
+    if (p->act_now[i]) out[i] = std::sqrt(p->hhost[(size_t)i * hstride(p->o)]);
   return AHOC_OK;
 }
 
@@ -2010,6 +2229,12 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
   }
   std::vector<double> beta0;
   CKS(norms(p, p->b, beta0));
+  for (int i = 0; i < nb; ++i)
+    if (live[i] && !is_fin(beta0[i])) {  // NaN or Inf in this problem's data: it fails alone
+      p->ps[i].status = AHOC_ENUMERIC;
+      live[i] = 0;
+      beta0[i] = 0.0;
+    }
   bool guess = false;
   bool any_rhs = false;
   for (int i = 0; i < nb; ++i) any_rhs = any_rhs || (live[i] && beta0[i] > 0);
@@ -2026,7 +2251,7 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     const double ctol = p->o.coarse_tol > tol ? p->o.coarse_tol : tol;
     // only the coarse Q is used: the coarse level skips its recovery of V and U
     ahoc_status cs_ = solve_internal(c, f_c, nullptr, ctol);
-    if (cs_ != AHOC_OK) return cs_;  // ENOCONV of a coarse level is kept in its stats, not an error
+    if (cs_ != AHOC_OK) return cs_;  // a coarse level's ENOCONV or ENUMERIC is kept in its stats
     CKS(harvest(p));
     for (int k = 0; k < AHOC_NK; ++k) {
       // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
@@ -2056,7 +2281,7 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     s.iters = go[i].iters;
     s.restarts = go[i].restarts;
     s.rel = live[i] && beta0[i] > 0 ? go[i].rel : 0.0;
-    s.status = go[i].status;
+    if (s.status == AHOC_OK) s.status = go[i].status;
     s.ms_mv += go[i].ms_mv;
   }
   if (!u) return AHOC_OK;  // a coarse level of the nested guess: Q only
@@ -2073,6 +2298,11 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     return AHOC_OK;
   }
   p->v_lazy = false;
+  if (p->o.tri) {  // W, V and U with the converged Q
+    CKS(solve_tri(p, p->Q, f, true));
+    RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W1, p->has_gD ? p->gD : nullptr, p->st));
+    return AHOC_OK;
+  }
   // recovery: V and U with the converged Q (and the data)
   CKS(solve_VU(p, p->Q, f, true));
   RUN(AHOC_K_OTHER, launch_write_full(g, u, p->W2, p->has_gD ? p->gD : nullptr, p->st));
@@ -2118,6 +2348,11 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
     for (int i = 0; i < nb; ++i) {
       if (!live[i]) continue;
       ProbStat& s = p->ps[i];
+      if (!is_fin(bn[i])) {  // NaN or Inf in this problem: it leaves the batch, the others refine on
+        s.status = AHOC_ENUMERIC;
+        live[i] = 0;
+        continue;
+      }
       if (step == 0) bref[i] = bn[i];
       s.rel = (bref[i] > 0) ? bn[i] / bref[i] : 0.0;
       s.hist[step] = s.rel;
@@ -2166,6 +2401,10 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
       s.restarts += gi[i].restarts;
       s.ms_mv += gi[i].ms_mv;
       s.inner[step] = gi[i].iters;
+      if (gi[i].status == AHOC_ENUMERIC) {
+        s.status = AHOC_ENUMERIC;
+        live[i] = 0;
+      }
     }
     // recovery of the correction and the FP64 update
     CKS(set_act(p, live));
@@ -2232,7 +2471,7 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
   for (int i = 0; i < p->g.nb; ++i) {
     if (!p->part[i]) continue;
     const ProbStat& s = p->ps[i];
-    if (s.status != AHOC_OK) st = s.status;
+    if (s.status != AHOC_OK && st != AHOC_ENUMERIC) st = s.status;
     if (!info) continue;
     ahoc_info* in = info + i;
     in->status = s.status;
@@ -2258,6 +2497,9 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
       in->kernel_launches_top[k] = p->kn[k] + p->kn_top[k];
     }
   }
+  if (st == AHOC_ENUMERIC)
+    return fail(st, "NaN or Inf in a problem's data or iterates: that problem was masked out of the batch "
+                    "(info[b].status), the others were solved");
   if (st != AHOC_OK) return fail(st, "GMRES reached max_iters (or refinement did not converge)");
   return AHOC_OK;
 }

@@ -87,7 +87,7 @@ __global__ void k_vrhs(Geom g, Coefs cf, T* __restrict__ out, const double* __re
     T m = (T)cf.Mc * (T)f[g.full(i, j, k)];
     m += (T)cf.Mn * (T)(f[g.full(i - 1, j, k)] + f[g.full(i + 1, j, k)] + f[g.full(i, j - 1, k)] + f[g.full(i, j + 1, k)]);
     if (g.dim == 3) m += (T)cf.Mn * (T)(f[g.full(i, j, k - 1)] + f[g.full(i, j, k + 1)]);
-    acc -= m;
+    acc += (T)cf.fsign * m;
   }
   if (srcv) acc -= srcv[t];
   out[t] = acc;
@@ -209,6 +209,52 @@ __global__ void k_trace(Geom g, Coefs cf, double* __restrict__ y, const T* __res
   y[q] = res;
 }
 
+// Triharmonic class: R_p = u_ssss(U)_p + lapt_w_p - Q_p at a clamped face point
+// (Lap^2 u there, with u_ssss one-sided from U_0 = g_D, U_1..U_4 and the data
+// u_s = -g_N, u_ss = g_NN), R_p = bilap_p - Q_p on the other faces (Lap^2 u is
+// data there).  Data arrays may be NULL (zero).
+__global__ void k_trace_tri(Geom g, Coefs cf, double* __restrict__ y, const double* __restrict__ U,
+                            const double* __restrict__ Q, const double* __restrict__ gD,
+                            const double* __restrict__ gN, const double* __restrict__ gNN,
+                            const double* __restrict__ laptw, const double* __restrict__ bilap) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bi = blockIdx.y;
+  if (q >= g.ngamma || g.skip(bi)) return;
+  const int64_t fo = (int64_t)bi * g.ngamma, ff = (int64_t)bi * g.nfull;
+  int f = 0;
+  while (q >= g.face_off[f + 1]) ++f;
+  const int a = f >> 1, side = f & 1;
+  const int64_t loc = q - g.face_off[f];
+  int c[3] = {0, 0, 0};
+  int64_t r = loc;
+  for (int b = 0; b < g.dim; ++b) {
+    if (b == a) continue;
+    const int nb = g.N[b] - 1;
+    c[b] = 1 + (int)(r % nb);
+    r /= nb;
+  }
+  c[a] = side ? g.N[a] : 0;
+  double res;
+  if (g.is_navier(f)) {
+    res = bilap ? bilap[ff + g.full(c[0], c[1], c[2])] : 0.0;
+  } else {
+    U += (int64_t)bi * g.npad;
+    const int step = side ? -1 : 1;
+    res = 0.0;
+    for (int m = 1; m <= 4; ++m) {
+      int p[3] = {c[0], c[1], c[2]};
+      p[a] = c[a] + m * step;
+      res += cf.w4[a][m] * U[g.pad(p[0], p[1], p[2])];
+    }
+    if (gD) res += cf.w4[a][0] * gD[ff + g.full(c[0], c[1], c[2])];
+    if (gN) res -= cf.w4s[a] * gN[fo + q];
+    if (gNN) res += cf.w4ss[a] * gNN[fo + q];
+    if (laptw) res += laptw[fo + q];
+  }
+  if (Q) res -= Q[fo + q];
+  y[fo + q] = res;
+}
+
 // full-grid output: interior from the padded field, boundary from bnd (or 0)
 __global__ void k_write_full(Geom g, double* __restrict__ out, const double* __restrict__ Uin,
                              const double* __restrict__ bnd) {
@@ -292,10 +338,48 @@ __global__ void k_face_gather(Geom g, double* __restrict__ face, const double* _
 
 __global__ void k_recip(double* __restrict__ out, const double* __restrict__ in, int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) out[t] = 1.0 / in[t];
+  if (t < n) out[t] = in ? 1.0 / in[t] : 1.0;  // in == NULL: a unit coefficient
 }
 
 static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+// min, max and sum of beta / alpha over n points, one triple per block
+// (out[3 b .. 3 b + 2]), summed by the host in block order
+constexpr int kStatThreads = 256;
+__global__ void __launch_bounds__(kStatThreads) k_ratio_stats(const double* __restrict__ beta,
+                                                              const double* __restrict__ alpha, int64_t n,
+                                                              double* __restrict__ out) {
+  __shared__ double smin[kStatThreads], smax[kStatThreads], ssum[kStatThreads];
+  double mn = INFINITY, mx = -INFINITY, sm = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double r = beta[t] / alpha[t];
+    mn = fmin(mn, r);
+    mx = fmax(mx, r);
+    sm += r;
+  }
+  smin[threadIdx.x] = mn;
+  smax[threadIdx.x] = mx;
+  ssum[threadIdx.x] = sm;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+      ssum[threadIdx.x] += ssum[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[3 * blockIdx.x] = smin[0];
+    out[3 * blockIdx.x + 1] = smax[0];
+    out[3 * blockIdx.x + 2] = ssum[0];
+  }
+}
+cudaError_t launch_ratio_stats(const double* beta, const double* alpha, int64_t n, double* out, int blocks,
+                               cudaStream_t st) {
+  k_ratio_stats<<<blocks, kStatThreads, 0, st>>>(beta, alpha, n, out);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_vrhs(const Geom& g, const Coefs& cf, T* out, const double* Q, const double* f,
@@ -316,6 +400,12 @@ cudaError_t launch_trace(const Geom& g, const Coefs& cf, double* y, const T* U, 
                          const double* afac, const double* gD, const double* gN, const double* lapt,
                          cudaStream_t st, const double* srcq, const double* gL) {
   k_trace<T><<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, y, U, Q, afac, gD, gN, lapt, srcq, gL);
+  return cudaGetLastError();
+}
+cudaError_t launch_trace_tri(const Geom& g, const Coefs& cf, double* y, const double* U, const double* Q,
+                             const double* gD, const double* gN, const double* gNN, const double* laptw,
+                             const double* bilap, cudaStream_t st) {
+  k_trace_tri<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, y, U, Q, gD, gN, gNN, laptw, bilap);
   return cudaGetLastError();
 }
 cudaError_t launch_write_full(const Geom& g, double* out, const double* Uin, const double* bnd, cudaStream_t st) {

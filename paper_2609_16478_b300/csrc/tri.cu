@@ -220,22 +220,65 @@ __device__ __forceinline__ T vgen(const VGen2D<T>& G, int k, int j, int Nt) {
   return v;
 }
 
-// right-hand side element: GEN 0 loaded, 1 generated, 2 loaded + generated
-template <typename T, int GEN>
-__device__ __forceinline__ T rhs_elem(const T* col, const VGen2D<T>& G, int k, int j, const TriShape& sh) {
-  if (GEN == 0) return col[(int64_t)j * sh.stride];
-  if (GEN == 1) return vgen(G, k, j, sh.Nt);
-  return col[(int64_t)j * sh.stride] + vgen(G, k, j, sh.Nt);
+// The generated right-hand side of one mode column m, as a function of the
+// row j: 2D from VGen2D (x-mode k = m + 1), 3D from VGen3D (x- and y-modes).
+template <typename T>
+struct ColGen2 {
+  VGen2D<T> G;
+  int k, Nt;
+  __device__ __forceinline__ T operator()(int j) const { return vgen(G, k, j, Nt); }
+};
+template <typename T>
+struct ColGen3 {
+  T ax, ay;
+  const T *A, *B, *Zm, *Zp;
+  int nx, ny, nt;
+  __device__ __forceinline__ T operator()(int j) const {
+    T v = ax * A[(int64_t)(j - 1) * ny] + ay * B[(int64_t)(j - 1) * nx];
+    if (j == 1) v += *Zm;
+    if (j == nt) v += *Zp;
+    return v;
+  }
+};
+template <typename T>
+__device__ __forceinline__ ColGen2<T> col_gen(VGen2D<T> G, const Geom& g, int b, int64_t m, const TriShape& sh) {
+  vgen_at(G, g, b);
+  return ColGen2<T>{G, (int)m + 1, sh.Nt};
+}
+template <typename T>
+__device__ __forceinline__ ColGen3<T> col_gen(const VGen3D<T>& G, const Geom& g, int b, int64_t m,
+                                              const TriShape& sh) {
+  ColGen3<T> c;
+  const int nx = g.N[0] - 1, ny = g.N[1] - 1;
+  const int ix = 1 + (int)(m % nx), iy = 1 + (int)(m / nx);
+  const T* gen = G.gen ? G.gen + (int64_t)b * g.ngamma : nullptr;
+  c.ax = G.sx ? G.sx[ix] : (T)0;
+  c.ay = G.sy ? G.sy[iy] : (T)0;
+  c.A = gen ? gen + g.face_off[(ix & 1) ? 0 : 1] + (iy - 1) : nullptr;
+  c.B = gen ? gen + g.face_off[(iy & 1) ? 2 : 3] + (ix - 1) : nullptr;
+  c.Zm = gen ? gen + g.face_off[4] + m : nullptr;
+  c.Zp = gen ? gen + g.face_off[5] + m : nullptr;
+  c.nx = nx;
+  c.ny = ny;
+  c.nt = sh.nt;
+  return c;
 }
 
-template <typename T, int L, int GEN>
+// right-hand side element: GEN 0 loaded, 1 generated, 2 loaded + generated
+template <typename T, int GEN, class CG>
+__device__ __forceinline__ T rhs_elem(const T* col, const CG& cg, int j, const TriShape& sh) {
+  if (GEN == 0) return col[(int64_t)j * sh.stride];
+  if (GEN == 1) return cg(j);
+  return col[(int64_t)j * sh.stride] + cg(j);
+}
+
+template <typename T, int L, int GEN, class GT>
 __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                double* __restrict__ E, VGen2D<T> G) {
+                                                double* __restrict__ E, GT G) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   a += (int64_t)blockIdx.y * g.npad;
   E += (int64_t)blockIdx.y * tri_sstride(sh);
-  vgen_at(G, g, blockIdx.y);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
   const int64_t m = t % sh.ncols;
@@ -244,10 +287,11 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   const int len = min(L, sh.nt - s0 + 1);
   const T* col = a + col_base(g, m);
   const T q1 = modes[m].q1, s = modes[m].s;
+  const auto cg = col_gen(G, g, blockIdx.y, m, sh);
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
-    d[q] = (q < len) ? rhs_elem<T, GEN>(col, G, (int)m + 1, s0 + q, sh) : (T)0;
+    d[q] = (q < len) ? rhs_elem<T, GEN>(col, cg, s0 + q, sh) : (T)0;
   T w = 0;
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -285,15 +329,14 @@ __global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const 
   }
 }
 
-template <typename T, int L, int GEN>
+template <typename T, int L, int GEN, class GT>
 __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const Mode<T>* __restrict__ modes,
-                                                const double* __restrict__ carry, double* __restrict__ B, VGen2D<T> G) {
+                                                const double* __restrict__ carry, double* __restrict__ B, GT G) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   a += (int64_t)blockIdx.y * g.npad;
   carry += (int64_t)blockIdx.y * tri_sstride(sh);
   B += (int64_t)blockIdx.y * tri_sstride(sh);
-  vgen_at(G, g, blockIdx.y);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= sh.ncols * sh.C) return;
   const int64_t m = t % sh.ncols;
@@ -302,10 +345,11 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
   const int len = min(L, sh.nt - s0 + 1);
   T* col = a + col_base(g, m);
   const T q1 = modes[m].q1, s = modes[m].s;
+  const auto cg = col_gen(G, g, blockIdx.y, m, sh);
   T d[L];
 #pragma unroll
   for (int q = 0; q < L; ++q)
-    d[q] = (q < len) ? rhs_elem<T, GEN>(col, G, (int)m + 1, s0 + q, sh) : (T)0;
+    d[q] = (q < len) ? rhs_elem<T, GEN>(col, cg, s0 + q, sh) : (T)0;
   T w = (T)carry[(int64_t)c * sh.ncols + m];
 #pragma unroll
   for (int q = 0; q < L; ++q)
@@ -741,9 +785,9 @@ size_t tri_chunked_scratch(const Geom& g, int L) {
   return (size_t)(4 * C + 1) * ncols;  // doubles (the carries are FP64 for every T)
 }
 
-template <typename T, int L, int GEN>
+template <typename T, int L, int GEN, class GT>
 static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
-                                 const double* rpow, double* scratch, const VGen2D<T>& G, cudaStream_t st) {
+                                 const double* rpow, double* scratch, const GT& G, cudaStream_t st) {
   const int nx = g.N[0] - 1;
   const int64_t ncols = (g.dim == 3) ? (int64_t)nx * (g.N[1] - 1) : nx;
   const int nt = ((g.dim == 3) ? g.N[2] : g.N[1]) - 1;
@@ -756,9 +800,9 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, cons
   const int64_t work = ncols * C;
   const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
   const dim3 cb((unsigned)((ncols + 127) / 128), (unsigned)g.nb);
-  k_tri_t1<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, G);
+  k_tri_t1<T, L, GEN, GT><<<gb, 128, 0, st>>>(g, a, modes, E, G);
   k_tri_t1b<<<cb, 128, 0, st>>>(g, md64, E, carry, L);
-  k_tri_t2<T, L, GEN><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
+  k_tri_t2<T, L, GEN, GT><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
   k_tri_t2b<<<cb, 128, 0, st>>>(g, md64, B, bcarry, Cc, L);
   k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, md64, rpow, bcarry, Cc);
   return cudaGetLastError();
@@ -820,6 +864,20 @@ cudaError_t launch_tri_chunked_gen(const Geom& g, T* a, const Mode<T>* modes, co
                          : tri_chunked_L<T, 8, 1>(g, a, modes, md64, rpow, scratch, G, st);
   return cudaErrorInvalidValue;
 }
+// the same solve with the 3D v-equation right-hand side generated from VGen3D
+template <typename T>
+cudaError_t launch_tri_chunked_gen3(const Geom& g, T* a, const Mode<T>* modes, const Mode<double>* md64,
+                                    const double* rpow, double* scratch, int L, const VGen3D<T>& G,
+                                    cudaStream_t st) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  if (L == 32) return tri_chunked_L<T, 32, 1>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 16) return tri_chunked_L<T, 16, 1>(g, a, modes, md64, rpow, scratch, G, st);
+  if (L == 8) return tri_chunked_L<T, 8, 1>(g, a, modes, md64, rpow, scratch, G, st);
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_tri_chunked_gen3<float>(const Geom&, float*, const Mode<float>*, const Mode<double>*,
+                                                    const double*, double*, int, const VGen3D<float>&, cudaStream_t);
+
 template cudaError_t launch_tri_chunked_gen<double>(const Geom&, double*, const Mode<double>*, const Mode<double>*,
                                                     const double*, double*, int, const VGen2D<double>&, cudaStream_t,
                                                     bool);

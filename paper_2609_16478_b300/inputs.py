@@ -568,6 +568,7 @@ class RequestSpec:
     N: int
     m: Tuple[int, ...]
     arrival: float  # seconds from the start of the stream
+    deadline: Optional[float] = None  # seconds from the start of the stream; None: no deadline
 
 
 def request_stream(n: int, rate: float, seed: int = 5, p2d: float = 0.7,

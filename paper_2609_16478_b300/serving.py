@@ -80,6 +80,7 @@ class Scheduler:
         self.slots: Dict[Key, List[SlotState]] = {}
         self.used = 0
         self.evicted: List[SlotState] = []  # plans the executor must free
+        self.expired: List = []  # queued requests whose deadline passed before they were admitted
 
     @staticmethod
     def key_of(req) -> Key:
@@ -90,6 +91,28 @@ class Scheduler:
 
     def pending(self) -> int:
         return sum(len(q) for q in self.queues.values())
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a queued request; False if it is not queued (already taken
+        into a batch, which then runs to its end, or unknown)."""
+        for q in self.queues.values():
+            for r in q:
+                if r.rid == rid:
+                    q.remove(r)
+                    return True
+        return False
+
+    def _expire(self, now: float) -> None:
+        for q in self.queues.values():
+            keep = [r for r in q if getattr(r, "deadline", None) is None or r.deadline >= now]
+            if len(keep) != len(q):
+                self.expired += [r for r in q if not (getattr(r, "deadline", None) is None or r.deadline >= now)]
+                q.clear()
+                q.extend(keep)
+
+    def take_expired(self) -> List:
+        out, self.expired = self.expired, []
+        return out
 
     def _evict_for(self, need: int, keep: Key) -> bool:
         """Evict idle plans of other shapes (LRU) until `need` more bytes fit."""
@@ -114,7 +137,9 @@ class Scheduler:
 
     def next_work(self, now: float) -> Optional[Work]:
         """The batch to run next: the shape whose oldest request has waited
-        longest among shapes with an idle plan or room for a new one."""
+        longest among shapes with an idle plan or room for a new one.  Queued
+        requests whose deadline has passed are dropped first (take_expired)."""
+        self._expire(now)
         order = sorted((q[0].arrival, k) for k, q in self.queues.items() if q)
         for _, k in order:
             ss = self.slots.setdefault(k, [])
@@ -165,19 +190,25 @@ class Scheduler:
 # device executor
 # ----------------------------------------------------------------------------
 
+STATUS_CANCELLED = -2  # withdrawn by Server.cancel while queued
+STATUS_EXPIRED = 6     # AHOC_ETIMEOUT: its deadline passed while queued
+
+
 @dataclass
 class Record:
     rid: int
     dim: int
     N: int
     arrival: float
-    start: float = 0.0
-    done: float = 0.0
+    start: float = 0.0   # taken from the queue by a worker
+    loaded: float = 0.0  # its coefficient and right-hand side in the plan (request data ready)
+    done: float = 0.0    # its solution in device memory (the solve returned)
     batch: int = 0       # requests solved together with this one (itself included)
     status: int = -1
     iters: int = 0
     refine_steps: int = 0
     err_inf: Optional[float] = None
+    new_plan: bool = False  # its batch created the plan it ran on
 
     @property
     def latency(self) -> float:
@@ -226,6 +257,9 @@ class Server:
         self.sched = Scheduler(budget_bytes, batch_for or default_batch, self._plan_bytes)
         self.results: Dict[int, object] = {}
         self.records: Dict[int, Record] = {}
+        # called with (spec, alpha, f) after a request's data are written into
+        # its plan slot, before the load (tests use it to alter a request)
+        self.data_hook: Optional[Callable] = None
         self.cv = threading.Condition()
         self.error: Optional[BaseException] = None
 
@@ -256,33 +290,41 @@ class Server:
     def _run_work(self, w: Work) -> None:
         from . import inputs
         torch = self.torch
+        t0 = time.perf_counter()
         if w.new_slot:
             w.slot.handle = Server._Slot(self, w.key, w.slot.batch)
         sl: Server._Slot = w.slot.handle
-        t0 = time.perf_counter()
         B = w.slot.batch
         nf = sl.nf
         with torch.cuda.stream(sl.stream):
+            # the request's data: synthesised here from its closed form (a client
+            # would send alpha and f); timed apart from the solve
             for i, spec in enumerate(w.reqs):
                 inputs.sample_request(spec, device=self.device, out_alpha=sl.alpha[i * nf:(i + 1) * nf],
                                       out_f=sl.f[i * nf:(i + 1) * nf])
+                if self.data_hook is not None:
+                    self.data_hook(spec, sl.alpha[i * nf:(i + 1) * nf], sl.f[i * nf:(i + 1) * nf])
                 sl.plan.load(i, sl.alpha[i * nf:(i + 1) * nf])
+            sl.stream.synchronize()
+            t_loaded = time.perf_counter()
             sl.plan.set_active([1 if i < len(w.reqs) else 0 for i in range(B)])
             _, infos = sl.plan.solve(sl.f, sl.u, tol=self.tol, check=False)
             if B == 1:
                 infos = [infos]
+            sl.stream.synchronize()
+            t1 = time.perf_counter()
+            # after the request is done: its result kept, its error against the exact u
             outs = []
             for i, spec in enumerate(w.reqs):
                 ui = sl.u[i * nf:(i + 1) * nf]
                 err = None
-                if self.check_exact:
+                if self.check_exact and infos[i]["status"] == 0:
                     err = float((ui - inputs.exact_request(spec, self.device)).abs().max())
                 outs.append((ui.clone() if self.keep else None, err))
             sl.stream.synchronize()
-        t1 = time.perf_counter()
         for i, spec in enumerate(w.reqs):
             r = self.records[spec.rid]
-            r.start, r.done, r.batch = t0, t1, len(w.reqs)
+            r.start, r.loaded, r.done, r.batch, r.new_plan = t0, t_loaded, t1, len(w.reqs), w.new_slot
             r.status, r.iters, r.refine_steps = infos[i]["status"], infos[i]["iters"], infos[i]["refine_steps"]
             r.err_inf = outs[i][1]
             if self.keep:
@@ -297,7 +339,11 @@ class Server:
                             return
                         if self._fed and self.sched.pending() == 0:
                             return  # every request is taken; in-flight batches finish on their workers
-                        w = self.sched.next_work(time.perf_counter() - t_start)
+                        now = time.perf_counter()
+                        w = self.sched.next_work(now - t_start)
+                        for spec in self.sched.take_expired():
+                            r = self.records[spec.rid]
+                            r.status, r.start, r.done = STATUS_EXPIRED, now, now
                         if w is not None:
                             evicted = self.sched.take_evicted()
                             break
@@ -342,8 +388,21 @@ class Server:
             raise self.error
         for r in self.records.values():
             r.start -= t_start
+            r.loaded -= t_start
             r.done -= t_start
         return [self.records[s.rid] for s in specs]
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request that is still queued (its record gets
+        STATUS_CANCELLED); a request already in a batch runs to its end."""
+        with self.cv:
+            if not self.sched.cancel(rid):
+                return False
+            r = self.records[rid]
+            now = time.perf_counter()
+            r.status, r.start, r.loaded, r.done = STATUS_CANCELLED, now, now, now
+            self.cv.notify_all()
+            return True
 
     def close(self) -> None:
         for ss in self.sched.slots.values():
@@ -354,12 +413,28 @@ class Server:
 
 
 def summarize(records: Sequence[Record]) -> Dict[str, float]:
-    """p50/p99 latency (ms), aggregate DOF/s over the makespan, batch sizes."""
+    """p50/p99 latency (ms) from arrival to the solution in device memory,
+    its parts (queue wait, request data synthesis and load, solve), the
+    aggregate DOF/s over the makespan and the batch sizes, over the requests
+    that were solved (cancelled and expired ones are counted apart)."""
     import numpy as np
+    served = [r for r in records if r.status not in (STATUS_CANCELLED, STATUS_EXPIRED)]
+    dropped = len(records) - len(served)
+    records = served
     lat = np.array([r.latency for r in records]) * 1e3
+    wait = np.array([r.start - r.arrival for r in records]) * 1e3
+    data = np.array([r.loaded - r.start for r in records]) * 1e3
+    solve = np.array([r.done - r.loaded for r in records]) * 1e3
     t0 = min(r.arrival for r in records)
     t1 = max(r.done for r in records)
     dof = sum(r.dof for r in records)
+    parts = {"queue_wait_ms": wait, "data_ms": data, "solve_ms": solve}
+    pct = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))} for k, v in parts.items()}
+    # the slowest 1%: where their time went, and how many ran on a plan created for them
+    k = max(1, len(records) // 100)
+    slow = np.argsort(lat)[-k:]
+    tail = {kk: float(np.mean(v[slow])) for kk, v in parts.items()}
+    tail["new_plan_fraction"] = float(np.mean([records[i].new_plan for i in slow]))
     shapes = {}
     for k in sorted({(r.dim, r.N) for r in records}):
         ls = np.array([r.latency for r in records if (r.dim, r.N) == k]) * 1e3
@@ -368,4 +443,5 @@ def summarize(records: Sequence[Record]) -> Dict[str, float]:
     return dict(requests=len(records), p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 mean_ms=float(lat.mean()), makespan_s=t1 - t0, dof_per_s=dof / (t1 - t0),
                 mean_batch=float(np.mean([r.batch for r in records])),
-                failed=int(sum(1 for r in records if r.status != 0)), by_shape=shapes)
+                failed=int(sum(1 for r in records if r.status != 0)), dropped=dropped, by_shape=shapes,
+                parts=pct, slowest_1pct_mean_ms=tail)

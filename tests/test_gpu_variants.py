@@ -129,3 +129,17 @@ def test_examples2_3_tables(prec, nmax):
             err = float((u.reshape(N + 1, N + 1, N + 1) - d["u_exact"]).abs().max())
             assert abs(err / float(row[col]) - 1) < (0.006 if N <= 256 else 0.01), (N, name, err, row[col], info["iters"])
             p.close()
+
+
+@pytest.mark.parametrize("name,N,variable", [("shift2d", [32, 32], False), ("singular2d", [32, 32], False),
+                                             ("varbeta2d", [32, 32], True)])
+def test_auto_shift_picks_the_beta_class(name, N, variable):
+    """opts.auto_shift: the plan reads beta / alpha and chooses the constant
+    shift (FFT v-solves only) or variable beta (BiCGSTAB v-solves)."""
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    p = ahoc.plan_for(d)
+    u, info = p.solve(torch.as_tensor(d["f"]).reshape(-1).contiguous().cuda(), tol=1e-12)
+    assert (info["vsolve_iters"] > 0) == variable, info["vsolve_iters"]
+    U = u.cpu().numpy().reshape(sol.U.shape)
+    assert np.linalg.norm(U - sol.U) / np.linalg.norm(sol.U) < 1e-10

@@ -64,3 +64,44 @@ def test_plan_larger_than_budget():
     s2.arrive(_req(1, 2, 128, 0.0))
     w = s2.next_work(0.0)
     assert w is not None and s2.next_work(0.0) is None
+
+
+def test_deadline_drops_expired_queued_requests():
+    s = _sched(10_000 * MB, batch=2)
+    a = _req(0, 2, 128, 0.0)
+    b = _req(1, 2, 128, 0.1)
+    b.deadline = 0.5
+    c = _req(2, 2, 128, 0.2)
+    for r in (a, b, c):
+        s.arrive(r)
+    w = s.next_work(1.0)  # b's deadline has passed: dropped, a and c batched
+    assert [r.rid for r in w.reqs] == [0, 2]
+    assert [r.rid for r in s.take_expired()] == [1] and s.take_expired() == []
+    assert s.pending() == 0
+
+
+def test_cancel_withdraws_a_queued_request():
+    s = _sched(10_000 * MB, batch=4)
+    for rid in range(3):
+        s.arrive(_req(rid, 3, 64, 0.1 * rid))
+    assert s.cancel(1) and not s.cancel(1) and not s.cancel(99)
+    w = s.next_work(1.0)
+    assert [r.rid for r in w.reqs] == [0, 2] and w.slot.batch == 2
+    assert not s.cancel(0)  # already in a batch: runs to its end
+    s.release(w, 2.0)
+    assert not w.slot.busy
+
+
+def test_no_over_admission_while_all_plans_busy():
+    """A shape whose plan is busy and whose next plan would exceed the
+    budget waits: the bytes in use never pass the budget (one resident plan
+    may run alone over it only when nothing else is resident)."""
+    s = _sched(300 * MB, batch=1, nbytes=200 * MB, max_slots=4)
+    for rid in range(4):
+        s.arrive(_req(rid, 2, 256, 0.0))
+    w = s.next_work(0.0)
+    assert w is not None and s.used == 200 * MB
+    assert s.next_work(0.0) is None and s.used <= s.budget  # a second 200 MB plan would not fit
+    s.release(w, 1.0)
+    w2 = s.next_work(1.5)  # the idle plan is reused
+    assert w2.slot is w.slot and s.used == 200 * MB
