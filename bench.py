@@ -344,9 +344,11 @@ def serving_variant(args, dev):
                     "Fourier coefficient (M=6, K=4, A=0.5, seed = request id) and u = prod sin^2(pi x) cos(m pi x), "
                     "m in 0..4; Schur tol %g"
                     % (len(specs), rate, cap["fp64"], cap["mixed"], list(inputs.SERVE_2D), list(inputs.SERVE_3D), tol),
-        "latency": "arrival to the solution in device memory; parts: queue wait, request data (synthesised on the "
-                   "worker's stream from closed forms and loaded into the plan), solve; the error check against the "
-                   "exact u runs after it",
+        "latency": "from the request's arrival with its data (alpha and f, synthesised from closed forms on a "
+                   "feeder stream before the request enters the queue, as a client upload would be complete) to "
+                   "its solution in device memory; parts: queue wait, copy of the data into the plan slot and "
+                   "ahoc_plan_load, solve; the error check against the exact u runs after it.  Plans of shapes "
+                   "up to 2^21 interior points run on high-priority streams",
         "batched_mixed": dict(sa, workers=args.serve_workers, plan_slots_per_shape=args.serve_slots,
                               batch="per shape from the autotuner: %s" % {k: v["batch"] for k, v in cache.items()}),
         "batched_fp64": dict(sb, workers=args.serve_workers, batch="as batched_mixed"),

@@ -358,7 +358,7 @@ int ahoc_batch(const ahoc_plan* p);
  *   AHOC_TUNE_TRI_CHUNK    rows per thread of the chunked tridiagonal solve
  *                          along the last axis: 8, 16 or 32 (key N: that axis)
  *   AHOC_TUNE_DST_THREADS  threads per CTA of the line DSTs along x and y:
- *                          128, 256 or 512 (key N: the x axis)
+ *                          128, 256, 512 or 1024 (key N: the x axis)
  * value 0 restores the built-in choice.  The shapes change rounding, not the
  * discrete problem: results stay within the solver's tolerance.  The FFT
  * radix is fixed (radix 4, one radix-2 stage when log2(N/2) is odd). */

@@ -5,8 +5,9 @@ solves of a seeded request of that shape (``inputs.sample_request``):
 
   * the chunk length of the tridiagonal solve along the last axis
     (``AHOC_TUNE_TRI_CHUNK``: 8, 16, 32 rows per thread);
-  * the CTA size of the line DSTs (``AHOC_TUNE_DST_THREADS``: 128, 256, 512
-    threads; it matters where a line has fewer than 512 / 8 points per thread);
+  * the CTA size of the line DSTs (``AHOC_TUNE_DST_THREADS``: 128, 256, 512,
+    1024 threads: the lines a CTA holds, hence the width of the row segments
+    the y-transform reads and writes);
   * the batch size B of the serving plans: the per-problem time of a batched
     solve for B = 1, 2, 4, ... up to a memory cap; among the batches that
     finish within ``latency_factor`` times a single solve, the smallest B
@@ -27,7 +28,7 @@ import time
 from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
 TRI_CHOICES = (8, 16, 32)
-CTA_CHOICES = (128, 256, 512)
+CTA_CHOICES = (128, 256, 512, 1024)
 
 # choices measured on a B300 for the serving shapes, mixed precision
 # (``tune([(2, 128), ..., (3, 256)], "mixed", path=...)``); re-run to refresh

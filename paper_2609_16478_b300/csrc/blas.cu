@@ -215,4 +215,135 @@ cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// GMRES's Hessenberg QR on the device (one thread per problem).  Per-problem
+// state (GivensLayout): the rotated columns R (column j at j * (m + 1)), the
+// rotations cs, sn, the rotated right-hand side g, and the scalars beta0
+// (||b||), tol and rel (the residual estimate); ints iters, maxit, status,
+// jend (columns of this cycle) and cyc (taking part in this cycle).
+// ---------------------------------------------------------------------------
+struct GivensView {
+  double *R, *cs, *sn, *g, *sc;
+  int* st;
+};
+__device__ __forceinline__ GivensView givens_view(double* gs, int* gi, int b, int m) {
+  GivensView v;
+  v.R = gs + (int64_t)b * givens_doubles(m);
+  v.cs = v.R + (int64_t)(m + 1) * m;
+  v.sn = v.cs + m;
+  v.g = v.sn + m;
+  v.sc = v.g + (m + 1);
+  v.st = gi + kGivensInts * b;
+  return v;
+}
+
+// start of a cycle: ini[3 b .. 3 b + 2] = (beta, beta0, tol), ii[2 b .. 2 b + 1] = (iters, maxit)
+__global__ void k_givens_init(int nb, int m, const int* __restrict__ act, const double* __restrict__ ini,
+                              const int* __restrict__ ii, double* __restrict__ gs, int* __restrict__ gi,
+                              double* __restrict__ rel) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  GivensView v = givens_view(gs, gi, b, m);
+  v.g[0] = ini[3 * b];
+  v.sc[0] = ini[3 * b + 1];
+  v.sc[1] = ini[3 * b + 2];
+  v.sc[2] = ini[3 * b + 1] > 0 ? ini[3 * b] / ini[3 * b + 1] : 0.0;
+  rel[b] = v.sc[2];
+  v.st[0] = ii[2 * b];
+  v.st[1] = ii[2 * b + 1];
+  v.st[2] = 0;
+  v.st[3] = 0;
+  v.st[4] = act[b];
+}
+
+// step j: column j of the Hessenberg matrix from the CGS2 coefficients of
+// both passes (h[k] + h[j + 1 + k]) and ||w|| (h[2 (j + 1)] holds ||w||^2),
+// the earlier rotations, a new rotation zeroing the subdiagonal, and the
+// residual estimate |g[j + 1]| / beta0.  A problem that converges, reaches
+// maxit or meets a NaN / Inf leaves the mask; the others get 1 / ||w|| for
+// the normalisation of the next Krylov vector.
+__global__ void k_givens_step(int j, int nb, int m, const double* __restrict__ hdev, int hs, int* __restrict__ act,
+                              double* __restrict__ scal, double* __restrict__ gs, int* __restrict__ gi,
+                              double* __restrict__ relo) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || !act[b]) return;
+  GivensView v = givens_view(gs, gi, b, m);
+  const double* hh = hdev + (int64_t)b * hs;
+  double* Hc = v.R + (int64_t)j * (m + 1);
+  bool bad = false;
+  for (int k = 0; k <= j; ++k) {
+    Hc[k] = hh[k] + hh[j + 1 + k];
+    bad = bad || !isfinite(Hc[k]);
+  }
+  const double hn = sqrt(hh[2 * (j + 1)]);
+  bad = bad || !isfinite(hn);
+  v.st[0] += 1;
+  if (bad) {  // this problem leaves the batch; its iterate stays as at the cycle start
+    v.st[2] = kGivensNumeric;
+    v.st[3] = 0;
+    act[b] = 0;
+    return;
+  }
+  Hc[j + 1] = hn;
+  for (int k = 0; k < j; ++k) {
+    const double a = Hc[k], c = Hc[k + 1];
+    Hc[k] = v.cs[k] * a + v.sn[k] * c;
+    Hc[k + 1] = -v.sn[k] * a + v.cs[k] * c;
+  }
+  const double den = hypot(Hc[j], Hc[j + 1]);
+  v.cs[j] = (den > 0) ? Hc[j] / den : 1.0;
+  v.sn[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
+  Hc[j] = den;
+  Hc[j + 1] = 0.0;
+  v.g[j + 1] = -v.sn[j] * v.g[j];
+  v.g[j] = v.cs[j] * v.g[j];
+  v.st[3] = j + 1;
+  const double rel = fabs(v.g[j + 1]) / v.sc[0];
+  v.sc[2] = rel;
+  relo[b] = rel;
+  if (rel <= v.sc[1] || hn == 0.0) {
+    act[b] = 0;  // converged
+  } else if (v.st[0] >= v.st[1]) {
+    act[b] = 0;
+    v.st[2] = kGivensNoConv;
+  } else {
+    scal[b] = 1.0 / hn;
+  }
+}
+
+// end of a cycle: y = R^-1 g over the cycle's columns (back substitution),
+// hy[b * hs + k] = -y_k for the update X -= Z hy, ncols[b] = the columns used
+// (0 for problems outside the cycle); summary[b] = (iters, status, jend) and
+// rel[b] for the host.
+__global__ void k_givens_solve(int nb, int m, const double* __restrict__ gs, const int* __restrict__ gi,
+                               double* __restrict__ hy, int hs, int* __restrict__ ncols) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  GivensView v = givens_view(const_cast<double*>(gs), const_cast<int*>(gi), b, m);
+  const int je = v.st[4] ? v.st[3] : 0;
+  ncols[b] = je;
+  double* y = hy + (int64_t)b * hs;
+  for (int k = je - 1; k >= 0; --k) {
+    double acc = v.g[k];
+    for (int l = k + 1; l < je; ++l) acc -= v.R[(int64_t)l * (m + 1) + k] * (-y[l]);
+    y[k] = -(acc / v.R[(int64_t)k * (m + 1) + k]);
+  }
+}
+
+cudaError_t launch_givens_init(int nb, int m, const int* act, const double* ini, const int* ii, double* gs, int* gi,
+                               double* rel, cudaStream_t st) {
+  k_givens_init<<<(nb + 31) / 32, 32, 0, st>>>(nb, m, act, ini, ii, gs, gi, rel);
+  return cudaGetLastError();
+}
+cudaError_t launch_givens_step(int j, int nb, int m, const double* hdev, int hs, int* act, double* scal, double* gs,
+                               int* gi, double* rel, cudaStream_t st) {
+  k_givens_step<<<(nb + 31) / 32, 32, 0, st>>>(j, nb, m, hdev, hs, act, scal, gs, gi, rel);
+  return cudaGetLastError();
+}
+cudaError_t launch_givens_solve(int nb, int m, const double* gs, const int* gi, double* hy, int hs, int* ncols,
+                                cudaStream_t st) {
+  k_givens_solve<<<(nb + 31) / 32, 32, 0, st>>>(nb, m, gs, gi, hy, hs, ncols);
+  return cudaGetLastError();
+}
+
 }  // namespace ahoc

@@ -297,7 +297,7 @@ __device__ __forceinline__ T mstencil3d(const Geom& g, const DstIO<T>& io, int i
 }
 
 template <typename T, int LOAD, int STORE>
-__global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<T> io,
+__global__ void __launch_bounds__(1024) k_dst_x(Geom g, T* __restrict__ a, DstIO<T> io,
                                                const typename Cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ sn, T scale, int logN, int TPL, int LPC) {
   const int bi = blockIdx.y;  // problem of the batch
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(512) k_dst_x(Geom g, T* __restrict__ a, DstIO<
 // columns are staged through shared memory so global accesses stay row-wise.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) k_dst_y(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
+__global__ void __launch_bounds__(1024) k_dst_y(Geom g, T* __restrict__ a, const typename Cplx<T>::t* __restrict__ tw,
                                                const T* __restrict__ sn, T scale, int logN, int TPL, int LPC, int LS) {
   const int bi = blockIdx.z;
   if (g.skip(bi)) return;

@@ -241,4 +241,18 @@ cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t
                          const double* a_b = nullptr, const int* act = nullptr, int64_t ystride = -1,
                          int64_t xstride = -1);
 
+// GMRES's Hessenberg QR on the device (blas.cu): per-problem state of
+// givens_doubles(m) doubles and kGivensInts ints (iters, maxit, status, jend,
+// cyc); status codes as ahoc_status (0 ok, kGivensNoConv, kGivensNumeric)
+constexpr int kGivensInts = 5;
+constexpr int kGivensNoConv = 4;   // AHOC_ENOCONV
+constexpr int kGivensNumeric = 5;  // AHOC_ENUMERIC
+__host__ __device__ inline int64_t givens_doubles(int m) { return (int64_t)(m + 1) * m + 2 * m + (m + 1) + 3; }
+cudaError_t launch_givens_init(int nb, int m, const int* act, const double* ini, const int* ii, double* gs, int* gi,
+                               double* rel, cudaStream_t st);
+cudaError_t launch_givens_step(int j, int nb, int m, const double* hdev, int hs, int* act, double* scal, double* gs,
+                               int* gi, double* rel, cudaStream_t st);
+cudaError_t launch_givens_solve(int nb, int m, const double* gs, const int* gi, double* hy, int hs, int* ncols,
+                                cudaStream_t st);
+
 }  // namespace ahoc

@@ -372,7 +372,9 @@ struct Layout {
       // part of Lap^2 u on the faces, Lap u gathered on the faces
       lapgD, bilap, gNN, laptw, vface,
       // fused 3D matvec of the mixed path: FP32 generator, y sine table and y trace weights
-      gen3f, skyf, tauyf, total;
+      gen3f, skyf, tauyf,
+      // GMRES's Hessenberg QR on the device: per-problem state, residual estimates, cycle start values
+      gs, gi, grel, gini, gii, total;
 };
 
 // The chunked tridiagonal form is used when the transverse modes alone give
@@ -412,6 +414,9 @@ bool chunked_for(const Geom& g, ahoc_precision prec) {
 bool tri2_for(const Geom& g) { return tri_ncols(g) < kChunkedBelow; }
 
 constexpr int kDotBlocks = 296;  // 2 x 148 SMs
+// Arnoldi steps per CUDA graph: the host reads the per-problem convergence
+// state once per block (the steps of a block run back to back on the device)
+constexpr int kArnoldiBlock = 4;
 
 // per-problem sizes of the GMRES scratch: dot partials and the device side
 // of the Hessenberg column exchange
@@ -514,6 +519,11 @@ Layout make_layout(const Geom& g, const Opts& o) {
   L.partial = take(B * (size_t)pstride(o) * sizeof(double));
   L.hdev = take(B * (size_t)hstride(o) * sizeof(double));
   L.cgscnt = take(B * (size_t)cgs_groups(o) * sizeof(int));
+  L.gs = take(B * (size_t)givens_doubles(o.restart) * sizeof(double));
+  L.gi = take(B * (size_t)kGivensInts * sizeof(int));
+  L.grel = take(B * sizeof(double));
+  L.gini = take(3 * B * sizeof(double));
+  L.gii = take(2 * B * sizeof(int));
   L.act = take(B * sizeof(int));
   L.scal = take(B * sizeof(double));
   L.ncolsb = take(B * sizeof(int));
@@ -650,6 +660,13 @@ struct ahoc_plan {
   double* scal = nullptr;  // per-problem scalars of the batched axpy
   int* ncolsb = nullptr;   // per-problem column counts of the batched update
   int* cgscnt = nullptr;   // zeroed counters of the fused CGS passes (launch_cgs)
+  // device Hessenberg QR (blas.cu, k_givens_*): state, residual estimates,
+  // cycle start values; pinned host copies of the start values and of the
+  // state read back after each block of Arnoldi steps
+  double *gs = nullptr, *grel = nullptr, *gini = nullptr;
+  int *gi = nullptr, *gii = nullptr;
+  double *gini_h = nullptr, *rb_rel = nullptr;
+  int *gii_h = nullptr, *rb_act = nullptr, *rb_gi = nullptr;
   std::vector<int> act_now, part;  // current mask; problems taking part in solves
   std::vector<ProbStat> ps;
   bool has_gD = false, has_vedge = false, has_gN = false, has_lapt = false;
@@ -1310,12 +1327,19 @@ ahoc_status ahoc_workspace_bytes(int dim, const int64_t* N, const ahoc_opts* opt
   CKS(make_geom(dim, N, nullptr, nullptr, &g));
   Opts o;
   CKS(read_opts(opts, &o));
-  if (opts && opts->auto_shift && !o.tri) {  // the data decide the beta class: size for the larger one
-    o.varb = 1;
-    o.shift = 1.0;
-  }
   g.nb = o.batch;
   apply_tuning(g, o);
+  if (opts && opts->auto_shift && !o.tri) {
+    // the data decide the beta class: size for the larger of the two
+    // (variable beta: BiCGSTAB fields; constant shift: shifted tables, U-hat slots)
+    Opts a = o, b = o;
+    a.varb = 1;
+    a.shift = 1.0;
+    b.varb = 0;
+    b.shift = 1.0;
+    *bytes = std::max(total_bytes(g, a), total_bytes(g, b));
+    return AHOC_OK;
+  }
   *bytes = total_bytes(g, o);
   return AHOC_OK;
 }
@@ -1450,6 +1474,11 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   p->scal = at<double>(p, L.scal);
   p->ncolsb = at<int>(p, L.ncolsb);
   p->cgscnt = at<int>(p, L.cgscnt);
+  p->gs = at<double>(p, L.gs);
+  p->gi = at<int>(p, L.gi);
+  p->grel = at<double>(p, L.grel);
+  p->gini = at<double>(p, L.gini);
+  p->gii = at<int>(p, L.gii);
   p->g.act = p->act;
   if (o.prec == AHOC_MIXED) {
     p->F1 = at<float>(p, L.F1);
@@ -1486,14 +1515,26 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
   CKC(cudaMallocHost(&p->hhost, B * (size_t)hstride(o) * sizeof(double)));
   CKC(cudaMallocHost(&p->scal_h, B * sizeof(double)));
   CKC(cudaMallocHost(&p->act_h, B * sizeof(int)));
+  CKC(cudaMallocHost(&p->gini_h, 3 * B * sizeof(double)));
+  CKC(cudaMallocHost(&p->gii_h, 2 * B * sizeof(int)));
+  CKC(cudaMallocHost(&p->rb_rel, B * sizeof(double)));
+  CKC(cudaMallocHost(&p->rb_act, B * sizeof(int)));
+  CKC(cudaMallocHost(&p->rb_gi, B * (size_t)kGivensInts * sizeof(int)));
   // the BiCGSTAB v-solves read residual norms on the host inside the matvec
   p->use_graphs = o.graphs && !o.timing && !(o.varb && o.prec == AHOC_FP64);
-  p->gexec.assign(o.restart, nullptr);
-  p->gcount.assign(o.restart, ahoc_plan::GCount{});
+  p->gexec.assign((o.restart + kArnoldiBlock - 1) / kArnoldiBlock, nullptr);
+  p->gcount.assign((o.restart + kArnoldiBlock - 1) / kArnoldiBlock, ahoc_plan::GCount{});
   CKC(cudaEventCreate(&p->ev0));
   CKC(cudaEventCreate(&p->ev1));
   if (p->use_graphs) {
-    CKC(cudaStreamCreateWithFlags(&p->gst, cudaStreamNonBlocking));
+    // the graph stream takes the caller's stream priority, so that a plan on a
+    // high-priority stream keeps it for its GMRES steps
+    int prio = 0;
+    if (stream == nullptr || cudaStreamGetPriority(stream, &prio) != cudaSuccess) {
+      cudaGetLastError();
+      prio = 0;
+    }
+    CKC(cudaStreamCreateWithPriority(&p->gst, cudaStreamNonBlocking, prio));
     CKC(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&p->gev_out, cudaEventDisableTiming));
   }
@@ -1795,7 +1836,8 @@ ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value) {
   if (N < 8 || N > kMaxN || !pow2(N)) return fail(AHOC_EINVAL, "N must be a power of two in [8, 4096]");
   if (prec != AHOC_FP64 && prec != AHOC_MIXED) return fail(AHOC_EINVAL, "prec must be AHOC_FP64 or AHOC_MIXED");
   const bool ok = value == 0 || (kind == AHOC_TUNE_TRI_CHUNK ? (value == 8 || value == 16 || value == 32)
-                                                             : (value == 128 || value == 256 || value == 512));
+                                                             : (value == 128 || value == 256 || value == 512 ||
+                                                                value == 1024));
   if (!ok) return fail(AHOC_EINVAL, "value not offered for this kind");
   g_tune[kind][dim - 2][prec][ilog2i(N)].store(value);
   return AHOC_OK;
@@ -1825,6 +1867,11 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
   if (p->hhost) cudaFreeHost(p->hhost);
   if (p->scal_h) cudaFreeHost(p->scal_h);
   if (p->act_h) cudaFreeHost(p->act_h);
+  if (p->gini_h) cudaFreeHost(p->gini_h);
+  if (p->gii_h) cudaFreeHost(p->gii_h);
+  if (p->rb_rel) cudaFreeHost(p->rb_rel);
+  if (p->rb_act) cudaFreeHost(p->rb_act);
+  if (p->rb_gi) cudaFreeHost(p->rb_gi);
   for (auto& ge : p->gexec)
     if (ge) cudaGraphExecDestroy(ge);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -1932,24 +1979,36 @@ ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
                                 p->hdev + (j + 1), p->st, g.nb, bd, hs, hs, p->cgscnt, false));
   RUN(AHOC_K_KRYLOV, launch_cgs(p->Kry, ld, 1, p->hdev + (j + 1), j + 1, p->tmp, w, n, p->partial, kDotBlocks,
                                 p->hdev + 2 * (j + 1), p->st, g.nb, bd, hs, hs, p->cgscnt, true));
-  CK(cudaMemcpyAsync(p->hhost, p->hdev, (size_t)g.nb * hstride(p->o) * sizeof(double), cudaMemcpyDeviceToHost,
-                     p->st));
+  // column j of the Hessenberg QR, the convergence test and the next 1 / ||w||, on the device
+  RUN(AHOC_K_KRYLOV, launch_givens_step(j, g.nb, p->o.restart, p->hdev, hs, p->act, p->scal, p->gs, p->gi, p->grel,
+                                        p->st));
   return AHOC_OK;
 }
 
-// Run Arnoldi step j with the mask in act_h and the scalars in scal_h: as a
-// replay of its CUDA graph (captured here the first time), or as plain
-// launches.  Returns after the host copy of the Hessenberg area is complete.
-ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
+// Arnoldi steps j0 .. j0 + K - 1 for the problems in the device mask (the
+// mask and the scalars pass from step to step on the device: a problem that
+// converges leaves the mask at once), then the per-problem state (mask,
+// counters, residual estimates) to pinned host memory: one CUDA graph per
+// block start, captured on first use and replayed, or plain launches.
+// Returns after the host copy is complete.
+ahoc_status arnoldi_block(ahoc_plan* p, int j0, int K, int64_t ld) {
   const int nb = p->g.nb;
+  const int slot = j0 / kArnoldiBlock;
   cudaStream_t user = p->st;
+  auto body = [&]() -> ahoc_status {
+    for (int j = j0; j < j0 + K; ++j) CKS(arnoldi_step(p, j, ld, j == 0 ? p->r : p->Kry + (int64_t)j * ld));
+    CK(cudaMemcpyAsync(p->rb_act, p->act, nb * sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaMemcpyAsync(p->rb_gi, p->gi, nb * (size_t)kGivensInts * sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaMemcpyAsync(p->rb_rel, p->grel, nb * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    return AHOC_OK;
+  };
   if (p->use_graphs) {
     // the caller's stream hands over to the plan's graph stream
     CK(cudaEventRecord(p->gev_in, user));
     CK(cudaStreamWaitEvent(p->gst, p->gev_in, 0));
     p->st = p->gst;
   }
-  if (p->use_graphs && !p->gexec[j]) {
+  if (p->use_graphs && !p->gexec[slot]) {
     const int64_t l0 = p->launches;
     int64_t k0[AHOC_NK];
     for (int k = 0; k < AHOC_NK; ++k) k0[k] = p->kn[k];
@@ -1959,21 +2018,17 @@ ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
       // while a capture is open
       std::lock_guard<std::recursive_mutex> lk(capture_mutex());
       if (cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        ahoc_status s = AHOC_OK;
-        if (cudaMemcpyAsync(p->act, p->act_h, nb * sizeof(int), cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
-            cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st) != cudaSuccess)
-          s = AHOC_ECUDA;
-        if (s == AHOC_OK) s = arnoldi_step(p, j, ld, src);
+        const ahoc_status s = body();
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(p->st, &graph);
         if (s == AHOC_OK && e == cudaSuccess && graph &&
-            cudaGraphInstantiate(&p->gexec[j], graph, 0) == cudaSuccess)
+            cudaGraphInstantiate(&p->gexec[slot], graph, 0) == cudaSuccess)
           captured = true;
         if (graph) cudaGraphDestroy(graph);
       }
     }
     // the capture issued nothing: count the graph's launches per replay instead
-    ahoc_plan::GCount& gc = p->gcount[j];
+    ahoc_plan::GCount& gc = p->gcount[slot];
     gc.launches = p->launches - l0;
     p->launches = l0;
     for (int k = 0; k < AHOC_NK; ++k) {
@@ -1985,32 +2040,30 @@ ahoc_status arnoldi_launch(ahoc_plan* p, int j, int64_t ld, const double* src) {
       // call (outside this library); drop the error it left and run this
       // plan with plain launches from now on
       cudaGetLastError();
-      p->gexec[j] = nullptr;
+      p->gexec[slot] = nullptr;
       p->use_graphs = false;
       g_err.clear();
     }
   }
   if (p->use_graphs) {
-    const cudaError_t e = cudaGraphLaunch(p->gexec[j], p->st);
+    const cudaError_t e = cudaGraphLaunch(p->gexec[slot], p->st);
     p->st = user;
     CK(e);
     CK(cudaEventRecord(p->gev_out, p->gst));
     CK(cudaStreamWaitEvent(user, p->gev_out, 0));
-    const ahoc_plan::GCount& gc = p->gcount[j];
+    const ahoc_plan::GCount& gc = p->gcount[slot];
     p->launches += gc.launches;
     for (int k = 0; k < AHOC_NK; ++k) p->kn[k] += gc.kn[k];
-    p->act_now.assign(p->act_h, p->act_h + nb);
   } else {
     if (p->st != user) {  // the capture failed: hand back to the caller's stream
       CK(cudaEventRecord(p->gev_out, p->st));
       p->st = user;
       CK(cudaStreamWaitEvent(user, p->gev_out, 0));
     }
-    CKS(set_act(p, std::vector<int>(p->act_h, p->act_h + nb)));
-    CK(cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    CKS(arnoldi_step(p, j, ld, src));
+    CKS(body());
   }
   CK(cudaStreamSynchronize(p->st));
+  p->act_now.assign(p->rb_act, p->rb_act + nb);
   return harvest(p);
 }
 
@@ -2069,9 +2122,7 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       if (go[i].rel <= tol[i]) live[i] = 0;
     }
   if (!any(live)) return AHOC_OK;
-  std::vector<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), gv((size_t)nb * (m + 1)),
-      y(m), hy((size_t)nb * hs, 0.0);
-  std::vector<int> jend(nb, 0), cyc(nb, 0), nc(nb, 0);
+  std::vector<int> cyc(nb, 0), nc(nb, 0);
   while (any(live)) {
     for (int i = 0; i < nb; ++i)
       if (live[i] && go[i].iters >= maxit[i]) {
@@ -2080,16 +2131,24 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
       }
     if (!any(live)) break;
     cyc = live;
+    // the cycle's start on the device: mask, 1 / beta, and the QR state
     for (int i = 0; i < nb; ++i) {
       p->scal_h[i] = live[i] ? 1.0 / beta[i] : 0.0;
-      jend[i] = 0;
-      std::fill(gv.begin() + (size_t)i * (m + 1), gv.begin() + (size_t)(i + 1) * (m + 1), 0.0);
-      gv[(size_t)i * (m + 1)] = beta[i];
+      p->gini_h[3 * i] = live[i] ? beta[i] : 0.0;
+      p->gini_h[3 * i + 1] = beta0[i];
+      p->gini_h[3 * i + 2] = tol[i];
+      p->gii_h[2 * i] = go[i].iters;
+      p->gii_h[2 * i + 1] = maxit[i];
     }
-    for (int j = 0; j < m; ++j) {
-      for (int i = 0; i < nb; ++i) p->act_h[i] = live[i];
+    CKS(set_act(p, live));
+    CK(cudaMemcpyAsync(p->scal, p->scal_h, nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->gini, p->gini_h, 3 * nb * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->gii, p->gii_h, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, p->st));
+    RUN(AHOC_K_KRYLOV, launch_givens_init(nb, m, p->act, p->gini, p->gii, p->gs, p->gi, p->grel, p->st));
+    for (int j0 = 0; j0 < m && any(live); j0 += kArnoldiBlock) {
+      const int K = std::min(kArnoldiBlock, m - j0);
       CK(cudaEventRecord(p->ev0, p->st));
-      CKS(arnoldi_launch(p, j, ld, j == 0 ? p->r : p->Kry + (int64_t)j * ld));
+      CKS(arnoldi_block(p, j0, K, ld));
       CK(cudaEventRecord(p->ev1, p->st));
       CK(cudaEventSynchronize(p->ev1));
       float evms = 0.f;
@@ -2098,65 +2157,17 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
         if (!live[i]) continue;
         ProbStat& gi = go[i];
         gi.ms_mv += evms;
-        ++gi.iters;
-        const double* hh = p->hhost + (size_t)i * hs;
-        double* Hc = &H[((size_t)i * m + j) * (m + 1)];
-        double* csi = &cs[(size_t)i * m];
-        double* sni = &sn[(size_t)i * m];
-        double* gvi = &gv[(size_t)i * (m + 1)];
-        for (int k = 0; k <= j; ++k) Hc[k] = hh[k] + hh[j + 1 + k];
-        const double hn = std::sqrt(hh[2 * (j + 1)]);
-        bool bad = !is_fin(hn);
-        for (int k = 0; k <= j && !bad; ++k) bad = !is_fin(Hc[k]);
-        if (bad) {
-          // a NaN or Inf in this problem's Arnoldi step: it leaves the batch
-          // with its iterate as it was at the start of the cycle
-          gi.status = AHOC_ENUMERIC;
-          live[i] = 0;
-          jend[i] = 0;
-          continue;
-        }
-        Hc[j + 1] = hn;
-        for (int k = 0; k < j; ++k) {
-          const double a = Hc[k], bb = Hc[k + 1];
-          Hc[k] = csi[k] * a + sni[k] * bb;
-          Hc[k + 1] = -sni[k] * a + csi[k] * bb;
-        }
-        const double den = std::hypot(Hc[j], Hc[j + 1]);
-        csi[j] = (den > 0) ? Hc[j] / den : 1.0;
-        sni[j] = (den > 0) ? Hc[j + 1] / den : 0.0;
-        Hc[j] = den;
-        Hc[j + 1] = 0.0;
-        gvi[j + 1] = -sni[j] * gvi[j];
-        gvi[j] = csi[j] * gvi[j];
-        jend[i] = j + 1;
-        gi.rel = std::fabs(gvi[j + 1]) / beta0[i];
-        if (gi.rel <= tol[i] || hn == 0.0) {
-          live[i] = 0;  // converged
-        } else if (gi.iters >= maxit[i]) {
-          live[i] = 0;
-          gi.status = AHOC_ENOCONV;
-        } else {
-          p->scal_h[i] = 1.0 / hn;  // v_{j+1} = w / ||w||, applied by the next step
-        }
+        const int* st = p->rb_gi + (size_t)kGivensInts * i;
+        gi.iters = st[0];
+        gi.rel = p->rb_rel[i];
+        if (st[2] == kGivensNumeric) gi.status = AHOC_ENUMERIC;
+        if (st[2] == kGivensNoConv) gi.status = AHOC_ENOCONV;
+        live[i] = p->rb_act[i];
       }
-      if (!any(live)) break;
     }
-    // y = H^-1 g (upper triangular), X += Z y, per problem of this cycle
-    for (int i = 0; i < nb; ++i) {
-      nc[i] = cyc[i] ? jend[i] : 0;
-      if (!cyc[i]) continue;
-      const double* gvi = &gv[(size_t)i * (m + 1)];
-      const int je = jend[i];
-      for (int k = je - 1; k >= 0; --k) {
-        double sacc = gvi[k];
-        for (int l = k + 1; l < je; ++l) sacc -= H[((size_t)i * m + l) * (m + 1) + k] * y[l];
-        y[k] = sacc / H[((size_t)i * m + k) * (m + 1) + k];
-      }
-      for (int k = 0; k < je; ++k) hy[(size_t)i * hs + k] = -y[k];
-    }
-    CK(cudaMemcpyAsync(p->hdev, hy.data(), hy.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    CK(cudaMemcpyAsync(p->ncolsb, nc.data(), nb * sizeof(int), cudaMemcpyHostToDevice, p->st));
+    // y = R^-1 g and X += Z y per problem of this cycle, on the device
+    RUN(AHOC_K_KRYLOV, launch_givens_solve(nb, m, p->gs, p->gi, p->hdev, hs, p->ncolsb, p->st));
+    for (int i = 0; i < nb; ++i) nc[i] = cyc[i] ? p->rb_gi[(size_t)kGivensInts * i + 3] : 0;
     CKS(set_act(p, cyc));
     CKS(gemv_sub(p, p->Zb, ld, 0, p->hdev, X, p->ncolsb));
     if (p->bank_valid) {

@@ -238,7 +238,8 @@ class Server:
 
     def __init__(self, device="cuda", prec="mixed", tol: float = 1e-10, workers: int = 4,
                  budget_bytes: Optional[int] = None, batch_for: Optional[Callable[[Key], int]] = None,
-                 restart: int = 60, keep_results: bool = False, check_exact: bool = False):
+                 restart: int = 60, keep_results: bool = False, check_exact: bool = False,
+                 data_at_arrival: bool = True, priority_dof: int = 1 << 21):
         import torch
 
         from . import ahoc
@@ -251,6 +252,15 @@ class Server:
         self.restart = restart
         self.keep = keep_results
         self.check_exact = check_exact
+        # a request arrives with its data (as a client's upload would): the
+        # feeder synthesises alpha and f on its own stream before the request
+        # enters the queue, and the worker copies them into its plan slot
+        self.data_at_arrival = data_at_arrival
+        self.pending: Dict[int, tuple] = {}
+        # plans of shapes with at most this many interior points run on
+        # high-priority streams, so that small requests are not held up behind
+        # the kernels of large ones (the plan's graph stream inherits it)
+        self.priority_dof = priority_dof
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.6 * free)
@@ -273,7 +283,8 @@ class Server:
         def __init__(self, srv: "Server", key: Key, B: int):
             torch = srv.torch
             dim, N = key
-            self.stream = torch.cuda.Stream(device=srv.device)
+            small = (N - 1) ** dim <= srv.priority_dof
+            self.stream = torch.cuda.Stream(device=srv.device, priority=-1 if small else 0)
             nf = (N + 1) ** dim
             self.nf = nf
             with torch.cuda.stream(self.stream):
@@ -297,14 +308,21 @@ class Server:
         B = w.slot.batch
         nf = sl.nf
         with torch.cuda.stream(sl.stream):
-            # the request's data: synthesised here from its closed form (a client
-            # would send alpha and f); timed apart from the solve
+            # the request's data into the plan slot: copied from what arrived
+            # with it, or synthesised here from its closed form
             for i, spec in enumerate(w.reqs):
-                inputs.sample_request(spec, device=self.device, out_alpha=sl.alpha[i * nf:(i + 1) * nf],
-                                      out_f=sl.f[i * nf:(i + 1) * nf])
-                if self.data_hook is not None:
-                    self.data_hook(spec, sl.alpha[i * nf:(i + 1) * nf], sl.f[i * nf:(i + 1) * nf])
-                sl.plan.load(i, sl.alpha[i * nf:(i + 1) * nf])
+                a_i, f_i = sl.alpha[i * nf:(i + 1) * nf], sl.f[i * nf:(i + 1) * nf]
+                with self.cv:
+                    arrived = self.pending.pop(spec.rid, None)
+                if arrived is not None:
+                    a_i.copy_(arrived[0])
+                    f_i.copy_(arrived[1])
+                else:
+                    inputs.sample_request(spec, device=self.device, out_alpha=a_i, out_f=f_i)
+                    if self.data_hook is not None:
+                        self.data_hook(spec, a_i, f_i)
+                sl.plan.load(i, a_i)
+                del arrived
             sl.stream.synchronize()
             t_loaded = time.perf_counter()
             sl.plan.set_active([1 if i < len(w.reqs) else 0 for i in range(B)])
@@ -342,8 +360,9 @@ class Server:
                         now = time.perf_counter()
                         w = self.sched.next_work(now - t_start)
                         for spec in self.sched.take_expired():
+                            self.pending.pop(spec.rid, None)
                             r = self.records[spec.rid]
-                            r.status, r.start, r.done = STATUS_EXPIRED, now, now
+                            r.status, r.start, r.loaded, r.done = STATUS_EXPIRED, now, now, now
                         if w is not None:
                             evicted = self.sched.take_evicted()
                             break
@@ -363,8 +382,11 @@ class Server:
 
     def run(self, specs: Sequence, realtime: bool = True) -> List[Record]:
         """Feed the requests at their arrival times (or all at once) and solve them."""
+        from . import inputs
+        torch = self.torch
         self.records = {s.rid: Record(s.rid, s.dim, s.N, s.arrival) for s in specs}
         self._fed = False
+        feed = torch.cuda.Stream(device=self.device) if self.data_at_arrival else None
         t_start = time.perf_counter()
         threads = [threading.Thread(target=self._worker, args=(t_start,), daemon=True)
                    for _ in range(self.workers)]
@@ -375,9 +397,18 @@ class Server:
                 dt = s.arrival - (time.perf_counter() - t_start)
                 if dt > 0:
                     time.sleep(dt)
+            if feed is not None:
+                with torch.cuda.stream(feed):
+                    d = inputs.sample_request(s, device=self.device)
+                    if self.data_hook is not None:
+                        self.data_hook(s, d["alpha"], d["f"])
+                feed.synchronize()
             with self.cv:
+                if feed is not None:
+                    self.pending[s.rid] = (d["alpha"], d["f"])
                 self.sched.arrive(s)
-                self.records[s.rid].arrival = s.arrival if realtime else 0.0
+                # the time the request (with its data) entered the queue
+                self.records[s.rid].arrival = (time.perf_counter() - t_start) if realtime else 0.0
                 self.cv.notify_all()
         with self.cv:
             self._fed = True
@@ -390,6 +421,7 @@ class Server:
             r.start -= t_start
             r.loaded -= t_start
             r.done -= t_start
+        self.pending.clear()
         return [self.records[s.rid] for s in specs]
 
     def cancel(self, rid: int) -> bool:
@@ -398,6 +430,7 @@ class Server:
         with self.cv:
             if not self.sched.cancel(rid):
                 return False
+            self.pending.pop(rid, None)
             r = self.records[rid]
             now = time.perf_counter()
             r.status, r.start, r.loaded, r.done = STATUS_CANCELLED, now, now, now

@@ -36,7 +36,7 @@ def test_tuning_table_through_abi():
     assert L.ahoc_tune_set(k, dim, N, prec, 8) == ahoc.AHOC_OK
     assert L.ahoc_tune_get(k, dim, N, prec) == 8
     assert L.ahoc_tune_set(k, dim, N, prec, 12) == ahoc.AHOC_EINVAL  # not offered
-    assert L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, prec, 1024) == ahoc.AHOC_EINVAL
+    assert L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, prec, 2048) == ahoc.AHOC_EINVAL
     assert L.ahoc_tune_set(k, 4, N, prec, 8) == ahoc.AHOC_EINVAL
     assert L.ahoc_tune_get(k, dim, 500, prec) == -1
     # the chunk length sets the tridiagonal scratch, so the workspace follows the table
