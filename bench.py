@@ -300,12 +300,13 @@ def serving_variant(args, dev):
     rate = 0.8 * min(cap.values())
     specs = inputs.request_stream(args.serve_requests, rate, seed=5)
 
-    def warm_specs(batch_for, size, rid0):
-        # `size` requests of every shape at once (at most the shape's batch):
-        # the pool then holds a plan of that size per shape
+    def warm_specs(batch_for, size, copies, rid0):
+        # `copies` batches of `size` requests of every shape at once (at most
+        # the shape's batch): with as many workers, the pool then holds that
+        # many plans of that size per shape
         out, rid = [], rid0
         for (dim, n) in mix:
-            for _ in range(min(size, batch_for((dim, n)))):
+            for _ in range(copies * min(size, batch_for((dim, n)))):
                 out.append(inputs.RequestSpec(rid, dim, n, (0,) * dim, 0.0))
                 rid += 1
         return out
@@ -314,10 +315,14 @@ def serving_variant(args, dev):
         srv = serving.Server(device=dev, prec=prec, tol=tol, workers=workers, batch_for=batch_for,
                              check_exact=True)
         srv.sched.max_slots = args.serve_slots
+        # plans of every power-of-two batch size, one per worker, resident before
+        # the stream starts: no plan is created inside a request's latency
         size = 1
-        while size <= max(batch_for(k) for k in mix):  # plans of every power-of-two size resident
-            srv.run(warm_specs(batch_for, size, 10 ** 7 + 1000 * size), realtime=False)
+        while size <= max(batch_for(k) for k in mix):
+            srv.sched.batch_for = lambda k, s=size: min(s, batch_for(k))  # batches of exactly this size
+            srv.run(warm_specs(batch_for, size, workers, 10 ** 7 + 10000 * size), realtime=False)
             size *= 2
+        srv.sched.batch_for = batch_for
         recs = srv.run(specs, realtime=True)
         srv.close()
         torch.cuda.empty_cache()
@@ -680,7 +685,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-tol", type=float, default=1e-12)
-    ap.add_argument("--serve-slots", type=int, default=8, help="plans per shape in the serving pool")
+    ap.add_argument("--serve-slots", type=int, default=24, help="plans per shape in the serving pool")
     ap.add_argument("--suite", choices=["bench", "paper", "serving"], default="bench",
                     help="paper: the paper's printed workloads at their largest sizes, one JSON line each; "
                          "serving: the serving workload alone")

@@ -58,6 +58,14 @@ __device__ __forceinline__ float negif(float x, bool f) {
   return __int_as_float(__float_as_int(x) ^ ((int)f << 31));
 }
 
+// Barrier of the threads of one line (see dst_lines): bar > 0 a named
+// barrier of TPL threads, bar == 0 the CTA, bar < 0 the warp.
+__device__ __forceinline__ void line_sync(int bar, int TPL) {
+  if (bar > 0) asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TPL) : "memory");
+  else if (bar == 0) __syncthreads();
+  else __syncwarp();
+}
+
 // In-place DST-I of the LPC lines of this CTA.  Line l occupies s[l*LS .. l*LS+N)
 // with s[l*LS] == 0.  Every thread of the CTA must call this.  wsum: >= 32
 // elements of scratch for the cross-warp scan.
@@ -68,6 +76,10 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
   const int tid = threadIdx.x;
   const int l = tid / TPL;
   const int lt = tid - l * TPL;
+  // the threads of one line synchronise among themselves: a named barrier per
+  // line (ids 1..15) when a line spans several warps, the warp itself when it
+  // fits in one, the whole CTA only when it holds more than 15 multi-warp lines
+  const int bar = (TPL <= 32) ? -1 : ((int)blockDim.x / TPL <= 15 ? l + 1 : 0);
   T* y = s + (int64_t)l * LS;
   C* c = reinterpret_cast<C*>(y);
   const int M = N >> 1;
@@ -82,7 +94,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
     y[j] = fmaT(f.x, a, f.y * b);
     if (j != (N >> 1)) y[N - j] = fmaT(f.y, a, f.x * b);
   }
-  __syncthreads();
+  line_sync(bar, TPL);
 
   // 2. complex FFT of length M (Stockham, natural order in and out)
   int Ns = 1;
@@ -94,7 +106,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       x[2 * q] = c[j];
       x[2 * q + 1] = c[j + (M >> 1)];
     }
-    __syncthreads();
+    line_sync(bar, TPL);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       int j = lt + q * TPL;
@@ -105,7 +117,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       c[2 * j] = u;
       c[2 * j + 1] = v;
     }
-    __syncthreads();
+    line_sync(bar, TPL);
     Ns = 2;
   }
   const int M4 = M >> 2;
@@ -124,7 +136,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       const bool s1 = dst_swap_w1(kk, Ns), s2 = dst_swap_w2(kk, Ns);
       const T c1 = f1.x, c1x = negif(f1.x, s1), c2 = f2.x, c2x = negif(f2.x, s2);
       tws += 2 * Ns;
-      __syncthreads();
+      line_sync(bar, TPL);
       C r = lf_rot(x2, f2.y, s2);
       C a0, a1, b0, b1;
       a0.x = fmaT(c2x, r.x, x0.x); a0.y = fmaT(c2, r.y, x0.y);
@@ -140,7 +152,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       y1.x = fmaT(c1, r.y, a1.x); y1.y = fmaT(-c1x, r.x, a1.y);
       y3.x = fmaT(-c1, r.y, a1.x); y3.y = fmaT(c1x, r.x, a1.y);
     } else {
-      __syncthreads();
+      line_sync(bar, TPL);
       C a0, a1, b0, b1;
       a0.x = x0.x + x2.x; a0.y = x0.y + x2.y;
       a1.x = x0.x - x2.x; a1.y = x0.y - x2.y;
@@ -157,7 +169,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
     c[o + Ns] = y1;
     c[o + 2 * Ns] = y2;
     c[o + 3 * Ns] = y3;
-    __syncthreads();
+    line_sync(bar, TPL);
   }
 
   // 3. post-processing: F_k and F_{M-k} from C_k, C_{M-k}; even outputs in
@@ -188,7 +200,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       y[2 * (M - k) + 1] = fmaT(-cx, r.x, E.x);
     }
   }
-  __syncthreads();
+  line_sync(bar, TPL);
 
   // 4. inclusive prefix sum over the odd slots: each thread owns 4 consecutive values
   T v0 = y[8 * lt + 1], v1 = y[8 * lt + 3], v2 = y[8 * lt + 5], v3 = y[8 * lt + 7];
@@ -212,7 +224,7 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
     const int warp = tid >> 5;
     const int wpl = TPL >> 5;  // warps per line (<= 32)
     if (lane == 31) wsum[warp] = x;
-    __syncthreads();
+    line_sync(bar, TPL);
     const int wl = warp - l * wpl;  // warp index within the line
     if (wl == 0) {
       T t = (lane < wpl) ? wsum[warp + lane] : (T)0;
@@ -225,14 +237,14 @@ __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename
       if (lane == 0) te = (T)0;
       if (lane < wpl) wsum[warp + lane] = te;
     }
-    __syncthreads();
+    line_sync(bar, TPL);
     ex += wsum[warp];
   }
   y[8 * lt + 1] = v0 + ex;
   y[8 * lt + 3] = v1 + ex;
   y[8 * lt + 5] = v2 + ex;
   y[8 * lt + 7] = v3 + ex;
-  __syncthreads();
+  __syncthreads();  // the callers' stores map threads across lines
 }
 
 // ---------------------------------------------------------------------------
@@ -520,7 +532,7 @@ static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const v
   const int N = (int)g.n0;
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  const int cta = g.dst_cta ? g.dst_cta : 512;
+  const int cta = g.dst_cta ? g.dst_cta : (g.dim == 3 ? 256 : 512);  // measured: 256 is faster in 3D
   const int LPC = TPL >= cta ? 1 : cta / TPL;
   const int threads = TPL * LPC;
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
@@ -599,7 +611,7 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
   const int N = g.N[1];
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  const int cta = g.dst_cta ? g.dst_cta : 512;
+  const int cta = g.dst_cta ? g.dst_cta : (g.dim == 3 ? 256 : 512);  // measured: 256 is faster in 3D
   int LPC = TPL >= cta ? 1 : cta / TPL;
   if (LPC > g.n0) LPC = (int)g.n0;
   const int threads = TPL * LPC;

@@ -197,6 +197,8 @@ cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, 
 // per block b: out[3b] = min, out[3b+1] = max, out[3b+2] = sum of beta/alpha over n points
 cudaError_t launch_ratio_stats(const double* beta, const double* alpha, int64_t n, double* out, int blocks,
                                cudaStream_t st);
+// out = a / in (in == NULL: out = a)
+cudaError_t launch_scaled_recip(double* out, const double* in, double a, int64_t n, cudaStream_t st);
 // out = 1 / in (in == NULL: out = 1)
 cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st);
 cudaError_t launch_v_full(const Geom& g, double* vfull, const double* Vpad, const double* Q, const double* vedge,

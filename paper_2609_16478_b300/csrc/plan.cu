@@ -97,7 +97,6 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
   if (d.tri) {
     if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "the triharmonic class runs in FP64 only");
     if (d.varb || d.shift != 0.0) return fail(AHOC_EINVAL, "the triharmonic class takes no beta");
-    d.precond = 0;  // the boundary-symbol preconditioner is the biharmonic's
     d.levels = 0;
     d.uhat = -1;
   }
@@ -1635,7 +1634,7 @@ ahoc_status plan_alloc(ahoc_plan** out, int dim, const int64_t* N, const double*
     CKC(launch_to_float(p->skyf, p->stab[1], 2 * (int64_t)g.N[1], p->st));
     CKC(launch_to_float(p->tauyf, p->tauy, g.N[1] + 1, p->st));
   }
-  if (o.precond) {
+  if (o.precond && !o.tri) {  // the triharmonic class measures its symbols (tri_symbols)
     const double* stp[3] = {p->stab[0], p->stab[1], g.dim == 3 ? p->stab[2] : nullptr};
     const double* ctp[3] = {p->ctab[0], p->ctab[1], g.dim == 3 ? p->ctab[2] : nullptr};
     CKC(launch_face_symbols(g, cf, p->pre, stp, ctp, p->st));
@@ -1732,6 +1731,43 @@ ahoc_status plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata
 }
 #undef CKC
 
+// Preconditioner of the triharmonic class.  With one clamped face and the
+// others simply supported, the Schur operator of that face is diagonal in the
+// face's sine basis (every Poisson solve of the mixed form then separates in
+// the transverse sine modes, as in Lemma 4), so one Schur action gives every
+// mode's symbol s: with T the face's DST-I (T^2 = c I, c the product of N_b/2
+// over the in-face axes) and Phi = T / sqrt(c), S Phi 1 = Phi s.  The
+// preconditioner (out = T(pre T(in))) then has pre = 1 / (c s) on a clamped
+// face, the exact inverse in that setting and the per-face inverse symbol
+// otherwise, and pre = -1 / c on a simply supported face (its rows are -I).
+// Measured on problem 0 (the symbol depends on the shape alone).
+ahoc_status tri_symbols(ahoc_plan* p) {
+  const Geom& g = p->g;
+  std::vector<int> m0(g.nb, 0);
+  m0[0] = 1;
+  CKS(set_act(p, m0));
+  for (int f = 0; f < 2 * g.dim; ++f) {
+    const int a = f >> 1;
+    double c = 1.0;
+    for (int b = 0; b < g.dim; ++b)
+      if (b != a) c *= g.N[b] / 2.0;
+    const int64_t off = g.face_off[f], len = g.face_off[f + 1] - g.face_off[f];
+    if (g.is_navier(f)) {
+      CK(launch_scaled_recip(p->pre + off, nullptr, -1.0 / c, len, p->st));
+      continue;
+    }
+    CK(cudaMemsetAsync(p->tmp, 0, (size_t)g.ngamma * sizeof(double), p->st));
+    CK(launch_scaled_recip(p->tmp + off, nullptr, 1.0 / std::sqrt(c), len, p->st));
+    CKS(face_dsts(p, p->tmp, a));  // Phi 1 on face f, zero elsewhere
+    CKS(matvec_dev(p, p->tmp, p->r));
+    CKS(face_dsts(p, p->r, a));    // T S Phi 1 = sqrt(c) s on face f
+    CK(launch_scaled_recip(p->pre + off, p->r + off, 1.0 / std::sqrt(c), len, p->st));
+  }
+  CK(cudaStreamSynchronize(p->st));
+  CKS(set_act(p, p->part));
+  return AHOC_OK;
+}
+
 // opts.auto_shift: the beta class from the data.  gamma = beta / alpha over
 // every point of every problem: one value everywhere -> the constant shift;
 // otherwise variable beta with the mean of gamma as the reference shift of the
@@ -1804,6 +1840,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
     s = plan_load(p, b, alpha ? alpha + (int64_t)b * g.nfull : nullptr, &bb);
   }
   if (s == AHOC_OK && cudaStreamSynchronize(p->st) != cudaSuccess) s = fail(AHOC_ECUDA, "plan setup failed");
+  if (s == AHOC_OK && o.tri && o.precond) s = tri_symbols(p);
   if (s != AHOC_OK) {
     if (p) ahoc_plan_destroy(p);
     return s;

@@ -429,6 +429,14 @@ cudaError_t launch_face_gather(const Geom& g, double* face, const double* full, 
   k_face_gather<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, face, full);
   return cudaGetLastError();
 }
+__global__ void k_fill_scaled_recip(double* __restrict__ out, const double* __restrict__ in, double a, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = in ? a / in[t] : a;
+}
+cudaError_t launch_scaled_recip(double* out, const double* in, double a, int64_t n, cudaStream_t st) {
+  k_fill_scaled_recip<<<nblk(n, 256), 256, 0, st>>>(out, in, a, n);
+  return cudaGetLastError();
+}
 cudaError_t launch_recip(double* out, const double* in, int64_t n, cudaStream_t st) {
   k_recip<<<nblk(n, 256), 256, 0, st>>>(out, in, n);
   return cudaGetLastError();
