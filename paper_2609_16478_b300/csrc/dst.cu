@@ -398,209 +398,6 @@ __global__ void __launch_bounds__(1024) k_dst_x(Geom g, T* __restrict__ a, DstIO
 }
 
 // ---------------------------------------------------------------------------
-// x axis in FP32, one warp per line (N = 64 R, R = 4 .. 32): the N/2-point
-// complex FFT of the DST-I (same pre- and post-processing as dst_lines) as a
-// four-step transform M = 32 R with no CTA barrier:
-//   n = 32 n1 + l (lane l), k = k1 + R k2;
-//   C_k = sum_l W32^(l k2) W_M^(l k1) sum_n1 c_(32 n1 + l) W_R^(n1 k1):
-// an R-point FFT in each lane's registers (radix-2 decimation in frequency,
-// bit-reversed output), the twiddles W_M^(l k1), a 32-point FFT across the
-// lanes by xor-shuffles (bit-reversed lanes), then C through warp-private
-// shared memory (padded so that lanes fall on distinct banks) for the
-// post-processing and the prefix sum of the odd outputs (a warp scan).
-// Loads and stores are coalesced rows through the same buffer.
-// ---------------------------------------------------------------------------
-constexpr int kWarpLinesPerCta = 8;
-
-__device__ __forceinline__ int bitrev_n(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
-
-template <int R, int LOAD, int STORE>
-__global__ void __launch_bounds__(32 * kWarpLinesPerCta) k_dstw_x(Geom g, float* __restrict__ a, DstIO<float> io,
-                                                                 const float2* __restrict__ tw, int post_off,
-                                                                 float scale) {
-  constexpr int N = 64 * R, M = 32 * R;
-  constexpr int LOGR = (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : 5;
-  constexpr int BUF = N + 64;
-  const int bi = blockIdx.y;
-  if (g.skip(bi)) return;
-  a += (int64_t)bi * g.npad;
-  if (io.src) io.src += (int64_t)bi * g.npad;
-  if (io.src2) io.src2 += (int64_t)bi * g.npad;
-  if (io.qa) io.qa += (int64_t)bi * g.ngamma;
-  if (io.ainv) io.ainv += (int64_t)bi * g.nfull;
-  extern __shared__ __align__(16) float sdyn[];  // kWarpLinesPerCta buffers of BUF floats
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nj = g.N[1] - 1;
-  const int nrows = nj * (g.kmax - g.kmin);
-  const int r = blockIdx.x * kWarpLinesPerCta + warp;
-  if (r >= nrows) return;  // whole warps: no block-wide barrier follows
-  const int j = 1 + r % nj, k = g.kmin + r / nj;
-  const int64_t rb = g.pad(0, j, k);
-  float* buf = sdyn + warp * BUF;
-
-  // 0. the line into the buffer (x_0 = x_N = 0)
-#pragma unroll 4
-  for (int t = 0; t < N / 32; ++t) {
-    const int pos = lane + 32 * t;
-    float v = 0.f;
-    if (pos > 0) {
-      if (LOAD == 0) {
-        v = io.src[rb + pos];
-        if (io.lscale != 1.f) v *= io.lscale;
-      } else if (LOAD == 1) {
-        v = mstencil2d<float>(g, io, pos, j);
-      } else {
-        v = mstencil3d<float>(g, io, pos, j, k);
-      }
-    }
-    buf[pos] = v;
-  }
-  if (lane == 0) buf[N] = 0.f;
-  __syncwarp();
-
-  // 1. pre-processing into this lane's registers: c_n = (z_2n, z_2n+1), n = 32 n1 + lane,
-  //    z_k = f(jj).x x_k + f(jj).y x_(N-k), jj = min(k, N - k)
-  const float2* pm = tw + N;
-  float2 A[R];
-#pragma unroll
-  for (int n1 = 0; n1 < R; ++n1) {
-    const int n = 32 * n1 + lane;
-    float zz[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int kk = 2 * n + e;
-      const int jj = kk <= N / 2 ? kk : N - kk;
-      const float2 f = pm[jj];
-      zz[e] = (kk == 0) ? 0.f : fmaf(f.x, buf[kk], f.y * buf[N - kk]);
-    }
-    A[n1] = make_float2(zz[0], zz[1]);
-  }
-  __syncwarp();
-
-  // 2. R-point FFT over n1 in registers (decimation in frequency; A[i] = X[bitrev(i)])
-#pragma unroll
-  for (int h = R / 2; h >= 1; h >>= 1) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      if (i & h) continue;
-      const float2 x0 = A[i], x1 = A[i + h];
-      const float2 w = tw[(i & (h - 1)) * (N / (2 * h))];  // W_(2h)^(i mod h)
-      const float dx = x0.x - x1.x, dy = x0.y - x1.y;
-      A[i] = make_float2(x0.x + x1.x, x0.y + x1.y);
-      A[i + h] = make_float2(fmaf(dx, w.x, -dy * w.y), fmaf(dx, w.y, dy * w.x));
-    }
-  }
-  // 3. twiddles W_M^(lane k1), k1 = bitrev(i)
-#pragma unroll
-  for (int i = 1; i < R; ++i) {
-    const int k1 = bitrev_n(i, LOGR);
-    const float2 w = tw[(2 * lane * k1) & (N - 1)];
-    const float2 x = A[i];
-    A[i] = make_float2(fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x));
-  }
-  // 4. 32-point FFT across the lanes (decimation in frequency; lane l ends with k2 = bitrev5(l))
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool upper = (lane & h) != 0;
-    const float2 w = tw[(lane & (h - 1)) * (N / (2 * h))];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const float px = __shfl_xor_sync(0xffffffffu, A[i].x, h);
-      const float py = __shfl_xor_sync(0xffffffffu, A[i].y, h);
-      if (!upper) {
-        A[i] = make_float2(A[i].x + px, A[i].y + py);
-      } else {
-        const float dx = px - A[i].x, dy = py - A[i].y;
-        A[i] = make_float2(fmaf(dx, w.x, -dy * w.y), fmaf(dx, w.y, dy * w.x));
-      }
-    }
-  }
-  // 5. C_(k1 + R k2) to the buffer at 2 k1 + (2 R + 1) k2 (lanes on distinct banks)
-  const int k2 = bitrev_n(lane, 5);
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int k1 = bitrev_n(i, LOGR);
-    const int ad = 2 * k1 + (2 * R + 1) * k2;
-    buf[ad] = A[i].x;
-    buf[ad + 1] = A[i].y;
-  }
-  __syncwarp();
-  auto cload = [&](int kk) {
-    const int ad = 2 * (kk % R) + (2 * R + 1) * (kk / R);
-    return make_float2(buf[ad], buf[ad + 1]);
-  };
-
-  // 6. post-processing of this lane's R consecutive k: X_2k and the odd-slot inputs
-  const float2* pp = tw + post_off;
-  float out[2 * R];
-#pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const int kk = lane * R + t;
-    float ev, od;
-    if (kk == 0) {
-      const float2 c0 = cload(0);
-      ev = 0.f;
-      od = c0.x + c0.y;
-    } else if (kk == M / 2) {
-      const float2 c0 = cload(kk);
-      ev = 2.f * c0.y;
-      od = 2.f * c0.x;
-    } else {
-      const bool lo = kk < M / 2;
-      const int k0 = lo ? kk : M - kk;
-      const float2 Ak = cload(k0), Bk = cload(M - k0);
-      float2 E, D, O;
-      E.x = Ak.x + Bk.x;
-      E.y = Ak.y - Bk.y;
-      D.x = Ak.x - Bk.x;
-      D.y = Ak.y + Bk.y;
-      O.x = D.y;
-      O.y = -D.x;
-      const float2 f = pp[k0];
-      const bool sw = dst_swap_post(k0, N);
-      const float2 rr = lf_rot(O, f.y, sw);
-      const float cx = negif(f.x, sw);
-      ev = lo ? fmaf(-f.x, rr.y, -E.y) : fmaf(-f.x, rr.y, E.y);
-      od = lo ? fmaf(cx, rr.x, E.x) : fmaf(-cx, rr.x, E.x);
-    }
-    out[2 * t] = ev;
-    out[2 * t + 1] = od;
-  }
-  // inclusive prefix sum of the odd slots over all k: this lane's run, then a warp scan
-#pragma unroll
-  for (int t = 1; t < R; ++t) out[2 * t + 1] += out[2 * t - 1];
-  float tot = out[2 * R - 1];
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float nb = __shfl_up_sync(0xffffffffu, tot, o);
-    if (lane >= o) tot += nb;
-  }
-  float ex = __shfl_up_sync(0xffffffffu, tot, 1);
-  if (lane == 0) ex = 0.f;
-#pragma unroll
-  for (int t = 0; t < R; ++t) out[2 * t + 1] += ex;
-  __syncwarp();
-  // 7. through the buffer (pos + pos / 32: distinct banks) to coalesced row stores
-#pragma unroll
-  for (int u = 0; u < 2 * R; ++u) {
-    const int pos = 2 * R * lane + u;
-    buf[pos + (pos >> 5)] = out[u];
-  }
-  __syncwarp();
-#pragma unroll 4
-  for (int t = 0; t < N / 32; ++t) {
-    const int pos = lane + 32 * t;
-    float v = buf[pos + (pos >> 5)];
-    if (STORE == 0) {
-      if (scale != 1.f) v *= scale;
-    } else {
-      v *= io.ainv[g.full(0, j, k) + pos];
-    }
-    a[rb + pos] = (pos == 0) ? 0.f : v;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // y axis (3D only): a CTA takes LPC adjacent x-columns of one z-plane; the
 // columns are staged through shared memory so global accesses stay row-wise.
 // ---------------------------------------------------------------------------
@@ -723,50 +520,26 @@ __global__ void __launch_bounds__(512) k_precond_lines(double* out, const double
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// CTA size of the line DSTs when the tuner has not set one (measured on
+// B300 with per-line barriers: 256 threads for the FP64 3D transforms, which
+// are bound by the FP64 pipe, 512 otherwise)
+template <typename T>
+static inline int default_cta(const Geom& g) {
+  return (sizeof(T) == 8 && g.dim == 3) ? 256 : 512;
+}
 static inline int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
   return l;
 }
 
-// the warp-per-line FP32 form for N = 256 .. 2048 (k_dstw_x)
-template <int LOAD, int STORE>
-static cudaError_t dstw_x(const Geom& g, float* dst, const DstIO<float>& io, const void* tw, float scale,
-                          cudaStream_t st) {
-  const int N = (int)g.n0;
-  const int post_off = (int)(dst_tw_len(N) - (N / 4 + 1));
-  const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
-  const dim3 grid((unsigned)((nrows + kWarpLinesPerCta - 1) / kWarpLinesPerCta), (unsigned)g.nb);
-  const float2* t2 = reinterpret_cast<const float2*>(tw);
-  const int th = 32 * kWarpLinesPerCta;
-  const size_t smem = (size_t)kWarpLinesPerCta * (N + 64) * sizeof(float);
-  auto go = [&](auto kern) -> cudaError_t {
-    if (smem > 48 * 1024) {
-      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    kern<<<grid, th, smem, st>>>(g, dst, io, t2, post_off, scale);
-    return cudaGetLastError();
-  };
-  if (N == 256) return go(k_dstw_x<4, LOAD, STORE>);
-  if (N == 512) return go(k_dstw_x<8, LOAD, STORE>);
-  if (N == 1024) return go(k_dstw_x<16, LOAD, STORE>);
-  if (N == 2048) return go(k_dstw_x<32, LOAD, STORE>);
-  return cudaErrorInvalidValue;
-}
-template <typename T> bool use_warp_dst(const Geom&) { return false; }
-template <> bool use_warp_dst<float>(const Geom& g) { return g.n0 >= 256 && g.n0 <= 2048 && g.dst_cta == 0; }
-
 template <typename T, int LOAD, int STORE>
 static cudaError_t dst_x_impl(const Geom& g, T* dst, const DstIO<T>& io, const void* tw, const T* sn, T scale,
                               cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
-    if (use_warp_dst<T>(g)) return dstw_x<LOAD, STORE>(g, dst, io, tw, scale, st);
-  }
   const int N = (int)g.n0;
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  const int cta = g.dst_cta ? g.dst_cta : (g.dim == 3 ? 256 : 512);  // measured: 256 is faster in 3D
+  const int cta = g.dst_cta ? g.dst_cta : default_cta<T>(g);
   const int LPC = TPL >= cta ? 1 : cta / TPL;
   const int threads = TPL * LPC;
   const int64_t nrows = (int64_t)(g.N[1] - 1) * (g.kmax - g.kmin);
@@ -845,7 +618,7 @@ cudaError_t launch_dst_y(const Geom& g, T* a, const void* tw, const T* sn, T sca
   const int N = g.N[1];
   const int logN = ilog2(N);
   const int TPL = N / 8;
-  const int cta = g.dst_cta ? g.dst_cta : (g.dim == 3 ? 256 : 512);  // measured: 256 is faster in 3D
+  const int cta = g.dst_cta ? g.dst_cta : default_cta<T>(g);
   int LPC = TPL >= cta ? 1 : cta / TPL;
   if (LPC > g.n0) LPC = (int)g.n0;
   const int threads = TPL * LPC;

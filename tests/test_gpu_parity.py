@@ -405,3 +405,20 @@ def test_fused3d_matvec_on_many_modes():
     y12 = pf.matvec(q1 + 2 * q2)
     lin = pf.matvec(q1) + 2 * pf.matvec(q2)
     assert float(torch.linalg.norm(y12 - lin) / torch.linalg.norm(lin)) < 1e-13
+
+
+@pytest.mark.parametrize("N", [(512, 512), (2048, 64), (256, 256, 8), (256, 2048, 8), (1024, 512, 8)])
+def test_mixed_matvec_matches_fp64_on_long_lines(N):
+    """The FP32 Schur action (line DSTs of 256 .. 2048 points in the
+    warp-per-line form, along x and, in 3D, y) against the FP64 action
+    (the oracle's Schur columns on small grids, the plain form beyond):
+    FP32-accurate."""
+    dim = len(N)
+    hi = [n / max(N) for n in N]   # equal spacing on every axis
+    prob = inputs.config_problem("fourier3d" if dim == 3 else "fourier2d")
+    d = inputs.sample(prob, list(N), lo=[0.0] * dim, hi=hi)
+    p64, p32 = _plan(d), _plan(d, prec="mixed")
+    g = torch.Generator("cuda").manual_seed(6)
+    q = torch.randn(p64.ngamma, dtype=torch.float64, device="cuda", generator=g)
+    y64, y32 = p64.matvec(q), p32.matvec(q)
+    assert float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64)) < 1e-5
