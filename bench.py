@@ -335,7 +335,7 @@ def serving_variant(args, dev):
     ra, sa = arm("mixed", args.serve_workers, bfor)
     for k in cache:  # the FP64 arms run with the built-in shapes
         dim, n, _ = k.split(":")
-        for kind in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS):
+        for kind in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS, ahoc.AHOC_TUNE_DST_RADIX):
             ahoc.lib().ahoc_tune_set(kind, int(dim), int(n), ahoc.AHOC_MIXED, 0)
     rb, sb = arm("fp64", args.serve_workers, bfor)
     rc, sc = arm("fp64", 1, lambda k: 1)
@@ -690,7 +690,22 @@ def main():
                     help="paper: the paper's printed workloads at their largest sizes, one JSON line each; "
                          "serving: the serving workload alone")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache (default: the shipped B300 choices)")
+    ap.add_argument("--dst-radix", type=int, default=0, choices=[0, 4, 8],
+                    help="FFT radix of the line DSTs for every shape and precision (0: built-in)")
+    ap.add_argument("--dst-cta", type=int, default=0, choices=[0, 128, 256, 512, 1024],
+                    help="CTA size of the line DSTs for every shape and precision (0: built-in)")
     args = ap.parse_args()
+    if args.dst_radix or args.dst_cta:
+        from paper_2609_16478_b300 import ahoc
+        for dim in (2, 3):
+            for lg in range(3, 13):
+                for prec in (ahoc.AHOC_FP64, ahoc.AHOC_MIXED):
+                    if args.dst_radix:
+                        ahoc._check(ahoc.lib().ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, 1 << lg, prec,
+                                                             args.dst_radix), "ahoc_tune_set")
+                    if args.dst_cta:
+                        ahoc._check(ahoc.lib().ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, 1 << lg, prec,
+                                                             args.dst_cta), "ahoc_tune_set")
     if args.tune_cache is None:
         from paper_2609_16478_b300 import autotune
         args.tune_cache = autotune.SHIPPED_MIXED

@@ -122,12 +122,17 @@ typedef struct {
                              solution's Q interpolated (cubic, along the faces) to the next
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
-                             every axis keeps >= 128 intervals, at most 3 levels); 0: off */
+                             every axis keeps >= 128 intervals, at most 3 levels; off in an
+                             AHOC_MIXED plan, where it only starts the first correction
+                             solve); 0: off.  In an AHOC_MIXED plan the coarse levels are
+                             mixed-precision solves too                                      */
   double coarse_tol;      /* [0] relative Schur residual the coarse levels of the nested guess
                              solve to (never tighter than the solve's tol).  The prolonged
                              guess is only as good as the coarse grid's discretisation and
                              the interpolation, so a coarse solve past that is wasted.
-                             <= 0: automatic (AHOC_COARSE_TOL_AUTO)                         */
+                             <= 0: automatic (AHOC_COARSE_TOL_AUTO, or
+                             AHOC_COARSE_TOL_AUTO_MIXED in an AHOC_MIXED plan, whose first
+                             FP32 correction only needs the guess to refine_tol)             */
   int batch;              /* [1] problems of this shape held by the plan and solved together:
                              every launch covers all of them (one grid dimension per problem),
                              GMRES runs in lockstep and a problem that has converged is masked
@@ -203,8 +208,10 @@ typedef struct {
                              ahoc_workspace_bytes sizes for the variable-beta class.          */
 } ahoc_opts;
 
-/* automatic coarse-level tolerance of the nested initial guess */
+/* automatic coarse-level tolerance of the nested initial guess (FP64 and
+   mixed-precision plans) */
 #define AHOC_COARSE_TOL_AUTO 3e-11
+#define AHOC_COARSE_TOL_AUTO_MIXED 1e-8
 
 typedef struct {
   int iters;              /* GMRES iterations (matrix-vector products) of the last solve        */
@@ -359,10 +366,13 @@ int ahoc_batch(const ahoc_plan* p);
  *                          along the last axis: 8, 16 or 32 (key N: that axis)
  *   AHOC_TUNE_DST_THREADS  threads per CTA of the line DSTs along x and y:
  *                          128, 256, 512 or 1024 (key N: the x axis)
+ *   AHOC_TUNE_DST_RADIX    radix of the FFT stages of the line DSTs along x
+ *                          and y: 4 (one radix-2 stage first when log2(N/2) is
+ *                          odd) or 8 (one radix-2 or radix-4 stage first when
+ *                          log2(N/2) is not a multiple of 3) (key N: the x axis)
  * value 0 restores the built-in choice.  The shapes change rounding, not the
- * discrete problem: results stay within the solver's tolerance.  The FFT
- * radix is fixed (radix 4, one radix-2 stage when log2(N/2) is odd). */
-enum { AHOC_TUNE_TRI_CHUNK = 0, AHOC_TUNE_DST_THREADS = 1, AHOC_TUNE_NKINDS = 2 };
+ * discrete problem: results stay within the solver's tolerance. */
+enum { AHOC_TUNE_TRI_CHUNK = 0, AHOC_TUNE_DST_THREADS = 1, AHOC_TUNE_DST_RADIX = 2, AHOC_TUNE_NKINDS = 3 };
 ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value);
 /* the table entry (0: built-in), or -1 for arguments out of range */
 int ahoc_tune_get(int kind, int dim, int64_t N, int prec);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libahoc.so")
 AHOC_OK, AHOC_EINVAL, AHOC_ENOMEM, AHOC_ECUDA, AHOC_ENOCONV, AHOC_ENUMERIC, AHOC_ETIMEOUT, \
     AHOC_EUNSUPPORTED, AHOC_EINTERNAL = range(9)
 AHOC_FP64, AHOC_MIXED = 0, 1
-AHOC_TUNE_TRI_CHUNK, AHOC_TUNE_DST_THREADS = 0, 1
+AHOC_TUNE_TRI_CHUNK, AHOC_TUNE_DST_THREADS, AHOC_TUNE_DST_RADIX = 0, 1, 2
 
 # every entry point declared in include/ahoc.h
 SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_matvec", "ahoc_schur_rhs",

@@ -8,6 +8,9 @@ solves of a seeded request of that shape (``inputs.sample_request``):
   * the CTA size of the line DSTs (``AHOC_TUNE_DST_THREADS``: 128, 256, 512,
     1024 threads: the lines a CTA holds, hence the width of the row segments
     the y-transform reads and writes);
+  * the FFT radix of the line DSTs (``AHOC_TUNE_DST_RADIX``: radix-4 or
+    radix-8 stages: fewer passes over shared memory against more registers
+    and half the threads busy in a radix-8 stage);
   * the batch size B of the serving plans: the per-problem time of a batched
     solve for B = 1, 2, 4, ... up to a memory cap; among the batches that
     finish within ``latency_factor`` times a single solve, the smallest B
@@ -29,6 +32,7 @@ from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
 TRI_CHOICES = (8, 16, 32)
 CTA_CHOICES = (128, 256, 512, 1024)
+RADIX_CHOICES = (4, 8)
 
 # choices measured on a B300 for the serving shapes, mixed precision
 # (``tune([(2, 128), ..., (3, 256)], "mixed", path=...)``); re-run to refresh
@@ -83,6 +87,9 @@ def apply(cache: Dict[str, dict]) -> None:
         if "dst_threads" in v:
             ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, int(dim), int(N), p, int(v["dst_threads"])),
                         "ahoc_tune_set")
+        if "dst_radix" in v:
+            ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, int(dim), int(N), p, int(v["dst_radix"])),
+                        "ahoc_tune_set")
 
 
 def batch_for(cache: Dict[str, dict], prec: str, default: Callable[[Tuple[int, int]], int]):
@@ -119,15 +126,16 @@ def _time_solves(dim, N, prec, B, reps=3, restart=60):
 
 def tune_shape(dim: int, N: int, prec: str, batches: Sequence[int] = (1, 2, 4, 8, 16),
                mem_cap: float = 0.25, slack: float = 0.05, reps: int = 3, latency_factor: float = 2.0) -> dict:
-    """Measure the three choices for one shape; the tuning table is left set."""
+    """Measure the four choices for one shape; the tuning table is left set."""
     import torch
 
     from . import ahoc
     L = ahoc.lib()
     p = ahoc._prec(prec)
     out: dict = {}
-    # chunk length, with the built-in CTA
+    # chunk length, with the built-in CTA and radix
     L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, p, 0)
+    L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, p, 0)
     tri = {}
     for c in TRI_CHOICES:
         ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_TRI_CHUNK, dim, N, p, c), "ahoc_tune_set")
@@ -141,6 +149,13 @@ def tune_shape(dim: int, N: int, prec: str, batches: Sequence[int] = (1, 2, 4, 8
         cta[c] = _time_solves(dim, N, prec, 1, reps)
     out["dst_threads"] = pick_fastest(cta)
     ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, p, out["dst_threads"]), "ahoc_tune_set")
+    # FFT radix, with the chosen CTA
+    rad = {}
+    for r in RADIX_CHOICES:
+        ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, p, r), "ahoc_tune_set")
+        rad[r] = _time_solves(dim, N, prec, 1, reps)
+    out["dst_radix"] = pick_fastest(rad)
+    ahoc._check(L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, p, out["dst_radix"]), "ahoc_tune_set")
     # batch size under a device-memory cap
     free, _ = torch.cuda.mem_get_info()
     per = {}
@@ -150,7 +165,7 @@ def tune_shape(dim: int, N: int, prec: str, batches: Sequence[int] = (1, 2, 4, 8
             break
         per[B] = _time_solves(dim, N, prec, B, reps) / B
     out["batch"] = pick_batch(per, slack, latency_factor)
-    out["ms"] = {"tri_chunk": tri, "dst_threads": cta, "per_problem_by_batch": per}
+    out["ms"] = {"tri_chunk": tri, "dst_threads": cta, "dst_radix": rad, "per_problem_by_batch": per}
     return out
 
 

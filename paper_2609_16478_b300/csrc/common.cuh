@@ -37,6 +37,7 @@ struct Geom {
   int navier;  // bit 2a + side: Navier face (v = alpha g_L is data); other faces clamped
   int triL;     // rows per chunk of the chunked tridiagonal solve (0: default)
   int dst_cta;  // threads per CTA of the line DSTs along x and y (0: default 512)
+  int dst_radix;  // FFT radix of the line DSTs along x and y: 4 or 8 (0: default)
 
   __host__ __device__ inline bool is_navier(int face_id) const { return (navier >> face_id) & 1; }
 
@@ -94,7 +95,8 @@ __host__ __device__ inline bool dst_swap_w1(int kk, int Ns) { return 2 * kk > Ns
 __host__ __device__ inline bool dst_swap_w2(int kk, int Ns) { return 4 * kk > Ns && 4 * kk < 3 * Ns; }
 __host__ __device__ inline bool dst_swap_post(int k, int N) { return 8 * k > N; }
 
-__host__ __device__ inline int64_t dst_tw_len(int N) {
+// Entries up to the end of the post-processing factors (the radix-4 layout).
+__host__ __device__ inline int64_t dst_tw_len_r4(int N) {
   const int M = N >> 1;
   int logM = 0;
   while ((1 << logM) < M) ++logM;
@@ -102,6 +104,25 @@ __host__ __device__ inline int64_t dst_tw_len(int N) {
   for (int Ns = (logM & 1) ? 2 : 1; Ns < M; Ns <<= 2)
     if (Ns > 1) len += 2 * (int64_t)Ns;
   return len + M / 2 + 1;
+}
+// Radix-8 plan of the M-point FFT (M = N/2): a stage without twiddles first
+// when log2 M is not a multiple of 3 (radix 2 for 1 mod 3, radix 4 with
+// Ns = 1 for 2 mod 3), then radix-8 stages from this Ns on.
+__host__ __device__ inline int dst_r8_first_ns(int logM) {
+  const int r = logM % 3;
+  return r == 0 ? 1 : (r == 1 ? 2 : 4);
+}
+// After the radix-4 layout, per radix-8 stage Ns entries (c, t) of each of
+// w = W^kk (W = exp(-2 pi i/(8 Ns))), w^2, w^4 and w e^{-i pi/4}, contiguous
+// in kk.  Swap rules: none for w, dst_swap_w1 for w^2, dst_swap_w2 for w^4,
+// kk > 0 for w e^{-i pi/4}.
+__host__ __device__ inline int64_t dst_tw_len(int N) {
+  const int M = N >> 1;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  int64_t len = dst_tw_len_r4(N);
+  for (int Ns = dst_r8_first_ns(logM); Ns < M; Ns <<= 3) len += 4 * (int64_t)Ns;
+  return len;
 }
 
 }  // namespace ahoc

@@ -79,6 +79,17 @@ __global__ void k_na_dst_stages(double* tw, int N) {
   }
   for (int k = threadIdx.x; k <= M / 2; k += blockDim.x)
     na_factor(-2.0 * k / N, dst_swap_post(k, N), tw + 2 * (off + k));
+  off += M / 2 + 1;
+  for (int Ns = dst_r8_first_ns(logM); Ns < M; Ns <<= 3) {  // radix-8 stages
+    for (int kk = threadIdx.x; kk < Ns; kk += blockDim.x) {
+      const double x = -(double)kk / (4.0 * Ns);
+      na_factor(x, false, tw + 2 * (off + kk));
+      na_factor(2 * x, dst_swap_w1(kk, Ns), tw + 2 * (off + Ns + kk));
+      na_factor(4 * x, dst_swap_w2(kk, Ns), tw + 2 * (off + 2 * Ns + kk));
+      na_factor(x - 0.25, kk > 0, tw + 2 * (off + 3 * Ns + kk));
+    }
+    off += 4 * (int64_t)Ns;
+  }
 }
 
 // sum of a few doubles with Neumaier compensation (the stencil-weight residue)

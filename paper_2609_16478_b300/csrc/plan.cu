@@ -81,6 +81,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.levels = o->levels;
     if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
     if (o->coarse_tol > 0) d.coarse_tol = o->coarse_tol;
+    else if (o->prec == AHOC_MIXED) d.coarse_tol = AHOC_COARSE_TOL_AUTO_MIXED;
     if (o->batch > 0) d.batch = o->batch;
     d.graphs = o->no_graphs ? 0 : 1;
     d.navier = o->navier;
@@ -93,13 +94,17 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.workspace_bytes = o->workspace_bytes;
   }
   if (d.prec != AHOC_FP64 && d.prec != AHOC_MIXED) return fail(AHOC_EUNSUPPORTED, "prec must be AHOC_FP64 or AHOC_MIXED");
-  if (d.prec == AHOC_MIXED) d.levels = 0;  // the nested initial guess belongs to the FP64 path
   if (d.tri) {
     if (d.prec != AHOC_FP64) return fail(AHOC_EUNSUPPORTED, "the triharmonic class runs in FP64 only");
     if (d.varb || d.shift != 0.0) return fail(AHOC_EINVAL, "the triharmonic class takes no beta");
     d.levels = 0;
     d.uhat = -1;
   }
+  // automatic depth: the nested guess of a mixed plan only shortens its first
+  // correction solve (the later ones start from zero), which did not repay
+  // the coarse solves on B300 (2D 4096^2: 55 against 47 ms; 3D 512^3: 2 %
+  // faster); an explicit depth is honoured
+  if (d.prec == AHOC_MIXED && d.levels < 0) d.levels = 0;
   if (d.precond != 0 && d.precond != 1) return fail(AHOC_EINVAL, "precond must be 0 (none) or 1 (boundary symbol)");
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.batch > 4096) return fail(AHOC_EINVAL, "batch > 4096");
@@ -287,6 +292,18 @@ void dst_tables(int N, std::vector<double>& tw, std::vector<double>& sn) {
   }
   for (int k = 0; k <= M / 2; ++k)
     dst_factor(-2.0L * pi * (long double)k / (long double)N, dst_swap_post(k, N), &tw[2 * (off + k)]);
+  off += (size_t)M / 2 + 1;
+  // radix-8 stages
+  for (int Ns = dst_r8_first_ns(logM); Ns < M; Ns <<= 3) {
+    for (int kk = 0; kk < Ns; ++kk) {
+      const long double th = -pi * (long double)kk / (4.0L * Ns);  // W^kk, W = exp(-2 pi i/(8 Ns))
+      dst_factor(th, false, &tw[2 * (off + kk)]);
+      dst_factor(2 * th, dst_swap_w1(kk, Ns), &tw[2 * (off + Ns + kk)]);
+      dst_factor(4 * th, dst_swap_w2(kk, Ns), &tw[2 * (off + 2 * Ns + kk)]);
+      dst_factor(th - pi / 4, kk > 0, &tw[2 * (off + 3 * Ns + kk)]);
+    }
+    off += 4 * (size_t)Ns;
+  }
   for (int j = 0; j <= N / 2; ++j) sn[j] = (double)(0.5L * sinl(pi * (long double)j / (long double)N));
 }
 
@@ -403,6 +420,7 @@ void apply_tuning(Geom& g, const Opts& o) {
   const int nt = g.dim == 3 ? g.N[2] : g.N[1];
   g.triL = g_tune[AHOC_TUNE_TRI_CHUNK][di][pi][ilog2i(nt)].load();
   g.dst_cta = g_tune[AHOC_TUNE_DST_THREADS][di][pi][ilog2i(g.N[0])].load();
+  g.dst_radix = g_tune[AHOC_TUNE_DST_RADIX][di][pi][ilog2i(g.N[0])].load();
 }
 int64_t tri_ncols(const Geom& g) { return (int64_t)(g.N[0] - 1) * (g.dim == 3 ? (g.N[1] - 1) : 1); }
 bool chunked_for(const Geom& g, ahoc_precision prec) {
@@ -1872,9 +1890,10 @@ ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value) {
   if (dim != 2 && dim != 3) return fail(AHOC_EINVAL, "dim must be 2 or 3");
   if (N < 8 || N > kMaxN || !pow2(N)) return fail(AHOC_EINVAL, "N must be a power of two in [8, 4096]");
   if (prec != AHOC_FP64 && prec != AHOC_MIXED) return fail(AHOC_EINVAL, "prec must be AHOC_FP64 or AHOC_MIXED");
-  const bool ok = value == 0 || (kind == AHOC_TUNE_TRI_CHUNK ? (value == 8 || value == 16 || value == 32)
-                                                             : (value == 128 || value == 256 || value == 512 ||
-                                                                value == 1024));
+  const bool ok = value == 0 || (kind == AHOC_TUNE_TRI_CHUNK    ? (value == 8 || value == 16 || value == 32)
+                                 : kind == AHOC_TUNE_DST_RADIX ? (value == 4 || value == 8)
+                                                               : (value == 128 || value == 256 || value == 512 ||
+                                                                  value == 1024));
   if (!ok) return fail(AHOC_EINVAL, "value not offered for this kind");
   g_tune[kind][dim - 2][prec][ilog2i(N)].store(value);
   return AHOC_OK;
@@ -2263,6 +2282,44 @@ ahoc_status norms(ahoc_plan* p, const double* v, std::vector<double>& out) {
 
 ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol);
 
+// Nested initial guess: solve on the coarser grid (recursively, in the
+// plan's precision scheme), then prolong its Q to this grid's faces (the
+// coarse-grid interpolated initial guess of Sec. 4.1) into X0.
+ahoc_status coarse_guess(ahoc_plan* p, const double* f, const std::vector<int>& live, double tol, double* X0) {
+  const Geom& g = p->g;
+  const int nb = g.nb;
+  ahoc_plan* c = p->coarse;
+  double* f_c = p->W2;  // W2 is free at this point of both solve paths
+  CKS(set_act(c, live));
+  RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  c->part = live;
+  const double ctol = p->o.coarse_tol > tol ? p->o.coarse_tol : tol;
+  // only the coarse Q is used: the coarse level skips its recovery of V and U
+  ahoc_status cs_ = solve_internal(c, f_c, nullptr, ctol);
+  if (cs_ != AHOC_OK) return cs_;  // a coarse level's ENOCONV or ENUMERIC is kept in its stats
+  CKS(harvest(p));
+  for (int k = 0; k < AHOC_NK; ++k) {
+    // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
+    const double cms = c->kms[k];
+    const int64_t cn = c->kn[k];
+    p->kms_top[k] -= cms;
+    p->kn_top[k] -= cn;
+    p->kms[k] += cms;
+    p->kn[k] += cn;
+  }
+  p->launches += c->launches;
+  for (int i = 0; i < nb; ++i) {
+    p->ps[i].coarse_iters = c->ps[i].iters + c->ps[i].coarse_iters;
+    p->ps[i].ms_mv += c->ps[i].ms_mv;
+  }
+  CKS(set_act(p, live));
+  RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, X0, c->Q, p->st));
+  // f_c borrowed W2 as a temporary: restore its zero padding
+  CK(cudaMemsetAsync(p->W2, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+  return AHOC_OK;
+}
+
 // Algorithm 1 in FP64: b = -R(0), GMRES on S_h Q = b (from the nested
 // coarse-grid guess when the plan has coarse levels), recovery of V and U.
 ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
@@ -2287,38 +2344,7 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
   bool any_rhs = false;
   for (int i = 0; i < nb; ++i) any_rhs = any_rhs || (live[i] && beta0[i] > 0);
   if (any_rhs && p->coarse) {
-    // nested initial guess: solve on the coarser grid (recursively), then
-    // prolong its Q to this grid's faces (the coarse-grid interpolated
-    // initial guess of Sec. 4.1)
-    ahoc_plan* c = p->coarse;
-    double* f_c = p->W2;
-    CKS(set_act(c, live));
-    RUN(AHOC_K_OTHER, launch_inject_full(c->g, g, f_c, f, p->st));
-    CK(cudaStreamSynchronize(p->st));
-    c->part = live;
-    const double ctol = p->o.coarse_tol > tol ? p->o.coarse_tol : tol;
-    // only the coarse Q is used: the coarse level skips its recovery of V and U
-    ahoc_status cs_ = solve_internal(c, f_c, nullptr, ctol);
-    if (cs_ != AHOC_OK) return cs_;  // a coarse level's ENOCONV or ENUMERIC is kept in its stats
-    CKS(harvest(p));
-    for (int k = 0; k < AHOC_NK; ++k) {
-      // kms_top collects minus the coarse share, so kms + kms_top is this level's own time
-      const double cms = c->kms[k];
-      const int64_t cn = c->kn[k];
-      p->kms_top[k] -= cms;
-      p->kn_top[k] -= cn;
-      p->kms[k] += cms;
-      p->kn[k] += cn;
-    }
-    p->launches += c->launches;
-    for (int i = 0; i < nb; ++i) {
-      p->ps[i].coarse_iters = c->ps[i].iters + c->ps[i].coarse_iters;
-      p->ps[i].ms_mv += c->ps[i].ms_mv;
-    }
-    CKS(set_act(p, live));
-    RUN(AHOC_K_KRYLOV, launch_face_prolong(g, c->g, p->Q, c->Q, p->st));
-    // f_c borrowed W2 as a temporary: restore its zero padding
-    CK(cudaMemsetAsync(p->W2, 0, (size_t)nb * g.npad * sizeof(double), p->st));
+    CKS(coarse_guess(p, f, live, tol, p->Q));
     guess = true;
   }
   std::vector<ProbStat> go(nb);
@@ -2440,8 +2466,15 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
       maxit[i] = p->o.max_iters - s.iters;
     }
     if (!any(live)) break;
+    // the first correction is the whole solution: it starts from the nested
+    // coarse-grid guess when the plan has coarse levels
+    bool guess = false;
+    if (step == 0 && p->coarse) {
+      CKS(coarse_guess(p, f, live, tol, p->dQ));
+      guess = true;
+    }
     std::vector<ProbStat> gi(nb);
-    CKS(gmres(p, p->b2, bn, p->dQ, false, itol, maxit, live, gi));
+    CKS(gmres(p, p->b2, bn, p->dQ, guess, itol, maxit, live, gi));
     for (int i = 0; i < nb; ++i) {
       if (!live[i]) continue;
       ProbStat& s = p->ps[i];

@@ -37,6 +37,10 @@ def test_tuning_table_through_abi():
     assert L.ahoc_tune_get(k, dim, N, prec) == 8
     assert L.ahoc_tune_set(k, dim, N, prec, 12) == ahoc.AHOC_EINVAL  # not offered
     assert L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, prec, 2048) == ahoc.AHOC_EINVAL
+    for r, want in ((4, ahoc.AHOC_OK), (8, ahoc.AHOC_OK), (2, ahoc.AHOC_EINVAL), (16, ahoc.AHOC_EINVAL)):
+        assert L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, prec, r) == want
+    assert L.ahoc_tune_get(ahoc.AHOC_TUNE_DST_RADIX, dim, N, prec) == 8
+    assert L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, prec, 0) == ahoc.AHOC_OK
     assert L.ahoc_tune_set(k, 4, N, prec, 8) == ahoc.AHOC_EINVAL
     assert L.ahoc_tune_get(k, dim, 500, prec) == -1
     # the chunk length sets the tridiagonal scratch, so the workspace follows the table
@@ -66,16 +70,18 @@ def test_tuned_shapes_same_solution(dim, N, prec):
     p_ = ahoc._prec(prec)
     for tri in autotune.TRI_CHOICES:
         for cta in autotune.CTA_CHOICES:
-            L.ahoc_tune_set(ahoc.AHOC_TUNE_TRI_CHUNK, dim, N, p_, tri)
-            L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, p_, cta)
-            p = ahoc.Plan(dim, [N] * dim, d["alpha"], prec=prec)
-            u, info = p.solve(d["f"], tol=1e-12)
-            U = u.cpu().numpy().reshape(ref.shape)
-            rel = np.linalg.norm(U - ref) / np.linalg.norm(ref)
-            assert rel < (1e-10 if prec == "fp64" else 1e-9), (tri, cta, rel)
-            p.close()
+            for rad in autotune.RADIX_CHOICES:
+                L.ahoc_tune_set(ahoc.AHOC_TUNE_TRI_CHUNK, dim, N, p_, tri)
+                L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_THREADS, dim, N, p_, cta)
+                L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N, p_, rad)
+                p = ahoc.Plan(dim, [N] * dim, d["alpha"], prec=prec)
+                u, info = p.solve(d["f"], tol=1e-12)
+                U = u.cpu().numpy().reshape(ref.shape)
+                rel = np.linalg.norm(U - ref) / np.linalg.norm(ref)
+                assert rel < (1e-10 if prec == "fp64" else 1e-9), (tri, cta, rad, rel)
+                p.close()
     entry = autotune.tune_shape(dim, N, prec, batches=(1, 2, 4), reps=1)
     assert entry["tri_chunk"] in autotune.TRI_CHOICES and entry["dst_threads"] in autotune.CTA_CHOICES
-    assert entry["batch"] in (1, 2, 4)
-    for k in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS):
+    assert entry["dst_radix"] in autotune.RADIX_CHOICES and entry["batch"] in (1, 2, 4)
+    for k in (ahoc.AHOC_TUNE_TRI_CHUNK, ahoc.AHOC_TUNE_DST_THREADS, ahoc.AHOC_TUNE_DST_RADIX):
         L.ahoc_tune_set(k, dim, N, p_, 0)
