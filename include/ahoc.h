@@ -206,6 +206,14 @@ typedef struct {
                              of gamma as the reference shift.  Uses a few KB of temporary
                              device memory (cudaMalloc) and synchronises the stream; with it,
                              ahoc_workspace_bytes sizes for the variable-beta class.          */
+  int first32;            /* [0] AHOC_MIXED: 0 takes the first correction (the whole solution)
+                             with its Schur right-hand side from the data and its recovery of
+                             V and U by FP64 solves (four FP64 Poisson solves), only its GMRES
+                             in FP32: an FP32 right-hand side or recovery of the whole
+                             solution carries rounding amplified by L_h (about eps32 / h^2
+                             relative), which stalls the first steps on high-wavenumber data
+                             and fine grids.  Nonzero keeps them in FP32 like the later
+                             corrections.  Variable-beta plans always do                      */
 } ahoc_opts;
 
 /* automatic coarse-level tolerance of the nested initial guess (FP64 and

@@ -46,7 +46,7 @@ class ahoc_opts(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("levels", C.c_int), ("coarse_tol", C.c_double),
                 ("batch", C.c_int), ("navier", C.c_int), ("shift", C.c_double), ("no_graphs", C.c_int),
                 ("variable_beta", C.c_int), ("uhat_slots", C.c_int), ("unfused", C.c_int),
-                ("triharmonic", C.c_int), ("auto_shift", C.c_int)]
+                ("triharmonic", C.c_int), ("auto_shift", C.c_int), ("first32", C.c_int)]
 
 
 class ahoc_info(C.Structure):
@@ -147,9 +147,10 @@ def _prec(prec) -> int:
 
 def _opts(prec, max_iters, restart, precond, workspace=None, timing=0, levels=-1, refine_tol=0.0, coarse_tol=0.0,
           batch=1, graphs=True, navier=0, shift=0.0, variable_beta=False, uhat_slots=0, fused=True,
-          triharmonic=False, auto_shift=False):
+          triharmonic=False, auto_shift=False, first32=False):
     o = ahoc_opts()
     o.auto_shift = 1 if auto_shift else 0
+    o.first32 = 1 if first32 else 0
     o.unfused = 0 if fused else 1
     o.triharmonic = 1 if triharmonic else 0
     o.variable_beta = 1 if variable_beta else 0
@@ -215,7 +216,7 @@ class Plan:
                  prec: int = AHOC_FP64,
                  max_iters: int = 500, restart: int = 100, precond: int = 1, stream=None, timing: bool = False,
                  levels: int = -1, refine_tol: float = 0.0, coarse_tol: float = 0.0, batch: int = 1,
-                 graphs: bool = True, uhat_slots: int = 0, fused: bool = True):
+                 graphs: bool = True, uhat_slots: int = 0, fused: bool = True, first32: bool = False):
         L = lib()
         self.dim = dim
         self.batch = int(batch)
@@ -250,7 +251,7 @@ class Plan:
                         _ptr(lap_gD, B * self.nfull, "lap_gD"), _ptr(bilap, B * self.nfull, "bilap"),
                         _ptr(g_NN, B * self.ngamma, "g_NN"), _ptr(lapt_w, B * self.ngamma, "lapt_w"))
         o = _opts(prec, max_iters, restart, precond, self._ws, timing, levels, refine_tol, coarse_tol, B, graphs,
-                  navier, shift, variable_beta, uhat_slots, fused, triharmonic, auto_shift)
+                  navier, shift, variable_beta, uhat_slots, fused, triharmonic, auto_shift, first32)
         h = C.c_void_p(0)
         n = (C.c_int64 * dim)(*self.N)
         lo_ = (C.c_double * dim)(*self.lo)

@@ -66,6 +66,7 @@ struct Opts {
   int uhat = 0;          // U-hat slots of the recovery (0 automatic, < 0 none)
   int unfused = 0;       // 3D: the plain Schur matvec (eight DST passes) instead of the fused one
   int tri = 0;           // the triharmonic class: Lap^3 u = f, navier = the simply supported faces
+  int first64 = 1;       // mixed: right-hand side and recovery of the first correction in FP64
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
 };
@@ -90,6 +91,7 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
     d.uhat = o->uhat_slots;
     d.unfused = o->unfused ? 1 : 0;
     d.tri = o->triharmonic ? 1 : 0;
+    d.first64 = o->first32 ? 0 : 1;
     d.workspace = o->workspace;
     d.workspace_bytes = o->workspace_bytes;
   }
@@ -2387,7 +2389,9 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
 // of the batch in lockstep.  Each step takes the FP64 residual of all three
 // block rows at x = (U, V, Q), solves the coupled correction system with FP32
 // Poisson solves (the same Schur method: b = -R_d(0), GMRES on S dQ = b to
-// refine_tol, recovery of dV, dU) and adds the correction in FP64.  The
+// refine_tol, recovery of dV, dU) and adds the correction in FP64 (the first
+// correction, the whole solution, takes its right-hand side and its recovery
+// from FP64 solves unless opts.first32).  The
 // relative size of the correction right-hand side -- the Schur residual of
 // the current iterate, evaluated from the FP64 residual -- is the stopping
 // test, so tol has the meaning it has on the FP64 path.
@@ -2401,21 +2405,29 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
   CK(cudaMemsetAsync(p->Q, 0, (size_t)nb * n * sizeof(double), p->st));
   std::vector<int> live = p->part;
   std::vector<double> bref(nb, 0.0), bn;
+  const bool first64 = p->o.first64 && !p->o.varb;
   for (int step = 0; step <= kMaxRefine && any(live); ++step) {
     CKS(set_act(p, live));
-    RUNN(AHOC_K_OTHER, 2,
-         launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->has_gD ? p->gD : nullptr,
-                         p->has_vedge ? p->vedge : nullptr, p->has_gN ? p->gN : nullptr,
-                         p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st, p->has_gL ? p->gL : nullptr, p->gam));
-    // correction right-hand side b = -R_d(0)
-    if (fused_ok(g)) {
-      CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));
+    if (step == 0 && first64) {
+      // x = 0: the correction system is the whole system; its Schur
+      // right-hand side -R(0) from the data by FP64 solves
+      CKS(schur_rhs_dev(p, f, p->b2));
     } else {
-      CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
-      RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
-                                            p->st, p->Rq));
+      RUNN(AHOC_K_OTHER, 2,
+           launch_residual(g, p->cf, p->Ru, p->Rv, p->Rq, p->U64, p->V64, p->Q, f, p->has_gD ? p->gD : nullptr,
+                           p->has_vedge ? p->vedge : nullptr, p->has_gN ? p->gN : nullptr,
+                           p->has_lapt ? p->lapt : nullptr, p->ainv, p->afac, p->st, p->has_gL ? p->gL : nullptr,
+                           p->gam));
+      // correction right-hand side b = -R_d(0)
+      if (fused_ok(g)) {
+        CKS(fused2d<float>(p, f2arrays_f(p), nullptr, p->Rv, p->Ru, p->Rq, p->b2, false));
+      } else {
+        CKS(solve_VU_f(p, nullptr, p->Rv, p->Ru));
+        RUN(AHOC_K_TRACE, launch_trace<float>(g, p->cf, p->b2, p->F2, nullptr, p->afac, nullptr, nullptr, nullptr,
+                                              p->st, p->Rq));
+      }
+      RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st, nb, nullptr, g.act));
     }
-    RUN(AHOC_K_KRYLOV, launch_axpby(p->b2, p->b2, -1.0, 0.0, n, p->st, nb, nullptr, g.act));
     CKS(norms(p, p->b2, bn));
     std::vector<double> itol(nb, 0.0);
     std::vector<int> maxit(nb, 0);
@@ -2434,20 +2446,21 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
         live[i] = 0;
         continue;
       }
-      // Stagnation (a step that removes less than a tenth of the residual):
-      // the residual has reached the floor of its FP64 evaluation (data
-      // whose Schur right-hand side is tiny next to the solution, or a tol
-      // at that floor).  If the last correction changed U by at most tol
-      // (relative 2-norm), the iterate is settled to the accuracy asked for
-      // and the solve has converged; if the corrections still shrink (at
-      // least halve), the next step settles it further; otherwise the FP32
-      // solves are too inaccurate for this grid and the solve has not
-      // converged.
+      // Slow steps: the residual has reached the floor of its evaluation
+      // (the FP32 recovery's rounding, amplified by L_h, or data whose Schur
+      // right-hand side is tiny next to the solution, or a tol at that
+      // floor).  A step that removed less than half of the residual while
+      // the last correction changed U by at most tol (relative 2-norm): the
+      // iterate is settled to the accuracy asked for, the solve has
+      // converged.  A step that removed less than a tenth: if the
+      // corrections still shrink (at least halve), the next step settles it
+      // further; otherwise the FP32 solves are too inaccurate for this grid
+      // and the solve has not converged.
+      if (step >= 2 && s.rel > 0.5 * s.hist[step - 1] && s.du[step - 1] <= tol) {
+        live[i] = 0;
+        continue;
+      }
       if (step >= 2 && s.rel > 0.9 * s.hist[step - 1]) {
-        if (s.du[step - 1] <= tol) {
-          live[i] = 0;
-          continue;
-        }
         if (!(s.du[step - 1] < 0.5 * s.du[step - 2])) {
           s.status = AHOC_ENOCONV;
           live[i] = 0;
@@ -2489,18 +2502,31 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
     }
     // recovery of the correction and the FP64 update
     CKS(set_act(p, live));
-    if (fused_ok(g))
-      CKS(fused2d<float>(p, f2arrays_f(p), p->dQ, p->Rv, p->Ru, nullptr, nullptr, true));
-    else
-      CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
-    RUNN(AHOC_K_OTHER, 2, launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->partial, kDotBlocks, p->hdev, p->st));
+    const bool rec64 = (step == 0 && first64);
+    if (rec64) {
+      // the first correction is the whole solution (x = 0): V and U from it
+      // by the FP64 solves.  An FP32 recovery here leaves rounding noise of
+      // the size of U itself, which L_h amplifies in the next FP64 residual
+      // and which then floors the next correction at about eps32 / h^2
+      // (relative); the later corrections are small, so is their noise.
+      CKS(solve_VU(p, p->dQ, f, true));
+      RUN(AHOC_K_OTHER, launch_axpby(p->U64, p->W2, 1.0, 0.0, g.npad, p->st, nb, nullptr, g.act));
+      RUN(AHOC_K_OTHER, launch_axpby(p->V64, p->W1, 1.0, 0.0, g.npad, p->st, nb, nullptr, g.act));
+    } else {
+      if (fused_ok(g))
+        CKS(fused2d<float>(p, f2arrays_f(p), p->dQ, p->Rv, p->Ru, nullptr, nullptr, true));
+      else
+        CKS(solve_VU_f(p, p->dQ, p->Rv, p->Ru));
+      RUNN(AHOC_K_OTHER, 2,
+           launch_accumulate(g, p->U64, p->F2, p->V64, p->F1, p->partial, kDotBlocks, p->hdev, p->st));
+    }
     RUN(AHOC_K_KRYLOV, launch_axpby(p->Q, p->dQ, 1.0, 1.0, n, p->st, nb, nullptr, g.act));
-    CKS(fetch(p));
+    if (!rec64) CKS(fetch(p));
     for (int i = 0; i < nb; ++i) {
       if (!live[i]) continue;
       ProbStat& s = p->ps[i];
       const double su = p->hhost[2 * i + 1], sdu = p->hhost[2 * i];
-      s.du[step] = su > 0 ? std::sqrt(sdu / su) : 0.0;
+      s.du[step] = rec64 ? 1.0 : (su > 0 ? std::sqrt(sdu / su) : 0.0);
       ++s.refine_steps;
       if (s.iters >= p->o.max_iters) {
         s.status = AHOC_ENOCONV;

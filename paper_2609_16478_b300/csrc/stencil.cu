@@ -596,6 +596,12 @@ __device__ __forceinline__ double vfull(const Geom& g, const double* V, const do
   return vedge ? vedge[g.full(i, j, k)] : 0.0;
 }
 
+// DIM: 2 or 3 (the stencil loops unroll: the 3D corners, which carry no
+// weight, cost nothing).  SH: the shift term of the v-row, 0 none, 1 the
+// constant cf.gam, 2 the field gam (separate instantiations: this kernel is
+// bound by the FP64 pipe, and a runtime branch becomes predicated FP64
+// operations)
+template <int DIM, int SH>
 __global__ void k_residual(Geom g, Coefs cf, const double* __restrict__ gam, float* __restrict__ ru,
                            float* __restrict__ rv, const double* __restrict__ U, const double* __restrict__ V, const double* __restrict__ Q,
                            const double* __restrict__ f, const double* __restrict__ gD,
@@ -625,12 +631,15 @@ __global__ void k_residual(Geom g, Coefs cf, const double* __restrict__ gam, flo
   }
   const bool near = near_bdry(g, i, j, k);
   double lu = 0.0, lv = 0.0;
-  const int dzlo = (g.dim == 3) ? -1 : 0, dzhi = (g.dim == 3) ? 1 : 0;
+  constexpr int dzlo = (DIM == 3) ? -1 : 0, dzhi = (DIM == 3) ? 1 : 0;
+#pragma unroll
   for (int dz = dzlo; dz <= dzhi; ++dz)
+#pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
+        if (DIM == 3 && dx != 0 && dy != 0 && dz != 0) continue;  // the 19-point stencil has no corners
         const double c = cf.L[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
-        if (c == 0.0) continue;
         const int ii = i + dx, jj = j + dy, kk = k + dz;
         if (near) {
           lu += c * ufull(g, U, gD, ii, jj, kk);
@@ -647,21 +656,25 @@ __global__ void k_residual(Geom g, Coefs cf, const double* __restrict__ gam, flo
   const int64_t fc = g.full(i, j, k);
   const double vc = V[t];
   double swn = 0.0, svn = 0.0, sgn = 0.0, sfn = 0.0;
-  for (int a = 0; a < g.dim; ++a)
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
     for (int s = -1; s <= 1; s += 2) {
       const int ii = i + (a == 0 ? s : 0), jj = j + (a == 1 ? s : 0), kk = k + (a == 2 ? s : 0);
       const int64_t fn = g.full(ii, jj, kk);
-      const double vn = vfull(g, V, Q, vedge, ii, jj, kk);
+      const double vn = near ? vfull(g, V, Q, vedge, ii, jj, kk) : V[g.pad(ii, jj, kk)];
       swn = fma(vn, ainv[fn], swn);
-      if (gam) sgn = fma(vn, gam[fn], sgn);
-      else svn += vn;
+      if (SH == 2) sgn = fma(vn, gam[fn], sgn);
+      if (SH == 1) svn += vn;
       if (f) sfn += f[fn];
     }
   const double mv = fma(cf.Mn, swn, cf.Mc * (vc * ainv[fc]));
-  const double mgv = gam ? fma(cf.Mn, sgn, cf.Mc * (vc * gam[fc])) : cf.gam * fma(cf.Mn, svn, cf.Mc * vc);
+  double mgv = 0.0;
+  if (SH == 2) mgv = fma(cf.Mn, sgn, cf.Mc * (vc * gam[fc]));
+  if (SH == 1) mgv = cf.gam * fma(cf.Mn, svn, cf.Mc * vc);
   const double mf = f ? fma(cf.Mn, sfn, cf.Mc * f[fc]) : 0.0;
   ru[t] = (float)(mv - lu);
-  rv[t] = (float)(mf + lv - mgv);
+  rv[t] = (float)(SH ? (mf + lv - mgv) : (mf + lv));
 }
 
 // r_q at every face point (FP64)
@@ -755,7 +768,19 @@ cudaError_t launch_residual(const Geom& g, const Coefs& cf, float* ru, float* rv
                             const double* V, const double* Q, const double* f, const double* gD, const double* vedge,
                             const double* gN, const double* lapt, const double* ainv, const double* afac,
                             cudaStream_t st, const double* gL, const double* gam) {
-  k_residual<<<dim3(nblk(g.npad, 256), g.nb), 256, 0, st>>>(g, cf, gam, ru, rv, U, V, Q, f, gD, vedge, ainv);
+  const dim3 grid(nblk(g.npad, 256), g.nb);
+  const int sh = gam ? 2 : (cf.gam != 0.0 ? 1 : 0);
+#define AHOC_RESID(D, S) k_residual<D, S><<<grid, 256, 0, st>>>(g, cf, gam, ru, rv, U, V, Q, f, gD, vedge, ainv)
+  if (g.dim == 3) {
+    if (sh == 2) AHOC_RESID(3, 2);
+    else if (sh == 1) AHOC_RESID(3, 1);
+    else AHOC_RESID(3, 0);
+  } else {
+    if (sh == 2) AHOC_RESID(2, 2);
+    else if (sh == 1) AHOC_RESID(2, 1);
+    else AHOC_RESID(2, 0);
+  }
+#undef AHOC_RESID
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_residual_q<<<dim3(nblk(g.ngamma, 256), g.nb), 256, 0, st>>>(g, cf, rq, U, Q, afac, gD, gN, lapt, gL);

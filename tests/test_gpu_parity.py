@@ -273,6 +273,23 @@ def test_nested_initial_guess_matches_oracle(name, N, levels):
 TOL_MIXED = 1e-9
 
 
+@pytest.mark.parametrize("name,N", [("fourier2d", [256, 256]), ("sincos3d", [32, 32, 32]), ("fourier3d", [32, 32, 32])])
+def test_mixed_first_step_fp64_and_fp32_match_oracle(name, N):
+    """The first correction's right-hand side and recovery by FP64 solves
+    (the default) or FP32 ones (opts.first32): both refined results against
+    the oracle, and the FP64 first step brings the Schur residual down by at
+    least the FP32 operator's accuracy."""
+    d = inputs.sample(inputs.config_problem(name), N)
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    f = _dev(d["f"])
+    shape = tuple(n + 1 for n in reversed(N))
+    u1, i1 = _plan(d, prec="mixed").solve(f, tol=1e-12)
+    assert i1["status"] == 0 and _rel(_host(u1, shape), sol.U) < TOL_MIXED, i1
+    assert i1["refine_hist"][1] < 1e-3, i1["refine_hist"]
+    u0, i0 = _plan(d, prec="mixed", first32=True).solve(f, tol=1e-12)
+    assert i0["status"] == 0 and _rel(_host(u0, shape), sol.U) < TOL_MIXED, i0
+
+
 @pytest.mark.parametrize("name,N,levels", [("fourier2d", [256, 256], 2), ("sincos3d", [32, 32, 32], 1)])
 def test_mixed_nested_guess_matches_oracle(name, N, levels):
     """A mixed plan with an explicit nested guess (coarse levels that are

@@ -20,7 +20,9 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("prec,realtime", [("mixed", False), ("fp64", True)])
 def test_served_equals_solo(prec, realtime):
     tol = 1e-12
-    specs = inputs.request_stream(20, rate=400.0 if realtime else 0.0, seed=9, sizes2d=(64, 128), sizes3d=(16, 32))
+    # realtime: 20 requests within about 5 ms, faster than three workers
+    # solve them one at a time, so same-shape requests meet in a batch
+    specs = inputs.request_stream(20, rate=4000.0 if realtime else 0.0, seed=9, sizes2d=(64, 128), sizes3d=(16, 32))
     srv = serving.Server(prec=prec, tol=tol, workers=3, keep_results=True, batch_for=lambda k: 4,
                          check_exact=True)
     recs = srv.run(specs, realtime=realtime)
