@@ -148,13 +148,6 @@ __device__ __forceinline__ void st_pair(double2* p, double2 u, double2 v, int) {
   p[1] = v;
 }
 
-// Output X_j of a line after dst_lines with natural == false: X_j at y[j]
-// for even j, X_{2m+1} at y[N + m].
-template <typename T>
-__device__ __forceinline__ T dst_out(const T* y, int N, int j) {
-  return y[(j & 1) ? N + (j >> 1) : j];
-}
-
 // The pre-processing of one pair (j, N-j) (step 1 of dst_lines), for callers
 // that fold it into their loads: z_j = (s_j + 1/4) x_j + (s_j - 1/4) x_{N-j}
 // and z_{N-j} the other way round; the middle pair (j = N/2) also clears the
@@ -171,8 +164,8 @@ __device__ __forceinline__ void dst_pre_pair(T* y, int N, int j, T xa, T xb, con
 // with s[l*LS] == 0, followed by N/2 elements of scratch (LS >= 3N/2); s and
 // LS * sizeof(T) are multiples of 16 bytes.  With `pre_done` the lines hold
 // the pre-processed z (dst_pre_pair) instead of x.  The output is in natural
-// order when `natural`, else the odd outputs X_{2m+1} are at y[N + m]
-// (dst_out).  Every thread of the CTA must call this.  wsum: >= 32 elements
+// order when `natural`; otherwise X_j is at y[j] for even j and X_{2m+1} at
+// y[N + m].  Every thread of the CTA must call this.  wsum: >= 32 elements
 // of scratch for the cross-warp scan.
 template <typename T, bool R8 = false>
 __device__ void dst_lines(T* s, int LS, int N, int logN, int TPL, const typename Cplx<T>::t* __restrict__ tw,
@@ -806,6 +799,31 @@ static inline int ilog2(int n) {
   return l;
 }
 
+// Dynamic shared memory above the 48 KB default: the kernel's limit is raised
+// once, to the device's opt-in maximum, not to each launch's size.  A launch
+// captured in a CUDA graph keeps its size; a later launch of the same kernel
+// with a smaller size must not lower the limit under it.  Cached per device
+// and kernel.
+static cudaError_t allow_smem(const void* kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({dev, kernel});
+  if (it != done.end()) return (size_t)it->second >= smem ? cudaSuccess : cudaErrorInvalidValue;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if ((size_t)optin < smem) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  done[{dev, kernel}] = optin;
+  return cudaSuccess;
+}
+
 // CTAs of one launch of a grid-stride line kernel (k_dst_y in FP32): its
 // groups of lines, but no more than the device holds resident at once
 // (occupancy x SMs, shared by the nb problems of a batch), so that every CTA
@@ -851,9 +869,8 @@ static cudaError_t dst_x_launch(const Geom& g, T* dst, const DstIO<T>& io, const
   const int64_t blocks = (nrows + LPC - 1) / LPC;
   const size_t smem =
       ((size_t)LPC * (N + N / 2) + 32) * sizeof(T) + (size_t)LPC * (2 * sizeof(int64_t) + 2 * sizeof(int));
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_dst_x<T, LOAD, STORE, R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_dst_x<T, LOAD, STORE, R8>), smem);
     if (e != cudaSuccess) return e;
   }
   k_dst_x<T, LOAD, STORE, R8><<<dim3((unsigned)blocks, (unsigned)g.nb), threads, smem, st>>>(
@@ -948,8 +965,8 @@ static cudaError_t dst_y_launch(const Geom& g, T* a, const void* tw, const T* sn
   if (off < (int)(16 / sizeof(T))) off = (int)(16 / sizeof(T));
   const int LS = N + N / 2 + off;
   const size_t smem = ((size_t)LPC * LS + 32) * sizeof(T);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_dst_y<T, R8, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_dst_y<T, R8, SC>), smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t groups = ((g.n0 + LPC - 1) / LPC) * (int64_t)(g.kmax - g.kmin);
@@ -979,8 +996,8 @@ cudaError_t launch_dst_gen(T* base, int nlines, int lpg, int64_t gstride, int64_
   const int threads = TPL * LPC;
   const int blocks = (nlines + LPC - 1) / LPC;
   const size_t smem = ((size_t)LPC * (N + N / 2) + 32) * sizeof(T);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_dst_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_dst_gen<T>), smem);
     if (e != cudaSuccess) return e;
   }
   k_dst_gen<T><<<dim3(blocks, nb), threads, smem, st>>>(base, nlines, lpg, gstride, lstride, estride, N,
@@ -1003,8 +1020,8 @@ cudaError_t launch_precond_lines(double* out, const double* in, const double* af
   const int threads = TPL * LPC;
   const int blocks = (nlines + LPC - 1) / LPC;
   const size_t smem = ((size_t)LPC * (N + N / 2) + 32) * sizeof(T);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_precond_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_precond_lines<T>), smem);
     if (e != cudaSuccess) return e;
   }
   k_precond_lines<T><<<dim3(blocks, nb), threads, smem, st>>>(out, in, afac, pre, nlines, lstride, N,

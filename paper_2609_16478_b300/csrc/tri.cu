@@ -299,34 +299,68 @@ __global__ void __launch_bounds__(128) k_tri_t1(Geom g, const T* __restrict__ a,
   E[(int64_t)c * sh.ncols + m] = (double)w;
 }
 
-__global__ void k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ E,
-                          double* __restrict__ carry, int L) {
+// Carries of the chunked tridiagonal solves.  Along a column the chunk values
+// v_c combine as s_{c+1} = v_c + rL s_c (forward, c = 0 .. C-1) or
+// s_c = v_c + rL s_{c+1} (backward, c = C-1 .. 0), from s = 0; out_c is the
+// value that enters chunk c (an exclusive scan) and the return value the
+// total.  A CTA takes kScanCols columns (one per lane, so every load and
+// store is coalesced across the columns) and cuts the C chunks into
+// kScanSegs segments, one per warp: each warp composes its segment's affine
+// map s -> rL^n s + b, the maps of the earlier segments are applied in
+// order from shared memory, and each warp writes its segment's outputs.  The
+// serial chain per column is C / kScanSegs chunks instead of C.
+constexpr int kScanCols = 32, kScanSegs = 8;
+template <bool FWD, class VF>
+__device__ __forceinline__ double carry_scan(int C, double rL, const VF& v, double* out, int64_t ostride,
+                                             bool in_range) {
+  __shared__ double mA[kScanSegs][kScanCols], mB[kScanSegs][kScanCols];
+  const int lane = threadIdx.x & (kScanCols - 1), seg = threadIdx.x / kScanCols;
+  const int per = (C + kScanSegs - 1) / kScanSegs;
+  const int c0 = seg * per, c1 = min(C, c0 + per);
+  // this segment's map, in the scan's direction
+  double a = 1.0, b = 0.0;
+  if (in_range) {
+    for (int q = 0; q < c1 - c0; ++q) {
+      const int c = FWD ? c0 + q : c1 - 1 - q;
+      b = fma(rL, b, v(c));
+      a *= rL;
+    }
+  }
+  mA[seg][lane] = a;
+  mB[seg][lane] = b;
+  __syncthreads();
+  // the value entering this segment: the earlier segments' maps in order
+  double sv = 0.0;
+  for (int t = 0; t < kScanSegs; ++t) {
+    const int u = FWD ? t : kScanSegs - 1 - t;
+    if (FWD ? (u >= seg) : (u <= seg)) break;
+    sv = fma(mA[u][lane], sv, mB[u][lane]);
+  }
+  double total = 0.0;
+  if (in_range) {
+    for (int q = 0; q < c1 - c0; ++q) {
+      const int c = FWD ? c0 + q : c1 - 1 - q;
+      out[(int64_t)c * ostride] = sv;
+      sv = fma(rL, sv, v(c));
+    }
+    total = sv;  // after the last segment in the scan's direction: the whole column's value
+  }
+  return total;
+}
+
+__global__ void __launch_bounds__(kScanCols * kScanSegs) k_tri_t1b(Geom g, const Mode<double>* __restrict__ modes,
+                                                                   const double* __restrict__ E,
+                                                                   double* __restrict__ carry, int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   E += (int64_t)blockIdx.y * tri_sstride(sh);
   carry += (int64_t)blockIdx.y * tri_sstride(sh);
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sh.ncols) return;
-  const double r = modes[m].r;
-  const double rL = ipow(r, L);
-  double cy = 0;
+  const int64_t m = (int64_t)blockIdx.x * kScanCols + (threadIdx.x & (kScanCols - 1));
+  const bool in = m < sh.ncols;
+  const double rL = in ? ipow(modes[m].r, L) : 0.0;
   // only the last chunk may be shorter; its carry-out is unused
-  constexpr int B = 8;
-  int c = 0;
-  for (; c + B <= sh.C; c += B) {
-    double e[B];
-#pragma unroll
-    for (int q = 0; q < B; ++q) e[q] = E[(int64_t)(c + q) * sh.ncols + m];
-#pragma unroll
-    for (int q = 0; q < B; ++q) {
-      carry[(int64_t)(c + q) * sh.ncols + m] = cy;
-      cy = e[q] + rL * cy;
-    }
-  }
-  for (; c < sh.C; ++c) {
-    carry[(int64_t)c * sh.ncols + m] = cy;
-    cy = E[(int64_t)c * sh.ncols + m] + rL * cy;
-  }
+  carry_scan<true>(sh.C, rL, [&](int c) { return E[(int64_t)c * sh.ncols + m]; }, carry + (in ? m : 0), sh.ncols,
+                   in);
 }
 
 template <typename T, int L, int GEN, class GT>
@@ -370,40 +404,22 @@ __global__ void __launch_bounds__(128) k_tri_t2(Geom g, T* __restrict__ a, const
   B[(int64_t)c * sh.ncols + m] = (double)p;
 }
 
-__global__ void k_tri_t2b(Geom g, const Mode<double>* __restrict__ modes, const double* __restrict__ B,
-                          double* __restrict__ bcarry, double* __restrict__ Cc, int L) {
+__global__ void __launch_bounds__(kScanCols * kScanSegs) k_tri_t2b(Geom g, const Mode<double>* __restrict__ modes,
+                                                                   const double* __restrict__ B,
+                                                                   double* __restrict__ bcarry, double* __restrict__ Cc,
+                                                                   int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   B += (int64_t)blockIdx.y * tri_sstride(sh);
   bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
   Cc += (int64_t)blockIdx.y * tri_sstride(sh);
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sh.ncols) return;
-  const double r = modes[m].r;
-  const double rL = ipow(r, L);
-  const int lastlen = sh.nt - (sh.C - 1) * L;
-  // last (possibly shorter) chunk first, then the full ones in batches
-  double bc = 0;
-  int c = sh.C - 1;
-  bcarry[(int64_t)c * sh.ncols + m] = bc;
-  bc = B[(int64_t)c * sh.ncols + m] + ipow(r, lastlen) * bc;  // p at the chunk start
-  --c;
-  constexpr int NB = 8;
-  for (; c - NB + 1 >= 0; c -= NB) {
-    double bv[NB];
-#pragma unroll
-    for (int q = 0; q < NB; ++q) bv[q] = B[(int64_t)(c - q) * sh.ncols + m];
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      bcarry[(int64_t)(c - q) * sh.ncols + m] = bc;
-      bc = bv[q] + rL * bc;
-    }
-  }
-  for (; c >= 0; --c) {
-    bcarry[(int64_t)c * sh.ncols + m] = bc;
-    bc = B[(int64_t)c * sh.ncols + m] + rL * bc;
-  }
-  Cc[m] = modes[m].kapC * bc;  // bc = p_1
+  const int64_t m = (int64_t)blockIdx.x * kScanCols + (threadIdx.x & (kScanCols - 1));
+  const bool in = m < sh.ncols;
+  const double rL = in ? ipow(modes[m].r, L) : 0.0;
+  // the last (possibly shorter) chunk enters first, from zero: its own power of r never multiplies
+  const double p1 = carry_scan<false>(sh.C, rL, [&](int c) { return B[(int64_t)c * sh.ncols + m]; },
+                                      bcarry + (in ? m : 0), sh.ncols, in);
+  if (in && threadIdx.x < kScanCols) Cc[m] = modes[m].kapC * p1;  // segment 0 ends at chunk 0: p_1
 }
 
 template <typename T, int L>
@@ -613,81 +629,51 @@ __global__ void __launch_bounds__(128) k_tri2_t1(Geom g, double* __restrict__ a,
     if (q < len) col[(int64_t)(s0 + q) * sh.stride] = d[q];
 }
 
-constexpr int kCarryThreads = 32;  // one thread per column; small CTAs spread the columns over the SMs
-constexpr int kCarryBatch = 8;
-
 // forward carries cf_c = w_{s0(c)-1}
-__global__ void __launch_bounds__(kCarryThreads) k_tri2_t1b(Geom g, const double* __restrict__ tab,
-                                                            const double* __restrict__ E,
-                                                            double* __restrict__ carry, int L) {
+__global__ void __launch_bounds__(kScanCols * kScanSegs) k_tri2_t1b(Geom g, const double* __restrict__ tab,
+                                                                    const double* __restrict__ E,
+                                                                    double* __restrict__ carry, int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   E += (int64_t)blockIdx.y * tri_sstride(sh);
   carry += (int64_t)blockIdx.y * tri_sstride(sh);
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sh.ncols) return;
+  const int64_t m = (int64_t)blockIdx.x * kScanCols + (threadIdx.x & (kScanCols - 1));
+  const bool in = m < sh.ncols;
   const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
-  const double rL = tab[o.rL + m];
-  double cy = 0.0;
-  int c = 0;
-  for (; c + kCarryBatch <= sh.C; c += kCarryBatch) {
-    double e[kCarryBatch];
-#pragma unroll
-    for (int q = 0; q < kCarryBatch; ++q) e[q] = E[(int64_t)(c + q) * sh.ncols + m];
-#pragma unroll
-    for (int q = 0; q < kCarryBatch; ++q) {
-      carry[(int64_t)(c + q) * sh.ncols + m] = cy;
-      cy = fma(rL, cy, e[q]);
-    }
-  }
-  for (; c < sh.C; ++c) {
-    carry[(int64_t)c * sh.ncols + m] = cy;
-    cy = fma(rL, cy, E[(int64_t)c * sh.ncols + m]);
-  }
+  const double rL = in ? tab[o.rL + m] : 0.0;
+  carry_scan<true>(sh.C, rL, [&](int c) { return E[(int64_t)c * sh.ncols + m]; }, carry + (in ? m : 0), sh.ncols,
+                   in);
 }
 
-// backward carries cb_c = p_{e0(c)+1} and C = kapC p_1
-__global__ void __launch_bounds__(kCarryThreads) k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes,
-                                                            const double* __restrict__ tab,
-                                                            const double* __restrict__ B,
-                                                            const double* __restrict__ carry,
-                                                            double* __restrict__ bcarry, double* __restrict__ Cc,
-                                                            int L) {
+// backward carries cb_c = p_{e0(c)+1} and C = kapC p_1; a chunk's value is
+// its local p plus the forward carry's share cf G_0 (G_0 of the shorter last
+// chunk for c = C - 1)
+__global__ void __launch_bounds__(kScanCols * kScanSegs) k_tri2_t2b(Geom g, const Mode<double>* __restrict__ modes,
+                                                                    const double* __restrict__ tab,
+                                                                    const double* __restrict__ B,
+                                                                    const double* __restrict__ carry,
+                                                                    double* __restrict__ bcarry,
+                                                                    double* __restrict__ Cc, int L) {
   if (g.skip(blockIdx.y)) return;
   const TriShape sh = tri_shape(g, L);
   B += (int64_t)blockIdx.y * tri_sstride(sh);
   carry += (int64_t)blockIdx.y * tri_sstride(sh);
   bcarry += (int64_t)blockIdx.y * tri_sstride(sh);
   Cc += (int64_t)blockIdx.y * tri_sstride(sh);
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= sh.ncols) return;
+  const int64_t m = (int64_t)blockIdx.x * kScanCols + (threadIdx.x & (kScanCols - 1));
+  const bool in = m < sh.ncols;
   const Tri2Off o = tri2_offsets(sh.ncols, sh.C, L);
-  const double rL = tab[o.rL + m], G0 = tab[o.G0f + m];
-  // the last (possibly shorter) chunk, then the full ones in batches
-  int c = sh.C - 1;
-  int64_t i = (int64_t)c * sh.ncols + m;
-  bcarry[i] = 0.0;
-  double bc = fma(carry[i], tab[o.G0l + m], B[i]);  // p at the chunk start
-  --c;
-  for (; c - kCarryBatch + 1 >= 0; c -= kCarryBatch) {
-    double h[kCarryBatch];
-#pragma unroll
-    for (int q = 0; q < kCarryBatch; ++q) {
-      const int64_t k = (int64_t)(c - q) * sh.ncols + m;
-      h[q] = fma(carry[k], G0, B[k]);
-    }
-#pragma unroll
-    for (int q = 0; q < kCarryBatch; ++q) {
-      bcarry[(int64_t)(c - q) * sh.ncols + m] = bc;
-      bc = fma(rL, bc, h[q]);
-    }
-  }
-  for (; c >= 0; --c) {
-    i = (int64_t)c * sh.ncols + m;
-    bcarry[i] = bc;
-    bc = fma(rL, bc, fma(carry[i], G0, B[i]));
-  }
-  Cc[m] = modes[m].kapC * bc;  // bc = p_1
+  const double rL = in ? tab[o.rL + m] : 0.0;
+  const double G0 = in ? tab[o.G0f + m] : 0.0, G0l = in ? tab[o.G0l + m] : 0.0;
+  const int last = sh.C - 1;
+  const double p1 = carry_scan<false>(
+      sh.C, rL,
+      [&](int c) {
+        const int64_t i = (int64_t)c * sh.ncols + m;
+        return fma(carry[i], c == last ? G0l : G0, B[i]);
+      },
+      bcarry + (in ? m : 0), sh.ncols, in);
+  if (in && threadIdx.x < kScanCols) Cc[m] = modes[m].kapC * p1;  // segment 0 ends at chunk 0: p_1
 }
 
 template <int L>
@@ -750,10 +736,10 @@ static cudaError_t tri2_L(const Geom& g, double* a, const Mode<double>* modes, c
   double* Cc = bcarry + (int64_t)C * ncols;
   const int64_t work = ncols * C;
   const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
-  const dim3 cb((unsigned)((ncols + kCarryThreads - 1) / kCarryThreads), (unsigned)g.nb);
+  const dim3 cb((unsigned)((ncols + kScanCols - 1) / kScanCols), (unsigned)g.nb);
   k_tri2_t1<L, GEN><<<gb, 128, 0, st>>>(g, a, modes, E, B, G);
-  k_tri2_t1b<<<cb, kCarryThreads, 0, st>>>(g, tab, E, carry, L);
-  k_tri2_t2b<<<cb, kCarryThreads, 0, st>>>(g, modes, tab, B, carry, bcarry, Cc, L);
+  k_tri2_t1b<<<cb, kScanCols * kScanSegs, 0, st>>>(g, tab, E, carry, L);
+  k_tri2_t2b<<<cb, kScanCols * kScanSegs, 0, st>>>(g, modes, tab, B, carry, bcarry, Cc, L);
   k_tri2_t3<L><<<gb, 128, 0, st>>>(g, a, modes, tab, carry, bcarry, Cc);
   return cudaGetLastError();
 }
@@ -799,11 +785,11 @@ static cudaError_t tri_chunked_L(const Geom& g, T* a, const Mode<T>* modes, cons
   double* Cc = bcarry + (int64_t)C * ncols;
   const int64_t work = ncols * C;
   const dim3 gb((unsigned)((work + 127) / 128), (unsigned)g.nb);
-  const dim3 cb((unsigned)((ncols + 127) / 128), (unsigned)g.nb);
+  const dim3 cb((unsigned)((ncols + kScanCols - 1) / kScanCols), (unsigned)g.nb);
   k_tri_t1<T, L, GEN, GT><<<gb, 128, 0, st>>>(g, a, modes, E, G);
-  k_tri_t1b<<<cb, 128, 0, st>>>(g, md64, E, carry, L);
+  k_tri_t1b<<<cb, kScanCols * kScanSegs, 0, st>>>(g, md64, E, carry, L);
   k_tri_t2<T, L, GEN, GT><<<gb, 128, 0, st>>>(g, a, modes, carry, B, G);
-  k_tri_t2b<<<cb, 128, 0, st>>>(g, md64, B, bcarry, Cc, L);
+  k_tri_t2b<<<cb, kScanCols * kScanSegs, 0, st>>>(g, md64, B, bcarry, Cc, L);
   k_tri_t3<T, L><<<gb, 128, 0, st>>>(g, a, modes, md64, rpow, bcarry, Cc);
   return cudaGetLastError();
 }

@@ -45,11 +45,22 @@ def _blank(N, dim, lo=None, hi=None):
 
 # --- component kernels --------------------------------------------------------
 
-@pytest.mark.parametrize("N,axis", [((8, 8), 0), ((64, 64), 0), ((4096, 16), 0), ((32, 16), 0),
-                                    ((16, 32, 8), 0), ((16, 32, 8), 1), ((8, 1024, 8), 1), ((128, 64, 16), 1)])
-def test_dst1_matches_definition(N, axis):
+@pytest.mark.parametrize("radix", [4, 8])
+@pytest.mark.parametrize("N,axis", [((8, 8), 0), ((64, 64), 0), ((4096, 16), 0), ((32, 16), 0), ((2048, 8), 0),
+                                    ((16, 32, 8), 0), ((16, 32, 8), 1), ((8, 1024, 8), 1), ((128, 64, 16), 1),
+                                    ((256, 512, 8), 1)])
+def test_dst1_matches_definition(N, axis, radix):
+    """DST-I along x and y against the definition (scipy), radix-4 and
+    radix-8 stages (the tuner's choice); the sizes cover each stage plan:
+    log2(N/2) = 0, 1, 2 mod 3 (radix-8: a radix-8 run, a radix-2 or a radix-4
+    stage first) and even and odd (radix-4: a radix-2 stage first)."""
     dim = len(N)
-    p = _plan(_blank(N, dim))
+    L = ahoc.lib()
+    L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N[0], ahoc.AHOC_FP64, radix)
+    try:
+        p = _plan(_blank(N, dim))
+    finally:
+        L.ahoc_tune_set(ahoc.AHOC_TUNE_DST_RADIX, dim, N[0], ahoc.AHOC_FP64, 0)
     rng = np.random.default_rng(7)
     shape = tuple(n - 1 for n in reversed(N))
     x = rng.normal(size=shape)
