@@ -122,10 +122,13 @@ typedef struct {
                              solution's Q interpolated (cubic, along the faces) to the next
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
-                             every axis keeps >= 128 intervals, at most 3 levels; off in an
-                             AHOC_MIXED plan, where it only starts the first correction
-                             solve); 0: off.  In an AHOC_MIXED plan the coarse levels are
-                             mixed-precision solves too                                      */
+                             every axis keeps >= 128 intervals, at most 3 levels, and use a
+                             coarse level for a problem only where it resolves the data: its
+                             Schur right-hand side, interpolated to the finer faces, within
+                             10% of the finer one's, which costs nothing more as the coarse
+                             solve starts from it; off in an AHOC_MIXED plan, where it only
+                             starts the first correction solve); 0: off.  In an AHOC_MIXED
+                             plan the coarse levels are mixed-precision solves too           */
   double coarse_tol;      /* [0] relative Schur residual the coarse levels of the nested guess
                              solve to (never tighter than the solve's tol).  The prolonged
                              guess is only as good as the coarse grid's discretisation and
@@ -230,7 +233,7 @@ typedef struct {
   int64_t launches;       /* kernels this library launched during the last solve                */
   double kernel_ms[AHOC_NK];      /* with opts.timing: summed device time per kernel class      */
   int64_t kernel_launches[AHOC_NK];
-  int levels;             /* coarse levels used for the initial guess                           */
+  int levels;             /* coarse levels this problem's initial guess used                    */
   int coarse_iters;       /* GMRES iterations summed over the coarse levels                     */
   double kernel_ms_top[AHOC_NK];      /* as kernel_ms, this grid's launches only (no coarse)  */
   int64_t kernel_launches_top[AHOC_NK];
