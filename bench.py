@@ -53,10 +53,10 @@ SERVE_LOAD = 0.6
 # (profiles/k_dst_fp64_3d512x256x256.md): at 512 x 256 x 256 the x-DST moves
 # 500.6 MB (`<2,0>`, M(V/alpha) load), 761.1 MB (`<0,1>`, 1/alpha store) and
 # 473.1 MB (`<0,0>`) per launch; 1023^3 / (511 x 255 x 255) = 32.22 times the
-# points; weighted by the finest grid's 25 / 25 / 8 launches of a solve
+# points; weighted by the finest grid's 19 / 19 / 8 launches of a solve
 # (profiles/launches_fourier3d_k32_1024_fp64.md)
 PROFILED_TRAFFIC = {("fourier3d_k32", (1024, 1024, 1024), "dst_x"):
-                    32.22e6 * (25 * 500.6 + 25 * 761.1 + 8 * 473.1) / 58}
+                    32.22e6 * (19 * 500.6 + 19 * 761.1 + 8 * 473.1) / 46}
 
 
 def _peaks():
