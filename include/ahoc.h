@@ -122,7 +122,8 @@ typedef struct {
                              solution's Q interpolated (cubic, along the faces) to the next
                              finer grid as GMRES's initial guess (the coarse-grid
                              interpolated guess of Sec. 4.1).  -1: automatic (halve while
-                             every axis keeps >= 128 intervals, at most 3 levels, and use a
+                             every axis keeps >= 512 intervals in 2D, >= 128 in 3D, at most
+                             3 levels, and use a
                              coarse level for a problem only where it resolves the data: its
                              Schur right-hand side, interpolated to the finer faces, within
                              10% of the finer one's, which costs nothing more as the coarse

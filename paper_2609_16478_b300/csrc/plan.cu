@@ -584,14 +584,19 @@ Layout make_layout(const Geom& g, const Opts& o) {
 }
 
 // Nested initial guess: coarse grids halve every axis.  Automatic depth:
-// coarsen while every axis keeps at least kMinCoarse intervals, at most
-// kAutoLevels times (deeper levels cost more in fixed latency than they save).
-constexpr int kMinCoarse = 128;
+// coarsen while every axis keeps at least kMinCoarse intervals (2D 512, 3D
+// 128), at most kAutoLevels times: deeper levels cost more in fixed latency
+// than they save.  Measured on B300 (FP64, ms per solve, levels 0/1/2/3):
+// 2D 512^2 6.1/7.5/9.6/11.6, 1024^2 9.5/8.9/10.3/12.3, 2048^2
+// 22.0/15.1/14.1/15.5, 4096^2 70.6/37.5/32.6/29.6; 3D 128^3 26.0/31.4/38.9,
+// 256^3 101/84/89/97, 512^3 698/440/423/429.
+constexpr int kMinCoarse2 = 512, kMinCoarse3 = 128;
 constexpr int kAutoLevels = 3;
 int coarse_levels(const Geom& g, int requested) {
   int maxl = 0;
   int n = 1 << 30;
   for (int a = 0; a < g.dim; ++a) n = (g.N[a] < n) ? g.N[a] : n;
+  const int kMinCoarse = g.dim == 2 ? kMinCoarse2 : kMinCoarse3;
   while ((n >> (maxl + 1)) >= kMinCoarse && (n >> (maxl + 1)) >= 8) ++maxl;
   if (requested < 0) return maxl < kAutoLevels ? maxl : kAutoLevels;
   // an explicit request may go down to 8 intervals per axis
