@@ -424,3 +424,37 @@ def test_examples2_3_tables_n32(col, name):
     sol = coupled.solve_direct(coupled.assemble(d), d)
     err = np.max(np.abs(sol.U - d["u_exact"]))
     assert abs(err / float(row[col]) - 1) < 0.005, (err, row[col])
+
+
+@pytest.mark.parametrize("name", ["sincos2d", "navier2d"])
+def test_schur_rhs_scale_between_grids(name):
+    """The Schur right-hand side b = F2 - A21 A11^-1 F1 (Lemma 1) on a clamped
+    face carries the 1/h of the one-sided trace (the outward g_N over h), so
+    at coinciding face points the fine grid's b is twice the coarse grid's for
+    smooth data; on a Navier face b is the data itself and does not scale.
+    The agreement improves with refinement."""
+    prob = inputs.config_problem(name)
+
+    def face_b(N):
+        d = inputs.sample(prob, [N, N])
+        s = coupled.assemble(d)
+        b = coupled.Blocks(s).schur_rhs()
+        o = s.grid.face_offsets()
+        return [b[o[f]:o[f + 1]] for f in range(4)]
+
+    prev = None
+    for Nc in (32, 64):
+        C, F = face_b(Nc), face_b(2 * Nc)
+        worst = 0.0
+        for f in range(4):
+            fine = F[f][1::2]                  # fine index 2i is coarse index i
+            k = 1.0 if f in prob.navier else 2.0
+            rel = np.linalg.norm(fine - k * C[f]) / np.linalg.norm(fine)
+            assert rel < 1e-3, (Nc, f, rel)
+            # the other factor is far off: b does (or does not) scale
+            k_wrong = 2.0 if k == 1.0 else 1.0
+            assert np.linalg.norm(fine - k_wrong * C[f]) / np.linalg.norm(fine) > 0.4
+            worst = max(worst, rel)
+        if prev is not None:
+            assert worst < prev / 2, (worst, prev)
+        prev = worst
