@@ -179,7 +179,8 @@ _SAMPLES = {}
 
 def cpu_oracle_sample(name: str, N_cpu: int):
     """Time the CPU oracle (assembly + SuperLU) on workload `name` at N_cpu
-    intervals per axis; returns (DOF/s, seconds, err against the exact u).
+    intervals per axis; returns (DOF/s, seconds, err against the exact u,
+    assembly seconds, SuperLU factor-and-solve seconds).
 
     The synthetic inputs are generated once, outside the timed region."""
     import numpy as np
@@ -193,10 +194,12 @@ def cpu_oracle_sample(name: str, N_cpu: int):
         _SAMPLES[key] = inputs.sample(prob, [N_cpu] * prob.dim)
     d = _SAMPLES[key]
     t0 = time.perf_counter()
-    sol = coupled.solve_direct(coupled.assemble(d), d)
+    sys_ = coupled.assemble(d)
+    t1 = time.perf_counter()
+    sol = coupled.solve_direct(sys_, d)
     dt = time.perf_counter() - t0
     err = float(np.max(np.abs(sol.U - d["u_exact"])))
-    return (N_cpu - 1) ** prob.dim / dt, dt, err
+    return (N_cpu - 1) ** prob.dim / dt, dt, err, t1 - t0, dt - (t1 - t0)
 
 
 def _cores():
@@ -215,10 +218,12 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         cpu_oracle_sample(name, N_cpu)
     t0 = time.perf_counter()
-    errs = []
+    errs, t_asm, t_lu = [], 0.0, 0.0
     for _ in range(args.steps):
-        _, _, e = cpu_oracle_sample(name, N_cpu)
+        _, _, e, ta, tl = cpu_oracle_sample(name, N_cpu)
         errs.append(e)
+        t_asm += ta
+        t_lu += tl
     dt = time.perf_counter() - t0
     value = args.steps * (N_cpu - 1) ** dim / dt
     sample = ("direct solve of the assembled coupled system (SuperLU, single-threaded; %d host cores visible) of "
@@ -231,7 +236,8 @@ def run_reference(args, rank, world):
                    "dim": dim, "N": N_cpu, "err_inf_vs_exact": max(errs),
                    "note": "a timing sample: the high-wavenumber u is not resolved at this N"
                    if name == "fourier3d_k32" else ""},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "split_s": {"assembly": t_asm, "superlu": t_lu}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -629,15 +635,18 @@ def run_ours(args, rank, world, local):
         variants["serving"] = serving_variant(args, dev)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        reps, tot = 0, 0.0
+        reps, tot, t_asm, t_lu = 0, 0.0, 0.0, 0.0
         while reps < 1 or (tot < 10.0 and reps < 5):  # about 10-30 s of CPU work
-            v, dt, _ = cpu_oracle_sample(name, args.cpu_n)
+            v, dt, _, ta, tl = cpu_oracle_sample(name, args.cpu_n)
             reps += 1
             tot += dt
+            t_asm += ta
+            t_lu += tl
         v = reps * (args.cpu_n - 1) ** dim / tot
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d direct solves (assembly + SuperLU) of the same workload at N=%d, %.1f s in all; "
-                         "single-threaded, %d host cores visible" % (reps, args.cpu_n, tot, _cores())}
+                         "single-threaded, %d host cores visible" % (reps, args.cpu_n, tot, _cores()),
+               "split_s": {"assembly": t_asm, "superlu": t_lu}}
     f_numel = 1
     for n in N:
         f_numel *= n + 1
