@@ -48,7 +48,7 @@ typedef enum {
   AHOC_ENOCONV = 4,       /* GMRES reached max_iters; outputs hold the best iterate */
   AHOC_ENUMERIC = 5,      /* NaN or Inf met in a residual norm */
   AHOC_ETIMEOUT = 6,      /* reserved: a bounded device wait ran out */
-  AHOC_EUNSUPPORTED = 7,  /* valid request outside what this build supports */
+  AHOC_EUNSUPPORTED = 7,  /* valid request outside what the library supports */
   AHOC_EINTERNAL = 8
 } ahoc_status;
 

@@ -1340,7 +1340,7 @@ const char* ahoc_status_string(ahoc_status s) {
     case AHOC_ENOCONV: return "AHOC_ENOCONV: GMRES did not reach the tolerance";
     case AHOC_ENUMERIC: return "AHOC_ENUMERIC: NaN or Inf in a residual";
     case AHOC_ETIMEOUT: return "AHOC_ETIMEOUT: device wait timed out";
-    case AHOC_EUNSUPPORTED: return "AHOC_EUNSUPPORTED: not supported by this build";
+    case AHOC_EUNSUPPORTED: return "AHOC_EUNSUPPORTED: not supported by the library";
     case AHOC_EINTERNAL: return "AHOC_EINTERNAL: internal error";
   }
   return "unknown ahoc_status";
