@@ -102,3 +102,43 @@ def test_every_bdata_field_reaches_each_problem():
     create = create[:create.index("s = plan_load(")]
     for f in fields:
         assert "bb.%s = bd->%s" % (f, f) in create, f
+
+
+def test_struct_layouts_and_constants_match_header(tmp_path):
+    """The binding's ctypes mirrors of ahoc_bdata, ahoc_opts and ahoc_info
+    have the header's field offsets and sizes, and its constants the
+    header's values: a C program compiled against include/ahoc.h prints
+    them (a field missing from the header fails to compile)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("ahoc_bdata", ahoc.ahoc_bdata), ("ahoc_opts", ahoc.ahoc_opts), ("ahoc_info", ahoc.ahoc_info)]
+    consts = [n for n in dir(ahoc) if re.fullmatch(r"AHOC_(E[A-Z]+|OK|FP64|MIXED|TUNE_[A-Z_]+)", n)]
+    assert {"AHOC_OK", "AHOC_EINTERNAL", "AHOC_MIXED", "AHOC_TUNE_DST_RADIX"} <= set(consts)
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ahoc.h"', "int main(void) {"]
+    for sname, cls in structs:
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (sname, sname))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu %%zu\\n", offsetof(%s, %s), sizeof(((%s*)0)->%s));'
+                         % (sname, fname, sname, fname, sname, fname))
+    for n in consts:
+        lines.append('  printf("%s %%d\\n", (int)%s);' % (n, n))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = dict(l.split(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for sname, cls in structs:
+        assert int(out[sname].split()[1]) == C.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            off, size = map(int, out["%s.%s" % (sname, fname)].split())
+            desc = getattr(cls, fname)
+            assert (off, size) == (desc.offset, desc.size), (sname, fname, off, size, desc.offset, desc.size)
+    for n in consts:
+        assert int(out[n]) == getattr(ahoc, n), n
