@@ -168,6 +168,23 @@ def max_over_ranks(values, world, device):
     return [float(x) for x in t]
 
 
+_HOST_GROUP = None  # gloo group of all ranks for the host barriers (None: the default group is gloo)
+
+
+def host_barrier(world: int, timeout_s: float) -> None:
+    """Bounded barrier of all ranks on the host.  A rank that raised, exited
+    or never arrives makes the others raise within `timeout_s` (the error
+    names the missing ranks) instead of waiting for the process group's own
+    timeout.  The caller synchronises its device first."""
+    if world <= 1:
+        return
+    import datetime
+
+    import torch.distributed as dist
+
+    dist.monitored_barrier(group=_HOST_GROUP, timeout=datetime.timedelta(seconds=timeout_s), wait_all_ranks=True)
+
+
 def whole_job_rate(world: int, steps: int, units_per_step: float, ms: float) -> float:
     """Units all ranks processed per second: each rank runs `steps` steps of
     `units_per_step` units, the job takes the slowest rank's `ms`."""
@@ -565,7 +582,8 @@ def run_ours(args, rank, world, local):
 
     def barrier():
         if world > 1:
-            torch.distributed.barrier()
+            torch.cuda.synchronize()
+            host_barrier(world, args.barrier_timeout)
 
     # device-resident timed region: inputs in HBM, exactly `steps` solves
     with ClockSampler(local) as clk:
@@ -714,6 +732,8 @@ def main():
                     help="paper: the paper's printed workloads at their largest sizes, one JSON line each; "
                          "serving: the serving workload alone")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache (default: the shipped B300 choices)")
+    ap.add_argument("--barrier-timeout", type=float, default=600.0,
+                    help="seconds a rank waits at a host barrier for the others before it raises (N > 1)")
     ap.add_argument("--dst-radix", type=int, default=0, choices=[0, 4, 8],
                     help="FFT radix of the line DSTs for every shape and precision (0: built-in)")
     ap.add_argument("--dst-cta", type=int, default=0, choices=[0, 128, 256, 512, 1024],
@@ -755,8 +775,10 @@ def main():
         import torch
         import torch.distributed as dist
 
+        global _HOST_GROUP
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+        _HOST_GROUP = dist.new_group(backend="gloo")
     run_ours(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
