@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ahoc.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -19,6 +21,15 @@ using namespace ahoc;
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range over one phase of a solve, for profilers (ncu --nvtx
+// --nvtx-include, nsys); with no tool attached a push or pop returns at once
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+};
 
 ahoc_status fail(ahoc_status s, const std::string& msg) {
   g_err = msg;
@@ -1108,6 +1119,7 @@ ahoc_status precond_apply(ahoc_plan* p, const double* in, double* out) {
 }
 
 ahoc_status schur_rhs_dev(ahoc_plan* p, const double* f, double* b) {
+  Phase ph("ahoc schur rhs");
   const Geom& g = p->g;
   if (p->o.tri) {
     CKS(solve_tri(p, nullptr, f, true));
@@ -1841,6 +1853,7 @@ extern "C" {
 ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const double* lo, const double* hi,
                              const double* alpha, const ahoc_bdata* bd, const ahoc_opts* opts, void* stream) {
   std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+  Phase ph("ahoc plan create");
   if (!out) return fail(AHOC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!alpha && !(opts && opts->triharmonic)) return fail(AHOC_EINVAL, "alpha is NULL");
@@ -1879,6 +1892,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
 
 ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_bdata* bd) {
   std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+  Phase ph("ahoc plan load");
   if (!p || (!alpha && !p->o.tri)) return fail(AHOC_EINVAL, "NULL argument");
   if (b < 0 || b >= p->g.nb) return fail(AHOC_EINVAL, "problem index out of range");
   p->have_last = false;
@@ -2058,6 +2072,7 @@ ahoc_status arnoldi_step(ahoc_plan* p, int j, int64_t ld, const double* src) {
 // block start, captured on first use and replayed, or plain launches.
 // Returns after the host copy is complete.
 ahoc_status arnoldi_block(ahoc_plan* p, int j0, int K, int64_t ld) {
+  Phase ph("ahoc arnoldi block");
   const int nb = p->g.nb;
   const int slot = j0 / kArnoldiBlock;
   cudaStream_t user = p->st;
@@ -2147,6 +2162,7 @@ ahoc_status arnoldi_block(ahoc_plan* p, int j0, int K, int64_t ld) {
 ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta0, double* X, bool guess,
                   const std::vector<double>& tol, const std::vector<int>& maxit, std::vector<int> live,
                   std::vector<ProbStat>& go) {
+  Phase ph("ahoc gmres");
   const Geom& g = p->g;
   const int nb = g.nb;
   const int64_t n = g.ngamma;
@@ -2309,6 +2325,7 @@ constexpr double kNestAgree = 0.1;
 // guess (X0 = 0 for those that did not).
 ahoc_status coarse_guess(ahoc_plan* p, const double* f, const std::vector<int>& live, double tol, double* X0,
                          const double* bfine, bool& used) {
+  Phase ph("ahoc nested guess");
   const Geom& g = p->g;
   const int nb = g.nb;
   ahoc_plan* c = p->coarse;
@@ -2415,6 +2432,7 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
     s.ms_mv += go[i].ms_mv;
   }
   if (!u) return AHOC_OK;  // a coarse level of the nested guess: Q only
+  Phase ph("ahoc recovery");
   CKS(set_act(p, p->part));
   if (p->bank_valid) {
     // U = U(data) + U(Q), U(Q) the inverse DST of the combined U-hat (linear
@@ -2461,6 +2479,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
   std::vector<double> bref(nb, 0.0), bn;
   const bool first64 = p->o.first64 && !p->o.varb;
   for (int step = 0; step <= kMaxRefine && any(live); ++step) {
+    Phase ph("ahoc refinement step");
     CKS(set_act(p, live));
     if (step == 0 && first64) {
       // x = 0: the correction system is the whole system; its Schur
@@ -2594,6 +2613,7 @@ ahoc_status solve_mixed(ahoc_plan* p, const double* f, double* u, double tol) {
 // One solve of the problems in p->part (statistics in p->ps); u == NULL: Q
 // only (the nested guess's coarse levels), V and U are not recovered.
 ahoc_status solve_internal(ahoc_plan* p, const double* f, double* u, double tol) {
+  Phase ph(p->o.prec == AHOC_MIXED ? "ahoc solve (mixed)" : "ahoc solve (fp64)");
   p->have_last = false;
   CK(cudaStreamSynchronize(p->st));
   CKS(harvest(p));
