@@ -297,6 +297,22 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
  * fails).  Returns when u_host is written; otherwise as ahoc_solve. */
 ahoc_status ahoc_solve_host(ahoc_plan* p, const double* f_host, double* u_host, double tol, ahoc_info* info);
 
+/* ahoc_solve with the caller's initial Q (the boundary values of v on the
+ * face interiors, the unknowns of S_h Q = b, Lemma 1): GMRES starts from q0
+ * instead of zero or the nested coarse-grid guess (Algorithm 1 with a warm
+ * start, as Sec. 4.1 starts from an interpolated coarse solution); the
+ * converged Q of an earlier solve of nearby data (ahoc_last_qv) is the
+ * typical q0.  The result is the same discrete solution to within tol.
+ *   q0  device, one face array (n_gamma doubles, the face order of ahoc_bdata)
+ *       per problem of the plan, back to back; read for the problems taking
+ *       part.  A problem whose Schur right-hand side is zero ignores it
+ *       (its Q is 0).  A NaN or Inf in a problem's q0 fails that problem alone
+ *       (AHOC_ENUMERIC, as ahoc_solve).
+ * FP64 plans only (a mixed plan's first refinement step solves for the whole
+ * solution: AHOC_EUNSUPPORTED).  Otherwise as ahoc_solve. */
+ahoc_status ahoc_solve_from(ahoc_plan* p, const double* f, const double* q0, double* u, double tol,
+                            ahoc_info* info);
+
 /* y = S_h q = R(q) - R(0) (Lemma 1; Algorithm 1, SchurMatVec), the
  * homogeneous part of the boundary residual: V(q) by the v-equation with
  * zero f and edge data, U(V) by the u-equation with zero g_D, then

@@ -24,8 +24,8 @@ AHOC_FP64, AHOC_MIXED = 0, 1
 AHOC_TUNE_TRI_CHUNK, AHOC_TUNE_DST_THREADS, AHOC_TUNE_DST_RADIX = 0, 1, 2
 
 # every entry point declared in include/ahoc.h
-SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_matvec", "ahoc_schur_rhs",
-           "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
+SYMBOLS = ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_solve_from",
+           "ahoc_matvec", "ahoc_schur_rhs", "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_status_string",
            "ahoc_last_error", "ahoc_n_gamma", "ahoc_poisson_noalloc", "ahoc_plan_load", "ahoc_set_active",
            "ahoc_batch", "ahoc_tune_set", "ahoc_tune_get")
 
@@ -82,6 +82,7 @@ def lib():
     L.ahoc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, i64p, dp, dp, C.c_void_p,
                                    C.POINTER(ahoc_bdata), C.POINTER(ahoc_opts), C.c_void_p]
     L.ahoc_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
+    L.ahoc_solve_from.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
     L.ahoc_solve_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ahoc_info)]
     L.ahoc_matvec.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     L.ahoc_schur_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -105,9 +106,9 @@ def lib():
     L.ahoc_tune_set.restype = C.c_int
     L.ahoc_tune_get.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int]
     L.ahoc_tune_get.restype = C.c_int
-    for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_matvec", "ahoc_schur_rhs",
-                 "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy", "ahoc_plan_load",
-                 "ahoc_set_active"):
+    for name in ("ahoc_workspace_bytes", "ahoc_plan_create", "ahoc_solve", "ahoc_solve_host", "ahoc_solve_from",
+                 "ahoc_matvec", "ahoc_schur_rhs", "ahoc_last_qv", "ahoc_dst1", "ahoc_poisson", "ahoc_plan_destroy",
+                 "ahoc_plan_load", "ahoc_set_active"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -265,18 +266,25 @@ class Plan:
 
     # -- Algorithm 1 ---------------------------------------------------------
     def solve(self, f: torch.Tensor, u: Optional[torch.Tensor] = None, tol: float = 1e-12,
-              check: bool = True):
+              check: bool = True, q0: Optional[torch.Tensor] = None):
         """u for f (one grid per problem of the plan); returns (u, info) with
         info a dict, or for a batched plan a list of dicts (None for problems
-        not taking part)."""
+        not taking part).  q0: GMRES's initial Q, one face array per problem
+        (``ahoc_solve_from``; FP64 plans)."""
         B = self.batch
         if u is None:
             u = torch.empty(B * self.nfull, dtype=torch.float64, device=self.device)
         infos = (ahoc_info * B)()
-        st = lib().ahoc_solve(self._h, _ptr(f, B * self.nfull, "f"), _ptr(u, B * self.nfull, "u"), float(tol),
-                              infos)
+        if q0 is None:
+            st = lib().ahoc_solve(self._h, _ptr(f, B * self.nfull, "f"), _ptr(u, B * self.nfull, "u"), float(tol),
+                                  infos)
+            name = "ahoc_solve"
+        else:
+            st = lib().ahoc_solve_from(self._h, _ptr(f, B * self.nfull, "f"), _ptr(q0, B * self.ngamma, "q0"),
+                                       _ptr(u, B * self.nfull, "u"), float(tol), infos)
+            name = "ahoc_solve_from"
         if check:
-            _check(st, "ahoc_solve")
+            _check(st, name)
         out = [_info_dict(infos[b], infos[b].status) if self.active[b] else None for b in range(B)]
         return u, (out[0] if B == 1 else out)
 

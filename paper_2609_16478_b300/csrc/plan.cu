@@ -683,6 +683,7 @@ struct ahoc_plan {
   int nbank = 0;
   bool bank_valid = false, v_lazy = false;
   bool rhs_ready = false;  // a coarse level's b was computed by the finer level's resolution check
+  const double* q0 = nullptr;  // the caller's initial Q for the current ahoc_solve_from call
   // mixed precision
   float *F1 = nullptr, *F2 = nullptr, *Ru = nullptr, *Rv = nullptr, *twf[3] = {nullptr, nullptr, nullptr},
         *snf[3] = {nullptr, nullptr, nullptr}, *trif = nullptr;
@@ -2178,6 +2179,9 @@ ahoc_status gmres(ahoc_plan* p, const double* b, const std::vector<double>& beta
   double* ux0 = p->nbank ? p->bank + (int64_t)p->nbank * nb * g.npad : nullptr;
   p->bank_valid = p->nbank > 0;
   if (guess) {
+    // the U-hat slot of a problem GMRES leaves alone (b = 0: Q = 0) must hold
+    // zero for the recovery, as after a cold start
+    if (ux0) CK(cudaMemsetAsync(ux0, 0, (size_t)nb * g.npad * sizeof(double), p->st));
     CKS(set_act(p, live));
     CKS(matvec_dev(p, X, p->tmp, ux0));
     RUN(AHOC_K_KRYLOV, launch_axpby(p->r, b, 1.0, 0.0, n, p->st, nb, nullptr, g.act));
@@ -2419,7 +2423,15 @@ ahoc_status solve_fp64(ahoc_plan* p, const double* f, double* u, double tol) {
   bool guess = false;
   bool any_rhs = false;
   for (int i = 0; i < nb; ++i) any_rhs = any_rhs || (live[i] && beta0[i] > 0);
-  if (any_rhs && p->coarse) CKS(coarse_guess(p, f, live, tol, p->Q, p->b, guess));
+  if (p->q0) {  // the caller's initial Q (ahoc_solve_from) in place of the nested guess
+    CK(cudaMemcpyAsync(p->Q, p->q0, (size_t)nb * g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    for (int i = 0; i < nb; ++i)  // b = 0: Q = 0 exactly (GMRES leaves such a problem's iterate alone)
+      if (!(live[i] && beta0[i] > 0))
+        CK(cudaMemsetAsync(p->Q + (int64_t)i * g.ngamma, 0, g.ngamma * sizeof(double), p->st));
+    guess = true;
+  } else if (any_rhs && p->coarse) {
+    CKS(coarse_guess(p, f, live, tol, p->Q, p->b, guess));
+  }
   std::vector<ProbStat> go(nb);
   CKS(gmres(p, p->b, beta0, p->Q, guess, std::vector<double>(nb, tol), std::vector<int>(nb, p->o.max_iters), live,
             go));
@@ -2680,6 +2692,19 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
                     "(info[b].status), the others were solved");
   if (st != AHOC_OK) return fail(st, "GMRES reached max_iters (or refinement did not converge)");
   return AHOC_OK;
+}
+
+// ahoc_solve with the caller's initial Q: GMRES starts from q0 (FP64 plans).
+ahoc_status ahoc_solve_from(ahoc_plan* p, const double* f, const double* q0, double* u, double tol,
+                            ahoc_info* info) {
+  if (!p || !f || !q0 || !u) return fail(AHOC_EINVAL, "NULL argument");
+  if (p->o.prec != AHOC_FP64)
+    return fail(AHOC_EUNSUPPORTED,
+                "an initial Q is taken by FP64 plans (a mixed plan's first step solves for all of u)");
+  p->q0 = q0;
+  const ahoc_status s = ahoc_solve(p, f, u, tol, info);
+  p->q0 = nullptr;
+  return s;
 }
 
 // ahoc_solve with host arrays: f of every problem taking part is copied to a

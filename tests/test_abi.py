@@ -77,6 +77,7 @@ def test_plan_create_rejects_before_allocating():
     # NULL plan to the compute calls
     assert L.ahoc_matvec(None, None, None) == ahoc.AHOC_EINVAL
     assert L.ahoc_solve(None, None, None, C.c_double(1e-12), None) == ahoc.AHOC_EINVAL
+    assert L.ahoc_solve_from(None, None, None, None, C.c_double(1e-12), None) == ahoc.AHOC_EINVAL
     assert L.ahoc_plan_destroy(None) == ahoc.AHOC_OK
     assert L.ahoc_n_gamma(None) == -1
 
