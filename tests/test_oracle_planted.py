@@ -140,3 +140,33 @@ def test_planted_dst_normalisation_is_caught():
     bad = _copy("dst", [("np.outer(j, j) / (n + 1)", "np.outer(j, j) / n")])
     assert np.allclose(2 * dst.dst1(x), scipy.fft.dst(x, type=1, axis=-1), rtol=1e-13, atol=1e-12)
     assert not np.allclose(2 * bad.dst1(x), scipy.fft.dst(x, type=1, axis=-1), rtol=1e-3)
+
+
+def _tri_error(tmod, N=(16, 8)):
+    """A degree-5 triharmonic solution with nonzero data of every kind, two
+    clamped faces, on an anisotropic grid: reproduced to rounding."""
+    d = inputs.sample_triharmonic(inputs.triharmonic_problem("tripoly2d"), list(N))
+    sol = tmod.solve_direct(tmod.assemble(d), d)
+    return float(np.max(np.abs(sol.U - d["u_exact"])) / np.max(np.abs(d["u_exact"])))
+
+
+PLANTED_TRIHARMONIC = {
+    "u_s with the outward sign": [("ws * (-gN[q])", "ws * gN[q]")],
+    "u_ss term dropped": [(" + wss * gNN[q]", "")],
+    "tangential part of Lap^2 u dropped": [(" + wss * gNN[q] + lw[q])", " + wss * gNN[q])")],
+    "one-sided weights scaled by h^-3": [("wU = [float(cm) / ha ** 4 for cm in cw]", "wU = [float(cm) / ha ** 3 for cm in cw]")],
+    "face V data dropped from M V": [("        np.add.at(F, ru[face], c * vb[jf[face]])\n", "")],
+    "U_0 weight without c_1": [("c0 = -sum(c14)", "c0 = -sum(c14[1:])")],
+    "edge and corner W data with the wrong sign": [("np.add.at(F, rw[edge], -c * wb[jf[edge]])",
+                                                    "np.add.at(F, rw[edge], c * wb[jf[edge]])")],
+}
+
+
+def test_triharmonic_control_passes():
+    from oracle import triharmonic
+    assert _tri_error(triharmonic) < 1e-11
+
+
+@pytest.mark.parametrize("what", sorted(PLANTED_TRIHARMONIC))
+def test_planted_triharmonic_mistake_is_caught(what):
+    assert _tri_error(_copy("triharmonic", PLANTED_TRIHARMONIC[what])) > 1e-6, what
