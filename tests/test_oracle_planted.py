@@ -170,3 +170,34 @@ def test_triharmonic_control_passes():
 @pytest.mark.parametrize("what", sorted(PLANTED_TRIHARMONIC))
 def test_planted_triharmonic_mistake_is_caught(what):
     assert _tri_error(_copy("triharmonic", PLANTED_TRIHARMONIC[what])) > 1e-6, what
+
+
+def _residual_of_solution(rmod, name="sincos2d", N=(16, 24)):
+    """The slicing residual of the assembled system's direct solution (which
+    the pins above fix): zero to rounding, relative to each row's terms."""
+    d = inputs.sample(inputs.config_problem(name), list(N))
+    sol = coupled.solve_direct(coupled.assemble(d), d)
+    ru, rv, rq = rmod.coupled_residual(sol.U, sol.V, d)
+    h2 = min((d["hi"][a] - d["lo"][a]) / d["N"][a] for a in range(2)) ** 2
+    scale = max(np.max(np.abs(sol.U)) / h2, np.max(np.abs(sol.V)) / h2, np.max(np.abs(d["f"])))
+    return max(np.max(np.abs(ru)), np.max(np.abs(rv)), np.max(np.abs(rq))) / scale
+
+
+PLANTED_RESIDUAL = {
+    "M f with the wrong sign": [("r_v = -apply_stencil(V, L) - apply_stencil(f, Mw)",
+                                 "r_v = -apply_stencil(V, L) + apply_stencil(f, Mw)")],
+    "U_3 read from layer 2": [("w3 * layer(U, a, side, 3)", "w3 * layer(U, a, side, 2)")],
+    "tangential Laplacian of g_D dropped": [("(dnn + lapt[off:off + n])", "(dnn)")],
+    "V / alpha as V": [("apply_stencil(V / alpha, Mw)", "apply_stencil(V, Mw)")],
+    "face offset not advanced": [("            off += n\n", "")],
+}
+
+
+def test_residual_control_passes():
+    from oracle import residual
+    assert _residual_of_solution(residual) < 1e-12
+
+
+@pytest.mark.parametrize("what", sorted(PLANTED_RESIDUAL))
+def test_planted_residual_mistake_is_caught(what):
+    assert _residual_of_solution(_copy("residual", PLANTED_RESIDUAL[what])) > 1e-8, what
