@@ -304,8 +304,9 @@ ahoc_status ahoc_solve_host(ahoc_plan* p, const double* f_host, double* u_host, 
  * converged Q of an earlier solve of nearby data (ahoc_last_qv) is the
  * typical q0.  The result is the same discrete solution to within tol.
  *   q0  device, one face array (n_gamma doubles, the face order of ahoc_bdata)
- *       per problem of the plan, back to back; read for the problems taking
- *       part.  A problem whose Schur right-hand side is zero ignores it
+ *       per problem of the plan, back to back (all of it is read; the
+ *       entries of problems not taking part are not used).  A problem whose
+ *       Schur right-hand side is zero ignores it
  *       (its Q is 0).  A NaN or Inf in a problem's q0 fails that problem alone
  *       (AHOC_ENUMERIC, as ahoc_solve).
  * FP64 plans only (a mixed plan's first refinement step solves for the whole
