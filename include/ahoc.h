@@ -23,7 +23,9 @@
  *           remaining axes keep their order, lowest axis fastest.  Their
  *           length is n_gamma = sum over faces of prod_{b != a} (N[b] - 1).
  * Memory    every array pointer is DEVICE memory owned by the caller unless
- *           stated otherwise; the library never frees caller memory.
+ *           stated otherwise; the library never frees caller memory.  A
+ *           device array of doubles must be 8-byte aligned (AHOC_EINVAL
+ *           otherwise, before any launch).
  * Streams   all work is enqueued on the plan's CUDA stream; calls return
  *           once the work is enqueued, except where stated.
  * Errors    every call returns an ahoc_status; no call aborts, throws or

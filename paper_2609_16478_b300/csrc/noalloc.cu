@@ -192,6 +192,9 @@ using namespace ahoc;
 extern "C" ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const double* lo, const double* hi,
                                             const double* rhs, double* w, void* stream) {
   if (!rhs || !w) return host_fail(AHOC_EINVAL, "NULL argument");
+  // 8-byte loads from a misaligned address would fault the context
+  if ((reinterpret_cast<uintptr_t>(rhs) | reinterpret_cast<uintptr_t>(w)) & 7)
+    return host_fail(AHOC_EINVAL, "device arrays of doubles must be 8-byte aligned");
   Geom g;
   ahoc_status s = host_make_geom(dim, N, lo, hi, &g);
   if (s != AHOC_OK) return s;

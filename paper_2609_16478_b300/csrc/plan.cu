@@ -36,6 +36,22 @@ ahoc_status fail(ahoc_status s, const std::string& msg) {
   return s;
 }
 
+// Device arrays of doubles must be 8-byte aligned: a kernel's 8-byte load
+// from a misaligned address would fault the context, so such a pointer is
+// refused on the host before any launch (NULL passes).
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
+
+bool bdata_misaligned(const ahoc_bdata* bd) {
+  if (!bd) return false;
+  const void* ps[] = {bd->g_D, bd->g_N, bd->lapt_gD, bd->v_edge, bd->g_L,
+                      bd->beta, bd->lap_gD, bd->bilap, bd->g_NN, bd->lapt_w};
+  for (const void* q : ps)
+    if (misaligned(q)) return true;
+  return false;
+}
+
+constexpr const char* kAlignMsg = "device arrays of doubles must be 8-byte aligned";
+
 // Serialises CUDA graph captures with the library's own synchronising entry
 // points (plan creation, loading, destruction: pinned allocations, frees,
 // stream synchronisations), which would otherwise invalidate a capture open
@@ -1858,6 +1874,7 @@ ahoc_status ahoc_plan_create(ahoc_plan** out, int dim, const int64_t* N, const d
   if (!out) return fail(AHOC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!alpha && !(opts && opts->triharmonic)) return fail(AHOC_EINVAL, "alpha is NULL");
+  if (misaligned(alpha) || bdata_misaligned(bd)) return fail(AHOC_EINVAL, kAlignMsg);
   Geom g;
   CKS(make_geom(dim, N, lo, hi, &g));
   Opts o;
@@ -1895,6 +1912,7 @@ ahoc_status ahoc_plan_load(ahoc_plan* p, int b, const double* alpha, const ahoc_
   std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   Phase ph("ahoc plan load");
   if (!p || (!alpha && !p->o.tri)) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(alpha) || bdata_misaligned(bd)) return fail(AHOC_EINVAL, kAlignMsg);
   if (b < 0 || b >= p->g.nb) return fail(AHOC_EINVAL, "problem index out of range");
   p->have_last = false;
   CKS(plan_load(p, b, alpha, bd));
@@ -1974,6 +1992,7 @@ ahoc_status ahoc_plan_destroy(ahoc_plan* p) {
 
 ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y) {
   if (!p || !q || !y) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(q) || misaligned(y)) return fail(AHOC_EINVAL, kAlignMsg);
   if (q == y) return fail(AHOC_EINVAL, "q and y may not alias");
   CKS(set_act(p, p->part));
   return matvec_dev(p, q, y);
@@ -1981,12 +2000,14 @@ ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y) {
 
 ahoc_status ahoc_schur_rhs(ahoc_plan* p, const double* f, double* b) {
   if (!p || !f || !b) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(f) || misaligned(b)) return fail(AHOC_EINVAL, kAlignMsg);
   CKS(set_act(p, p->part));
   return schur_rhs_dev(p, f, b);
 }
 
 ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, double scale) {
   if (!p || !in || !out) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(in) || misaligned(out)) return fail(AHOC_EINVAL, kAlignMsg);
   if (p->g.nb != 1) return fail(AHOC_EINVAL, "ahoc_dst1 takes a single-problem plan");
   if (axis < 0 || axis >= p->g.dim - 1) return fail(AHOC_EINVAL, "axis must be < dim - 1");
   CKS(set_act(p, p->part));
@@ -1999,6 +2020,7 @@ ahoc_status ahoc_dst1(ahoc_plan* p, int axis, const double* in, double* out, dou
 
 ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
   if (!p || !rhs || !w) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(rhs) || misaligned(w)) return fail(AHOC_EINVAL, kAlignMsg);
   if (p->g.nb != 1) return fail(AHOC_EINVAL, "ahoc_poisson takes a single-problem plan");
   CKS(set_act(p, p->part));
   RUN(AHOC_K_OTHER, launch_unpack(p->g, p->W1, rhs, p->st));
@@ -2009,6 +2031,7 @@ ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w) {
 
 ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v) {
   if (!p || !q) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(q) || misaligned(v)) return fail(AHOC_EINVAL, kAlignMsg);
   if (!p->have_last) return fail(AHOC_EINVAL, "no solve has completed on this plan");
   if (v && p->o.tri) return fail(AHOC_EUNSUPPORTED, "a triharmonic plan returns Q only (v must be NULL)");
   CK(cudaMemcpyAsync(q, p->Q, (size_t)p->g.nb * p->g.ngamma * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
@@ -2653,6 +2676,7 @@ extern "C" {
 // Algorithm 1, Main procedure (FP64, or FP32 inner solves with FP64 refinement).
 ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, ahoc_info* info) {
   if (!p || !f || !u) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(f) || misaligned(u)) return fail(AHOC_EINVAL, kAlignMsg);
   if (!(tol > 0) || !std::isfinite(tol)) return fail(AHOC_EINVAL, "tol must be positive");
   const auto t0 = std::chrono::steady_clock::now();
   CKS(solve_internal(p, f, u, tol));
@@ -2698,6 +2722,7 @@ ahoc_status ahoc_solve(ahoc_plan* p, const double* f, double* u, double tol, aho
 ahoc_status ahoc_solve_from(ahoc_plan* p, const double* f, const double* q0, double* u, double tol,
                             ahoc_info* info) {
   if (!p || !f || !q0 || !u) return fail(AHOC_EINVAL, "NULL argument");
+  if (misaligned(q0)) return fail(AHOC_EINVAL, kAlignMsg);
   if (p->o.prec != AHOC_FP64)
     return fail(AHOC_EUNSUPPORTED,
                 "an initial Q is taken by FP64 plans (a mixed plan's first step solves for all of u)");

@@ -143,3 +143,23 @@ def test_struct_layouts_and_constants_match_header(tmp_path):
             assert (off, size) == (desc.offset, desc.size), (sname, fname, off, size, desc.offset, desc.size)
     for n in consts:
         assert int(out[n]) == getattr(ahoc, n), n
+
+
+def test_misaligned_device_arrays_are_refused_on_the_host():
+    """A device array of doubles at an address that is not a multiple of 8
+    is refused with AHOC_EINVAL before any launch (an 8-byte load from it
+    would fault the kernel)."""
+    L = ahoc.lib()
+    n = (C.c_int64 * 2)(16, 16)
+    lo = (C.c_double * 2)(0.0, 0.0)
+    hi = (C.c_double * 2)(1.0, 1.0)
+    h = C.c_void_p()
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(260), None, None, None) == ahoc.AHOC_EINVAL
+    assert b"aligned" in L.ahoc_last_error()
+    bd = ahoc.ahoc_bdata()
+    bd.g_N = C.c_void_p(1028)
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), C.byref(bd), None, None) == ahoc.AHOC_EINVAL
+    assert b"aligned" in L.ahoc_last_error()
+    assert h.value is None
+    assert L.ahoc_poisson_noalloc(2, n, lo, hi, C.c_void_p(4100), C.c_void_p(8192), None) == ahoc.AHOC_EINVAL
+    assert b"aligned" in L.ahoc_last_error()
