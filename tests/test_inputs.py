@@ -37,3 +37,28 @@ def test_request_stream_mix():
     assert {r.N for r in s if r.dim == 3} == set(inputs.SERVE_3D)
     assert all(0 <= v <= 4 for r in s for v in r.m)
     assert s[17] == inputs.request_stream(2000, 50.0, seed=5)[17]  # reproducible
+
+
+@pytest.mark.parametrize("dim,M,K,A,seed", [(2, 8, 6, 0.4, 1), (3, 6, 4, 0.4, 2), (3, 6, 4, 0.5, 3)])
+def test_fourier_coefficient_recipe(dim, M, K, A, seed):
+    """The seeded coefficient fields of the Fourier-coefficient workloads:
+    modes drawn with 0 <= k_a <= K and k != 0, alpha = 1 + A phi / max|phi|
+    with the maximum taken on a fixed lattice (1024 points per axis in 2D,
+    128 in 3D), so alpha reaches 1 +- A there, stays positive everywhere,
+    does not depend on the solve's grid, and is the same for the same seed."""
+    modes = inputs.fourier_modes(dim, M, K, seed)
+    assert len(modes) == M
+    assert all(any(k) and all(0 <= v <= K for v in k) for k, _, _ in modes)
+    assert all(-1 <= c <= 1 and 0 <= th <= 2 * np.pi for _, c, th in modes)
+    assert modes == inputs.fourier_modes(dim, M, K, seed)
+    alpha = sp.lambdify(inputs.X[:dim], inputs.fourier_alpha(dim, M, K, A, seed), "numpy")
+    L = 1024 if dim == 2 else 128
+    t = np.linspace(0.0, 1.0, L + 1)
+    lat = alpha(*np.meshgrid(*([t] * dim), indexing="ij"))
+    assert abs(np.max(np.abs(lat - 1)) - A) < 1e-12
+    pts = np.random.default_rng(0).uniform(size=(dim, 20000))
+    vals = alpha(*pts)
+    # between lattice points |phi| may exceed its lattice maximum by the
+    # lattice's second-order error only
+    assert np.max(np.abs(vals - 1)) < A * (1 + 2e-3)
+    assert np.min(vals) > 0
