@@ -458,3 +458,20 @@ def test_schur_rhs_scale_between_grids(name):
         if prev is not None:
             assert worst < prev / 2, (worst, prev)
         prev = worst
+
+
+def test_indefinite_shift_converges():
+    """The operator of the high-wavenumber problem (Sec. 4.2): alpha = 1,
+    beta = -k^2, so the v-equation is a Helmholtz equation with an indefinite
+    shift.  The oracle's assembled system still converges at fourth order to
+    a manufactured solution (k = 10)."""
+    x, y = inputs.X[:2]
+    u = sp.sin(sp.pi * x) ** 2 * sp.sin(sp.pi * y) ** 2 * sp.sin(3 * sp.pi * x)
+    prob = inputs.Problem("indefinite", 2, sp.Integer(1), u, beta=-100)
+    errs = []
+    for N in (32, 64, 128):
+        d = inputs.sample(prob, [N, N])
+        sol = coupled.solve_direct(coupled.assemble(d), d)
+        errs.append(np.max(np.abs(sol.U - d["u_exact"])))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.8, rates
