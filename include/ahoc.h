@@ -153,7 +153,9 @@ typedef struct {
                              beta term of Eq. 1.  The v-equation is -L_h V + gamma M V = M f
                              (Sec. 2.2 with beta / alpha constant, e.g. constant alpha and
                              beta): its Poisson solves take the shifted eigenvalues
-                             -lambda_L + gamma lambda_M.  gamma >= 0; with variable_beta set,
+                             -lambda_L + gamma lambda_M.  gamma >= 0 (a negative gamma, the
+                             indefinite Helmholtz v-equation of the high-wavenumber problem
+                             of Sec. 4.2, gives AHOC_EUNSUPPORTED); with variable_beta set,
                              the reference shift of the iterative v-solve                      */
   int no_graphs;          /* [0] 0: each GMRES iteration (mask and scalar uploads, the
                              normalisation of v_j, the preconditioner, the Schur matvec, CGS2
@@ -209,7 +211,8 @@ typedef struct {
                              gamma = beta / alpha over every point of every problem
                              (bd->beta; none: beta = 0), one value everywhere gives the
                              constant shift gamma, several give variable beta with the mean
-                             of gamma as the reference shift.  Uses a few KB of temporary
+                             of gamma as the reference shift (gamma < 0 anywhere:
+                             AHOC_EUNSUPPORTED, as for opts.shift).  Uses a few KB of temporary
                              device memory (cudaMalloc) and synchronises the stream; with it,
                              ahoc_workspace_bytes sizes for the variable-beta class.          */
   int first32;            /* [0] AHOC_MIXED: 0 takes the first correction (the whole solution)

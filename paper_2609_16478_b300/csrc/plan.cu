@@ -52,6 +52,12 @@ bool bdata_misaligned(const ahoc_bdata* bd) {
 
 constexpr const char* kAlignMsg = "device arrays of doubles must be 8-byte aligned";
 
+// beta / alpha < 0 (the high-wavenumber problem of Sec. 4.2, beta = -k^2)
+// makes the v-equation a Helmholtz equation with an indefinite shift, whose
+// per-mode factors along the last axis are not diagonally dominant
+constexpr const char* kIndefiniteMsg =
+    "beta / alpha < 0 (an indefinite Helmholtz v-equation) is outside the exact last-axis factorisation";
+
 // Serialises CUDA graph captures with the library's own synchronising entry
 // points (plan creation, loading, destruction: pinned allocations, frees,
 // stream synchronisations), which would otherwise invalidate a capture open
@@ -140,7 +146,8 @@ ahoc_status read_opts(const ahoc_opts* o, Opts* out) {
   if (d.restart > 1000) return fail(AHOC_EINVAL, "restart > 1000");
   if (d.batch > 4096) return fail(AHOC_EINVAL, "batch > 4096");
   if (d.navier < 0 || d.navier > 63) return fail(AHOC_EINVAL, "navier must be a mask of faces 0..5");
-  if (!(d.shift >= 0) || !std::isfinite(d.shift)) return fail(AHOC_EINVAL, "shift must be finite and >= 0");
+  if (!std::isfinite(d.shift)) return fail(AHOC_EINVAL, "shift must be finite");
+  if (d.shift < 0) return fail(AHOC_EUNSUPPORTED, kIndefiniteMsg);
   if (d.levels < -1 || d.levels > 8) return fail(AHOC_EINVAL, "levels must be -1 (automatic) or 0..8");
   if (d.workspace && (reinterpret_cast<uintptr_t>(d.workspace) & 255))
     return fail(AHOC_EINVAL, "workspace must be 256-byte aligned");
@@ -1853,7 +1860,7 @@ ahoc_status derive_shift(const Geom& g, Opts& o, const double* alpha, const ahoc
     sum += h[3 * b + 2];
   }
   if (!std::isfinite(mn) || !std::isfinite(mx) || !std::isfinite(sum)) return fail(AHOC_EINVAL, "beta/alpha not finite");
-  if (mn < 0) return fail(AHOC_EINVAL, "beta/alpha must be >= 0");
+  if (mn < 0) return fail(AHOC_EUNSUPPORTED, kIndefiniteMsg);
   if (mn == mx) {
     o.shift = mn;
   } else {

@@ -163,3 +163,24 @@ def test_misaligned_device_arrays_are_refused_on_the_host():
     assert h.value is None
     assert L.ahoc_poisson_noalloc(2, n, lo, hi, C.c_void_p(4100), C.c_void_p(8192), None) == ahoc.AHOC_EINVAL
     assert b"aligned" in L.ahoc_last_error()
+
+
+def test_indefinite_shift_is_unsupported():
+    """beta / alpha < 0 (the high-wavenumber problem's indefinite Helmholtz
+    v-equation) is a valid problem outside the library: AHOC_EUNSUPPORTED,
+    before any allocation; a non-finite shift is an invalid argument."""
+    L = ahoc.lib()
+    n = (C.c_int64 * 2)(64, 64)
+    lo = (C.c_double * 2)(0.0, 0.0)
+    hi = (C.c_double * 2)(1.0, 1.0)
+    h = C.c_void_p()
+    o = ahoc.ahoc_opts()
+    o.shift = -100.0
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), None, C.byref(o), None) == \
+        ahoc.AHOC_EUNSUPPORTED
+    assert b"indefinite" in L.ahoc_last_error()
+    nbytes = C.c_size_t()
+    assert L.ahoc_workspace_bytes(2, n, C.byref(o), C.byref(nbytes)) == ahoc.AHOC_EUNSUPPORTED
+    o.shift = float("nan")
+    assert L.ahoc_plan_create(C.byref(h), 2, n, lo, hi, C.c_void_p(256), None, C.byref(o), None) == ahoc.AHOC_EINVAL
+    assert h.value is None
