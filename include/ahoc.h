@@ -330,9 +330,11 @@ ahoc_status ahoc_matvec(ahoc_plan* p, const double* q, double* y);
  * (device, full grid); b: device face array. */
 ahoc_status ahoc_schur_rhs(ahoc_plan* p, const double* f, double* b);
 
-/* Copy the augmented unknowns Q of the last successful ahoc_solve into q
- * (device face array), and, if v is not NULL, V on the full grid (faces =
- * Q, edges and corners = v_edge) into v.  AHOC_EINVAL before any solve. */
+/* Copy the augmented unknowns Q (v = alpha Laplace u on the face interiors,
+ * Sec. 2.2; the solution of S_h Q = b, Lemma 1) of the last successful
+ * ahoc_solve into q (device face array), and, if v is not NULL, V on the
+ * full grid (faces = Q, edges and corners = v_edge) into v.  Caller-owned
+ * outputs, one per problem of the plan.  AHOC_EINVAL before any solve. */
 ahoc_status ahoc_last_qv(ahoc_plan* p, double* q, double* v);
 
 /* Component entry points (the building blocks of SchurMatVec) ------------- */
@@ -374,9 +376,14 @@ ahoc_status ahoc_poisson(ahoc_plan* p, const double* rhs, double* w);
 ahoc_status ahoc_poisson_noalloc(int dim, const int64_t* N, const double* lo, const double* hi,
                                  const double* rhs, double* w, void* stream);
 
+/* Free a plan and everything it allocated (workspace unless caller-owned,
+ * coarse levels, staging grids, streams and graphs); NULL is accepted.
+ * Synchronises the plan's stream first.  No counterpart in the paper. */
 ahoc_status ahoc_plan_destroy(ahoc_plan* p);
 
-/* Batched plans (serving) ---------------------------------------------------- */
+/* Batched plans (serving; no counterpart in the paper, which solves one
+ * problem at a time: a plan of opts.batch same-shape problems runs every
+ * step of Algorithm 1 for all of them in each launch) ---------------------- */
 
 /* Replace problem b's coefficient and boundary data (single-problem sizes,
  * device) in an existing plan, coarse levels included; the shape tables and
@@ -411,11 +418,14 @@ ahoc_status ahoc_tune_set(int kind, int dim, int64_t N, int prec, int value);
 /* the table entry (0: built-in), or -1 for arguments out of range */
 int ahoc_tune_get(int kind, int dim, int64_t N, int prec);
 
-/* Static strings; never NULL. */
+/* Error reporting (no counterpart in the paper): the name of a status, and
+ * a one-line description of the calling thread's most recent failure.
+ * Static or thread-local strings owned by the library; never NULL. */
 const char* ahoc_status_string(ahoc_status s);
 const char* ahoc_last_error(void);
 
-/* Length of the face arrays of a plan. */
+/* n_gamma, the number of augmented unknowns Q of one problem (the face
+ * relative interiors, Sec. 2.2): the length of a face array.  -1 for NULL. */
 int64_t ahoc_n_gamma(const ahoc_plan* p);
 
 #ifdef __cplusplus
